@@ -1,0 +1,299 @@
+"""Pins of the FP64 CPU oracle against facts fixed outside the oracle itself.
+
+Each test cites the passage or the mathematics that fixes the expected value.
+None of these tests touches a GPU or the CUDA library.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests._golden import paper_values
+
+
+# --------------------------------------------------------------------------
+# Philox4x64-10: the published generator, checked against numpy's own
+# implementation of it (numpy.random.Philox increments the counter before
+# each block, hence the +1 on c0).
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("ctr,key", [((0, 0, 0, 0), (0, 0)), ((7, 3, 99, 1), (12345, 0)),
+                                     ((2**64 - 2, 2**63, 5, 4), (2**64 - 1, 17))])
+def test_philox_matches_numpy(ctr, key):
+    bg = np.random.Philox(key=np.array(key, dtype=np.uint64),
+                          counter=np.array(ctr, dtype=np.uint64))
+    ref = [int(x) for x in bg.random_raw(4)]
+    c = list(ctr)
+    c[0] = (c[0] + 1) % 2**64
+    assert O.philox4x64(c, key) == ref
+
+
+# --------------------------------------------------------------------------
+# Haar U(4) sampler (Methods, "Sampling U(d^2)"): unitary, and the Haar
+# moments E|U_ij|^2 = 1/d, E|U_ij|^4 = 2/(d(d+1)), E Tr U = 0, E|Tr U|^2 = 1.
+# --------------------------------------------------------------------------
+def test_haar_sampler_unitary_and_moments():
+    N = 12000
+    mats = np.array([O.haar_u4(11, p, p % 2, p // 2) for p in range(N)])
+    err = np.abs(np.einsum("nji,njk->nik", mats.conj(), mats) - np.eye(4)).max()
+    assert err < 1e-13
+    a2 = np.abs(mats) ** 2
+    m2, m4 = a2.mean(), (a2 ** 2).mean()
+    # 16 correlated entries per matrix: use per-matrix means for the error bar
+    se2 = a2.mean(axis=(1, 2)).std() / math.sqrt(N)
+    se4 = (a2 ** 2).mean(axis=(1, 2)).std() / math.sqrt(N)
+    assert abs(m2 - 0.25) < 5 * se2 + 1e-12
+    assert abs(m4 - 0.1) < 5 * se4
+    tr = np.trace(mats, axis1=1, axis2=2)
+    assert abs(tr.mean()) < 5 / math.sqrt(N)
+    t2 = np.abs(tr) ** 2
+    assert abs(t2.mean() - 1) < 5 * t2.std() / math.sqrt(N)
+
+
+def _lis_le(perm, d):
+    best = []
+    for x in perm:
+        i = np.searchsorted(best, x)
+        if i == len(best):
+            best.append(x)
+        else:
+            best[i] = x
+    return len(best) <= d
+
+
+def haar_frame_potential(k, d):
+    """E|Tr U|^{2k} over Haar U(d) = number of permutations of k elements with
+    no increasing subsequence longer than d (Rains 1998); equals k! for k <= d."""
+    return sum(1 for p in itertools.permutations(range(k)) if _lis_le(p, d))
+
+
+def test_haar_count_reduces_to_paper_value():
+    pv = paper_values()
+    for k in range(1, 5):
+        assert haar_frame_potential(k, 4) == pv[f"haar_F_k{k}"] == math.factorial(k)
+
+
+def test_single_haar_gate_frame_potential():
+    # n = 2, l = 1 is one Haar U(4) gate: F^(k) is the Haar value (Supp.,
+    # "Validation of sampling Haar random two-qubit unitaries"); k! holds
+    # for k <= d = 4, beyond that the exact Haar value applies.
+    d = O.desc(O.PARALLEL, 2, 1, seed=2024)
+    tr = O.trace_batch(d, 0, 200000, "dense", threads=8)
+    F, se = O.moments(tr, 6)
+    for k in range(1, 7):
+        exact = haar_frame_potential(k, 4)
+        assert abs(F[k - 1] - exact) < 5 * se[k - 1], (k, F[k - 1], exact, se[k - 1])
+
+
+# --------------------------------------------------------------------------
+# Brute force: dense 2^n matrices vs variable elimination, all ensembles.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,n,dmin,dmax,extra", [
+    (O.PARALLEL, 6, 1, 5, {}), (O.PARALLEL, 7, 1, 4, {}), (O.PARALLEL, 8, 4, 4, {}),
+    (O.HEA, 5, 1, 4, {}), (O.HEA, 6, 2, 3, {}),
+    (O.LOCAL, 6, 1, 1, dict(T_min=4, T_max=24, T_step=4)),
+    (O.LOCAL, 7, 1, 1, dict(T_min=10, T_max=30, T_step=10)),
+])
+def test_dense_matches_variable_elimination(kind, n, dmin, dmax, extra):
+    d = O.desc(kind, n, dmin, dmax, seed=77 + n, **extra)
+    for p in range(6):
+        a = O.trace_pair(d, p, "dense")
+        b = O.trace_pair(d, p, "ve")
+        assert abs(a - b) <= 1e-12 * max(1.0, abs(a))
+
+
+# --------------------------------------------------------------------------
+# The paper's amplitude formulation (Sec. "Algorithm description"):
+# <Psi| U^dagger V |Psi> with |Psi> = M|0> and M = prod_j CNOT_{a_j,t_j} H_{a_j}
+# equals Tr(U^dagger V) / 2^n.  Built here with numpy Kronecker products,
+# independently of the oracle's C code.
+# --------------------------------------------------------------------------
+def _kron_all(ms):
+    out = np.array([[1.0 + 0j]])
+    for m in ms:
+        out = np.kron(out, m)
+    return out
+
+
+def _dense_from_gates(n, gates):
+    U = np.eye(2 ** n, dtype=complex)
+    for kind, q, m in gates:
+        if kind == O.OP_GATE1:
+            full = _kron_all([np.eye(2)] * q + [m] + [np.eye(2)] * (n - q - 1))
+        else:
+            mm = np.diag(m) if kind == O.OP_DIAG2 else m
+            full = _kron_all([np.eye(2)] * q + [mm] + [np.eye(2)] * (n - q - 2))
+        U = full @ U
+    return U
+
+
+@pytest.mark.parametrize("kind,n,depth", [(O.PARALLEL, 3, 3), (O.PARALLEL, 4, 2), (O.HEA, 3, 2)])
+def test_ancilla_amplitude_identity(kind, n, depth):
+    d = O.desc(kind, n, depth, seed=5)
+    U = _dense_from_gates(n, O.circuit(d, 0, 0))
+    V = _dense_from_gates(n, O.circuit(d, 0, 1))
+    # registers ordered (a_0..a_{n-1}, t_0..t_{n-1})
+    H = np.array([[1, 1], [1, -1]]) / math.sqrt(2)
+    N2 = 2 * n
+    psi = np.zeros(2 ** N2, dtype=complex)
+    psi[0] = 1
+    for j in range(n):
+        psi = _kron_all([np.eye(2)] * j + [H] + [np.eye(2)] * (N2 - j - 1)) @ psi
+    for j in range(n):   # CNOT control a_j (bit position n-1-j from the top half), target t_j
+        idx = np.arange(2 ** N2)
+        ca = (idx >> (N2 - 1 - j)) & 1
+        flip = idx ^ (ca << (N2 - 1 - (n + j)))
+        psi = psi[flip]
+    W = np.kron(np.eye(2 ** n), U.conj().T @ V)
+    amp = np.vdot(psi, W @ psi)
+    tr = O.trace_pair(d, 0, "dense")
+    assert abs(amp * 2 ** n - tr) < 1e-12
+    assert abs(np.trace(U.conj().T @ V) - tr) < 1e-12
+
+
+def test_fig3b_tensor_identity():
+    # H_{m0} CNOT_{m i 0} CNOT_{m 0 j} H_{0 m} summed over m (Fig. 3b).  The
+    # figure's derivation states delta_ij; with the 1/sqrt(2) of each Hadamard
+    # kept it is delta_ij / 2, the per-qubit factor behind the 2^-n of the
+    # amplitude identity in the same section (reading recorded with the others).
+    H = np.array([[1, 1], [1, -1]]) / math.sqrt(2)
+    C = np.zeros((2, 2, 2))   # C[k, i, j]: control k, target out i, target in j
+    for k in range(2):
+        for i in range(2):
+            for j in range(2):
+                C[k, i, j] = (k == 0) * (i == j) + (k == 1) * (i != j)
+    T = np.einsum("m,mi,mj,m->ij", H[:, 0], C[:, :, 0], C[:, 0, :], H[0, :])
+    assert np.allclose(T, np.eye(2) / 2)
+
+
+# --------------------------------------------------------------------------
+# Invariants and closed forms at full size (n = 50).
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,n,depth,extra", [(O.PARALLEL, 50, 5, {}), (O.HEA, 50, 4, {}),
+                                                (O.LOCAL, 20, 1, dict(T_min=40, T_max=40))])
+def test_self_pair_trace_is_dimension(kind, n, depth, extra):
+    # Tr(U^dagger U) = Tr(I) = 2^n
+    d = O.desc(kind, n, depth, seed=9, self_pair=True, **extra)
+    tr = O.trace_pair(d, 3, "ve")
+    assert abs(tr - 2.0 ** n) <= 1e-10 * 2.0 ** n
+
+
+@pytest.mark.parametrize("n", [7, 8, 50])
+def test_brickwork_one_layer_product_form(n):
+    # l = 1: U^dagger V is a product of independent 2-qubit gates, so the trace
+    # factorises into per-gate traces; an untouched qubit (odd n) gives Tr(I_2) = 2.
+    d = O.desc(O.PARALLEL, n, 1, seed=31)
+    for p in range(3):
+        U, V = O.circuit(d, p, 0), O.circuit(d, p, 1)
+        ref = np.prod([np.trace(gu[2].conj().T @ gv[2]) for gu, gv in zip(U, V)]) * 2 ** (n % 2)
+        assert abs(O.trace_pair(d, p, "ve") - ref) <= 1e-12 * max(1, abs(ref))
+
+
+def _hea_angles(seed, pair, which, t, q):
+    x = O.philox4x64([t, q, pair, which], [seed, 0])
+    return [2 * math.pi * ((v >> 11) * 2.0 ** -53) for v in x[:2]]
+
+
+def test_hea_one_layer_closed_form():
+    # L = 1: the CZ ladders cancel, Tr = prod_q Tr(R_q^U^dagger R_q^V) with
+    # R = RY(theta) RZ(phi), whose trace is 2 cos(dtheta/2) cos(dphi/2).
+    n, seed = 50, 13
+    d = O.desc(O.HEA, n, 1, seed=seed)
+    for p in range(3):
+        ref = 1.0
+        for q in range(n):
+            tu, pu = _hea_angles(seed, p, 0, 0, q)
+            tv, pv = _hea_angles(seed, p, 1, 0, q)
+            ref *= 2 * math.cos((tv - tu) / 2) * math.cos((pv - pu) / 2)
+        assert abs(O.trace_pair(d, p, "ve") - ref) <= 1e-12 * max(1, abs(ref))
+
+
+@pytest.mark.parametrize("as_kind", [O.OP_GATE2, O.OP_DIAG2])
+def test_diagonal_gates_transfer_matrix(as_kind):
+    # Diagonal 2-qubit gates: U^dagger V is diagonal, Tr = sum_x prod_g phase_g(x),
+    # a classical 1D transfer-matrix product 1^T M_0 ... M_{n-2} 1.
+    rng = np.random.default_rng(3)
+    n, layers = 30, 4
+    U, V = [], []
+    for circ in (U, V):
+        for t in range(layers):
+            for b in range(t % 2, n - 1, 2):
+                ph = np.exp(1j * rng.uniform(0, 2 * np.pi, 4))
+                circ.append((as_kind, b, np.diag(ph) if as_kind == O.OP_GATE2 else ph))
+    phase = {b: np.ones(4, dtype=complex) for b in range(n - 1)}
+    for (_, b, m) in U:
+        phase[b] *= np.conj(np.diag(m) if as_kind == O.OP_GATE2 else m)
+    for (_, b, m) in V:
+        phase[b] *= np.diag(m) if as_kind == O.OP_GATE2 else m
+    vec = np.ones(2, dtype=complex)
+    for b in range(n - 1):
+        M = phase[b].reshape(2, 2)        # M[x_b, x_{b+1}]
+        vec = vec @ M
+    ref = vec.sum()
+    got = O.trace_ops(n, U, V, "ve")
+    assert abs(got - ref) <= 1e-11 * max(1, abs(ref))
+
+
+# --------------------------------------------------------------------------
+# Exact ensemble F^(2) of brickwork circuits (Weingarten transfer matrix).
+# --------------------------------------------------------------------------
+def test_weingarten_two_qubits_is_haar():
+    # n = 2: a product of independent Haar U(4) gates is Haar, F^(2) = 2! = 2.
+    for l in range(1, 7):
+        assert abs(O.weingarten_f2_brickwork(2, l) - 2.0) < 1e-12
+
+
+def test_weingarten_one_layer_and_paper_bound():
+    pv = paper_values()
+    for n in range(2, 13):
+        ng = n // 2
+        exact_l1 = 2.0 ** ng * 16.0 ** (n % 2)
+        assert abs(O.weingarten_f2_brickwork(n, 1) - exact_l1) < 1e-9 * exact_l1
+    # Eq. theory_eq: F^(2) < 2 (1 + (2q/(q^2+1))^{2(l-1)})^{n_g - 1}, n_g = floor(n/2), q = 2,
+    # an equality at l = 1 for even n (bound = 2^{n_g}).
+    q = 2
+    for n in range(4, 13, 2):
+        ng = n // 2
+        for l in range(1, 7):
+            bound = 2 * (1 + (2 * q / (q * q + 1)) ** (2 * (l - 1))) ** (ng - 1)
+            f = O.weingarten_f2_brickwork(n, l)
+            if l == 1:
+                assert abs(f - bound) < 1e-9 * bound
+            else:
+                assert f < bound
+    # the paper's slope constant from the same formula: C = 1/log((q^2+1)/2q),
+    # layers grow as 2 C log(q) per qubit (Eq. k=2)
+    C = 1 / math.log((q * q + 1) / (2 * q))
+    assert abs(2 * C * math.log(q) - pv["theory_slope_k2"]) < 0.05
+
+
+@pytest.mark.parametrize("n,l", [(4, 2), (4, 3), (5, 2), (6, 2)])
+def test_weingarten_matches_monte_carlo(n, l):
+    d = O.desc(O.PARALLEL, n, l, seed=100 + 10 * n + l)
+    tr = O.trace_batch(d, 0, 120000, "dense", threads=8)
+    F, se = O.moments(tr, 2)
+    assert abs(F[0] - 1.0) < 5 * se[0]              # brickwork with l >= 2 is a 1-design
+    exact = O.weingarten_f2_brickwork(n, l)
+    assert abs(F[1] - exact) < 5 * se[1], (F[1], exact, se[1])
+
+
+def test_hea_two_qubits_one_layer_moments():
+    # per qubit |2 cos(a/2) cos(b/2)|^{2k} averages to (C(2k,k)/2^k)^2 / ... ->
+    # E = (binom(2k,k)^2 / 4^k) per qubit; two qubits multiply.
+    d = O.desc(O.HEA, 2, 1, seed=8)
+    tr = O.trace_batch(d, 0, 100000, "dense", threads=8)
+    F, se = O.moments(tr, 3)
+    for k in range(1, 4):
+        exact = (math.comb(2 * k, k) ** 2 / 4 ** k) ** 2
+        assert abs(F[k - 1] - exact) < 5 * se[k - 1], (k, F[k - 1], exact)
+
+
+def test_moments_match_numpy():
+    rng = np.random.default_rng(0)
+    tr = rng.normal(size=5000) + 1j * rng.normal(size=5000)
+    F, se = O.moments(tr, 3)
+    for k in range(1, 4):
+        x = np.abs(tr) ** (2 * k)
+        assert abs(F[k - 1] - x.mean()) < 1e-12 * x.mean()
+        assert abs(se[k - 1] - x.std(ddof=1) / math.sqrt(len(x))) < 1e-10 * se[k - 1]
