@@ -1,0 +1,300 @@
+#!/usr/bin/env python
+"""Throughput of Tr(U^dagger V) contractions at n = 50 on one or more GB300s.
+
+Workload: brickwork ("parallel") random circuits, n = 50 qubits on an open
+chain, depth l drawn uniformly from 2..10 per pair, Haar U(4) gates,
+100,000 pairs per step (a fresh range of pair indices every step).
+One step is the whole hot path over one batch: gate sampling, merging,
+factor tables, both boundary sweeps, the FP64 meet, and the FP64 moments of
+|Tr|^{2k}, k = 1..4, per depth group.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  `value` is device-timed (CUDA events on the
+library's stream); `e2e` is the same metric through fp_frame_potential, the
+call a user makes, with results returned to host memory.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Tr(U^dagger V) contractions/s at n=50 (brickwork, l=2..10)"
+WORK = dict(n=50, depth_min=2, depth_max=10, pairs=100_000, seed=4, k_max=4)
+SM_COUNT, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--pairs", type=int, default=WORK["pairs"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args, world):
+    return {"workload": "brickwork n=50, l uniform in 2..10 per pair, Haar U(4), "
+                        f"{args.pairs} pairs per step per GPU",
+            "n": WORK["n"], "depth": [WORK["depth_min"], WORK["depth_max"]], "pairs_per_step": args.pairs,
+            "k_max": WORK["k_max"], "precision": args.prec, "parallelism": f"pairs sharded over {world} GPU(s)",
+            "l2": "per-step device working set (sampled gates, tables, boundaries) is GBs, larger than L2"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reported baseline; the only use of oracle/ in this file)
+# ---------------------------------------------------------------------------
+def oracle_sample(first_pair, cores, max_depth=8):
+    """Pairs of the workload in index order, skipping those deeper than max_depth
+    (the oracle needs ~30 s for l = 9 and minutes for l = 10 at n = 50)."""
+    import oracle as O
+    d = O.desc(O.PARALLEL, WORK["n"], WORK["depth_min"], WORK["depth_max"], seed=WORK["seed"])
+    pairs, p = [], first_pair
+    while len(pairs) < 2 * cores:
+        if O.pair_depth(d, p) <= max_depth:
+            pairs.append(p)
+        p += 1
+    return d, pairs
+
+
+def oracle_time(first_pair, cores):
+    import numpy as np
+    import oracle as O
+    d, pairs = oracle_sample(first_pair, cores)
+    # one pair per thread: contiguous runs are not guaranteed, so time each pair range
+    t0 = time.perf_counter()
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda p: O.trace_batch(d, p, 1, "ve", threads=1), pairs))
+    dt = time.perf_counter() - t0
+    depths = [O.pair_depth(d, p) for p in pairs]
+    return len(pairs) / dt, dt, len(pairs), depths
+
+
+def cpu_baseline_obj(rate, cores, npairs, depths):
+    return {"value": rate, "unit": "contractions/s", "cores": cores, "kind": "oracle",
+            "sample": f"{npairs} pairs of the workload in index order with l<=8 (depths "
+                      f"{min(depths)}..{max(depths)}), one pair per thread, FP64 variable elimination; "
+                      "pairs with l=9,10 left out (the oracle needs ~30 s and minutes per such pair)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    first = 10_000_000
+    for _ in range(args.warmup):
+        oracle_time(first, cores)
+        first += 4 * cores
+    rates, times, last = [], [], None
+    for _ in range(args.steps):
+        r, dt, npairs, depths = oracle_time(first, cores)
+        first += 4 * cores
+        rates.append(r)
+        times.append(dt)
+        last = (npairs, depths)
+    value = args.steps / sum(t / (last[0]) for t in times) if times else 0.0
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "contractions/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded circuit pairs)",
+            "config": workload_config(args, args.gpus),
+            "cpu_baseline": cpu_baseline_obj(value, cores, last[0], last[1]),
+            "e2e": {"value": value, "unit": "contractions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2205_09900_gb300 import build as fpbuild
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_2205_09900_gb300", "libfp_gb300.so")):
+        fpbuild.build()
+    if dist:
+        dist.barrier()
+    import paper_2205_09900_gb300 as fp
+
+    prec = fp.PREC_FP32 if args.prec == "fp32" else fp.PREC_FP64
+    stream = torch.cuda.current_stream()
+    P, K = args.pairs, WORK["k_max"]
+    ens = fp.Ensemble(fp.PARALLEL, WORK["n"], WORK["depth_min"], WORK["depth_max"], seed=WORK["seed"],
+                      flags=fp.FLAG_TIMING, stream=stream.cuda_stream)
+    ng = len(ens.groups())
+    tr = torch.empty(2 * P, dtype=torch.float64, device="cuda")
+    kap = torch.empty(P, dtype=torch.float64, device="cuda")
+    grp = torch.empty(P, dtype=torch.int32, device="cuda")
+    mom = torch.empty(ng * (2 * K + 1), dtype=torch.float64, device="cuda")
+
+    def first_of(step):
+        return (step * world + rank) * P
+
+    def step(s):
+        ens.trace_batch(first_of(s), P, prec, tr, kap, grp)
+        ens.reduce_moments(tr, grp, P, K, mom)
+
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+    ens.kernel_stats(reset=True)
+
+    clk = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(args.warmup, args.warmup + args.steps):
+        step(s)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ks = ens.kernel_stats(reset=True)
+    launches = int(sum(ks.launches[i] for i in range(8)))
+
+    # e2e: the public Monte Carlo call, results to host memory, host wall clock
+    e2e = None
+    if not args.no_e2e:
+        ens.frame_potential(first_of(args.warmup + args.steps), P, K, 0.0, prec)   # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            ens.frame_potential(first_of(args.warmup + args.steps + 1 + s), P, K, 0.0, prec)
+        dt = time.perf_counter() - t0
+        # host->device per step: PairInfo (40 B) + order (4 B) + group (4 B) per pair;
+        # device->host: kappa (8 B/pair, FP32 policy) + per-batch moments
+        batches = 0
+        b, done = 4096, 0
+        while done < P:
+            done += min(b, P - done)
+            batches += 1
+            b = min(b * 2, 1 << 20)
+        h2d = P * (40 + 4 + 4)
+        d2h = (P * 8 if prec == fp.PREC_FP32 else 0) + batches * ng * (2 * K + 1) * 8
+        e2e = {"value": world * P * args.steps / dt, "unit": "contractions/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    value = world * P * args.steps / (ms / 1e3)
+    # roofline of the dominant kernel class
+    cls = max(range(8), key=lambda i: ks.ms[i])
+    flops = 8.0 * ks.work[cls]                 # complex multiply-add = 8 real flops
+    achieved = flops / (ks.ms[cls] / 1e3) / 1e12 if ks.ms[cls] > 0 else 0.0
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    if prec == fp.PREC_FP64:
+        peak = peak / 64.0       # FP64 FMA rate is a small fraction of FP32 on this part
+    traffic = None
+    roof = {"bound": "alu", "kernel": fp.K_NAMES.get(cls, str(cls)), "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
+            "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+            "kernel_ms_share": ks.ms[cls] / ms if ms else None}
+
+    line = {"metric": METRIC, "value": value, "unit": "contractions/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec != fp.PREC_FP64 else "f64",
+            "data": "synthetic (seeded circuit pairs)", "config": workload_config(args, world),
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "kernel_ms": {fp.K_NAMES.get(i, str(i)): ks.ms[i] for i in range(8) if ks.launches[i]}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        r, dt, npairs, depths = oracle_time(10_000_000, cores)
+        line["cpu_baseline"] = cpu_baseline_obj(r, cores, npairs, depths)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ens.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * fp.h -- C ABI of the GB300 (sm_103a) frame-potential library.
+ *
+ * The library estimates the frame potential of a random-circuit ensemble,
+ *     F^(k) = E_{U,V} |Tr(U^dagger V)|^{2k}        (paper: Sec. "Frame potential", Eq. for F^(k))
+ * by Monte Carlo over sampled circuit pairs,
+ *     F^(k) ~= (1/N) sum_pairs |Tr(U^dagger V)|^{2k} (paper: Sec. "Algorithm description")
+ * where every sample is an exact contraction of the closed trace network of
+ * U^dagger V along the qubit (space) direction (paper: Sec. "Algorithm
+ * description", Fig. 3a).  Ensembles (paper: Fig. 2, Sec. "Results"):
+ *   FP_PARALLEL  brickwork of Haar U(4) gates on an open chain, layer t acting
+ *                on bonds (b, b+1) with b = (t-1) mod 2, b+2, ...;
+ *   FP_LOCAL     T Haar U(4) gates, each on a uniformly random bond;
+ *   FP_HEA       hardware-efficient ansatz: per layer RY(theta) RZ(phi) on every
+ *                qubit (theta, phi uniform in [0, 2 pi)), then CZ on every bond.
+ *
+ * Conventions: qubit 0 is the most significant bit of a basis index; a
+ * 2-qubit gate on bond (b, b+1) has matrix index (a_b a_{b+1}) with a_b the
+ * more significant bit; U = G_T ... G_1 (G_1 acts first); RY(t) =
+ * exp(-i t Y/2), RZ(p) = exp(-i p Z/2), RZ acts first within a layer.
+ *
+ * Random numbers.  Every draw is one block of Philox4x64-10 (Salmon et al.,
+ * SC'11) with key {seed, 0} and counter {c0, c1, pair, stream}, giving words
+ * x0..x3:
+ *   Haar gate g of circuit w (0 = U, 1 = V): c0 = 0..7, c1 = g, stream = w;
+ *     entry k = 4r+c of the 4x4 complex Gaussian uses block k/2, words
+ *     (x0,x1) for even k, (x2,x3) for odd k: u1 = ((xa>>11)+1) 2^-53,
+ *     u2 = (xb>>11) 2^-53, Z_k = sqrt(-2 ln u1) e^{2 pi i u2} / sqrt 2; the gate
+ *     is Q of Z = QR with R's diagonal made positive real (Haar measure).
+ *   Local bond of gate g of circuit w: c0 = 0, c1 = g, stream = 2+w,
+ *     bond = ((x0 >> 32)(n-1)) >> 32.
+ *   Per-pair depth (l or L) or gate count T: c0 = c1 = 0, stream = 4,
+ *     choice = ((x0 >> 32) * n_choices) >> 32.
+ *   HEA angles of circuit w, layer t (0-based), qubit q: c0 = t, c1 = q,
+ *     stream = w: theta = 2 pi (x0>>11) 2^-53, phi = 2 pi (x1>>11) 2^-53.
+ *   FP_FLAG_DIAGONAL_GATES replaces each Haar gate g of circuit w by
+ *     diag(e^{i 2 pi u_j}), u_j = (x_j >> 11) 2^-53 from c0 = 0, c1 = g, stream = w.
+ * Pair p of an ensemble is therefore fully determined by (seed, p).
+ *
+ * Memory and ownership.  The library owns ensembles and their device
+ * workspaces.  The caller owns every output array.  An output pointer may be
+ * host memory (pageable or pinned) or device memory (e.g. a PyTorch tensor's
+ * data_ptr()); the library detects which.  All device work is ordered on the
+ * stream given at creation (NULL = the legacy default stream).  Every call
+ * returns after its results are in the caller's arrays.
+ *
+ * Errors.  Calls return an fp_status; nothing is thrown across the ABI.
+ * fp_last_error() gives a thread-local message for the last failing call on
+ * the calling thread.  A failed call leaves caller arrays unspecified and the
+ * ensemble usable.
+ */
+#ifndef FP_H
+#define FP_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FP_OK = 0,
+    FP_ERR_ARG = -1,          /* invalid argument */
+    FP_ERR_CUDA = -2,         /* CUDA runtime error (message in fp_last_error) */
+    FP_ERR_OOM = -3,          /* device or host allocation failed */
+    FP_ERR_TIMEOUT = -4,      /* a bounded device wait ran out */
+    FP_ERR_INFEASIBLE = -5    /* a pair's boundary exceeds FP_MAX_STATE_BITS */
+} fp_status;
+
+typedef enum { FP_PARALLEL = 0, FP_LOCAL = 1, FP_HEA = 2 } fp_kind;
+
+/* Arithmetic of the contraction.  The final boundary dot product, the
+ * |Tr|^{2k} powers and all Monte Carlo moments are FP64 in every mode. */
+typedef enum {
+    FP_PREC_FP64 = 0,         /* boundary tensors and gate maps in FP64 */
+    FP_PREC_FP32 = 1,         /* boundary tensors and gate maps in FP32 (FFMA),
+                                 FP64 meet and reduction; a pair whose
+                                 cancellation ratio exceeds kappa_max is
+                                 recontracted in FP64 */
+    FP_PREC_FP32_RAW = 2      /* FP32 as above without the FP64 recontraction */
+} fp_prec;
+
+enum {
+    FP_FLAG_SELF_PAIR = 1,        /* V := U for every pair (Tr = 2^n exactly) */
+    FP_FLAG_DIAGONAL_GATES = 2,   /* FP_PARALLEL/FP_LOCAL with random diagonal gates */
+    FP_FLAG_GENERIC_ONLY = 4,     /* never use the specialised brickwork kernels */
+    FP_FLAG_TIMING = 8            /* record CUDA-event time of every launch (fp_kernel_stats_get) */
+};
+
+/* Kernel classes of fp_kernel_stats. */
+enum {
+    FP_K_SAMPLE = 0,      /* gate sampler */
+    FP_K_MERGE = 1,       /* gate merging */
+    FP_K_TABLES = 2,      /* factor tables */
+    FP_K_SWEEP = 3,       /* generic boundary sweep + meet */
+    FP_K_BRICK = 4,       /* brickwork boundary sweep + meet */
+    FP_K_MOMENTS = 5,     /* Monte Carlo moments */
+    FP_K_CLASSES = 8
+};
+
+#define FP_MAX_STATE_BITS 24      /* largest boundary: 2^24 amplitudes per side */
+#define FP_MAX_KMAX 8
+
+typedef struct {
+    int32_t kind;             /* fp_kind */
+    int32_t n;                /* qubits, 2 <= n <= 64 */
+    int32_t depth_min;        /* l (FP_PARALLEL) or L (FP_HEA), >= 1 */
+    int32_t depth_max;        /* >= depth_min; each pair draws its depth uniformly */
+    int32_t T_min, T_max, T_step;   /* FP_LOCAL: T drawn uniformly from
+                                       {T_min, T_min+T_step, ..., <= T_max} */
+    int32_t flags;            /* FP_FLAG_* */
+    uint64_t seed;
+    double kappa_max;         /* FP_PREC_FP32 recontraction threshold; <= 0: 1e3 */
+    uint64_t workspace_bytes; /* device workspace cap; 0: library default */
+} fp_ensemble_desc;
+
+typedef struct fp_ensemble fp_ensemble;
+
+/* Per-run statistics of fp_frame_potential. */
+typedef struct {
+    uint64_t pairs;           /* pairs contracted */
+    uint64_t fp64_recontracted;   /* pairs moved to FP64 by the kappa policy */
+    double gpu_seconds;       /* device time of the contraction batches */
+    double max_kappa;         /* largest cancellation ratio seen */
+    int32_t n_groups;         /* groups reported (depth or T values) */
+    int32_t reached_target;   /* 1 if every group met target_rel_stderr on F^(2) */
+} fp_run_stats;
+
+/* Per-kernel-class counters, accumulated while FP_FLAG_TIMING is set. */
+typedef struct {
+    double ms[FP_K_CLASSES];          /* device milliseconds (CUDA events on the ensemble's stream) */
+    uint64_t launches[FP_K_CLASSES];  /* kernel launches */
+    double work[FP_K_CLASSES];        /* algorithmic work: complex multiply-adds for the sweep
+                                         classes, pairs for the others */
+    uint64_t pairs;                   /* pairs contracted */
+} fp_kernel_stats;
+
+/* Create an ensemble.  `cuda_stream` is a cudaStream_t (NULL: default stream).
+ * Validates the descriptor (FP_ERR_ARG) and allocates nothing on the device
+ * until the first contraction. */
+fp_status fp_ensemble_create(const fp_ensemble_desc *desc, void *cuda_stream, fp_ensemble **out);
+
+/* Release an ensemble and all its device memory.  NULL is allowed. */
+void fp_ensemble_destroy(fp_ensemble *ens);
+
+/* Number of groups F is reported for (depth or T values) and the group value
+ * of each: values[g] = depth_min + g or T_min + g*T_step.  `values` may be NULL. */
+fp_status fp_groups(const fp_ensemble *ens, int32_t *n_groups, int32_t *values);
+
+/* Group index of pairs first..first+count-1 (host array of count int32). */
+fp_status fp_pair_groups(const fp_ensemble *ens, uint64_t first, uint64_t count, int32_t *group);
+
+/* Sampled gates of circuit `which` (0 = U, 1 = V) of one pair, as they enter
+ * the contraction: per gate a record {int32 kind, int32 qubit, 32 doubles =
+ * 16 complex entries (re,im)}, kind 0 = 4x4 on (q,q+1), 1 = 2x2 on q in the
+ * first 4 entries, 2 = diagonal 2-qubit (4 entries).  *bytes is in/out:
+ * capacity of host_buf on entry, bytes needed on return.  host_buf may be
+ * NULL to query the size. */
+fp_status fp_export_gates(fp_ensemble *ens, uint64_t pair, int32_t which, void *host_buf,
+                          size_t *bytes);
+
+/* Contract pairs first..first+count-1.
+ *   tr     [2*count] doubles: Tr(U^dagger V) as (re, im) per pair;
+ *   kappa  [count] doubles or NULL: cancellation ratio sum_j |L_j R_j| / |sum_j L_j R_j|
+ *          of the final boundary dot product (1 when no cancellation);
+ *   group  [count] int32 or NULL: group index of each pair.
+ * Host or device pointers.  FP_ERR_INFEASIBLE if a pair's boundary exceeds
+ * FP_MAX_STATE_BITS (nothing is written then). */
+fp_status fp_trace_batch(fp_ensemble *ens, uint64_t first, uint64_t count, int32_t prec,
+                         double *tr, double *kappa, int32_t *group);
+
+/* FP64 moments of |Tr|^{2k} per group (the reduction of the estimator):
+ * moments[g*(2*k_max+1) + 0] = N_g, [.. + k] = sum |Tr|^{2k}, [.. + k_max + k] =
+ * sum |Tr|^{4k}, for k = 1..k_max.  tr/group as produced by fp_trace_batch,
+ * on the device; moments on host or device.  Deterministic (fixed tree). */
+fp_status fp_reduce_moments(fp_ensemble *ens, const double *tr, const int32_t *group,
+                            uint64_t count, int32_t k_max, double *moments);
+
+/* Monte Carlo frame potential.  Contracts pairs first, first+1, ... in batches
+ * until every group's relative standard error of F^(2) (or of F^(1) when
+ * k_max = 1) is <= target_rel_stderr, or max_pairs pairs are done.
+ *   F, stderr  [n_groups * k_max] doubles (host), F[g*k_max + k-1] = F^(k) of group g,
+ *              stderr = s/sqrt(N) with s the N-1 sample deviation;
+ *   stats      may be NULL. */
+fp_status fp_frame_potential(fp_ensemble *ens, uint64_t first, uint64_t max_pairs, int32_t k_max,
+                             double target_rel_stderr, int32_t prec, double *F, double *stderr_,
+                             fp_run_stats *stats);
+
+/* Copy the ensemble's kernel counters into *out; reset them if `reset`. */
+fp_status fp_kernel_stats_get(fp_ensemble *ens, fp_kernel_stats *out, int32_t reset);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char *fp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,202 @@
+"""Python binding of the GB300 frame-potential library (``libfp_gb300.so``).
+
+Argument marshalling only: every step of the hot path (sampling, merging,
+boundary sweeps, the FP64 meet and the moment reduction) runs in the CUDA
+kernels behind the C ABI declared in ``include/fp.h``.  There is no CPU
+fallback: importing the binding without the built library raises.
+
+PyTorch supplies device memory and streams; tensors are passed by
+``data_ptr()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfp_gb300.so")
+
+PARALLEL, LOCAL, HEA = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_FP32_RAW = 0, 1, 2
+FLAG_SELF_PAIR, FLAG_DIAGONAL_GATES, FLAG_GENERIC_ONLY, FLAG_TIMING = 1, 2, 4, 8
+K_SAMPLE, K_MERGE, K_TABLES, K_SWEEP, K_BRICK, K_MOMENTS, K_CLASSES = 0, 1, 2, 3, 4, 5, 8
+K_NAMES = {0: "sample", 1: "merge", 2: "tables", 3: "sweep_generic", 4: "sweep_brick", 5: "moments"}
+MAX_STATE_BITS = 24
+STATUS = {0: "FP_OK", -1: "FP_ERR_ARG", -2: "FP_ERR_CUDA", -3: "FP_ERR_OOM", -4: "FP_ERR_TIMEOUT",
+          -5: "FP_ERR_INFEASIBLE"}
+
+EXPORTED = ["fp_ensemble_create", "fp_ensemble_destroy", "fp_groups", "fp_pair_groups", "fp_export_gates",
+            "fp_trace_batch", "fp_reduce_moments", "fp_frame_potential", "fp_kernel_stats_get", "fp_last_error"]
+
+
+class FpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("depth_min", ctypes.c_int32),
+                ("depth_max", ctypes.c_int32), ("T_min", ctypes.c_int32), ("T_max", ctypes.c_int32),
+                ("T_step", ctypes.c_int32), ("flags", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("kappa_max", ctypes.c_double), ("workspace_bytes", ctypes.c_uint64)]
+
+
+class RunStats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_uint64), ("fp64_recontracted", ctypes.c_uint64),
+                ("gpu_seconds", ctypes.c_double), ("max_kappa", ctypes.c_double),
+                ("n_groups", ctypes.c_int32), ("reached_target", ctypes.c_int32)]
+
+
+class KernelStats(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8), ("work", ctypes.c_double * 8),
+                ("pairs", ctypes.c_uint64)]
+
+
+class GateRec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("q", ctypes.c_int32), ("m", ctypes.c_double * 32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2205_09900_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P, vp = ctypes.POINTER, ctypes.c_void_p
+    L.fp_ensemble_create.argtypes = [P(Desc), vp, P(vp)]
+    L.fp_ensemble_destroy.argtypes = [vp]
+    L.fp_ensemble_destroy.restype = None
+    L.fp_groups.argtypes = [vp, P(ctypes.c_int32), vp]
+    L.fp_pair_groups.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, vp]
+    L.fp_export_gates.argtypes = [vp, ctypes.c_uint64, ctypes.c_int32, vp, P(ctypes.c_size_t)]
+    L.fp_trace_batch.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, vp, vp, vp]
+    L.fp_reduce_moments.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.c_int32, vp]
+    L.fp_frame_potential.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double,
+                                     ctypes.c_int32, vp, vp, P(RunStats)]
+    L.fp_kernel_stats_get.argtypes = [vp, P(KernelStats), ctypes.c_int32]
+    L.fp_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("fp_ensemble_destroy", "fp_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != 0:
+        raise FpError(status, load().fp_last_error().decode())
+
+
+def _ptr(x):
+    """Address of a torch tensor, a numpy array, or None."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+class Ensemble:
+    """One ensemble of circuit pairs (``fp_ensemble``)."""
+
+    def __init__(self, kind, n, depth_min=1, depth_max=None, T_min=0, T_max=0, T_step=1, seed=1,
+                 flags=0, kappa_max=0.0, workspace_bytes=0, stream=None):
+        L = load()
+        self.desc = Desc(kind, n, depth_min, depth_min if depth_max is None else depth_max, T_min, T_max,
+                         T_step, flags, seed, kappa_max, workspace_bytes)
+        h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(stream)
+        _check(L.fp_ensemble_create(ctypes.byref(self.desc), st, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fp_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def groups(self):
+        import numpy as np
+        ng = ctypes.c_int32()
+        _check(load().fp_groups(self._h, ctypes.byref(ng), None))
+        vals = np.zeros(ng.value, dtype=np.int32)
+        _check(load().fp_groups(self._h, ctypes.byref(ng), _ptr(vals)))
+        return vals
+
+    def pair_groups(self, first, count):
+        import numpy as np
+        g = np.zeros(count, dtype=np.int32)
+        _check(load().fp_pair_groups(self._h, first, count, _ptr(g)))
+        return g
+
+    def export_gates(self, pair, which):
+        """Sampled gates of U (which=0) or V (which=1): list of (kind, qubit, matrix)."""
+        import numpy as np
+        nb = ctypes.c_size_t(0)
+        _check(load().fp_export_gates(self._h, pair, which, None, ctypes.byref(nb)))
+        cnt = nb.value // ctypes.sizeof(GateRec)
+        buf = (GateRec * max(1, cnt))()
+        _check(load().fp_export_gates(self._h, pair, which, ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(nb)))
+        out = []
+        for i in range(cnt):
+            m = np.array(buf[i].m[:])
+            z = m[0::2] + 1j * m[1::2]
+            if buf[i].kind == 0:
+                mat = z.reshape(4, 4)
+            elif buf[i].kind == 1:
+                mat = z[:4].reshape(2, 2)
+            else:
+                mat = z[:4].copy()
+            out.append((buf[i].kind, buf[i].q, mat))
+        return out
+
+    def trace_batch(self, first, count, prec=PREC_FP64, tr=None, kappa=None, group=None):
+        """Contract pairs first..first+count-1 into caller buffers (torch tensors or numpy
+        arrays, host or device).  Allocates numpy host arrays for omitted ones and
+        returns (tr complex, kappa, group)."""
+        import numpy as np
+        own = tr is None
+        if own:
+            tr = np.zeros(2 * count, dtype=np.float64)
+            kappa = np.zeros(count, dtype=np.float64) if kappa is None else kappa
+            group = np.zeros(count, dtype=np.int32) if group is None else group
+        _check(load().fp_trace_batch(self._h, first, count, prec, _ptr(tr), _ptr(kappa), _ptr(group)))
+        if own:
+            return tr[0::2] + 1j * tr[1::2], kappa, group
+        return tr, kappa, group
+
+    def reduce_moments(self, tr_dev, group_dev, count, k_max, out):
+        _check(load().fp_reduce_moments(self._h, _ptr(tr_dev), _ptr(group_dev), count, k_max, _ptr(out)))
+        return out
+
+    def kernel_stats(self, reset=False):
+        st = KernelStats()
+        _check(load().fp_kernel_stats_get(self._h, ctypes.byref(st), int(bool(reset))))
+        return st
+
+    def frame_potential(self, first, max_pairs, k_max, target_rel_stderr=0.0, prec=PREC_FP64):
+        import numpy as np
+        ng = len(self.groups())
+        F = np.zeros(ng * k_max)
+        se = np.zeros(ng * k_max)
+        st = RunStats()
+        _check(load().fp_frame_potential(self._h, first, max_pairs, k_max, target_rel_stderr, prec, _ptr(F),
+                                         _ptr(se), ctypes.byref(st)))
+        return F.reshape(ng, k_max), se.reshape(ng, k_max), st

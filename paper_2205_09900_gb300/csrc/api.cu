@@ -1,0 +1,619 @@
+// api.cu -- the C ABI declared in include/fp.h.
+//
+// Host side of the hot path: per-pair depth draws, plan cache (one plan per
+// depth for fixed-topology ensembles, one per pair for local circuits),
+// batching under a device-memory budget, the launches (sampler -> merge ->
+// tables -> sweep+meet), the FP32->FP64 recontraction policy and the
+// Monte Carlo driver.  Every step of the path runs in the kernels; the host
+// only plans, marshals and orders work.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "fp.h"
+#include "kernels.h"
+#include "planner.h"
+
+using namespace fpk;
+
+namespace {
+
+thread_local std::string g_err;
+
+fp_status fail(fp_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA,      \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+// Device buffer that grows on demand.
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DBuf() { if (p) cudaFree(p); }
+    cudaError_t reserve(size_t b) {
+        if (b <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e == cudaSuccess) bytes = b;
+        return e;
+    }
+    template <typename T> T *as() const { return (T *)p; }
+};
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct fp_ensemble {
+    fp_ensemble_desc d;
+    cudaStream_t st = nullptr;
+    int device = 0;
+    int sms = 0;
+    int raw_kind = RAW_HAAR4;
+    int n_groups = 0;
+    size_t ws_budget = 0;
+    // fixed-topology plan cache
+    std::map<int, int> plan_of_depth;
+    std::vector<HostPlan> plans;
+    bool dev_plans_dirty = true;
+    // device plan pools (fixed topology) and per-batch pools (local)
+    DBuf d_plans, d_ops, d_recipes, d_items, d_refs;
+    // batch buffers
+    DBuf d_pairs, d_order, d_raw, d_merged, d_tables, d_ws, d_ticket, d_tr, d_kappa, d_group;
+    DBuf d_partials, d_moments;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t kev[2 * FP_K_CLASSES] = {};
+    fp_kernel_stats kst{};
+    bool timing = false;
+};
+
+namespace {
+
+int depth_of_pair(const fp_ensemble_desc &d, uint64_t pair) {
+    U64x4 x = philox(d.seed, 0, 0, pair, 4);
+    if (d.kind == FP_LOCAL) {
+        uint32_t choices = (uint32_t)((d.T_max - d.T_min) / d.T_step + 1);
+        return d.T_min + (int)pick(x.x[0], choices) * d.T_step;
+    }
+    uint32_t choices = (uint32_t)(d.depth_max - d.depth_min + 1);
+    return d.depth_min + (int)pick(x.x[0], choices);
+}
+
+int group_of_depth(const fp_ensemble_desc &d, int depth) {
+    return d.kind == FP_LOCAL ? (depth - d.T_min) / d.T_step : depth - d.depth_min;
+}
+
+std::vector<int> local_bonds(const fp_ensemble_desc &d, uint64_t pair, int which, int T) {
+    int w = (d.flags & FP_FLAG_SELF_PAIR) ? 0 : which;
+    std::vector<int> b(T);
+    for (int g = 0; g < T; ++g) {
+        U64x4 x = philox(d.seed, 0, (uint64_t)g, pair, (uint64_t)(2 + w));
+        b[g] = (int)pick(x.x[0], (uint32_t)(d.n - 1));
+    }
+    return b;
+}
+
+HostPlan build_plan(const fp_ensemble_desc &d, int raw_kind, int depth, uint64_t pair) {
+    std::vector<GateSlot> U, V;
+    int n_raw = 0;
+    if (d.kind == FP_PARALLEL) {
+        U = V = layout_brickwork(d.n, depth);
+        n_raw = (int)U.size();
+    } else if (d.kind == FP_HEA) {
+        U = V = layout_hea(d.n, depth);
+        n_raw = depth * d.n;
+    } else {
+        U = layout_local(d.n, local_bonds(d, pair, 0, depth));
+        V = layout_local(d.n, local_bonds(d, pair, 1, depth));
+        n_raw = depth;
+    }
+    return make_plan(d.n, U, V, raw_kind, n_raw, d.n / 2, FP_MAX_STATE_BITS);
+}
+
+// Flatten host plans into device pools.
+struct PlanPools {
+    std::vector<DevPlan> plans;
+    std::vector<DevOp> ops;
+    std::vector<DevRecipe> recipes;
+    std::vector<MergeItem> items;
+    std::vector<MergeRef> refs;
+    void add(const HostPlan &h) {
+        DevPlan p;
+        std::memset(&p, 0, sizeof p);
+        p.n_left = h.n_left;
+        p.n_right = h.n_right;
+        p.ops_off = (int)ops.size();
+        p.rec_off = (int)recipes.size();
+        p.merge_off = (int)items.size();
+        p.n_merged = (int)h.merges.size();
+        p.ref_off = (int)refs.size();
+        p.n_raw = h.n_raw;
+        p.raw_kind = h.raw_kind;
+        p.bits_max = h.bits_max;
+        p.bits_final = h.bits_final;
+        p.left_final_buf = h.left_final_buf;
+        for (int k = 0; k < FP_MAX_STATE_BITS; ++k) p.dot_perm[k] = h.dot_perm[k];
+        p.prefactor = h.prefactor;
+        p.cost = h.cost;
+        ops.insert(ops.end(), h.ops.begin(), h.ops.end());
+        recipes.insert(recipes.end(), h.recipes.begin(), h.recipes.end());
+        items.insert(items.end(), h.merges.begin(), h.merges.end());
+        refs.insert(refs.end(), h.refs.begin(), h.refs.end());
+        plans.push_back(p);
+    }
+};
+
+template <typename T>
+cudaError_t upload(DBuf &b, const std::vector<T> &v, cudaStream_t st) {
+    size_t bytes = std::max<size_t>(sizeof(T), v.size() * sizeof(T));
+    cudaError_t e = b.reserve(bytes);
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+fp_status upload_pools(fp_ensemble *E, const PlanPools &pp) {
+    CK(upload(E->d_plans, pp.plans, E->st));
+    CK(upload(E->d_ops, pp.ops, E->st));
+    CK(upload(E->d_recipes, pp.recipes, E->st));
+    CK(upload(E->d_items, pp.items, E->st));
+    CK(upload(E->d_refs, pp.refs, E->st));
+    return FP_OK;
+}
+
+// Optional per-launch CUDA-event timing (FP_FLAG_TIMING).
+struct KTimer {
+    fp_ensemble *E;
+    int cls;
+    KTimer(fp_ensemble *e, int c) : E(e), cls(c) {
+        if (E->timing) cudaEventRecord(E->kev[2 * cls], E->st);
+    }
+    cudaError_t stop(double work) {
+        if (!E->timing) return cudaSuccess;
+        cudaError_t e = cudaEventRecord(E->kev[2 * cls + 1], E->st);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaEventSynchronize(E->kev[2 * cls + 1])) != cudaSuccess) return e;
+        float ms = 0;
+        if ((e = cudaEventElapsedTime(&ms, E->kev[2 * cls], E->kev[2 * cls + 1])) != cudaSuccess) return e;
+        E->kst.ms[cls] += ms;
+        E->kst.launches[cls] += 1;
+        E->kst.work[cls] += work;
+        return cudaSuccess;
+    }
+};
+
+// Contract pairs [first, first+count) into device arrays E->d_tr / E->d_kappa
+// (indices relative to `first`), groups into E->d_group.
+fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec, float *gpu_ms,
+                       uint64_t *requeued, double *max_kappa) {
+    const fp_ensemble_desc &d = E->d;
+    const bool local = d.kind == FP_LOCAL;
+    std::vector<int> depth(count), grp(count), plan_idx(count);
+    std::vector<HostPlan> local_plans;
+    PlanPools pools;
+    for (uint64_t i = 0; i < count; ++i) {
+        depth[i] = depth_of_pair(d, first + i);
+        grp[i] = group_of_depth(d, depth[i]);
+    }
+    if (!local) {
+        for (uint64_t i = 0; i < count; ++i) {
+            auto it = E->plan_of_depth.find(depth[i]);
+            if (it == E->plan_of_depth.end()) {
+                HostPlan h = build_plan(d, E->raw_kind, depth[i], first + i);
+                if (h.infeasible) return fail(FP_ERR_INFEASIBLE, "depth %d: %s", depth[i], h.error.c_str());
+                if (!h.error.empty()) return fail(FP_ERR_ARG, "planner: %s", h.error.c_str());
+                E->plans.push_back(std::move(h));
+                it = E->plan_of_depth.emplace(depth[i], (int)E->plans.size() - 1).first;
+                E->dev_plans_dirty = true;
+            }
+            plan_idx[i] = it->second;
+        }
+        if (E->dev_plans_dirty) {
+            for (const auto &h : E->plans) pools.add(h);
+            fp_status s = upload_pools(E, pools);
+            if (s != FP_OK) return s;
+            E->dev_plans_dirty = false;
+        }
+    } else {
+        local_plans.reserve(count);
+        for (uint64_t i = 0; i < count; ++i) {
+            HostPlan h = build_plan(d, E->raw_kind, depth[i], first + i);
+            if (h.infeasible)
+                return fail(FP_ERR_INFEASIBLE, "pair %llu (T=%d): %s", (unsigned long long)(first + i), depth[i],
+                            h.error.c_str());
+            if (!h.error.empty()) return fail(FP_ERR_ARG, "planner: %s", h.error.c_str());
+            pools.add(h);
+            plan_idx[i] = (int)i;
+            local_plans.push_back(std::move(h));
+        }
+        fp_status s = upload_pools(E, pools);
+        if (s != FP_OK) return s;
+        E->dev_plans_dirty = true;   // the fixed-topology pool was overwritten
+    }
+    auto hp = [&](uint64_t i) -> const HostPlan & { return local ? local_plans[i] : E->plans[plan_idx[i]]; };
+
+    const bool fp32 = prec != FP_PREC_FP64;
+    const size_t celem = fp32 ? sizeof(float2) : sizeof(double2);
+    CK(E->d_tr.reserve(count * 2 * sizeof(double)));
+    CK(E->d_kappa.reserve(count * sizeof(double)));
+    CK(E->d_group.reserve(count * sizeof(int32_t)));
+    CK(cudaMemcpyAsync(E->d_group.p, grp.data(), count * sizeof(int32_t), cudaMemcpyHostToDevice, E->st));
+    CK(E->d_ticket.reserve(sizeof(int) * 4));
+
+    if (gpu_ms) *gpu_ms = 0;
+    uint64_t done = 0;
+    while (done < count) {
+        // sub-batch under the memory budget
+        uint64_t nb = 0;
+        size_t raw_b = 0, mer_b = 0, tab_b = 0;
+        int bits_max = 0, max_raw = 0, max_mer = 0, max_ops = 0;
+        const int ctas_full = E->sms * 2;
+        while (done + nb < count && nb < 65535) {
+            const HostPlan &h = hp(done + nb);
+            size_t r = (size_t)2 * h.n_raw * 16 * sizeof(double2);
+            size_t m = h.merges.size() * 16 * sizeof(double2);
+            size_t t = h.ops.size() * 16 * sizeof(double2);   // FP64 tables may be needed for recontraction
+            int bm = std::max(bits_max, h.bits_max);
+            size_t ws = (size_t)std::min<uint64_t>(ctas_full, nb + 1) * 3 * ((size_t)1 << bm) * sizeof(double2);
+            if (nb > 0 && raw_b + r + mer_b + m + tab_b + t + ws > E->ws_budget) break;
+            raw_b += r; mer_b += m; tab_b += t; bits_max = bm;
+            max_raw = std::max(max_raw, h.n_raw);
+            max_mer = std::max<int>(max_mer, (int)h.merges.size());
+            max_ops = std::max<int>(max_ops, (int)h.ops.size());
+            ++nb;
+        }
+        std::vector<PairInfo> pinfo(nb);
+        int64_t ro = 0, mo = 0, to = 0;
+        for (uint64_t i = 0; i < nb; ++i) {
+            const HostPlan &h = hp(done + i);
+            pinfo[i].pair = first + done + i;
+            pinfo[i].plan = plan_idx[done + i];
+            pinfo[i].n_raw = h.n_raw;
+            pinfo[i].raw_off = ro;
+            pinfo[i].merged_off = mo;
+            pinfo[i].table_off = to;
+            ro += 2 * h.n_raw;
+            mo += (int64_t)h.merges.size();
+            to += (int64_t)h.ops.size();
+        }
+        std::vector<int32_t> order(nb);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hp(done + a).cost > hp(done + b).cost; });
+        int ctas = (int)std::min<uint64_t>(nb, (uint64_t)ctas_full);
+        size_t ws_elems = (size_t)1 << bits_max;
+        CK(upload(E->d_pairs, pinfo, E->st));
+        CK(upload(E->d_order, order, E->st));
+        CK(E->d_raw.reserve(std::max<size_t>(16, ro * 16 * sizeof(double2))));
+        CK(E->d_merged.reserve(std::max<size_t>(16, mo * 16 * sizeof(double2))));
+        CK(E->d_tables.reserve(std::max<size_t>(16, to * 16 * sizeof(double2))));
+        CK(E->d_ws.reserve((size_t)ctas * 3 * ws_elems * celem));
+
+        SampleParams sp;
+        sp.seed = d.seed;
+        sp.n = d.n;
+        sp.raw_kind = E->raw_kind;
+        sp.self_pair = (d.flags & FP_FLAG_SELF_PAIR) ? 1 : 0;
+        double *trb = E->d_tr.as<double>() + 2 * done;
+        double *kab = E->d_kappa.as<double>() + done;
+        double cmacs = 0;
+        for (uint64_t i = 0; i < nb; ++i) cmacs += hp(done + i).cost;
+        CK(cudaEventRecord(E->ev0, E->st));
+        {
+            KTimer t(E, FP_K_SAMPLE);
+            CK(launch_sample(sp, E->d_pairs.as<PairInfo>(), (int)nb, max_raw, E->d_raw.as<double2>(), E->st));
+            CK(t.stop((double)nb));
+        }
+        {
+            KTimer t(E, FP_K_MERGE);
+            CK(launch_merge(E->d_pairs.as<PairInfo>(), (int)nb, max_mer, E->d_plans.as<DevPlan>(),
+                            E->d_items.as<MergeItem>(), E->d_refs.as<MergeRef>(), E->d_raw.as<double2>(),
+                            E->d_merged.as<double2>(), E->st));
+            CK(t.stop((double)nb));
+        }
+        {
+            KTimer t(E, FP_K_TABLES);
+            CK(launch_tables(E->d_pairs.as<PairInfo>(), (int)nb, max_ops, E->d_plans.as<DevPlan>(),
+                             E->d_recipes.as<DevRecipe>(), E->d_merged.as<double2>(), E->d_tables.p, fp32, E->st));
+            CK(t.stop((double)nb));
+        }
+        {
+            KTimer t(E, FP_K_SWEEP);
+            CK(launch_sweep_generic(E->d_pairs.as<PairInfo>(), E->d_order.as<int32_t>(), (int)nb, E->d_plans.as<DevPlan>(),
+                                    E->d_ops.as<DevOp>(), E->d_tables.p, fp32, E->d_ws.p, ws_elems, ctas,
+                                    E->d_ticket.as<int>(), trb, kab, E->st));
+            CK(t.stop(cmacs));
+        }
+        E->kst.pairs += nb;
+        CK(cudaEventRecord(E->ev1, E->st));
+        CK(cudaEventSynchronize(E->ev1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, E->ev0, E->ev1));
+        if (gpu_ms) *gpu_ms += ms;
+
+        if (prec == FP_PREC_FP32 || max_kappa) {
+            std::vector<double> kap(nb);
+            CK(cudaMemcpyAsync(kap.data(), kab, nb * sizeof(double), cudaMemcpyDeviceToHost, E->st));
+            CK(cudaStreamSynchronize(E->st));
+            double kmax_allowed = d.kappa_max > 0 ? d.kappa_max : 1e3;
+            std::vector<int32_t> redo;
+            for (uint64_t i = 0; i < nb; ++i) {
+                if (max_kappa && std::isfinite(kap[i])) *max_kappa = std::max(*max_kappa, kap[i]);
+                if (prec == FP_PREC_FP32 && !(kap[i] <= kmax_allowed)) redo.push_back((int32_t)i);
+            }
+            if (!redo.empty()) {
+                if (requeued) *requeued += redo.size();
+                CK(upload(E->d_order, redo, E->st));
+                CK(E->d_ws.reserve((size_t)std::min<size_t>(ctas, redo.size()) * 3 * ws_elems * sizeof(double2)));
+                double rc = 0;
+                for (int32_t i : redo) rc += hp(done + i).cost;
+                CK(cudaEventRecord(E->ev0, E->st));
+                {
+                    KTimer t(E, FP_K_TABLES);
+                    CK(launch_tables(E->d_pairs.as<PairInfo>(), (int)nb, max_ops, E->d_plans.as<DevPlan>(),
+                                     E->d_recipes.as<DevRecipe>(), E->d_merged.as<double2>(), E->d_tables.p, false, E->st));
+                    CK(t.stop((double)nb));
+                }
+                {
+                    KTimer t(E, FP_K_SWEEP);
+                    CK(launch_sweep_generic(E->d_pairs.as<PairInfo>(), E->d_order.as<int32_t>(), (int)redo.size(),
+                                            E->d_plans.as<DevPlan>(), E->d_ops.as<DevOp>(), E->d_tables.p, false,
+                                            E->d_ws.p, ws_elems, (int)std::min<size_t>(ctas, redo.size()),
+                                            E->d_ticket.as<int>(), trb, kab, E->st));
+                    CK(t.stop(rc));
+                }
+                CK(cudaEventRecord(E->ev1, E->st));
+                CK(cudaEventSynchronize(E->ev1));
+                CK(cudaEventElapsedTime(&ms, E->ev0, E->ev1));
+                if (gpu_ms) *gpu_ms += ms;
+            }
+        }
+        done += nb;
+    }
+    return FP_OK;
+}
+
+fp_status copy_out(fp_ensemble *E, void *dst, const void *src, size_t bytes) {
+    if (!dst) return FP_OK;
+    cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(dst, src, bytes, k, E->st));
+    return FP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fp_last_error(void) { return g_err.c_str(); }
+
+fp_status fp_ensemble_create(const fp_ensemble_desc *desc, void *cuda_stream, fp_ensemble **out) {
+    if (!desc || !out) return fail(FP_ERR_ARG, "null argument");
+    *out = nullptr;
+    const fp_ensemble_desc &d = *desc;
+    if (d.kind < FP_PARALLEL || d.kind > FP_HEA) return fail(FP_ERR_ARG, "unknown ensemble kind %d", d.kind);
+    if (d.n < 2 || d.n > 64) return fail(FP_ERR_ARG, "n = %d outside [2, 64]", d.n);
+    if (d.kind == FP_LOCAL) {
+        if (d.T_min < 1 || d.T_max < d.T_min || d.T_step < 1)
+            return fail(FP_ERR_ARG, "bad local-circuit gate counts [%d, %d] step %d", d.T_min, d.T_max, d.T_step);
+    } else if (d.depth_min < 1 || d.depth_max < d.depth_min) {
+        return fail(FP_ERR_ARG, "bad depth range [%d, %d]", d.depth_min, d.depth_max);
+    }
+    if ((d.flags & FP_FLAG_DIAGONAL_GATES) && d.kind == FP_HEA)
+        return fail(FP_ERR_ARG, "FP_FLAG_DIAGONAL_GATES applies to Haar-gate ensembles only");
+    std::unique_ptr<fp_ensemble> E(new fp_ensemble());
+    E->d = d;
+    E->st = (cudaStream_t)cuda_stream;
+    CK(cudaGetDevice(&E->device));
+    CK(cudaDeviceGetAttribute(&E->sms, cudaDevAttrMultiProcessorCount, E->device));
+    E->raw_kind = d.kind == FP_HEA ? RAW_ROT2 : ((d.flags & FP_FLAG_DIAGONAL_GATES) ? RAW_DIAG4 : RAW_HAAR4);
+    E->n_groups = d.kind == FP_LOCAL ? (d.T_max - d.T_min) / d.T_step + 1 : d.depth_max - d.depth_min + 1;
+    size_t freeb = 0, totb = 0;
+    CK(cudaMemGetInfo(&freeb, &totb));
+    size_t cap = d.workspace_bytes ? (size_t)d.workspace_bytes : ((size_t)8 << 30);
+    E->ws_budget = std::min(cap, freeb / 2);
+    CK(cudaEventCreate(&E->ev0));
+    CK(cudaEventCreate(&E->ev1));
+    E->timing = (d.flags & FP_FLAG_TIMING) != 0;
+    for (int k = 0; k < 2 * FP_K_CLASSES; ++k) CK(cudaEventCreate(&E->kev[k]));
+    *out = E.release();
+    return FP_OK;
+}
+
+void fp_ensemble_destroy(fp_ensemble *ens) {
+    if (!ens) return;
+    if (ens->st) cudaStreamSynchronize(ens->st);
+    else cudaDeviceSynchronize();
+    if (ens->ev0) cudaEventDestroy(ens->ev0);
+    if (ens->ev1) cudaEventDestroy(ens->ev1);
+    for (int k = 0; k < 2 * FP_K_CLASSES; ++k)
+        if (ens->kev[k]) cudaEventDestroy(ens->kev[k]);
+    delete ens;
+}
+
+fp_status fp_groups(const fp_ensemble *ens, int32_t *n_groups, int32_t *values) {
+    if (!ens || !n_groups) return fail(FP_ERR_ARG, "null argument");
+    *n_groups = ens->n_groups;
+    if (values)
+        for (int g = 0; g < ens->n_groups; ++g)
+            values[g] = ens->d.kind == FP_LOCAL ? ens->d.T_min + g * ens->d.T_step : ens->d.depth_min + g;
+    return FP_OK;
+}
+
+fp_status fp_pair_groups(const fp_ensemble *ens, uint64_t first, uint64_t count, int32_t *group) {
+    if (!ens || (!group && count)) return fail(FP_ERR_ARG, "null argument");
+    for (uint64_t i = 0; i < count; ++i) group[i] = group_of_depth(ens->d, depth_of_pair(ens->d, first + i));
+    return FP_OK;
+}
+
+fp_status fp_export_gates(fp_ensemble *ens, uint64_t pair, int32_t which, void *host_buf, size_t *bytes) {
+    if (!ens || !bytes || (which != 0 && which != 1)) return fail(FP_ERR_ARG, "bad argument");
+    const fp_ensemble_desc &d = ens->d;
+    int depth = depth_of_pair(d, pair);
+    std::vector<GateSlot> lay;
+    int n_raw;
+    if (d.kind == FP_PARALLEL) { lay = layout_brickwork(d.n, depth); n_raw = (int)lay.size(); }
+    else if (d.kind == FP_HEA) { lay = layout_hea(d.n, depth); n_raw = depth * d.n; }
+    else { lay = layout_local(d.n, local_bonds(d, pair, which, depth)); n_raw = depth; }
+    struct Rec { int32_t kind, q; double m[32]; };
+    size_t need = lay.size() * sizeof(Rec);
+    if (!host_buf) { *bytes = need; return FP_OK; }
+    if (*bytes < need) { *bytes = need; return fail(FP_ERR_ARG, "buffer too small: need %zu bytes", need); }
+    *bytes = need;
+    PairInfo pi;
+    pi.pair = pair; pi.plan = 0; pi.n_raw = n_raw; pi.raw_off = 0; pi.merged_off = 0; pi.table_off = 0;
+    CK(upload(ens->d_pairs, std::vector<PairInfo>{pi}, ens->st));
+    CK(ens->d_raw.reserve((size_t)2 * n_raw * 16 * sizeof(double2)));
+    SampleParams sp;
+    sp.seed = d.seed; sp.n = d.n; sp.raw_kind = ens->raw_kind; sp.self_pair = (d.flags & FP_FLAG_SELF_PAIR) ? 1 : 0;
+    CK(launch_sample(sp, ens->d_pairs.as<PairInfo>(), 1, n_raw, ens->d_raw.as<double2>(), ens->st));
+    std::vector<double2> raw((size_t)2 * n_raw * 16);
+    CK(cudaMemcpyAsync(raw.data(), ens->d_raw.p, raw.size() * sizeof(double2), cudaMemcpyDeviceToHost, ens->st));
+    CK(cudaStreamSynchronize(ens->st));
+    Rec *out = (Rec *)host_buf;
+    for (size_t i = 0; i < lay.size(); ++i) {
+        std::memset(&out[i], 0, sizeof(Rec));
+        out[i].q = lay[i].q;
+        if (lay[i].kind == 2) {
+            out[i].kind = 2;
+            double dg[4] = {1, 1, 1, -1};
+            for (int k = 0; k < 4; ++k) out[i].m[2 * k] = dg[k];
+            continue;
+        }
+        out[i].kind = lay[i].kind;
+        const double2 *g = &raw[((size_t)which * n_raw + lay[i].raw) * 16];
+        for (int k = 0; k < 16; ++k) { out[i].m[2 * k] = g[k].x; out[i].m[2 * k + 1] = g[k].y; }
+    }
+    return FP_OK;
+}
+
+fp_status fp_trace_batch(fp_ensemble *ens, uint64_t first, uint64_t count, int32_t prec, double *tr,
+                         double *kappa, int32_t *group) {
+    if (!ens || (!tr && count)) return fail(FP_ERR_ARG, "null argument");
+    if (prec < FP_PREC_FP64 || prec > FP_PREC_FP32_RAW) return fail(FP_ERR_ARG, "unknown precision %d", prec);
+    if (count == 0) return FP_OK;
+    fp_status s = trace_device(ens, first, count, prec, nullptr, nullptr, nullptr);
+    if (s != FP_OK) return s;
+    if ((s = copy_out(ens, tr, ens->d_tr.p, count * 2 * sizeof(double))) != FP_OK) return s;
+    if ((s = copy_out(ens, kappa, ens->d_kappa.p, count * sizeof(double))) != FP_OK) return s;
+    if ((s = copy_out(ens, group, ens->d_group.p, count * sizeof(int32_t))) != FP_OK) return s;
+    CK(cudaStreamSynchronize(ens->st));
+    return FP_OK;
+}
+
+fp_status fp_reduce_moments(fp_ensemble *ens, const double *tr, const int32_t *group, uint64_t count,
+                            int32_t k_max, double *moments) {
+    if (!ens || !tr || !moments) return fail(FP_ERR_ARG, "null argument");
+    if (k_max < 1 || k_max > FP_MAX_KMAX) return fail(FP_ERR_ARG, "k_max = %d outside [1, %d]", k_max, FP_MAX_KMAX);
+    if (!is_device_ptr(tr) || (group && !is_device_ptr(group)))
+        return fail(FP_ERR_ARG, "tr and group must be device pointers");
+    int ng = group ? ens->n_groups : 1, nb = moments_blocks(count), nv = 2 * k_max + 1;
+    CK(ens->d_partials.reserve((size_t)nb * ng * nv * sizeof(double)));
+    CK(ens->d_moments.reserve((size_t)ng * nv * sizeof(double)));
+    {
+        KTimer t(ens, FP_K_MOMENTS);
+        CK(launch_moments(tr, group, count, k_max, ng, ens->d_partials.as<double>(), nb, ens->d_moments.as<double>(), ens->st));
+        CK(t.stop((double)count));
+    }
+    fp_status s = copy_out(ens, moments, ens->d_moments.p, (size_t)ng * nv * sizeof(double));
+    if (s != FP_OK) return s;
+    CK(cudaStreamSynchronize(ens->st));
+    return FP_OK;
+}
+
+fp_status fp_frame_potential(fp_ensemble *ens, uint64_t first, uint64_t max_pairs, int32_t k_max,
+                             double target_rel_stderr, int32_t prec, double *F, double *stderr_,
+                             fp_run_stats *stats) {
+    if (!ens || !F || !stderr_) return fail(FP_ERR_ARG, "null argument");
+    if (k_max < 1 || k_max > FP_MAX_KMAX) return fail(FP_ERR_ARG, "k_max = %d outside [1, %d]", k_max, FP_MAX_KMAX);
+    if (prec < FP_PREC_FP64 || prec > FP_PREC_FP32_RAW) return fail(FP_ERR_ARG, "unknown precision %d", prec);
+    const int ng = ens->n_groups, nv = 2 * k_max + 1;
+    std::vector<double> acc((size_t)ng * nv, 0.0), comp((size_t)ng * nv, 0.0), part((size_t)ng * nv);
+    fp_run_stats st;
+    std::memset(&st, 0, sizeof st);
+    st.n_groups = ng;
+    const int kt = k_max >= 2 ? 2 : 1;
+    uint64_t batch = 4096, done = 0;
+    bool reached = false;
+    while (done < max_pairs && !reached) {
+        uint64_t nb = std::min<uint64_t>(batch, max_pairs - done);
+        float ms = 0;
+        fp_status s = trace_device(ens, first + done, nb, prec, &ms, &st.fp64_recontracted, &st.max_kappa);
+        if (s != FP_OK) return s;
+        st.gpu_seconds += ms * 1e-3;
+        int nb_blocks = moments_blocks(nb);
+        CK(ens->d_partials.reserve((size_t)nb_blocks * ng * nv * sizeof(double)));
+        CK(ens->d_moments.reserve((size_t)ng * nv * sizeof(double)));
+        {
+            KTimer t(ens, FP_K_MOMENTS);
+            CK(launch_moments(ens->d_tr.as<double>(), ens->d_group.as<int32_t>(), nb, k_max, ng,
+                              ens->d_partials.as<double>(), nb_blocks, ens->d_moments.as<double>(), ens->st));
+            CK(t.stop((double)nb));
+        }
+        CK(cudaMemcpyAsync(part.data(), ens->d_moments.p, part.size() * sizeof(double), cudaMemcpyDeviceToHost, ens->st));
+        CK(cudaStreamSynchronize(ens->st));
+        for (size_t i = 0; i < part.size(); ++i) {   // Neumaier accumulation across batches
+            double y = acc[i] + part[i];
+            comp[i] += std::fabs(acc[i]) >= std::fabs(part[i]) ? (acc[i] - y) + part[i] : (part[i] - y) + acc[i];
+            acc[i] = y;
+        }
+        done += nb;
+        st.pairs = done;
+        reached = target_rel_stderr > 0;
+        for (int g = 0; g < ng; ++g) {
+            double N = acc[g * nv] + comp[g * nv];
+            for (int k = 1; k <= k_max; ++k) {
+                double S = acc[g * nv + k] + comp[g * nv + k];
+                double Q = acc[g * nv + k_max + k] + comp[g * nv + k_max + k];
+                double mean = N > 0 ? S / N : NAN;
+                double var = N > 1 ? std::max(0.0, (Q - S * S / N) / (N - 1)) : NAN;
+                F[g * k_max + k - 1] = mean;
+                stderr_[g * k_max + k - 1] = N > 1 ? std::sqrt(var / N) : NAN;
+            }
+            double f = F[g * k_max + kt - 1], e = stderr_[g * k_max + kt - 1];
+            if (!(N > 1 && f > 0 && e / f <= target_rel_stderr)) reached = false;
+        }
+        if (batch < (1u << 20)) batch *= 2;
+    }
+    st.reached_target = reached ? 1 : 0;
+    if (stats) *stats = st;
+    return FP_OK;
+}
+
+fp_status fp_kernel_stats_get(fp_ensemble *ens, fp_kernel_stats *out, int32_t reset) {
+    if (!ens || !out) return fail(FP_ERR_ARG, "null argument");
+    *out = ens->kst;
+    if (reset) std::memset(&ens->kst, 0, sizeof ens->kst);
+    return FP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+// fp_internal.h -- structures shared by the host planner and the sm_103a kernels.
+#pragma once
+#include <cstdint>
+#include <cstddef>
+
+#include "fp.h"
+
+#if defined(__CUDACC__)
+#define FP_HD __host__ __device__ __forceinline__
+#else
+#define FP_HD inline
+#endif
+
+namespace fpk {
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), used on host (per-pair
+// depth, local-circuit bonds) and device (gate sampling).  Keying is stated
+// in fp.h.
+// ---------------------------------------------------------------------------
+struct U64x4 { uint64_t x[4]; };
+
+FP_HD void mul_hilo(uint64_t a, uint64_t b, uint64_t &hi, uint64_t &lo) {
+#if defined(__CUDA_ARCH__)
+    lo = a * b;
+    hi = __umul64hi(a, b);
+#else
+    unsigned __int128 p = (unsigned __int128)a * b;
+    hi = (uint64_t)(p >> 64);
+    lo = (uint64_t)p;
+#endif
+}
+
+FP_HD U64x4 philox(uint64_t seed, uint64_t c0, uint64_t c1, uint64_t pair, uint64_t stream) {
+    uint64_t c[4] = {c0, c1, pair, stream};
+    uint64_t k0 = seed, k1 = 0;
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+#endif
+    for (int r = 0; r < 10; ++r) {
+        uint64_t hi0, lo0, hi1, lo1;
+        mul_hilo(0xD2E7470EE14C6C93ULL, c[0], hi0, lo0);
+        mul_hilo(0xCA5A826395121157ULL, c[2], hi1, lo1);
+        uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        k0 += 0x9E3779B97F4A7C15ULL;
+        k1 += 0xBB67AE8584CAA73BULL;
+    }
+    U64x4 o;
+    o.x[0] = c[0]; o.x[1] = c[1]; o.x[2] = c[2]; o.x[3] = c[3];
+    return o;
+}
+
+FP_HD uint32_t pick(uint64_t x, uint32_t choices) {   // uniform index in [0, choices)
+    return (uint32_t)(((x >> 32) * (uint64_t)choices) >> 32);
+}
+
+// ---------------------------------------------------------------------------
+// Raw gates (as sampled) and merged gates live in 16-slot complex records:
+// a 4x4 matrix row-major, or a 2x2 in slots 0..3.
+// ---------------------------------------------------------------------------
+enum RawKind : int32_t { RAW_HAAR4 = 0, RAW_ROT2 = 1, RAW_DIAG4 = 2 };
+
+// One raw-gate reference inside a merged product.
+struct MergeRef {
+    int32_t which;    // 0 = U, 1 = V
+    int32_t gate;     // raw gate index within that circuit
+    int32_t dagger;   // 1: use the conjugate transpose
+    int32_t dim;      // 4 or 2
+};
+
+// A merged gate = product of refs[first .. first+count-1], refs[first] acting first.
+struct MergeItem {
+    int32_t first;
+    int32_t count;
+};
+
+// One operation of a sweep program: multiply the state by a factor table over
+// <= 4 binary variables, each consumed (summed, removed), kept, or new.
+struct DevOp {
+    uint8_t nc, nk, nn, b_in;
+    uint8_t b_out, inplace2, pad0, pad1;
+    uint8_t cons_pos[4];   // ascending positions in the input layout
+    uint8_t keep_pos[4];   // positions in the output layout
+    uint8_t new_pos[4];    // ascending positions in the output layout
+};
+
+// How to fill one op's table (16 entries, index e = cons | keep<<nc | new<<(nc+nk)).
+struct DevRecipe {
+    int32_t merged;        // merged gate id, or -1 for constants
+    int32_t nent;          // 2^(nc+nk+nn)
+    int8_t src[16][4];     // merged-gate slots summed into entry e (-1: unused)
+    double cre[16];        // constant entries (merged == -1)
+    double cim[16];
+};
+
+// Device view of one plan (one topology).
+struct DevPlan {
+    int32_t n_left, n_right;       // ops in each sweep
+    int32_t ops_off;               // first op in the op pool (left ops, then right ops)
+    int32_t rec_off;               // first recipe in the recipe pool (same order)
+    int32_t merge_off;             // first MergeItem in the merge pool
+    int32_t n_merged;
+    int32_t ref_off;               // MergeRef pool offset (MergeItem.first is relative)
+    int32_t n_raw;                 // raw gates per circuit
+    int32_t raw_kind;              // RawKind
+    int32_t bits_max;              // largest state in either sweep
+    int32_t bits_final;            // bits of the meeting boundary
+    int32_t left_final_buf;        // 0/1: buffer holding the left result
+    uint8_t dot_perm[FP_MAX_STATE_BITS];   // right-layout position of left bit k
+    double prefactor;              // 2^(free wire loops)
+    double cost;                   // estimated complex MACs per pair
+};
+
+}  // namespace fpk

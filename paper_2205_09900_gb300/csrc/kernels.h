@@ -1,0 +1,48 @@
+// kernels.h -- launch wrappers of the sm_103a kernels (host-callable).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fp_internal.h"
+
+namespace fpk {
+
+struct PairInfo {
+    uint64_t pair;        // global pair index (Philox counter word)
+    int32_t plan;         // DevPlan index
+    int32_t n_raw;        // raw gates per circuit
+    int64_t raw_off;      // first raw gate (16-slot records) of this pair
+    int64_t merged_off;   // first merged gate
+    int64_t table_off;    // first op table
+};
+
+struct SampleParams {
+    uint64_t seed;
+    int32_t n;
+    int32_t raw_kind;     // RawKind
+    int32_t self_pair;
+};
+
+// Sampler: raw gates of U and V for every pair of the batch (FP64).
+cudaError_t launch_sample(const SampleParams &sp, const PairInfo *pairs, int npairs, int max_raw,
+                          double2 *raw, cudaStream_t st);
+// Merged gates: ordered products of raw gates (FP64).
+cudaError_t launch_merge(const PairInfo *pairs, int npairs, int max_merged, const DevPlan *plans,
+                         const MergeItem *items, const MergeRef *refs, const double2 *raw,
+                         double2 *merged, cudaStream_t st);
+// Op tables (16 entries per op) in FP64 or FP32.
+cudaError_t launch_tables(const PairInfo *pairs, int npairs, int max_ops, const DevPlan *plans,
+                          const DevRecipe *recipes, const double2 *merged, void *tables, bool fp32,
+                          cudaStream_t st);
+// Generic boundary sweep + meet: one CTA per pair at a time, persistent over a
+// ticket queue.  Writes tr[2*i], kappa[i] for pair i of `order`.
+cudaError_t launch_sweep_generic(const PairInfo *pairs, const int32_t *order, int count,
+                                 const DevPlan *plans, const DevOp *ops, const void *tables,
+                                 bool fp32, void *workspace, size_t ws_elems_per_cta, int ctas,
+                                 int *ticket, double *tr, double *kappa, cudaStream_t st);
+// FP64 moments per group (deterministic).
+cudaError_t launch_moments(const double *tr, const int32_t *group, uint64_t count, int k_max,
+                           int n_groups, double *partials, int nblocks, double *out,
+                           cudaStream_t st);
+int moments_blocks(uint64_t count);
+
+}  // namespace fpk

@@ -1,0 +1,226 @@
+// kernels_sample.cu -- gate sampler (K1), gate merging and op-table builder (K2).
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace fpk {
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// Haar U(4): QR of a 4x4 complex Gaussian by Householder reflections, then
+// the columns of Q rotated so that R's diagonal is positive real (the Haar
+// sampler of the Methods section, "Sampling U(d^2)", realised as in Mezzadri
+// 2007).  Gaussian entries by Box-Muller from Philox words (keying in fp.h).
+__device__ void haar_u4(uint64_t seed, uint64_t pair, int w, int g, double2 *out) {
+    double2 A[4][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        U64x4 x = philox(seed, (uint64_t)j, (uint64_t)g, pair, (uint64_t)w);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint64_t xa = x.x[2 * h], xb = x.x[2 * h + 1];
+            double u1 = (double)((xa >> 11) + 1) * 0x1.0p-53;
+            double u2 = (double)(xb >> 11) * 0x1.0p-53;
+            double rad = sqrt(-2.0 * log(u1)) * 0.70710678118654752440;
+            double s, c;
+            sincospi(2.0 * u2, &s, &c);
+            int k = 2 * j + h;
+            A[k / 4][k % 4] = make_double2(rad * c, rad * s);
+        }
+    }
+    double2 Q[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Q[r][c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double nrm2 = 0;
+#pragma unroll
+        for (int r = k; r < 4; ++r) nrm2 += A[r][k].x * A[r][k].x + A[r][k].y * A[r][k].y;
+        double nrm = sqrt(nrm2);
+        double a0 = hypot(A[k][k].x, A[k][k].y);
+        double2 ph = a0 > 0 ? make_double2(A[k][k].x / a0, A[k][k].y / a0) : make_double2(1.0, 0.0);
+        double2 alpha = make_double2(-ph.x * nrm, -ph.y * nrm);
+        double2 v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[r] = r < k ? make_double2(0, 0) : A[r][k];
+        v[k].x -= alpha.x;
+        v[k].y -= alpha.y;
+        double vn2 = 0;
+#pragma unroll
+        for (int r = k; r < 4; ++r) vn2 += v[r].x * v[r].x + v[r].y * v[r].y;
+        if (vn2 == 0) continue;
+        double f = 2.0 / vn2;
+        // A <- (I - f v v^H) A
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            double2 s = make_double2(0, 0);
+#pragma unroll
+            for (int r = k; r < 4; ++r) { double2 t = cmul(cconj(v[r]), A[r][c]); s.x += t.x; s.y += t.y; }
+#pragma unroll
+            for (int r = k; r < 4; ++r) { double2 t = cmul(v[r], s); A[r][c].x -= f * t.x; A[r][c].y -= f * t.y; }
+        }
+        // Q <- Q (I - f v v^H)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            double2 s = make_double2(0, 0);
+#pragma unroll
+            for (int j = k; j < 4; ++j) { double2 t = cmul(Q[r][j], v[j]); s.x += t.x; s.y += t.y; }
+#pragma unroll
+            for (int j = k; j < 4; ++j) { double2 t = cmul(s, cconj(v[j])); Q[r][j].x -= f * t.x; Q[r][j].y -= f * t.y; }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        double a = hypot(A[c][c].x, A[c][c].y);
+        double2 ph = a > 0 ? make_double2(A[c][c].x / a, A[c][c].y / a) : make_double2(1.0, 0.0);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) out[4 * r + c] = cmul(Q[r][c], ph);
+    }
+}
+
+__global__ void sample_kernel(SampleParams sp, const PairInfo *__restrict__ pairs, double2 *__restrict__ raw) {
+    const PairInfo pi = pairs[blockIdx.y];
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 2 * pi.n_raw) return;
+    int w = idx / pi.n_raw, g = idx % pi.n_raw;
+    int wr = sp.self_pair ? 0 : w;
+    double2 *out = raw + (pi.raw_off + idx) * 16;
+    if (sp.raw_kind == RAW_HAAR4) {
+        haar_u4(sp.seed, pi.pair, wr, g, out);
+    } else if (sp.raw_kind == RAW_DIAG4) {
+        U64x4 x = philox(sp.seed, 0, (uint64_t)g, pi.pair, (uint64_t)wr);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) out[k] = make_double2(0, 0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            double s, c;
+            sincospi(2.0 * ((double)(x.x[k] >> 11) * 0x1.0p-53), &s, &c);
+            out[5 * k] = make_double2(c, s);
+        }
+    } else {   // RAW_ROT2: HEA rotation RY(theta) RZ(phi), raw index g = t*n + q
+        int t = g / sp.n, q = g % sp.n;
+        U64x4 x = philox(sp.seed, (uint64_t)t, (uint64_t)q, pi.pair, (uint64_t)wr);
+        double th = (double)(x.x[0] >> 11) * 0x1.0p-53;   // in turns of 2 pi
+        double ph = (double)(x.x[1] >> 11) * 0x1.0p-53;
+        double sth, cth, sph, cph;
+        sincospi(th, &sth, &cth);            // sin, cos of theta/2 = pi * th
+        sincospi(ph, &sph, &cph);            // sin, cos of phi/2
+        double2 em = make_double2(cph, -sph), ep = make_double2(cph, sph);
+#pragma unroll
+        for (int k = 4; k < 16; ++k) out[k] = make_double2(0, 0);
+        out[0] = make_double2(cth * em.x, cth * em.y);
+        out[1] = make_double2(-sth * ep.x, -sth * ep.y);
+        out[2] = make_double2(sth * em.x, sth * em.y);
+        out[3] = make_double2(cth * ep.x, cth * ep.y);
+    }
+}
+
+__global__ void merge_kernel(const PairInfo *__restrict__ pairs, const DevPlan *__restrict__ plans,
+                             const MergeItem *__restrict__ items, const MergeRef *__restrict__ refs,
+                             const double2 *__restrict__ raw, double2 *__restrict__ merged) {
+    const PairInfo pi = pairs[blockIdx.y];
+    const DevPlan &pl = plans[pi.plan];
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= pl.n_merged) return;
+    MergeItem it = items[pl.merge_off + m];
+    double2 M[16];
+    int dim = refs[pl.ref_off + it.first].dim;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) M[k] = make_double2(0, 0);
+    for (int r = 0; r < dim; ++r) M[r * dim + r] = make_double2(1, 0);
+    for (int c = 0; c < it.count; ++c) {
+        MergeRef rf = refs[pl.ref_off + it.first + c];
+        const double2 *A = raw + (pi.raw_off + (int64_t)rf.which * pi.n_raw + rf.gate) * 16;
+        double2 G[16], N[16];
+        for (int r = 0; r < dim; ++r)
+            for (int s = 0; s < dim; ++s)
+                G[r * dim + s] = rf.dagger ? cconj(A[s * dim + r]) : A[r * dim + s];
+        for (int r = 0; r < dim; ++r)
+            for (int s = 0; s < dim; ++s) {
+                double2 acc = make_double2(0, 0);
+                for (int k = 0; k < dim; ++k) {
+                    double2 t = cmul(G[r * dim + k], M[k * dim + s]);
+                    acc.x += t.x; acc.y += t.y;
+                }
+                N[r * dim + s] = acc;
+            }
+        for (int k = 0; k < dim * dim; ++k) M[k] = N[k];
+    }
+    double2 *out = merged + (pi.merged_off + m) * 16;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) out[k] = M[k];
+}
+
+template <typename C>
+__device__ __forceinline__ C to_c(double re, double im);
+template <>
+__device__ __forceinline__ double2 to_c<double2>(double re, double im) { return make_double2(re, im); }
+template <>
+__device__ __forceinline__ float2 to_c<float2>(double re, double im) { return make_float2((float)re, (float)im); }
+
+template <typename C>
+__global__ void table_kernel(const PairInfo *__restrict__ pairs, const DevPlan *__restrict__ plans,
+                             const DevRecipe *__restrict__ recipes, const double2 *__restrict__ merged,
+                             C *__restrict__ tables) {
+    const PairInfo pi = pairs[blockIdx.y];
+    const DevPlan &pl = plans[pi.plan];
+    int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= pl.n_left + pl.n_right) return;
+    const DevRecipe &r = recipes[pl.rec_off + o];
+    C *out = tables + (pi.table_off + o) * 16;
+    const double2 *M = r.merged >= 0 ? merged + (pi.merged_off + r.merged) * 16 : nullptr;
+    for (int e = 0; e < 16; ++e) {
+        double re = 0, im = 0;
+        if (e < r.nent) {
+            if (M) {
+                for (int s = 0; s < 4; ++s) {
+                    int k = r.src[e][s];
+                    if (k >= 0) { re += M[k].x; im += M[k].y; }
+                }
+            } else {
+                re = r.cre[e];
+                im = r.cim[e];
+            }
+        }
+        out[e] = to_c<C>(re, im);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_sample(const SampleParams &sp, const PairInfo *pairs, int npairs, int max_raw,
+                          double2 *raw, cudaStream_t st) {
+    if (npairs <= 0) return cudaSuccess;
+    dim3 grid((2 * max_raw + 127) / 128, npairs);
+    sample_kernel<<<grid, 128, 0, st>>>(sp, pairs, raw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const PairInfo *pairs, int npairs, int max_merged, const DevPlan *plans,
+                         const MergeItem *items, const MergeRef *refs, const double2 *raw,
+                         double2 *merged, cudaStream_t st) {
+    if (npairs <= 0 || max_merged <= 0) return cudaSuccess;
+    dim3 grid((max_merged + 127) / 128, npairs);
+    merge_kernel<<<grid, 128, 0, st>>>(pairs, plans, items, refs, raw, merged);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tables(const PairInfo *pairs, int npairs, int max_ops, const DevPlan *plans,
+                          const DevRecipe *recipes, const double2 *merged, void *tables, bool fp32,
+                          cudaStream_t st) {
+    if (npairs <= 0 || max_ops <= 0) return cudaSuccess;
+    dim3 grid((max_ops + 127) / 128, npairs);
+    if (fp32)
+        table_kernel<float2><<<grid, 128, 0, st>>>(pairs, plans, recipes, merged, (float2 *)tables);
+    else
+        table_kernel<double2><<<grid, 128, 0, st>>>(pairs, plans, recipes, merged, (double2 *)tables);
+    return cudaGetLastError();
+}
+
+}  // namespace fpk

@@ -1,0 +1,50 @@
+"""The C-ABI library builds for sm_103a and exports every function that
+include/*.h declares.  No compute call is made (no GPU is needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(fp_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2205_09900_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_api():
+    names = declared_functions()
+    for required in ("fp_ensemble_create", "fp_trace_batch", "fp_frame_potential", "fp_ensemble_destroy",
+                     "fp_last_error", "fp_export_gates", "fp_reduce_moments"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    import paper_2205_09900_gb300 as fp
+    assert sorted(fp.EXPORTED) == declared_functions()
+
+
+def test_last_error_without_gpu(lib):
+    lib.fp_last_error.restype = ctypes.c_char_p
+    assert isinstance(lib.fp_last_error(), bytes)

@@ -1,0 +1,248 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Inputs are the same (seed, pair) on both sides; each side draws its own
+random numbers from the Philox keying stated in include/fp.h and
+oracle/fp_oracle.h.  Tolerances:
+  FP64 path:  |dTr| <= 1e-10 * max(|Tr|, 1)
+  FP32 path:  |dTr| <= 1e-4  (traces are plain Tr(U^dagger V), E|Tr|^2 = 1 for
+              a 1-design), F^(k) within 1e-3 relative of the FP64 path.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def fp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_09900_gb300 import build
+    build.build()
+    import paper_2205_09900_gb300 as fpm
+    fpm.load()
+    return fpm
+
+
+KIND = {"parallel": (O.PARALLEL, 0), "hea": (O.HEA, 2), "local": (O.LOCAL, 1)}
+
+
+def make(fp, kind, n, depth=1, depth_max=None, T=None, seed=1, flags=0):
+    ok, fk = KIND[kind]
+    dmax = depth if depth_max is None else depth_max
+    if T is not None:
+        Tmin, Tmax, Tstep = T
+        od = O.desc(ok, n, 1, 1, T_min=Tmin, T_max=Tmax, T_step=Tstep, seed=seed,
+                    self_pair=bool(flags & fp.FLAG_SELF_PAIR))
+        ens = fp.Ensemble(fk, n, 1, 1, Tmin, Tmax, Tstep, seed=seed, flags=flags)
+    else:
+        od = O.desc(ok, n, depth, dmax, seed=seed, self_pair=bool(flags & fp.FLAG_SELF_PAIR))
+        ens = fp.Ensemble(fk, n, depth, dmax, seed=seed, flags=flags)
+    return ens, od
+
+
+def rel_err(a, b):
+    return np.abs(a - b) / np.maximum(np.abs(b), 1.0)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,n,depth,T", [("parallel", 8, 4, None), ("parallel", 7, 3, None),
+                                            ("hea", 6, 3, None), ("local", 9, 1, (5, 25, 5))])
+def test_sampler_matches_oracle(fp, kind, n, depth, T):
+    ens, od = make(fp, kind, n, depth, T=T, seed=42)
+    for pair in range(4):
+        for which in (0, 1):
+            g = ens.export_gates(pair, which)
+            o = O.circuit(od, pair, which)
+            assert len(g) == len(o)
+            for (k1, q1, m1), (k2, q2, m2) in zip(g, o):
+                assert (k1, q1) == (k2, q2)          # integer structure: bit-exact
+                assert np.abs(np.asarray(m1) - np.asarray(m2)).max() < 1e-13
+
+
+def test_pair_depth_draws_match_oracle(fp):
+    ens, od = make(fp, "parallel", 50, 2, 10, seed=99)
+    g = ens.pair_groups(0, 500)
+    assert all(g[p] + 2 == O.pair_depth(od, p) for p in range(500))
+    ens, od = make(fp, "local", 20, T=(20, 200, 20), seed=5)
+    g = ens.pair_groups(1000, 300)
+    assert all(20 + 20 * g[i] == O.pair_depth(od, 1000 + i) for i in range(300))
+
+
+# ---------------------------------------------------------------------------
+def test_fp64_brickwork_n8_l4_dense(fp):
+    # the n=8, l=4 brickwork workload: every pair against the dense 256x256 oracle
+    ens, od = make(fp, "parallel", 8, 4, seed=1)
+    N = 512
+    tr, kap, grp = ens.trace_batch(0, N, fp.PREC_FP64)
+    ref = O.trace_batch(od, 0, N, "dense", threads=8)
+    assert rel_err(tr, ref).max() <= TOL64
+    assert np.all(kap >= 1.0 - 1e-12)
+
+
+@pytest.mark.parametrize("kind,n,depth,T,npairs", [
+    ("parallel", 2, 3, None, 8), ("parallel", 3, 2, None, 8), ("parallel", 8, 1, None, 8),
+    ("parallel", 9, 3, None, 8), ("parallel", 50, 1, None, 4), ("parallel", 50, 2, None, 6),
+    ("parallel", 50, 5, None, 4), ("parallel", 51, 4, None, 4), ("parallel", 50, 7, None, 2),
+    ("hea", 2, 1, None, 8), ("hea", 7, 3, None, 6), ("hea", 50, 1, None, 4), ("hea", 50, 4, None, 4),
+    ("hea", 50, 6, None, 2),
+    ("local", 6, 1, (1, 12, 1), 12), ("local", 20, 1, (20, 60, 20), 6),
+])
+def test_fp64_trace_matches_oracle(fp, kind, n, depth, T, npairs):
+    ens, od = make(fp, kind, n, depth, T=T, seed=7 + n)
+    tr, kap, grp = ens.trace_batch(0, npairs, fp.PREC_FP64)
+    ref = O.trace_batch(od, 0, npairs, "auto", threads=8)
+    assert rel_err(tr, ref).max() <= TOL64, (tr, ref)
+
+
+def test_fp64_mixed_depth_batch(fp):
+    # pairs of depths 2..7 in one batch, ragged plan sizes in one launch
+    ens, od = make(fp, "parallel", 50, 2, 7, seed=3)
+    N = 24
+    tr, kap, grp = ens.trace_batch(5, N, fp.PREC_FP64)
+    ref = O.trace_batch(od, 5, N, "ve", threads=8)
+    assert rel_err(tr, ref).max() <= TOL64
+    assert sorted(set(grp.tolist())) == sorted(set((np.array([O.pair_depth(od, 5 + i) for i in range(N)]) - 2).tolist()))
+
+
+# ---------------------------------------------------------------------------
+# Full-size properties: hold at any depth, so they cover the largest boundaries.
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-5)])
+def test_self_pair_full_size(fp, prec, tol):
+    ens, _ = make(fp, "parallel", 50, 9, 10, seed=11, flags=1)   # FLAG_SELF_PAIR
+    tr, kap, grp = ens.trace_batch(0, 4, prec)
+    assert np.all(np.abs(tr - 2.0 ** 50) <= tol * 2.0 ** 50), tr
+
+
+def _diag_phases(seed, pair, which, g):
+    x = O.philox4x64([0, g, pair, which], [seed, 0])
+    return np.exp(2j * np.pi * np.array([(v >> 11) * 2.0 ** -53 for v in x]))
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
+def test_diagonal_gates_full_size(fp, prec, tol):
+    # diagonal gates: Tr(U^dagger V) is a classical 1D transfer-matrix product
+    n, seed = 50, 17
+    ens, od = make(fp, "parallel", n, 10, seed=seed, flags=2)    # FLAG_DIAGONAL_GATES
+    tr, kap, grp = ens.trace_batch(0, 3, prec)
+    for p in range(3):
+        l = 10
+        phase = {b: np.ones(4, dtype=complex) for b in range(n - 1)}
+        g = 0
+        for t in range(1, l + 1):
+            for b in range((t - 1) % 2, n - 1, 2):
+                phase[b] *= np.conj(_diag_phases(seed, p, 0, g)) * _diag_phases(seed, p, 1, g)
+                g += 1
+        v = np.ones(2, dtype=complex)
+        for b in range(n - 1):
+            v = v @ phase[b].reshape(2, 2)
+        ref = v.sum()
+        assert abs(tr[p] - ref) <= tol * max(1.0, abs(ref)), (p, tr[p], ref)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,n,depth,dmax,npairs", [("parallel", 50, 2, 8, 16), ("hea", 50, 2, 6, 12),
+                                                      ("parallel", 8, 4, 4, 256)])
+def test_fp32_path_matches_oracle(fp, kind, n, depth, dmax, npairs):
+    ens, od = make(fp, kind, n, depth, dmax, seed=21)
+    tr32, kap, _ = ens.trace_batch(0, npairs, fp.PREC_FP32)
+    ref = O.trace_batch(od, 0, npairs, "auto", threads=8)
+    err = np.abs(tr32 - ref)
+    assert err.max() <= TOL32, (err.max(), kap[np.argmax(err)])
+
+
+def test_fp32_frame_potential_within_1e3_of_fp64(fp):
+    ens, _ = make(fp, "parallel", 20, 2, 6, seed=23)
+    N = 4000
+    t64, _, g = ens.trace_batch(0, N, fp.PREC_FP64)
+    t32, kap, _ = ens.trace_batch(0, N, fp.PREC_FP32)
+    for k in (1, 2, 3, 4):
+        f64 = np.mean(np.abs(t64) ** (2 * k))
+        f32 = np.mean(np.abs(t32) ** (2 * k))
+        assert abs(f32 - f64) <= 1e-3 * f64
+
+
+# ---------------------------------------------------------------------------
+def test_reduce_moments_matches_oracle(fp):
+    import torch
+    ens, _ = make(fp, "parallel", 8, 1, 3, seed=2)
+    rng = np.random.default_rng(5)
+    N, kmax = 30001, 4
+    trc = rng.normal(size=N) + 1j * rng.normal(size=N)
+    grp = rng.integers(0, 3, size=N).astype(np.int32)
+    tr_d = torch.tensor(np.stack([trc.real, trc.imag], 1).reshape(-1), device="cuda", dtype=torch.float64)
+    g_d = torch.tensor(grp, device="cuda")
+    out = np.zeros(3 * (2 * kmax + 1))
+    ens.reduce_moments(tr_d, g_d, N, kmax, out)
+    out = out.reshape(3, 2 * kmax + 1)
+    for gi in range(3):
+        sel = trc[grp == gi]
+        assert out[gi, 0] == len(sel)
+        F, se = O.moments(sel, kmax)
+        for k in range(1, kmax + 1):
+            S, Q = out[gi, k], out[gi, kmax + k]
+            n = len(sel)
+            assert abs(S / n - F[k - 1]) <= 1e-12 * F[k - 1]
+            se_gpu = math.sqrt((Q - S * S / n) / (n - 1) / n)
+            assert abs(se_gpu - se[k - 1]) <= 1e-8 * se[k - 1]
+
+
+def test_frame_potential_matches_weingarten(fp):
+    ens, _ = make(fp, "parallel", 4, 2, seed=31)
+    F, se, st = ens.frame_potential(0, 200000, 2, 0.0, fp.PREC_FP64)
+    exact = O.weingarten_f2_brickwork(4, 2)
+    assert abs(F[0, 0] - 1.0) < 5 * se[0, 0]
+    assert abs(F[0, 1] - exact) < 5 * se[0, 1], (F, se, exact)
+    assert st.pairs == 200000
+
+
+def test_frame_potential_single_haar_gate(fp):
+    ens, _ = make(fp, "parallel", 2, 1, seed=37)
+    F, se, st = ens.frame_potential(0, 300000, 4, 0.0, fp.PREC_FP64)
+    for k in range(1, 5):
+        assert abs(F[0, k - 1] - math.factorial(k)) < 5 * se[0, k - 1]
+
+
+def test_frame_potential_stops_at_target(fp):
+    ens, _ = make(fp, "parallel", 6, 3, seed=41)
+    F, se, st = ens.frame_potential(0, 10 ** 7, 2, 0.02, fp.PREC_FP64)
+    assert st.reached_target == 1
+    assert se[0, 1] / F[0, 1] <= 0.02
+    assert st.pairs < 10 ** 7
+
+
+# ---------------------------------------------------------------------------
+def test_errors_and_edges(fp):
+    with pytest.raises(fp.FpError) as e:
+        fp.Ensemble(0, 1, 2)
+    assert e.value.status == -1
+    ens, _ = make(fp, "parallel", 50, 14, seed=1)   # 26-bit boundary
+    with pytest.raises(fp.FpError) as e:
+        ens.trace_batch(0, 1, fp.PREC_FP64)
+    assert e.value.status == -5
+    ens, od = make(fp, "parallel", 8, 3, seed=1)
+    tr, kap, g = ens.trace_batch(0, 0, fp.PREC_FP64)
+    assert len(tr) == 0
+    tr1, _, _ = ens.trace_batch(10, 1, fp.PREC_FP64)      # single pair, offset start
+    assert rel_err(tr1, O.trace_batch(od, 10, 1, "dense")).max() <= TOL64
+
+
+def test_device_output_pointers(fp):
+    import torch
+    ens, od = make(fp, "parallel", 8, 4, seed=1)
+    N = 64
+    tr = torch.zeros(2 * N, dtype=torch.float64, device="cuda")
+    kap = torch.zeros(N, dtype=torch.float64, device="cuda")
+    grp = torch.zeros(N, dtype=torch.int32, device="cuda")
+    ens.trace_batch(0, N, fp.PREC_FP64, tr, kap, grp)
+    t = tr.cpu().numpy()
+    ref = O.trace_batch(od, 0, N, "dense", threads=8)
+    assert rel_err(t[0::2] + 1j * t[1::2], ref).max() <= TOL64
