@@ -21,6 +21,7 @@
 
 #include "fp.h"
 #include "kernels.h"
+#include "brick.h"
 #include "planner.h"
 
 using namespace fpk;
@@ -76,6 +77,11 @@ bool is_device_ptr(const void *p) {
 
 }  // namespace
 
+struct BrickCache {
+    BrickHostPlan hp;
+    DBuf d_gates;
+};
+
 struct fp_ensemble {
     fp_ensemble_desc d;
     cudaStream_t st = nullptr;
@@ -96,7 +102,12 @@ struct fp_ensemble {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t kev[2 * FP_K_CLASSES] = {};
     fp_kernel_stats kst{};
+    uint64_t kst_requeued = 0;
     bool timing = false;
+    // brickwork fast path
+    std::map<int, std::unique_ptr<BrickCache>> brick_plans;   // key 2*l + fp32
+    DBuf d_maps, d_states;
+    int tile_bits32 = 14, tile_bits64 = 13;
 };
 
 namespace {
@@ -213,28 +224,27 @@ struct KTimer {
     }
 };
 
-// Contract pairs [first, first+count) into device arrays E->d_tr / E->d_kappa
-// (indices relative to `first`), groups into E->d_group.
-fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec, float *gpu_ms,
-                       uint64_t *requeued, double *max_kappa) {
+// Generic path over a subset of pairs: outputs go to slots idx[i] of the
+// device arrays (pairs first + idx[i]).
+fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx,
+                      const std::vector<int> &depth, int prec, double *tr, double *kappa, float *gpu_ms) {
     const fp_ensemble_desc &d = E->d;
     const bool local = d.kind == FP_LOCAL;
-    std::vector<int> depth(count), grp(count), plan_idx(count);
+    const uint64_t count = idx.size();
+    if (count == 0) return FP_OK;
+    std::vector<int> plan_idx(count);
     std::vector<HostPlan> local_plans;
     PlanPools pools;
-    for (uint64_t i = 0; i < count; ++i) {
-        depth[i] = depth_of_pair(d, first + i);
-        grp[i] = group_of_depth(d, depth[i]);
-    }
     if (!local) {
         for (uint64_t i = 0; i < count; ++i) {
-            auto it = E->plan_of_depth.find(depth[i]);
+            const int dep = depth[idx[i]];
+            auto it = E->plan_of_depth.find(dep);
             if (it == E->plan_of_depth.end()) {
-                HostPlan h = build_plan(d, E->raw_kind, depth[i], first + i);
-                if (h.infeasible) return fail(FP_ERR_INFEASIBLE, "depth %d: %s", depth[i], h.error.c_str());
+                HostPlan h = build_plan(d, E->raw_kind, dep, first + idx[i]);
+                if (h.infeasible) return fail(FP_ERR_INFEASIBLE, "depth %d: %s", dep, h.error.c_str());
                 if (!h.error.empty()) return fail(FP_ERR_ARG, "planner: %s", h.error.c_str());
                 E->plans.push_back(std::move(h));
-                it = E->plan_of_depth.emplace(depth[i], (int)E->plans.size() - 1).first;
+                it = E->plan_of_depth.emplace(dep, (int)E->plans.size() - 1).first;
                 E->dev_plans_dirty = true;
             }
             plan_idx[i] = it->second;
@@ -248,10 +258,10 @@ fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec,
     } else {
         local_plans.reserve(count);
         for (uint64_t i = 0; i < count; ++i) {
-            HostPlan h = build_plan(d, E->raw_kind, depth[i], first + i);
+            HostPlan h = build_plan(d, E->raw_kind, depth[idx[i]], first + idx[i]);
             if (h.infeasible)
-                return fail(FP_ERR_INFEASIBLE, "pair %llu (T=%d): %s", (unsigned long long)(first + i), depth[i],
-                            h.error.c_str());
+                return fail(FP_ERR_INFEASIBLE, "pair %llu (T=%d): %s", (unsigned long long)(first + idx[i]),
+                            depth[idx[i]], h.error.c_str());
             if (!h.error.empty()) return fail(FP_ERR_ARG, "planner: %s", h.error.c_str());
             pools.add(h);
             plan_idx[i] = (int)i;
@@ -262,19 +272,10 @@ fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec,
         E->dev_plans_dirty = true;   // the fixed-topology pool was overwritten
     }
     auto hp = [&](uint64_t i) -> const HostPlan & { return local ? local_plans[i] : E->plans[plan_idx[i]]; };
-
     const bool fp32 = prec != FP_PREC_FP64;
     const size_t celem = fp32 ? sizeof(float2) : sizeof(double2);
-    CK(E->d_tr.reserve(count * 2 * sizeof(double)));
-    CK(E->d_kappa.reserve(count * sizeof(double)));
-    CK(E->d_group.reserve(count * sizeof(int32_t)));
-    CK(cudaMemcpyAsync(E->d_group.p, grp.data(), count * sizeof(int32_t), cudaMemcpyHostToDevice, E->st));
-    CK(E->d_ticket.reserve(sizeof(int) * 4));
-
-    if (gpu_ms) *gpu_ms = 0;
     uint64_t done = 0;
     while (done < count) {
-        // sub-batch under the memory budget
         uint64_t nb = 0;
         size_t raw_b = 0, mer_b = 0, tab_b = 0;
         int bits_max = 0, max_raw = 0, max_mer = 0, max_ops = 0;
@@ -283,7 +284,7 @@ fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec,
             const HostPlan &h = hp(done + nb);
             size_t r = (size_t)2 * h.n_raw * 16 * sizeof(double2);
             size_t m = h.merges.size() * 16 * sizeof(double2);
-            size_t t = h.ops.size() * 16 * sizeof(double2);   // FP64 tables may be needed for recontraction
+            size_t t = h.ops.size() * 16 * sizeof(double2);
             int bm = std::max(bits_max, h.bits_max);
             size_t ws = (size_t)std::min<uint64_t>(ctas_full, nb + 1) * 3 * ((size_t)1 << bm) * sizeof(double2);
             if (nb > 0 && raw_b + r + mer_b + m + tab_b + t + ws > E->ws_budget) break;
@@ -295,17 +296,20 @@ fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec,
         }
         std::vector<PairInfo> pinfo(nb);
         int64_t ro = 0, mo = 0, to = 0;
+        double cmacs = 0;
         for (uint64_t i = 0; i < nb; ++i) {
             const HostPlan &h = hp(done + i);
-            pinfo[i].pair = first + done + i;
+            pinfo[i].pair = first + idx[done + i];
             pinfo[i].plan = plan_idx[done + i];
             pinfo[i].n_raw = h.n_raw;
             pinfo[i].raw_off = ro;
             pinfo[i].merged_off = mo;
             pinfo[i].table_off = to;
+            pinfo[i].out = (int64_t)idx[done + i];
             ro += 2 * h.n_raw;
             mo += (int64_t)h.merges.size();
             to += (int64_t)h.ops.size();
+            cmacs += h.cost;
         }
         std::vector<int32_t> order(nb);
         std::iota(order.begin(), order.end(), 0);
@@ -318,16 +322,11 @@ fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec,
         CK(E->d_merged.reserve(std::max<size_t>(16, mo * 16 * sizeof(double2))));
         CK(E->d_tables.reserve(std::max<size_t>(16, to * 16 * sizeof(double2))));
         CK(E->d_ws.reserve((size_t)ctas * 3 * ws_elems * celem));
-
         SampleParams sp;
         sp.seed = d.seed;
         sp.n = d.n;
         sp.raw_kind = E->raw_kind;
         sp.self_pair = (d.flags & FP_FLAG_SELF_PAIR) ? 1 : 0;
-        double *trb = E->d_tr.as<double>() + 2 * done;
-        double *kab = E->d_kappa.as<double>() + done;
-        double cmacs = 0;
-        for (uint64_t i = 0; i < nb; ++i) cmacs += hp(done + i).cost;
         CK(cudaEventRecord(E->ev0, E->st));
         {
             KTimer t(E, FP_K_SAMPLE);
@@ -351,54 +350,153 @@ fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec,
             KTimer t(E, FP_K_SWEEP);
             CK(launch_sweep_generic(E->d_pairs.as<PairInfo>(), E->d_order.as<int32_t>(), (int)nb, E->d_plans.as<DevPlan>(),
                                     E->d_ops.as<DevOp>(), E->d_tables.p, fp32, E->d_ws.p, ws_elems, ctas,
-                                    E->d_ticket.as<int>(), trb, kab, E->st));
+                                    E->d_ticket.as<int>(), tr, kappa, E->st));
             CK(t.stop(cmacs));
         }
-        E->kst.pairs += nb;
         CK(cudaEventRecord(E->ev1, E->st));
         CK(cudaEventSynchronize(E->ev1));
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, E->ev0, E->ev1));
         if (gpu_ms) *gpu_ms += ms;
-
-        if (prec == FP_PREC_FP32 || max_kappa) {
-            std::vector<double> kap(nb);
-            CK(cudaMemcpyAsync(kap.data(), kab, nb * sizeof(double), cudaMemcpyDeviceToHost, E->st));
-            CK(cudaStreamSynchronize(E->st));
-            double kmax_allowed = d.kappa_max > 0 ? d.kappa_max : 1e3;
-            std::vector<int32_t> redo;
-            for (uint64_t i = 0; i < nb; ++i) {
-                if (max_kappa && std::isfinite(kap[i])) *max_kappa = std::max(*max_kappa, kap[i]);
-                if (prec == FP_PREC_FP32 && !(kap[i] <= kmax_allowed)) redo.push_back((int32_t)i);
-            }
-            if (!redo.empty()) {
-                if (requeued) *requeued += redo.size();
-                CK(upload(E->d_order, redo, E->st));
-                CK(E->d_ws.reserve((size_t)std::min<size_t>(ctas, redo.size()) * 3 * ws_elems * sizeof(double2)));
-                double rc = 0;
-                for (int32_t i : redo) rc += hp(done + i).cost;
-                CK(cudaEventRecord(E->ev0, E->st));
-                {
-                    KTimer t(E, FP_K_TABLES);
-                    CK(launch_tables(E->d_pairs.as<PairInfo>(), (int)nb, max_ops, E->d_plans.as<DevPlan>(),
-                                     E->d_recipes.as<DevRecipe>(), E->d_merged.as<double2>(), E->d_tables.p, false, E->st));
-                    CK(t.stop((double)nb));
-                }
-                {
-                    KTimer t(E, FP_K_SWEEP);
-                    CK(launch_sweep_generic(E->d_pairs.as<PairInfo>(), E->d_order.as<int32_t>(), (int)redo.size(),
-                                            E->d_plans.as<DevPlan>(), E->d_ops.as<DevOp>(), E->d_tables.p, false,
-                                            E->d_ws.p, ws_elems, (int)std::min<size_t>(ctas, redo.size()),
-                                            E->d_ticket.as<int>(), trb, kab, E->st));
-                    CK(t.stop(rc));
-                }
-                CK(cudaEventRecord(E->ev1, E->st));
-                CK(cudaEventSynchronize(E->ev1));
-                CK(cudaEventElapsedTime(&ms, E->ev0, E->ev1));
-                if (gpu_ms) *gpu_ms += ms;
-            }
-        }
+        E->kst.pairs += nb;
         done += nb;
+    }
+    return FP_OK;
+}
+
+// Brickwork fast path for pairs of one depth l >= 2.
+fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx, int l, int prec,
+                    double *tr, double *kappa, float *gpu_ms) {
+    const fp_ensemble_desc &d = E->d;
+    const uint64_t count = idx.size();
+    if (count == 0) return FP_OK;
+    const bool fp32 = prec != FP_PREC_FP64;
+    const int N = 2 * (l - 1);
+    if (N > FP_MAX_STATE_BITS)
+        return fail(FP_ERR_INFEASIBLE, "depth %d: boundary of %d bits exceeds the limit of %d", l, N, FP_MAX_STATE_BITS);
+    const int key = l * 2 + (fp32 ? 1 : 0);
+    auto it = E->brick_plans.find(key);
+    if (it == E->brick_plans.end()) {
+        auto bc = std::make_unique<BrickCache>();
+        const int kt = fp32 ? E->tile_bits32 : E->tile_bits64;
+        bc->hp = make_brick_plan(d.n, l, N <= kt ? 0 : kt, fp32 ? 5 : 4);
+        CK(upload(bc->d_gates, bc->hp.gates, E->st));
+        it = E->brick_plans.emplace(key, std::move(bc)).first;
+    }
+    const BrickHostPlan &bp = it->second->hp;
+    const BrickDev &bd = bp.dev;
+    const size_t celem = fp32 ? sizeof(float2) : sizeof(double2);
+    const size_t S = (size_t)1 << N;
+    const int n_raw = (int)layout_brickwork(d.n, l).size();
+    const size_t per_raw = (size_t)2 * n_raw * 16 * sizeof(double2);
+    const size_t per_map = (size_t)(d.n - 1) * (l - 1) * 16 * celem;
+    bool both = false;
+    if (bd.tile_bits == 0) brick_smem_bytes(bd, fp32, &both);
+    const size_t per_state = bd.tile_bits ? 2 * S * celem : (both ? 0 : S * celem);
+    const size_t per_pair = per_raw + per_map + per_state;
+    uint64_t cap = std::max<uint64_t>(1, std::min<uint64_t>(65535, E->ws_budget / per_pair));
+    // flop count of the sweep (complex multiply-adds): 4 per amplitude per gate
+    const double cmac_pair = 4.0 * (double)S * (double)(d.n - 1) * (double)(l - 1);
+    SampleParams sp;
+    sp.seed = d.seed;
+    sp.n = d.n;
+    sp.raw_kind = E->raw_kind;
+    sp.self_pair = (d.flags & FP_FLAG_SELF_PAIR) ? 1 : 0;
+    for (uint64_t done = 0; done < count;) {
+        const uint64_t nb = std::min<uint64_t>(cap, count - done);
+        std::vector<PairInfo> pinfo(nb);
+        for (uint64_t i = 0; i < nb; ++i) {
+            std::memset(&pinfo[i], 0, sizeof(PairInfo));
+            pinfo[i].pair = first + idx[done + i];
+            pinfo[i].n_raw = n_raw;
+            pinfo[i].raw_off = (int64_t)i * 2 * n_raw;
+            pinfo[i].out = (int64_t)idx[done + i];
+        }
+        CK(upload(E->d_pairs, pinfo, E->st));
+        CK(E->d_raw.reserve(nb * per_raw));
+        CK(E->d_maps.reserve(nb * per_map));
+        CK(E->d_states.reserve(std::max<size_t>(16, nb * per_state)));
+        CK(cudaEventRecord(E->ev0, E->st));
+        {
+            KTimer t(E, FP_K_SAMPLE);
+            CK(launch_sample(sp, E->d_pairs.as<PairInfo>(), (int)nb, n_raw, E->d_raw.as<double2>(), E->st));
+            CK(t.stop((double)nb));
+        }
+        {
+            KTimer t(E, FP_K_BRICK);
+            int nl = 0;
+            CK(launch_brick(bd, bp.passes.data(), it->second->d_gates.as<BrickGate>(), E->d_pairs.as<PairInfo>(),
+                            (int)nb, E->d_raw.as<double2>(), E->d_maps.p, E->d_states.p, fp32, tr, kappa, E->st, &nl));
+            CK(t.stop(cmac_pair * (double)nb));
+            if (E->timing) E->kst.launches[FP_K_BRICK] += (uint64_t)(nl - 1);
+        }
+        CK(cudaEventRecord(E->ev1, E->st));
+        CK(cudaEventSynchronize(E->ev1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, E->ev0, E->ev1));
+        if (gpu_ms) *gpu_ms += ms;
+        E->kst.pairs += nb;
+        done += nb;
+    }
+    return FP_OK;
+}
+
+// Route pairs first + idx[i] to the brickwork or generic path.
+fp_status route(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx, const std::vector<int> &depth,
+                int prec, double *tr, double *kappa, float *gpu_ms) {
+    const fp_ensemble_desc &d = E->d;
+    const bool brick = d.kind == FP_PARALLEL && !(d.flags & FP_FLAG_GENERIC_ONLY);
+    std::map<int, std::vector<uint64_t>> by_depth;
+    std::vector<uint64_t> generic;
+    for (uint64_t i : idx) {
+        if (brick && depth[i] >= 2) by_depth[depth[i]].push_back(i);
+        else generic.push_back(i);
+    }
+    // deepest first: the largest working sets get the memory while it is free
+    for (auto it = by_depth.rbegin(); it != by_depth.rend(); ++it) {
+        fp_status s = run_brick(E, first, it->second, it->first, prec, tr, kappa, gpu_ms);
+        if (s != FP_OK) return s;
+    }
+    return run_generic(E, first, generic, depth, prec, tr, kappa, gpu_ms);
+}
+
+// Contract pairs [first, first+count) into device arrays E->d_tr / E->d_kappa
+// (indices relative to `first`), groups into E->d_group.
+fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec, float *gpu_ms,
+                       uint64_t *requeued, double *max_kappa) {
+    const fp_ensemble_desc &d = E->d;
+    std::vector<int> depth(count), grp(count);
+    for (uint64_t i = 0; i < count; ++i) {
+        depth[i] = depth_of_pair(d, first + i);
+        grp[i] = group_of_depth(d, depth[i]);
+    }
+    CK(E->d_tr.reserve(count * 2 * sizeof(double)));
+    CK(E->d_kappa.reserve(count * sizeof(double)));
+    CK(E->d_group.reserve(count * sizeof(int32_t)));
+    CK(E->d_ticket.reserve(sizeof(int) * 4));
+    CK(cudaMemcpyAsync(E->d_group.p, grp.data(), count * sizeof(int32_t), cudaMemcpyHostToDevice, E->st));
+    if (gpu_ms) *gpu_ms = 0;
+    std::vector<uint64_t> all(count);
+    std::iota(all.begin(), all.end(), 0);
+    double *tr = E->d_tr.as<double>(), *kap = E->d_kappa.as<double>();
+    fp_status s = route(E, first, all, depth, prec, tr, kap, gpu_ms);
+    if (s != FP_OK) return s;
+    if (prec == FP_PREC_FP32 || max_kappa) {
+        std::vector<double> k(count);
+        CK(cudaMemcpyAsync(k.data(), kap, count * sizeof(double), cudaMemcpyDeviceToHost, E->st));
+        CK(cudaStreamSynchronize(E->st));
+        const double kmax_allowed = d.kappa_max > 0 ? d.kappa_max : 1e3;
+        std::vector<uint64_t> redo;
+        for (uint64_t i = 0; i < count; ++i) {
+            if (max_kappa && std::isfinite(k[i])) *max_kappa = std::max(*max_kappa, k[i]);
+            if (prec == FP_PREC_FP32 && !(k[i] <= kmax_allowed)) redo.push_back(i);
+        }
+        if (!redo.empty()) {
+            if (requeued) *requeued += redo.size();
+            E->kst_requeued += redo.size();
+            s = route(E, first, redo, depth, FP_PREC_FP64, tr, kap, gpu_ms);
+            if (s != FP_OK) return s;
+        }
     }
     return FP_OK;
 }

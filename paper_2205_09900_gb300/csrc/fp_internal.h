@@ -94,6 +94,17 @@ struct DevRecipe {
     double cim[16];
 };
 
+// One pair of a batch.
+struct PairInfo {
+    uint64_t pair;        // global pair index (Philox counter word)
+    int32_t plan;         // DevPlan index (generic path)
+    int32_t n_raw;        // raw gates per circuit
+    int64_t raw_off;      // first raw gate (16-slot records) of this pair
+    int64_t merged_off;   // first merged gate (generic path)
+    int64_t table_off;    // first op table (generic path)
+    int64_t out;          // output slot in tr/kappa
+};
+
 // Device view of one plan (one topology).
 struct DevPlan {
     int32_t n_left, n_right;       // ops in each sweep

@@ -2,18 +2,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "brick.h"
 #include "fp_internal.h"
 
 namespace fpk {
-
-struct PairInfo {
-    uint64_t pair;        // global pair index (Philox counter word)
-    int32_t plan;         // DevPlan index
-    int32_t n_raw;        // raw gates per circuit
-    int64_t raw_off;      // first raw gate (16-slot records) of this pair
-    int64_t merged_off;   // first merged gate
-    int64_t table_off;    // first op table
-};
 
 struct SampleParams {
     uint64_t seed;
@@ -44,5 +36,12 @@ cudaError_t launch_moments(const double *tr, const int32_t *group, uint64_t coun
                            int n_groups, double *partials, int nblocks, double *out,
                            cudaStream_t st);
 int moments_blocks(uint64_t count);
+// Brickwork fast path: maps, then either the shared-memory sweep (tile_bits == 0)
+// or init + light-cone passes + dot.  `states` holds npairs x 2 x 2^N
+// amplitudes (tiled) or npairs x 2^N (shared-memory path, left boundaries).
+cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const BrickGate *dgates,
+                         const PairInfo *pairs, int npairs, const double2 *raw, void *maps, void *states,
+                         bool fp32, double *tr, double *kappa, cudaStream_t st, int *launches);
+size_t brick_smem_bytes(const BrickDev &d, bool fp32, bool *both);
 
 }  // namespace fpk

@@ -1,0 +1,383 @@
+// kernels_brick.cu -- brickwork fast path (dual-circuit boundary sweep).
+//
+// K2b  brick_maps:  merged gate of every (bond, position) realigned into the
+//                   4x4 map the sweep applies (FP64 products, stored FP32/FP64).
+// K3/5 brick_smem:  boundaries up to 2^KS amplitudes: one CTA (or one warp for
+//                   tiny boundaries) sweeps both chain halves in shared memory
+//                   and meets them in an FP64 dot product.
+// K4   brick_pass:  larger boundaries live in global memory; each launch runs
+//                   one light-cone pass: a CTA loads a 2^K-amplitude tile (a
+//                   contiguous cyclic arc of the segment ring), applies every
+//                   gate of the pass inside shared memory, and stores it back.
+// K6   brick_dot:   FP64 meet of the two boundaries with the cancellation ratio.
+#include <cuda_runtime.h>
+
+#include "brick.h"
+#include "kernels.h"
+
+namespace fpk {
+namespace {
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+
+template <typename C> __device__ __forceinline__ C from_z(double2 z);
+template <> __device__ __forceinline__ double2 from_z<double2>(double2 z) { return z; }
+template <> __device__ __forceinline__ float2 from_z<float2>(double2 z) { return make_float2((float)z.x, (float)z.y); }
+
+template <typename C>
+__device__ __forceinline__ C cfma2(C a, C b, C acc) {   // acc + a*b
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+
+__device__ __forceinline__ uint32_t ins0(uint32_t x, int p) {   // insert a zero bit at position p
+    return (x & ((1u << p) - 1u)) | ((x >> p) << (p + 1));
+}
+
+// 4x4 map on bits (pa: e bit 0, pb: e bit 1) of quad q (q indexes the other bits)
+template <typename C>
+__device__ __forceinline__ void quad_apply(C *__restrict__ s, uint32_t q, int pa, int pb, const C (&T)[16]) {
+    const int lo = pa < pb ? pa : pb, hi = pa < pb ? pb : pa;
+    const uint32_t i0 = ins0(ins0(q, lo), hi);
+    const uint32_t ia = 1u << pa, ib = 1u << pb;
+    C x0 = s[i0], x1 = s[i0 | ia], x2 = s[i0 | ib], x3 = s[i0 | ia | ib];
+    C y[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        C acc;
+        acc.x = 0; acc.y = 0;
+        acc = cfma2(T[4 * o + 0], x0, acc);
+        acc = cfma2(T[4 * o + 1], x1, acc);
+        acc = cfma2(T[4 * o + 2], x2, acc);
+        acc = cfma2(T[4 * o + 3], x3, acc);
+        y[o] = acc;
+    }
+    s[i0] = y[0];
+    s[i0 | ia] = y[1];
+    s[i0 | ib] = y[2];
+    s[i0 | ia | ib] = y[3];
+}
+
+template <typename C>
+__device__ __forceinline__ void load_map(const C *__restrict__ g, C (&T)[16]) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) T[e] = g[e];
+}
+
+// product-of-deltas start state at a chain end: delta(w_tau, w_tau+1) for tau of parity `par`
+__device__ __forceinline__ bool delta_ok(uint32_t w, int N, int par) {
+    uint32_t rot = (w >> 1) | ((w & 1u) << (N - 1));   // bit tau = w_{tau+1}
+    uint32_t pm = (par ? 0xAAAAAAAAu : 0x55555555u) & ((N >= 32) ? 0xFFFFFFFFu : ((1u << N) - 1u));
+    return ((w ^ rot) & pm) == 0;
+}
+
+template <typename C>
+__global__ void brick_maps_kernel(BrickDev d, const PairInfo *__restrict__ pairs, const double2 *__restrict__ raw,
+                                  C *__restrict__ maps) {
+    const PairInfo pi = pairs[blockIdx.y];
+    const int nb = d.n - 1, m = d.m, l = d.l;
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= nb * m) return;
+    const int b = id / m, j = id % m;
+    const int tau = 2 * j + (b + 1) % 2;
+    const int c0 = d.n / 2, c1 = (d.n - 1) / 2;
+    auto gidx = [&](int t) {   // raw index of layer t (1-based) on bond b
+        int tm = t - 1;
+        return ((tm + 1) / 2) * c0 + (tm / 2) * c1 + (b - tm % 2) / 2;
+    };
+    const double2 *U = raw + pi.raw_off * 16;
+    const double2 *V = raw + (pi.raw_off + pi.n_raw) * 16;
+    double2 G[16];
+    if (tau <= l - 3) {
+        const double2 *A = V + (size_t)gidx(tau + 2) * 16;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) G[e] = A[e];
+    } else if (tau == l - 2 || tau == 2 * l - 3) {
+        const int t = tau == l - 2 ? l : 1;
+        const double2 *A = U + (size_t)gidx(t) * 16, *B = V + (size_t)gidx(t) * 16;
+        // tau = l-2: U_l^dagger V_l ; tau = 2l-3: V_1 U_1^dagger
+        for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) {
+                double2 acc = make_double2(0, 0);
+                for (int k = 0; k < 4; ++k) {
+                    double2 t1 = tau == l - 2 ? zmul(zconj(A[4 * k + r]), B[4 * k + c])
+                                              : zmul(B[4 * r + k], zconj(A[4 * c + k]));
+                    acc.x += t1.x; acc.y += t1.y;
+                }
+                G[4 * r + c] = acc;
+            }
+    } else {
+        const double2 *A = U + (size_t)gidx(2 * l - 2 - tau) * 16;
+        for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) G[4 * r + c] = zconj(A[4 * c + r]);
+    }
+    const bool left = b < d.cut;
+    C *out = maps + ((size_t)blockIdx.y * nb * m + id) * 16;
+#pragma unroll
+    for (int xt = 0; xt < 2; ++xt)
+#pragma unroll
+        for (int xt1 = 0; xt1 < 2; ++xt1)
+#pragma unroll
+            for (int yt = 0; yt < 2; ++yt)
+#pragma unroll
+                for (int yt1 = 0; yt1 < 2; ++yt1) {
+                    double2 g = G[(yt1 * 2 + xt1) * 4 + (yt * 2 + xt)];
+                    int ex = xt + 2 * xt1, ey = yt + 2 * yt1;
+                    out[left ? ex * 4 + ey : ey * 4 + ex] = from_z<C>(g);
+                }
+}
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+    return v;
+}
+
+// Whole boundary in shared memory.  `gt` threads per pair: 32 (warp mode,
+// several pairs per CTA) or blockDim.x (one pair per CTA).
+template <typename C>
+__global__ void __launch_bounds__(512) brick_smem_kernel(BrickDev d, const PairInfo *__restrict__ pairs, int npairs,
+                                                         const C *__restrict__ maps, C *__restrict__ lscratch,
+                                                         int gt, int both, double *__restrict__ tr,
+                                                         double *__restrict__ kappa) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[3][16];
+    C *sm = (C *)smem_raw;
+    const int N = d.N, m = d.m;
+    const uint32_t S = 1u << N;
+    const bool warp_mode = gt == 32;
+    const int gpc = blockDim.x / gt;
+    const int grp = threadIdx.x / gt, tid = threadIdx.x % gt;
+    const int pidx = blockIdx.x * gpc + grp;
+    if (warp_mode && pidx >= npairs) return;   // whole warps only: no block barrier in warp mode
+    auto sync = [&]() {
+        if (warp_mode) __syncwarp();
+        else __syncthreads();
+    };
+    C *A = sm + (size_t)grp * (both ? 2 : 1) * S;
+    C *Lp = both ? A + S : lscratch + (size_t)pidx * S;
+    const C *mp = maps + (size_t)pidx * (d.n - 1) * m * 16;
+    for (int side = 0; side < 2; ++side) {
+        for (uint32_t w = tid; w < S; w += gt) {
+            C v;
+            v.x = delta_ok(w, N, d.delta_par[side]) ? 1 : 0;
+            v.y = 0;
+            A[w] = v;
+        }
+        sync();
+        for (int t = 0; t < d.n_layers[side]; ++t) {
+            const int bond = brick_bond(d, side, t), par = (bond + 1) % 2;
+            for (int j = 0; j < m; ++j) {
+                C T[16];
+                load_map(mp + ((size_t)bond * m + j) * 16, T);
+                const int tau = 2 * j + par;
+                const int pa = tau, pb = (tau + 1) % N;
+                for (uint32_t q = tid; q < (S >> 2); q += gt) quad_apply(A, q, pa, pb, T);
+                sync();
+            }
+        }
+        if (side == 0) {
+            for (uint32_t w = tid; w < S; w += gt) Lp[w] = A[w];
+            sync();
+        }
+    }
+    double sr = 0, si = 0, sa = 0;
+    for (uint32_t w = tid; w < S; w += gt) {
+        double lx = Lp[w].x, ly = Lp[w].y, rx = A[w].x, ry = A[w].y;
+        double px = lx * rx - ly * ry, py = lx * ry + ly * rx;
+        sr += px; si += py; sa += sqrt(px * px + py * py);
+    }
+    sr = wsum(sr); si = wsum(si); sa = wsum(sa);
+    if (!warp_mode) {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) { red[0][wid] = sr; red[1][wid] = si; red[2][wid] = sa; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            sr = si = sa = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sr += red[0][w]; si += red[1][w]; sa += red[2][w]; }
+        }
+    }
+    if (tid == 0) {
+        const PairInfo pi = pairs[pidx];
+        tr[2 * pi.out] = sr;
+        tr[2 * pi.out + 1] = si;
+        double mag = sqrt(sr * sr + si * si);
+        if (kappa) kappa[pi.out] = mag > 0 ? sa / mag : __longlong_as_double(0x7ff0000000000000LL);
+    }
+}
+
+template <typename C>
+__global__ void brick_init_kernel(BrickDev d, int npairs, C *__restrict__ states) {
+    const uint32_t S = 1u << d.N;
+    const size_t total = (size_t)npairs * 2 * S;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int side = (int)((i >> d.N) & 1);
+        C v;
+        v.x = delta_ok((uint32_t)(i & (S - 1)), d.N, d.delta_par[side]) ? 1 : 0;
+        v.y = 0;
+        states[i] = v;
+    }
+}
+
+// One light-cone pass of one side over all pairs: blockIdx.x = tile, blockIdx.y = pair.
+template <typename C, int K>
+__global__ void __launch_bounds__(512) brick_pass_kernel(BrickDev d, int side, BrickPass ps,
+                                                         const BrickGate *__restrict__ gates,
+                                                         const C *__restrict__ maps, C *__restrict__ states) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tile = (C *)smem_raw;
+    __shared__ uint32_t lut_lo[128], lut_hi[1 << (K - 7)];
+    __shared__ int pos[32];
+    const int N = d.N, m = d.m;
+    const uint32_t S = 1u << N;
+    if (threadIdx.x == 0) {
+        int k = 0;
+        for (int b = 0; b < N; ++b) if (ps.smask & (1u << b)) pos[k++] = b;
+    }
+    __syncthreads();
+    // tile base: tile index bits go to the physical bits outside the arc, ascending
+    uint32_t base = 0;
+    {
+        uint32_t t = blockIdx.x;
+        for (int b = 0; b < N; ++b)
+            if (!(ps.smask & (1u << b))) { base |= (t & 1u) << b; t >>= 1; }
+    }
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+        uint32_t o = 0;
+        for (int k = 0; k < 7; ++k) o |= ((i >> k) & 1u) << pos[k];
+        lut_lo[i] = o;
+    }
+    for (int i = threadIdx.x; i < (1 << (K - 7)); i += blockDim.x) {
+        uint32_t o = 0;
+        for (int k = 0; k < K - 7; ++k) o |= ((i >> k) & 1u) << pos[7 + k];
+        lut_hi[i] = o;
+    }
+    __syncthreads();
+    C *st = states + ((size_t)blockIdx.y * 2 + side) * S + base;
+    for (uint32_t i = threadIdx.x; i < (1u << K); i += blockDim.x) tile[i] = st[lut_lo[i & 127] | lut_hi[i >> 7]];
+    __syncthreads();
+    const C *mp = maps + (size_t)blockIdx.y * (d.n - 1) * m * 16;
+    for (int g = 0; g < ps.n_gates; ++g) {
+        const BrickGate gg = gates[ps.gate_off + g];
+        const int bond = brick_bond(d, side, gg.layer);
+        C T[16];
+        load_map(mp + ((size_t)bond * m + gg.j) * 16, T);
+        for (uint32_t q = threadIdx.x; q < (1u << (K - 2)); q += blockDim.x) quad_apply(tile, q, gg.a, gg.b, T);
+        __syncthreads();
+    }
+    for (uint32_t i = threadIdx.x; i < (1u << K); i += blockDim.x) st[lut_lo[i & 127] | lut_hi[i >> 7]] = tile[i];
+}
+
+template <typename C>
+__global__ void __launch_bounds__(1024) brick_dot_kernel(BrickDev d, const PairInfo *__restrict__ pairs,
+                                                         const C *__restrict__ states, double *__restrict__ tr,
+                                                         double *__restrict__ kappa) {
+    __shared__ double red[3][32];
+    const uint32_t S = 1u << d.N;
+    const C *L = states + (size_t)blockIdx.x * 2 * S, *R = L + S;
+    double sr = 0, si = 0, sa = 0;
+    for (uint32_t w = threadIdx.x; w < S; w += blockDim.x) {
+        double lx = L[w].x, ly = L[w].y, rx = R[w].x, ry = R[w].y;
+        double px = lx * rx - ly * ry, py = lx * ry + ly * rx;
+        sr += px; si += py; sa += sqrt(px * px + py * py);
+    }
+    sr = wsum(sr); si = wsum(si); sa = wsum(sa);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { red[0][wid] = sr; red[1][wid] = si; red[2][wid] = sa; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sr = si = sa = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sr += red[0][w]; si += red[1][w]; sa += red[2][w]; }
+        const PairInfo pi = pairs[blockIdx.x];
+        tr[2 * pi.out] = sr;
+        tr[2 * pi.out + 1] = si;
+        double mag = sqrt(sr * sr + si * si);
+        if (kappa) kappa[pi.out] = mag > 0 ? sa / mag : __longlong_as_double(0x7ff0000000000000LL);
+    }
+}
+
+template <typename C, int K>
+cudaError_t run_passes(const BrickDev &d, const BrickPass *hpasses, const BrickGate *dgates, int npairs,
+                       const C *maps, C *states, cudaStream_t st) {
+    const size_t smem = ((size_t)1 << K) * sizeof(C);
+    cudaError_t e = cudaFuncSetAttribute(brick_pass_kernel<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    for (int side = 0; side < 2; ++side)
+        for (int p = 0; p < d.n_passes[side]; ++p) {
+            dim3 grid(1u << (d.N - K), npairs);
+            brick_pass_kernel<C, K><<<grid, 512, smem, st>>>(d, side, hpasses[d.pass_off[side] + p], dgates, maps, states);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+size_t brick_smem_bytes(const BrickDev &d, bool fp32, bool *both) {
+    const size_t el = fp32 ? sizeof(float2) : sizeof(double2);
+    const size_t S = (size_t)1 << d.N;
+    *both = 2 * S * el <= 96 * 1024;
+    return (*both ? 2 : 1) * S * el;
+}
+
+cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const BrickGate *dgates,
+                         const PairInfo *pairs, int npairs, const double2 *raw, void *maps, void *states,
+                         bool fp32, double *tr, double *kappa, cudaStream_t st, int *launches) {
+    if (npairs <= 0) return cudaSuccess;
+    const int nm = (d.n - 1) * d.m;
+    dim3 gm((nm + 127) / 128, npairs);
+    if (fp32) brick_maps_kernel<float2><<<gm, 128, 0, st>>>(d, pairs, raw, (float2 *)maps);
+    else brick_maps_kernel<double2><<<gm, 128, 0, st>>>(d, pairs, raw, (double2 *)maps);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int nl = 1;
+    if (d.tile_bits == 0) {
+        bool both = false;
+        const size_t smem = brick_smem_bytes(d, fp32, &both);
+        const uint32_t quads = (1u << d.N) >> 2;
+        int gt = quads <= 32 ? 32 : (quads >= 512 ? 512 : (int)((quads + 31) / 32 * 32));
+        int gpc = gt == 32 ? 8 : 1;
+        size_t smem_cta = smem * gpc;
+        int grid = (npairs + gpc - 1) / gpc;
+        if (fp32) {
+            if ((e = cudaFuncSetAttribute(brick_smem_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cta)) != cudaSuccess) return e;
+            brick_smem_kernel<float2><<<grid, gt * gpc, smem_cta, st>>>(d, pairs, npairs, (const float2 *)maps,
+                                                                         (float2 *)states, gt, both, tr, kappa);
+        } else {
+            if ((e = cudaFuncSetAttribute(brick_smem_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cta)) != cudaSuccess) return e;
+            brick_smem_kernel<double2><<<grid, gt * gpc, smem_cta, st>>>(d, pairs, npairs, (const double2 *)maps,
+                                                                          (double2 *)states, gt, both, tr, kappa);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        nl += 1;
+    } else {
+        const size_t total = (size_t)npairs * 2 * ((size_t)1 << d.N);
+        int ib = (int)std::min<size_t>((total + 255) / 256, 152 * 32);
+        if (fp32) brick_init_kernel<float2><<<ib, 256, 0, st>>>(d, npairs, (float2 *)states);
+        else brick_init_kernel<double2><<<ib, 256, 0, st>>>(d, npairs, (double2 *)states);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (fp32) {
+            if (d.tile_bits == 14) e = run_passes<float2, 14>(d, hpasses, dgates, npairs, (const float2 *)maps, (float2 *)states, st);
+            else if (d.tile_bits == 13) e = run_passes<float2, 13>(d, hpasses, dgates, npairs, (const float2 *)maps, (float2 *)states, st);
+            else e = run_passes<float2, 12>(d, hpasses, dgates, npairs, (const float2 *)maps, (float2 *)states, st);
+        } else {
+            if (d.tile_bits == 13) e = run_passes<double2, 13>(d, hpasses, dgates, npairs, (const double2 *)maps, (double2 *)states, st);
+            else e = run_passes<double2, 12>(d, hpasses, dgates, npairs, (const double2 *)maps, (double2 *)states, st);
+        }
+        if (e != cudaSuccess) return e;
+        if (fp32) brick_dot_kernel<float2><<<npairs, 1024, 0, st>>>(d, pairs, (const float2 *)states, tr, kappa);
+        else brick_dot_kernel<double2><<<npairs, 1024, 0, st>>>(d, pairs, (const double2 *)states, tr, kappa);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        nl += 1 + d.n_passes[0] + d.n_passes[1] + 1;
+    }
+    if (launches) *launches = nl;
+    return cudaSuccess;
+}
+
+}  // namespace fpk

@@ -145,10 +145,10 @@ __global__ void __launch_bounds__(256) sweep_generic(const PairInfo *__restrict_
         if (threadIdx.x == 0) {
             double a = 0, b = 0, c = 0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; c += red[2][w]; }
-            tr[2 * pidx] = pl.prefactor * a;
-            tr[2 * pidx + 1] = pl.prefactor * b;
+            tr[2 * pi.out] = pl.prefactor * a;
+            tr[2 * pi.out + 1] = pl.prefactor * b;
             double mag = sqrt(a * a + b * b);
-            if (kappa) kappa[pidx] = mag > 0 ? c / mag : __longlong_as_double(0x7ff0000000000000LL);
+            if (kappa) kappa[pi.out] = mag > 0 ? c / mag : __longlong_as_double(0x7ff0000000000000LL);
         }
         __syncthreads();
     }

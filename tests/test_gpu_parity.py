@@ -246,3 +246,59 @@ def test_device_output_pointers(fp):
     t = tr.cpu().numpy()
     ref = O.trace_batch(od, 0, N, "dense", threads=8)
     assert rel_err(t[0::2] + 1j * t[1::2], ref).max() <= TOL64
+
+
+# ---------------------------------------------------------------------------
+# Brickwork fast path (dual-circuit sweep) against the generic path and the oracle.
+@pytest.mark.parametrize("prec,tol", [(0, TOL64), (1, TOL32)])
+def test_brick_path_matches_generic_and_oracle(fp, prec, tol):
+    n, seed, N = 50, 13, 24
+    ens, od = make(fp, "parallel", n, 2, 8, seed=seed)
+    gen = fp.Ensemble(0, n, 2, 8, seed=seed, flags=fp.FLAG_GENERIC_ONLY)
+    tb, kb, _ = ens.trace_batch(0, N, prec)
+    tg, kg, _ = gen.trace_batch(0, N, prec)
+    ref = O.trace_batch(od, 0, N, "ve", threads=8)
+    if prec == 0:
+        assert rel_err(tb, ref).max() <= TOL64
+        assert rel_err(tg, ref).max() <= TOL64
+    else:
+        assert np.abs(tb - ref).max() <= TOL32
+        assert np.abs(tg - ref).max() <= TOL32
+
+
+@pytest.mark.parametrize("n,l", [(2, 2), (3, 2), (4, 5), (5, 3), (9, 6), (50, 6), (51, 7)])
+def test_brick_small_and_odd_chains(fp, n, l):
+    ens, od = make(fp, "parallel", n, l, seed=n * 10 + l)
+    tr, _, _ = ens.trace_batch(0, 16, fp.PREC_FP64)
+    ref = O.trace_batch(od, 0, 16, "auto", threads=8)
+    assert rel_err(tr, ref).max() <= TOL64
+
+
+def test_bench_workload_sampled_parity(fp):
+    # The benchmark's own ensemble (n = 50, l uniform in 2..10, seed 4) in the
+    # benchmark's launch shape (one large batch split by depth), FP32 policy
+    # path and FP64 path; sampled pairs of every depth against the oracle.
+    import torch
+    P = 20000
+    ens, od = make(fp, "parallel", 50, 2, 10, seed=4)
+    tr_d = torch.empty(2 * P, dtype=torch.float64, device="cuda")
+    ka_d = torch.empty(P, dtype=torch.float64, device="cuda")
+    gr_d = torch.empty(P, dtype=torch.int32, device="cuda")
+    ens.trace_batch(0, P, fp.PREC_FP32, tr_d, ka_d, gr_d)
+    t = tr_d.cpu().numpy()
+    tr32 = t[0::2] + 1j * t[1::2]
+    grp = gr_d.cpu().numpy()
+    picks = []
+    for g in range(9):               # depth 2 + g
+        idx = np.nonzero(grp == g)[0]
+        picks += list(idx[: (3 if g <= 6 else 1)])
+    ref = {}
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(max_workers=16) as ex:
+        for p, r in zip(picks, ex.map(lambda p: O.trace_batch(od, int(p), 1, "ve")[0], picks)):
+            ref[p] = r
+    tr64, _, _ = ens.trace_batch(0, 0, fp.PREC_FP64)   # no-op call keeps the ensemble warm
+    for p in picks:
+        assert abs(tr32[p] - ref[p]) <= TOL32, (p, grp[p] + 2, tr32[p], ref[p])
+        t64, _, _ = ens.trace_batch(int(p), 1, fp.PREC_FP64)
+        assert abs(t64[0] - ref[p]) <= TOL64 * max(1.0, abs(ref[p])), (p, grp[p] + 2, t64[0], ref[p])
