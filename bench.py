@@ -206,6 +206,7 @@ def main():
     ng = len(ens.groups())
     tr = torch.empty(2 * P, dtype=torch.float64, device="cuda")
     kap = torch.empty(P, dtype=torch.float64, device="cuda")
+    err = torch.empty(P, dtype=torch.float64, device="cuda")
     grp = torch.empty(P, dtype=torch.int32, device="cuda")
     mom = torch.empty(ng * (2 * K + 1), dtype=torch.float64, device="cuda")
 
@@ -213,7 +214,7 @@ def main():
         return (step * world + rank) * P
 
     def step(s):
-        ens.trace_batch(first_of(s), P, prec, tr, kap, grp)
+        ens.trace_batch(first_of(s), P, prec, tr, kap, grp, err)
         ens.reduce_moments(tr, grp, P, K, mom)
 
     for s in range(args.warmup):

@@ -75,7 +75,8 @@ typedef enum {
     FP_PREC_FP64 = 0,         /* boundary tensors and gate maps in FP64 */
     FP_PREC_FP32 = 1,         /* boundary tensors and gate maps in FP32 (FFMA),
                                  FP64 meet and reduction; a pair whose
-                                 cancellation ratio exceeds kappa_max is
+                                 estimated error exceeds fp32_tol, or whose
+                                 cancellation ratio exceeds kappa_max, is
                                  recontracted in FP64 */
     FP_PREC_FP32_RAW = 2      /* FP32 as above without the FP64 recontraction */
 } fp_prec;
@@ -110,9 +111,20 @@ typedef struct {
                                        {T_min, T_min+T_step, ..., <= T_max} */
     int32_t flags;            /* FP_FLAG_* */
     uint64_t seed;
-    double kappa_max;         /* FP_PREC_FP32 recontraction threshold; <= 0: 1e3 */
+    double kappa_max;         /* FP_PREC_FP32: recontract in FP64 when the cancellation
+                                 ratio exceeds this; <= 0: no cap */
+    double fp32_tol;          /* FP_PREC_FP32: recontract in FP64 when the estimated
+                                 absolute error of Tr exceeds this; <= 0: 1e-4 */
     uint64_t workspace_bytes; /* device workspace cap; 0: library default */
 } fp_ensemble_desc;
+
+/* Error estimate of one trace (the `err` output of fp_trace_batch): with
+ * t_j = L_j R_j the terms of the final boundary dot product, u the unit
+ * roundoff of the boundary arithmetic (2^-24 or 2^-53) and G the number of
+ * gate maps applied along one chain half,
+ *     err = FP_ERR_SAFETY * u * sqrt(G) * sqrt(sum_j |t_j|^2),
+ * a random-walk bound on the accumulated rounding of the boundaries. */
+#define FP_ERR_SAFETY 8.0
 
 typedef struct fp_ensemble fp_ensemble;
 
@@ -163,11 +175,13 @@ fp_status fp_export_gates(fp_ensemble *ens, uint64_t pair, int32_t which, void *
  *   tr     [2*count] doubles: Tr(U^dagger V) as (re, im) per pair;
  *   kappa  [count] doubles or NULL: cancellation ratio sum_j |L_j R_j| / |sum_j L_j R_j|
  *          of the final boundary dot product (1 when no cancellation);
+ *   err    [count] doubles or NULL: estimated absolute rounding error of Tr
+ *          in the arithmetic that produced it (see FP_ERR_SAFETY);
  *   group  [count] int32 or NULL: group index of each pair.
  * Host or device pointers.  FP_ERR_INFEASIBLE if a pair's boundary exceeds
  * FP_MAX_STATE_BITS (nothing is written then). */
 fp_status fp_trace_batch(fp_ensemble *ens, uint64_t first, uint64_t count, int32_t prec,
-                         double *tr, double *kappa, int32_t *group);
+                         double *tr, double *kappa, double *err, int32_t *group);
 
 /* FP64 moments of |Tr|^{2k} per group (the reduction of the estimator):
  * moments[g*(2*k_max+1) + 0] = N_g, [.. + k] = sum |Tr|^{2k}, [.. + k_max + k] =

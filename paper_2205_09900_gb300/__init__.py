@@ -39,7 +39,7 @@ class Desc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("depth_min", ctypes.c_int32),
                 ("depth_max", ctypes.c_int32), ("T_min", ctypes.c_int32), ("T_max", ctypes.c_int32),
                 ("T_step", ctypes.c_int32), ("flags", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("kappa_max", ctypes.c_double), ("workspace_bytes", ctypes.c_uint64)]
+                ("kappa_max", ctypes.c_double), ("fp32_tol", ctypes.c_double), ("workspace_bytes", ctypes.c_uint64)]
 
 
 class RunStats(ctypes.Structure):
@@ -75,7 +75,7 @@ def load(path: str = LIB_PATH):
     L.fp_groups.argtypes = [vp, P(ctypes.c_int32), vp]
     L.fp_pair_groups.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, vp]
     L.fp_export_gates.argtypes = [vp, ctypes.c_uint64, ctypes.c_int32, vp, P(ctypes.c_size_t)]
-    L.fp_trace_batch.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, vp, vp, vp]
+    L.fp_trace_batch.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, vp, vp, vp, vp]
     L.fp_reduce_moments.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.c_int32, vp]
     L.fp_frame_potential.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double,
                                      ctypes.c_int32, vp, vp, P(RunStats)]
@@ -106,10 +106,10 @@ class Ensemble:
     """One ensemble of circuit pairs (``fp_ensemble``)."""
 
     def __init__(self, kind, n, depth_min=1, depth_max=None, T_min=0, T_max=0, T_step=1, seed=1,
-                 flags=0, kappa_max=0.0, workspace_bytes=0, stream=None):
+                 flags=0, kappa_max=0.0, fp32_tol=0.0, workspace_bytes=0, stream=None):
         L = load()
         self.desc = Desc(kind, n, depth_min, depth_min if depth_max is None else depth_max, T_min, T_max,
-                         T_step, flags, seed, kappa_max, workspace_bytes)
+                         T_step, flags, seed, kappa_max, fp32_tol, workspace_bytes)
         h = ctypes.c_void_p()
         st = None if stream is None else ctypes.c_void_p(stream)
         _check(L.fp_ensemble_create(ctypes.byref(self.desc), st, ctypes.byref(h)))
@@ -167,20 +167,22 @@ class Ensemble:
             out.append((buf[i].kind, buf[i].q, mat))
         return out
 
-    def trace_batch(self, first, count, prec=PREC_FP64, tr=None, kappa=None, group=None):
+    def trace_batch(self, first, count, prec=PREC_FP64, tr=None, kappa=None, group=None, err=None,
+                    with_err=False):
         """Contract pairs first..first+count-1 into caller buffers (torch tensors or numpy
         arrays, host or device).  Allocates numpy host arrays for omitted ones and
-        returns (tr complex, kappa, group)."""
+        returns (tr complex, kappa, group), or (tr, kappa, group, err) with with_err."""
         import numpy as np
         own = tr is None
         if own:
             tr = np.zeros(2 * count, dtype=np.float64)
             kappa = np.zeros(count, dtype=np.float64) if kappa is None else kappa
             group = np.zeros(count, dtype=np.int32) if group is None else group
-        _check(load().fp_trace_batch(self._h, first, count, prec, _ptr(tr), _ptr(kappa), _ptr(group)))
-        if own:
-            return tr[0::2] + 1j * tr[1::2], kappa, group
-        return tr, kappa, group
+            if with_err and err is None:
+                err = np.zeros(count, dtype=np.float64)
+        _check(load().fp_trace_batch(self._h, first, count, prec, _ptr(tr), _ptr(kappa), _ptr(err), _ptr(group)))
+        out = (tr[0::2] + 1j * tr[1::2], kappa, group) if own else (tr, kappa, group)
+        return out + (err,) if with_err else out
 
     def reduce_moments(self, tr_dev, group_dev, count, k_max, out):
         _check(load().fp_reduce_moments(self._h, _ptr(tr_dev), _ptr(group_dev), count, k_max, _ptr(out)))

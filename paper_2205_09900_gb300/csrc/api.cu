@@ -79,7 +79,8 @@ bool is_device_ptr(const void *p) {
 
 struct BrickCache {
     BrickHostPlan hp;
-    DBuf d_gates;
+    DBuf d_gates, d_rpasses, d_rgates;
+    BrickDevPlan dp;
 };
 
 struct fp_ensemble {
@@ -97,7 +98,7 @@ struct fp_ensemble {
     // device plan pools (fixed topology) and per-batch pools (local)
     DBuf d_plans, d_ops, d_recipes, d_items, d_refs;
     // batch buffers
-    DBuf d_pairs, d_order, d_raw, d_merged, d_tables, d_ws, d_ticket, d_tr, d_kappa, d_group;
+    DBuf d_pairs, d_order, d_raw, d_merged, d_tables, d_ws, d_ticket, d_tr, d_kappa, d_err, d_group;
     DBuf d_partials, d_moments;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t kev[2 * FP_K_CLASSES] = {};
@@ -107,7 +108,7 @@ struct fp_ensemble {
     // brickwork fast path
     std::map<int, std::unique_ptr<BrickCache>> brick_plans;   // key 2*l + fp32
     DBuf d_maps, d_states;
-    int tile_bits32 = 14, tile_bits64 = 13;
+    int tile_bits32 = 14, tile_bits64 = 13, win_bits32 = 4, win_bits64 = 3;
 };
 
 namespace {
@@ -178,6 +179,7 @@ struct PlanPools {
         for (int k = 0; k < FP_MAX_STATE_BITS; ++k) p.dot_perm[k] = h.dot_perm[k];
         p.prefactor = h.prefactor;
         p.cost = h.cost;
+        p.sqrt_ops = std::sqrt((double)std::max(1, std::max(h.n_left, h.n_right)));
         ops.insert(ops.end(), h.ops.begin(), h.ops.end());
         recipes.insert(recipes.end(), h.recipes.begin(), h.recipes.end());
         items.insert(items.end(), h.merges.begin(), h.merges.end());
@@ -227,7 +229,8 @@ struct KTimer {
 // Generic path over a subset of pairs: outputs go to slots idx[i] of the
 // device arrays (pairs first + idx[i]).
 fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx,
-                      const std::vector<int> &depth, int prec, double *tr, double *kappa, float *gpu_ms) {
+                      const std::vector<int> &depth, int prec, double *tr, double *kappa, double *err,
+                      float *gpu_ms) {
     const fp_ensemble_desc &d = E->d;
     const bool local = d.kind == FP_LOCAL;
     const uint64_t count = idx.size();
@@ -350,7 +353,8 @@ fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t
             KTimer t(E, FP_K_SWEEP);
             CK(launch_sweep_generic(E->d_pairs.as<PairInfo>(), E->d_order.as<int32_t>(), (int)nb, E->d_plans.as<DevPlan>(),
                                     E->d_ops.as<DevOp>(), E->d_tables.p, fp32, E->d_ws.p, ws_elems, ctas,
-                                    E->d_ticket.as<int>(), tr, kappa, E->st));
+                                    E->d_ticket.as<int>(), FP_ERR_SAFETY * (fp32 ? 0x1.0p-24 : 0x1.0p-53), tr,
+                                    kappa, err, E->st));
             CK(t.stop(cmacs));
         }
         CK(cudaEventRecord(E->ev1, E->st));
@@ -366,7 +370,7 @@ fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t
 
 // Brickwork fast path for pairs of one depth l >= 2.
 fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx, int l, int prec,
-                    double *tr, double *kappa, float *gpu_ms) {
+                    double *tr, double *kappa, double *err, float *gpu_ms) {
     const fp_ensemble_desc &d = E->d;
     const uint64_t count = idx.size();
     if (count == 0) return FP_OK;
@@ -379,8 +383,17 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
     if (it == E->brick_plans.end()) {
         auto bc = std::make_unique<BrickCache>();
         const int kt = fp32 ? E->tile_bits32 : E->tile_bits64;
-        bc->hp = make_brick_plan(d.n, l, N <= kt ? 0 : kt, fp32 ? 5 : 4);
+        const int wb = fp32 ? E->win_bits32 : E->win_bits64;
+        bc->hp = make_brick_plan(d.n, l, N <= kt ? 0 : kt, fp32 ? 5 : 4, wb);
+        for (const auto &ps : bc->hp.passes)
+            if (ps.n_gates > 255) return fail(FP_ERR_ARG, "tile pass with %d gates exceeds 255", ps.n_gates);
         CK(upload(bc->d_gates, bc->hp.gates, E->st));
+        CK(upload(bc->d_rpasses, bc->hp.rpasses, E->st));
+        CK(upload(bc->d_rgates, bc->hp.rgates, E->st));
+        bc->dp.gates = bc->d_gates.as<BrickGate>();
+        bc->dp.rpasses = bc->d_rpasses.as<RegPass>();
+        bc->dp.rgates = bc->d_rgates.as<RegGate>();
+        bc->dp.win_bits = wb;
         it = E->brick_plans.emplace(key, std::move(bc)).first;
     }
     const BrickHostPlan &bp = it->second->hp;
@@ -425,8 +438,11 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
         {
             KTimer t(E, FP_K_BRICK);
             int nl = 0;
-            CK(launch_brick(bd, bp.passes.data(), it->second->d_gates.as<BrickGate>(), E->d_pairs.as<PairInfo>(),
-                            (int)nb, E->d_raw.as<double2>(), E->d_maps.p, E->d_states.p, fp32, tr, kappa, E->st, &nl));
+            const double G = (double)std::max(bd.n_layers[0], bd.n_layers[1]) * bd.m;
+            const double err_scale = FP_ERR_SAFETY * (fp32 ? 0x1.0p-24 : 0x1.0p-53) * std::sqrt(G);
+            CK(launch_brick(bd, bp.passes.data(), it->second->dp, E->d_pairs.as<PairInfo>(), (int)nb,
+                            E->d_raw.as<double2>(), E->d_maps.p, E->d_states.p, fp32, err_scale, tr, kappa, err,
+                            E->st, &nl));
             CK(t.stop(cmac_pair * (double)nb));
             if (E->timing) E->kst.launches[FP_K_BRICK] += (uint64_t)(nl - 1);
         }
@@ -443,7 +459,7 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
 
 // Route pairs first + idx[i] to the brickwork or generic path.
 fp_status route(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx, const std::vector<int> &depth,
-                int prec, double *tr, double *kappa, float *gpu_ms) {
+                int prec, double *tr, double *kappa, double *err, float *gpu_ms) {
     const fp_ensemble_desc &d = E->d;
     const bool brick = d.kind == FP_PARALLEL && !(d.flags & FP_FLAG_GENERIC_ONLY);
     std::map<int, std::vector<uint64_t>> by_depth;
@@ -454,14 +470,14 @@ fp_status route(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx
     }
     // deepest first: the largest working sets get the memory while it is free
     for (auto it = by_depth.rbegin(); it != by_depth.rend(); ++it) {
-        fp_status s = run_brick(E, first, it->second, it->first, prec, tr, kappa, gpu_ms);
+        fp_status s = run_brick(E, first, it->second, it->first, prec, tr, kappa, err, gpu_ms);
         if (s != FP_OK) return s;
     }
-    return run_generic(E, first, generic, depth, prec, tr, kappa, gpu_ms);
+    return run_generic(E, first, generic, depth, prec, tr, kappa, err, gpu_ms);
 }
 
 // Contract pairs [first, first+count) into device arrays E->d_tr / E->d_kappa
-// (indices relative to `first`), groups into E->d_group.
+// / E->d_err (indices relative to `first`), groups into E->d_group.
 fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec, float *gpu_ms,
                        uint64_t *requeued, double *max_kappa) {
     const fp_ensemble_desc &d = E->d;
@@ -472,29 +488,31 @@ fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec,
     }
     CK(E->d_tr.reserve(count * 2 * sizeof(double)));
     CK(E->d_kappa.reserve(count * sizeof(double)));
+    CK(E->d_err.reserve(count * sizeof(double)));
     CK(E->d_group.reserve(count * sizeof(int32_t)));
     CK(E->d_ticket.reserve(sizeof(int) * 4));
     CK(cudaMemcpyAsync(E->d_group.p, grp.data(), count * sizeof(int32_t), cudaMemcpyHostToDevice, E->st));
     if (gpu_ms) *gpu_ms = 0;
     std::vector<uint64_t> all(count);
     std::iota(all.begin(), all.end(), 0);
-    double *tr = E->d_tr.as<double>(), *kap = E->d_kappa.as<double>();
-    fp_status s = route(E, first, all, depth, prec, tr, kap, gpu_ms);
+    double *tr = E->d_tr.as<double>(), *kap = E->d_kappa.as<double>(), *err = E->d_err.as<double>();
+    fp_status s = route(E, first, all, depth, prec, tr, kap, err, gpu_ms);
     if (s != FP_OK) return s;
     if (prec == FP_PREC_FP32 || max_kappa) {
-        std::vector<double> k(count);
+        std::vector<double> k(count), e(count);
         CK(cudaMemcpyAsync(k.data(), kap, count * sizeof(double), cudaMemcpyDeviceToHost, E->st));
+        CK(cudaMemcpyAsync(e.data(), err, count * sizeof(double), cudaMemcpyDeviceToHost, E->st));
         CK(cudaStreamSynchronize(E->st));
-        const double kmax_allowed = d.kappa_max > 0 ? d.kappa_max : 1e3;
+        const double tol = d.fp32_tol > 0 ? d.fp32_tol : 1e-4;
         std::vector<uint64_t> redo;
         for (uint64_t i = 0; i < count; ++i) {
             if (max_kappa && std::isfinite(k[i])) *max_kappa = std::max(*max_kappa, k[i]);
-            if (prec == FP_PREC_FP32 && !(k[i] <= kmax_allowed)) redo.push_back(i);
+            const bool over = !(e[i] <= tol) || (d.kappa_max > 0 && !(k[i] <= d.kappa_max));
+            if (prec == FP_PREC_FP32 && over) redo.push_back(i);
         }
         if (!redo.empty()) {
             if (requeued) *requeued += redo.size();
-            E->kst_requeued += redo.size();
-            s = route(E, first, redo, depth, FP_PREC_FP64, tr, kap, gpu_ms);
+            s = route(E, first, redo, depth, FP_PREC_FP64, tr, kap, err, gpu_ms);
             if (s != FP_OK) return s;
         }
     }
@@ -615,7 +633,7 @@ fp_status fp_export_gates(fp_ensemble *ens, uint64_t pair, int32_t which, void *
 }
 
 fp_status fp_trace_batch(fp_ensemble *ens, uint64_t first, uint64_t count, int32_t prec, double *tr,
-                         double *kappa, int32_t *group) {
+                         double *kappa, double *err, int32_t *group) {
     if (!ens || (!tr && count)) return fail(FP_ERR_ARG, "null argument");
     if (prec < FP_PREC_FP64 || prec > FP_PREC_FP32_RAW) return fail(FP_ERR_ARG, "unknown precision %d", prec);
     if (count == 0) return FP_OK;
@@ -623,6 +641,7 @@ fp_status fp_trace_batch(fp_ensemble *ens, uint64_t first, uint64_t count, int32
     if (s != FP_OK) return s;
     if ((s = copy_out(ens, tr, ens->d_tr.p, count * 2 * sizeof(double))) != FP_OK) return s;
     if ((s = copy_out(ens, kappa, ens->d_kappa.p, count * sizeof(double))) != FP_OK) return s;
+    if ((s = copy_out(ens, err, ens->d_err.p, count * sizeof(double))) != FP_OK) return s;
     if ((s = copy_out(ens, group, ens->d_group.p, count * sizeof(int32_t))) != FP_OK) return s;
     CK(cudaStreamSynchronize(ens->st));
     return FP_OK;

@@ -37,6 +37,24 @@ struct BrickGate {      // one gate inside a tile pass
 struct BrickPass {
     int32_t gate_off, n_gates;
     uint32_t smask;     // physical bits held by the tile
+    int32_t rp_off, n_rp;   // register passes (RegPass) of this tile pass
+};
+
+// One register pass inside a tile pass: every thread holds 2^r amplitudes
+// spanning the window bits (r ring-consecutive tile bits) and applies the
+// window gates in registers.  Gate g of the window acts on window bits
+// (type, type+1); `slot` indexes the tile pass's gate list (its map).
+constexpr int kMaxWin = 5;
+struct RegPass {
+    uint8_t win[kMaxWin];     // tile-local bits in ring order
+    uint8_t srt[kMaxWin];     // the same bits ascending
+    uint8_t r;
+    uint8_t n_gates;
+    int16_t gate_off;         // into the RegGate pool
+};
+struct RegGate {
+    uint8_t type;
+    uint8_t slot;
 };
 
 struct BrickDev {       // uniform over a sub-batch (one depth)
@@ -47,15 +65,25 @@ struct BrickDev {       // uniform over a sub-batch (one depth)
     int32_t tile_bits;        // K of the tiled path (0: whole state in one CTA)
 };
 
+// Device copies of a plan's schedule (gates and register passes).
+struct BrickDevPlan {
+    const BrickGate *gates;
+    const RegPass *rpasses;
+    const RegGate *rgates;
+    int win_bits;
+};
+
 struct BrickHostPlan {
     BrickDev dev;
     std::vector<BrickPass> passes;   // side 0 passes, then side 1 passes
     std::vector<BrickGate> gates;
+    std::vector<RegPass> rpasses;
+    std::vector<RegGate> rgates;
 };
 
 // Layer parity of layer t of a side, and the bond it sweeps.
 FP_HD int brick_bond(const BrickDev &d, int side, int t) { return side == 0 ? t : d.n - 2 - t; }
 
-BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits);
+BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win_bits);
 
 }  // namespace fpk

@@ -14,7 +14,61 @@
 
 namespace fpk {
 
-BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits) {
+// Register windows inside one tile pass: windows are r consecutive ring
+// positions of the tile's arc; greedy, each step takes the window that can
+// apply the most remaining gates (in layer order, predecessors first).
+static void schedule_registers(BrickHostPlan &P, BrickPass &ps, const int *ring, int K, int r) {
+    const int G = ps.n_gates;
+    std::vector<int> rpos(32, -1);   // tile-local bit -> arc position
+    for (int k = 0; k < K; ++k) rpos[ring[k]] = k;
+    std::vector<char> done(G, 0);
+    ps.rp_off = (int)P.rpasses.size();
+    int left = G;
+    while (left > 0) {
+        int best_c = -1;
+        std::vector<std::pair<int, int>> best;   // (gate index, type)
+        for (int c = 0; c + r <= K; ++c) {
+            std::vector<char> got(G, 0);
+            std::vector<std::pair<int, int>> list;
+            for (int g = 0; g < G; ++g) {
+                if (done[g]) continue;
+                const BrickGate &bg = P.gates[ps.gate_off + g];
+                int pa = rpos[bg.a], pb = rpos[bg.b];
+                if (pb != pa + 1 || pa < c || pb >= c + r) continue;
+                bool ok = true;
+                for (int h = 0; h < g && ok; ++h) {       // earlier gates of the pass sharing a bit
+                    const BrickGate &bh = P.gates[ps.gate_off + h];
+                    if (bh.layer >= bg.layer) continue;
+                    bool share = bh.a == bg.a || bh.a == bg.b || bh.b == bg.a || bh.b == bg.b;
+                    if (share && !done[h] && !got[h]) ok = false;
+                }
+                if (ok) { got[g] = 1; list.push_back({g, pa - c}); }
+            }
+            if (list.size() > best.size()) { best = list; best_c = c; }
+        }
+        if (best.empty()) break;
+        RegPass rp;
+        std::memset(&rp, 0, sizeof rp);
+        rp.r = (uint8_t)r;
+        for (int i = 0; i < r; ++i) rp.win[i] = (uint8_t)ring[best_c + i];
+        for (int i = 0; i < r; ++i) rp.srt[i] = rp.win[i];
+        std::sort(rp.srt, rp.srt + r);
+        rp.n_gates = (uint8_t)best.size();
+        rp.gate_off = (int16_t)P.rgates.size();
+        for (auto &x : best) {
+            RegGate rg;
+            rg.type = (uint8_t)x.second;
+            rg.slot = (uint8_t)x.first;
+            P.rgates.push_back(rg);
+            done[x.first] = 1;
+        }
+        left -= (int)best.size();
+        P.rpasses.push_back(rp);
+    }
+    ps.n_rp = (int)P.rpasses.size() - ps.rp_off;
+}
+
+BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win_bits) {
     BrickHostPlan P;
     BrickDev &d = P.dev;
     std::memset(&d, 0, sizeof d);
@@ -76,6 +130,7 @@ BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits) {
             }
             if (best.empty()) break;   // cannot happen for K >= 2
             BrickPass ps;
+            std::memset(&ps, 0, sizeof ps);
             ps.gate_off = (int)P.gates.size();
             ps.n_gates = (int)best.size();
             ps.smask = best_mask;
@@ -92,6 +147,13 @@ BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits) {
                 done[id] = 1;
             }
             left -= best.size();
+            // ring order of the arc: start where the previous ring bit is outside it
+            int ring[32], start = 0;
+            for (int b = 0; b < N; ++b)
+                if ((best_mask & (1u << b)) && !(best_mask & (1u << ((b + N - 1) % N)))) start = b;
+            for (int k = 0; k < K; ++k) ring[k] = loc[(start + k) % N];
+            if (K == N) for (int k = 0; k < K; ++k) ring[k] = loc[k];
+            schedule_registers(P, ps, ring, K, std::min(win_bits, K));
             P.passes.push_back(ps);
         }
         d.n_passes[side] = (int)P.passes.size() - d.pass_off[side];

@@ -121,6 +121,7 @@ struct DevPlan {
     uint8_t dot_perm[FP_MAX_STATE_BITS];   // right-layout position of left bit k
     double prefactor;              // 2^(free wire loops)
     double cost;                   // estimated complex MACs per pair
+    double sqrt_ops;               // sqrt(ops of the longer sweep), for the error estimate
 };
 
 }  // namespace fpk

@@ -30,7 +30,8 @@ cudaError_t launch_tables(const PairInfo *pairs, int npairs, int max_ops, const 
 cudaError_t launch_sweep_generic(const PairInfo *pairs, const int32_t *order, int count,
                                  const DevPlan *plans, const DevOp *ops, const void *tables,
                                  bool fp32, void *workspace, size_t ws_elems_per_cta, int ctas,
-                                 int *ticket, double *tr, double *kappa, cudaStream_t st);
+                                 int *ticket, double err_unit, double *tr, double *kappa, double *err,
+                                 cudaStream_t st);
 // FP64 moments per group (deterministic).
 cudaError_t launch_moments(const double *tr, const int32_t *group, uint64_t count, int k_max,
                            int n_groups, double *partials, int nblocks, double *out,
@@ -39,9 +40,10 @@ int moments_blocks(uint64_t count);
 // Brickwork fast path: maps, then either the shared-memory sweep (tile_bits == 0)
 // or init + light-cone passes + dot.  `states` holds npairs x 2 x 2^N
 // amplitudes (tiled) or npairs x 2^N (shared-memory path, left boundaries).
-cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const BrickGate *dgates,
+cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const BrickDevPlan &dp,
                          const PairInfo *pairs, int npairs, const double2 *raw, void *maps, void *states,
-                         bool fp32, double *tr, double *kappa, cudaStream_t st, int *launches);
+                         bool fp32, double err_scale, double *tr, double *kappa, double *err, cudaStream_t st,
+                         int *launches);
 size_t brick_smem_bytes(const BrickDev &d, bool fp32, bool *both);
 
 }  // namespace fpk

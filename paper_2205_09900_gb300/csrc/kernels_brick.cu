@@ -144,10 +144,11 @@ __device__ __forceinline__ double wsum(double v) {
 template <typename C>
 __global__ void __launch_bounds__(512) brick_smem_kernel(BrickDev d, const PairInfo *__restrict__ pairs, int npairs,
                                                          const C *__restrict__ maps, C *__restrict__ lscratch,
-                                                         int gt, int both, double *__restrict__ tr,
-                                                         double *__restrict__ kappa) {
+                                                         int gt, int both, double err_scale,
+                                                         double *__restrict__ tr, double *__restrict__ kappa,
+                                                         double *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[3][16];
+    __shared__ double red[4][16];
     C *sm = (C *)smem_raw;
     const int N = d.N, m = d.m;
     const uint32_t S = 1u << N;
@@ -187,20 +188,21 @@ __global__ void __launch_bounds__(512) brick_smem_kernel(BrickDev d, const PairI
             sync();
         }
     }
-    double sr = 0, si = 0, sa = 0;
+    double sr = 0, si = 0, sa = 0, s2 = 0;
     for (uint32_t w = tid; w < S; w += gt) {
         double lx = Lp[w].x, ly = Lp[w].y, rx = A[w].x, ry = A[w].y;
         double px = lx * rx - ly * ry, py = lx * ry + ly * rx;
-        sr += px; si += py; sa += sqrt(px * px + py * py);
+        double q = px * px + py * py;
+        sr += px; si += py; sa += sqrt(q); s2 += q;
     }
-    sr = wsum(sr); si = wsum(si); sa = wsum(sa);
+    sr = wsum(sr); si = wsum(si); sa = wsum(sa); s2 = wsum(s2);
     if (!warp_mode) {
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (lane == 0) { red[0][wid] = sr; red[1][wid] = si; red[2][wid] = sa; }
+        if (lane == 0) { red[0][wid] = sr; red[1][wid] = si; red[2][wid] = sa; red[3][wid] = s2; }
         __syncthreads();
         if (threadIdx.x == 0) {
-            sr = si = sa = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sr += red[0][w]; si += red[1][w]; sa += red[2][w]; }
+            sr = si = sa = s2 = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sr += red[0][w]; si += red[1][w]; sa += red[2][w]; s2 += red[3][w]; }
         }
     }
     if (tid == 0) {
@@ -209,6 +211,7 @@ __global__ void __launch_bounds__(512) brick_smem_kernel(BrickDev d, const PairI
         tr[2 * pi.out + 1] = si;
         double mag = sqrt(sr * sr + si * si);
         if (kappa) kappa[pi.out] = mag > 0 ? sa / mag : __longlong_as_double(0x7ff0000000000000LL);
+        if (err) err[pi.out] = err_scale * sqrt(s2);
     }
 }
 
@@ -225,13 +228,59 @@ __global__ void brick_init_kernel(BrickDev d, int npairs, C *__restrict__ states
     }
 }
 
+// Shared-memory tile layout: the low 4 index bits are XORed with a fold of
+// the higher nibbles, so that threads whose indices differ only above bit 3
+// still spread over all banks.
+__device__ __forceinline__ uint32_t swz(uint32_t i) {
+    uint32_t h = i >> 4;
+    return i ^ ((h ^ (h >> 4) ^ (h >> 8)) & 15u);
+}
+
+// 4x4 map on register bits (k, k+1) of a 2^R register block.
+template <typename C, int k, int R>
+__device__ __forceinline__ void win_apply(C (&v)[1 << R], const C *__restrict__ T) {
+#pragma unroll
+    for (int i = 0; i < (1 << R); ++i) {
+        if (i & (3 << k)) continue;
+        C x0 = v[i], x1 = v[i | (1 << k)], x2 = v[i | (2 << k)], x3 = v[i | (3 << k)];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            C acc;
+            acc.x = 0; acc.y = 0;
+            acc = cfma2(T[4 * o + 0], x0, acc);
+            acc = cfma2(T[4 * o + 1], x1, acc);
+            acc = cfma2(T[4 * o + 2], x2, acc);
+            acc = cfma2(T[4 * o + 3], x3, acc);
+            v[i | (o << k)] = acc;
+        }
+    }
+}
+
+template <typename C, int R>
+__device__ __forceinline__ void win_dispatch(int type, C (&v)[1 << R], const C *__restrict__ T) {
+    switch (type) {
+        case 0: win_apply<C, 0, R>(v, T); break;
+        case 1: if constexpr (R > 2) win_apply<C, 1, R>(v, T); break;
+        case 2: if constexpr (R > 3) win_apply<C, 2, R>(v, T); break;
+        case 3: if constexpr (R > 4) win_apply<C, 3, R>(v, T); break;
+        default: break;
+    }
+}
+
 // One light-cone pass of one side over all pairs: blockIdx.x = tile, blockIdx.y = pair.
-template <typename C, int K>
+// The tile (2^K amplitudes, a contiguous cyclic arc of segment bits) is loaded
+// into shared memory, the pass's gate maps are staged next to it, and the
+// gates are applied window by window with 2^R amplitudes per thread in
+// registers; one barrier per window.
+template <typename C, int K, int R>
 __global__ void __launch_bounds__(512) brick_pass_kernel(BrickDev d, int side, BrickPass ps,
                                                          const BrickGate *__restrict__ gates,
+                                                         const RegPass *__restrict__ rps,
+                                                         const RegGate *__restrict__ rgs,
                                                          const C *__restrict__ maps, C *__restrict__ states) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tile = (C *)smem_raw;
+    C *smaps = tile + (1u << K);
     __shared__ uint32_t lut_lo[128], lut_hi[1 << (K - 7)];
     __shared__ int pos[32];
     const int N = d.N, m = d.m;
@@ -241,7 +290,6 @@ __global__ void __launch_bounds__(512) brick_pass_kernel(BrickDev d, int side, B
         for (int b = 0; b < N; ++b) if (ps.smask & (1u << b)) pos[k++] = b;
     }
     __syncthreads();
-    // tile base: tile index bits go to the physical bits outside the arc, ascending
     uint32_t base = 0;
     {
         uint32_t t = blockIdx.x;
@@ -258,60 +306,94 @@ __global__ void __launch_bounds__(512) brick_pass_kernel(BrickDev d, int side, B
         for (int k = 0; k < K - 7; ++k) o |= ((i >> k) & 1u) << pos[7 + k];
         lut_hi[i] = o;
     }
+    const C *mp = maps + (size_t)blockIdx.y * (d.n - 1) * m * 16;
+    for (int i = threadIdx.x; i < ps.n_gates * 16; i += blockDim.x) {
+        const BrickGate gg = gates[ps.gate_off + i / 16];
+        const int bond = brick_bond(d, side, gg.layer);
+        smaps[i] = mp[((size_t)bond * m + gg.j) * 16 + (i % 16)];
+    }
     __syncthreads();
     C *st = states + ((size_t)blockIdx.y * 2 + side) * S + base;
-    for (uint32_t i = threadIdx.x; i < (1u << K); i += blockDim.x) tile[i] = st[lut_lo[i & 127] | lut_hi[i >> 7]];
+    for (uint32_t i = threadIdx.x; i < (1u << K); i += blockDim.x) tile[swz(i)] = st[lut_lo[i & 127] | lut_hi[i >> 7]];
     __syncthreads();
-    const C *mp = maps + (size_t)blockIdx.y * (d.n - 1) * m * 16;
-    for (int g = 0; g < ps.n_gates; ++g) {
-        const BrickGate gg = gates[ps.gate_off + g];
-        const int bond = brick_bond(d, side, gg.layer);
-        C T[16];
-        load_map(mp + ((size_t)bond * m + gg.j) * 16, T);
-        for (uint32_t q = threadIdx.x; q < (1u << (K - 2)); q += blockDim.x) quad_apply(tile, q, gg.a, gg.b, T);
+    for (int p = 0; p < ps.n_rp; ++p) {
+        const RegPass rp = rps[ps.rp_off + p];
+        uint32_t o[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) o[k] = 1u << rp.win[k];
+        for (uint32_t t = threadIdx.x; t < (1u << (K - R)); t += blockDim.x) {
+            uint32_t b0 = t;
+#pragma unroll
+            for (int k = 0; k < R; ++k) b0 = ins0(b0, rp.srt[k]);
+            C v[1 << R];
+#pragma unroll
+            for (int i = 0; i < (1 << R); ++i) {
+                uint32_t a = b0;
+#pragma unroll
+                for (int k = 0; k < R; ++k) if ((i >> k) & 1) a |= o[k];
+                v[i] = tile[swz(a)];
+            }
+            for (int g = 0; g < rp.n_gates; ++g) {
+                const RegGate rg = rgs[rp.gate_off + g];
+                win_dispatch<C, R>(rg.type, v, smaps + rg.slot * 16);
+            }
+#pragma unroll
+            for (int i = 0; i < (1 << R); ++i) {
+                uint32_t a = b0;
+#pragma unroll
+                for (int k = 0; k < R; ++k) if ((i >> k) & 1) a |= o[k];
+                tile[swz(a)] = v[i];
+            }
+        }
         __syncthreads();
     }
-    for (uint32_t i = threadIdx.x; i < (1u << K); i += blockDim.x) st[lut_lo[i & 127] | lut_hi[i >> 7]] = tile[i];
+    for (uint32_t i = threadIdx.x; i < (1u << K); i += blockDim.x) st[lut_lo[i & 127] | lut_hi[i >> 7]] = tile[swz(i)];
 }
 
 template <typename C>
 __global__ void __launch_bounds__(1024) brick_dot_kernel(BrickDev d, const PairInfo *__restrict__ pairs,
-                                                         const C *__restrict__ states, double *__restrict__ tr,
-                                                         double *__restrict__ kappa) {
-    __shared__ double red[3][32];
+                                                         const C *__restrict__ states, double err_scale,
+                                                         double *__restrict__ tr, double *__restrict__ kappa,
+                                                         double *__restrict__ err) {
+    __shared__ double red[4][32];
     const uint32_t S = 1u << d.N;
     const C *L = states + (size_t)blockIdx.x * 2 * S, *R = L + S;
-    double sr = 0, si = 0, sa = 0;
+    double sr = 0, si = 0, sa = 0, s2 = 0;
     for (uint32_t w = threadIdx.x; w < S; w += blockDim.x) {
         double lx = L[w].x, ly = L[w].y, rx = R[w].x, ry = R[w].y;
         double px = lx * rx - ly * ry, py = lx * ry + ly * rx;
-        sr += px; si += py; sa += sqrt(px * px + py * py);
+        double q = px * px + py * py;
+        sr += px; si += py; sa += sqrt(q); s2 += q;
     }
-    sr = wsum(sr); si = wsum(si); sa = wsum(sa);
+    sr = wsum(sr); si = wsum(si); sa = wsum(sa); s2 = wsum(s2);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) { red[0][wid] = sr; red[1][wid] = si; red[2][wid] = sa; }
+    if (lane == 0) { red[0][wid] = sr; red[1][wid] = si; red[2][wid] = sa; red[3][wid] = s2; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        sr = si = sa = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sr += red[0][w]; si += red[1][w]; sa += red[2][w]; }
+        sr = si = sa = s2 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sr += red[0][w]; si += red[1][w]; sa += red[2][w]; s2 += red[3][w]; }
         const PairInfo pi = pairs[blockIdx.x];
         tr[2 * pi.out] = sr;
         tr[2 * pi.out + 1] = si;
         double mag = sqrt(sr * sr + si * si);
         if (kappa) kappa[pi.out] = mag > 0 ? sa / mag : __longlong_as_double(0x7ff0000000000000LL);
+        if (err) err[pi.out] = err_scale * sqrt(s2);
     }
 }
 
-template <typename C, int K>
-cudaError_t run_passes(const BrickDev &d, const BrickPass *hpasses, const BrickGate *dgates, int npairs,
+template <typename C, int K, int R>
+cudaError_t run_passes(const BrickDev &d, const BrickPass *hpasses, const BrickDevPlan &dp, int npairs,
                        const C *maps, C *states, cudaStream_t st) {
-    const size_t smem = ((size_t)1 << K) * sizeof(C);
-    cudaError_t e = cudaFuncSetAttribute(brick_pass_kernel<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int maxg = 0;
+    for (int i = 0; i < d.n_passes[0] + d.n_passes[1]; ++i) maxg = hpasses[i].n_gates > maxg ? hpasses[i].n_gates : maxg;
+    const size_t smem = (((size_t)1 << K) + (size_t)maxg * 16) * sizeof(C);
+    cudaError_t e = cudaFuncSetAttribute(brick_pass_kernel<C, K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     for (int side = 0; side < 2; ++side)
         for (int p = 0; p < d.n_passes[side]; ++p) {
             dim3 grid(1u << (d.N - K), npairs);
-            brick_pass_kernel<C, K><<<grid, 512, smem, st>>>(d, side, hpasses[d.pass_off[side] + p], dgates, maps, states);
+            brick_pass_kernel<C, K, R><<<grid, 512, smem, st>>>(d, side, hpasses[d.pass_off[side] + p], dp.gates,
+                                                                 dp.rpasses, dp.rgates, maps, states);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     return cudaSuccess;
@@ -326,9 +408,10 @@ size_t brick_smem_bytes(const BrickDev &d, bool fp32, bool *both) {
     return (*both ? 2 : 1) * S * el;
 }
 
-cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const BrickGate *dgates,
+cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const BrickDevPlan &dp,
                          const PairInfo *pairs, int npairs, const double2 *raw, void *maps, void *states,
-                         bool fp32, double *tr, double *kappa, cudaStream_t st, int *launches) {
+                         bool fp32, double err_scale, double *tr, double *kappa, double *err, cudaStream_t st,
+                         int *launches) {
     if (npairs <= 0) return cudaSuccess;
     const int nm = (d.n - 1) * d.m;
     dim3 gm((nm + 127) / 128, npairs);
@@ -348,11 +431,11 @@ cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const Bric
         if (fp32) {
             if ((e = cudaFuncSetAttribute(brick_smem_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cta)) != cudaSuccess) return e;
             brick_smem_kernel<float2><<<grid, gt * gpc, smem_cta, st>>>(d, pairs, npairs, (const float2 *)maps,
-                                                                         (float2 *)states, gt, both, tr, kappa);
+                                                                         (float2 *)states, gt, both, err_scale, tr, kappa, err);
         } else {
             if ((e = cudaFuncSetAttribute(brick_smem_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cta)) != cudaSuccess) return e;
             brick_smem_kernel<double2><<<grid, gt * gpc, smem_cta, st>>>(d, pairs, npairs, (const double2 *)maps,
-                                                                          (double2 *)states, gt, both, tr, kappa);
+                                                                          (double2 *)states, gt, both, err_scale, tr, kappa, err);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         nl += 1;
@@ -362,17 +445,26 @@ cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const Bric
         if (fp32) brick_init_kernel<float2><<<ib, 256, 0, st>>>(d, npairs, (float2 *)states);
         else brick_init_kernel<double2><<<ib, 256, 0, st>>>(d, npairs, (double2 *)states);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int key = d.tile_bits * 10 + dp.win_bits;
         if (fp32) {
-            if (d.tile_bits == 14) e = run_passes<float2, 14>(d, hpasses, dgates, npairs, (const float2 *)maps, (float2 *)states, st);
-            else if (d.tile_bits == 13) e = run_passes<float2, 13>(d, hpasses, dgates, npairs, (const float2 *)maps, (float2 *)states, st);
-            else e = run_passes<float2, 12>(d, hpasses, dgates, npairs, (const float2 *)maps, (float2 *)states, st);
+            const float2 *mp = (const float2 *)maps;
+            float2 *sp = (float2 *)states;
+            switch (key) {
+                case 144: e = run_passes<float2, 14, 4>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 134: e = run_passes<float2, 13, 4>(d, hpasses, dp, npairs, mp, sp, st); break;
+                default: return cudaErrorInvalidValue;
+            }
         } else {
-            if (d.tile_bits == 13) e = run_passes<double2, 13>(d, hpasses, dgates, npairs, (const double2 *)maps, (double2 *)states, st);
-            else e = run_passes<double2, 12>(d, hpasses, dgates, npairs, (const double2 *)maps, (double2 *)states, st);
+            const double2 *mp = (const double2 *)maps;
+            double2 *sp = (double2 *)states;
+            switch (key) {
+                case 133: e = run_passes<double2, 13, 3>(d, hpasses, dp, npairs, mp, sp, st); break;
+                default: return cudaErrorInvalidValue;
+            }
         }
         if (e != cudaSuccess) return e;
-        if (fp32) brick_dot_kernel<float2><<<npairs, 1024, 0, st>>>(d, pairs, (const float2 *)states, tr, kappa);
-        else brick_dot_kernel<double2><<<npairs, 1024, 0, st>>>(d, pairs, (const double2 *)states, tr, kappa);
+        if (fp32) brick_dot_kernel<float2><<<npairs, 1024, 0, st>>>(d, pairs, (const float2 *)states, err_scale, tr, kappa, err);
+        else brick_dot_kernel<double2><<<npairs, 1024, 0, st>>>(d, pairs, (const double2 *)states, err_scale, tr, kappa, err);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         nl += 1 + d.n_passes[0] + d.n_passes[1] + 1;
     }

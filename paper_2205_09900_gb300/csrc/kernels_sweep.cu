@@ -91,9 +91,10 @@ template <typename C>
 __global__ void __launch_bounds__(256) sweep_generic(const PairInfo *__restrict__ pairs,
         const int32_t *__restrict__ order, int count, const DevPlan *__restrict__ plans,
         const DevOp *__restrict__ ops, const C *__restrict__ tables, C *__restrict__ ws,
-        size_t ws_elems, int *ticket, double *__restrict__ tr, double *__restrict__ kappa) {
+        size_t ws_elems, int *ticket, double err_unit, double *__restrict__ tr, double *__restrict__ kappa,
+        double *__restrict__ err) {
     __shared__ int item;
-    __shared__ double red[3][8];
+    __shared__ double red[4][8];
     C *buf0 = ws + (size_t)blockIdx.x * 3 * ws_elems;
     C *bufs[3] = {buf0, buf0 + ws_elems, buf0 + 2 * ws_elems};
     for (;;) {
@@ -129,22 +130,24 @@ __global__ void __launch_bounds__(256) sweep_generic(const PairInfo *__restrict_
         }
         const C *R = rb[rc];
         // FP64 meet
-        double sr = 0, si = 0, sa = 0;
+        double sr = 0, si = 0, sa = 0, s2 = 0;
         const uint32_t nf = 1u << pl.bits_final;
         for (uint32_t o = threadIdx.x; o < nf; o += blockDim.x) {
             uint32_t ri = 0;
             for (int k = 0; k < pl.bits_final; ++k) ri |= ((o >> k) & 1u) << pl.dot_perm[k];
             double lx = (double)L[o].x, ly = (double)L[o].y, rx = (double)R[ri].x, ry = (double)R[ri].y;
             double px = lx * rx - ly * ry, py = lx * ry + ly * rx;
-            sr += px; si += py; sa += sqrt(px * px + py * py);
+            double q = px * px + py * py;
+            sr += px; si += py; sa += sqrt(q); s2 += q;
         }
-        sr = warp_sum(sr); si = warp_sum(si); sa = warp_sum(sa);
+        sr = warp_sum(sr); si = warp_sum(si); sa = warp_sum(sa); s2 = warp_sum(s2);
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (lane == 0) { red[0][wid] = sr; red[1][wid] = si; red[2][wid] = sa; }
+        if (lane == 0) { red[0][wid] = sr; red[1][wid] = si; red[2][wid] = sa; red[3][wid] = s2; }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double a = 0, b = 0, c = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; c += red[2][w]; }
+            double a = 0, b = 0, c = 0, q2 = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; c += red[2][w]; q2 += red[3][w]; }
+            if (err) err[pi.out] = err_unit * pl.sqrt_ops * pl.prefactor * sqrt(q2);
             tr[2 * pi.out] = pl.prefactor * a;
             tr[2 * pi.out + 1] = pl.prefactor * b;
             double mag = sqrt(a * a + b * b);
@@ -159,16 +162,17 @@ __global__ void __launch_bounds__(256) sweep_generic(const PairInfo *__restrict_
 cudaError_t launch_sweep_generic(const PairInfo *pairs, const int32_t *order, int count,
                                  const DevPlan *plans, const DevOp *ops, const void *tables,
                                  bool fp32, void *workspace, size_t ws_elems_per_cta, int ctas,
-                                 int *ticket, double *tr, double *kappa, cudaStream_t st) {
+                                 int *ticket, double err_unit, double *tr, double *kappa, double *err,
+                                 cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     if (fp32)
         sweep_generic<float2><<<ctas, 256, 0, st>>>(pairs, order, count, plans, ops, (const float2 *)tables,
-                                                    (float2 *)workspace, ws_elems_per_cta, ticket, tr, kappa);
+                                                    (float2 *)workspace, ws_elems_per_cta, ticket, err_unit, tr, kappa, err);
     else
         sweep_generic<double2><<<ctas, 256, 0, st>>>(pairs, order, count, plans, ops, (const double2 *)tables,
-                                                     (double2 *)workspace, ws_elems_per_cta, ticket, tr, kappa);
+                                                     (double2 *)workspace, ws_elems_per_cta, ticket, err_unit, tr, kappa, err);
     return cudaGetLastError();
 }
 

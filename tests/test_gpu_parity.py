@@ -159,6 +159,27 @@ def test_fp32_path_matches_oracle(fp, kind, n, depth, dmax, npairs):
     assert err.max() <= TOL32, (err.max(), kap[np.argmax(err)])
 
 
+def test_error_estimate_bounds_fp32_error(fp):
+    # the per-result error estimate is an upper bound of the actual FP32 error
+    # (FP64 path as the reference) at every depth of the benchmark ensemble
+    ens, _ = make(fp, "parallel", 50, 2, 10, seed=19)
+    N = 3000
+    t64, _, g, e64 = ens.trace_batch(0, N, fp.PREC_FP64, with_err=True)
+    t32, _, _, e32 = ens.trace_batch(0, N, fp.PREC_FP32_RAW, with_err=True)
+    actual = np.abs(t32 - t64)
+    assert np.all(actual <= e32), (actual / e32).max()
+    assert np.all(e64 < 1e-9)
+
+
+def test_fp32_policy_recontracts_flagged_pairs(fp):
+    # a tolerance below the FP32 error estimates forces every pair onto the FP64 path
+    ens = fp.Ensemble(0, 20, 2, 6, seed=29, fp32_tol=1e-12)
+    t32, _, _, e = ens.trace_batch(0, 64, fp.PREC_FP32, with_err=True)
+    ref, _, _ = ens.trace_batch(0, 64, fp.PREC_FP64)
+    assert rel_err(t32, ref).max() <= TOL64
+    assert np.all(e < 1e-9)
+
+
 def test_fp32_frame_potential_within_1e3_of_fp64(fp):
     ens, _ = make(fp, "parallel", 20, 2, 6, seed=23)
     N = 4000
