@@ -108,7 +108,7 @@ struct fp_ensemble {
     // brickwork fast path
     std::map<int, std::unique_ptr<BrickCache>> brick_plans;   // key 2*l + fp32
     DBuf d_maps, d_states;
-    int tile_bits32 = 14, tile_bits64 = 13, win_bits32 = 4, win_bits64 = 3;
+    std::string gpu_name;
 };
 
 namespace {
@@ -368,6 +368,111 @@ fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t
     return FP_OK;
 }
 
+// Build and upload one brickwork plan variant.
+fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, std::unique_ptr<BrickCache> &out) {
+    const int N = 2 * (l - 1);
+    auto bc = std::make_unique<BrickCache>();
+    bc->hp = make_brick_plan(E->d.n, l, N <= K ? 0 : K, fp32 ? 5 : 4, R);
+    for (const auto &ps : bc->hp.passes) {
+        if (ps.n_gates > 255) return fail(FP_ERR_ARG, "tile pass with %d gates exceeds 255", ps.n_gates);
+        if (ps.n_rp > 96) return fail(FP_ERR_ARG, "tile pass with %d register passes exceeds 96", ps.n_rp);
+    }
+    CK(upload(bc->d_gates, bc->hp.gates, E->st));
+    CK(upload(bc->d_rpasses, bc->hp.rpasses, E->st));
+    CK(upload(bc->d_rgates, bc->hp.rgates, E->st));
+    bc->dp.gates = bc->d_gates.as<BrickGate>();
+    bc->dp.rpasses = bc->d_rpasses.as<RegPass>();
+    bc->dp.rgates = bc->d_rgates.as<RegGate>();
+    bc->dp.win_bits = R;
+    out = std::move(bc);
+    return FP_OK;
+}
+
+// Autotuner: time every (tile bits, window bits) variant of the tiled
+// brickwork sweep on a trial batch of this depth (sampler and maps once, then
+// each variant's init + passes + meet), keep the fastest.  Results persist in
+// the file named by FP_AUTOTUNE_CACHE (if set), keyed by GPU name, n, l and
+// precision.
+fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx, int l, bool fp32) {
+    const fp_ensemble_desc &d = E->d;
+    const int N = 2 * (l - 1);
+    const int key = l * 2 + (fp32 ? 1 : 0);
+    struct Cand { int K, R; };
+    std::vector<Cand> cands = fp32 ? std::vector<Cand>{{14, 4}, {14, 5}, {13, 4}, {13, 5}}
+                                   : std::vector<Cand>{{13, 3}, {13, 4}};
+    const int kmin = fp32 ? 13 : 13;
+    char ckey[256];
+    snprintf(ckey, sizeof ckey, "%s n=%d l=%d %s", E->gpu_name.c_str(), d.n, l, fp32 ? "fp32" : "fp64");
+    int bestK = cands[0].K, bestR = cands[0].R;
+    bool have = false;
+    const char *cache = getenv("FP_AUTOTUNE_CACHE");
+    if (N <= kmin + (fp32 ? 1 : 0)) {
+        have = true;            // whole boundary in one CTA: nothing to tune
+    } else if (cache) {
+        FILE *f = fopen(cache, "r");
+        if (f) {
+            char line[512];
+            while (fgets(line, sizeof line, f)) {
+                int K, R;
+                char k2[256];
+                if (sscanf(line, "%255[^|]|%d %d", k2, &K, &R) == 3 && strcmp(k2, ckey) == 0) {
+                    bestK = K; bestR = R; have = true;
+                }
+            }
+            fclose(f);
+        }
+    }
+    if (!have && !idx.empty()) {
+        const uint64_t nt = std::min<uint64_t>(idx.size(), 96);
+        const int n_raw = (int)layout_brickwork(d.n, l).size();
+        const size_t celem = fp32 ? sizeof(float2) : sizeof(double2);
+        std::vector<PairInfo> pinfo(nt);
+        for (uint64_t i = 0; i < nt; ++i) {
+            std::memset(&pinfo[i], 0, sizeof(PairInfo));
+            pinfo[i].pair = first + idx[i];
+            pinfo[i].n_raw = n_raw;
+            pinfo[i].raw_off = (int64_t)i * 2 * n_raw;
+            pinfo[i].out = (int64_t)idx[i];
+        }
+        CK(upload(E->d_pairs, pinfo, E->st));
+        CK(E->d_raw.reserve(nt * 2 * n_raw * 16 * sizeof(double2)));
+        CK(E->d_maps.reserve(nt * (d.n - 1) * (l - 1) * 16 * celem));
+        CK(E->d_states.reserve(nt * 2 * ((size_t)1 << N) * celem));
+        SampleParams sp;
+        sp.seed = d.seed; sp.n = d.n; sp.raw_kind = E->raw_kind; sp.self_pair = (d.flags & FP_FLAG_SELF_PAIR) ? 1 : 0;
+        CK(launch_sample(sp, E->d_pairs.as<PairInfo>(), (int)nt, n_raw, E->d_raw.as<double2>(), E->st));
+        float best_ms = 1e30f;
+        for (const Cand &c : cands) {
+            std::unique_ptr<BrickCache> bc;
+            fp_status s = make_brick_cache(E, l, fp32, c.K, c.R, bc);
+            if (s != FP_OK) continue;
+            float ms_sum = 0;
+            for (int rep = 0; rep < 2; ++rep) {
+                CK(cudaEventRecord(E->ev0, E->st));
+                int nl = 0;
+                CK(launch_brick(bc->hp.dev, bc->hp.passes.data(), bc->dp, E->d_pairs.as<PairInfo>(), (int)nt,
+                                E->d_raw.as<double2>(), E->d_maps.p, E->d_states.p, fp32, 0.0, E->d_tr.as<double>(),
+                                nullptr, nullptr, E->st, &nl));
+                CK(cudaEventRecord(E->ev1, E->st));
+                CK(cudaEventSynchronize(E->ev1));
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, E->ev0, E->ev1));
+                if (rep == 1) ms_sum += ms;     // first repetition warms caches and code
+            }
+            if (ms_sum < best_ms) { best_ms = ms_sum; bestK = c.K; bestR = c.R; }
+        }
+        if (cache) {
+            FILE *f = fopen(cache, "a");
+            if (f) { fprintf(f, "%s|%d %d\n", ckey, bestK, bestR); fclose(f); }
+        }
+    }
+    std::unique_ptr<BrickCache> bc;
+    fp_status s = make_brick_cache(E, l, fp32, bestK, bestR, bc);
+    if (s != FP_OK) return s;
+    E->brick_plans.emplace(key, std::move(bc));
+    return FP_OK;
+}
+
 // Brickwork fast path for pairs of one depth l >= 2.
 fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx, int l, int prec,
                     double *tr, double *kappa, double *err, float *gpu_ms) {
@@ -381,20 +486,9 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
     const int key = l * 2 + (fp32 ? 1 : 0);
     auto it = E->brick_plans.find(key);
     if (it == E->brick_plans.end()) {
-        auto bc = std::make_unique<BrickCache>();
-        const int kt = fp32 ? E->tile_bits32 : E->tile_bits64;
-        const int wb = fp32 ? E->win_bits32 : E->win_bits64;
-        bc->hp = make_brick_plan(d.n, l, N <= kt ? 0 : kt, fp32 ? 5 : 4, wb);
-        for (const auto &ps : bc->hp.passes)
-            if (ps.n_gates > 255) return fail(FP_ERR_ARG, "tile pass with %d gates exceeds 255", ps.n_gates);
-        CK(upload(bc->d_gates, bc->hp.gates, E->st));
-        CK(upload(bc->d_rpasses, bc->hp.rpasses, E->st));
-        CK(upload(bc->d_rgates, bc->hp.rgates, E->st));
-        bc->dp.gates = bc->d_gates.as<BrickGate>();
-        bc->dp.rpasses = bc->d_rpasses.as<RegPass>();
-        bc->dp.rgates = bc->d_rgates.as<RegGate>();
-        bc->dp.win_bits = wb;
-        it = E->brick_plans.emplace(key, std::move(bc)).first;
+        fp_status s = tune_brick(E, first, idx, l, fp32);
+        if (s != FP_OK) return s;
+        it = E->brick_plans.find(key);
     }
     const BrickHostPlan &bp = it->second->hp;
     const BrickDev &bd = bp.dev;
@@ -551,6 +645,11 @@ fp_status fp_ensemble_create(const fp_ensemble_desc *desc, void *cuda_stream, fp
     E->st = (cudaStream_t)cuda_stream;
     CK(cudaGetDevice(&E->device));
     CK(cudaDeviceGetAttribute(&E->sms, cudaDevAttrMultiProcessorCount, E->device));
+    {
+        cudaDeviceProp prop;
+        CK(cudaGetDeviceProperties(&prop, E->device));
+        E->gpu_name = prop.name;
+    }
     E->raw_kind = d.kind == FP_HEA ? RAW_ROT2 : ((d.flags & FP_FLAG_DIAGONAL_GATES) ? RAW_DIAG4 : RAW_HAAR4);
     E->n_groups = d.kind == FP_LOCAL ? (d.T_max - d.T_min) / d.T_step + 1 : d.depth_max - d.depth_min + 1;
     size_t freeb = 0, totb = 0;

@@ -228,17 +228,22 @@ __global__ void brick_init_kernel(BrickDev d, int npairs, C *__restrict__ states
     }
 }
 
-// Shared-memory tile layout: the low 4 index bits are XORed with a fold of
+// Shared-memory tile layout: the low 4 index bits are XORed with the XOR of
 // the higher nibbles, so that threads whose indices differ only above bit 3
-// still spread over all banks.
+// still spread over all banks.  The map is linear over GF(2):
+// swz(a ^ b) = swz(a) ^ swz(b), so an address built from disjoint bit groups
+// is the XOR of their swizzled parts.
 __device__ __forceinline__ uint32_t swz(uint32_t i) {
     uint32_t h = i >> 4;
-    return i ^ ((h ^ (h >> 4) ^ (h >> 8)) & 15u);
+    return i ^ ((h ^ (h >> 4) ^ (h >> 8) ^ (h >> 12)) & 15u);
 }
 
 // 4x4 map on register bits (k, k+1) of a 2^R register block.
 template <typename C, int k, int R>
 __device__ __forceinline__ void win_apply(C (&v)[1 << R], const C *__restrict__ T) {
+    C t[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) t[e] = T[e];
 #pragma unroll
     for (int i = 0; i < (1 << R); ++i) {
         if (i & (3 << k)) continue;
@@ -247,10 +252,10 @@ __device__ __forceinline__ void win_apply(C (&v)[1 << R], const C *__restrict__ 
         for (int o = 0; o < 4; ++o) {
             C acc;
             acc.x = 0; acc.y = 0;
-            acc = cfma2(T[4 * o + 0], x0, acc);
-            acc = cfma2(T[4 * o + 1], x1, acc);
-            acc = cfma2(T[4 * o + 2], x2, acc);
-            acc = cfma2(T[4 * o + 3], x3, acc);
+            acc = cfma2(t[4 * o + 0], x0, acc);
+            acc = cfma2(t[4 * o + 1], x1, acc);
+            acc = cfma2(t[4 * o + 2], x2, acc);
+            acc = cfma2(t[4 * o + 3], x3, acc);
             v[i | (o << k)] = acc;
         }
     }
@@ -267,28 +272,36 @@ __device__ __forceinline__ void win_dispatch(int type, C (&v)[1 << R], const C *
     }
 }
 
+constexpr int kMaxRegPasses = 96;
+
+__device__ __forceinline__ int srp_gate_base(const RegPass *rps, const BrickPass &ps) { return rps[ps.rp_off].gate_off; }
+
 // One light-cone pass of one side over all pairs: blockIdx.x = tile, blockIdx.y = pair.
 // The tile (2^K amplitudes, a contiguous cyclic arc of segment bits) is loaded
-// into shared memory, the pass's gate maps are staged next to it, and the
-// gates are applied window by window with 2^R amplitudes per thread in
-// registers; one barrier per window.
-template <typename C, int K, int R>
-__global__ void __launch_bounds__(512) brick_pass_kernel(BrickDev d, int side, BrickPass ps,
-                                                         const BrickGate *__restrict__ gates,
-                                                         const RegPass *__restrict__ rps,
-                                                         const RegGate *__restrict__ rgs,
-                                                         const C *__restrict__ maps, C *__restrict__ states) {
+// into shared memory, the pass's gate maps and schedule are staged next to it,
+// and the gates are applied window by window with 2^R amplitudes per thread
+// in registers; one barrier per window.
+template <typename C, int K, int R, int TH>
+__global__ void __launch_bounds__(TH) brick_pass_kernel(BrickDev d, int side, BrickPass ps,
+                                                        const BrickGate *__restrict__ gates,
+                                                        const RegPass *__restrict__ rps,
+                                                        const RegGate *__restrict__ rgs,
+                                                        const C *__restrict__ maps, C *__restrict__ states) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tile = (C *)smem_raw;
     C *smaps = tile + (1u << K);
     __shared__ uint32_t lut_lo[128], lut_hi[1 << (K - 7)];
     __shared__ int pos[32];
+    __shared__ RegPass srp[kMaxRegPasses];
+    __shared__ RegGate srg[256];
     const int N = d.N, m = d.m;
     const uint32_t S = 1u << N;
     if (threadIdx.x == 0) {
         int k = 0;
         for (int b = 0; b < N; ++b) if (ps.smask & (1u << b)) pos[k++] = b;
     }
+    for (int i = threadIdx.x; i < ps.n_rp; i += TH) srp[i] = rps[ps.rp_off + i];
+    for (int i = threadIdx.x; i < ps.n_gates; i += TH) srg[i] = rgs[srp_gate_base(rps, ps) + i];
     __syncthreads();
     uint32_t base = 0;
     {
@@ -296,58 +309,60 @@ __global__ void __launch_bounds__(512) brick_pass_kernel(BrickDev d, int side, B
         for (int b = 0; b < N; ++b)
             if (!(ps.smask & (1u << b))) { base |= (t & 1u) << b; t >>= 1; }
     }
-    for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+    for (int i = threadIdx.x; i < 128; i += TH) {
         uint32_t o = 0;
         for (int k = 0; k < 7; ++k) o |= ((i >> k) & 1u) << pos[k];
         lut_lo[i] = o;
     }
-    for (int i = threadIdx.x; i < (1 << (K - 7)); i += blockDim.x) {
+    for (int i = threadIdx.x; i < (1 << (K - 7)); i += TH) {
         uint32_t o = 0;
         for (int k = 0; k < K - 7; ++k) o |= ((i >> k) & 1u) << pos[7 + k];
         lut_hi[i] = o;
     }
     const C *mp = maps + (size_t)blockIdx.y * (d.n - 1) * m * 16;
-    for (int i = threadIdx.x; i < ps.n_gates * 16; i += blockDim.x) {
+    for (int i = threadIdx.x; i < ps.n_gates * 16; i += TH) {
         const BrickGate gg = gates[ps.gate_off + i / 16];
         const int bond = brick_bond(d, side, gg.layer);
         smaps[i] = mp[((size_t)bond * m + gg.j) * 16 + (i % 16)];
     }
     __syncthreads();
     C *st = states + ((size_t)blockIdx.y * 2 + side) * S + base;
-    for (uint32_t i = threadIdx.x; i < (1u << K); i += blockDim.x) tile[swz(i)] = st[lut_lo[i & 127] | lut_hi[i >> 7]];
+    for (uint32_t i = threadIdx.x; i < (1u << K); i += TH) tile[swz(i)] = st[lut_lo[i & 127] | lut_hi[i >> 7]];
     __syncthreads();
+    const int g0 = srp[0].gate_off;
     for (int p = 0; p < ps.n_rp; ++p) {
-        const RegPass rp = rps[ps.rp_off + p];
-        uint32_t o[R];
+        const RegPass rp = srp[p];
+        uint32_t sw[R];
 #pragma unroll
-        for (int k = 0; k < R; ++k) o[k] = 1u << rp.win[k];
-        for (uint32_t t = threadIdx.x; t < (1u << (K - R)); t += blockDim.x) {
+        for (int k = 0; k < R; ++k) sw[k] = swz(1u << rp.win[k]);
+        for (uint32_t t = threadIdx.x; t < (1u << (K - R)); t += TH) {
             uint32_t b0 = t;
 #pragma unroll
             for (int k = 0; k < R; ++k) b0 = ins0(b0, rp.srt[k]);
+            const uint32_t sb = swz(b0);
             C v[1 << R];
 #pragma unroll
             for (int i = 0; i < (1 << R); ++i) {
-                uint32_t a = b0;
+                uint32_t a = sb;
 #pragma unroll
-                for (int k = 0; k < R; ++k) if ((i >> k) & 1) a |= o[k];
-                v[i] = tile[swz(a)];
+                for (int k = 0; k < R; ++k) if ((i >> k) & 1) a ^= sw[k];
+                v[i] = tile[a];
             }
             for (int g = 0; g < rp.n_gates; ++g) {
-                const RegGate rg = rgs[rp.gate_off + g];
+                const RegGate rg = srg[rp.gate_off - g0 + g];
                 win_dispatch<C, R>(rg.type, v, smaps + rg.slot * 16);
             }
 #pragma unroll
             for (int i = 0; i < (1 << R); ++i) {
-                uint32_t a = b0;
+                uint32_t a = sb;
 #pragma unroll
-                for (int k = 0; k < R; ++k) if ((i >> k) & 1) a |= o[k];
-                tile[swz(a)] = v[i];
+                for (int k = 0; k < R; ++k) if ((i >> k) & 1) a ^= sw[k];
+                tile[a] = v[i];
             }
         }
         __syncthreads();
     }
-    for (uint32_t i = threadIdx.x; i < (1u << K); i += blockDim.x) st[lut_lo[i & 127] | lut_hi[i >> 7]] = tile[swz(i)];
+    for (uint32_t i = threadIdx.x; i < (1u << K); i += TH) st[lut_lo[i & 127] | lut_hi[i >> 7]] = tile[swz(i)];
 }
 
 template <typename C>
@@ -381,19 +396,19 @@ __global__ void __launch_bounds__(1024) brick_dot_kernel(BrickDev d, const PairI
     }
 }
 
-template <typename C, int K, int R>
+template <typename C, int K, int R, int TH>
 cudaError_t run_passes(const BrickDev &d, const BrickPass *hpasses, const BrickDevPlan &dp, int npairs,
                        const C *maps, C *states, cudaStream_t st) {
     int maxg = 0;
     for (int i = 0; i < d.n_passes[0] + d.n_passes[1]; ++i) maxg = hpasses[i].n_gates > maxg ? hpasses[i].n_gates : maxg;
     const size_t smem = (((size_t)1 << K) + (size_t)maxg * 16) * sizeof(C);
-    cudaError_t e = cudaFuncSetAttribute(brick_pass_kernel<C, K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(brick_pass_kernel<C, K, R, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     for (int side = 0; side < 2; ++side)
         for (int p = 0; p < d.n_passes[side]; ++p) {
             dim3 grid(1u << (d.N - K), npairs);
-            brick_pass_kernel<C, K, R><<<grid, 512, smem, st>>>(d, side, hpasses[d.pass_off[side] + p], dp.gates,
-                                                                 dp.rpasses, dp.rgates, maps, states);
+            brick_pass_kernel<C, K, R, TH><<<grid, TH, smem, st>>>(d, side, hpasses[d.pass_off[side] + p], dp.gates,
+                                                                    dp.rpasses, dp.rgates, maps, states);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     return cudaSuccess;
@@ -450,15 +465,18 @@ cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const Bric
             const float2 *mp = (const float2 *)maps;
             float2 *sp = (float2 *)states;
             switch (key) {
-                case 144: e = run_passes<float2, 14, 4>(d, hpasses, dp, npairs, mp, sp, st); break;
-                case 134: e = run_passes<float2, 13, 4>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 144: e = run_passes<float2, 14, 4, 512>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 145: e = run_passes<float2, 14, 5, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 134: e = run_passes<float2, 13, 4, 512>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 135: e = run_passes<float2, 13, 5, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
                 default: return cudaErrorInvalidValue;
             }
         } else {
             const double2 *mp = (const double2 *)maps;
             double2 *sp = (double2 *)states;
             switch (key) {
-                case 133: e = run_passes<double2, 13, 3>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 133: e = run_passes<double2, 13, 3, 512>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 134: e = run_passes<double2, 13, 4, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
                 default: return cudaErrorInvalidValue;
             }
         }
