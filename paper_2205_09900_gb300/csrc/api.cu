@@ -369,7 +369,7 @@ fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t
 }
 
 // Build and upload one brickwork plan variant.
-fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, std::unique_ptr<BrickCache> &out) {
+fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int TH, std::unique_ptr<BrickCache> &out) {
     const int N = 2 * (l - 1);
     auto bc = std::make_unique<BrickCache>();
     bc->hp = make_brick_plan(E->d.n, l, N <= K ? 0 : K, fp32 ? 5 : 4, R);
@@ -384,6 +384,7 @@ fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, std::
     bc->dp.rpasses = bc->d_rpasses.as<RegPass>();
     bc->dp.rgates = bc->d_rgates.as<RegGate>();
     bc->dp.win_bits = R;
+    bc->dp.threads = TH;
     out = std::move(bc);
     return FP_OK;
 }
@@ -397,13 +398,13 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
     const fp_ensemble_desc &d = E->d;
     const int N = 2 * (l - 1);
     const int key = l * 2 + (fp32 ? 1 : 0);
-    struct Cand { int K, R; };
-    std::vector<Cand> cands = fp32 ? std::vector<Cand>{{14, 4}, {14, 5}, {13, 4}, {13, 5}}
-                                   : std::vector<Cand>{{13, 3}, {13, 4}};
+    struct Cand { int K, R, TH; };
+    std::vector<Cand> cands = fp32 ? std::vector<Cand>{{14, 4, 512}, {14, 5, 256}, {13, 4, 512}, {13, 4, 256}, {13, 5, 256}}
+                                   : std::vector<Cand>{{13, 3, 512}, {13, 4, 256}};
     const int kmin = fp32 ? 13 : 13;
     char ckey[256];
     snprintf(ckey, sizeof ckey, "%s n=%d l=%d %s", E->gpu_name.c_str(), d.n, l, fp32 ? "fp32" : "fp64");
-    int bestK = cands[0].K, bestR = cands[0].R;
+    int bestK = cands[0].K, bestR = cands[0].R, bestT = cands[0].TH;
     bool have = false;
     const char *cache = getenv("FP_AUTOTUNE_CACHE");
     if (N <= kmin + (fp32 ? 1 : 0)) {
@@ -413,10 +414,10 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
         if (f) {
             char line[512];
             while (fgets(line, sizeof line, f)) {
-                int K, R;
+                int K, R, T;
                 char k2[256];
-                if (sscanf(line, "%255[^|]|%d %d", k2, &K, &R) == 3 && strcmp(k2, ckey) == 0) {
-                    bestK = K; bestR = R; have = true;
+                if (sscanf(line, "%255[^|]|%d %d %d", k2, &K, &R, &T) == 4 && strcmp(k2, ckey) == 0) {
+                    bestK = K; bestR = R; bestT = T; have = true;
                 }
             }
             fclose(f);
@@ -444,7 +445,7 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
         float best_ms = 1e30f;
         for (const Cand &c : cands) {
             std::unique_ptr<BrickCache> bc;
-            fp_status s = make_brick_cache(E, l, fp32, c.K, c.R, bc);
+            fp_status s = make_brick_cache(E, l, fp32, c.K, c.R, c.TH, bc);
             if (s != FP_OK) continue;
             float ms_sum = 0;
             for (int rep = 0; rep < 2; ++rep) {
@@ -459,15 +460,15 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
                 CK(cudaEventElapsedTime(&ms, E->ev0, E->ev1));
                 if (rep == 1) ms_sum += ms;     // first repetition warms caches and code
             }
-            if (ms_sum < best_ms) { best_ms = ms_sum; bestK = c.K; bestR = c.R; }
+            if (ms_sum < best_ms) { best_ms = ms_sum; bestK = c.K; bestR = c.R; bestT = c.TH; }
         }
         if (cache) {
             FILE *f = fopen(cache, "a");
-            if (f) { fprintf(f, "%s|%d %d\n", ckey, bestK, bestR); fclose(f); }
+            if (f) { fprintf(f, "%s|%d %d %d\n", ckey, bestK, bestR, bestT); fclose(f); }
         }
     }
     std::unique_ptr<BrickCache> bc;
-    fp_status s = make_brick_cache(E, l, fp32, bestK, bestR, bc);
+    fp_status s = make_brick_cache(E, l, fp32, bestK, bestR, bestT, bc);
     if (s != FP_OK) return s;
     E->brick_plans.emplace(key, std::move(bc));
     return FP_OK;

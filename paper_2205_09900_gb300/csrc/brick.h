@@ -71,6 +71,7 @@ struct BrickDevPlan {
     const RegPass *rpasses;
     const RegGate *rgates;
     int win_bits;
+    int threads;
 };
 
 struct BrickHostPlan {

@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(512) brick_smem_kernel(BrickDev d, const PairI
         tr[2 * pi.out + 1] = si;
         double mag = sqrt(sr * sr + si * si);
         if (kappa) kappa[pi.out] = mag > 0 ? sa / mag : __longlong_as_double(0x7ff0000000000000LL);
-        if (err) err[pi.out] = err_scale * sqrt(s2);
+        if (err) err[pi.out] = err_scale * (sqrt(s2) + mag);
     }
 }
 
@@ -238,9 +238,95 @@ __device__ __forceinline__ uint32_t swz(uint32_t i) {
     return i ^ ((h ^ (h >> 4) ^ (h >> 8) ^ (h >> 12)) & 15u);
 }
 
+// Packed FP32 pair FMA (two lanes per instruction): d = a * b + c lane-wise.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+// Map entries as staged in shared memory: FP64 keeps the complex entry; FP32
+// keeps two broadcast pairs (tr, tr) and (-ti, ti) so that a complex
+// multiply-add is two packed FMAs: acc += (tr,tr)*(xr,xi) + (-ti,ti)*(xi,xr).
+template <typename C> struct MapSlot { static constexpr int width = 16; };
+template <> struct MapSlot<float2> { static constexpr int width = 32; };
+
+template <typename C>
+__device__ __forceinline__ void stage_entry(C *dst, int e, C t) { dst[e] = t; }
+template <>
+__device__ __forceinline__ void stage_entry<float2>(float2 *dst, int e, float2 t) {
+    dst[2 * e] = make_float2(t.x, t.x);
+    dst[2 * e + 1] = make_float2(-t.y, t.y);
+}
+
 // 4x4 map on register bits (k, k+1) of a 2^R register block.
 template <typename C, int k, int R>
+struct WinApply {
+    static __device__ __forceinline__ void run(C (&v)[1 << R], const C *__restrict__ T);
+};
+
+template <int k, int R>
+struct WinApply<float2, k, R> {
+    static __device__ __forceinline__ void run(float2 (&v)[1 << R], const float2 *__restrict__ T) {
+        float2 t[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) t[e] = T[e];
+#pragma unroll
+        for (int i = 0; i < (1 << R); ++i) {
+            if (i & (3 << k)) continue;
+            float2 x[4], xs[4];
+            x[0] = v[i]; x[1] = v[i | (1 << k)]; x[2] = v[i | (2 << k)]; x[3] = v[i | (3 << k)];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) xs[f] = make_float2(x[f].y, x[f].x);
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    acc = ffma2(t[2 * (4 * o + f)], x[f], acc);
+                    acc = ffma2(t[2 * (4 * o + f) + 1], xs[f], acc);
+                }
+                v[i | (o << k)] = acc;
+            }
+        }
+    }
+};
+
+template <int k, int R>
+struct WinApply<double2, k, R> {
+    static __device__ __forceinline__ void run(double2 (&v)[1 << R], const double2 *__restrict__ T) {
+        double2 t[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) t[e] = T[e];
+#pragma unroll
+        for (int i = 0; i < (1 << R); ++i) {
+            if (i & (3 << k)) continue;
+            double2 x0 = v[i], x1 = v[i | (1 << k)], x2 = v[i | (2 << k)], x3 = v[i | (3 << k)];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                double2 acc = make_double2(0, 0);
+                acc = cfma2(t[4 * o + 0], x0, acc);
+                acc = cfma2(t[4 * o + 1], x1, acc);
+                acc = cfma2(t[4 * o + 2], x2, acc);
+                acc = cfma2(t[4 * o + 3], x3, acc);
+                v[i | (o << k)] = acc;
+            }
+        }
+    }
+};
+
+template <typename C, int k, int R>
 __device__ __forceinline__ void win_apply(C (&v)[1 << R], const C *__restrict__ T) {
+    WinApply<C, k, R>::run(v, T);
+}
+
+// (generic complex version, kept for reference by the shared-memory kernel)
+template <typename C, int k, int R>
+__device__ __forceinline__ void win_apply_plain(C (&v)[1 << R], const C *__restrict__ T) {
     C t[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) t[e] = T[e];
@@ -290,6 +376,7 @@ __global__ void __launch_bounds__(TH) brick_pass_kernel(BrickDev d, int side, Br
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *tile = (C *)smem_raw;
     C *smaps = tile + (1u << K);
+    constexpr int MW = MapSlot<C>::width;
     __shared__ uint32_t lut_lo[128], lut_hi[1 << (K - 7)];
     __shared__ int pos[32];
     __shared__ RegPass srp[kMaxRegPasses];
@@ -323,7 +410,7 @@ __global__ void __launch_bounds__(TH) brick_pass_kernel(BrickDev d, int side, Br
     for (int i = threadIdx.x; i < ps.n_gates * 16; i += TH) {
         const BrickGate gg = gates[ps.gate_off + i / 16];
         const int bond = brick_bond(d, side, gg.layer);
-        smaps[i] = mp[((size_t)bond * m + gg.j) * 16 + (i % 16)];
+        stage_entry<C>(smaps + (i / 16) * MW, i % 16, mp[((size_t)bond * m + gg.j) * 16 + (i % 16)]);
     }
     __syncthreads();
     C *st = states + ((size_t)blockIdx.y * 2 + side) * S + base;
@@ -350,7 +437,7 @@ __global__ void __launch_bounds__(TH) brick_pass_kernel(BrickDev d, int side, Br
             }
             for (int g = 0; g < rp.n_gates; ++g) {
                 const RegGate rg = srg[rp.gate_off - g0 + g];
-                win_dispatch<C, R>(rg.type, v, smaps + rg.slot * 16);
+                win_dispatch<C, R>(rg.type, v, smaps + rg.slot * MW);
             }
 #pragma unroll
             for (int i = 0; i < (1 << R); ++i) {
@@ -392,7 +479,7 @@ __global__ void __launch_bounds__(1024) brick_dot_kernel(BrickDev d, const PairI
         tr[2 * pi.out + 1] = si;
         double mag = sqrt(sr * sr + si * si);
         if (kappa) kappa[pi.out] = mag > 0 ? sa / mag : __longlong_as_double(0x7ff0000000000000LL);
-        if (err) err[pi.out] = err_scale * sqrt(s2);
+        if (err) err[pi.out] = err_scale * (sqrt(s2) + mag);
     }
 }
 
@@ -401,7 +488,7 @@ cudaError_t run_passes(const BrickDev &d, const BrickPass *hpasses, const BrickD
                        const C *maps, C *states, cudaStream_t st) {
     int maxg = 0;
     for (int i = 0; i < d.n_passes[0] + d.n_passes[1]; ++i) maxg = hpasses[i].n_gates > maxg ? hpasses[i].n_gates : maxg;
-    const size_t smem = (((size_t)1 << K) + (size_t)maxg * 16) * sizeof(C);
+    const size_t smem = (((size_t)1 << K) + (size_t)maxg * MapSlot<C>::width) * sizeof(C);
     cudaError_t e = cudaFuncSetAttribute(brick_pass_kernel<C, K, R, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     for (int side = 0; side < 2; ++side)
@@ -460,23 +547,24 @@ cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const Bric
         if (fp32) brick_init_kernel<float2><<<ib, 256, 0, st>>>(d, npairs, (float2 *)states);
         else brick_init_kernel<double2><<<ib, 256, 0, st>>>(d, npairs, (double2 *)states);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const int key = d.tile_bits * 10 + dp.win_bits;
+        const int key = d.tile_bits * 100 + dp.win_bits * 10 + (dp.threads == 256 ? 1 : 0);
         if (fp32) {
             const float2 *mp = (const float2 *)maps;
             float2 *sp = (float2 *)states;
             switch (key) {
-                case 144: e = run_passes<float2, 14, 4, 512>(d, hpasses, dp, npairs, mp, sp, st); break;
-                case 145: e = run_passes<float2, 14, 5, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
-                case 134: e = run_passes<float2, 13, 4, 512>(d, hpasses, dp, npairs, mp, sp, st); break;
-                case 135: e = run_passes<float2, 13, 5, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 1440: e = run_passes<float2, 14, 4, 512>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 1451: e = run_passes<float2, 14, 5, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 1340: e = run_passes<float2, 13, 4, 512>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 1341: e = run_passes<float2, 13, 4, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 1351: e = run_passes<float2, 13, 5, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
                 default: return cudaErrorInvalidValue;
             }
         } else {
             const double2 *mp = (const double2 *)maps;
             double2 *sp = (double2 *)states;
             switch (key) {
-                case 133: e = run_passes<double2, 13, 3, 512>(d, hpasses, dp, npairs, mp, sp, st); break;
-                case 134: e = run_passes<double2, 13, 4, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 1330: e = run_passes<double2, 13, 3, 512>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 1341: e = run_passes<double2, 13, 4, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
                 default: return cudaErrorInvalidValue;
             }
         }

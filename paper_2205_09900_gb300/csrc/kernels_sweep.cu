@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256) sweep_generic(const PairInfo *__restrict_
         if (threadIdx.x == 0) {
             double a = 0, b = 0, c = 0, q2 = 0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; c += red[2][w]; q2 += red[3][w]; }
-            if (err) err[pi.out] = err_unit * pl.sqrt_ops * pl.prefactor * sqrt(q2);
+            if (err) err[pi.out] = err_unit * pl.sqrt_ops * pl.prefactor * (sqrt(q2) + sqrt(a * a + b * b));
             tr[2 * pi.out] = pl.prefactor * a;
             tr[2 * pi.out + 1] = pl.prefactor * b;
             double mag = sqrt(a * a + b * b);
