@@ -205,6 +205,33 @@ fp_status fp_frame_potential(fp_ensemble *ens, uint64_t first, uint64_t max_pair
 /* Copy the ensemble's kernel counters into *out; reset them if `reset`. */
 fp_status fp_kernel_stats_get(fp_ensemble *ens, fp_kernel_stats *out, int32_t reset);
 
+/* Allocation-free brickwork traces (the paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they need
+ * traces -- code running while a stream is captured into a CUDA graph, where
+ * an allocation is not stream-ordered; plugins inside a framework whose pool
+ * already holds the device memory; loops that must not block in an
+ * allocator).  It contracts pairs first..first+count-1 of the brickwork
+ * ensemble (n qubits, every pair of depth l, Philox key `seed`) on the
+ * brickwork shared-memory path, with all intermediate data in one scratch
+ * array of FP_STATIC_SCRATCH_BYTES compiled into the library (held by every
+ * GPU that loads it until the process exits).  It calls no cudaMalloc or
+ * cudaFree and no allocating library routine.
+ *   l         2..7 (boundaries of at most 12 bits);
+ *   prec      FP_PREC_FP64 or FP_PREC_FP32_RAW (no FP64 recontraction);
+ *   tr        [2*count] doubles, kappa [count] doubles or NULL: device (or
+ *             managed) memory owned by the caller;
+ *   cuda_stream  the launches are ordered on it; the call does not wait for
+ *             them (results are in tr/kappa once the stream reaches that point).
+ * A count whose scratch would exceed FP_STATIC_SCRATCH_BYTES returns
+ * FP_ERR_ARG with the largest count that fits (fp_last_error).  The first
+ * call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU
+ * (unordered streams) race; nothing in it needs to start at zero. */
+#define FP_STATIC_SCRATCH_BYTES (32u << 20)
+fp_status fp_trace_brick_static(int32_t n, int32_t l, uint64_t seed, uint64_t first, uint64_t count,
+                                int32_t prec, double *tr, double *kappa, void *cuda_stream);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char *fp_last_error(void);
 

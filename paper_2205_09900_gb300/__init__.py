@@ -26,7 +26,8 @@ STATUS = {0: "FP_OK", -1: "FP_ERR_ARG", -2: "FP_ERR_CUDA", -3: "FP_ERR_OOM", -4:
           -5: "FP_ERR_INFEASIBLE"}
 
 EXPORTED = ["fp_ensemble_create", "fp_ensemble_destroy", "fp_groups", "fp_pair_groups", "fp_export_gates",
-            "fp_trace_batch", "fp_reduce_moments", "fp_frame_potential", "fp_kernel_stats_get", "fp_last_error"]
+            "fp_trace_batch", "fp_reduce_moments", "fp_frame_potential", "fp_kernel_stats_get",
+            "fp_trace_brick_static", "fp_last_error"]
 
 
 class FpError(RuntimeError):
@@ -80,6 +81,8 @@ def load(path: str = LIB_PATH):
     L.fp_frame_potential.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double,
                                      ctypes.c_int32, vp, vp, P(RunStats)]
     L.fp_kernel_stats_get.argtypes = [vp, P(KernelStats), ctypes.c_int32]
+    L.fp_trace_brick_static.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
+                                        ctypes.c_uint64, ctypes.c_int32, vp, vp, vp]
     L.fp_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name not in ("fp_ensemble_destroy", "fp_last_error"):
@@ -100,6 +103,16 @@ def _ptr(x):
     if hasattr(x, "data_ptr"):
         return ctypes.c_void_p(x.data_ptr())
     return ctypes.c_void_p(x.ctypes.data)
+
+
+def trace_brick_static(n, l, seed, first, count, prec, tr, kappa=None, stream=None):
+    """Brickwork traces through the allocation-free entry point.  `tr` (2*count
+    float64) and `kappa` (count float64, optional) must be CUDA tensors; the
+    launches are ordered on `stream` (a cudaStream_t handle, None = default) and
+    the call does not wait for them."""
+    st = None if stream is None else ctypes.c_void_p(stream)
+    _check(load().fp_trace_brick_static(n, l, seed, first, count, prec, _ptr(tr), _ptr(kappa), st))
+    return tr, kappa
 
 
 class Ensemble:

@@ -77,6 +77,10 @@ bool is_device_ptr(const void *p) {
 
 }  // namespace
 
+namespace fpk {
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace fpk
+
 struct BrickCache {
     BrickHostPlan hp;
     DBuf d_gates, d_rpasses, d_rgates;

@@ -45,5 +45,7 @@ cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const Bric
                          bool fp32, double err_scale, double *tr, double *kappa, double *err, cudaStream_t st,
                          int *launches);
 size_t brick_smem_bytes(const BrickDev &d, bool fp32, bool *both);
+// Set the thread-local message returned by fp_last_error().
+void set_last_error(const char *msg);
 
 }  // namespace fpk
