@@ -376,10 +376,10 @@ fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t
 fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int TH, std::unique_ptr<BrickCache> &out) {
     const int N = 2 * (l - 1);
     auto bc = std::make_unique<BrickCache>();
-    bc->hp = make_brick_plan(E->d.n, l, N <= K ? 0 : K, fp32 ? 5 : 4, R);
+    bc->hp = make_brick_plan(E->d.n, l, K, fp32 ? 5 : 4, R);   // K > N: shared-memory sweep, K == N: one tile
     for (const auto &ps : bc->hp.passes) {
         if (ps.n_gates > 255) return fail(FP_ERR_ARG, "tile pass with %d gates exceeds 255", ps.n_gates);
-        if (ps.n_rp > 96) return fail(FP_ERR_ARG, "tile pass with %d register passes exceeds 96", ps.n_rp);
+        if (ps.n_rp > 160) return fail(FP_ERR_ARG, "tile pass with %d register passes exceeds 160", ps.n_rp);
     }
     CK(upload(bc->d_gates, bc->hp.gates, E->st));
     CK(upload(bc->d_rpasses, bc->hp.rpasses, E->st));
@@ -403,16 +403,19 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
     const int N = 2 * (l - 1);
     const int key = l * 2 + (fp32 ? 1 : 0);
     struct Cand { int K, R, TH; };
+    // K = 99: whole boundary in one CTA's shared memory (brick_smem_kernel)
     std::vector<Cand> cands = fp32 ? std::vector<Cand>{{14, 4, 512}, {14, 5, 256}, {13, 4, 512}, {13, 4, 256}, {13, 5, 256}}
                                    : std::vector<Cand>{{13, 3, 512}, {13, 4, 256}};
-    const int kmin = fp32 ? 13 : 13;
+    if (((size_t)1 << N) * (fp32 ? sizeof(float2) : sizeof(double2)) <= (size_t)200 * 1024) cands.push_back({99, 0, 0});
+    const int kmin = 12;   // boundaries up to 2^12: shared-memory sweep, nothing to tune
     char ckey[256];
     snprintf(ckey, sizeof ckey, "%s n=%d l=%d %s", E->gpu_name.c_str(), d.n, l, fp32 ? "fp32" : "fp64");
     int bestK = cands[0].K, bestR = cands[0].R, bestT = cands[0].TH;
     bool have = false;
     const char *cache = getenv("FP_AUTOTUNE_CACHE");
-    if (N <= kmin + (fp32 ? 1 : 0)) {
+    if (N <= kmin) {
         have = true;            // whole boundary in one CTA: nothing to tune
+        bestK = 99;
     } else if (cache) {
         FILE *f = fopen(cache, "r");
         if (f) {
@@ -455,9 +458,13 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
             for (int rep = 0; rep < 2; ++rep) {
                 CK(cudaEventRecord(E->ev0, E->st));
                 int nl = 0;
-                CK(launch_brick(bc->hp.dev, bc->hp.passes.data(), bc->dp, E->d_pairs.as<PairInfo>(), (int)nt,
-                                E->d_raw.as<double2>(), E->d_maps.p, E->d_states.p, fp32, 0.0, E->d_tr.as<double>(),
-                                nullptr, nullptr, E->st, &nl));
+                if (launch_brick(bc->hp.dev, bc->hp.passes.data(), bc->dp, E->d_pairs.as<PairInfo>(), (int)nt,
+                                 E->d_raw.as<double2>(), E->d_maps.p, E->d_states.p, fp32, 0.0, E->d_tr.as<double>(),
+                                 nullptr, nullptr, E->st, &nl) != cudaSuccess) {
+                    cudaGetLastError();   // a variant this device cannot launch: skip it
+                    ms_sum = 1e30f;
+                    break;
+                }
                 CK(cudaEventRecord(E->ev1, E->st));
                 CK(cudaEventSynchronize(E->ev1));
                 float ms = 0;

@@ -17,7 +17,7 @@ namespace fpk {
 // Register windows inside one tile pass: windows are r consecutive ring
 // positions of the tile's arc; greedy, each step takes the window that can
 // apply the most remaining gates (in layer order, predecessors first).
-static void schedule_registers(BrickHostPlan &P, BrickPass &ps, const int *ring, int K, int r) {
+static void schedule_registers(BrickHostPlan &P, BrickPass &ps, const int *ring, int K, int r, bool cyclic) {
     const int G = ps.n_gates;
     std::vector<int> rpos(32, -1);   // tile-local bit -> arc position
     for (int k = 0; k < K; ++k) rpos[ring[k]] = k;
@@ -27,14 +27,17 @@ static void schedule_registers(BrickHostPlan &P, BrickPass &ps, const int *ring,
     while (left > 0) {
         int best_c = -1;
         std::vector<std::pair<int, int>> best;   // (gate index, type)
-        for (int c = 0; c + r <= K; ++c) {
+        const int nwin = cyclic ? K : K - r + 1;
+        for (int c = 0; c < nwin; ++c) {
             std::vector<char> got(G, 0);
             std::vector<std::pair<int, int>> list;
             for (int g = 0; g < G; ++g) {
                 if (done[g]) continue;
                 const BrickGate &bg = P.gates[ps.gate_off + g];
                 int pa = rpos[bg.a], pb = rpos[bg.b];
-                if (pb != pa + 1 || pa < c || pb >= c + r) continue;
+                int i = cyclic ? (pa - c + K) % K : pa - c;
+                if (cyclic ? pb != (pa + 1) % K : pb != pa + 1) continue;
+                if (i < 0 || i > r - 2) continue;
                 bool ok = true;
                 for (int h = 0; h < g && ok; ++h) {       // earlier gates of the pass sharing a bit
                     const BrickGate &bh = P.gates[ps.gate_off + h];
@@ -42,7 +45,7 @@ static void schedule_registers(BrickHostPlan &P, BrickPass &ps, const int *ring,
                     bool share = bh.a == bg.a || bh.a == bg.b || bh.b == bg.a || bh.b == bg.b;
                     if (share && !done[h] && !got[h]) ok = false;
                 }
-                if (ok) { got[g] = 1; list.push_back({g, pa - c}); }
+                if (ok) { got[g] = 1; list.push_back({g, i}); }
             }
             if (list.size() > best.size()) { best = list; best_c = c; }
         }
@@ -50,7 +53,7 @@ static void schedule_registers(BrickHostPlan &P, BrickPass &ps, const int *ring,
         RegPass rp;
         std::memset(&rp, 0, sizeof rp);
         rp.r = (uint8_t)r;
-        for (int i = 0; i < r; ++i) rp.win[i] = (uint8_t)ring[best_c + i];
+        for (int i = 0; i < r; ++i) rp.win[i] = (uint8_t)ring[(best_c + i) % K];
         for (int i = 0; i < r; ++i) rp.srt[i] = rp.win[i];
         std::sort(rp.srt, rp.srt + r);
         rp.n_gates = (uint8_t)best.size();
@@ -82,9 +85,11 @@ BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win
     d.delta_par[0] = 0;        // qubit 0 is idle where bond 0 (parity 1 positions) is not
     d.delta_par[1] = n % 2;    // qubit n-1 is idle where bond n-2 is not
     const int N = d.N, m = d.m;
-    d.tile_bits = tile_bits >= N ? 0 : tile_bits;
+    // tile_bits == N: the whole ring is one tile (one pass per side)
+    d.tile_bits = tile_bits > N ? 0 : tile_bits;
     if (d.tile_bits == 0) return P;
     const int K = tile_bits;
+    const bool whole = K == N;
     // candidate arcs: those holding the low bits first (coalesced tile loads);
     // every arc when none of those can make progress
     std::vector<uint32_t> arcs, all_arcs;
@@ -152,8 +157,8 @@ BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win
             for (int b = 0; b < N; ++b)
                 if ((best_mask & (1u << b)) && !(best_mask & (1u << ((b + N - 1) % N)))) start = b;
             for (int k = 0; k < K; ++k) ring[k] = loc[(start + k) % N];
-            if (K == N) for (int k = 0; k < K; ++k) ring[k] = loc[k];
-            schedule_registers(P, ps, ring, K, std::min(win_bits, K));
+            if (whole) for (int k = 0; k < K; ++k) ring[k] = loc[k];
+            schedule_registers(P, ps, ring, K, std::min(win_bits, K), whole);
             P.passes.push_back(ps);
         }
         d.n_passes[side] = (int)P.passes.size() - d.pass_off[side];

@@ -133,6 +133,33 @@ __global__ void brick_maps_kernel(BrickDev d, const PairInfo *__restrict__ pairs
                 }
 }
 
+// Accumulators of the meet: the trace sum in FP64; the |t| and |t|^2 sums
+// (cancellation ratio, error estimate) in the boundary precision per thread,
+// combined in FP64 across threads.  A term t = L_j R_j is formed in the
+// boundary's own precision (one rounding of values that carry FP32 rounding
+// already); FP64 conversions and square roots are costly on this part.
+template <typename C> struct MeetAcc;
+template <> struct MeetAcc<float2> {
+    double sr = 0, si = 0;
+    float sa = 0, s2 = 0;
+    __device__ __forceinline__ void add(float2 l, float2 r) {
+        const float px = fmaf(l.x, r.x, -l.y * r.y), py = fmaf(l.x, r.y, l.y * r.x);
+        const float q = fmaf(px, px, py * py);
+        sr += (double)px;
+        si += (double)py;
+        sa += sqrtf(q);
+        s2 += q;
+    }
+};
+template <> struct MeetAcc<double2> {
+    double sr = 0, si = 0, sa = 0, s2 = 0;
+    __device__ __forceinline__ void add(double2 l, double2 r) {
+        const double px = l.x * r.x - l.y * r.y, py = l.x * r.y + l.y * r.x;
+        const double q = px * px + py * py;
+        sr += px; si += py; sa += sqrt(q); s2 += q;
+    }
+};
+
 __device__ __forceinline__ double wsum(double v) {
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
@@ -188,13 +215,9 @@ __global__ void __launch_bounds__(512) brick_smem_kernel(BrickDev d, const PairI
             sync();
         }
     }
-    double sr = 0, si = 0, sa = 0, s2 = 0;
-    for (uint32_t w = tid; w < S; w += gt) {
-        double lx = Lp[w].x, ly = Lp[w].y, rx = A[w].x, ry = A[w].y;
-        double px = lx * rx - ly * ry, py = lx * ry + ly * rx;
-        double q = px * px + py * py;
-        sr += px; si += py; sa += sqrt(q); s2 += q;
-    }
+    MeetAcc<C> acc;
+    for (uint32_t w = tid; w < S; w += gt) acc.add(Lp[w], A[w]);
+    double sr = acc.sr, si = acc.si, sa = (double)acc.sa, s2 = (double)acc.s2;
     sr = wsum(sr); si = wsum(si); sa = wsum(sa); s2 = wsum(s2);
     if (!warp_mode) {
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -358,7 +381,7 @@ __device__ __forceinline__ void win_dispatch(int type, C (&v)[1 << R], const C *
     }
 }
 
-constexpr int kMaxRegPasses = 96;
+constexpr int kMaxRegPasses = 160;
 
 __device__ __forceinline__ int srp_gate_base(const RegPass *rps, const BrickPass &ps) { return rps[ps.rp_off].gate_off; }
 
@@ -460,13 +483,9 @@ __global__ void __launch_bounds__(1024) brick_dot_kernel(BrickDev d, const PairI
     __shared__ double red[4][32];
     const uint32_t S = 1u << d.N;
     const C *L = states + (size_t)blockIdx.x * 2 * S, *R = L + S;
-    double sr = 0, si = 0, sa = 0, s2 = 0;
-    for (uint32_t w = threadIdx.x; w < S; w += blockDim.x) {
-        double lx = L[w].x, ly = L[w].y, rx = R[w].x, ry = R[w].y;
-        double px = lx * rx - ly * ry, py = lx * ry + ly * rx;
-        double q = px * px + py * py;
-        sr += px; si += py; sa += sqrt(q); s2 += q;
-    }
+    MeetAcc<C> acc;
+    for (uint32_t w = threadIdx.x; w < S; w += blockDim.x) acc.add(L[w], R[w]);
+    double sr = acc.sr, si = acc.si, sa = (double)acc.sa, s2 = (double)acc.s2;
     sr = wsum(sr); si = wsum(si); sa = wsum(sa); s2 = wsum(s2);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) { red[0][wid] = sr; red[1][wid] = si; red[2][wid] = sa; red[3][wid] = s2; }
