@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-target", action="store_true", help="skip the GPU-seconds-to-1%% measurement")
     return ap.parse_args()
 
 
@@ -117,6 +118,52 @@ def run_reference(args):
             "cpu_baseline": cpu_baseline_obj(value, cores, last[0], last[1]),
             "e2e": {"value": value, "unit": "contractions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU-seconds to F^(2) at 1% relative standard error, mixed vs plain FP64
+# ---------------------------------------------------------------------------
+def per_pair_cost(fp, l, prec, count, first):
+    """Device seconds per pair of depth l (all kernels of the trace path)."""
+    ens = fp.Ensemble(fp.PARALLEL, WORK["n"], l, l, seed=WORK["seed"], flags=fp.FLAG_TIMING)
+    ens.trace_batch(first, min(count, 64), prec)             # plans, autotuning, warm caches
+    ens.kernel_stats(reset=True)
+    ens.trace_batch(first + 64, count, prec)
+    ks = ens.kernel_stats(reset=True)
+    ens.close()
+    return sum(ks.ms[i] for i in range(8)) / 1e3 / count
+
+
+def gpu_seconds_to_target(fp, mom, P, K, ng, rel=0.01):
+    """N_g pairs per depth group for rel. stderr of F^(2) <= rel, from the moments of
+    the last timed step; GPU-s = sum_g N_g x measured per-pair device time of depth g,
+    for the FP32 (mixed) and FP64 paths; plus an actual adaptive run on the mixed path."""
+    m = mom.cpu().numpy().reshape(ng, 2 * K + 1)
+    out = {"target_rel_stderr": rel, "groups": {}}
+    tot32 = tot64 = 0.0
+    for g in range(ng):
+        l = WORK["depth_min"] + g
+        N, S2, Q2 = m[g, 0], m[g, 2], m[g, K + 2]
+        F2 = S2 / N
+        var = (Q2 - S2 * S2 / N) / (N - 1)
+        need = var / (rel * F2) ** 2
+        c32 = per_pair_cost(fp, l, fp.PREC_FP32, 2000 if l >= 9 else 4000, 50_000_000)
+        c64 = per_pair_cost(fp, l, fp.PREC_FP64, 32 if l >= 10 else (64 if l == 9 else 256), 60_000_000)
+        out["groups"][str(l)] = {"F2": F2, "pairs_needed": need, "s_per_pair_fp32": c32, "s_per_pair_fp64": c64}
+        tot32 += need * c32
+        tot64 += need * c64
+    out["gpu_s_mixed_fp32"] = tot32
+    out["gpu_s_plain_fp64"] = tot64
+    out["speedup"] = tot64 / tot32 if tot32 > 0 else None
+    out["method"] = ("pairs_needed from the variance of |Tr|^4 per depth group (last timed step); per-pair "
+                     "device seconds measured per depth with CUDA events; GPU-s = sum over groups")
+    ens = fp.Ensemble(fp.PARALLEL, WORK["n"], WORK["depth_min"], WORK["depth_max"], seed=WORK["seed"])
+    F, se, st = ens.frame_potential(70_000_000, 3_000_000, 2, rel, fp.PREC_FP32)
+    ens.close()
+    out["mixed_run"] = {"pairs": int(st.pairs), "gpu_seconds": st.gpu_seconds, "reached": bool(st.reached_target),
+                        "fp64_recontracted": int(st.fp64_recontracted),
+                        "F2_by_depth": {str(WORK["depth_min"] + g): [float(F[g, 1]), float(se[g, 1])] for g in range(ng)}}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -246,12 +293,17 @@ def main():
     # e2e: the public Monte Carlo call, results to host memory, host wall clock
     e2e = None
     if not args.no_e2e:
-        ens.frame_potential(first_of(args.warmup + args.steps), P, K, 0.0, prec)   # warm
+        # a user's ensemble: no per-kernel timing, so sub-batches replay CUDA graphs
+        ens_u = fp.Ensemble(fp.PARALLEL, WORK["n"], WORK["depth_min"], WORK["depth_max"], seed=WORK["seed"],
+                            stream=stream.cuda_stream)
+        ens_u.frame_potential(first_of(args.warmup + args.steps), P, K, 0.0, prec)   # warm
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for s in range(args.steps):
-            ens.frame_potential(first_of(args.warmup + args.steps + 1 + s), P, K, 0.0, prec)
+            ens_u.frame_potential(first_of(args.warmup + args.steps + 1 + s), P, K, 0.0, prec)
         dt = time.perf_counter() - t0
+        replays = int(ens_u.kernel_stats().graph_replays)
+        ens_u.close()
         # host->device per step: PairInfo (40 B) + order (4 B) + group (4 B) per pair;
         # device->host: kappa (8 B/pair, FP32 policy) + per-batch moments
         batches = 0
@@ -263,7 +315,8 @@ def main():
         h2d = P * (40 + 4 + 4)
         d2h = (P * 8 if prec == fp.PREC_FP32 else 0) + batches * ng * (2 * K + 1) * 8
         e2e = {"value": world * P * args.steps / dt, "unit": "contractions/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+               "d2h_bytes_per_step": d2h, "api": "fp_frame_potential (results to host)",
+               "graph_replays": replays}
 
     value = world * P * args.steps / (ms / 1e3)
     # roofline of the dominant kernel class
@@ -286,6 +339,8 @@ def main():
             "data": "synthetic (seeded circuit pairs)", "config": workload_config(args, world),
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
             "kernel_ms": {fp.K_NAMES.get(i, str(i)): ks.ms[i] for i in range(8) if ks.launches[i]}}
+    if rank == 0 and world == 1 and not args.no_target:
+        line["gpu_s_to_1pct_F2"] = gpu_seconds_to_target(fp, mom, P, K, ng)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         r, dt, npairs, depths = oracle_time(10_000_000, cores)

@@ -85,7 +85,9 @@ enum {
     FP_FLAG_SELF_PAIR = 1,        /* V := U for every pair (Tr = 2^n exactly) */
     FP_FLAG_DIAGONAL_GATES = 2,   /* FP_PARALLEL/FP_LOCAL with random diagonal gates */
     FP_FLAG_GENERIC_ONLY = 4,     /* never use the specialised brickwork kernels */
-    FP_FLAG_TIMING = 8            /* record CUDA-event time of every launch (fp_kernel_stats_get) */
+    FP_FLAG_TIMING = 8,           /* record CUDA-event time of every launch (fp_kernel_stats_get);
+                                     also disables CUDA-graph replay */
+    FP_FLAG_NO_GRAPHS = 16        /* launch every kernel directly (no CUDA-graph replay) */
 };
 
 /* Kernel classes of fp_kernel_stats. */
@@ -147,6 +149,7 @@ typedef struct {
     double work[FP_K_CLASSES];        /* algorithmic work: complex multiply-adds for the sweep
                                          classes, pairs for the others */
     uint64_t pairs;                   /* pairs contracted */
+    uint64_t graph_replays;           /* sub-batches run by CUDA-graph replay (counted always) */
 } fp_kernel_stats;
 
 /* Create an ensemble.  `cuda_stream` is a cudaStream_t (NULL: default stream).

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libfp_gb300.so")
 
 PARALLEL, LOCAL, HEA = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_FP32_RAW = 0, 1, 2
-FLAG_SELF_PAIR, FLAG_DIAGONAL_GATES, FLAG_GENERIC_ONLY, FLAG_TIMING = 1, 2, 4, 8
+FLAG_SELF_PAIR, FLAG_DIAGONAL_GATES, FLAG_GENERIC_ONLY, FLAG_TIMING, FLAG_NO_GRAPHS = 1, 2, 4, 8, 16
 K_SAMPLE, K_MERGE, K_TABLES, K_SWEEP, K_BRICK, K_MOMENTS, K_CLASSES = 0, 1, 2, 3, 4, 5, 8
 K_NAMES = {0: "sample", 1: "merge", 2: "tables", 3: "sweep_generic", 4: "sweep_brick", 5: "moments"}
 MAX_STATE_BITS = 24
@@ -51,7 +51,7 @@ class RunStats(ctypes.Structure):
 
 class KernelStats(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8), ("work", ctypes.c_double * 8),
-                ("pairs", ctypes.c_uint64)]
+                ("pairs", ctypes.c_uint64), ("graph_replays", ctypes.c_uint64)]
 
 
 class GateRec(ctypes.Structure):

@@ -16,6 +16,7 @@
 #include <map>
 #include <memory>
 #include <numeric>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -81,6 +82,16 @@ namespace fpk {
 void set_last_error(const char *msg) { g_err = msg; }
 }  // namespace fpk
 
+struct GraphKey {
+    int key;
+    uint64_t nb;
+    const void *pairs, *raw, *maps, *states, *tr, *kappa, *err;
+    bool operator<(const GraphKey &o) const {
+        return std::tie(key, nb, pairs, raw, maps, states, tr, kappa, err) <
+               std::tie(o.key, o.nb, o.pairs, o.raw, o.maps, o.states, o.tr, o.kappa, o.err);
+    }
+};
+
 struct BrickCache {
     BrickHostPlan hp;
     DBuf d_gates, d_rpasses, d_rgates;
@@ -113,6 +124,11 @@ struct fp_ensemble {
     std::map<int, std::unique_ptr<BrickCache>> brick_plans;   // key 2*l + fp32
     DBuf d_maps, d_states;
     std::string gpu_name;
+    // CUDA graphs of the brickwork sub-batch pipeline
+    cudaStream_t gst = nullptr;
+    cudaEvent_t gev[2] = {};
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    uint64_t graph_replays = 0;
 };
 
 namespace {
@@ -535,22 +551,62 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
         CK(E->d_raw.reserve(nb * per_raw));
         CK(E->d_maps.reserve(nb * per_map));
         CK(E->d_states.reserve(std::max<size_t>(16, nb * per_state)));
+        const double G = (double)std::max(bd.n_layers[0], bd.n_layers[1]) * bd.m;
+        const double err_scale = FP_ERR_SAFETY * (fp32 ? 0x1.0p-24 : 0x1.0p-53) * std::sqrt(G);
+        // CUDA graph replay: the launch sequence of a sub-batch (sampler, maps,
+        // init, passes, meet) is captured once per (depth, precision, size,
+        // buffers) on the ensemble's internal stream and replayed with fresh
+        // pair records; the first sub-batch of a shape runs directly (it also
+        // sets the kernels' shared-memory attributes outside any capture).
+        const bool use_graph = !E->timing && !(d.flags & FP_FLAG_NO_GRAPHS);
+        GraphKey gk{key, nb, E->d_pairs.p, E->d_raw.p, E->d_maps.p, E->d_states.p, tr, kappa, err};
+        auto git = use_graph ? E->graphs.find(gk) : E->graphs.end();
         CK(cudaEventRecord(E->ev0, E->st));
-        {
-            KTimer t(E, FP_K_SAMPLE);
-            CK(launch_sample(sp, E->d_pairs.as<PairInfo>(), (int)nb, n_raw, E->d_raw.as<double2>(), E->st));
-            CK(t.stop((double)nb));
-        }
-        {
-            KTimer t(E, FP_K_BRICK);
-            int nl = 0;
-            const double G = (double)std::max(bd.n_layers[0], bd.n_layers[1]) * bd.m;
-            const double err_scale = FP_ERR_SAFETY * (fp32 ? 0x1.0p-24 : 0x1.0p-53) * std::sqrt(G);
-            CK(launch_brick(bd, bp.passes.data(), it->second->dp, E->d_pairs.as<PairInfo>(), (int)nb,
-                            E->d_raw.as<double2>(), E->d_maps.p, E->d_states.p, fp32, err_scale, tr, kappa, err,
-                            E->st, &nl));
-            CK(t.stop(cmac_pair * (double)nb));
-            if (E->timing) E->kst.launches[FP_K_BRICK] += (uint64_t)(nl - 1);
+        if (use_graph && git != E->graphs.end() && git->second) {
+            CK(cudaEventRecord(E->gev[0], E->st));
+            CK(cudaStreamWaitEvent(E->gst, E->gev[0], 0));
+            CK(cudaGraphLaunch(git->second, E->gst));
+            CK(cudaEventRecord(E->gev[1], E->gst));
+            CK(cudaStreamWaitEvent(E->st, E->gev[1], 0));
+            E->graph_replays++;
+        } else {
+            {
+                KTimer t(E, FP_K_SAMPLE);
+                CK(launch_sample(sp, E->d_pairs.as<PairInfo>(), (int)nb, n_raw, E->d_raw.as<double2>(), E->st));
+                CK(t.stop((double)nb));
+            }
+            {
+                KTimer t(E, FP_K_BRICK);
+                int nl = 0;
+                CK(launch_brick(bd, bp.passes.data(), it->second->dp, E->d_pairs.as<PairInfo>(), (int)nb,
+                                E->d_raw.as<double2>(), E->d_maps.p, E->d_states.p, fp32, err_scale, tr, kappa, err,
+                                E->st, &nl));
+                CK(t.stop(cmac_pair * (double)nb));
+                if (E->timing) E->kst.launches[FP_K_BRICK] += (uint64_t)(nl - 1);
+            }
+            if (use_graph) {
+                if (E->graphs.size() > 64) {
+                    for (auto &kv : E->graphs) if (kv.second) cudaGraphExecDestroy(kv.second);
+                    E->graphs.clear();
+                }
+                cudaGraph_t graph = nullptr;
+                cudaGraphExec_t exec = nullptr;
+                CK(cudaStreamBeginCapture(E->gst, cudaStreamCaptureModeThreadLocal));
+                cudaError_t ce = launch_sample(sp, E->d_pairs.as<PairInfo>(), (int)nb, n_raw, E->d_raw.as<double2>(), E->gst);
+                int nl = 0;
+                if (ce == cudaSuccess)
+                    ce = launch_brick(bd, bp.passes.data(), it->second->dp, E->d_pairs.as<PairInfo>(), (int)nb,
+                                      E->d_raw.as<double2>(), E->d_maps.p, E->d_states.p, fp32, err_scale, tr, kappa,
+                                      err, E->gst, &nl);
+                cudaError_t ee = cudaStreamEndCapture(E->gst, &graph);
+                if (ce == cudaSuccess && ee == cudaSuccess && graph) {
+                    ce = cudaGraphInstantiate(&exec, graph, 0);
+                    if (ce != cudaSuccess) exec = nullptr;
+                }
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();           // a failed capture leaves the direct path in use
+                E->graphs[gk] = exec;
+            }
         }
         CK(cudaEventRecord(E->ev1, E->st));
         CK(cudaEventSynchronize(E->ev1));
@@ -671,6 +727,9 @@ fp_status fp_ensemble_create(const fp_ensemble_desc *desc, void *cuda_stream, fp
     CK(cudaEventCreate(&E->ev0));
     CK(cudaEventCreate(&E->ev1));
     E->timing = (d.flags & FP_FLAG_TIMING) != 0;
+    CK(cudaStreamCreateWithFlags(&E->gst, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&E->gev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&E->gev[1], cudaEventDisableTiming));
     for (int k = 0; k < 2 * FP_K_CLASSES; ++k) CK(cudaEventCreate(&E->kev[k]));
     *out = E.release();
     return FP_OK;
@@ -684,6 +743,10 @@ void fp_ensemble_destroy(fp_ensemble *ens) {
     if (ens->ev1) cudaEventDestroy(ens->ev1);
     for (int k = 0; k < 2 * FP_K_CLASSES; ++k)
         if (ens->kev[k]) cudaEventDestroy(ens->kev[k]);
+    if (ens->gst) cudaStreamSynchronize(ens->gst);
+    for (auto &kv : ens->graphs) if (kv.second) cudaGraphExecDestroy(kv.second);
+    for (int k = 0; k < 2; ++k) if (ens->gev[k]) cudaEventDestroy(ens->gev[k]);
+    if (ens->gst) cudaStreamDestroy(ens->gst);
     delete ens;
 }
 
@@ -840,7 +903,11 @@ fp_status fp_frame_potential(fp_ensemble *ens, uint64_t first, uint64_t max_pair
 fp_status fp_kernel_stats_get(fp_ensemble *ens, fp_kernel_stats *out, int32_t reset) {
     if (!ens || !out) return fail(FP_ERR_ARG, "null argument");
     *out = ens->kst;
-    if (reset) std::memset(&ens->kst, 0, sizeof ens->kst);
+    out->graph_replays = ens->graph_replays;
+    if (reset) {
+        std::memset(&ens->kst, 0, sizeof ens->kst);
+        ens->graph_replays = 0;
+    }
     return FP_OK;
 }
 

@@ -295,6 +295,21 @@ def test_brick_small_and_odd_chains(fp, n, l):
     assert rel_err(tr, ref).max() <= TOL64
 
 
+@pytest.mark.parametrize("l,prec", [(8, 2), (10, 2), (6, 0)])
+def test_graph_replay_matches_direct_launches(fp, l, prec):
+    # the same sub-batch shape three times: the first runs directly and is
+    # captured, the next two replay the CUDA graph; results are bit-identical
+    # to an ensemble that never uses graphs
+    a = fp.Ensemble(0, 30, l, l, seed=5)
+    b = fp.Ensemble(0, 30, l, l, seed=5, flags=fp.FLAG_NO_GRAPHS)
+    for first in (0, 1000, 2000):
+        ta, ka, _, ea = a.trace_batch(first, 96, prec, with_err=True)
+        tb, kb, _, eb = b.trace_batch(first, 96, prec, with_err=True)
+        assert np.array_equal(ta, tb) and np.array_equal(ka, kb) and np.array_equal(ea, eb)
+    assert a.kernel_stats().graph_replays >= 2
+    assert b.kernel_stats().graph_replays == 0
+
+
 def test_bench_workload_sampled_parity(fp):
     # The benchmark's own ensemble (n = 50, l uniform in 2..10, seed 4) in the
     # benchmark's launch shape (one large batch split by depth), FP32 policy
