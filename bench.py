@@ -30,7 +30,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Tr(U^dagger V) contractions/s at n=50 (brickwork, l=2..10)"
-WORK = dict(n=50, depth_min=2, depth_max=10, pairs=100_000, seed=4, k_max=4)
+WORK = dict(n=50, depth_min=2, depth_max=10, pairs=100_000, seed=4, k_max=4, kind=0, name="brickwork")
+# other workloads (parity-test configurations, measurable with --workload)
+WORKLOADS = {
+    "brickwork": dict(WORK),
+    "hea": dict(n=50, depth_min=1, depth_max=8, pairs=1_000_000, seed=3, k_max=4, kind=2, name="hea"),
+}
 SM_COUNT, FP32_LANES = 152, 128
 
 
@@ -45,12 +50,19 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-target", action="store_true", help="skip the GPU-seconds-to-1%% measurement")
-    return ap.parse_args()
+    ap.add_argument("--workload", default="brickwork", choices=sorted(WORKLOADS),
+                    help="brickwork (the headline workload) or hea (n=50, L=1..8)")
+    a = ap.parse_args()
+    WORK.update(WORKLOADS[a.workload])
+    if a.pairs == 100_000 and a.workload != "brickwork":
+        a.pairs = WORK["pairs"]
+    return a
 
 
 def workload_config(args, world):
-    return {"workload": "brickwork n=50, l uniform in 2..10 per pair, Haar U(4), "
-                        f"{args.pairs} pairs per step per GPU",
+    desc = ("brickwork n=50, l uniform in 2..10 per pair, Haar U(4)" if WORK["name"] == "brickwork" else
+            "HEA n=50, L uniform in 1..8 per pair, RY(theta)RZ(phi) + CZ ladder")
+    return {"workload": f"{desc}, {args.pairs} pairs per step per GPU",
             "n": WORK["n"], "depth": [WORK["depth_min"], WORK["depth_max"]], "pairs_per_step": args.pairs,
             "k_max": WORK["k_max"], "precision": args.prec, "parallelism": f"pairs sharded over {world} GPU(s)",
             "l2": "per-step device working set (sampled gates, tables, boundaries) is GBs, larger than L2"}
@@ -248,7 +260,7 @@ def main():
     prec = fp.PREC_FP32 if args.prec == "fp32" else fp.PREC_FP64
     stream = torch.cuda.current_stream()
     P, K = args.pairs, WORK["k_max"]
-    ens = fp.Ensemble(fp.PARALLEL, WORK["n"], WORK["depth_min"], WORK["depth_max"], seed=WORK["seed"],
+    ens = fp.Ensemble(WORK["kind"], WORK["n"], WORK["depth_min"], WORK["depth_max"], seed=WORK["seed"],
                       flags=fp.FLAG_TIMING, stream=stream.cuda_stream)
     ng = len(ens.groups())
     tr = torch.empty(2 * P, dtype=torch.float64, device="cuda")
@@ -294,7 +306,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         # a user's ensemble: no per-kernel timing, so sub-batches replay CUDA graphs
-        ens_u = fp.Ensemble(fp.PARALLEL, WORK["n"], WORK["depth_min"], WORK["depth_max"], seed=WORK["seed"],
+        ens_u = fp.Ensemble(WORK["kind"], WORK["n"], WORK["depth_min"], WORK["depth_max"], seed=WORK["seed"],
                             stream=stream.cuda_stream)
         ens_u.frame_potential(first_of(args.warmup + args.steps), P, K, 0.0, prec)   # warm
         torch.cuda.synchronize()
@@ -333,15 +345,16 @@ def main():
             "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz",
             "kernel_ms_share": ks.ms[cls] / ms if ms else None}
 
-    line = {"metric": METRIC, "value": value, "unit": "contractions/s", "n_gpus": world, "steps": args.steps,
+    metric = METRIC if WORK["name"] == "brickwork" else "Tr(U^dagger V) contractions/s at n=50 (HEA, L=1..8)"
+    line = {"metric": metric, "value": value, "unit": "contractions/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec != fp.PREC_FP64 else "f64",
             "data": "synthetic (seeded circuit pairs)", "config": workload_config(args, world),
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
             "kernel_ms": {fp.K_NAMES.get(i, str(i)): ks.ms[i] for i in range(8) if ks.launches[i]}}
-    if rank == 0 and world == 1 and not args.no_target:
+    if rank == 0 and world == 1 and not args.no_target and WORK["name"] == "brickwork":
         line["gpu_s_to_1pct_F2"] = gpu_seconds_to_target(fp, mom, P, K, ng)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and WORK["name"] == "brickwork":
         cores = os.cpu_count() or 1
         r, dt, npairs, depths = oracle_time(10_000_000, cores)
         line["cpu_baseline"] = cpu_baseline_obj(r, cores, npairs, depths)

@@ -390,9 +390,9 @@ fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t
 
 // Build and upload one brickwork plan variant.
 fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int TH, std::unique_ptr<BrickCache> &out) {
-    const int N = 2 * (l - 1);
     auto bc = std::make_unique<BrickCache>();
-    bc->hp = make_brick_plan(E->d.n, l, K, fp32 ? 5 : 4, R);   // K > N: shared-memory sweep, K == N: one tile
+    // K > N: shared-memory sweep, K == N: one tile
+    bc->hp = make_brick_plan(E->d.n, l, K, fp32 ? 5 : 4, R, E->d.kind == FP_HEA ? 1 : 0);
     for (const auto &ps : bc->hp.passes) {
         if (ps.n_gates > 255) return fail(FP_ERR_ARG, "tile pass with %d gates exceeds 255", ps.n_gates);
         if (ps.n_rp > 160) return fail(FP_ERR_ARG, "tile pass with %d register passes exceeds 160", ps.n_rp);
@@ -448,7 +448,8 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
     }
     if (!have && !idx.empty()) {
         const uint64_t nt = std::min<uint64_t>(idx.size(), 96);
-        const int n_raw = (int)layout_brickwork(d.n, l).size();
+        const int n_raw = d.kind == FP_HEA ? l * d.n : (int)layout_brickwork(d.n, l).size();
+        const int n_maps = (d.kind == FP_HEA ? 2 * d.n : d.n - 1) * (l - 1);
         const size_t celem = fp32 ? sizeof(float2) : sizeof(double2);
         std::vector<PairInfo> pinfo(nt);
         for (uint64_t i = 0; i < nt; ++i) {
@@ -460,7 +461,7 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
         }
         CK(upload(E->d_pairs, pinfo, E->st));
         CK(E->d_raw.reserve(nt * 2 * n_raw * 16 * sizeof(double2)));
-        CK(E->d_maps.reserve(nt * (d.n - 1) * (l - 1) * 16 * celem));
+        CK(E->d_maps.reserve(nt * n_maps * 16 * celem));
         CK(E->d_states.reserve(nt * 2 * ((size_t)1 << N) * celem));
         SampleParams sp;
         sp.seed = d.seed; sp.n = d.n; sp.raw_kind = E->raw_kind; sp.self_pair = (d.flags & FP_FLAG_SELF_PAIR) ? 1 : 0;
@@ -522,16 +523,16 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
     const BrickDev &bd = bp.dev;
     const size_t celem = fp32 ? sizeof(float2) : sizeof(double2);
     const size_t S = (size_t)1 << N;
-    const int n_raw = (int)layout_brickwork(d.n, l).size();
+    const int n_raw = d.kind == FP_HEA ? l * d.n : (int)layout_brickwork(d.n, l).size();
     const size_t per_raw = (size_t)2 * n_raw * 16 * sizeof(double2);
-    const size_t per_map = (size_t)(d.n - 1) * (l - 1) * 16 * celem;
+    const size_t per_map = (size_t)maps_per_pair(bd) * 16 * celem;
     bool both = false;
     if (bd.tile_bits == 0) brick_smem_bytes(bd, fp32, &both);
     const size_t per_state = bd.tile_bits ? 2 * S * celem : (both ? 0 : S * celem);
     const size_t per_pair = per_raw + per_map + per_state;
     uint64_t cap = std::max<uint64_t>(1, std::min<uint64_t>(65535, E->ws_budget / per_pair));
     // flop count of the sweep (complex multiply-adds): 4 per amplitude per gate
-    const double cmac_pair = 4.0 * (double)S * (double)(d.n - 1) * (double)(l - 1);
+    const double cmac_pair = 4.0 * (double)S * (double)maps_per_pair(bd);
     SampleParams sp;
     sp.seed = d.seed;
     sp.n = d.n;
@@ -623,7 +624,7 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
 fp_status route(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx, const std::vector<int> &depth,
                 int prec, double *tr, double *kappa, double *err, float *gpu_ms) {
     const fp_ensemble_desc &d = E->d;
-    const bool brick = d.kind == FP_PARALLEL && !(d.flags & FP_FLAG_GENERIC_ONLY);
+    const bool brick = (d.kind == FP_PARALLEL || d.kind == FP_HEA) && !(d.flags & FP_FLAG_GENERIC_ONLY);
     std::map<int, std::vector<uint64_t>> by_depth;
     std::vector<uint64_t> generic;
     for (uint64_t i : idx) {

@@ -59,8 +59,11 @@ struct RegGate {
 
 struct BrickDev {       // uniform over a sub-batch (one depth)
     int32_t n, l, m, N, cut;
-    int32_t n_layers[2];      // side 0: bonds 0..cut-1; side 1: bonds n-2..cut
-    int32_t delta_par[2];     // delta(w_tau, w_tau+1) for tau of this parity at the chain end
+    int32_t kind;             // 0: brickwork (l = depth), 1: HEA (l = L)
+    int32_t n_layers[2];      // brickwork: side 0 bonds 0..cut-1, side 1 bonds n-2..cut;
+                              // HEA: two layers per qubit (see below)
+    int32_t delta_par[2];     // brickwork: delta(w_tau, w_tau+1) for tau of this parity at
+                              // the chain end; HEA: the chain ends start from all ones
     int32_t pass_off[2], n_passes[2];
     int32_t tile_bits;        // K of the tiled path (0: whole state in one CTA)
 };
@@ -82,9 +85,30 @@ struct BrickHostPlan {
     std::vector<RegGate> rgates;
 };
 
-// Layer parity of layer t of a side, and the bond it sweeps.
+// Brickwork: the bond that layer t of a side sweeps.
 FP_HD int brick_bond(const BrickDev &d, int side, int t) { return side == 0 ? t : d.n - 2 - t; }
+// Pairing of layer t: gates on bits (2j + p, 2j + p + 1 mod N).
+FP_HD int layer_parity(const BrickDev &d, int side, int t) {
+    return d.kind == 0 ? (brick_bond(d, side, t) + 1) % 2 : t % 2;
+}
+// Maps of a pair are stored [side][layer][j]: index of gate j of layer t.
+FP_HD int map_index(const BrickDev &d, int side, int t, int j) {
+    return ((side ? d.n_layers[0] : 0) + t) * d.m + j;
+}
+FP_HD int maps_per_pair(const BrickDev &d) { return (d.n_layers[0] + d.n_layers[1]) * d.m; }
+// HEA (kind 1).  U^dagger V after the merges is a cycle of 2L-2 rotation
+// slots per qubit with a CZ ladder after each: slot s = 0: R_1^V R_1^U^dagger,
+// s = 1..L-2: R_{s+1}^V, s = L-1: R_L^U^dagger R_L^V, s = L..2L-3:
+// R_{2L-1-s}^U^dagger.  Segment s of a wire runs from slot s through ladder s
+// to slot s+1, so the boundary is a state over the 2L-2 segments of one qubit.
+// Sweeping qubit q multiplies by its rotations, R_{q,s}[y_s, y_{s-1}] (a
+// diagonal map on bits (s-1, s)), then crosses the CZ ladder, an
+// unnormalised Hadamard [[1,1],[1,-1]] on every bit.  As brickwork layers:
+// layer 2i: diagonal maps on pairs (2j, 2j+1) (slots 2j+1); layer 2i+1: the
+// diagonal maps on pairs (2j+1, 2j+2) (slots 2j+2) followed by H x H.  Side 0
+// sweeps qubits 0..cut-1; side 1 qubits n-1..cut+1 and finally qubit cut's
+// rotations without a ladder.
 
-BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win_bits);
+BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win_bits, int kind = 0);
 
 }  // namespace fpk

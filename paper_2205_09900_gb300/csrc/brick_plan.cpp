@@ -71,7 +71,7 @@ static void schedule_registers(BrickHostPlan &P, BrickPass &ps, const int *ring,
     ps.n_rp = (int)P.rpasses.size() - ps.rp_off;
 }
 
-BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win_bits) {
+BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win_bits, int kind) {
     BrickHostPlan P;
     BrickDev &d = P.dev;
     std::memset(&d, 0, sizeof d);
@@ -80,8 +80,9 @@ BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win
     d.m = l - 1;
     d.N = 2 * d.m;
     d.cut = n / 2;
-    d.n_layers[0] = d.cut;
-    d.n_layers[1] = n - 1 - d.cut;
+    d.kind = kind;
+    d.n_layers[0] = kind == 0 ? d.cut : 2 * d.cut;
+    d.n_layers[1] = kind == 0 ? n - 1 - d.cut : 2 * (n - 1 - d.cut) + 2;
     d.delta_par[0] = 0;        // qubit 0 is idle where bond 0 (parity 1 positions) is not
     d.delta_par[1] = n % 2;    // qubit n-1 is idle where bond n-2 is not
     const int N = d.N, m = d.m;
@@ -104,7 +105,7 @@ BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win
         const int L = d.n_layers[side];
         d.pass_off[side] = (int)P.passes.size();
         std::vector<char> done((size_t)L * m, 0);
-        auto par = [&](int t) { return (brick_bond(d, side, t) + 1) % 2; };
+        auto par = [&](int t) { return layer_parity(d, side, t); };
         auto bits = [&](int t, int j) {
             int tau = 2 * j + par(t);
             return (1u << tau) | (1u << ((tau + 1) % N));

@@ -78,29 +78,85 @@ __device__ __forceinline__ bool delta_ok(uint32_t w, int N, int par) {
 }
 
 template <typename C>
+__device__ __forceinline__ void store_map(C *out, const double2 (&G)[16]) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) out[e] = from_z<C>(G[e]);
+}
+
+template <typename C>
 __global__ void brick_maps_kernel(BrickDev d, const PairInfo *__restrict__ pairs, const double2 *__restrict__ raw,
                                   C *__restrict__ maps) {
     const PairInfo pi = pairs[blockIdx.y];
-    const int nb = d.n - 1, m = d.m, l = d.l;
+    const int m = d.m, l = d.l;
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= nb * m) return;
-    const int b = id / m, j = id % m;
-    const int tau = 2 * j + (b + 1) % 2;
-    const int c0 = d.n / 2, c1 = (d.n - 1) / 2;
-    auto gidx = [&](int t) {   // raw index of layer t (1-based) on bond b
-        int tm = t - 1;
-        return ((tm + 1) / 2) * c0 + (tm / 2) * c1 + (b - tm % 2) / 2;
-    };
+    if (id >= maps_per_pair(d)) return;
+    const int g = id / m, j = id % m;
+    const int side = g < d.n_layers[0] ? 0 : 1, t = side ? g - d.n_layers[0] : g;
     const double2 *U = raw + pi.raw_off * 16;
     const double2 *V = raw + (pi.raw_off + pi.n_raw) * 16;
+    C *out = maps + ((size_t)blockIdx.y * maps_per_pair(d) + id) * 16;
+    double2 M[16];
+    if (d.kind == 1) {
+        // HEA: rotation slot s of qubit q as a diagonal map, with H x H on odd layers
+        const int q = side == 0 ? t / 2 : d.n - 1 - t / 2;
+        const int half = t % 2, N = d.N, L = l;
+        const int s = half == 0 ? 2 * j + 1 : (2 * j + 2) % N;
+        auto rot = [&](const double2 *C0, int tl) { return C0 + ((size_t)(tl - 1) * d.n + q) * 16; };
+        double2 R[4];
+        if (s == 0 || s == L - 1) {
+            const int tl = s == 0 ? 1 : L;
+            const double2 *A = rot(U, tl), *B = rot(V, tl);
+            // s = 0: R_1^V R_1^U^dagger ; s = L-1: R_L^U^dagger R_L^V
+            for (int r = 0; r < 2; ++r)
+                for (int c = 0; c < 2; ++c) {
+                    double2 acc = make_double2(0, 0);
+                    for (int k = 0; k < 2; ++k) {
+                        double2 t1 = s == 0 ? zmul(B[2 * r + k], zconj(A[2 * c + k])) : zmul(zconj(A[2 * k + r]), B[2 * k + c]);
+                        acc.x += t1.x; acc.y += t1.y;
+                    }
+                    R[2 * r + c] = acc;
+                }
+        } else if (s <= L - 2) {
+            const double2 *A = rot(V, s + 1);
+            for (int e = 0; e < 4; ++e) R[e] = A[e];
+        } else {
+            const double2 *A = rot(U, 2 * L - 1 - s);
+            for (int r = 0; r < 2; ++r)
+                for (int c = 0; c < 2; ++c) R[2 * r + c] = zconj(A[2 * c + r]);
+        }
+        // diagonal factor D[e], e = y_in + 2 y_out (bit 0: segment s-1, bit 1: segment s)
+        const bool ladder = half == 1 && !(side == 1 && q == d.cut);
+        for (int xe = 0; xe < 4; ++xe)
+            for (int ye = 0; ye < 4; ++ye) {
+                double2 v = make_double2(0, 0);
+                if (ladder) {
+                    const int sgn = ((xe & 1) & (ye & 1)) ^ ((xe >> 1) & (ye >> 1));
+                    v = R[ye];
+                    if (sgn) { v.x = -v.x; v.y = -v.y; }
+                } else if (xe == ye) {
+                    v = R[ye];
+                }
+                M[4 * xe + ye] = v;
+            }
+        store_map(out, M);
+        return;
+    }
+    // brickwork
+    const int b = brick_bond(d, side, t);
+    const int tau = 2 * j + (b + 1) % 2;
+    const int c0 = d.n / 2, c1 = (d.n - 1) / 2;
+    auto gidx = [&](int tl) {   // raw index of layer tl (1-based) on bond b
+        int tm = tl - 1;
+        return ((tm + 1) / 2) * c0 + (tm / 2) * c1 + (b - tm % 2) / 2;
+    };
     double2 G[16];
     if (tau <= l - 3) {
         const double2 *A = V + (size_t)gidx(tau + 2) * 16;
 #pragma unroll
         for (int e = 0; e < 16; ++e) G[e] = A[e];
     } else if (tau == l - 2 || tau == 2 * l - 3) {
-        const int t = tau == l - 2 ? l : 1;
-        const double2 *A = U + (size_t)gidx(t) * 16, *B = V + (size_t)gidx(t) * 16;
+        const int tl = tau == l - 2 ? l : 1;
+        const double2 *A = U + (size_t)gidx(tl) * 16, *B = V + (size_t)gidx(tl) * 16;
         // tau = l-2: U_l^dagger V_l ; tau = 2l-3: V_1 U_1^dagger
         for (int r = 0; r < 4; ++r)
             for (int c = 0; c < 4; ++c) {
@@ -117,8 +173,7 @@ __global__ void brick_maps_kernel(BrickDev d, const PairInfo *__restrict__ pairs
         for (int r = 0; r < 4; ++r)
             for (int c = 0; c < 4; ++c) G[4 * r + c] = zconj(A[4 * c + r]);
     }
-    const bool left = b < d.cut;
-    C *out = maps + ((size_t)blockIdx.y * nb * m + id) * 16;
+    const bool left = side == 0;
 #pragma unroll
     for (int xt = 0; xt < 2; ++xt)
 #pragma unroll
@@ -127,10 +182,11 @@ __global__ void brick_maps_kernel(BrickDev d, const PairInfo *__restrict__ pairs
             for (int yt = 0; yt < 2; ++yt)
 #pragma unroll
                 for (int yt1 = 0; yt1 < 2; ++yt1) {
-                    double2 g = G[(yt1 * 2 + xt1) * 4 + (yt * 2 + xt)];
+                    double2 gv = G[(yt1 * 2 + xt1) * 4 + (yt * 2 + xt)];
                     int ex = xt + 2 * xt1, ey = yt + 2 * yt1;
-                    out[left ? ex * 4 + ey : ey * 4 + ex] = from_z<C>(g);
+                    M[left ? ex * 4 + ey : ey * 4 + ex] = gv;
                 }
+    store_map(out, M);
 }
 
 // Accumulators of the meet: the trace sum in FP64; the |t| and |t|^2 sums
@@ -190,20 +246,20 @@ __global__ void __launch_bounds__(512) brick_smem_kernel(BrickDev d, const PairI
     };
     C *A = sm + (size_t)grp * (both ? 2 : 1) * S;
     C *Lp = both ? A + S : lscratch + (size_t)pidx * S;
-    const C *mp = maps + (size_t)pidx * (d.n - 1) * m * 16;
+    const C *mp = maps + (size_t)pidx * maps_per_pair(d) * 16;
     for (int side = 0; side < 2; ++side) {
         for (uint32_t w = tid; w < S; w += gt) {
             C v;
-            v.x = delta_ok(w, N, d.delta_par[side]) ? 1 : 0;
+            v.x = (d.kind == 1 || delta_ok(w, N, d.delta_par[side])) ? 1 : 0;
             v.y = 0;
             A[w] = v;
         }
         sync();
         for (int t = 0; t < d.n_layers[side]; ++t) {
-            const int bond = brick_bond(d, side, t), par = (bond + 1) % 2;
+            const int par = layer_parity(d, side, t);
             for (int j = 0; j < m; ++j) {
                 C T[16];
-                load_map(mp + ((size_t)bond * m + j) * 16, T);
+                load_map(mp + (size_t)map_index(d, side, t, j) * 16, T);
                 const int tau = 2 * j + par;
                 const int pa = tau, pb = (tau + 1) % N;
                 for (uint32_t q = tid; q < (S >> 2); q += gt) quad_apply(A, q, pa, pb, T);
@@ -245,7 +301,7 @@ __global__ void brick_init_kernel(BrickDev d, int npairs, C *__restrict__ states
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int side = (int)((i >> d.N) & 1);
         C v;
-        v.x = delta_ok((uint32_t)(i & (S - 1)), d.N, d.delta_par[side]) ? 1 : 0;
+        v.x = (d.kind == 1 || delta_ok((uint32_t)(i & (S - 1)), d.N, d.delta_par[side])) ? 1 : 0;
         v.y = 0;
         states[i] = v;
     }
@@ -429,11 +485,10 @@ __global__ void __launch_bounds__(TH) brick_pass_kernel(BrickDev d, int side, Br
         for (int k = 0; k < K - 7; ++k) o |= ((i >> k) & 1u) << pos[7 + k];
         lut_hi[i] = o;
     }
-    const C *mp = maps + (size_t)blockIdx.y * (d.n - 1) * m * 16;
+    const C *mp = maps + (size_t)blockIdx.y * maps_per_pair(d) * 16;
     for (int i = threadIdx.x; i < ps.n_gates * 16; i += TH) {
         const BrickGate gg = gates[ps.gate_off + i / 16];
-        const int bond = brick_bond(d, side, gg.layer);
-        stage_entry<C>(smaps + (i / 16) * MW, i % 16, mp[((size_t)bond * m + gg.j) * 16 + (i % 16)]);
+        stage_entry<C>(smaps + (i / 16) * MW, i % 16, mp[(size_t)map_index(d, side, gg.layer, gg.j) * 16 + (i % 16)]);
     }
     __syncthreads();
     C *st = states + ((size_t)blockIdx.y * 2 + side) * S + base;
@@ -534,7 +589,7 @@ cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const Bric
                          bool fp32, double err_scale, double *tr, double *kappa, double *err, cudaStream_t st,
                          int *launches) {
     if (npairs <= 0) return cudaSuccess;
-    const int nm = (d.n - 1) * d.m;
+    const int nm = maps_per_pair(d);
     dim3 gm((nm + 127) / 128, npairs);
     if (fp32) brick_maps_kernel<float2><<<gm, 128, 0, st>>>(d, pairs, raw, (float2 *)maps);
     else brick_maps_kernel<double2><<<gm, 128, 0, st>>>(d, pairs, raw, (double2 *)maps);

@@ -287,6 +287,39 @@ def test_brick_path_matches_generic_and_oracle(fp, prec, tol):
         assert np.abs(tg - ref).max() <= TOL32
 
 
+@pytest.mark.parametrize("prec,tol", [(0, TOL64), (1, TOL32)])
+def test_hea_brick_path_matches_generic_and_oracle(fp, prec, tol):
+    # HEA on the dual-circuit kernels (rotations as diagonal maps, CZ ladders as
+    # Hadamards on segment bits) against the generic planner path and the oracle
+    n, seed, N = 50, 17, 16
+    ens, od = make(fp, "hea", n, 2, 8, seed=seed)
+    gen = fp.Ensemble(2, n, 2, 8, seed=seed, flags=fp.FLAG_GENERIC_ONLY)
+    tb, _, _ = ens.trace_batch(0, N, prec)
+    tg, _, _ = gen.trace_batch(0, N, prec)
+    ref = O.trace_batch(od, 0, N, "ve", threads=8)
+    if prec == 0:
+        assert rel_err(tb, ref).max() <= TOL64
+        assert rel_err(tg, ref).max() <= TOL64
+    else:
+        assert np.abs(tb - ref).max() <= TOL32
+        assert np.abs(tg - ref).max() <= TOL32
+
+
+@pytest.mark.parametrize("n,L", [(2, 2), (3, 3), (5, 4), (8, 2), (51, 5)])
+def test_hea_small_and_odd_chains(fp, n, L):
+    ens, od = make(fp, "hea", n, L, seed=n * 7 + L)
+    tr, _, _ = ens.trace_batch(0, 12, fp.PREC_FP64)
+    ref = O.trace_batch(od, 0, 12, "auto", threads=8)
+    assert rel_err(tr, ref).max() <= TOL64
+
+
+def test_hea_self_pair_full_size(fp):
+    ens, _ = make(fp, "hea", 50, 8, seed=3, flags=1)
+    for prec, tol in ((0, 1e-10), (1, 1e-5)):
+        tr, _, _ = ens.trace_batch(0, 4, prec)
+        assert np.all(np.abs(tr - 2.0 ** 50) <= tol * 2.0 ** 50), tr
+
+
 @pytest.mark.parametrize("n,l", [(2, 2), (3, 2), (4, 5), (5, 3), (9, 6), (50, 6), (51, 7)])
 def test_brick_small_and_odd_chains(fp, n, l):
     ens, od = make(fp, "parallel", n, l, seed=n * 10 + l)
