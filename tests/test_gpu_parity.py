@@ -225,6 +225,17 @@ def test_frame_potential_matches_weingarten(fp):
     assert st.pairs == 200000
 
 
+@pytest.mark.parametrize("l", [5, 6])
+def test_frame_potential_n50_matches_weingarten(fp, l):
+    # full-size end-to-end check: the Monte Carlo F^(2) of the benchmark ensemble
+    # (n = 50) against the exact ensemble value from the Weingarten transfer matrix
+    ens = fp.Ensemble(0, 50, l, l, seed=123 + l)
+    F, se, st = ens.frame_potential(0, 400000, 2, 0.0, fp.PREC_FP32)
+    exact = O.weingarten_f2_brickwork(50, l)
+    assert abs(F[0, 0] - 1.0) < 5 * se[0, 0]
+    assert abs(F[0, 1] - exact) < 5 * se[0, 1], (F[0, 1], exact, se[0, 1])
+
+
 def test_frame_potential_single_haar_gate(fp):
     ens, _ = make(fp, "parallel", 2, 1, seed=37)
     F, se, st = ens.frame_potential(0, 300000, 4, 0.0, fp.PREC_FP64)
