@@ -269,8 +269,10 @@ def main():
     grp = torch.empty(P, dtype=torch.int32, device="cuda")
     mom = torch.empty(ng * (2 * K + 1), dtype=torch.float64, device="cuda")
 
+    from paper_2205_09900_gb300.shard import max_over_ranks, pair_range
+
     def first_of(step):
-        return (step * world + rank) * P
+        return pair_range(step, rank, world, P)[0]
 
     def step(s):
         ens.trace_batch(first_of(s), P, prec, tr, kap, grp, err)
@@ -293,11 +295,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, device="cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     ks = ens.kernel_stats(reset=True)
     launches = int(sum(ks.launches[i] for i in range(8)))
