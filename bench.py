@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-target", action="store_true", help="skip the GPU-seconds-to-1%% measurement")
+    ap.add_argument("--no-cv", action="store_true", help="skip the control-variate report")
     ap.add_argument("--workload", default="brickwork", choices=sorted(WORKLOADS),
                     help="brickwork (the headline workload) or hea (n=50, L=1..8)")
     a = ap.parse_args()
@@ -176,6 +177,35 @@ def gpu_seconds_to_target(fp, mom, P, K, ng, rel=0.01):
                         "fp64_recontracted": int(st.fp64_recontracted),
                         "F2_by_depth": {str(WORK["depth_min"] + g): [float(F[g, 1]), float(se[g, 1])] for g in range(ng)}}
     return out
+
+
+# ---------------------------------------------------------------------------
+# learned control variate for HEA F^(2) (L = 4..6) against the plain estimator
+# ---------------------------------------------------------------------------
+def control_variate_report(fp, n_train=100_000, n_correct=10_000, m_surrogate=10_000_000):
+    out = {}
+    for L in (4, 5, 6):
+        ens = fp.Ensemble(fp.HEA, 50, L, L, seed=50 + L)
+        r = ens.cv_frame_potential(0, n_train, n_correct, m_surrogate)
+        # plain estimator: per-pair device cost on this depth, pairs needed for the CV's stderr
+        ens_t = fp.Ensemble(fp.HEA, 50, L, L, seed=50 + L, flags=fp.FLAG_TIMING)
+        ens_t.trace_batch(90_000_000, 4096, fp.PREC_FP32)
+        ens_t.kernel_stats(reset=True)
+        ens_t.trace_batch(91_000_000, 100_000, fp.PREC_FP32)
+        ks = ens_t.kernel_stats(reset=True)
+        c_pair = sum(ks.ms[i] for i in range(8)) / 1e3 / 100_000
+        ens_t.close()
+        ens.close()
+        cv_s = r.gpu_seconds_exact + r.gpu_seconds_train + r.gpu_seconds_surrogate
+        plain_pairs = r.var_f / r.stderr_ ** 2
+        out[str(L)] = {"F2_cv": r.F2, "stderr_cv": r.stderr_, "F2_plain_on_corrections": r.F2_plain,
+                       "stderr_plain_on_corrections": r.stderr_plain,
+                       "variance_reduction": r.var_f / r.var_f_minus_g if r.var_f_minus_g > 0 else None,
+                       "gpu_s_cv": cv_s, "gpu_s_plain_same_stderr": plain_pairs * c_pair,
+                       "train_loss": r.train_loss}
+    return {"config": f"HEA n=50, L=4..6, {n_train} training pairs, {m_surrogate} surrogate evaluations, "
+                      f"{n_correct} exact corrections; MLP 4nL-256-256-256-1 GELU, Adam",
+            "by_depth": out}
 
 
 # ---------------------------------------------------------------------------
@@ -353,6 +383,8 @@ def main():
             "kernel_ms": {fp.K_NAMES.get(i, str(i)): ks.ms[i] for i in range(8) if ks.launches[i]}}
     if rank == 0 and world == 1 and not args.no_target and WORK["name"] == "brickwork":
         line["gpu_s_to_1pct_F2"] = gpu_seconds_to_target(fp, mom, P, K, ng)
+    if rank == 0 and world == 1 and not args.no_cv and WORK["name"] == "brickwork":
+        line["control_variate"] = control_variate_report(fp)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and WORK["name"] == "brickwork":
         cores = os.cpu_count() or 1
         r, dt, npairs, depths = oracle_time(10_000_000, cores)

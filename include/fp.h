@@ -208,6 +208,43 @@ fp_status fp_frame_potential(fp_ensemble *ens, uint64_t first, uint64_t max_pair
 /* Copy the ensemble's kernel counters into *out; reset them if `reset`. */
 fp_status fp_kernel_stats_get(fp_ensemble *ens, fp_kernel_stats *out, int32_t reset);
 
+/* Learned control variate for F^(2) (the paper has none; the estimate is the
+ * paper's F^(2), Sec. "Frame potential").  For a single-depth HEA ensemble
+ * (depth_min == depth_max == L) an MLP g -- input the 4nL angles of both
+ * circuits as 2u-1 (u the uniform draw of each angle), three hidden layers of
+ * `hidden` units with GELU, one output -- is trained (Adam, mean squared
+ * error on |Tr|^4 divided by its training mean) on n_train exactly contracted
+ * pairs, then
+ *     F^(2) = mean over m_surrogate pairs of g + mean over n_correct pairs of (|Tr|^4 - g),
+ * the three pair ranges consecutive from `first` and disjoint, so the
+ * estimate is unbiased for any g; stderr_ = sqrt(Var g / M + Var(f - g) / N).
+ * The plain estimate on the correction pairs is returned beside it.  Exact
+ * contractions use FP_PREC_FP32 (with the FP64 recontraction policy). */
+typedef struct {
+    int32_t hidden;           /* hidden width (<= 1024; 0: 256) */
+    int32_t epochs;           /* training epochs (0: 20) */
+    int32_t batch;            /* minibatch size (0: 512) */
+    int32_t reserved;
+    double lr;                /* Adam learning rate (0: 1e-3) */
+    uint64_t first;           /* first pair of the training range */
+    uint64_t n_train;         /* exactly contracted training pairs (>= batch) */
+    uint64_t n_correct;       /* exactly contracted correction pairs (>= 2) */
+    uint64_t m_surrogate;     /* surrogate-only pairs (>= 2) */
+} fp_cv_config;
+
+typedef struct {
+    double F2, stderr_;               /* control-variate estimate and its standard error */
+    double F2_plain, stderr_plain;    /* plain estimate on the correction pairs */
+    double var_f, var_f_minus_g, var_g;   /* per-pair variances */
+    double target_scale;              /* training mean of |Tr|^4 (g's unit) */
+    double train_loss;                /* last epoch's mean squared error (scaled units) */
+    double gpu_seconds_exact;         /* device time of the exact contractions */
+    double gpu_seconds_train;         /* device time of feature generation and training */
+    double gpu_seconds_surrogate;     /* device time of correction and surrogate evaluation */
+} fp_cv_result;
+
+fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config *cfg, fp_cv_result *res);
+
 /* Allocation-free brickwork traces (the paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they need
  * traces -- code running while a stream is captured into a CUDA graph, where

@@ -27,7 +27,7 @@ STATUS = {0: "FP_OK", -1: "FP_ERR_ARG", -2: "FP_ERR_CUDA", -3: "FP_ERR_OOM", -4:
 
 EXPORTED = ["fp_ensemble_create", "fp_ensemble_destroy", "fp_groups", "fp_pair_groups", "fp_export_gates",
             "fp_trace_batch", "fp_reduce_moments", "fp_frame_potential", "fp_kernel_stats_get",
-            "fp_trace_brick_static", "fp_last_error"]
+            "fp_trace_brick_static", "fp_cv_frame_potential", "fp_last_error"]
 
 
 class FpError(RuntimeError):
@@ -52,6 +52,18 @@ class RunStats(ctypes.Structure):
 class KernelStats(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8), ("work", ctypes.c_double * 8),
                 ("pairs", ctypes.c_uint64), ("graph_replays", ctypes.c_uint64)]
+
+
+class CvConfig(ctypes.Structure):
+    _fields_ = [("hidden", ctypes.c_int32), ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("lr", ctypes.c_double), ("first", ctypes.c_uint64),
+                ("n_train", ctypes.c_uint64), ("n_correct", ctypes.c_uint64), ("m_surrogate", ctypes.c_uint64)]
+
+
+class CvResult(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("F2", "stderr_", "F2_plain", "stderr_plain", "var_f", "var_f_minus_g",
+                                               "var_g", "target_scale", "train_loss", "gpu_seconds_exact",
+                                               "gpu_seconds_train", "gpu_seconds_surrogate")]
 
 
 class GateRec(ctypes.Structure):
@@ -83,6 +95,7 @@ def load(path: str = LIB_PATH):
     L.fp_kernel_stats_get.argtypes = [vp, P(KernelStats), ctypes.c_int32]
     L.fp_trace_brick_static.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
                                         ctypes.c_uint64, ctypes.c_int32, vp, vp, vp]
+    L.fp_cv_frame_potential.argtypes = [vp, P(CvConfig), P(CvResult)]
     L.fp_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name not in ("fp_ensemble_destroy", "fp_last_error"):
@@ -205,6 +218,13 @@ class Ensemble:
         st = KernelStats()
         _check(load().fp_kernel_stats_get(self._h, ctypes.byref(st), int(bool(reset))))
         return st
+
+    def cv_frame_potential(self, first, n_train, n_correct, m_surrogate, hidden=256, epochs=20, batch=512, lr=1e-3):
+        """Control-variate F^(2) of a single-depth HEA ensemble (see fp_cv_frame_potential)."""
+        cfg = CvConfig(hidden, epochs, batch, 0, lr, first, n_train, n_correct, m_surrogate)
+        res = CvResult()
+        _check(load().fp_cv_frame_potential(self._h, ctypes.byref(cfg), ctypes.byref(res)))
+        return res
 
     def frame_potential(self, first, max_pairs, k_max, target_rel_stderr=0.0, prec=PREC_FP64):
         import numpy as np

@@ -682,6 +682,22 @@ fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec,
     return FP_OK;
 }
 
+}  // namespace
+
+namespace fpk {
+fp_status api_fail(fp_status s, const char *msg) { return fail(s, "%s", msg); }
+fp_ensemble_desc ens_desc(const fp_ensemble *E) { return E->d; }
+cudaStream_t ens_stream(const fp_ensemble *E) { return E->st; }
+fp_status cv_trace(fp_ensemble *E, uint64_t first, uint64_t count, double **tr_dev, float *gpu_ms) {
+    fp_status s = trace_device(E, first, count, FP_PREC_FP32, gpu_ms, nullptr, nullptr);
+    if (s != FP_OK) return s;
+    *tr_dev = E->d_tr.as<double>();
+    return FP_OK;
+}
+}  // namespace fpk
+
+namespace {
+
 fp_status copy_out(fp_ensemble *E, void *dst, const void *src, size_t bytes) {
     if (!dst) return FP_OK;
     cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

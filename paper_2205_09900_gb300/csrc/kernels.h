@@ -47,5 +47,12 @@ cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const Bric
 size_t brick_smem_bytes(const BrickDev &d, bool fp32, bool *both);
 // Set the thread-local message returned by fp_last_error().
 void set_last_error(const char *msg);
+// Internal access for the control-variate driver (cv.cu).
+fp_status api_fail(fp_status s, const char *msg);
+fp_ensemble_desc ens_desc(const fp_ensemble *E);
+cudaStream_t ens_stream(const fp_ensemble *E);
+// FP32-policy traces of pairs [first, first+count) into the ensemble's device
+// array (*tr_dev, 2*count doubles), device milliseconds into *gpu_ms.
+fp_status cv_trace(fp_ensemble *E, uint64_t first, uint64_t count, double **tr_dev, float *gpu_ms);
 
 }  // namespace fpk

@@ -236,6 +236,19 @@ def test_frame_potential_n50_matches_weingarten(fp, l):
     assert abs(F[0, 1] - exact) < 5 * se[0, 1], (F[0, 1], exact, se[0, 1])
 
 
+def test_control_variate_is_unbiased(fp):
+    # HEA n = 50, L = 4: the control-variate F^(2) and the plain estimate on its
+    # correction pairs agree with an independent plain estimate on other pairs
+    ens = fp.Ensemble(2, 50, 4, 4, seed=77)
+    r = ens.cv_frame_potential(0, 20000, 20000, 400000, epochs=6)
+    F, se, st = ens.frame_potential(10_000_000, 400000, 2, 0.0, fp.PREC_FP32)
+    ref, ref_se = F[0, 1], se[0, 1]
+    assert r.var_f > 0 and r.var_f_minus_g > 0 and r.stderr_ > 0
+    assert abs(r.F2 - ref) < 5 * math.sqrt(r.stderr_ ** 2 + ref_se ** 2), (r.F2, r.stderr_, ref, ref_se)
+    assert abs(r.F2_plain - ref) < 5 * math.sqrt(r.stderr_plain ** 2 + ref_se ** 2)
+    assert math.isfinite(r.train_loss)
+
+
 def test_frame_potential_single_haar_gate(fp):
     ens, _ = make(fp, "parallel", 2, 1, seed=37)
     F, se, st = ens.frame_potential(0, 300000, 4, 0.0, fp.PREC_FP64)
