@@ -198,13 +198,20 @@ def control_variate_report(fp, n_train=100_000, n_correct=10_000, m_surrogate=10
         ens.close()
         cv_s = r.gpu_seconds_exact + r.gpu_seconds_train + r.gpu_seconds_surrogate
         plain_pairs = r.var_f / r.stderr_ ** 2
+        # MLP work of the surrogate phase (correction + surrogate evaluations), algorithmic FLOPs
+        D, H = 4 * 50 * L, 256
+        mlp_flop = 2.0 * (D * H + 2 * H * H + H) * (n_correct + m_surrogate)
         out[str(L)] = {"F2_cv": r.F2, "stderr_cv": r.stderr_, "F2_plain_on_corrections": r.F2_plain,
                        "stderr_plain_on_corrections": r.stderr_plain,
                        "variance_reduction": r.var_f / r.var_f_minus_g if r.var_f_minus_g > 0 else None,
-                       "gpu_s_cv": cv_s, "gpu_s_plain_same_stderr": plain_pairs * c_pair,
+                       "gpu_s_cv": cv_s, "gpu_s_exact": r.gpu_seconds_exact, "gpu_s_train": r.gpu_seconds_train,
+                       "gpu_s_surrogate": r.gpu_seconds_surrogate,
+                       "surrogate_phase_mlp_tflops": mlp_flop / r.gpu_seconds_surrogate / 1e12,
+                       "gpu_s_plain_same_stderr": plain_pairs * c_pair,
                        "train_loss": r.train_loss}
     return {"config": f"HEA n=50, L=4..6, {n_train} training pairs, {m_surrogate} surrogate evaluations, "
-                      f"{n_correct} exact corrections; MLP 4nL-256-256-256-1 GELU, Adam",
+                      f"{n_correct} exact corrections; MLP 4nL-256-256-256-1 GELU, Adam; hidden layers "
+                      f"as BF16 tcgen05 GEMMs with FP32 accumulation",
             "by_depth": out}
 
 

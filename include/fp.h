@@ -272,6 +272,28 @@ fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config *cfg, fp_cv
 fp_status fp_trace_brick_static(int32_t n, int32_t l, uint64_t seed, uint64_t first, uint64_t count,
                                 int32_t prec, double *tr, double *kappa, void *cuda_stream);
 
+/* The dense layer of the control-variate MLP on the tensor cores (tcgen05,
+ * BF16 operands, FP32 accumulation); the training and surrogate passes of
+ * fp_cv_frame_potential run on the same kernel.  The paper has no control
+ * variate: this is the MLP that predicts |Tr(U^dagger V)|^4 (Sec. "Frame
+ * potential" defines F^(2) = E|Tr|^4).
+ *   C[M x N] = A[M x K] . Bt[N x K]^T + bias,  then by `mode`:
+ *     0: C as is;  1: GELU(C) (exact erf form), the pre-activation written to
+ *     Z if Z is non-null;  2: C * GELU'(Z) elementwise (Z is read: the
+ *     backward pass through a GELU layer).
+ *   A       [M x K] BF16 row-major, leading dimension lda (>= K, multiple of 8);
+ *   Bt      [N x K] BF16 row-major (the right factor transposed), ldb likewise;
+ *   bias    [N] FP32 or NULL;  Z [M x N] FP32 row-major (leading dimension N);
+ *   C       [M x N] FP32 row-major, C_bf16 [M x N] BF16 row-major and
+ *   Ct_bf16 [N x M] BF16 (C transposed): any non-empty subset, others NULL.
+ * All pointers are device memory owned by the caller, 16-byte aligned (C_bf16
+ * 8-byte).  Needs N % 16 == 0 and K % 8 == 0 (FP_ERR_ARG otherwise); M may be
+ * anything >= 0.  Ordered on cuda_stream; the call waits for the result and
+ * returns FP_ERR_TIMEOUT if a bounded device wait ran out. */
+fp_status fp_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *A, int32_t lda, const void *Bt, int32_t ldb,
+                       const float *bias, int32_t mode, float *Z, float *C, void *C_bf16, void *Ct_bf16,
+                       void *cuda_stream);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char *fp_last_error(void);
 

@@ -27,7 +27,7 @@ STATUS = {0: "FP_OK", -1: "FP_ERR_ARG", -2: "FP_ERR_CUDA", -3: "FP_ERR_OOM", -4:
 
 EXPORTED = ["fp_ensemble_create", "fp_ensemble_destroy", "fp_groups", "fp_pair_groups", "fp_export_gates",
             "fp_trace_batch", "fp_reduce_moments", "fp_frame_potential", "fp_kernel_stats_get",
-            "fp_trace_brick_static", "fp_cv_frame_potential", "fp_last_error"]
+            "fp_trace_brick_static", "fp_cv_frame_potential", "fp_gemm_bf16", "fp_last_error"]
 
 
 class FpError(RuntimeError):
@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH):
     L.fp_trace_brick_static.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
                                         ctypes.c_uint64, ctypes.c_int32, vp, vp, vp]
     L.fp_cv_frame_potential.argtypes = [vp, P(CvConfig), P(CvResult)]
+    i32 = ctypes.c_int32
+    L.fp_gemm_bf16.argtypes = [i32, i32, i32, vp, i32, vp, i32, vp, i32, vp, vp, vp, vp, vp]
     L.fp_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name not in ("fp_ensemble_destroy", "fp_last_error"):
@@ -126,6 +128,20 @@ def trace_brick_static(n, l, seed, first, count, prec, tr, kappa=None, stream=No
     st = None if stream is None else ctypes.c_void_p(stream)
     _check(load().fp_trace_brick_static(n, l, seed, first, count, prec, _ptr(tr), _ptr(kappa), st))
     return tr, kappa
+
+
+def gemm_bf16(A, Bt, bias=None, mode=0, Z=None, C=None, C_bf16=None, Ct_bf16=None, stream=None):
+    """The control-variate MLP's dense layer on the tensor cores (fp_gemm_bf16):
+    C = A . Bt^T + bias, then mode 0 (as is), 1 (GELU; pre-activation to Z) or
+    2 (times GELU'(Z)).  A [M x K] and Bt [N x K] are bfloat16 CUDA tensors
+    (row-major, leading dimensions from their strides); bias [N], Z [M x N], C
+    [M x N] float32, C_bf16 [M x N] and Ct_bf16 [N x M] bfloat16 CUDA tensors
+    (contiguous) owned by the caller.  Waits for the result."""
+    M, K = A.shape
+    N = Bt.shape[0]
+    st = None if stream is None else ctypes.c_void_p(stream)
+    _check(load().fp_gemm_bf16(M, N, K, _ptr(A), A.stride(0), _ptr(Bt), Bt.stride(0), _ptr(bias), mode, _ptr(Z),
+                               _ptr(C), _ptr(C_bf16), _ptr(Ct_bf16), st))
 
 
 class Ensemble:

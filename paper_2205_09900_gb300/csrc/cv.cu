@@ -9,37 +9,46 @@
 // the correction pairs is reported beside it (it judges the variance
 // reduction).  The paper has no control variate; F^(2) itself is the paper's
 // (Sec. "Frame potential", Sec. "Algorithm description").
+//
+// Precision: the three hidden layers (forward, and both backward products)
+// run as BF16 GEMMs with FP32 accumulation on the tensor cores (tc_gemm.cu);
+// the weights are kept in FP32 for Adam and cast to BF16 copies after every
+// step; the 1-wide output layer, the loss and the estimator sums are FP32 /
+// FP64 SIMT kernels.  The steps of one training epoch are captured once as a
+// CUDA graph and replayed; the data are reshuffled (a gather on the device)
+// between epochs.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <numeric>
 #include <random>
 #include <vector>
 
 #include "fp.h"
 #include "kernels.h"
 
-
-
 namespace {
 
+using bf16 = __nv_bfloat16;
 using fpk::U64x4;
 using fpk::philox;
 
-// features: u in [0,1) of every angle of both circuits, mapped to 2u - 1;
-// index ((w * L + t) * n + q) * 2 + a  (a = 0: theta, 1: phi)
-__global__ void features_kernel(uint64_t seed, uint64_t first, int count, int n, int L, float *X) {
-    const int D = 4 * n * L;
+// features: u in [0,1) of every angle of both circuits, mapped to 2u - 1, in
+// column ((w * L + t) * n + q) * 2 + a  (a = 0: theta, 1: phi) of the row-major
+// [count x ldx] BF16 matrix X (columns >= 4nL untouched)
+__global__ void features_kernel(uint64_t seed, uint64_t first, int count, int n, int L, bf16 *X, int ldx) {
     const long long total = (long long)count * (2 * L * n);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         const int p = (int)(i / (2 * L * n));
         const int r = (int)(i % (2 * L * n));
         const int w = r / (L * n), t = (r / n) % L, q = r % n;
         U64x4 x = philox(seed, (uint64_t)t, (uint64_t)q, first + p, (uint64_t)w);
-        float *o = X + (size_t)p * D + (size_t)((w * L + t) * n + q) * 2;
-        o[0] = 2.0f * (float)((double)(x.x[0] >> 11) * 0x1.0p-53) - 1.0f;
-        o[1] = 2.0f * (float)((double)(x.x[1] >> 11) * 0x1.0p-53) - 1.0f;
+        const int c = ((w * L + t) * n + q) * 2;
+        X[(size_t)p * ldx + c] = __float2bfloat16(2.0f * (float)((double)(x.x[0] >> 11) * 0x1.0p-53) - 1.0f);
+        X[(size_t)p * ldx + c + 1] = __float2bfloat16(2.0f * (float)((double)(x.x[1] >> 11) * 0x1.0p-53) - 1.0f);
     }
 }
 
@@ -51,94 +60,161 @@ __global__ void abs4_kernel(const double *tr, int count, double scale, float *y,
     if (y) y[i] = (float)(a2 * a2 * scale);
 }
 
-// C[M x N] = A[M x K] B[K x N] (+ bias) with general strides; optional GELU.
-// A(i,k) = A[i*sar + k*sac], B(k,j) = B[k*sbr + j*sbc].  Z (pre-activation) is
-// stored when non-null.  accumulate: C += product.
-constexpr int TBM = 64, TBN = 64, TBK = 16;
-__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const float *__restrict__ A, long long sar,
-                                                   long long sac, const float *__restrict__ B, long long sbr,
-                                                   long long sbc, float *__restrict__ C, int ldc,
-                                                   const float *__restrict__ bias, int gelu, float *__restrict__ Z,
-                                                   int accumulate) {
-    __shared__ float As[TBK][TBM + 1], Bs[TBK][TBN + 1];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const int i0 = blockIdx.y * TBM, j0 = blockIdx.x * TBN;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += TBK) {
-        for (int e = threadIdx.x; e < TBK * TBM; e += 256) {
-            int kk = e / TBM, ii = e % TBM;
-            int gi = i0 + ii, gk = k0 + kk;
-            As[kk][ii] = (gi < M && gk < K) ? A[gi * sar + gk * sac] : 0.f;
-        }
-        for (int e = threadIdx.x; e < TBK * TBN; e += 256) {
-            int kk = e / TBN, jj = e % TBN;
-            int gj = j0 + jj, gk = k0 + kk;
-            Bs[kk][jj] = (gj < N && gk < K) ? B[gk * sbr + gj * sbc] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < TBK; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            int gi = i0 + ty * 4 + r, gj = j0 + tx * 4 + c;
-            if (gi >= M || gj >= N) continue;
-            float v = acc[r][c] + (bias ? bias[gj] : 0.f);
-            if (accumulate) v += C[(size_t)gi * ldc + gj];
-            if (Z) Z[(size_t)gi * ldc + gj] = v;
-            if (gelu) v = 0.5f * v * (1.0f + erff(v * 0.70710678f));
-            C[(size_t)gi * ldc + gj] = v;
-        }
-}
-
-// dZ = dA * gelu'(Z)
-__global__ void gelu_back_kernel(long long n, const float *Z, const float *dA, float *dZ) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float z = Z[i];
-        float d = 0.5f * (1.0f + erff(z * 0.70710678f)) + z * 0.39894228f * expf(-0.5f * z * z);
-        dZ[i] = dA[i] * d;
+// rows of a [rows x ld] BF16 matrix gathered by perm (16-byte chunks), and the
+// matching targets
+__global__ void gather_rows_kernel(int rows, int ld, const int *perm, const bf16 *src, bf16 *dst, const float *y,
+                                   float *ye) {
+    const int cpr = ld / 8;
+    const long long total = (long long)rows * cpr;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / cpr), c = (int)(i % cpr);
+        const int s = perm[r];
+        ((uint4 *)(dst + (size_t)r * ld))[c] = ((const uint4 *)(src + (size_t)s * ld))[c];
+        if (c == 0) ye[r] = y[s];
     }
 }
 
-// dY = 2 (Y - y) / B  for a [B x 1] output
-__global__ void mse_grad_kernel(int B, const float *Y, const float *y, float *dY, double *loss) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= B) return;
-    float e = Y[i] - y[i];
-    dY[i] = 2.0f * e / (float)B;
-    atomicAdd(loss, (double)e * (double)e / (double)B);
+// dst[c * ldd + r] = src[r * lds + c] for r < rows, c < cols; 32 x 32 tiles,
+// blockIdx.x over row tiles, blockIdx.y over column tiles, 32 x 8 threads
+__global__ void transpose_bf16_kernel(int rows, int cols, const bf16 *src, int lds, bf16 *dst, int ldd) {
+    __shared__ bf16 t[32][33];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) t[k][threadIdx.x] = src[(size_t)r * lds + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) dst[(size_t)c * ldd + r] = t[threadIdx.x][k];
+    }
 }
 
-// db[j] = sum_i dZ[i, j]
-__global__ void colsum_kernel(int B, int N, const float *dZ, float *db) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
+// output layer (H -> 1): out[i] = A[i] . w + b, one warp per row.  With
+// targets y: dY[i] = 2 (out - y) / rows and the loss accumulates; the first
+// thread also counts the step (Adam's bias correction reads the counter).
+__global__ void out_kernel(int rows, int H, const bf16 *__restrict__ A, const float *__restrict__ w,
+                           const float *__restrict__ b, const float *__restrict__ y, float *__restrict__ out,
+                           float *__restrict__ dY, double *loss, int *step) {
+    const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (step && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(step, 1);
+    if (warp >= rows) return;
+    const bf16 *a = A + (size_t)warp * H;
     float s = 0.f;
-    for (int i = 0; i < B; ++i) s += dZ[(size_t)i * N + j];
-    db[j] = s;
+    for (int k = 2 * lane; k < H; k += 64) {
+        const float2 v = __bfloat1622float2(*(const __nv_bfloat162 *)(a + k));
+        s = fmaf(v.x, w[k], fmaf(v.y, w[k + 1], s));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const float v = s + b[0];
+        if (out) out[warp] = v;
+        if (y) {
+            const float e = v - y[warp];
+            dY[warp] = 2.0f * e / (float)rows;
+            atomicAdd(loss, (double)e * (double)e / (double)rows);
+        }
+    }
 }
 
+// output-layer gradients: dW[k] = sum_i AT[k][i] dY[i] (k < H), db = sum_i dY[i]
+// (block H); one block of 128 threads per k
+__global__ void out_grad_kernel(int B, int H, const bf16 *__restrict__ AT, const float *__restrict__ dY,
+                                float *__restrict__ dW, float *__restrict__ db) {
+    __shared__ float sh[4];
+    const int k = blockIdx.x;
+    float s = 0.f;
+    for (int i = threadIdx.x; i < B; i += blockDim.x)
+        s += (k < H ? __bfloat162float(AT[(size_t)k * B + i]) : 1.0f) * dY[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const float t = sh[0] + sh[1] + sh[2] + sh[3];
+        if (k < H) dW[k] = t; else db[0] = t;
+    }
+}
+
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678f)) + z * 0.39894228f * expf(-0.5f * z * z);
+}
+
+// dZ[i][k] = dY[i] w[k] GELU'(Z[i][k]) into BF16 row-major dZ [B x H] and
+// transposed dZT [H x B]; 32 x 32 tiles as in transpose_bf16_kernel
+__global__ void dz_out_kernel(int B, int H, const float *__restrict__ dY, const float *__restrict__ w,
+                              const float *__restrict__ Z, bf16 *__restrict__ dZ, bf16 *__restrict__ dZT) {
+    __shared__ bf16 t[32][33];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        if (r < B && c < H) {
+            const bf16 v = __float2bfloat16(dY[r] * w[c] * gelu_grad(Z[(size_t)r * H + c]));
+            dZ[(size_t)r * H + c] = v;
+            t[k][threadIdx.x] = v;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (r < B && c < H) dZT[(size_t)c * B + r] = t[threadIdx.x][k];
+    }
+}
+
+// db[k] = sum_i dZT[k][i], one warp per row k
+__global__ void rowsum_kernel(int H, int B, const bf16 *__restrict__ dZT, float *__restrict__ db) {
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (k >= H) return;
+    float s = 0.f;
+    for (int i = lane; i < B; i += 32) s += __bfloat162float(dZT[(size_t)k * B + i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) db[k] = s;
+}
+
+// BF16 copies of the hidden layers' weights: Wb[l] = W_l [fin x fout] (if
+// non-null) and Wtb[l] = W_l^T [fout x finp] (columns fin..finp-1 stay zero)
+struct WCast {
+    long long woff[3];
+    int fin[3], fout[3], finp[3];
+    bf16 *Wb[3], *Wtb[3];
+};
+
+__device__ __forceinline__ void cast_weight(const WCast &c, long long i, float w) {
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        const long long o = i - c.woff[l];
+        if (o >= 0 && o < (long long)c.fin[l] * c.fout[l]) {
+            const int k = (int)(o / c.fout[l]), j = (int)(o % c.fout[l]);
+            const bf16 v = __float2bfloat16(w);
+            if (c.Wb[l]) c.Wb[l][o] = v;
+            c.Wtb[l][(size_t)j * c.finp[l] + k] = v;
+        }
+    }
+}
+
+// Adam step (bias corrections from the device step counter), then the BF16
+// casts; update = 0 casts only (the initial weights)
 __global__ void adam_kernel(long long n, float *w, const float *g, float *m, float *v, float lr, float b1, float b2,
-                            float c1, float c2) {
+                            const int *step, int update, WCast c) {
+    float c1 = 1.f, c2 = 1.f;
+    if (update) {
+        const float t = (float)*step;
+        c1 = 1.f - powf(b1, t);
+        c2 = 1.f - powf(b2, t);
+    }
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float gi = g[i];
-        float mi = b1 * m[i] + (1.f - b1) * gi, vi = b2 * v[i] + (1.f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+        float wi = w[i];
+        if (update) {
+            const float gi = g[i];
+            const float mi = b1 * m[i] + (1.f - b1) * gi, vi = b2 * v[i] + (1.f - b2) * gi * gi;
+            m[i] = mi;
+            v[i] = vi;
+            wi -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+            w[i] = wi;
+        }
+        cast_weight(c, i, wi);
     }
 }
 
@@ -170,51 +246,69 @@ struct Buf {
     cudaError_t alloc(size_t b) { return cudaMalloc(&p, std::max<size_t>(b, 16)); }
     float *f() const { return (float *)p; }
     double *d() const { return (double *)p; }
+    bf16 *h() const { return (bf16 *)p; }
+    int *i() const { return (int *)p; }
 };
 
+size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
 struct Mlp {
-    int D, H;
-    // layers: 0: D->H, 1: H->H, 2: H->H, 3: H->1
+    int D, Dp, H;
+    // layers: 0: D->H, 1: H->H, 2: H->H, 3: H->1; FP32 master copy [fin x fout]
+    // row-major, each weight block and bias 16-byte aligned
     int fin[4], fout[4];
     size_t woff[4], boff[4], total;
+    // BF16 copies of layers 0..2: W (row-major) and W^T (inputs padded to Dp for layer 0)
+    size_t wboff[3], wtoff[3], btotal;
 };
 
 Mlp make_mlp(int D, int H) {
     Mlp m;
     m.D = D;
+    m.Dp = (int)up(D, 8);
     m.H = H;
     int in[4] = {D, H, H, H}, out[4] = {H, H, H, 1};
-    size_t o = 0;
+    size_t o = 0, ob = 0;
     for (int l = 0; l < 4; ++l) {
         m.fin[l] = in[l];
         m.fout[l] = out[l];
         m.woff[l] = o;
-        o += (size_t)in[l] * out[l];
+        o += up((size_t)in[l] * out[l], 4);
         m.boff[l] = o;
-        o += out[l];
+        o += up(out[l], 4);
+        if (l < 3) {
+            m.wboff[l] = ob;
+            ob += up((size_t)in[l] * out[l], 8);
+            m.wtoff[l] = ob;
+            ob += (size_t)out[l] * (l == 0 ? m.Dp : in[l]);
+        }
     }
     m.total = o;
+    m.btotal = ob;
     return m;
 }
 
-cudaError_t gemm(cudaStream_t st, int M, int N, int K, const float *A, long long sar, long long sac, const float *B,
-                 long long sbr, long long sbc, float *C, int ldc, const float *bias, int gelu, float *Z, int accumulate) {
-    dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM);
-    gemm_kernel<<<grid, 256, 0, st>>>(M, N, K, A, sar, sac, B, sbr, sbc, C, ldc, bias, gelu, Z, accumulate);
-    return cudaGetLastError();
-}
-
-// forward pass of a batch: acts[l] = activation after layer l (acts[-1] = X);
-// zs[l] = pre-activations (layers 0..2); out = [B x 1]
-cudaError_t forward(cudaStream_t st, const Mlp &m, const float *W, const float *X, int B, float *const *acts,
-                    float *const *zs, float *out) {
-    const float *in = X;
-    for (int l = 0; l < 4; ++l) {
-        float *dst = l < 3 ? acts[l] : out;
-        cudaError_t e = gemm(st, B, m.fout[l], m.fin[l], in, m.fin[l], 1, W + m.woff[l], m.fout[l], 1, dst, m.fout[l],
-                             W + m.boff[l], l < 3 ? 1 : 0, l < 3 && zs ? zs[l] : nullptr, 0);
+// forward through the three hidden layers: act = GELU(in W + b) in BF16,
+// optionally keeping the pre-activations Z (FP32) and transposed activations
+cudaError_t hidden_forward(cudaStream_t st, const Mlp &m, const float *W, const bf16 *Wbf, const bf16 *X, int rows,
+                           bf16 *const *act, float *const *Z, bf16 *const *actT, int *err) {
+    const bf16 *in = X;
+    int ld = m.Dp;
+    for (int l = 0; l < 3; ++l) {
+        fpk::TcGemm g{};
+        g.M = rows, g.N = m.H, g.K = l == 0 ? m.Dp : m.H;   // layer 0: zero-padded inputs
+        g.A = in, g.lda = ld;
+        g.Bt = Wbf + m.wtoff[l], g.ldb = g.K;
+        g.bias = W + m.boff[l];
+        g.mode = 1;
+        g.Z = Z ? Z[l] : nullptr, g.ldz = m.H;
+        g.Cb = act[l], g.ldcb = m.H;
+        g.Cbt = actT ? actT[l] : nullptr, g.ldct = rows;
+        g.err = err;
+        cudaError_t e = fpk::launch_tc_gemm(g, st);
         if (e != cudaSuccess) return e;
-        in = dst;
+        in = act[l];
+        ld = m.H;
     }
     return cudaSuccess;
 }
@@ -233,13 +327,50 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
     const int B = cfg->batch > 0 ? cfg->batch : 512;
     const float lr = cfg->lr > 0 ? (float)cfg->lr : 1e-3f;
     const uint64_t NT = cfg->n_train, NC = cfg->n_correct, MS = cfg->m_surrogate;
-    if (NT < (uint64_t)B || NC < 2 || MS < 2 || H > 1024)
-        return fpk::api_fail(FP_ERR_ARG, "need n_train >= batch, n_correct >= 2, m_surrogate >= 2, hidden <= 1024");
-    cudaStream_t st = fpk::ens_stream(ens);
+    if (NT < (uint64_t)B || NC < 2 || MS < 2 || H > 1024 || H % 16 != 0 || B % 8 != 0 || NT > (1u << 30))
+        return fpk::api_fail(FP_ERR_ARG, "need n_train >= batch, n_correct >= 2, m_surrogate >= 2, hidden a multiple "
+                                         "of 16 up to 1024, batch a multiple of 8");
+    cudaStream_t ust = fpk::ens_stream(ens);
     std::memset(res, 0, sizeof *res);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    // the work runs on a private stream (capturable), ordered after and before the caller's stream
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, ord = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    auto cleanup = [&]() {
+        if (st) {
+            if (ord && cudaEventRecord(ord, st) == cudaSuccess) cudaStreamWaitEvent(ust, ord, 0);
+            cudaStreamSynchronize(st);
+        }
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        if (st) cudaStreamDestroy(st);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (ord) cudaEventDestroy(ord);
+    };
+#define CKC(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            cleanup();                                                                             \
+            return fpk::api_fail(e_ == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA,       \
+                                 cudaGetErrorString(e_));                                          \
+        }                                                                                          \
+    } while (0)
+#define CKS(call)                                  \
+    do {                                           \
+        fp_status s_ = (call);                     \
+        if (s_ != FP_OK) { cleanup(); return s_; } \
+    } while (0)
+    CKC(cudaEventCreate(&e0));
+    CKC(cudaEventCreate(&e1));
+    CKC(cudaEventCreateWithFlags(&ord, cudaEventDisableTiming));
+    CKC(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    auto join_user = [&]() -> cudaError_t {   // st waits for everything queued on the caller's stream
+        cudaError_t e = cudaEventRecord(ord, ust);
+        return e == cudaSuccess ? cudaStreamWaitEvent(st, ord, 0) : e;
+    };
     auto elapsed = [&]() {
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
@@ -247,31 +378,28 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
         cudaEventElapsedTime(&ms, e0, e1);
         return ms * 1e-3;
     };
-#define CKC(call)                                                                          \
-    do {                                                                                   \
-        cudaError_t e_ = (call);                                                           \
-        if (e_ != cudaSuccess) {                                                           \
-            cudaEventDestroy(e0);                                                          \
-            cudaEventDestroy(e1);                                                          \
-            return fpk::api_fail(e_ == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA,    \
-                            cudaGetErrorString(e_));                                       \
-        }                                                                                  \
-    } while (0)
-#define CKS(call)                                                                          \
-    do {                                                                                   \
-        fp_status s_ = (call);                                                             \
-        if (s_ != FP_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s_; }        \
-    } while (0)
+    Buf derr;
+    CKC(derr.alloc(sizeof(int)));
+    CKC(cudaMemsetAsync(derr.p, 0, sizeof(int), st));
+    auto check_err = [&]() -> fp_status {
+        int h = 0;
+        if (cudaMemcpyAsync(&h, derr.p, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return fpk::api_fail(FP_ERR_CUDA, "control variate: device error");
+        return h ? fpk::api_fail(FP_ERR_TIMEOUT, "tcgen05 GEMM: an mbarrier wait ran out") : FP_OK;
+    };
 
     const uint64_t f_train = cfg->first, f_corr = f_train + NT, f_sur = f_corr + NC;
+    Mlp m = make_mlp(D, H);
     // ---- 1. exact contractions of the training pairs -> targets
-    Buf X, y, f;
-    CKC(X.alloc(NT * D * sizeof(float)));
+    Buf X, y;
+    CKC(X.alloc(NT * m.Dp * sizeof(bf16)));
     CKC(y.alloc(NT * sizeof(float)));
     float ms_trace = 0;
     double *dtr = nullptr;
     CKS(fpk::cv_trace(ens, f_train, NT, &dtr, &ms_trace));
     res->gpu_seconds_exact += ms_trace * 1e-3;
+    CKC(join_user());
     CKC(cudaEventRecord(e0, st));
     {
         std::vector<double> h(2 * NT);
@@ -287,105 +415,176 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
     }
     abs4_kernel<<<(unsigned)((NT + 255) / 256), 256, 0, st>>>(dtr, (int)NT, 1.0 / res->target_scale, y.f(), nullptr);
     CKC(cudaGetLastError());
-    features_kernel<<<1024, 256, 0, st>>>(d.seed, f_train, (int)NT, n, L, X.f());
+    CKC(cudaMemsetAsync(X.p, 0, NT * m.Dp * sizeof(bf16), st));
+    features_kernel<<<1024, 256, 0, st>>>(d.seed, f_train, (int)NT, n, L, X.h(), m.Dp);
     CKC(cudaGetLastError());
     // ---- 2. training (Adam on the mean squared error of |Tr|^4 / mean)
-    Mlp m = make_mlp(D, H);
-    Buf W, G, Mm, Vv, acts[3], zs[3], dA, dZ, out, dY, loss;
+    Buf W, Wbf, G, Mm, Vv, Xe, XeT, ye, Z[3], act[3], actT[3], dZ[2], dZT[2], out, dY, loss, step, perm;
     CKC(W.alloc(m.total * sizeof(float)));
+    CKC(Wbf.alloc(m.btotal * sizeof(bf16)));
     CKC(G.alloc(m.total * sizeof(float)));
     CKC(Mm.alloc(m.total * sizeof(float)));
     CKC(Vv.alloc(m.total * sizeof(float)));
     CKC(cudaMemsetAsync(Mm.p, 0, m.total * sizeof(float), st));
     CKC(cudaMemsetAsync(Vv.p, 0, m.total * sizeof(float), st));
+    CKC(cudaMemsetAsync(G.p, 0, m.total * sizeof(float), st));
+    CKC(cudaMemsetAsync(Wbf.p, 0, m.btotal * sizeof(bf16), st));
+    WCast wc;
+    for (int l = 0; l < 3; ++l) {
+        wc.woff[l] = (long long)m.woff[l];
+        wc.fin[l] = m.fin[l];
+        wc.fout[l] = m.fout[l];
+        wc.finp[l] = l == 0 ? m.Dp : m.fin[l];
+        wc.Wb[l] = l == 0 ? nullptr : Wbf.h() + m.wboff[l];   // layer 0 needs no input gradient
+        wc.Wtb[l] = Wbf.h() + m.wtoff[l];
+    }
+    std::vector<float> hw(m.total, 0.f);
     {
         std::mt19937_64 rng(d.seed ^ 0x5DEECE66DULL);
-        std::vector<float> w(m.total, 0.f);
         for (int l = 0; l < 4; ++l) {
             std::normal_distribution<float> nd(0.f, std::sqrt(2.0f / (float)m.fin[l]));
-            for (size_t i = 0; i < (size_t)m.fin[l] * m.fout[l]; ++i) w[m.woff[l] + i] = nd(rng);
+            for (size_t i = 0; i < (size_t)m.fin[l] * m.fout[l]; ++i) hw[m.woff[l] + i] = nd(rng);
         }
-        CKC(cudaMemcpyAsync(W.p, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-        CKC(cudaStreamSynchronize(st));
+        CKC(cudaMemcpyAsync(W.p, hw.data(), hw.size() * sizeof(float), cudaMemcpyHostToDevice, st));
     }
-    const int HB = std::max(H, D);
+    adam_kernel<<<1024, 256, 0, st>>>((long long)m.total, W.f(), G.f(), Mm.f(), Vv.f(), lr, 0.9f, 0.999f, nullptr, 0,
+                                      wc);
+    CKC(cudaGetLastError());
+    const int nb = (int)(NT / B);
+    const size_t NE = (size_t)nb * B;   // rows used per epoch
+    CKC(Xe.alloc(NE * m.Dp * sizeof(bf16)));
+    CKC(XeT.alloc((size_t)m.D * NE * sizeof(bf16)));
+    CKC(ye.alloc(NE * sizeof(float)));
     for (int l = 0; l < 3; ++l) {
-        CKC(acts[l].alloc((size_t)B * H * sizeof(float)));
-        CKC(zs[l].alloc((size_t)B * H * sizeof(float)));
+        CKC(Z[l].alloc((size_t)B * H * sizeof(float)));
+        CKC(act[l].alloc((size_t)B * H * sizeof(bf16)));
+        CKC(actT[l].alloc((size_t)H * B * sizeof(bf16)));
     }
-    CKC(dA.alloc((size_t)B * HB * sizeof(float)));
-    CKC(dZ.alloc((size_t)B * HB * sizeof(float)));
+    for (int i = 0; i < 2; ++i) {
+        CKC(dZ[i].alloc((size_t)B * H * sizeof(bf16)));
+        CKC(dZT[i].alloc((size_t)H * B * sizeof(bf16)));
+    }
     CKC(out.alloc((size_t)B * sizeof(float)));
     CKC(dY.alloc((size_t)B * sizeof(float)));
     CKC(loss.alloc(sizeof(double)));
-    float *ap[3] = {acts[0].f(), acts[1].f(), acts[2].f()}, *zp[3] = {zs[0].f(), zs[1].f(), zs[2].f()};
-    const int nb = (int)(NT / B);
-    int step = 0;
+    CKC(step.alloc(sizeof(int)));
+    CKC(perm.alloc(NT * sizeof(int)));
+    CKC(cudaMemsetAsync(step.p, 0, sizeof(int), st));
+    bf16 *ap[3] = {act[0].h(), act[1].h(), act[2].h()}, *apT[3] = {actT[0].h(), actT[1].h(), actT[2].h()};
+    float *zp[3] = {Z[0].f(), Z[1].f(), Z[2].f()};
+    // one training step on rows [b*B, (b+1)*B) of the shuffled epoch data
+    auto train_step = [&](int b) -> cudaError_t {
+        cudaError_t e;
+        const bf16 *xb = Xe.h() + (size_t)b * B * m.Dp;
+        if ((e = hidden_forward(st, m, W.f(), Wbf.h(), xb, B, ap, zp, apT, derr.i())) != cudaSuccess) return e;
+        out_kernel<<<(B * 32 + 255) / 256, 256, 0, st>>>(B, H, ap[2], W.f() + m.woff[3], W.f() + m.boff[3],
+                                                         ye.f() + (size_t)b * B, out.f(), dY.f(), loss.d(), step.i());
+        out_grad_kernel<<<H + 1, 128, 0, st>>>(B, H, apT[2], dY.f(), G.f() + m.woff[3], G.f() + m.boff[3]);
+        dz_out_kernel<<<dim3((B + 31) / 32, (H + 31) / 32), dim3(32, 8), 0, st>>>(
+            B, H, dY.f(), W.f() + m.woff[3], zp[2], dZ[0].h(), dZT[0].h());
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        int cur = 0;
+        for (int l = 2; l >= 0; --l) {
+            // dW_l = act_{l-1}^T . dZ_l  (the batch is the contracted dimension)
+            fpk::TcGemm g{};
+            g.M = m.fin[l], g.N = H, g.K = B;
+            if (l == 0) {
+                g.A = XeT.h() + (size_t)b * B, g.lda = (int)NE;
+            } else {
+                g.A = apT[l - 1], g.lda = B;
+            }
+            g.Bt = dZT[cur].h(), g.ldb = B;
+            g.mode = 0;
+            g.Cf = G.f() + m.woff[l], g.ldcf = H;
+            g.err = derr.i();
+            if ((e = fpk::launch_tc_gemm(g, st)) != cudaSuccess) return e;
+            rowsum_kernel<<<(H * 32 + 255) / 256, 256, 0, st>>>(H, B, dZT[cur].h(), G.f() + m.boff[l]);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (l > 0) {
+                // dZ_{l-1} = (dZ_l . W_l^T) * GELU'(Z_{l-1})
+                fpk::TcGemm h{};
+                h.M = B, h.N = m.fin[l], h.K = H;
+                h.A = dZ[cur].h(), h.lda = H;
+                h.Bt = Wbf.h() + m.wboff[l], h.ldb = H;
+                h.mode = 2;
+                h.Z = zp[l - 1], h.ldz = H;
+                h.Cb = dZ[cur ^ 1].h(), h.ldcb = H;
+                h.Cbt = dZT[cur ^ 1].h(), h.ldct = B;
+                h.err = derr.i();
+                if ((e = fpk::launch_tc_gemm(h, st)) != cudaSuccess) return e;
+                cur ^= 1;
+            }
+        }
+        adam_kernel<<<1024, 256, 0, st>>>((long long)m.total, W.f(), G.f(), Mm.f(), Vv.f(), lr, 0.9f, 0.999f,
+                                          step.i(), 1, wc);
+        return cudaGetLastError();
+    };
+    std::mt19937_64 prng(d.seed ^ 0x9E3779B97F4A7C15ULL);
+    std::vector<int> hperm(NT);
     double last_loss = 0;
     for (int ep = 0; ep < epochs; ++ep) {
+        std::iota(hperm.begin(), hperm.end(), 0);
+        std::shuffle(hperm.begin(), hperm.end(), prng);
+        CKC(cudaMemcpyAsync(perm.p, hperm.data(), NT * sizeof(int), cudaMemcpyHostToDevice, st));
+        gather_rows_kernel<<<1024, 256, 0, st>>>((int)NE, m.Dp, perm.i(), X.h(), Xe.h(), y.f(), ye.f());
+        transpose_bf16_kernel<<<dim3((unsigned)((NE + 31) / 32), (m.D + 31) / 32), dim3(32, 8), 0, st>>>(
+            (int)NE, m.D, Xe.h(), m.Dp, XeT.h(), (int)NE);
+        CKC(cudaGetLastError());
         CKC(cudaMemsetAsync(loss.p, 0, sizeof(double), st));
-        const int shift = (int)((ep * 7919LL) % nb);
-        for (int bi = 0; bi < nb; ++bi) {
-            const int b = (bi + shift) % nb;
-            const float *xb = X.f() + (size_t)b * B * D;
-            const float *yb = y.f() + (size_t)b * B;
-            CKC(forward(st, m, W.f(), xb, B, ap, zp, out.f()));
-            mse_grad_kernel<<<(B + 255) / 256, 256, 0, st>>>(B, out.f(), yb, dY.f(), loss.d());
-            // layer 3 (H -> 1): dW3 = A2^T dY, db3 = sum dY, dA2 = dY W3^T
-            const float *dcur = dY.f();
-            int ncur = 1;
-            for (int l = 3; l >= 0; --l) {
-                const float *ain = l == 0 ? xb : ap[l - 1];
-                const int fin = m.fin[l], fout = m.fout[l];
-                // dW = ain^T [fin x B] . dcur [B x fout]
-                CKC(gemm(st, fin, fout, B, ain, 1, fin, dcur, ncur, 1, G.f() + m.woff[l], fout, nullptr, 0, nullptr, 0));
-                colsum_kernel<<<(fout + 127) / 128, 128, 0, st>>>(B, fout, dcur, G.f() + m.boff[l]);
-                if (l > 0) {
-                    // dA_{l-1} = dcur [B x fout] . W^T [fout x fin]
-                    CKC(gemm(st, B, fin, fout, dcur, ncur, 1, W.f() + m.woff[l], 1, fout, dA.f(), fin, nullptr, 0,
-                             nullptr, 0));
-                    // dZ_{l-1} = dA * gelu'(Z_{l-1}); dZ is read again only by the next layer
-                    gelu_back_kernel<<<1024, 256, 0, st>>>((long long)B * fin, zp[l - 1], dA.f(), dZ.f());
-                    dcur = dZ.f();
-                    ncur = fin;
-                }
+        // step 0 runs directly (it also sets the GEMM kernel's attributes);
+        // steps 1..nb-1 are captured in the first epoch and replayed after
+        CKC(train_step(0));
+        if (nb > 1) {
+            if (!gexec) {
+                CKC(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                cudaError_t ce = cudaSuccess;
+                for (int b = 1; b < nb && ce == cudaSuccess; ++b) ce = train_step(b);
+                cudaError_t ee = cudaStreamEndCapture(st, &graph);
+                CKC(ce);
+                CKC(ee);
+                CKC(cudaGraphInstantiate(&gexec, graph, 0));
             }
-            ++step;
-            const float b1 = 0.9f, b2 = 0.999f;
-            adam_kernel<<<1024, 256, 0, st>>>((long long)m.total, W.f(), G.f(), Mm.f(), Vv.f(), lr, b1, b2,
-                                              1.f - std::pow(b1, (float)step), 1.f - std::pow(b2, (float)step));
-            CKC(cudaGetLastError());
+            CKC(cudaGraphLaunch(gexec, st));
         }
+        // the host buffer holds this epoch's permutation until the copy has run
         double lh = 0;
         CKC(cudaMemcpyAsync(&lh, loss.p, sizeof(double), cudaMemcpyDeviceToHost, st));
         CKC(cudaStreamSynchronize(st));
         last_loss = lh / nb;
     }
+    CKS(check_err());
     res->train_loss = last_loss;
     res->gpu_seconds_train = elapsed();
     // ---- 3. correction pairs: exact f and the surrogate g on the same pairs
-    Buf Xc, gc, fc, sums;
+    Buf Xc, gc, fc, sums, big[3];
     const size_t chunk = 1 << 16;
-    CKC(Xc.alloc(chunk * D * sizeof(float)));
+    CKC(Xc.alloc(chunk * m.Dp * sizeof(bf16)));
+    CKC(cudaMemsetAsync(Xc.p, 0, chunk * m.Dp * sizeof(bf16), st));
     CKC(gc.alloc(chunk * sizeof(float)));
     CKC(sums.alloc(4 * sizeof(double)));
-    float *cap[3], *dummy = nullptr;
-    Buf big[3];
+    bf16 *cap[3];
     for (int l = 0; l < 3; ++l) {
-        CKC(big[l].alloc(chunk * H * sizeof(float)));
-        cap[l] = big[l].f();
+        CKC(big[l].alloc(chunk * H * sizeof(bf16)));
+        cap[l] = big[l].h();
     }
-    (void)dummy;
+    auto surrogate = [&](uint64_t f0, int cnt) -> cudaError_t {
+        features_kernel<<<1024, 256, 0, st>>>(d.seed, f0, cnt, n, L, Xc.h(), m.Dp);
+        cudaError_t e = hidden_forward(st, m, W.f(), Wbf.h(), Xc.h(), cnt, cap, nullptr, nullptr, derr.i());
+        if (e != cudaSuccess) return e;
+        out_kernel<<<(unsigned)(((size_t)cnt * 32 + 255) / 256), 256, 0, st>>>(
+            cnt, H, cap[2], W.f() + m.woff[3], W.f() + m.boff[3], nullptr, gc.f(), nullptr, nullptr, nullptr);
+        return cudaGetLastError();
+    };
     CKS(fpk::cv_trace(ens, f_corr, NC, &dtr, &ms_trace));
     res->gpu_seconds_exact += ms_trace * 1e-3;
+    CKC(join_user());
     CKC(cudaEventRecord(e0, st));
     CKC(fc.alloc(NC * sizeof(double)));
     abs4_kernel<<<(unsigned)((NC + 255) / 256), 256, 0, st>>>(dtr, (int)NC, 1.0, nullptr, fc.d());
     CKC(cudaMemsetAsync(sums.p, 0, 4 * sizeof(double), st));
     for (uint64_t c0 = 0; c0 < NC; c0 += chunk) {
         const int cnt = (int)std::min<uint64_t>(chunk, NC - c0);
-        features_kernel<<<1024, 256, 0, st>>>(d.seed, f_corr + c0, cnt, n, L, Xc.f());
-        CKC(forward(st, m, W.f(), Xc.f(), cnt, cap, nullptr, gc.f()));
+        CKC(surrogate(f_corr + c0, cnt));
         cv_sums_kernel<<<256, 256, 0, st>>>(cnt, gc.f(), res->target_scale, fc.d() + c0, sums.d());
         CKC(cudaGetLastError());
     }
@@ -399,13 +598,13 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
     CKC(cudaMemsetAsync(sums.p, 0, 4 * sizeof(double), st));
     for (uint64_t c0 = 0; c0 < MS; c0 += chunk) {
         const int cnt = (int)std::min<uint64_t>(chunk, MS - c0);
-        features_kernel<<<1024, 256, 0, st>>>(d.seed, f_sur + c0, cnt, n, L, Xc.f());
-        CKC(forward(st, m, W.f(), Xc.f(), cnt, cap, nullptr, gc.f()));
+        CKC(surrogate(f_sur + c0, cnt));
         cv_sums_kernel<<<256, 256, 0, st>>>(cnt, gc.f(), res->target_scale, nullptr, sums.d());
         CKC(cudaGetLastError());
     }
     CKC(cudaMemcpyAsync(sc, sums.p, sizeof sc, cudaMemcpyDeviceToHost, st));
     CKC(cudaStreamSynchronize(st));
+    CKS(check_err());
     const double Ms = (double)MS;
     const double mean_g = sc[0] / Ms, var_g = (sc[1] - sc[0] * sc[0] / Ms) / (Ms - 1);
     res->gpu_seconds_surrogate = elapsed();
@@ -416,8 +615,7 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
     res->var_f = var_f;
     res->var_f_minus_g = var_fg;
     res->var_g = var_g;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    cleanup();
 #undef CKC
 #undef CKS
     return FP_OK;

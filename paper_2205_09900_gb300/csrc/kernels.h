@@ -1,5 +1,6 @@
 // kernels.h -- launch wrappers of the sm_103a kernels (host-callable).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "brick.h"
@@ -54,5 +55,32 @@ cudaStream_t ens_stream(const fp_ensemble *E);
 // FP32-policy traces of pairs [first, first+count) into the ensemble's device
 // array (*tr_dev, 2*count doubles), device milliseconds into *gpu_ms.
 fp_status cv_trace(fp_ensemble *E, uint64_t first, uint64_t count, double **tr_dev, float *gpu_ms);
+
+// BF16 tensor-core GEMM (tc_gemm.cu): C[M x N] = A[M x K] . Bt[N x K]^T (+ bias),
+// FP32 accumulation, epilogue mode 0 identity / 1 GELU (pre-activation to Z if
+// set) / 2 times GELU'(Z); outputs FP32 row-major (Cf), BF16 row-major (Cb),
+// BF16 transposed (Cbt[col * ldct + row]); any subset.  err (device int, may be
+// null) is set to 1 if a bounded wait ran out.
+struct TcGemm {
+    int M, N, K;
+    const __nv_bfloat16 *A;
+    int lda;
+    const __nv_bfloat16 *Bt;
+    int ldb;
+    const float *bias;
+    int mode;
+    float *Z;
+    int ldz;
+    float *Cf;
+    int ldcf;
+    __nv_bfloat16 *Cb;
+    int ldcb;
+    __nv_bfloat16 *Cbt;
+    int ldct;
+    int *err;
+};
+const char *tc_gemm_check(const TcGemm &g);   // nullptr if the arguments are valid
+cudaError_t launch_tc_gemm(const TcGemm &g, cudaStream_t st);
+size_t tc_gemm_smem_bytes();
 
 }  // namespace fpk

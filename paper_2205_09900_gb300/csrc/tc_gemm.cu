@@ -1,0 +1,305 @@
+// tc_gemm.cu -- BF16 GEMM on the sm_103a tensor cores (tcgen05) with fused
+// epilogues: the dense layers (forward and backward) of the control-variate MLP.
+//
+//   C[M x N] = A[M x K] . Bt[N x K]^T (+ bias),  BF16 operands, FP32 accumulate
+//
+// One CTA (128 threads) owns a 128 x NT output tile (NT <= 256 columns) whose
+// FP32 accumulator lives in tensor memory (TMEM: NT columns x 128 lanes).  The
+// K loop runs in stages of 64 through two shared-memory buffers: the threads
+// copy the A and B tiles of stage k+1 into the K-major "core matrix" layout
+// (8 rows x 16 bytes per core matrix, no swizzle) while the tensor core works
+// on stage k; one elected thread issues four tcgen05.mma (K = 16 each) per
+// stage and a tcgen05.commit to that buffer's mbarrier, which the threads wait
+// on before they overwrite the buffer.  The epilogue reads the accumulator back
+// with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. tile rows
+// 32w..32w+31), adds the bias and applies one of
+//   mode 0: identity,
+//   mode 1: GELU (the pre-activation optionally kept in Z),
+//   mode 2: multiply by GELU'(Z) (Z read: the backward pass of a GELU layer),
+// then stores FP32 row-major, BF16 row-major and/or BF16 transposed results.
+// Every wait is bounded: on timeout the kernel raises the error flag, still
+// releases its TMEM, and returns; launches that find the flag raised return at
+// once.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fp.h"
+#include "kernels.h"
+
+namespace fpk {
+namespace {
+
+constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 128, TC_MAXN = 256, TC_STAGES = 2;
+constexpr long long TC_WAIT_LIMIT = 1LL << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor (tcgen05): start address, leading-dimension
+// byte offset (between core matrices adjacent in K), stride-dimension byte
+// offset (between core matrices adjacent in M/N), all >> 4; version 1; no swizzle
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
+// (bits 7-9 = 1) and B (bits 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__device__ __forceinline__ uint32_t make_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+    for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ float gelu_f(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678f)) + z * 0.39894228f * expf(-0.5f * z * z);
+}
+
+// copy rows [r0, r0 + rows) x K-columns [k0, k0 + 64) of a row-major BF16
+// matrix (leading dimension ld; rows < rmax and columns < K valid, the rest
+// zero) into the core-matrix layout: 16-byte chunk (r, kg) goes to byte
+// ((r/8)*8 + kg)*128 + (r%8)*16.  In each warp, lanes 0-7 take 8 consecutive
+// rows of one chunk column (a conflict-free 128-byte shared store) and lanes
+// 8i+j the next chunk columns (64 contiguous bytes of a row per global load).
+__device__ __forceinline__ void load_tile(unsigned char *dst, const __nv_bfloat16 *__restrict__ src, int ld, int r0,
+                                          int rows, int rmax, int k0, int K, int tid) {
+    for (int idx = tid; idx < rows * 8; idx += TC_THREADS) {
+        const int t = idx & 31, q = idx >> 5;
+        const int r = (q >> 1) * 8 + (t & 7), kg = (q & 1) * 4 + (t >> 3);
+        uint4 v = make_uint4(0, 0, 0, 0);
+        const int k = k0 + kg * 8;
+        if (r0 + r < rmax && k < K) v = *(const uint4 *)(src + (size_t)(r0 + r) * ld + k);
+        *(uint4 *)(dst + (((r >> 3) * 8 + kg) * 128 + (r & 7) * 16)) = v;
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcGemm g) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[TC_STAGES];
+    __shared__ uint32_t taddr_sh;
+    __shared__ int abort_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // an earlier launch timed out: do nothing (one read, so that the whole CTA agrees)
+    if (tid == 0) abort_sh = g.err ? *(volatile const int *)g.err : 0;
+    __syncthreads();
+    if (abort_sh) return;
+    const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_MAXN;
+    const int NT = min(TC_MAXN, g.N - n0);   // a multiple of 16
+    const uint32_t ncols = NT <= 32 ? 32u : (NT <= 64 ? 64u : (NT <= 128 ? 128u : 256u));
+    const int stage_bytes = (TC_BM + TC_MAXN) * TC_BK * 2;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_sh)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t taddr = taddr_sh;
+    const uint32_t idesc = make_idesc(TC_BM, NT);
+    const int nk = (g.K + TC_BK - 1) / TC_BK;
+    auto load_stage = [&](int s, int kt) {
+        unsigned char *sa = smem + s * stage_bytes;
+        load_tile(sa, g.A, g.lda, m0, TC_BM, g.M, kt * TC_BK, g.K, tid);
+        load_tile(sa + TC_BM * TC_BK * 2, g.Bt, g.ldb, n0, NT, g.N, kt * TC_BK, g.K, tid);
+    };
+    load_stage(0, 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    uint32_t ph[TC_STAGES] = {0, 0};
+    for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt & 1;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t sa = smem_u32(smem + s * stage_bytes), sb = sa + TC_BM * TC_BK * 2;
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                const uint64_t ad = make_desc(sa + kk * 256, 128, 1024);
+                const uint64_t bd = make_desc(sb + kk * 256, 128, 1024);
+                const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.u32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mbar[s]))
+                         : "memory");
+        }
+        if (kt + 1 < nk) {
+            bool ok = true;
+            if (kt >= 1) {   // the other buffer is free once stage kt-1's MMAs are done
+                ok = mbar_wait(smem_u32(&mbar[s ^ 1]), ph[s ^ 1]);
+                ph[s ^ 1] ^= 1u;
+            }
+            if (ok) {
+                load_stage(s ^ 1, kt + 1);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            } else {
+                abort_sh = 1;
+            }
+        }
+        __syncthreads();
+        if (abort_sh) break;
+    }
+    if (!abort_sh) {   // the last one or two commits have not been waited on
+        bool ok = true;
+        if (nk >= 2) ok = mbar_wait(smem_u32(&mbar[(nk - 2) & 1]), ph[(nk - 2) & 1]);
+        if (ok) ok = mbar_wait(smem_u32(&mbar[(nk - 1) & 1]), ph[(nk - 1) & 1]);
+        if (!ok) abort_sh = 1;
+    }
+    __syncthreads();
+    if (abort_sh) {
+        if (tid == 0 && g.err) atomicExch(g.err, 1);
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int row = m0 + warp * 32 + lane;
+        const bool rv = row < g.M;
+        for (int c0 = 0; c0 < NT; c0 += 32) {
+            uint32_t r[32];
+            const uint32_t ta = taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (!rv) continue;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (c0 + 4 * q >= NT) break;   // NT is a multiple of 16: groups of 4 are whole
+                const int col = n0 + c0 + 4 * q;
+                float v[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[e] = __uint_as_float(r[4 * q + e]);
+                if (g.bias) {
+                    const float4 b = *(const float4 *)(g.bias + col);
+                    v[0] += b.x, v[1] += b.y, v[2] += b.z, v[3] += b.w;
+                }
+                if (g.mode == 1) {
+                    if (g.Z) *(float4 *)(g.Z + (size_t)row * g.ldz + col) = make_float4(v[0], v[1], v[2], v[3]);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v[e] = gelu_f(v[e]);
+                } else if (g.mode == 2) {
+                    const float4 z = *(const float4 *)(g.Z + (size_t)row * g.ldz + col);
+                    v[0] *= gelu_grad(z.x), v[1] *= gelu_grad(z.y), v[2] *= gelu_grad(z.z), v[3] *= gelu_grad(z.w);
+                }
+                if (g.Cf) *(float4 *)(g.Cf + (size_t)row * g.ldcf + col) = make_float4(v[0], v[1], v[2], v[3]);
+                if (g.Cb) {
+                    __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
+                    uint2 u;
+                    u.x = *(uint32_t *)&p0;
+                    u.y = *(uint32_t *)&p1;
+                    *(uint2 *)(g.Cb + (size_t)row * g.ldcb + col) = u;
+                }
+                if (g.Cbt) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) g.Cbt[(size_t)(col + e) * g.ldct + row] = __float2bfloat16(v[e]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+}  // namespace
+
+size_t tc_gemm_smem_bytes() { return (size_t)TC_STAGES * (TC_BM + TC_MAXN) * TC_BK * 2; }
+
+const char *tc_gemm_check(const TcGemm &g) {
+    if (g.M < 0 || g.N <= 0 || g.N % 16 != 0 || g.K <= 0 || g.K % 8 != 0) return "need N % 16 == 0 and K % 8 == 0";
+    if (g.M == 0) return nullptr;   // nothing is read or written
+    if (!g.A || !g.Bt || g.lda < g.K || g.ldb < g.K || g.lda % 8 || g.ldb % 8 || !aligned(g.A, 16) ||
+        !aligned(g.Bt, 16))
+        return "A and Bt need 16-byte alignment and leading dimensions >= K that are multiples of 8";
+    if (!g.Cf && !g.Cb && !g.Cbt) return "no output";
+    if (g.mode < 0 || g.mode > 2 || (g.mode == 2 && !g.Z)) return "mode must be 0, 1 or 2 (mode 2 needs Z)";
+    if (g.Z && (g.ldz < g.N || g.ldz % 4 || !aligned(g.Z, 16)))
+        return "Z needs a leading dimension >= N that is a multiple of 4, and 16-byte alignment";
+    if (g.bias && !aligned(g.bias, 16)) return "bias needs 16-byte alignment";
+    if (g.Cf && (g.ldcf < g.N || g.ldcf % 4 || !aligned(g.Cf, 16)))
+        return "C needs a leading dimension >= N that is a multiple of 4, and 16-byte alignment";
+    if (g.Cb && (g.ldcb < g.N || g.ldcb % 4 || !aligned(g.Cb, 8)))
+        return "C_bf16 needs a leading dimension >= N that is a multiple of 4, and 8-byte alignment";
+    if (g.Cbt && (g.ldct < g.M || !aligned(g.Cbt, 2))) return "Ct_bf16 needs a leading dimension >= M";
+    return nullptr;
+}
+
+cudaError_t launch_tc_gemm(const TcGemm &g, cudaStream_t st) {
+    if (g.M == 0) return cudaSuccess;
+    if (tc_gemm_check(g)) return cudaErrorInvalidValue;
+    const size_t smem = tc_gemm_smem_bytes();
+    // the attribute is set outside stream capture (a launch being captured
+    // follows a direct launch on the same device, which has set it)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs == cudaStreamCaptureStatusNone) {
+        e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((g.M + TC_BM - 1) / TC_BM, (g.N + TC_MAXN - 1) / TC_MAXN);
+    tc_gemm_kernel<<<grid, TC_THREADS, smem, st>>>(g);
+    return cudaGetLastError();
+}
+
+}  // namespace fpk
+
+extern "C" fp_status fp_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *A, int32_t lda, const void *Bt,
+                                  int32_t ldb, const float *bias, int32_t mode, float *Z, float *C, void *C_bf16,
+                                  void *Ct_bf16, void *cuda_stream) {
+    fpk::TcGemm g{};
+    g.M = M, g.N = N, g.K = K;
+    g.A = (const __nv_bfloat16 *)A, g.lda = lda;
+    g.Bt = (const __nv_bfloat16 *)Bt, g.ldb = ldb;
+    g.bias = bias, g.mode = mode;
+    g.Z = Z, g.ldz = N;
+    g.Cf = C, g.ldcf = N;
+    g.Cb = (__nv_bfloat16 *)C_bf16, g.ldcb = N;
+    g.Cbt = (__nv_bfloat16 *)Ct_bf16, g.ldct = M;
+    if (const char *why = fpk::tc_gemm_check(g)) return fpk::api_fail(FP_ERR_ARG, why);
+    if (M == 0) return FP_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int *derr = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&derr, sizeof(int), st);
+    if (e != cudaSuccess) return fpk::api_fail(FP_ERR_OOM, cudaGetErrorString(e));
+    g.err = derr;
+    int herr = 0;
+    e = cudaMemsetAsync(derr, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = fpk::launch_tc_gemm(g, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(derr, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fpk::api_fail(FP_ERR_CUDA, cudaGetErrorString(e));
+    if (herr) return fpk::api_fail(FP_ERR_TIMEOUT, "tcgen05 GEMM: an mbarrier wait ran out");
+    return FP_OK;
+}

@@ -48,3 +48,19 @@ def test_binding_names_match_header():
 def test_last_error_without_gpu(lib):
     lib.fp_last_error.restype = ctypes.c_char_p
     assert isinstance(lib.fp_last_error(), bytes)
+
+
+def test_gemm_argument_checks_without_gpu(lib):
+    # shape and alignment checks run before any CUDA call
+    f = lib.fp_gemm_bf16
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    f.argtypes = [i32, i32, i32, vp, i32, vp, i32, vp, i32, vp, vp, vp, vp, vp]
+    f.restype = ctypes.c_int
+    lib.fp_last_error.restype = ctypes.c_char_p
+    fake = vp(1 << 20)   # never dereferenced: every call below fails its checks
+    assert f(4, 24, 64, fake, 64, fake, 64, None, 0, None, fake, None, None, None) == -1   # N % 16
+    assert b"N % 16" in lib.fp_last_error()
+    assert f(4, 16, 60, fake, 64, fake, 64, None, 0, None, fake, None, None, None) == -1   # K % 8
+    assert f(4, 16, 64, fake, 64, fake, 64, None, 2, None, fake, None, None, None) == -1   # mode 2 needs Z
+    assert f(4, 16, 64, vp((1 << 20) + 8), 64, fake, 64, None, 0, None, fake, None, None, None) == -1  # alignment
+    assert f(4, 16, 64, fake, 64, fake, 64, None, 0, None, None, None, None, None) == -1   # no output
