@@ -5,25 +5,29 @@
 //
 // One CTA (128 threads) owns a 128 x NT output tile (NT <= 256 columns) whose
 // FP32 accumulator lives in tensor memory (TMEM: NT columns x 128 lanes).  The
-// K loop runs in stages of 64 through two shared-memory buffers: the threads
-// copy the A and B tiles of stage k+1 into the K-major "core matrix" layout
-// (8 rows x 16 bytes per core matrix, no swizzle) while the tensor core works
-// on stage k; one elected thread issues four tcgen05.mma (K = 16 each) per
-// stage and a tcgen05.commit to that buffer's mbarrier, which the threads wait
-// on before they overwrite the buffer.  The epilogue reads the accumulator back
-// with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. tile rows
-// 32w..32w+31), adds the bias and applies one of
+// K loop streams stages of 64 columns through a ring of TC_STAGES shared-memory
+// buffers, warp-specialised: one lane issues the TMA loads
+// (cp.async.bulk.tensor, completing on the stage's "full" mbarrier), one lane
+// waits for them and issues four tcgen05.mma (K = 16 each) and a
+// tcgen05.commit to the stage's "empty" mbarrier, which the loader waits on
+// before it refills the buffer.  A last commit signals the accumulator; the
+// epilogue reads it back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31,
+// i.e. tile rows 32w..32w+31), adds the bias and applies one of
 //   mode 0: identity,
 //   mode 1: GELU (the pre-activation optionally kept in Z),
 //   mode 2: multiply by GELU'(Z) (Z read: the backward pass of a GELU layer),
 // then stores FP32 row-major, BF16 row-major and/or BF16 transposed results.
+// Rows and K-chunks beyond the matrices are zero-filled by the TMA unit.
 // Every wait is bounded: on timeout the kernel raises the error flag, still
 // releases its TMEM, and returns; launches that find the flag raised return at
 // once.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "fp.h"
 #include "kernels.h"
@@ -31,7 +35,7 @@
 namespace fpk {
 namespace {
 
-constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 128, TC_MAXN = 256, TC_STAGES = 2;
+constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 128, TC_MAXN = 256, TC_STAGES = 4;
 constexpr long long TC_WAIT_LIMIT = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -70,27 +74,29 @@ __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678f)) + z * 0.39894228f * expf(-0.5f * z * z);
 }
 
-// copy rows [r0, r0 + rows) x K-columns [k0, k0 + 64) of a row-major BF16
-// matrix (leading dimension ld; rows < rmax and columns < K valid, the rest
-// zero) into the core-matrix layout: 16-byte chunk (r, kg) goes to byte
-// ((r/8)*8 + kg)*128 + (r%8)*16.  In each warp, lanes 0-7 take 8 consecutive
-// rows of one chunk column (a conflict-free 128-byte shared store) and lanes
-// 8i+j the next chunk columns (64 contiguous bytes of a row per global load).
-__device__ __forceinline__ void load_tile(unsigned char *dst, const __nv_bfloat16 *__restrict__ src, int ld, int r0,
-                                          int rows, int rmax, int k0, int K, int tid) {
-    for (int idx = tid; idx < rows * 8; idx += TC_THREADS) {
-        const int t = idx & 31, q = idx >> 5;
-        const int r = (q >> 1) * 8 + (t & 7), kg = (q & 1) * 4 + (t >> 3);
-        uint4 v = make_uint4(0, 0, 0, 0);
-        const int k = k0 + kg * 8;
-        if (r0 + r < rmax && k < K) v = *(const uint4 *)(src + (size_t)(r0 + r) * ld + k);
-        *(uint4 *)(dst + (((r >> 3) * 8 + kg) * 128 + (r & 7) * 16)) = v;
-    }
+__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count));
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcGemm g) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[TC_STAGES];
+// one TMA box (8 BF16 columns x `rows` rows, K-chunk x, first row y) of a
+// 2-D tensor map into shared memory, completing `bytes` on the mbarrier
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+// Shared memory per stage: A as 8 boxes [128 rows x 16 bytes] (one per
+// 8-column K-chunk, 2 KB apart), then B as 8 boxes [boxn rows x 16 bytes]
+// (boxn * 16 bytes apart).  Inside a box, the 8-row groups are the 128-byte
+// core matrices, so the MMA descriptors take stride (M/N) offset 128 and
+// leading (K) offset = the box size.
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcGemm g, const __grid_constant__ CUtensorMap tmA,
+                                                                const __grid_constant__ CUtensorMap tmB, int boxn) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
     __shared__ uint32_t taddr_sh;
     __shared__ int abort_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -98,44 +104,67 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcGemm g) {
     if (tid == 0) abort_sh = g.err ? *(volatile const int *)g.err : 0;
     __syncthreads();
     if (abort_sh) return;
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_MAXN;
     const int NT = min(TC_MAXN, g.N - n0);   // a multiple of 16
     const uint32_t ncols = NT <= 32 ? 32u : (NT <= 64 ? 64u : (NT <= 128 ? 128u : 256u));
-    const int stage_bytes = (TC_BM + TC_MAXN) * TC_BK * 2;
+    const uint32_t a_bytes = TC_BM * TC_BK * 2, b_bytes = (uint32_t)boxn * TC_BK * 2;
+    const uint32_t stage_bytes = a_bytes + TC_MAXN * TC_BK * 2;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_sh)),
                      "r"(ncols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
+    if (tid == 32) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t taddr = taddr_sh;
-    const uint32_t idesc = make_idesc(TC_BM, NT);
     const int nk = (g.K + TC_BK - 1) / TC_BK;
-    auto load_stage = [&](int s, int kt) {
-        unsigned char *sa = smem + s * stage_bytes;
-        load_tile(sa, g.A, g.lda, m0, TC_BM, g.M, kt * TC_BK, g.K, tid);
-        load_tile(sa + TC_BM * TC_BK * 2, g.Bt, g.ldb, n0, NT, g.N, kt * TC_BK, g.K, tid);
-    };
-    load_stage(0, 0);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    uint32_t ph[TC_STAGES] = {0, 0};
-    for (int kt = 0; kt < nk; ++kt) {
-        const int s = kt & 1;
-        if (tid == 0) {
+    const uint32_t sbase = smem_u32(smem);
+    if (tid == 0) {
+        // producer: TMA loads of stage kt once the MMAs of stage kt - S have drained the buffer
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % TC_STAGES, u = kt / TC_STAGES;
+            if (u > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)(u - 1) & 1u)) {
+                abort_sh = 1;
+                break;
+            }
+            const uint32_t fb = smem_u32(&full[s]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(a_bytes + b_bytes)
+                         : "memory");
+            const uint32_t sa = sbase + s * stage_bytes, sb = sa + a_bytes;
+#pragma unroll
+            for (int kg = 0; kg < 8; ++kg) {
+                tma_load(sa + kg * (TC_BM * 16), &tmA, kt * TC_BK + kg * 8, m0, fb);
+                tma_load(sb + kg * (boxn * 16), &tmB, kt * TC_BK + kg * 8, n0, fb);
+            }
+        }
+    } else if (tid == 32) {
+        // MMA issuer: four K = 16 steps per stage, then release the buffer
+        const uint32_t idesc = make_idesc(TC_BM, NT);
+        bool ok = true;
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % TC_STAGES, u = kt / TC_STAGES;
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)u & 1u)) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t sa = smem_u32(smem + s * stage_bytes), sb = sa + TC_BM * TC_BK * 2;
+            const uint32_t sa = sbase + s * stage_bytes, sb = sa + a_bytes;
 #pragma unroll
             for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                const uint64_t ad = make_desc(sa + kk * 256, 128, 1024);
-                const uint64_t bd = make_desc(sb + kk * 256, 128, 1024);
+                const uint64_t ad = make_desc(sa + kk * 2 * (TC_BM * 16), TC_BM * 16, 128);
+                const uint64_t bd = make_desc(sb + kk * 2 * (boxn * 16), (uint32_t)boxn * 16, 128);
                 const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
@@ -144,31 +173,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcGemm g) {
                     "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&mbar[s]))
+                             smem_u32(&empty[s]))
                          : "memory");
         }
-        if (kt + 1 < nk) {
-            bool ok = true;
-            if (kt >= 1) {   // the other buffer is free once stage kt-1's MMAs are done
-                ok = mbar_wait(smem_u32(&mbar[s ^ 1]), ph[s ^ 1]);
-                ph[s ^ 1] ^= 1u;
-            }
-            if (ok) {
-                load_stage(s ^ 1, kt + 1);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            } else {
-                abort_sh = 1;
-            }
-        }
-        __syncthreads();
-        if (abort_sh) break;
+        if (ok)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&done))
+                         : "memory");
+        else
+            abort_sh = 1;
     }
-    if (!abort_sh) {   // the last one or two commits have not been waited on
-        bool ok = true;
-        if (nk >= 2) ok = mbar_wait(smem_u32(&mbar[(nk - 2) & 1]), ph[(nk - 2) & 1]);
-        if (ok) ok = mbar_wait(smem_u32(&mbar[(nk - 1) & 1]), ph[(nk - 1) & 1]);
-        if (!ok) abort_sh = 1;
-    }
+    __syncwarp();
+    // everyone: wait for the accumulator (the last commit covers every MMA issued before it)
+    if (!mbar_wait(smem_u32(&done), 0u)) abort_sh = 1;
     __syncthreads();
     if (abort_sh) {
         if (tid == 0 && g.err) atomicExch(g.err, 1);
@@ -233,7 +250,7 @@ bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0;
 
 }  // namespace
 
-size_t tc_gemm_smem_bytes() { return (size_t)TC_STAGES * (TC_BM + TC_MAXN) * TC_BK * 2; }
+size_t tc_gemm_smem_bytes() { return (size_t)TC_STAGES * (TC_BM + TC_MAXN) * TC_BK * 2 + 128; }
 
 const char *tc_gemm_check(const TcGemm &g) {
     if (g.M < 0 || g.N <= 0 || g.N % 16 != 0 || g.K <= 0 || g.K % 8 != 0) return "need N % 16 == 0 and K % 8 == 0";
@@ -254,9 +271,45 @@ const char *tc_gemm_check(const TcGemm &g) {
     return nullptr;
 }
 
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// tensor map of a row-major [rows x ld] BF16 matrix whose first `cols`
+// columns are valid; boxes of 8 columns x box_rows rows
+bool make_map(CUtensorMap *m, const void *base, int rows, int cols, int ld, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {8u, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1u, 1u};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
 cudaError_t launch_tc_gemm(const TcGemm &g, cudaStream_t st) {
     if (g.M == 0) return cudaSuccess;
     if (tc_gemm_check(g)) return cudaErrorInvalidValue;
+    const int boxn = g.N < TC_MAXN ? g.N : TC_MAXN;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, g.A, g.M, g.K, g.lda, TC_BM) || !make_map(&mb, g.Bt, g.N, g.K, g.ldb, boxn))
+        return cudaErrorInvalidValue;
     const size_t smem = tc_gemm_smem_bytes();
     // the attribute is set outside stream capture (a launch being captured
     // follows a direct launch on the same device, which has set it)
@@ -268,7 +321,7 @@ cudaError_t launch_tc_gemm(const TcGemm &g, cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     dim3 grid((g.M + TC_BM - 1) / TC_BM, (g.N + TC_MAXN - 1) / TC_MAXN);
-    tc_gemm_kernel<<<grid, TC_THREADS, smem, st>>>(g);
+    tc_gemm_kernel<<<grid, TC_THREADS, smem, st>>>(g, ma, mb, boxn);
     return cudaGetLastError();
 }
 

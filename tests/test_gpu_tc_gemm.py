@@ -97,3 +97,25 @@ def test_gemm_bf16_empty_and_errors(env):
         fp.gemm_bf16(A, torch.zeros((16, 64), dtype=torch.bfloat16, device="cuda"), mode=2,
                      C=torch.zeros((4, 16), device="cuda"))          # mode 2 without Z
     assert e.value.status == -1
+
+
+def test_gemm_bf16_full_size_sampled(env):
+    # the surrogate-inference shape of the first layer at L = 6 (65536 pairs per
+    # chunk, 4nL = 1200 inputs, 256 hidden units), BF16 output only as in the
+    # inference pass; 64 sampled rows against the float64 definition
+    fp, torch = env
+    M, N, K = 65536, 256, 1200
+    g = torch.Generator(device="cuda").manual_seed(11)
+    A = (torch.rand(M, K, device="cuda", generator=g) * 2 - 1).to(torch.bfloat16)
+    Bt = (torch.randn(N, K, device="cuda", generator=g) / math.sqrt(K)).to(torch.bfloat16)
+    bias = torch.randn(N, device="cuda", generator=g)
+    Cb = torch.zeros(M, N, dtype=torch.bfloat16, device="cuda")
+    fp.gemm_bf16(A, Bt, bias, 1, None, None, Cb)
+    rows = torch.randint(0, M, (64,), generator=torch.Generator().manual_seed(3))
+    rows[0], rows[1] = 0, M - 1
+    a64, b64 = A[rows].cpu().double(), Bt.cpu().double()
+    pre = a64 @ b64.T + bias.cpu().double()
+    ref = gelu64(pre, torch)
+    tol = 1.2 * (K * 2.0 ** -23 * (a64.abs() @ b64.abs().T) + 1e-6) + 2.0 ** -8 * ref.abs() + 1e-6
+    err = (Cb[rows].cpu().double() - ref).abs()
+    assert torch.all(err <= tol), float((err / tol).max())
