@@ -17,7 +17,9 @@
 //   mode 1: GELU (the pre-activation optionally kept in Z),
 //   mode 2: multiply by GELU'(Z) (Z read: the backward pass of a GELU layer),
 // then stores FP32 row-major, BF16 row-major and/or BF16 transposed results.
-// Rows and K-chunks beyond the matrices are zero-filled by the TMA unit.
+// Tiles are 128-byte rows (64 BF16 of K) in the 128-byte swizzle, one TMA box
+// per operand and stage; rows and columns beyond the matrices are zero-filled
+// by the TMA unit.
 // Every wait is bounded: on timeout the kernel raises the error flag, still
 // releases its TMEM, and returns; launches that find the flag raised return at
 // once.
@@ -40,12 +42,15 @@ constexpr long long TC_WAIT_LIMIT = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor (tcgen05): start address, leading-dimension
-// byte offset (between core matrices adjacent in K), stride-dimension byte
-// offset (between core matrices adjacent in M/N), all >> 4; version 1; no swizzle
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+// shared-memory matrix descriptor (tcgen05) of a K-major tile stored as
+// 128-byte rows with the 128-byte swizzle (16-byte chunk c of row r at chunk
+// c ^ (r % 8)), tile base 1024-byte aligned: start address >> 4, leading
+// offset unused (1), stride offset 1024 bytes (8 rows) >> 4, version 1,
+// layout type 2 (128-byte swizzle) in bits 61-63.  Advancing K by 16 BF16
+// elements adds 32 bytes to the start address.
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
 }
 
 // instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
@@ -78,8 +83,8 @@ __device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count));
 }
 
-// one TMA box (8 BF16 columns x `rows` rows, K-chunk x, first row y) of a
-// 2-D tensor map into shared memory, completing `bytes` on the mbarrier
+// one TMA box (64 BF16 columns = 128 bytes x box rows, first column x, first
+// row y) of a 2-D tensor map into shared memory, completing its bytes on the mbarrier
 __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -88,11 +93,9 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// Shared memory per stage: A as 8 boxes [128 rows x 16 bytes] (one per
-// 8-column K-chunk, 2 KB apart), then B as 8 boxes [boxn rows x 16 bytes]
-// (boxn * 16 bytes apart).  Inside a box, the 8-row groups are the 128-byte
-// core matrices, so the MMA descriptors take stride (M/N) offset 128 and
-// leading (K) offset = the box size.
+// Shared memory per stage: the A tile [128 rows x 128 bytes] then the B tile
+// [boxn rows x 128 bytes], both written by the TMA unit with the 128-byte
+// swizzle that the MMA descriptors declare; stage bases 1024-byte aligned.
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcGemm g, const __grid_constant__ CUtensorMap tmA,
                                                                 const __grid_constant__ CUtensorMap tmB, int boxn) {
     extern __shared__ unsigned char smem_raw[];
@@ -104,7 +107,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcGemm g, const 
     if (tid == 0) abort_sh = g.err ? *(volatile const int *)g.err : 0;
     __syncthreads();
     if (abort_sh) return;
-    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_MAXN;
     const int NT = min(TC_MAXN, g.N - n0);   // a multiple of 16
     const uint32_t ncols = NT <= 32 ? 32u : (NT <= 64 ? 64u : (NT <= 128 ? 128u : 256u));
@@ -143,11 +146,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcGemm g, const 
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(a_bytes + b_bytes)
                          : "memory");
             const uint32_t sa = sbase + s * stage_bytes, sb = sa + a_bytes;
-#pragma unroll
-            for (int kg = 0; kg < 8; ++kg) {
-                tma_load(sa + kg * (TC_BM * 16), &tmA, kt * TC_BK + kg * 8, m0, fb);
-                tma_load(sb + kg * (boxn * 16), &tmB, kt * TC_BK + kg * 8, n0, fb);
-            }
+            tma_load(sa, &tmA, kt * TC_BK, m0, fb);
+            tma_load(sb, &tmB, kt * TC_BK, n0, fb);
         }
     } else if (tid == 32) {
         // MMA issuer: four K = 16 steps per stage, then release the buffer
@@ -163,8 +163,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcGemm g, const 
             const uint32_t sa = sbase + s * stage_bytes, sb = sa + a_bytes;
 #pragma unroll
             for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                const uint64_t ad = make_desc(sa + kk * 2 * (TC_BM * 16), TC_BM * 16, 128);
-                const uint64_t bd = make_desc(sb + kk * 2 * (boxn * 16), (uint32_t)boxn * 16, 128);
+                const uint64_t ad = make_desc_sw128(sa + kk * 32);
+                const uint64_t bd = make_desc_sw128(sb + kk * 32);
                 const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
@@ -250,7 +250,7 @@ bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0;
 
 }  // namespace
 
-size_t tc_gemm_smem_bytes() { return (size_t)TC_STAGES * (TC_BM + TC_MAXN) * TC_BK * 2 + 128; }
+size_t tc_gemm_smem_bytes() { return (size_t)TC_STAGES * (TC_BM + TC_MAXN) * TC_BK * 2 + 1024; }
 
 const char *tc_gemm_check(const TcGemm &g) {
     if (g.M < 0 || g.N <= 0 || g.N % 16 != 0 || g.K <= 0 || g.K % 8 != 0) return "need N % 16 == 0 and K % 8 == 0";
@@ -288,16 +288,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // tensor map of a row-major [rows x ld] BF16 matrix whose first `cols`
-// columns are valid; boxes of 8 columns x box_rows rows
+// columns are valid; boxes of 64 columns (128 bytes) x box_rows rows, 128-byte swizzle
 bool make_map(CUtensorMap *m, const void *base, int rows, int cols, int ld, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    cuuint32_t box[2] = {8u, (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1u, 1u};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
