@@ -35,6 +35,10 @@ WORK = dict(n=50, depth_min=2, depth_max=10, pairs=100_000, seed=4, k_max=4, kin
 WORKLOADS = {
     "brickwork": dict(WORK),
     "hea": dict(n=50, depth_min=1, depth_max=8, pairs=1_000_000, seed=3, k_max=4, kind=2, name="hea"),
+    # local random circuits: n = 20, T in {20, 40, ..., 100} gates per circuit (T >= 120 is
+    # reported separately: its boundaries reach the 2^24 limit, see local_large_T_report)
+    "local": dict(n=20, depth_min=1, depth_max=1, T=(20, 100, 20), pairs=20_000, seed=2, k_max=4, kind=1,
+                  name="local"),
 }
 SM_COUNT, FP32_LANES = 152, 128
 
@@ -52,7 +56,7 @@ def parse():
     ap.add_argument("--no-target", action="store_true", help="skip the GPU-seconds-to-1%% measurement")
     ap.add_argument("--no-cv", action="store_true", help="skip the control-variate report")
     ap.add_argument("--workload", default="brickwork", choices=sorted(WORKLOADS),
-                    help="brickwork (the headline workload) or hea (n=50, L=1..8)")
+                    help="brickwork (the headline workload), hea (n=50, L=1..8) or local (n=20, T=20..100)")
     a = ap.parse_args()
     WORK.update(WORKLOADS[a.workload])
     if a.pairs == 100_000 and a.workload != "brickwork":
@@ -60,11 +64,22 @@ def parse():
     return a
 
 
+def make_ensemble(fp, flags=0, stream=None):
+    T = WORK.get("T", (0, 0, 1))
+    if WORK["name"] == "local":
+        flags |= fp.FLAG_SKIP_INFEASIBLE   # rare pairs beyond the 2^24 boundary are counted, not contracted
+    return fp.Ensemble(WORK["kind"], WORK["n"], WORK["depth_min"], WORK["depth_max"], T[0], T[1], T[2],
+                       seed=WORK["seed"], flags=flags, stream=stream)
+
+
 def workload_config(args, world):
-    desc = ("brickwork n=50, l uniform in 2..10 per pair, Haar U(4)" if WORK["name"] == "brickwork" else
-            "HEA n=50, L uniform in 1..8 per pair, RY(theta)RZ(phi) + CZ ladder")
+    desc = {"brickwork": "brickwork n=50, l uniform in 2..10 per pair, Haar U(4)",
+            "hea": "HEA n=50, L uniform in 1..8 per pair, RY(theta)RZ(phi) + CZ ladder",
+            "local": "local random circuits n=20, T uniform in {20,40,...,100} Haar U(4) gates on uniformly "
+                     "random neighbour bonds per circuit"}[WORK["name"]]
     return {"workload": f"{desc}, {args.pairs} pairs per step per GPU",
-            "n": WORK["n"], "depth": [WORK["depth_min"], WORK["depth_max"]], "pairs_per_step": args.pairs,
+            "n": WORK["n"], "depth": list(WORK["T"]) if "T" in WORK else [WORK["depth_min"], WORK["depth_max"]],
+            "pairs_per_step": args.pairs,
             "k_max": WORK["k_max"], "precision": args.prec, "parallelism": f"pairs sharded over {world} GPU(s)",
             "l2": "per-step device working set (sampled gates, tables, boundaries) is GBs, larger than L2"}
 
@@ -215,6 +230,33 @@ def control_variate_report(fp, n_train=100_000, n_correct=10_000, m_surrogate=10
             "by_depth": out}
 
 
+def local_large_T_report(fp, per_T=12):
+    """Local circuits with T >= 120 gates (n = 20): per T, the fraction of sampled pairs
+    whose boundary fits the 2^24-amplitude limit, and the device time per feasible pair
+    (one pair per call, FP32 policy)."""
+    import numpy as np
+    out = {}
+    for T in (120, 140, 160, 180, 200):
+        ens = fp.Ensemble(1, 20, 1, 1, T, T, 1, seed=WORK["seed"] + T, flags=fp.FLAG_TIMING)
+        feas, ms = 0, 0.0
+        for p in range(per_T):
+            ens.kernel_stats(reset=True)
+            try:
+                ens.trace_batch(p, 1, fp.PREC_FP32)
+            except fp.FpError as e:
+                if e.status != -5:
+                    raise
+                continue
+            feas += 1
+            ks = ens.kernel_stats(reset=True)
+            ms += sum(ks.ms[i] for i in range(8))
+        ens.close()
+        out[str(T)] = {"sampled": per_T, "feasible": feas,
+                       "gpu_ms_per_feasible_pair": ms / feas if feas else None}
+    return {"note": "pairs whose boundary exceeds 2^24 amplitudes return FP_ERR_INFEASIBLE; a cluster "
+                    "of 16 CTAs contracts each large pair on the generic path", "by_T": out}
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -297,8 +339,7 @@ def main():
     prec = fp.PREC_FP32 if args.prec == "fp32" else fp.PREC_FP64
     stream = torch.cuda.current_stream()
     P, K = args.pairs, WORK["k_max"]
-    ens = fp.Ensemble(WORK["kind"], WORK["n"], WORK["depth_min"], WORK["depth_max"], seed=WORK["seed"],
-                      flags=fp.FLAG_TIMING, stream=stream.cuda_stream)
+    ens = make_ensemble(fp, fp.FLAG_TIMING, stream.cuda_stream)
     ng = len(ens.groups())
     tr = torch.empty(2 * P, dtype=torch.float64, device="cuda")
     kap = torch.empty(P, dtype=torch.float64, device="cuda")
@@ -311,13 +352,18 @@ def main():
     def first_of(step):
         return pair_range(step, rank, world, P)[0]
 
+    skipped = torch.zeros((), dtype=torch.int64, device="cuda")
+
     def step(s):
         ens.trace_batch(first_of(s), P, prec, tr, kap, grp, err)
         ens.reduce_moments(tr, grp, P, K, mom)
+        if WORK["name"] == "local":
+            skipped.add_((grp < 0).sum())
 
     for s in range(args.warmup):
         step(s)
     torch.cuda.synchronize()
+    skipped.zero_()
     ens.kernel_stats(reset=True)
 
     clk = Clocks(local)
@@ -342,13 +388,14 @@ def main():
     e2e = None
     if not args.no_e2e:
         # a user's ensemble: no per-kernel timing, so sub-batches replay CUDA graphs
-        ens_u = fp.Ensemble(WORK["kind"], WORK["n"], WORK["depth_min"], WORK["depth_max"], seed=WORK["seed"],
-                            stream=stream.cuda_stream)
+        ens_u = make_ensemble(fp, 0, stream.cuda_stream)
         ens_u.frame_potential(first_of(args.warmup + args.steps), P, K, 0.0, prec)   # warm
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        contracted = 0
         for s in range(args.steps):
-            ens_u.frame_potential(first_of(args.warmup + args.steps + 1 + s), P, K, 0.0, prec)
+            _, _, rst = ens_u.frame_potential(first_of(args.warmup + args.steps + 1 + s), P, K, 0.0, prec)
+            contracted += rst.pairs
         dt = time.perf_counter() - t0
         replays = int(ens_u.kernel_stats().graph_replays)
         ens_u.close()
@@ -362,11 +409,15 @@ def main():
             b = min(b * 2, 1 << 20)
         h2d = P * (40 + 4 + 4)
         d2h = (P * 8 if prec == fp.PREC_FP32 else 0) + batches * ng * (2 * K + 1) * 8
-        e2e = {"value": world * P * args.steps / dt, "unit": "contractions/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": world * contracted / dt, "unit": "contractions/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "api": "fp_frame_potential (results to host)",
                "graph_replays": replays}
+        if WORK["name"] == "local":
+            e2e["note"] = ("includes the host planning of every pair (own topology per pair); the per-pair "
+                           "contraction programs it uploads are not counted in h2d_bytes_per_step")
 
-    value = world * P * args.steps / (ms / 1e3)
+    n_skipped = int(skipped.item())
+    value = world * (P * args.steps - n_skipped) / (ms / 1e3)
     # roofline of the dominant kernel class
     cls = max(range(8), key=lambda i: ks.ms[i])
     flops = 8.0 * ks.work[cls]                 # complex multiply-add = 8 real flops
@@ -381,17 +432,22 @@ def main():
             "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz",
             "kernel_ms_share": ks.ms[cls] / ms if ms else None}
 
-    metric = METRIC if WORK["name"] == "brickwork" else "Tr(U^dagger V) contractions/s at n=50 (HEA, L=1..8)"
+    metric = {"brickwork": METRIC, "hea": "Tr(U^dagger V) contractions/s at n=50 (HEA, L=1..8)",
+              "local": "Tr(U^dagger V) contractions/s at n=20 (local circuits, T=20..100)"}[WORK["name"]]
     line = {"metric": metric, "value": value, "unit": "contractions/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec != fp.PREC_FP64 else "f64",
             "data": "synthetic (seeded circuit pairs)", "config": workload_config(args, world),
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
             "kernel_ms": {fp.K_NAMES.get(i, str(i)): ks.ms[i] for i in range(8) if ks.launches[i]}}
+    if WORK["name"] == "local":
+        line["infeasible_pairs_in_timed_steps"] = n_skipped
     if rank == 0 and world == 1 and not args.no_target and WORK["name"] == "brickwork":
         line["gpu_s_to_1pct_F2"] = gpu_seconds_to_target(fp, mom, P, K, ng)
     if rank == 0 and world == 1 and not args.no_cv and WORK["name"] == "brickwork":
         line["control_variate"] = control_variate_report(fp)
+    if rank == 0 and world == 1 and WORK["name"] == "local":
+        line["local_large_T"] = local_large_T_report(fp)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and WORK["name"] == "brickwork":
         cores = os.cpu_count() or 1
         r, dt, npairs, depths = oracle_time(10_000_000, cores)

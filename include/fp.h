@@ -44,6 +44,11 @@
  * stream given at creation (NULL = the legacy default stream).  Every call
  * returns after its results are in the caller's arrays.
  *
+ * Environment.  FP_AUTOTUNE_CACHE names a file in which the brickwork
+ * autotuner keeps its choices; FP_SWEEP_CLUSTER (1, 4, 8 or 16) fixes the
+ * number of CTAs that share one pair on the generic sweep (default: by
+ * boundary size).
+ *
  * Errors.  Calls return an fp_status; nothing is thrown across the ABI.
  * fp_last_error() gives a thread-local message for the last failing call on
  * the calling thread.  A failed call leaves caller arrays unspecified and the
@@ -87,7 +92,11 @@ enum {
     FP_FLAG_GENERIC_ONLY = 4,     /* never use the specialised brickwork kernels */
     FP_FLAG_TIMING = 8,           /* record CUDA-event time of every launch (fp_kernel_stats_get);
                                      also disables CUDA-graph replay */
-    FP_FLAG_NO_GRAPHS = 16        /* launch every kernel directly (no CUDA-graph replay) */
+    FP_FLAG_NO_GRAPHS = 16,       /* launch every kernel directly (no CUDA-graph replay) */
+    FP_FLAG_SKIP_INFEASIBLE = 32  /* pairs whose boundary exceeds FP_MAX_STATE_BITS are left
+                                     uncontracted instead of failing the call: NaN results,
+                                     group -1, left out of the moments, counted in
+                                     fp_run_stats.infeasible */
 };
 
 /* Kernel classes of fp_kernel_stats. */
@@ -140,6 +149,7 @@ typedef struct {
     double max_kappa;         /* largest cancellation ratio seen */
     int32_t n_groups;         /* groups reported (depth or T values) */
     int32_t reached_target;   /* 1 if every group met target_rel_stderr on F^(2) */
+    uint64_t infeasible;      /* pairs left out under FP_FLAG_SKIP_INFEASIBLE */
 } fp_run_stats;
 
 /* Per-kernel-class counters, accumulated while FP_FLAG_TIMING is set. */
@@ -184,7 +194,8 @@ fp_status fp_export_gates(fp_ensemble *ens, uint64_t pair, int32_t which, void *
  *          in the arithmetic that produced it (see FP_ERR_SAFETY);
  *   group  [count] int32 or NULL: group index of each pair.
  * Host or device pointers.  FP_ERR_INFEASIBLE if a pair's boundary exceeds
- * FP_MAX_STATE_BITS (nothing is written then). */
+ * FP_MAX_STATE_BITS (nothing is written then), unless FP_FLAG_SKIP_INFEASIBLE
+ * is set: then such pairs get tr = kappa = err = NaN and group = -1. */
 fp_status fp_trace_batch(fp_ensemble *ens, uint64_t first, uint64_t count, int32_t prec,
                          double *tr, double *kappa, double *err, int32_t *group);
 

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libfp_gb300.so")
 PARALLEL, LOCAL, HEA = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_FP32_RAW = 0, 1, 2
 FLAG_SELF_PAIR, FLAG_DIAGONAL_GATES, FLAG_GENERIC_ONLY, FLAG_TIMING, FLAG_NO_GRAPHS = 1, 2, 4, 8, 16
+FLAG_SKIP_INFEASIBLE = 32
 K_SAMPLE, K_MERGE, K_TABLES, K_SWEEP, K_BRICK, K_MOMENTS, K_CLASSES = 0, 1, 2, 3, 4, 5, 8
 K_NAMES = {0: "sample", 1: "merge", 2: "tables", 3: "sweep_generic", 4: "sweep_brick", 5: "moments"}
 MAX_STATE_BITS = 24
@@ -46,7 +47,7 @@ class Desc(ctypes.Structure):
 class RunStats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_uint64), ("fp64_recontracted", ctypes.c_uint64),
                 ("gpu_seconds", ctypes.c_double), ("max_kappa", ctypes.c_double),
-                ("n_groups", ctypes.c_int32), ("reached_target", ctypes.c_int32)]
+                ("n_groups", ctypes.c_int32), ("reached_target", ctypes.c_int32), ("infeasible", ctypes.c_uint64)]
 
 
 class KernelStats(ctypes.Structure):

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -18,6 +19,7 @@
 #include <numeric>
 #include <tuple>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "fp.h"
@@ -129,6 +131,12 @@ struct fp_ensemble {
     cudaEvent_t gev[2] = {};
     std::map<GraphKey, cudaGraphExec_t> graphs;
     uint64_t graph_replays = 0;
+    // FP_FLAG_SKIP_INFEASIBLE: slots (relative to the current call's first pair)
+    // left uncontracted because their boundary exceeds FP_MAX_STATE_BITS
+    std::vector<uint64_t> skipped;
+    DBuf d_skip;
+    // resident clusters of the generic sweep per cluster size (index log2 cs) and precision; -1 unknown
+    int sweep_slots[5][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};
 };
 
 namespace {
@@ -155,6 +163,30 @@ std::vector<int> local_bonds(const fp_ensemble_desc &d, uint64_t pair, int which
         b[g] = (int)pick(x.x[0], (uint32_t)(d.n - 1));
     }
     return b;
+}
+
+// f(i) for i in [0, count) on the host cores (at most 64 threads; serial for
+// small counts).  f must be safe to run concurrently for different i.
+template <typename F>
+void parallel_for(uint64_t count, F f) {
+    unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+    if (count < 64 || nt == 1) {
+        for (uint64_t i = 0; i < count; ++i) f(i);
+        return;
+    }
+    nt = (unsigned)std::min<uint64_t>(nt, count / 16);
+    std::atomic<uint64_t> next{0};
+    auto work = [&]() {
+        for (;;) {
+            const uint64_t i0 = next.fetch_add(16);
+            if (i0 >= count) return;
+            for (uint64_t i = i0; i < std::min(count, i0 + 16); ++i) f(i);
+        }
+    };
+    std::vector<std::thread> th;
+    for (unsigned t = 1; t < nt; ++t) th.emplace_back(work);
+    work();
+    for (auto &t : th) t.join();
 }
 
 HostPlan build_plan(const fp_ensemble_desc &d, int raw_kind, int depth, uint64_t pair) {
@@ -248,29 +280,37 @@ struct KTimer {
 
 // Generic path over a subset of pairs: outputs go to slots idx[i] of the
 // device arrays (pairs first + idx[i]).
-fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx,
+fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx_in,
                       const std::vector<int> &depth, int prec, double *tr, double *kappa, double *err,
                       float *gpu_ms) {
     const fp_ensemble_desc &d = E->d;
     const bool local = d.kind == FP_LOCAL;
-    const uint64_t count = idx.size();
-    if (count == 0) return FP_OK;
-    std::vector<int> plan_idx(count);
+    const bool skip = (d.flags & FP_FLAG_SKIP_INFEASIBLE) != 0;
+    if (idx_in.empty()) return FP_OK;
+    std::vector<int> plan_idx;
     std::vector<HostPlan> local_plans;
+    std::vector<uint64_t> kept;   // output slots contracted here, in batch order
     PlanPools pools;
     if (!local) {
-        for (uint64_t i = 0; i < count; ++i) {
-            const int dep = depth[idx[i]];
+        for (uint64_t slot : idx_in) {
+            const int dep = depth[slot];
             auto it = E->plan_of_depth.find(dep);
             if (it == E->plan_of_depth.end()) {
-                HostPlan h = build_plan(d, E->raw_kind, dep, first + idx[i]);
-                if (h.infeasible) return fail(FP_ERR_INFEASIBLE, "depth %d: %s", dep, h.error.c_str());
-                if (!h.error.empty()) return fail(FP_ERR_ARG, "planner: %s", h.error.c_str());
+                HostPlan h = build_plan(d, E->raw_kind, dep, first + slot);
+                if (!h.error.empty() && !h.infeasible) return fail(FP_ERR_ARG, "planner: %s", h.error.c_str());
+                if (h.infeasible && !skip) return fail(FP_ERR_INFEASIBLE, "depth %d: %s", dep, h.error.c_str());
                 E->plans.push_back(std::move(h));
                 it = E->plan_of_depth.emplace(dep, (int)E->plans.size() - 1).first;
                 E->dev_plans_dirty = true;
             }
-            plan_idx[i] = it->second;
+            const HostPlan &h = E->plans[it->second];
+            if (h.infeasible) {
+                if (!skip) return fail(FP_ERR_INFEASIBLE, "depth %d: %s", dep, h.error.c_str());
+                E->skipped.push_back(slot);
+                continue;
+            }
+            plan_idx.push_back(it->second);
+            kept.push_back(slot);
         }
         if (E->dev_plans_dirty) {
             for (const auto &h : E->plans) pools.add(h);
@@ -279,37 +319,75 @@ fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t
             E->dev_plans_dirty = false;
         }
     } else {
-        local_plans.reserve(count);
-        for (uint64_t i = 0; i < count; ++i) {
-            HostPlan h = build_plan(d, E->raw_kind, depth[idx[i]], first + idx[i]);
-            if (h.infeasible)
-                return fail(FP_ERR_INFEASIBLE, "pair %llu (T=%d): %s", (unsigned long long)(first + idx[i]),
-                            depth[idx[i]], h.error.c_str());
+        // every local-circuit pair has its own topology: plan them on the host
+        // cores in parallel, then order the batch by boundary size so that the
+        // memory-budgeted sub-batches below group pairs of similar workspace
+        const uint64_t n_in = idx_in.size();
+        std::vector<HostPlan> all(n_in);
+        parallel_for(n_in, [&](uint64_t i) {
+            all[i] = build_plan(d, E->raw_kind, depth[idx_in[i]], first + idx_in[i]);
+        });
+        std::vector<uint64_t> feas;
+        for (uint64_t i = 0; i < n_in; ++i) {
+            const HostPlan &h = all[i];
+            if (h.infeasible) {
+                if (!skip)
+                    return fail(FP_ERR_INFEASIBLE, "pair %llu (T=%d): %s", (unsigned long long)(first + idx_in[i]),
+                                depth[idx_in[i]], h.error.c_str());
+                E->skipped.push_back(idx_in[i]);
+                continue;
+            }
             if (!h.error.empty()) return fail(FP_ERR_ARG, "planner: %s", h.error.c_str());
-            pools.add(h);
-            plan_idx[i] = (int)i;
-            local_plans.push_back(std::move(h));
+            feas.push_back(i);
         }
-        fp_status s = upload_pools(E, pools);
-        if (s != FP_OK) return s;
-        E->dev_plans_dirty = true;   // the fixed-topology pool was overwritten
+        std::stable_sort(feas.begin(), feas.end(),
+                         [&](uint64_t a, uint64_t b) { return all[a].bits_max < all[b].bits_max; });
+        for (uint64_t i : feas) {
+            local_plans.push_back(std::move(all[i]));
+            kept.push_back(idx_in[i]);
+        }
+        for (uint64_t i = 0; i < local_plans.size(); ++i) {
+            pools.add(local_plans[i]);
+            plan_idx.push_back((int)i);
+        }
+        if (!local_plans.empty()) {
+            fp_status s = upload_pools(E, pools);
+            if (s != FP_OK) return s;
+            E->dev_plans_dirty = true;   // the fixed-topology pool was overwritten
+        }
     }
+    const uint64_t count = kept.size();
+    if (count == 0) return FP_OK;
+    const std::vector<uint64_t> &idx = kept;
     auto hp = [&](uint64_t i) -> const HostPlan & { return local ? local_plans[i] : E->plans[plan_idx[i]]; };
     const bool fp32 = prec != FP_PREC_FP64;
     const size_t celem = fp32 ? sizeof(float2) : sizeof(double2);
+    // pairs with large boundaries get a cluster of CTAs each (see sweep_cluster_size)
+    auto cluster_of = [&](int bits) {
+        int cs = sweep_cluster_size(bits);
+        while (cs > 1) {
+            int lg = cs == 4 ? 2 : (cs == 8 ? 3 : 4);
+            int &slots = E->sweep_slots[lg][fp32 ? 1 : 0];
+            if (slots < 0) slots = sweep_max_clusters(cs, fp32);
+            if (slots > 0) return std::make_pair(cs, slots);
+            cs /= 2;   // clusters of this size cannot launch here: smaller ones
+            if (cs == 2) cs = 1;
+        }
+        return std::make_pair(1, E->sms * 2);
+    };
     uint64_t done = 0;
     while (done < count) {
         uint64_t nb = 0;
         size_t raw_b = 0, mer_b = 0, tab_b = 0;
         int bits_max = 0, max_raw = 0, max_mer = 0, max_ops = 0;
-        const int ctas_full = E->sms * 2;
         while (done + nb < count && nb < 65535) {
             const HostPlan &h = hp(done + nb);
             size_t r = (size_t)2 * h.n_raw * 16 * sizeof(double2);
             size_t m = h.merges.size() * 16 * sizeof(double2);
             size_t t = h.ops.size() * 16 * sizeof(double2);
             int bm = std::max(bits_max, h.bits_max);
-            size_t ws = (size_t)std::min<uint64_t>(ctas_full, nb + 1) * 3 * ((size_t)1 << bm) * sizeof(double2);
+            const int slots_full = cluster_of(bm).second;
+            size_t ws = (size_t)std::min<uint64_t>(slots_full, nb + 1) * 3 * ((size_t)1 << bm) * sizeof(double2);
             if (nb > 0 && raw_b + r + mer_b + m + tab_b + t + ws > E->ws_budget) break;
             raw_b += r; mer_b += m; tab_b += t; bits_max = bm;
             max_raw = std::max(max_raw, h.n_raw);
@@ -337,14 +415,16 @@ fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t
         std::vector<int32_t> order(nb);
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hp(done + a).cost > hp(done + b).cost; });
-        int ctas = (int)std::min<uint64_t>(nb, (uint64_t)ctas_full);
+        const auto cl = cluster_of(bits_max);
+        const int slots = (int)std::min<uint64_t>(nb, (uint64_t)cl.second);
+        const int ctas = slots * cl.first;
         size_t ws_elems = (size_t)1 << bits_max;
         CK(upload(E->d_pairs, pinfo, E->st));
         CK(upload(E->d_order, order, E->st));
         CK(E->d_raw.reserve(std::max<size_t>(16, ro * 16 * sizeof(double2))));
         CK(E->d_merged.reserve(std::max<size_t>(16, mo * 16 * sizeof(double2))));
         CK(E->d_tables.reserve(std::max<size_t>(16, to * 16 * sizeof(double2))));
-        CK(E->d_ws.reserve((size_t)ctas * 3 * ws_elems * celem));
+        CK(E->d_ws.reserve((size_t)slots * 3 * ws_elems * celem));
         SampleParams sp;
         sp.seed = d.seed;
         sp.n = d.n;
@@ -373,7 +453,7 @@ fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t
             KTimer t(E, FP_K_SWEEP);
             CK(launch_sweep_generic(E->d_pairs.as<PairInfo>(), E->d_order.as<int32_t>(), (int)nb, E->d_plans.as<DevPlan>(),
                                     E->d_ops.as<DevOp>(), E->d_tables.p, fp32, E->d_ws.p, ws_elems, ctas,
-                                    E->d_ticket.as<int>(), FP_ERR_SAFETY * (fp32 ? 0x1.0p-24 : 0x1.0p-53), tr,
+                                    cl.first, E->d_ticket.as<int>(), FP_ERR_SAFETY * (fp32 ? 0x1.0p-24 : 0x1.0p-53), tr,
                                     kappa, err, E->st));
             CK(t.stop(cmacs));
         }
@@ -621,15 +701,32 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
 }
 
 // Route pairs first + idx[i] to the brickwork or generic path.
+__global__ void mark_skipped_kernel(const uint64_t *slots, uint64_t n, double *tr, double *kappa, double *err) {
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t s = slots[i];
+    tr[2 * s] = tr[2 * s + 1] = NAN;
+    kappa[s] = NAN;
+    err[s] = NAN;
+}
+
 fp_status route(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx, const std::vector<int> &depth,
                 int prec, double *tr, double *kappa, double *err, float *gpu_ms) {
     const fp_ensemble_desc &d = E->d;
     const bool brick = (d.kind == FP_PARALLEL || d.kind == FP_HEA) && !(d.flags & FP_FLAG_GENERIC_ONLY);
+    const bool skip = (d.flags & FP_FLAG_SKIP_INFEASIBLE) != 0;
     std::map<int, std::vector<uint64_t>> by_depth;
     std::vector<uint64_t> generic;
     for (uint64_t i : idx) {
-        if (brick && depth[i] >= 2) by_depth[depth[i]].push_back(i);
-        else generic.push_back(i);
+        if (brick && depth[i] >= 2) {
+            if (skip && 2 * (depth[i] - 1) > FP_MAX_STATE_BITS) {   // boundary of 2(l-1) segment bits
+                E->skipped.push_back(i);
+                continue;
+            }
+            by_depth[depth[i]].push_back(i);
+        } else {
+            generic.push_back(i);
+        }
     }
     // deepest first: the largest working sets get the memory while it is free
     for (auto it = by_depth.rbegin(); it != by_depth.rend(); ++it) {
@@ -659,8 +756,22 @@ fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec,
     std::vector<uint64_t> all(count);
     std::iota(all.begin(), all.end(), 0);
     double *tr = E->d_tr.as<double>(), *kap = E->d_kappa.as<double>(), *err = E->d_err.as<double>();
+    E->skipped.clear();
     fp_status s = route(E, first, all, depth, prec, tr, kap, err, gpu_ms);
     if (s != FP_OK) return s;
+    std::vector<char> skipped(count, 0);
+    if (!E->skipped.empty()) {
+        // uncontracted pairs: NaN results, group -1 (left out of every moment)
+        for (uint64_t i : E->skipped) {
+            skipped[i] = 1;
+            grp[i] = -1;
+        }
+        CK(cudaMemcpyAsync(E->d_group.p, grp.data(), count * sizeof(int32_t), cudaMemcpyHostToDevice, E->st));
+        CK(upload(E->d_skip, E->skipped, E->st));
+        mark_skipped_kernel<<<(unsigned)((E->skipped.size() + 255) / 256), 256, 0, E->st>>>(
+            E->d_skip.as<uint64_t>(), E->skipped.size(), tr, kap, err);
+        CK(cudaGetLastError());
+    }
     if (prec == FP_PREC_FP32 || max_kappa) {
         std::vector<double> k(count), e(count);
         CK(cudaMemcpyAsync(k.data(), kap, count * sizeof(double), cudaMemcpyDeviceToHost, E->st));
@@ -671,7 +782,7 @@ fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec,
         for (uint64_t i = 0; i < count; ++i) {
             if (max_kappa && std::isfinite(k[i])) *max_kappa = std::max(*max_kappa, k[i]);
             const bool over = !(e[i] <= tol) || (d.kappa_max > 0 && !(k[i] <= d.kappa_max));
-            if (prec == FP_PREC_FP32 && over) redo.push_back(i);
+            if (prec == FP_PREC_FP32 && over && !skipped[i]) redo.push_back(i);
         }
         if (!redo.empty()) {
             if (requeued) *requeued += redo.size();
@@ -877,6 +988,7 @@ fp_status fp_frame_potential(fp_ensemble *ens, uint64_t first, uint64_t max_pair
         float ms = 0;
         fp_status s = trace_device(ens, first + done, nb, prec, &ms, &st.fp64_recontracted, &st.max_kappa);
         if (s != FP_OK) return s;
+        st.infeasible += ens->skipped.size();
         st.gpu_seconds += ms * 1e-3;
         int nb_blocks = moments_blocks(nb);
         CK(ens->d_partials.reserve((size_t)nb_blocks * ng * nv * sizeof(double)));
@@ -895,7 +1007,7 @@ fp_status fp_frame_potential(fp_ensemble *ens, uint64_t first, uint64_t max_pair
             acc[i] = y;
         }
         done += nb;
-        st.pairs = done;
+        st.pairs = done - st.infeasible;
         reached = target_rel_stderr > 0;
         for (int g = 0; g < ng; ++g) {
             double N = acc[g * nv] + comp[g * nv];

@@ -26,13 +26,19 @@ cudaError_t launch_merge(const PairInfo *pairs, int npairs, int max_merged, cons
 cudaError_t launch_tables(const PairInfo *pairs, int npairs, int max_ops, const DevPlan *plans,
                           const DevRecipe *recipes, const double2 *merged, void *tables, bool fp32,
                           cudaStream_t st);
-// Generic boundary sweep + meet: one CTA per pair at a time, persistent over a
-// ticket queue.  Writes tr[2*i], kappa[i] for pair i of `order`.
+// Generic boundary sweep + meet: one cluster of `cs` CTAs (1, 4, 8 or 16) per
+// pair at a time, persistent over a ticket queue; `ctas` is a multiple of cs
+// and the workspace holds ctas/cs slots of 3 x ws_elems amplitudes.  Writes
+// tr[2*i], kappa[i] for pair i of `order`.
 cudaError_t launch_sweep_generic(const PairInfo *pairs, const int32_t *order, int count,
                                  const DevPlan *plans, const DevOp *ops, const void *tables,
-                                 bool fp32, void *workspace, size_t ws_elems_per_cta, int ctas,
+                                 bool fp32, void *workspace, size_t ws_elems_per_cta, int ctas, int cs,
                                  int *ticket, double err_unit, double *tr, double *kappa, double *err,
                                  cudaStream_t st);
+// Cluster size for a batch whose largest boundary has `bits` bits, and how many
+// such clusters can be resident (0 if clusters of that size cannot launch).
+int sweep_cluster_size(int bits);
+int sweep_max_clusters(int cs, bool fp32);
 // FP64 moments per group (deterministic).
 cudaError_t launch_moments(const double *tr, const int32_t *group, uint64_t count, int k_max,
                            int n_groups, double *partials, int nblocks, double *out,

@@ -76,23 +76,40 @@ bool commute(const SeqEl &a, const SeqEl &b) {
 bool same_support(const SeqEl &a, const SeqEl &b) { return a.kind == b.kind && a.q == b.q; }
 
 void merge_sequence(std::vector<SeqEl> &seq) {
+    // The sequence is cyclic; merged-away operators are unlinked from a
+    // doubly linked ring (no element moves), and passes in index order repeat
+    // until nothing merges.  Survivors keep their relative order.
+    const int N0 = (int)seq.size();
+    if (N0 < 2) return;
+    std::vector<int> nxt(N0), prv(N0);
+    std::vector<char> alive(N0, 1);
+    for (int i = 0; i < N0; ++i) {
+        nxt[i] = (i + 1) % N0;
+        prv[i] = (i + N0 - 1) % N0;
+    }
+    int n_alive = N0;
+    auto unlink = [&](int i) {
+        nxt[prv[i]] = nxt[i];
+        prv[nxt[i]] = prv[i];
+        alive[i] = 0;
+        --n_alive;
+    };
     bool changed = true;
-    while (changed && seq.size() > 1) {
+    while (changed && n_alive > 1) {
         changed = false;
-        const size_t N = seq.size();
-        for (size_t i = 0; i < N && !changed; ++i) {
+        for (int i = 0; i < N0 && n_alive > 1; ++i) {
+            if (!alive[i]) continue;
             // walk forward (cyclically) while seq[i] commutes with what it passes;
             // stop at the first operator with the same support (merge) or the
             // first one it does not commute with (no merge)
-            size_t j = N;
-            for (size_t s = 1; s < N; ++s) {
-                size_t k = (i + s) % N;
+            int j = -1;
+            for (int s = 1, k = nxt[i]; s < n_alive; ++s, k = nxt[k]) {
                 if (same_support(seq[i], seq[k])) { j = k; break; }
                 if (!commute(seq[i], seq[k])) break;
             }
-            if (j == N) continue;
+            if (j < 0) continue;
             // seq[i] moves forward (cyclically) past commuting operators to seq[j]
-            SeqEl m = seq[j];
+            SeqEl &m = seq[j];
             if (m.kind == 2) {
                 bool ident = true;
                 for (int e = 0; e < 4; ++e) {
@@ -101,23 +118,22 @@ void merge_sequence(std::vector<SeqEl> &seq) {
                     m.dre[e] = re; m.dim[e] = im;
                     if (re != 1.0 || im != 0.0) ident = false;
                 }
-                if (ident) {
-                    size_t hi = std::max(i, j), lo = std::min(i, j);
-                    seq.erase(seq.begin() + hi);
-                    seq.erase(seq.begin() + lo);
-                    changed = true;
-                    break;
-                }
+                if (ident) unlink(j);   // CZ . CZ = identity: both go
             } else {
-                std::vector<MergeRef> c = seq[i].chain;
+                // application order: seq[i]'s chain first, then m's
+                std::vector<MergeRef> c = std::move(seq[i].chain);
                 c.insert(c.end(), m.chain.begin(), m.chain.end());
-                m.chain = c;
+                m.chain = std::move(c);
             }
-            seq[j] = m;
-            seq.erase(seq.begin() + i);
+            unlink(i);
             changed = true;
         }
     }
+    std::vector<SeqEl> out;
+    out.reserve(n_alive);
+    for (int i = 0; i < N0; ++i)
+        if (alive[i]) out.push_back(std::move(seq[i]));
+    seq = std::move(out);
 }
 
 struct Factor {
@@ -142,6 +158,7 @@ int slot_entry(const Factor &f, const int *val) {
 HostPlan make_plan(int n, const std::vector<GateSlot> &U, const std::vector<GateSlot> &V,
                    int raw_kind, int n_raw, int cut, int max_bits) {
     HostPlan P;
+    max_bits = std::min(max_bits, FP_MAX_STATE_BITS);   // device tables are sized for this
     P.n = n;
     P.n_raw = n_raw;
     P.raw_kind = raw_kind;

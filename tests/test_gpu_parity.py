@@ -395,3 +395,44 @@ def test_bench_workload_sampled_parity(fp):
         assert abs(tr32[p] - ref[p]) <= TOL32, (p, grp[p] + 2, tr32[p], ref[p])
         t64, _, _ = ens.trace_batch(int(p), 1, fp.PREC_FP64)
         assert abs(t64[0] - ref[p]) <= TOL64 * max(1.0, abs(ref[p])), (p, grp[p] + 2, t64[0], ref[p])
+
+
+def test_skip_infeasible_pairs(fp):
+    # local circuits n = 20 with T in {20, 200}: T = 200 boundaries exceed 2^24 amplitudes.
+    # Without the flag the call fails; with it those pairs come back NaN / group -1 and
+    # the feasible ones still match the oracle.
+    ens, od = make(fp, "local", 20, T=(20, 200, 180), seed=21)
+    with pytest.raises(fp.FpError) as e:
+        ens.trace_batch(0, 16, fp.PREC_FP64)
+    assert e.value.status == -5
+    ens2 = fp.Ensemble(1, 20, 1, 1, 20, 200, 180, seed=21, flags=fp.FLAG_SKIP_INFEASIBLE)
+    tr, kap, grp = ens2.trace_batch(0, 16, fp.PREC_FP64)
+    T = np.array([O.pair_depth(od, p) for p in range(16)])
+    assert set(T.tolist()) == {20, 200}
+    big = T == 200
+    assert np.all(grp[big] == -1) and np.all(grp[~big] == 0)
+    assert np.all(np.isnan(tr[big])) and np.all(np.isnan(kap[big]))
+    idx = np.flatnonzero(~big)
+    ref = np.array([O.trace_batch(od, int(p), 1, "ve")[0] for p in idx])
+    assert rel_err(tr[idx], ref).max() <= TOL64
+    F, se, st = ens2.frame_potential(0, 64, 2, 0.0, fp.PREC_FP32)
+    assert st.infeasible + st.pairs == 64 and st.infeasible > 0
+    assert np.isfinite(F[0, 0]) and np.isnan(F[1, 0])
+    # brickwork depth 14 (26-bit boundary) under the flag: every pair skipped
+    ens3 = fp.Ensemble(0, 50, 14, 14, seed=1, flags=fp.FLAG_SKIP_INFEASIBLE)
+    tr3, _, grp3 = ens3.trace_batch(0, 4, fp.PREC_FP32)
+    assert np.all(np.isnan(tr3)) and np.all(grp3 == -1)
+
+
+@pytest.mark.parametrize("cluster", ["1", "4", "8", "16"])
+def test_generic_sweep_cluster_sizes(fp, cluster, monkeypatch):
+    # the generic sweep with every cluster size (CTAs sharing one pair's ops),
+    # local circuits n = 20, T = 40..80, FP64 against the oracle and FP32 within 1e-4
+    monkeypatch.setenv("FP_SWEEP_CLUSTER", cluster)
+    ens, od = make(fp, "local", 20, T=(40, 80, 20), seed=31)
+    N = 10
+    tr, kap, grp = ens.trace_batch(0, N, fp.PREC_FP64)
+    ref = O.trace_batch(od, 0, N, "ve", threads=8)
+    assert rel_err(tr, ref).max() <= TOL64
+    tr32, _, _ = ens.trace_batch(0, N, fp.PREC_FP32_RAW)
+    assert np.abs(tr32 - ref).max() <= TOL32
