@@ -10,6 +10,7 @@ The C source (``fp_oracle.c``) is compiled on first use into
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -79,6 +80,9 @@ def lib():
             L.orc_moments.argtypes = [P(ctypes.c_double), ctypes.c_int64, ctypes.c_int,
                                       P(ctypes.c_double), P(ctypes.c_double)]
             L.orc_weingarten_f2_brickwork.argtypes = [ctypes.c_int, ctypes.c_int]
+            L.orc_bootstrap.argtypes = [P(ctypes.c_double), P(ctypes.c_int32), ctypes.c_int64, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_uint64, P(ctypes.c_double)]
+            L.orc_bootstrap.restype = None
             L.orc_weingarten_f2_brickwork.restype = ctypes.c_double
             _lib = L
     return _lib
@@ -182,3 +186,46 @@ def moments(tr, kmax):
 
 def weingarten_f2_brickwork(n, l):
     return float(lib().orc_weingarten_f2_brickwork(n, l))
+
+
+def bootstrap(tr, group, n_groups, kmax, B, seed):
+    """Bootstrap distribution of F^(k): array [n_groups, kmax, B] (see orc_bootstrap)."""
+    tr = np.asarray(tr)
+    t = np.ascontiguousarray(np.stack([np.real(tr), np.imag(tr)], axis=1).reshape(-1), dtype=np.float64)
+    g = np.ascontiguousarray(group, dtype=np.int32)
+    out = np.zeros(n_groups * kmax * B)
+    lib().orc_bootstrap(_dp(t), g.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(tr), n_groups, kmax, B,
+                        seed, _dp(out))
+    return out.reshape(n_groups, kmax, B)
+
+
+def log10_epsilon_max(F, k, n, q=2):
+    """log10 of epsilon_max = d^k sqrt(F - k!), d = q^n (Sec. "Frame potential",
+    Eq. epsilonmax); NaN when F <= k!."""
+    dev = F - math.factorial(k)
+    if not dev > 0:
+        return float("nan")
+    return k * n * math.log10(q) + 0.5 * math.log10(dev)
+
+
+def design_layers(depths, F, k, n, q=2, eps=0.1, dev_max=5.0):
+    """Layers for an eps-approximate k-design from a depth sweep (Sec. "Frame
+    potential", Eqs. exponential and layers; fitting region of the supplementary
+    "Choice of curve fitting region"): keep depths with 0 < (F - k!)/k! < dev_max,
+    fit log(F - k!) = a + s l by least squares, then A = exp(a/2), C = -2/s and
+    l_eps = C (k n ln q + ln A + ln(1/eps)).  Returns (l_eps, A, C); NaNs if fewer
+    than two depths qualify or the fitted slope is not negative."""
+    fh = math.factorial(k)
+    pts = [(float(l), math.log(f - fh)) for l, f in zip(depths, F) if 0 < (f - fh) / fh < dev_max]
+    if len(pts) < 2:
+        return float("nan"), float("nan"), float("nan")
+    x = np.array([p[0] for p in pts])
+    y = np.array([p[1] for p in pts])
+    xm, ym = x.mean(), y.mean()
+    s = float(((x - xm) * (y - ym)).sum() / ((x - xm) ** 2).sum())
+    a = float(ym - s * xm)
+    if not s < 0:
+        return float("nan"), float("nan"), float("nan")
+    C = -2.0 / s
+    lnA = a / 2.0
+    return C * (k * n * math.log(q) + lnA + math.log(1.0 / eps)), math.exp(lnA), C

@@ -484,6 +484,49 @@ void orc_moments(const double *tr, int64_t N, int kmax, double *F, double *se)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Bootstrap of the frame-potential estimator (Supplementary, "Bootstrapping */
+/* for uncertainty quantification"): a resample draws N samples with         */
+/* replacement from the N stored traces and evaluates F^(k) on them; the     */
+/* paper uses 300 resamples.  Written as the definition: one draw at a time. */
+/* ------------------------------------------------------------------------ */
+void orc_bootstrap(const double *tr, const int32_t *group, int64_t count, int n_groups, int kmax,
+                   int B, uint64_t seed, double *F_boot)
+{
+    for (int g = 0; g < n_groups; ++g) {
+        int64_t Ng = 0;
+        for (int64_t i = 0; i < count; ++i) Ng += group[i] == g;
+        int64_t *members = malloc((size_t)(Ng > 0 ? Ng : 1) * sizeof(int64_t));
+        int64_t m = 0;
+        for (int64_t i = 0; i < count; ++i)
+            if (group[i] == g) members[m++] = i;
+        for (int b = 0; b < B; ++b) {
+            for (int k = 1; k <= kmax; ++k) F_boot[((int64_t)g * kmax + k - 1) * B + b] = NAN;
+            if (Ng == 0) continue;
+            double *s = calloc((size_t)kmax, sizeof(double)), *c = calloc((size_t)kmax, sizeof(double));
+            for (int64_t i = 0; i < Ng; ++i) {
+                const uint64_t ctr[4] = {(uint64_t)b, (uint64_t)(i / 4), (uint64_t)g, 5};
+                const uint64_t key[2] = {seed, 0};
+                uint64_t x[4];
+                orc_philox4x64(ctr, key, x);
+                const uint64_t pos = ((x[i % 4] >> 32) * (uint64_t)Ng) >> 32;
+                const int64_t j = members[pos];
+                const double a2 = tr[2 * j] * tr[2 * j] + tr[2 * j + 1] * tr[2 * j + 1];
+                double p = 1.0;
+                for (int k = 1; k <= kmax; ++k) {
+                    p *= a2;
+                    neumaier_add(&s[k - 1], &c[k - 1], p);
+                }
+            }
+            for (int k = 1; k <= kmax; ++k)
+                F_boot[((int64_t)g * kmax + k - 1) * B + b] = (s[k - 1] + c[k - 1]) / (double)Ng;
+            free(s);
+            free(c);
+        }
+        free(members);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exact ensemble F^(2) of brickwork circuits (the statistical-mechanics    */
 /* model behind Eq. theory_eq).  After averaging each Haar U(4) gate g of  */
 /* the cyclic U^dagger V circuit over the Haar measure, g becomes           */

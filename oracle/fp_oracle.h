@@ -19,6 +19,8 @@
  *   F^(k) ~= (1/N) sum |Tr(U^dagger V)|^{2k}                 (Sec. "Algorithm description")
  *   exact ensemble F^(2) of brickwork circuits by a Weingarten
  *   transfer matrix                                           (Eq. theory_eq context)
+ *   bootstrap distribution of F^(k)                           (Supplementary, "Bootstrapping
+ *                                                              for uncertainty quantification")
  *
  * Conventions (the paper leaves them open; the GPU library states the same
  * conventions in its own header, written separately):
@@ -84,6 +86,16 @@ int    orc_trace_batch(const orc_desc *d, uint64_t first, uint64_t count, int me
                        int nthreads, double *tr);
 void   orc_moments(const double *tr, int64_t N, int kmax, double *F, double *se);
 double orc_weingarten_f2_brickwork(int n, int l);
+/* Bootstrap distribution of F^(k) per group (Supplementary "Bootstrapping for
+ * uncertainty quantification"): every group's N_g traces are resampled N_g
+ * times with replacement, B times.  Draw i of resample b in group g takes
+ * position ((x >> 32) N_g) >> 32 of the group's pairs listed in increasing
+ * index order, x = word i mod 4 of the Philox4x64-10 block with key
+ * {seed, 0} and counter {b, i / 4, g, 5}.  Pairs with group < 0 or
+ * >= n_groups are ignored.  F_boot[(g * kmax + k - 1) * B + b]; NaN for an
+ * empty group. */
+void   orc_bootstrap(const double *tr, const int32_t *group, int64_t count, int n_groups, int kmax,
+                     int B, uint64_t seed, double *F_boot);
 
 #ifdef __cplusplus
 }

@@ -297,3 +297,89 @@ def test_moments_match_numpy():
         x = np.abs(tr) ** (2 * k)
         assert abs(F[k - 1] - x.mean()) < 1e-12 * x.mean()
         assert abs(se[k - 1] - x.std(ddof=1) / math.sqrt(len(x))) < 1e-10 * se[k - 1]
+
+
+# ---------------------------------------------------------------------------
+# Bootstrap (Supplementary "Bootstrapping for uncertainty quantification") and the
+# derived outputs of Sec. "Frame potential" (epsilon_max, Eqs. exponential/layers).
+def test_bootstrap_resamples_follow_the_multinomial_law():
+    # brute force on three samples: each resample mean is the mean of one of the
+    # 10 multisets of size 3, with probability 3!/(n1! n2! n3!) / 27
+    x = np.array([1.0, 10.0, 100.0])                 # |Tr|^2 values, distinct multiset means
+    tr = np.sqrt(x) + 0j
+    B = 40000
+    Fb = O.bootstrap(tr, np.zeros(3, dtype=np.int32), 1, 1, B, seed=12)[0, 0]
+    probs = {}
+    for c in itertools.product(range(3), repeat=3):
+        m = round(float(np.mean(x[list(c)])), 9)
+        probs[m] = probs.get(m, 0) + 1 / 27
+    assert len(probs) == 10
+    vals, counts = np.unique(np.round(Fb, 9), return_counts=True)
+    assert set(vals.tolist()) <= set(probs)
+    for v, c in zip(vals, counts):
+        p = probs[float(v)]
+        assert abs(c / B - p) < 5 * math.sqrt(p * (1 - p) / B), (v, c / B, p)
+
+
+def test_bootstrap_moments_match_plugin_standard_error():
+    rng = np.random.default_rng(3)
+    tr = rng.normal(size=400) + 1j * rng.normal(size=400)
+    B = 3000
+    Fb = O.bootstrap(tr, np.zeros(400, dtype=np.int32), 1, 2, B, seed=5)[0]
+    for k in (1, 2):
+        xk = np.abs(tr) ** (2 * k)
+        # E[mean of a resample] = sample mean; Var = (1/N) * (1/N) sum (x - xbar)^2
+        se_plug = xk.std(ddof=0) / math.sqrt(len(xk))
+        assert abs(Fb[k - 1].mean() - xk.mean()) < 5 * se_plug / math.sqrt(B)
+        assert abs(Fb[k - 1].std() / se_plug - 1.0) < 0.08
+
+
+def test_bootstrap_groups_are_separate_and_deterministic():
+    tr = np.array([1, 2, 3, 1000, 2000, 5], dtype=complex)
+    grp = np.array([0, 0, 0, 1, 1, -1], dtype=np.int32)   # -1: ignored
+    Fb = O.bootstrap(tr, grp, 3, 2, 200, seed=9)
+    assert Fb[0, 0].min() >= 1 and Fb[0, 0].max() <= 9          # group 0: |Tr|^2 in {1, 4, 9}
+    assert Fb[1, 0].min() >= 1000 ** 2 and Fb[1, 0].max() <= 2000 ** 2
+    assert np.all(np.isnan(Fb[2]))                                # empty group
+    assert np.array_equal(Fb, O.bootstrap(tr, grp, 3, 2, 200, seed=9), equal_nan=True)
+    assert not np.array_equal(Fb, O.bootstrap(tr, grp, 3, 2, 200, seed=10), equal_nan=True)
+    one = O.bootstrap(np.array([2 + 1j]), np.array([0], dtype=np.int32), 1, 3, 10, seed=1)[0]
+    assert np.allclose(one, np.array([[5.0], [25.0], [125.0]]))
+
+
+def test_epsilon_max_closed_form():
+    # n = 2 qubits, k = 2: d^k = 16, F - 2! = 1 -> epsilon_max = 16
+    assert abs(O.log10_epsilon_max(3.0, 2, 2) - math.log10(16.0)) < 1e-15
+    # n = 50: 2^100 sqrt(F - 2) in log10
+    assert abs(O.log10_epsilon_max(2.25, 2, 50) - (100 * math.log10(2) + math.log10(0.5))) < 1e-12
+    assert math.isnan(O.log10_epsilon_max(1.9, 2, 50))
+
+
+def test_design_layers_recovers_an_exact_exponential():
+    # F(l) - k! = A^2 exp(-2 l / C) exactly; the first depths are pushed out of the
+    # fitting region ((F - k!)/k! >= 5) and must not bias the fit
+    k, n, A, C = 2, 30, 3.0, 2.5
+    depths = list(range(1, 13))
+    F = [math.factorial(k) + A * A * math.exp(-2 * l / C) for l in depths]
+    F[0] = F[1] = 1e6
+    l_eps, A_fit, C_fit = O.design_layers(depths, F, k, n)
+    assert abs(A_fit - A) < 1e-9 and abs(C_fit - C) < 1e-12
+    assert abs(l_eps - C * (k * n * math.log(2) + math.log(A) + math.log(10))) < 1e-9
+    assert all(math.isnan(v) for v in O.design_layers([3], [2.5], k, n))
+
+
+def test_design_layers_on_the_theory_bound():
+    # Eq. theory_eq: F^(2) < 2 (1 + (2q/(q^2+1))^{2(l-1)})^{n_g - 1}; in the fitting
+    # region the bound decays as (4/5)^{4(l-1)} for q = 2, i.e. C = -2 / ln(16/25) per
+    # layer, and the layer count grows linearly in n (Eq. k=2)
+    def bound(n, l):
+        return 2 * (1 + (4 / 5) ** (2 * (l - 1))) ** (n // 2 - 1)
+    res = {}
+    for n in (20, 40, 80):
+        depths = list(range(2, 80))
+        l_eps, A_fit, C_fit = O.design_layers(depths, [bound(n, l) for l in depths], 2, n)
+        assert abs(C_fit - (-2 / math.log(16 / 25))) < 0.02 * C_fit
+        res[n] = l_eps
+    slope1 = (res[40] - res[20]) / 20
+    slope2 = (res[80] - res[40]) / 40
+    assert abs(slope1 / slope2 - 1) < 0.05       # linear in n
