@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-target", action="store_true", help="skip the GPU-seconds-to-1%% measurement")
+    ap.add_argument("--no-target", action="store_true",
+                    help="skip the GPU-seconds-to-1%% measurement, the bootstrap report and the large-T report")
     ap.add_argument("--no-cv", action="store_true", help="skip the control-variate report")
     ap.add_argument("--workload", default="brickwork", choices=sorted(WORKLOADS),
                     help="brickwork (the headline workload), hea (n=50, L=1..8) or local (n=20, T=20..100)")
@@ -228,6 +229,36 @@ def control_variate_report(fp, n_train=100_000, n_correct=10_000, m_surrogate=10
                       f"{n_correct} exact corrections; MLP 4nL-256-256-256-1 GELU, Adam; hidden layers "
                       f"as BF16 tcgen05 GEMMs with FP32 accumulation",
             "by_depth": out}
+
+
+def bootstrap_report(fp, pairs=200_000, B=300):
+    """The paper's uncertainty analysis at n = 50 (brickwork, l = 2..10): traces of
+    `pairs` pairs, B bootstrap resamples of F^(k) per depth on the GPU, then per
+    resample the exponential fit of F - k! over depth and the layers for a
+    0.1-approximate k-design; medians and 5-95 % ranges of the bootstrap."""
+    import numpy as np
+    import torch
+    ens = fp.Ensemble(0, 50, 2, 10, seed=WORK["seed"] + 1000, flags=fp.FLAG_TIMING)
+    tr = torch.empty(2 * pairs, dtype=torch.float64, device="cuda")
+    grp = torch.empty(pairs, dtype=torch.int32, device="cuda")
+    ens.trace_batch(0, pairs, fp.PREC_FP32, tr, None, grp)
+    ens.kernel_stats(reset=True)
+    K = 4
+    Fb = ens.bootstrap(tr, grp, pairs, K, B, seed=7)           # [9 depths, K, B]
+    ks = ens.kernel_stats(reset=True)
+    ens.close()
+    depths = np.arange(2, 11)
+    pct = lambda v: [float(np.nanpercentile(v, q)) for q in (5, 50, 95)]
+    out = {"pairs": pairs, "resamples": B, "bootstrap_gpu_ms": ks.ms[fp.K_BOOTSTRAP],
+           "F2_by_depth_p5_p50_p95": {int(l): pct(Fb[i, 1]) for i, l in enumerate(depths)},
+           "log10_eps_max_k2_median": {int(l): fp.epsilon_max_log10(float(np.median(Fb[i, 1])), 2, 50)
+                                       for i, l in enumerate(depths)}}
+    for k in (2, 3, 4):
+        ls = np.array([fp.design_layers(depths, Fb[:, k - 1, b], k, 50)[0] for b in range(B)])
+        ok = np.isfinite(ls)
+        out[f"layers_eps0.1_k{k}"] = {"p5_p50_p95": pct(ls[ok]) if ok.any() else None,
+                                      "fits_converged": int(ok.sum())}
+    return out
 
 
 def local_large_T_report(fp, per_T=12):
@@ -446,7 +477,9 @@ def main():
         line["gpu_s_to_1pct_F2"] = gpu_seconds_to_target(fp, mom, P, K, ng)
     if rank == 0 and world == 1 and not args.no_cv and WORK["name"] == "brickwork":
         line["control_variate"] = control_variate_report(fp)
-    if rank == 0 and world == 1 and WORK["name"] == "local":
+    if rank == 0 and world == 1 and not args.no_target and WORK["name"] == "brickwork":
+        line["bootstrap"] = bootstrap_report(fp)
+    if rank == 0 and world == 1 and not args.no_target and WORK["name"] == "local":
         line["local_large_T"] = local_large_T_report(fp)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and WORK["name"] == "brickwork":
         cores = os.cpu_count() or 1

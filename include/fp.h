@@ -107,6 +107,7 @@ enum {
     FP_K_SWEEP = 3,       /* generic boundary sweep + meet */
     FP_K_BRICK = 4,       /* brickwork boundary sweep + meet */
     FP_K_MOMENTS = 5,     /* Monte Carlo moments */
+    FP_K_BOOTSTRAP = 6,   /* bootstrap resampling */
     FP_K_CLASSES = 8
 };
 
@@ -205,6 +206,39 @@ fp_status fp_trace_batch(fp_ensemble *ens, uint64_t first, uint64_t count, int32
  * on the device; moments on host or device.  Deterministic (fixed tree). */
 fp_status fp_reduce_moments(fp_ensemble *ens, const double *tr, const int32_t *group,
                             uint64_t count, int32_t k_max, double *moments);
+
+/* Bootstrap distribution of F^(k) per group (paper: Supplementary,
+ * "Bootstrapping for uncertainty quantification"; the paper takes 300
+ * resamples and reports medians and the spread).  Each group's stored traces
+ * are resampled with replacement, as many draws as the group has pairs, and
+ * F^(k) = mean |Tr|^{2k} is evaluated on every resample.
+ *   tr      [2*count] doubles (re, im), group [count] int32 (entries outside
+ *           [0, n_groups) are ignored): host or device, e.g. the outputs of
+ *           fp_trace_batch;
+ *   F_boot  [n_groups * k_max * n_resamples] doubles, host or device:
+ *           F_boot[(g*k_max + k-1)*n_resamples + b]; NaN for an empty group.
+ * Draw i of resample b in group g takes position ((x >> 32) N_g) >> 32 of the
+ * group's pairs in increasing index order, x = word i mod 4 of the Philox
+ * block with counter {b, i / 4, g, 5} and key {seed, 0}.  Deterministic.
+ * count < 2^32; 1 <= n_resamples <= 2^31 - 1. */
+fp_status fp_bootstrap(fp_ensemble *ens, const double *tr, const int32_t *group, uint64_t count, int32_t k_max,
+                       int32_t n_resamples, uint64_t seed, double *F_boot);
+
+/* log10 of epsilon_max = d^k sqrt(F - k!) with d = q^n (paper: Sec. "Frame
+ * potential", Eq. epsilonmax): the ensemble is at least an
+ * epsilon_max-approximate k-design.  *log10_eps = NaN when F <= k!. */
+fp_status fp_epsilon_max(double F, int32_t k, int32_t n, int32_t q, double *log10_eps);
+
+/* Layers for an eps-approximate k-design from a depth sweep (paper: Sec.
+ * "Frame potential", Eqs. exponential and layers; fitting region from the
+ * supplementary "Choice of curve fitting region", dev_max = 5 there): depths
+ * with 0 < (F - k!)/k! < dev_max are kept, log(F - k!) = a + s l is fitted by
+ * least squares, then A = exp(a/2), C = -2/s and
+ *     l_eps = C (k n ln q + ln A + ln(1/eps)).
+ * Host arrays depths[n_depths], F[n_depths].  Outputs are NaN (status FP_OK)
+ * when fewer than two depths qualify or the slope is not negative. */
+fp_status fp_design_layers(int32_t n_depths, const double *depths, const double *F, int32_t k, int32_t n,
+                           int32_t q, double eps, double dev_max, double *l_eps, double *A, double *C);
 
 /* Monte Carlo frame potential.  Contracts pairs first, first+1, ... in batches
  * until every group's relative standard error of F^(2) (or of F^(1) when

@@ -20,15 +20,17 @@ PARALLEL, LOCAL, HEA = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_FP32_RAW = 0, 1, 2
 FLAG_SELF_PAIR, FLAG_DIAGONAL_GATES, FLAG_GENERIC_ONLY, FLAG_TIMING, FLAG_NO_GRAPHS = 1, 2, 4, 8, 16
 FLAG_SKIP_INFEASIBLE = 32
-K_SAMPLE, K_MERGE, K_TABLES, K_SWEEP, K_BRICK, K_MOMENTS, K_CLASSES = 0, 1, 2, 3, 4, 5, 8
-K_NAMES = {0: "sample", 1: "merge", 2: "tables", 3: "sweep_generic", 4: "sweep_brick", 5: "moments"}
+K_SAMPLE, K_MERGE, K_TABLES, K_SWEEP, K_BRICK, K_MOMENTS, K_BOOTSTRAP, K_CLASSES = 0, 1, 2, 3, 4, 5, 6, 8
+K_NAMES = {0: "sample", 1: "merge", 2: "tables", 3: "sweep_generic", 4: "sweep_brick", 5: "moments",
+           6: "bootstrap"}
 MAX_STATE_BITS = 24
 STATUS = {0: "FP_OK", -1: "FP_ERR_ARG", -2: "FP_ERR_CUDA", -3: "FP_ERR_OOM", -4: "FP_ERR_TIMEOUT",
           -5: "FP_ERR_INFEASIBLE"}
 
 EXPORTED = ["fp_ensemble_create", "fp_ensemble_destroy", "fp_groups", "fp_pair_groups", "fp_export_gates",
             "fp_trace_batch", "fp_reduce_moments", "fp_frame_potential", "fp_kernel_stats_get",
-            "fp_trace_brick_static", "fp_cv_frame_potential", "fp_gemm_bf16", "fp_last_error"]
+            "fp_trace_brick_static", "fp_cv_frame_potential", "fp_gemm_bf16", "fp_bootstrap", "fp_epsilon_max",
+            "fp_design_layers", "fp_last_error"]
 
 
 class FpError(RuntimeError):
@@ -99,6 +101,10 @@ def load(path: str = LIB_PATH):
     L.fp_cv_frame_potential.argtypes = [vp, P(CvConfig), P(CvResult)]
     i32 = ctypes.c_int32
     L.fp_gemm_bf16.argtypes = [i32, i32, i32, vp, i32, vp, i32, vp, i32, vp, vp, vp, vp, vp]
+    f64, u64 = ctypes.c_double, ctypes.c_uint64
+    L.fp_bootstrap.argtypes = [vp, vp, vp, u64, i32, i32, u64, vp]
+    L.fp_epsilon_max.argtypes = [f64, i32, i32, i32, P(f64)]
+    L.fp_design_layers.argtypes = [i32, vp, vp, i32, i32, i32, f64, f64, P(f64), P(f64), P(f64)]
     L.fp_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name not in ("fp_ensemble_destroy", "fp_last_error"):
@@ -143,6 +149,24 @@ def gemm_bf16(A, Bt, bias=None, mode=0, Z=None, C=None, C_bf16=None, Ct_bf16=Non
     st = None if stream is None else ctypes.c_void_p(stream)
     _check(load().fp_gemm_bf16(M, N, K, _ptr(A), A.stride(0), _ptr(Bt), Bt.stride(0), _ptr(bias), mode, _ptr(Z),
                                _ptr(C), _ptr(C_bf16), _ptr(Ct_bf16), st))
+
+
+def epsilon_max_log10(F, k, n, q=2):
+    """log10 of epsilon_max = q^{nk} sqrt(F - k!) (fp_epsilon_max); NaN when F <= k!."""
+    out = ctypes.c_double()
+    _check(load().fp_epsilon_max(float(F), k, n, q, ctypes.byref(out)))
+    return out.value
+
+
+def design_layers(depths, F, k, n, q=2, eps=0.1, dev_max=5.0):
+    """(l_eps, A, C) of the exponential fit of F - k! over depths (fp_design_layers)."""
+    import numpy as np
+    d = np.ascontiguousarray(depths, dtype=np.float64)
+    f = np.ascontiguousarray(F, dtype=np.float64)
+    le, A, C = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().fp_design_layers(len(d), _ptr(d), _ptr(f), k, n, q, eps, dev_max, ctypes.byref(le),
+                                   ctypes.byref(A), ctypes.byref(C)))
+    return le.value, A.value, C.value
 
 
 class Ensemble:
@@ -226,6 +250,17 @@ class Ensemble:
         _check(load().fp_trace_batch(self._h, first, count, prec, _ptr(tr), _ptr(kappa), _ptr(err), _ptr(group)))
         out = (tr[0::2] + 1j * tr[1::2], kappa, group) if own else (tr, kappa, group)
         return out + (err,) if with_err else out
+
+    def bootstrap(self, tr, group, count, k_max, n_resamples=300, seed=1, out=None):
+        """Bootstrap distribution of F^(k) per group (fp_bootstrap): tr [2*count] float64 and
+        group [count] int32 (host or device); returns (or fills) [n_groups, k_max, n_resamples]."""
+        import numpy as np
+        ng = len(self.groups())
+        own = out is None
+        if own:
+            out = np.zeros(ng * k_max * n_resamples, dtype=np.float64)
+        _check(load().fp_bootstrap(self._h, _ptr(tr), _ptr(group), count, k_max, n_resamples, seed, _ptr(out)))
+        return out.reshape(ng, k_max, n_resamples) if own else out
 
     def reduce_moments(self, tr_dev, group_dev, count, k_max, out):
         _check(load().fp_reduce_moments(self._h, _ptr(tr_dev), _ptr(group_dev), count, k_max, _ptr(out)))

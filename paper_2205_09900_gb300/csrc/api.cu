@@ -135,6 +135,8 @@ struct fp_ensemble {
     // left uncontracted because their boundary exceeds FP_MAX_STATE_BITS
     std::vector<uint64_t> skipped;
     DBuf d_skip;
+    // bootstrap buffers
+    DBuf d_boot_tr, d_boot_members, d_boot_off, d_boot_xs, d_boot_out;
     // resident clusters of the generic sweep per cluster size (index log2 cs) and precision; -1 unknown
     int sweep_slots[5][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};
 };
@@ -964,6 +966,50 @@ fp_status fp_reduce_moments(fp_ensemble *ens, const double *tr, const int32_t *g
         CK(t.stop((double)count));
     }
     fp_status s = copy_out(ens, moments, ens->d_moments.p, (size_t)ng * nv * sizeof(double));
+    if (s != FP_OK) return s;
+    CK(cudaStreamSynchronize(ens->st));
+    return FP_OK;
+}
+
+fp_status fp_bootstrap(fp_ensemble *ens, const double *tr, const int32_t *group, uint64_t count, int32_t k_max,
+                       int32_t n_resamples, uint64_t seed, double *F_boot) {
+    if (!ens || !tr || !group || !F_boot) return fail(FP_ERR_ARG, "null argument");
+    if (k_max < 1 || k_max > FP_MAX_KMAX) return fail(FP_ERR_ARG, "k_max = %d outside [1, %d]", k_max, FP_MAX_KMAX);
+    if (n_resamples < 1) return fail(FP_ERR_ARG, "n_resamples = %d must be positive", n_resamples);
+    if (count >= (1ull << 32)) return fail(FP_ERR_ARG, "count must be below 2^32");
+    const int ng = ens->n_groups;
+    // group lists in increasing pair order (a stable counting sort on the host)
+    std::vector<int32_t> hg(count);
+    if (count) CK(cudaMemcpyAsync(hg.data(), group, count * sizeof(int32_t), cudaMemcpyDefault, ens->st));
+    CK(cudaStreamSynchronize(ens->st));
+    std::vector<uint64_t> off(ng + 1, 0);
+    for (uint64_t i = 0; i < count; ++i)
+        if (hg[i] >= 0 && hg[i] < ng) ++off[hg[i] + 1];
+    for (int g = 0; g < ng; ++g) off[g + 1] += off[g];
+    std::vector<uint32_t> members(std::max<uint64_t>(off[ng], 1));
+    {
+        std::vector<uint64_t> pos(off.begin(), off.end() - 1);
+        for (uint64_t i = 0; i < count; ++i)
+            if (hg[i] >= 0 && hg[i] < ng) members[pos[hg[i]]++] = (uint32_t)i;
+    }
+    const double *dtr = tr;
+    if (!is_device_ptr(tr)) {
+        CK(ens->d_boot_tr.reserve(std::max<uint64_t>(count, 1) * 2 * sizeof(double)));
+        if (count) CK(cudaMemcpyAsync(ens->d_boot_tr.p, tr, count * 2 * sizeof(double), cudaMemcpyHostToDevice, ens->st));
+        dtr = ens->d_boot_tr.as<double>();
+    }
+    CK(upload(ens->d_boot_members, members, ens->st));
+    CK(upload(ens->d_boot_off, off, ens->st));
+    CK(ens->d_boot_xs.reserve(members.size() * sizeof(double)));
+    const size_t nout = (size_t)ng * k_max * n_resamples;
+    CK(ens->d_boot_out.reserve(nout * sizeof(double)));
+    {
+        KTimer t(ens, FP_K_BOOTSTRAP);
+        CK(launch_bootstrap(dtr, ens->d_boot_members.as<uint32_t>(), off[ng], ens->d_boot_off.as<uint64_t>(), ng, k_max,
+                            n_resamples, seed, ens->d_boot_xs.as<double>(), ens->d_boot_out.as<double>(), ens->st));
+        CK(t.stop((double)off[ng] * n_resamples));
+    }
+    fp_status s = copy_out(ens, F_boot, ens->d_boot_out.p, nout * sizeof(double));
     if (s != FP_OK) return s;
     CK(cudaStreamSynchronize(ens->st));
     return FP_OK;

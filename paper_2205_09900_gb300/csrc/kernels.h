@@ -44,6 +44,11 @@ cudaError_t launch_moments(const double *tr, const int32_t *group, uint64_t coun
                            int n_groups, double *partials, int nblocks, double *out,
                            cudaStream_t st);
 int moments_blocks(uint64_t count);
+// Bootstrap of F^(k): members lists the pairs of group g at [goff[g], goff[g+1]);
+// xs (n_members doubles) is scratch; out[(g*k_max + k-1)*B + b].
+cudaError_t launch_bootstrap(const double *tr, const uint32_t *members, uint64_t n_members, const uint64_t *goff,
+                             int n_groups, int k_max, int B, uint64_t seed, double *xs, double *out,
+                             cudaStream_t st);
 // Brickwork fast path: maps, then either the shared-memory sweep (tile_bits == 0)
 // or init + light-cone passes + dot.  `states` holds npairs x 2 x 2^N
 // amplitudes (tiled) or npairs x 2^N (shared-memory path, left boundaries).

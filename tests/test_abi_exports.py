@@ -64,3 +64,26 @@ def test_gemm_argument_checks_without_gpu(lib):
     assert f(4, 16, 64, fake, 64, fake, 64, None, 2, None, fake, None, None, None) == -1   # mode 2 needs Z
     assert f(4, 16, 64, vp((1 << 20) + 8), 64, fake, 64, None, 0, None, fake, None, None, None) == -1  # alignment
     assert f(4, 16, 64, fake, 64, fake, 64, None, 0, None, None, None, None, None) == -1   # no output
+
+
+def test_derived_outputs_match_the_oracle_without_gpu(lib):
+    # epsilon_max and the design-layer fit are host code behind the C ABI
+    import math
+
+    import numpy as np
+
+    import oracle as O
+    import paper_2205_09900_gb300 as fp
+    for F, k, n in [(3.0, 2, 2), (2.25, 2, 50), (1.5, 2, 50), (6.2, 3, 20), (30.0, 4, 12)]:
+        a, b = fp.epsilon_max_log10(F, k, n), O.log10_epsilon_max(F, k, n)
+        assert (math.isnan(a) and math.isnan(b)) or abs(a - b) <= 1e-12 * abs(b)
+    rng = np.random.default_rng(4)
+    for k in (1, 2, 3):
+        for _ in range(20):
+            depths = np.arange(2, 14)
+            F = math.factorial(k) * (1 + np.exp(rng.normal(1.0, 1.0) - depths / rng.uniform(1, 4)
+                                                + rng.normal(0, 0.3, size=len(depths))))
+            got = fp.design_layers(depths, F, k, 50)
+            ref = O.design_layers(depths, F, k, 50)
+            for g, r in zip(got, ref):
+                assert (math.isnan(g) and math.isnan(r)) or abs(g - r) <= 1e-9 * abs(r), (got, ref)

@@ -353,10 +353,13 @@ def test_brick_small_and_odd_chains(fp, n, l):
 
 
 @pytest.mark.parametrize("l,prec", [(8, 2), (10, 2), (6, 0)])
-def test_graph_replay_matches_direct_launches(fp, l, prec):
+def test_graph_replay_matches_direct_launches(fp, l, prec, tmp_path, monkeypatch):
     # the same sub-batch shape three times: the first runs directly and is
     # captured, the next two replay the CUDA graph; results are bit-identical
-    # to an ensemble that never uses graphs
+    # to an ensemble that never uses graphs.  Both ensembles share one autotune
+    # cache, so they run the same kernel variant (the tuner's timing-based pick
+    # could otherwise differ, and with it the FP32 rounding).
+    monkeypatch.setenv("FP_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
     a = fp.Ensemble(0, 30, l, l, seed=5)
     b = fp.Ensemble(0, 30, l, l, seed=5, flags=fp.FLAG_NO_GRAPHS)
     for first in (0, 1000, 2000):
@@ -436,3 +439,23 @@ def test_generic_sweep_cluster_sizes(fp, cluster, monkeypatch):
     assert rel_err(tr, ref).max() <= TOL64
     tr32, _, _ = ens.trace_batch(0, N, fp.PREC_FP32_RAW)
     assert np.abs(tr32 - ref).max() <= TOL32
+
+
+def test_bootstrap_matches_oracle(fp):
+    # traces of a mixed-depth brickwork batch; the GPU bootstrap against the
+    # oracle's draw-by-draw resampling on the same traces (same Philox draws)
+    import torch
+    ens, od = make(fp, "parallel", 12, 2, 5, seed=17)
+    N, K, B = 3000, 3, 64
+    tr, kap, grp = ens.trace_batch(0, N, fp.PREC_FP64)
+    t = np.ascontiguousarray(np.stack([tr.real, tr.imag], axis=1).reshape(-1))
+    grp[::97] = -1                                   # ignored entries
+    ref = O.bootstrap(tr, grp, 4, K, B, seed=23)
+    got = ens.bootstrap(t, grp, N, K, B, seed=23)   # host inputs
+    assert np.allclose(got, ref, rtol=1e-12, atol=0, equal_nan=True)
+    td, gd = torch.from_numpy(t).cuda(), torch.from_numpy(grp).cuda()
+    out = torch.empty(4 * K * B, dtype=torch.float64, device="cuda")
+    ens.bootstrap(td, gd, N, K, B, seed=23, out=out)   # device inputs and output
+    assert np.allclose(out.cpu().numpy().reshape(4, K, B), ref, rtol=1e-12, atol=0, equal_nan=True)
+    # deterministic
+    assert np.array_equal(ens.bootstrap(t, grp, N, K, B, seed=23), got, equal_nan=True)
