@@ -24,7 +24,7 @@ _LIB_PATH = os.path.join(_HERE, "libfp_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PARALLEL, LOCAL, HEA = 0, 1, 2
+PARALLEL, LOCAL, HEA, HEA_CNOT, HEA_CZ = 0, 1, 2, 3, 4
 OP_GATE2, OP_GATE1, OP_DIAG2 = 0, 1, 2
 
 
@@ -84,6 +84,8 @@ def lib():
                                         ctypes.c_int, ctypes.c_int, ctypes.c_uint64, P(ctypes.c_double)]
             L.orc_bootstrap.restype = None
             L.orc_weingarten_f2_brickwork.restype = ctypes.c_double
+            L.orc_weingarten_fk_brickwork.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.orc_weingarten_fk_brickwork.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -119,7 +121,7 @@ def pair_depth(d, pair):
 
 def circuit(d, pair, which):
     """Gate list of U (which=0) or V (which=1) of a pair, as (kind, q, matrix) tuples."""
-    cap = 4 + max(d.depth_max, d.T_max) * 2 * d.n
+    cap = 4 + (max(d.depth_max, d.T_max) + 1) * 3 * d.n
     ops = (Op * cap)()
     cnt = lib().orc_circuit(ctypes.byref(d), pair, which, ops, cap)
     if cnt < 0:
@@ -186,6 +188,11 @@ def moments(tr, kmax):
 
 def weingarten_f2_brickwork(n, l):
     return float(lib().orc_weingarten_f2_brickwork(n, l))
+
+
+def weingarten_fk_brickwork(n, l, k):
+    """Exact ensemble F^(k) (k = 2, 3) of brickwork circuits."""
+    return float(lib().orc_weingarten_fk_brickwork(n, l, k))
 
 
 def bootstrap(tr, group, n_groups, kmax, B, seed):

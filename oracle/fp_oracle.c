@@ -157,6 +157,54 @@ int orc_circuit(const orc_desc *d, uint64_t pair, int which, orc_op *ops, int ma
                 set_c(op, 0, 1); set_c(op, 1, 1); set_c(op, 2, 1); set_c(op, 3, -1);
             }
         }
+    } else if (d->kind == ORC_HEA_CNOT || d->kind == ORC_HEA_CZ) {
+        /* the wall of RY(pi/4) = cos(pi/8) I - i sin(pi/8) Y */
+        for (int q = 0; q < n; ++q) {
+            if (cnt >= max_ops) return -1;
+            orc_op *op = &ops[cnt++];
+            memset(op, 0, sizeof *op);
+            op->kind = ORC_OP_GATE1; op->q = q;
+            double c = cos(ORC_PI / 8), s = sin(ORC_PI / 8);
+            set_c(op, 0, c);  set_c(op, 1, -s);
+            set_c(op, 2, s);  set_c(op, 3, c);
+        }
+        const cplx pauli[3][4] = {{0, 1, 1, 0}, {0, -I, I, 0}, {1, 0, 0, -1}};
+        for (int t = 0; t < depth; ++t) {
+            for (int q = 0; q < n; ++q) {
+                uint64_t x[4];
+                if (cnt >= max_ops) return -1;
+                draw(d->seed, (uint64_t)t, (uint64_t)q, pair, (uint64_t)w, x);
+                double th = 2.0 * ORC_PI * unit53(x[0]);
+                int axis = (int)(((x[1] >> 32) * 3u) >> 32);
+                orc_op *op = &ops[cnt++];
+                memset(op, 0, sizeof *op);
+                op->kind = ORC_OP_GATE1; op->q = q;
+                /* exp(-i theta P / 2) = cos(theta/2) I - i sin(theta/2) P, as P^2 = I */
+                for (int k = 0; k < 4; ++k) {
+                    cplx id = (k == 0 || k == 3) ? 1 : 0;
+                    set_c(op, k, cos(th / 2) * id - I * sin(th / 2) * pauli[axis][k]);
+                }
+            }
+            for (int par = 0; par < 2; ++par)
+                for (int b = par; b <= n - 2; b += 2) {
+                    if (cnt >= max_ops) return -1;
+                    orc_op *op = &ops[cnt++];
+                    memset(op, 0, sizeof *op);
+                    op->q = b;
+                    if (d->kind == ORC_HEA_CZ) {
+                        op->kind = ORC_OP_DIAG2;
+                        set_c(op, 0, 1); set_c(op, 1, 1); set_c(op, 2, 1); set_c(op, 3, -1);
+                    } else {
+                        /* CNOT, control b (the more significant index bit), target b+1:
+                           |c t> -> |c, t xor c> */
+                        op->kind = ORC_OP_GATE2;
+                        for (int ct = 0; ct < 4; ++ct) {
+                            int c = ct >> 1, tt = ct & 1;
+                            set_c(op, 4 * ((c << 1) | (tt ^ c)) + ct, 1);
+                        }
+                    }
+                }
+        }
     } else {
         return -2;
     }
@@ -404,7 +452,8 @@ int orc_trace_pair(const orc_desc *d, uint64_t pair, int method, double tr[2])
     int cap;
     if (d->kind == ORC_PARALLEL) cap = depth * d->n;
     else if (d->kind == ORC_LOCAL) cap = depth;
-    else cap = depth * 2 * d->n;
+    else if (d->kind == ORC_HEA) cap = depth * 2 * d->n;
+    else cap = (depth + 1) * 3 * d->n;
     cap += 4;
     orc_op *U = malloc(sizeof(orc_op) * cap), *V = malloc(sizeof(orc_op) * cap);
     if (!U || !V) { free(U); free(V); return -3; }
@@ -524,6 +573,153 @@ void orc_bootstrap(const double *tr, const int32_t *group, int64_t count, int n_
         }
         free(members);
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact ensemble F^(k), k = 2 or 3, of brickwork circuits: the same         */
+/* statistical-mechanics model as orc_weingarten_f2_brickwork with the       */
+/* pairings running over the permutation group S_k.  Averaging a Haar U(d)   */
+/* gate over k copies of U and k of U^* gives                                */
+/*   sum_{sigma, tau in S_k} Wg(sigma^-1 tau, d) |sigma>><<tau|              */
+/* with the Weingarten function of U(d), d = 4 (Collins 2003):               */
+/*   k = 2: Wg(e) = 1/(d^2-1), Wg(2-cycle) = -1/(d(d^2-1));                  */
+/*   k = 3: Wg(e) = (d^2-2)/(d(d^2-1)(d^2-4)), Wg(2-cycle) =                 */
+/*          -1/((d^2-1)(d^2-4)), Wg(3-cycle) = 2/(d(d^2-1)(d^2-4)).          */
+/* Along a qubit wire, the output pairing sigma_a of a gate meets the input  */
+/* pairing tau_b of the next gate on the wire: q^{#cycles(sigma_a^-1 tau_b)} */
+/* with q = 2; a qubit touched by no gate gives q^{2k}.  Summed with the     */
+/* same explicit transfer matrix over bonds as the k = 2 routine.            */
+/* ------------------------------------------------------------------------ */
+static int perms_of(int k, int P[6][3])
+{
+    int np = 0;
+    for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b)
+            for (int c = 0; c < k; ++c) {
+                int v[3] = {a, b, c};
+                int ok = 1;
+                for (int i = 0; i < k; ++i)
+                    for (int j = i + 1; j < k; ++j) if (v[i] == v[j]) ok = 0;
+                if (k < 3 && c != 0) ok = 0;
+                if (k < 2 && b != 0) ok = 0;
+                if (!ok) continue;
+                for (int i = 0; i < 3; ++i) P[np][i] = v[i];
+                ++np;
+            }
+    return np;
+}
+
+static int cycles_of(const int *a, const int *b, int k)   /* #cycles of a^-1 b */
+{
+    int ainv[3], seen[3] = {0, 0, 0}, c = 0;
+    for (int i = 0; i < k; ++i) ainv[a[i]] = i;
+    for (int i = 0; i < k; ++i) {
+        if (seen[i]) continue;
+        ++c;
+        for (int j = i; !seen[j]; j = ainv[b[j]]) seen[j] = 1;
+    }
+    return c;
+}
+
+double orc_weingarten_fk_brickwork(int n, int l, int k)
+{
+    if (n < 2 || l < 1 || k < 2 || k > 3) return NAN;
+    const double d = 4.0;
+    int Pm[6][3];
+    const int np = perms_of(k, Pm), sg = np * np;   /* (sigma, tau) states per gate */
+    double wg_by_cycles[4] = {0, 0, 0, 0};
+    if (k == 2) {
+        wg_by_cycles[2] = 1.0 / (d * d - 1);
+        wg_by_cycles[1] = -1.0 / (d * (d * d - 1));
+    } else {
+        wg_by_cycles[3] = (d * d - 2) / (d * (d * d - 1) * (d * d - 4));
+        wg_by_cycles[2] = -1.0 / ((d * d - 1) * (d * d - 4));
+        wg_by_cycles[1] = 2.0 / (d * (d * d - 1) * (d * d - 4));
+    }
+    double wg[36], link[6][6];
+    for (int s = 0; s < np; ++s)
+        for (int t = 0; t < np; ++t) {
+            int c = cycles_of(Pm[s], Pm[t], k);
+            wg[s * np + t] = wg_by_cycles[c];
+            link[s][t] = ldexp(1.0, c);
+        }
+    const double idle = ldexp(1.0, 2 * k);
+    int P = (l == 1) ? 1 : 2 * (l - 1), nb = n - 1;
+    int *g_of_bond = calloc(nb, sizeof(int));
+    int **times = calloc(nb, sizeof(int *));
+    for (int b = 0; b < nb; ++b) {
+        times[b] = malloc(sizeof(int) * P);
+        for (int t = 0; t < P; ++t) {
+            int par = (l == 1) ? 0 : (t + 1) % 2;
+            if (b % 2 == par) times[b][g_of_bond[b]++] = t;
+        }
+    }
+    int gmax = 0;
+    for (int b = 0; b < nb; ++b) if (g_of_bond[b] > gmax) gmax = g_of_bond[b];
+    size_t S = 1;
+    for (int j = 0; j < gmax; ++j) S *= (size_t)sg;
+    double *v = malloc(sizeof(double) * S), *w = malloc(sizeof(double) * S);
+    /* configuration c of a bond: digit j (base sg) = sigma_j * np + tau_j of gate j */
+#define DIGIT(c, j) ((int)(((c) / pw[j]) % (size_t)sg))
+    size_t pw[16];
+    pw[0] = 1;
+    for (int j = 1; j < 16; ++j) pw[j] = pw[j - 1] * (size_t)sg;
+    {   /* qubit 0: links among bond-0 gates */
+        int g0 = g_of_bond[0];
+        for (size_t c = 0; c < pw[g0]; ++c) {
+            double p = g0 == 0 ? idle : 1.0;
+            for (int j = 0; j < g0; ++j) {
+                int dj = DIGIT(c, j), dn = DIGIT(c, (j + 1) % g0);
+                p *= wg[dj] * link[dj / np][dn % np];
+            }
+            v[c] = p;
+        }
+    }
+    for (int b = 1; b < nb; ++b) {
+        int ga = g_of_bond[b - 1], gb = g_of_bond[b], tot = ga + gb;
+        int *who = malloc(sizeof(int) * (tot > 0 ? tot : 1)), *idx = malloc(sizeof(int) * (tot > 0 ? tot : 1));
+        int ia = 0, ib = 0, kk = 0;
+        while (ia < ga || ib < gb) {
+            if (ib >= gb || (ia < ga && times[b - 1][ia] < times[b][ib])) { who[kk] = 0; idx[kk++] = ia++; }
+            else { who[kk] = 1; idx[kk++] = ib++; }
+        }
+        for (size_t cb = 0; cb < pw[gb]; ++cb) {
+            double gw = 1;
+            for (int j = 0; j < gb; ++j) gw *= wg[DIGIT(cb, j)];
+            double acc = 0;
+            for (size_t ca = 0; ca < pw[ga]; ++ca) {
+                double p = v[ca];
+                if (tot == 0) p *= idle;
+                for (int j = 0; j < tot; ++j) {
+                    int jn = (j + 1) % tot;
+                    int dj = who[j] ? DIGIT(cb, idx[j]) : DIGIT(ca, idx[j]);
+                    int dn = who[jn] ? DIGIT(cb, idx[jn]) : DIGIT(ca, idx[jn]);
+                    p *= link[dj / np][dn % np];
+                }
+                acc += p;
+            }
+            w[cb] = acc * gw;
+        }
+        double *tmp = v; v = w; w = tmp;
+        free(who); free(idx);
+    }
+    double result = 0;
+    {   /* qubit n-1: links among bond n-2 gates */
+        int g = g_of_bond[nb - 1];
+        for (size_t c = 0; c < pw[g]; ++c) {
+            double p = v[c];
+            if (g == 0) p *= idle;
+            for (int j = 0; j < g; ++j) {
+                int dj = DIGIT(c, j), dn = DIGIT(c, (j + 1) % g);
+                p *= link[dj / np][dn % np];
+            }
+            result += p;
+        }
+    }
+#undef DIGIT
+    for (int b = 0; b < nb; ++b) free(times[b]);
+    free(times); free(g_of_bond); free(v); free(w);
+    return result;
 }
 
 /* ------------------------------------------------------------------------ */

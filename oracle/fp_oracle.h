@@ -17,8 +17,8 @@
  * What it computes (paper sections cited per function in fp_oracle.c):
  *   Tr(U^dagger V) = sum_{ij} conj(U_ij) V_ij                (Sec. "Frame potential")
  *   F^(k) ~= (1/N) sum |Tr(U^dagger V)|^{2k}                 (Sec. "Algorithm description")
- *   exact ensemble F^(2) of brickwork circuits by a Weingarten
- *   transfer matrix                                           (Eq. theory_eq context)
+ *   exact ensemble F^(2) and F^(3) of brickwork circuits by a
+ *   Weingarten transfer matrix                                (Eq. theory_eq context)
  *   bootstrap distribution of F^(k)                           (Supplementary, "Bootstrapping
  *                                                              for uncertainty quantification")
  *
@@ -45,6 +45,9 @@
  *       index = ((x0 >> 32) * choices) >> 32.
  *     HEA angles of circuit w, layer t (0-based), qubit q: c0 = t, c1 = q,
  *       stream = w; theta = 2 pi (x0 >> 11) 2^-53, phi = 2 pi (x1 >> 11) 2^-53.
+ *     Paper-HEA rotation of circuit w, layer t, qubit q: the same block;
+ *       theta = 2 pi (x0 >> 11) 2^-53, Pauli axis ((x1 >> 32) * 3) >> 32
+ *       (0: X, 1: Y, 2: Z).
  */
 #ifndef FP_ORACLE_H
 #define FP_ORACLE_H
@@ -54,13 +57,18 @@
 extern "C" {
 #endif
 
-enum { ORC_PARALLEL = 0, ORC_LOCAL = 1, ORC_HEA = 2 };
+/* ORC_HEA_CNOT / ORC_HEA_CZ: the paper's hardware-efficient ansatz (Fig. 2c):
+ * a fixed RY(pi/4) wall, then per layer exp(-i theta P / 2) on every qubit
+ * (P uniform in {X, Y, Z}, theta uniform in [0, 2 pi)) and two entangling
+ * walls, on the even bonds and then on the odd bonds, of CNOT (control b,
+ * target b+1) or CZ. */
+enum { ORC_PARALLEL = 0, ORC_LOCAL = 1, ORC_HEA = 2, ORC_HEA_CNOT = 3, ORC_HEA_CZ = 4 };
 enum { ORC_OP_GATE2 = 0, ORC_OP_GATE1 = 1, ORC_OP_DIAG2 = 2 };
 
 typedef struct {
-    int32_t kind;            /* ORC_PARALLEL, ORC_LOCAL, ORC_HEA */
+    int32_t kind;            /* ORC_PARALLEL, ORC_LOCAL, ORC_HEA, ORC_HEA_CNOT, ORC_HEA_CZ */
     int32_t n;               /* qubits on an open chain */
-    int32_t depth_min;       /* l (parallel) or L (HEA) */
+    int32_t depth_min;       /* l (parallel) or L (the HEA kinds) */
     int32_t depth_max;
     int32_t T_min, T_max, T_step;   /* local circuits: gate count choices */
     int32_t self_pair;       /* nonzero: V := U (test invariant Tr = 2^n) */
@@ -86,6 +94,9 @@ int    orc_trace_batch(const orc_desc *d, uint64_t first, uint64_t count, int me
                        int nthreads, double *tr);
 void   orc_moments(const double *tr, int64_t N, int kmax, double *F, double *se);
 double orc_weingarten_f2_brickwork(int n, int l);
+/* Exact ensemble F^(k), k = 2 or 3, of brickwork circuits (the same model
+ * over S_k pairings); NaN for other k. */
+double orc_weingarten_fk_brickwork(int n, int l, int k);
 /* Bootstrap distribution of F^(k) per group (Supplementary "Bootstrapping for
  * uncertainty quantification"): every group's N_g traces are resampled N_g
  * times with replacement, B times.  Draw i of resample b in group g takes

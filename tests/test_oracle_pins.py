@@ -92,6 +92,7 @@ def test_single_haar_gate_frame_potential():
 @pytest.mark.parametrize("kind,n,dmin,dmax,extra", [
     (O.PARALLEL, 6, 1, 5, {}), (O.PARALLEL, 7, 1, 4, {}), (O.PARALLEL, 8, 4, 4, {}),
     (O.HEA, 5, 1, 4, {}), (O.HEA, 6, 2, 3, {}),
+    (O.HEA_CNOT, 5, 1, 4, {}), (O.HEA_CNOT, 6, 2, 3, {}), (O.HEA_CZ, 6, 1, 4, {}),
     (O.LOCAL, 6, 1, 1, dict(T_min=4, T_max=24, T_step=4)),
     (O.LOCAL, 7, 1, 1, dict(T_min=10, T_max=30, T_step=10)),
 ])
@@ -128,7 +129,8 @@ def _dense_from_gates(n, gates):
     return U
 
 
-@pytest.mark.parametrize("kind,n,depth", [(O.PARALLEL, 3, 3), (O.PARALLEL, 4, 2), (O.HEA, 3, 2)])
+@pytest.mark.parametrize("kind,n,depth", [(O.PARALLEL, 3, 3), (O.PARALLEL, 4, 2), (O.HEA, 3, 2),
+                                           (O.HEA_CNOT, 3, 2), (O.HEA_CZ, 4, 2)])
 def test_ancilla_amplitude_identity(kind, n, depth):
     d = O.desc(kind, n, depth, seed=5)
     U = _dense_from_gates(n, O.circuit(d, 0, 0))
@@ -171,6 +173,7 @@ def test_fig3b_tensor_identity():
 # Invariants and closed forms at full size (n = 50).
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("kind,n,depth,extra", [(O.PARALLEL, 50, 5, {}), (O.HEA, 50, 4, {}),
+                                                (O.HEA_CNOT, 50, 3, {}), (O.HEA_CZ, 50, 4, {}),
                                                 (O.LOCAL, 20, 1, dict(T_min=40, T_max=40))])
 def test_self_pair_trace_is_dimension(kind, n, depth, extra):
     # Tr(U^dagger U) = Tr(I) = 2^n
@@ -278,6 +281,30 @@ def test_weingarten_matches_monte_carlo(n, l):
     assert abs(F[1] - exact) < 5 * se[1], (F[1], exact, se[1])
 
 
+def test_weingarten_k3_closed_forms():
+    # k = 3 over S_3 pairings: n = 2 is one Haar U(4) gate at any depth, F^(3) = 3! = 6
+    # (k <= d); l = 1 is a product of floor(n/2) independent gates and, for odd n, one
+    # idle qubit with Tr(I_2)^6 = 64; the k = 2 specialisation reproduces the pinned
+    # F^(2) routine.
+    for l in range(1, 5):
+        assert abs(O.weingarten_fk_brickwork(2, l, 3) - 6.0) < 1e-12
+    for n in range(2, 10):
+        exact = 6.0 ** (n // 2) * 64.0 ** (n % 2)
+        assert abs(O.weingarten_fk_brickwork(n, 1, 3) - exact) < 1e-9 * exact
+    for n, l in [(4, 3), (5, 2), (7, 4), (50, 5)]:
+        a, b = O.weingarten_fk_brickwork(n, l, 2), O.weingarten_f2_brickwork(n, l)
+        assert abs(a - b) < 1e-12 * b
+
+
+@pytest.mark.parametrize("n,l", [(4, 2), (5, 3)])
+def test_weingarten_k3_matches_monte_carlo(n, l):
+    d = O.desc(O.PARALLEL, n, l, seed=300 + 10 * n + l)
+    tr = O.trace_batch(d, 0, 200000, "dense", threads=8)
+    F, se = O.moments(tr, 3)
+    exact = O.weingarten_fk_brickwork(n, l, 3)
+    assert abs(F[2] - exact) < 5 * se[2], (F[2], exact, se[2])
+
+
 def test_hea_two_qubits_one_layer_moments():
     # per qubit |2 cos(a/2) cos(b/2)|^{2k} averages to (C(2k,k)/2^k)^2 / ... ->
     # E = (binom(2k,k)^2 / 4^k) per qubit; two qubits multiply.
@@ -286,6 +313,86 @@ def test_hea_two_qubits_one_layer_moments():
     F, se = O.moments(tr, 3)
     for k in range(1, 4):
         exact = (math.comb(2 * k, k) ** 2 / 4 ** k) ** 2
+        assert abs(F[k - 1] - exact) < 5 * se[k - 1], (k, F[k - 1], exact)
+
+
+# --------------------------------------------------------------------------
+# The paper's hardware-efficient ansatz (Fig. 2c; Sec. "Hardware-efficient
+# ansatze as approximate k-designs"): RY(pi/4) wall, then per layer a random
+# Pauli rotation on every qubit and CNOT (or CZ) walls on the even and the
+# odd bonds.
+# --------------------------------------------------------------------------
+_PAULI = [np.array([[0, 1], [1, 0]], dtype=complex), np.array([[0, -1j], [1j, 0]]),
+          np.array([[1, 0], [0, -1]], dtype=complex)]
+
+
+def _pauli_rotation_draw(seed, pair, which, t, q):
+    x = O.philox4x64([t, q, pair, which], [seed, 0])
+    return 2 * math.pi * ((x[0] >> 11) * 2.0 ** -53), ((x[1] >> 32) * 3) >> 32
+
+
+@pytest.mark.parametrize("kind", [O.HEA_CNOT, O.HEA_CZ])
+def test_paper_hea_gates_match_their_definition(kind):
+    # every gate against its definition through scipy's matrix exponential:
+    # RY(pi/4) = expm(-i pi/8 Y), R_P(theta) = expm(-i theta P / 2), and the
+    # textbook CNOT (control = the more significant index bit) or CZ
+    expm = pytest.importorskip("scipy.linalg").expm
+    n, L, seed = 5, 3, 41
+    d = O.desc(kind, n, L, seed=seed)
+    cnot = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=complex)
+    for which in (0, 1):
+        g = O.circuit(d, 0, which)
+        expect = [(O.OP_GATE1, q, expm(-1j * math.pi / 8 * _PAULI[1])) for q in range(n)]
+        for t in range(L):
+            for q in range(n):
+                th, ax = _pauli_rotation_draw(seed, 0, which, t, q)
+                expect.append((O.OP_GATE1, q, expm(-0.5j * th * _PAULI[ax])))
+            for b in list(range(0, n - 1, 2)) + list(range(1, n - 1, 2)):
+                if kind == O.HEA_CNOT:
+                    expect.append((O.OP_GATE2, b, cnot))
+                else:
+                    expect.append((O.OP_DIAG2, b, np.array([1, 1, 1, -1], dtype=complex)))
+        assert len(g) == len(expect)
+        for (k1, q1, m1), (k2, q2, m2) in zip(g, expect):
+            assert (k1, q1) == (k2, q2)
+            assert np.abs(np.asarray(m1) - m2).max() < 1e-15
+
+
+def _pauli_trace_one_layer(seed, pair, n):
+    # L = 1: the entangling walls of U and V and the RY(pi/4) walls cancel in
+    # Tr(U^dagger V) = Tr(R_U^dagger R_V); with R_P(t) = cos(t/2) I - i sin(t/2) P
+    # and Tr(P P') = 2 delta_PP', each qubit gives 2 (c c' + delta s s').
+    ref = 1.0
+    for q in range(n):
+        tu, au = _pauli_rotation_draw(seed, pair, 0, 0, q)
+        tv, av = _pauli_rotation_draw(seed, pair, 1, 0, q)
+        ref *= 2 * (math.cos(tu / 2) * math.cos(tv / 2) + (au == av) * math.sin(tu / 2) * math.sin(tv / 2))
+    return ref
+
+
+@pytest.mark.parametrize("kind", [O.HEA_CNOT, O.HEA_CZ])
+def test_paper_hea_one_layer_product_form(kind):
+    n, seed = 50, 17
+    d = O.desc(kind, n, 1, seed=seed)
+    for p in range(4):
+        ref = _pauli_trace_one_layer(seed, p, n)
+        assert abs(O.trace_pair(d, p, "ve") - ref) <= 1e-12 * max(1, abs(ref))
+    d8 = O.desc(kind, 8, 1, seed=seed)
+    for p in range(2):
+        assert abs(O.trace_pair(d8, p, "dense") - _pauli_trace_one_layer(seed, p, 8)) < 1e-12
+
+
+def test_paper_hea_two_qubits_one_layer_moments():
+    # per qubit E|t|^{2k} = binom(2k,k)/3 + (2/3) binom(2k,k)^2 / 4^k (same axis
+    # with probability 1/3: t = 2 cos(dtheta/2); different axes: t = 2 c c',
+    # and E cos^{2k} of a uniform angle is binom(2k,k)/4^k); qubits multiply:
+    # F^(1) = (4/3)^n, F^(2) = (7/2)^n, F^(3) = (65/6)^n.
+    d = O.desc(O.HEA_CNOT, 2, 1, seed=23)
+    tr = O.trace_batch(d, 0, 100000, "dense", threads=8)
+    F, se = O.moments(tr, 3)
+    for k in range(1, 4):
+        c = math.comb(2 * k, k)
+        exact = (c / 3 + 2 / 3 * c * c / 4 ** k) ** 2
         assert abs(F[k - 1] - exact) < 5 * se[k - 1], (k, F[k - 1], exact)
 
 
