@@ -35,6 +35,9 @@ WORK = dict(n=50, depth_min=2, depth_max=10, pairs=100_000, seed=4, k_max=4, kin
 WORKLOADS = {
     "brickwork": dict(WORK),
     "hea": dict(n=50, depth_min=1, depth_max=8, pairs=1_000_000, seed=3, k_max=4, kind=2, name="hea"),
+    # the paper's own HEA: RY(pi/4) wall, random Pauli rotations, CNOT walls on even then odd bonds
+    "hea_paper": dict(n=50, depth_min=1, depth_max=8, pairs=100_000, seed=6, k_max=4, kind=3,
+                      name="hea_paper"),
     # local random circuits: n = 20, T in {20, 40, ..., 100} gates per circuit (T >= 120 is
     # reported separately: its boundaries reach the 2^24 limit, see local_large_T_report)
     "local": dict(n=20, depth_min=1, depth_max=1, T=(20, 100, 20), pairs=20_000, seed=2, k_max=4, kind=1,
@@ -57,7 +60,8 @@ def parse():
                     help="skip the GPU-seconds-to-1%% measurement, the bootstrap report and the large-T report")
     ap.add_argument("--no-cv", action="store_true", help="skip the control-variate report")
     ap.add_argument("--workload", default="brickwork", choices=sorted(WORKLOADS),
-                    help="brickwork (the headline workload), hea (n=50, L=1..8) or local (n=20, T=20..100)")
+                    help="brickwork (the headline workload), hea (n=50, L=1..8), hea_paper (n=50, L=1..8) "
+                         "or local (n=20, T=20..100)")
     a = ap.parse_args()
     WORK.update(WORKLOADS[a.workload])
     if a.pairs == 100_000 and a.workload != "brickwork":
@@ -76,6 +80,8 @@ def make_ensemble(fp, flags=0, stream=None):
 def workload_config(args, world):
     desc = {"brickwork": "brickwork n=50, l uniform in 2..10 per pair, Haar U(4)",
             "hea": "HEA n=50, L uniform in 1..8 per pair, RY(theta)RZ(phi) + CZ ladder",
+            "hea_paper": "paper HEA n=50, L uniform in 1..8 per pair, RY(pi/4) wall, random Pauli rotations, "
+                         "CNOT walls on even then odd bonds",
             "local": "local random circuits n=20, T uniform in {20,40,...,100} Haar U(4) gates on uniformly "
                      "random neighbour bonds per circuit"}[WORK["name"]]
     return {"workload": f"{desc}, {args.pairs} pairs per step per GPU",
@@ -152,6 +158,20 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU-seconds to F^(2) at 1% relative standard error, mixed vs plain FP64
 # ---------------------------------------------------------------------------
+def moments_report(mom, groups, K):
+    """F^(k) and its standard error per group from fp_reduce_moments output."""
+    out = {}
+    for g, depth in enumerate(groups):
+        row = mom[g * (2 * K + 1):(g + 1) * (2 * K + 1)]
+        N = row[0]
+        if N < 2:
+            continue
+        F = [row[k] / N for k in range(1, K + 1)]
+        se = [math.sqrt(max(row[K + k] / N - F[k - 1] ** 2, 0.0) * N / (N - 1) / N) for k in range(1, K + 1)]
+        out[str(int(depth))] = {"pairs": int(N), "F": F, "stderr": se}
+    return out
+
+
 def per_pair_cost(fp, l, prec, count, first):
     """Device seconds per pair of depth l (all kernels of the trace path)."""
     ens = fp.Ensemble(fp.PARALLEL, WORK["n"], l, l, seed=WORK["seed"], flags=fp.FLAG_TIMING)
@@ -258,6 +278,27 @@ def bootstrap_report(fp, pairs=200_000, B=300):
         ok = np.isfinite(ls)
         out[f"layers_eps0.1_k{k}"] = {"p5_p50_p95": pct(ls[ok]) if ok.any() else None,
                                       "fits_converged": int(ok.sum())}
+    return out
+
+
+def exact_fk_report(fp, mc=None):
+    """Exact ensemble F^(2) (l = 2..10) and F^(3) (l = 2..6) of the n = 50 brickwork
+    ensemble by the Weingarten transfer-matrix sweep on the GPU, with the time of
+    each call, and the Monte Carlo F^(2) of the adaptive run beside it (z-score)."""
+    out = {"F2": {}, "F3": {}}
+    for k, depths in ((2, range(2, 11)), (3, range(2, 7))):
+        for l in depths:
+            t0 = time.perf_counter()
+            f = fp.exact_brickwork_fk(WORK["n"], l, k)
+            row = {"exact": f, "seconds": time.perf_counter() - t0}
+            if k == 2 and mc and str(l) in mc:
+                F, se = mc[str(l)]
+                row["monte_carlo"] = [F, se]
+                row["z"] = (F - f) / se if se > 0 else None
+            out[f"F{k}"][str(l)] = row
+    out["note"] = ("variance-free reference: Haar average of every gate as a sum over S_k pairings with U(4) "
+                   "Weingarten weights, summed by an FP64 transfer-matrix sweep over the bonds; Monte Carlo "
+                   "z-scores use the naive standard error, unreliable for the heavy tails at l <= 4")
     return out
 
 
@@ -464,6 +505,7 @@ def main():
             "kernel_ms_share": ks.ms[cls] / ms if ms else None}
 
     metric = {"brickwork": METRIC, "hea": "Tr(U^dagger V) contractions/s at n=50 (HEA, L=1..8)",
+              "hea_paper": "Tr(U^dagger V) contractions/s at n=50 (paper HEA with CNOT walls, L=1..8)",
               "local": "Tr(U^dagger V) contractions/s at n=20 (local circuits, T=20..100)"}[WORK["name"]]
     line = {"metric": metric, "value": value, "unit": "contractions/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -473,12 +515,16 @@ def main():
             "kernel_ms": {fp.K_NAMES.get(i, str(i)): ks.ms[i] for i in range(8) if ks.launches[i]}}
     if WORK["name"] == "local":
         line["infeasible_pairs_in_timed_steps"] = n_skipped
+    if WORK["name"] == "hea_paper":
+        line["F_by_depth_last_step"] = moments_report(mom.cpu().numpy(), ens.groups(), K)
     if rank == 0 and world == 1 and not args.no_target and WORK["name"] == "brickwork":
         line["gpu_s_to_1pct_F2"] = gpu_seconds_to_target(fp, mom, P, K, ng)
     if rank == 0 and world == 1 and not args.no_cv and WORK["name"] == "brickwork":
         line["control_variate"] = control_variate_report(fp)
     if rank == 0 and world == 1 and not args.no_target and WORK["name"] == "brickwork":
         line["bootstrap"] = bootstrap_report(fp)
+        mc = line.get("gpu_s_to_1pct_F2", {}).get("mixed_run", {}).get("F2_by_depth")
+        line["exact_weingarten"] = exact_fk_report(fp, mc)
     if rank == 0 and world == 1 and not args.no_target and WORK["name"] == "local":
         line["local_large_T"] = local_large_T_report(fp)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and WORK["name"] == "brickwork":

@@ -12,7 +12,16 @@
  *                on bonds (b, b+1) with b = (t-1) mod 2, b+2, ...;
  *   FP_LOCAL     T Haar U(4) gates, each on a uniformly random bond;
  *   FP_HEA       hardware-efficient ansatz: per layer RY(theta) RZ(phi) on every
- *                qubit (theta, phi uniform in [0, 2 pi)), then CZ on every bond.
+ *                qubit (theta, phi uniform in [0, 2 pi)), then CZ on every bond;
+ *   FP_HEA_PAULI the paper's hardware-efficient ansatz (Fig. 2c, Sec.
+ *                "Hardware-efficient ansatze as approximate k-designs"): a
+ *                fixed wall of RY(pi/4) on every qubit, then per layer a
+ *                rotation R_P(theta) = exp(-i theta P/2) on every qubit with
+ *                the Pauli axis P uniform in {X, Y, Z} and theta uniform in
+ *                [0, 2 pi), followed by two walls of CNOTs (control b, target
+ *                b+1): first on the even bonds b = 0, 2, ..., then on the odd
+ *                bonds b = 1, 3, ...  FP_FLAG_HEA_CZ puts CZ in place of CNOT
+ *                (the controlled-phase variant the paper compares against).
  *
  * Conventions: qubit 0 is the most significant bit of a basis index; a
  * 2-qubit gate on bond (b, b+1) has matrix index (a_b a_{b+1}) with a_b the
@@ -33,6 +42,9 @@
  *     choice = ((x0 >> 32) * n_choices) >> 32.
  *   HEA angles of circuit w, layer t (0-based), qubit q: c0 = t, c1 = q,
  *     stream = w: theta = 2 pi (x0>>11) 2^-53, phi = 2 pi (x1>>11) 2^-53.
+ *   FP_HEA_PAULI rotation of circuit w, layer t, qubit q: the same block;
+ *     theta = 2 pi (x0>>11) 2^-53, axis = ((x1 >> 32) * 3) >> 32 (0: X,
+ *     1: Y, 2: Z).
  *   FP_FLAG_DIAGONAL_GATES replaces each Haar gate g of circuit w by
  *     diag(e^{i 2 pi u_j}), u_j = (x_j >> 11) 2^-53 from c0 = 0, c1 = g, stream = w.
  * Pair p of an ensemble is therefore fully determined by (seed, p).
@@ -72,7 +84,7 @@ typedef enum {
     FP_ERR_INFEASIBLE = -5    /* a pair's boundary exceeds FP_MAX_STATE_BITS */
 } fp_status;
 
-typedef enum { FP_PARALLEL = 0, FP_LOCAL = 1, FP_HEA = 2 } fp_kind;
+typedef enum { FP_PARALLEL = 0, FP_LOCAL = 1, FP_HEA = 2, FP_HEA_PAULI = 3 } fp_kind;
 
 /* Arithmetic of the contraction.  The final boundary dot product, the
  * |Tr|^{2k} powers and all Monte Carlo moments are FP64 in every mode. */
@@ -93,10 +105,11 @@ enum {
     FP_FLAG_TIMING = 8,           /* record CUDA-event time of every launch (fp_kernel_stats_get);
                                      also disables CUDA-graph replay */
     FP_FLAG_NO_GRAPHS = 16,       /* launch every kernel directly (no CUDA-graph replay) */
-    FP_FLAG_SKIP_INFEASIBLE = 32  /* pairs whose boundary exceeds FP_MAX_STATE_BITS are left
+    FP_FLAG_SKIP_INFEASIBLE = 32, /* pairs whose boundary exceeds FP_MAX_STATE_BITS are left
                                      uncontracted instead of failing the call: NaN results,
                                      group -1, left out of the moments, counted in
                                      fp_run_stats.infeasible */
+    FP_FLAG_HEA_CZ = 64           /* FP_HEA_PAULI with CZ walls instead of CNOT walls */
 };
 
 /* Kernel classes of fp_kernel_stats. */
@@ -117,7 +130,7 @@ enum {
 typedef struct {
     int32_t kind;             /* fp_kind */
     int32_t n;                /* qubits, 2 <= n <= 64 */
-    int32_t depth_min;        /* l (FP_PARALLEL) or L (FP_HEA), >= 1 */
+    int32_t depth_min;        /* l (FP_PARALLEL) or L (FP_HEA, FP_HEA_PAULI), >= 1 */
     int32_t depth_max;        /* >= depth_min; each pair draws its depth uniformly */
     int32_t T_min, T_max, T_step;   /* FP_LOCAL: T drawn uniformly from
                                        {T_min, T_min+T_step, ..., <= T_max} */
@@ -181,7 +194,9 @@ fp_status fp_pair_groups(const fp_ensemble *ens, uint64_t first, uint64_t count,
 /* Sampled gates of circuit `which` (0 = U, 1 = V) of one pair, as they enter
  * the contraction: per gate a record {int32 kind, int32 qubit, 32 doubles =
  * 16 complex entries (re,im)}, kind 0 = 4x4 on (q,q+1), 1 = 2x2 on q in the
- * first 4 entries, 2 = diagonal 2-qubit (4 entries).  *bytes is in/out:
+ * first 4 entries, 2 = diagonal 2-qubit (4 entries).  FP_HEA_PAULI with CNOT
+ * walls lists each CNOT as H on the target, CZ, H on the target (the form
+ * the contraction uses: CZ leaves both wires uncut).  *bytes is in/out:
  * capacity of host_buf on entry, bytes needed on return.  host_buf may be
  * NULL to query the size. */
 fp_status fp_export_gates(fp_ensemble *ens, uint64_t pair, int32_t which, void *host_buf,
@@ -239,6 +254,23 @@ fp_status fp_epsilon_max(double F, int32_t k, int32_t n, int32_t q, double *log1
  * when fewer than two depths qualify or the slope is not negative. */
 fp_status fp_design_layers(int32_t n_depths, const double *depths, const double *F, int32_t k, int32_t n,
                            int32_t q, double eps, double dev_max, double *l_eps, double *A, double *C);
+
+/* Exact ensemble frame potential F^(k), k = 2 or 3, of brickwork circuits
+ * (FP_PARALLEL ensembles of one depth l), with no sampling: every Haar U(4)
+ * gate of the cyclic U^dagger V circuit averaged over the Haar measure
+ * becomes a sum over pairings sigma, tau in S_k weighted by the Weingarten
+ * function of U(4), and consecutive gates on a qubit wire meet with weight
+ * 2^{#cycles(sigma^-1 tau)} -- the statistical-mechanics model behind the
+ * paper's Eq. theory_eq (Sec. "Frame potential").  The sum over all pairings
+ * runs as a transfer-matrix sweep over the bonds on the device, in FP64, with
+ * a state of (k!)^{2(l-1)} entries (k = 3, l = 7: 17.4 GB) allocated for the
+ * call and freed before it returns.  A variance-free reference for the Monte
+ * Carlo estimates of F^(2) and F^(3).
+ *   n >= 2; l in [2, 12] for k = 2, [2, 7] for k = 3 (FP_ERR_ARG otherwise);
+ *   F  host double: the exact F^(k) of the ensemble.
+ * Ordered on cuda_stream; waits for the result.  FP_ERR_OOM when the state
+ * does not fit in free device memory. */
+fp_status fp_exact_brickwork_fk(int32_t n, int32_t l, int32_t k, void *cuda_stream, double *F);
 
 /* Monte Carlo frame potential.  Contracts pairs first, first+1, ... in batches
  * until every group's relative standard error of F^(2) (or of F^(1) when

@@ -16,10 +16,10 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfp_gb300.so")
 
-PARALLEL, LOCAL, HEA = 0, 1, 2
+PARALLEL, LOCAL, HEA, HEA_PAULI = 0, 1, 2, 3
 PREC_FP64, PREC_FP32, PREC_FP32_RAW = 0, 1, 2
 FLAG_SELF_PAIR, FLAG_DIAGONAL_GATES, FLAG_GENERIC_ONLY, FLAG_TIMING, FLAG_NO_GRAPHS = 1, 2, 4, 8, 16
-FLAG_SKIP_INFEASIBLE = 32
+FLAG_SKIP_INFEASIBLE, FLAG_HEA_CZ = 32, 64
 K_SAMPLE, K_MERGE, K_TABLES, K_SWEEP, K_BRICK, K_MOMENTS, K_BOOTSTRAP, K_CLASSES = 0, 1, 2, 3, 4, 5, 6, 8
 K_NAMES = {0: "sample", 1: "merge", 2: "tables", 3: "sweep_generic", 4: "sweep_brick", 5: "moments",
            6: "bootstrap"}
@@ -30,7 +30,7 @@ STATUS = {0: "FP_OK", -1: "FP_ERR_ARG", -2: "FP_ERR_CUDA", -3: "FP_ERR_OOM", -4:
 EXPORTED = ["fp_ensemble_create", "fp_ensemble_destroy", "fp_groups", "fp_pair_groups", "fp_export_gates",
             "fp_trace_batch", "fp_reduce_moments", "fp_frame_potential", "fp_kernel_stats_get",
             "fp_trace_brick_static", "fp_cv_frame_potential", "fp_gemm_bf16", "fp_bootstrap", "fp_epsilon_max",
-            "fp_design_layers", "fp_last_error"]
+            "fp_design_layers", "fp_exact_brickwork_fk", "fp_last_error"]
 
 
 class FpError(RuntimeError):
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
     L.fp_bootstrap.argtypes = [vp, vp, vp, u64, i32, i32, u64, vp]
     L.fp_epsilon_max.argtypes = [f64, i32, i32, i32, P(f64)]
     L.fp_design_layers.argtypes = [i32, vp, vp, i32, i32, i32, f64, f64, P(f64), P(f64), P(f64)]
+    L.fp_exact_brickwork_fk.argtypes = [i32, i32, i32, vp, P(f64)]
     L.fp_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name not in ("fp_ensemble_destroy", "fp_last_error"):
@@ -149,6 +150,15 @@ def gemm_bf16(A, Bt, bias=None, mode=0, Z=None, C=None, C_bf16=None, Ct_bf16=Non
     st = None if stream is None else ctypes.c_void_p(stream)
     _check(load().fp_gemm_bf16(M, N, K, _ptr(A), A.stride(0), _ptr(Bt), Bt.stride(0), _ptr(bias), mode, _ptr(Z),
                                _ptr(C), _ptr(C_bf16), _ptr(Ct_bf16), st))
+
+
+def exact_brickwork_fk(n, l, k, stream=None):
+    """Exact ensemble F^(k) (k = 2, 3) of depth-l brickwork circuits on n qubits,
+    by the Weingarten transfer-matrix sweep on the GPU (fp_exact_brickwork_fk)."""
+    out = ctypes.c_double()
+    st = None if stream is None else ctypes.c_void_p(stream)
+    _check(load().fp_exact_brickwork_fk(n, l, k, st, ctypes.byref(out)))
+    return out.value
 
 
 def epsilon_max_log10(F, k, n, q=2):

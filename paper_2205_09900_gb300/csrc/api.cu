@@ -191,20 +191,30 @@ void parallel_for(uint64_t count, F f) {
     for (auto &t : th) t.join();
 }
 
-HostPlan build_plan(const fp_ensemble_desc &d, int raw_kind, int depth, uint64_t pair) {
-    std::vector<GateSlot> U, V;
-    int n_raw = 0;
-    if (d.kind == FP_PARALLEL) {
-        U = V = layout_brickwork(d.n, depth);
-        n_raw = (int)U.size();
-    } else if (d.kind == FP_HEA) {
-        U = V = layout_hea(d.n, depth);
-        n_raw = depth * d.n;
-    } else {
-        U = layout_local(d.n, local_bonds(d, pair, 0, depth));
-        V = layout_local(d.n, local_bonds(d, pair, 1, depth));
-        n_raw = depth;
+// Gate layout of circuit `which` of a pair and the number of raw gates per circuit.
+std::vector<GateSlot> circuit_layout(const fp_ensemble_desc &d, uint64_t pair, int which, int depth, int *n_raw) {
+    switch (d.kind) {
+        case FP_PARALLEL: {
+            std::vector<GateSlot> g = layout_brickwork(d.n, depth);
+            *n_raw = (int)g.size();
+            return g;
+        }
+        case FP_HEA:
+            *n_raw = depth * d.n;
+            return layout_hea(d.n, depth);
+        case FP_HEA_PAULI:
+            *n_raw = 1 + d.n + depth * d.n;
+            return layout_hea_pauli(d.n, depth, (d.flags & FP_FLAG_HEA_CZ) != 0);
+        default:
+            *n_raw = depth;
+            return layout_local(d.n, local_bonds(d, pair, which, depth));
     }
+}
+
+HostPlan build_plan(const fp_ensemble_desc &d, int raw_kind, int depth, uint64_t pair) {
+    int n_raw = 0;
+    std::vector<GateSlot> U = circuit_layout(d, pair, 0, depth, &n_raw);
+    std::vector<GateSlot> V = circuit_layout(d, pair, 1, depth, &n_raw);
     return make_plan(d.n, U, V, raw_kind, n_raw, d.n / 2, FP_MAX_STATE_BITS);
 }
 
@@ -828,7 +838,7 @@ fp_status fp_ensemble_create(const fp_ensemble_desc *desc, void *cuda_stream, fp
     if (!desc || !out) return fail(FP_ERR_ARG, "null argument");
     *out = nullptr;
     const fp_ensemble_desc &d = *desc;
-    if (d.kind < FP_PARALLEL || d.kind > FP_HEA) return fail(FP_ERR_ARG, "unknown ensemble kind %d", d.kind);
+    if (d.kind < FP_PARALLEL || d.kind > FP_HEA_PAULI) return fail(FP_ERR_ARG, "unknown ensemble kind %d", d.kind);
     if (d.n < 2 || d.n > 64) return fail(FP_ERR_ARG, "n = %d outside [2, 64]", d.n);
     if (d.kind == FP_LOCAL) {
         if (d.T_min < 1 || d.T_max < d.T_min || d.T_step < 1)
@@ -836,8 +846,10 @@ fp_status fp_ensemble_create(const fp_ensemble_desc *desc, void *cuda_stream, fp
     } else if (d.depth_min < 1 || d.depth_max < d.depth_min) {
         return fail(FP_ERR_ARG, "bad depth range [%d, %d]", d.depth_min, d.depth_max);
     }
-    if ((d.flags & FP_FLAG_DIAGONAL_GATES) && d.kind == FP_HEA)
+    if ((d.flags & FP_FLAG_DIAGONAL_GATES) && (d.kind == FP_HEA || d.kind == FP_HEA_PAULI))
         return fail(FP_ERR_ARG, "FP_FLAG_DIAGONAL_GATES applies to Haar-gate ensembles only");
+    if ((d.flags & FP_FLAG_HEA_CZ) && d.kind != FP_HEA_PAULI)
+        return fail(FP_ERR_ARG, "FP_FLAG_HEA_CZ applies to FP_HEA_PAULI only");
     std::unique_ptr<fp_ensemble> E(new fp_ensemble());
     E->d = d;
     E->st = (cudaStream_t)cuda_stream;
@@ -848,7 +860,9 @@ fp_status fp_ensemble_create(const fp_ensemble_desc *desc, void *cuda_stream, fp
         CK(cudaGetDeviceProperties(&prop, E->device));
         E->gpu_name = prop.name;
     }
-    E->raw_kind = d.kind == FP_HEA ? RAW_ROT2 : ((d.flags & FP_FLAG_DIAGONAL_GATES) ? RAW_DIAG4 : RAW_HAAR4);
+    E->raw_kind = d.kind == FP_HEA ? RAW_ROT2
+                : d.kind == FP_HEA_PAULI ? RAW_PAULI
+                : ((d.flags & FP_FLAG_DIAGONAL_GATES) ? RAW_DIAG4 : RAW_HAAR4);
     E->n_groups = d.kind == FP_LOCAL ? (d.T_max - d.T_min) / d.T_step + 1 : d.depth_max - d.depth_min + 1;
     size_t freeb = 0, totb = 0;
     CK(cudaMemGetInfo(&freeb, &totb));
@@ -899,11 +913,8 @@ fp_status fp_export_gates(fp_ensemble *ens, uint64_t pair, int32_t which, void *
     if (!ens || !bytes || (which != 0 && which != 1)) return fail(FP_ERR_ARG, "bad argument");
     const fp_ensemble_desc &d = ens->d;
     int depth = depth_of_pair(d, pair);
-    std::vector<GateSlot> lay;
-    int n_raw;
-    if (d.kind == FP_PARALLEL) { lay = layout_brickwork(d.n, depth); n_raw = (int)lay.size(); }
-    else if (d.kind == FP_HEA) { lay = layout_hea(d.n, depth); n_raw = depth * d.n; }
-    else { lay = layout_local(d.n, local_bonds(d, pair, which, depth)); n_raw = depth; }
+    int n_raw = 0;
+    std::vector<GateSlot> lay = circuit_layout(d, pair, which, depth, &n_raw);
     struct Rec { int32_t kind, q; double m[32]; };
     size_t need = lay.size() * sizeof(Rec);
     if (!host_buf) { *bytes = need; return FP_OK; }
@@ -929,7 +940,7 @@ fp_status fp_export_gates(fp_ensemble *ens, uint64_t pair, int32_t which, void *
             for (int k = 0; k < 4; ++k) out[i].m[2 * k] = dg[k];
             continue;
         }
-        out[i].kind = lay[i].kind;
+        out[i].kind = lay[i].kind == 3 ? 1 : lay[i].kind;
         const double2 *g = &raw[((size_t)which * n_raw + lay[i].raw) * 16];
         for (int k = 0; k < 16; ++k) { out[i].m[2 * k] = g[k].x; out[i].m[2 * k + 1] = g[k].y; }
     }

@@ -59,7 +59,9 @@ FP_HD uint32_t pick(uint64_t x, uint32_t choices) {   // uniform index in [0, ch
 // Raw gates (as sampled) and merged gates live in 16-slot complex records:
 // a 4x4 matrix row-major, or a 2x2 in slots 0..3.
 // ---------------------------------------------------------------------------
-enum RawKind : int32_t { RAW_HAAR4 = 0, RAW_ROT2 = 1, RAW_DIAG4 = 2 };
+// RAW_PAULI (the paper's HEA): raw 0 = Hadamard, raw 1..n = the RY(pi/4)
+// wall, raw 1 + n + t n + q = rotation R_P(theta) of layer t on qubit q.
+enum RawKind : int32_t { RAW_HAAR4 = 0, RAW_ROT2 = 1, RAW_DIAG4 = 2, RAW_PAULI = 3 };
 
 // One raw-gate reference inside a merged product.
 struct MergeRef {

@@ -103,6 +103,38 @@ __global__ void sample_kernel(SampleParams sp, const PairInfo *__restrict__ pair
             sincospi(2.0 * ((double)(x.x[k] >> 11) * 0x1.0p-53), &s, &c);
             out[5 * k] = make_double2(c, s);
         }
+    } else if (sp.raw_kind == RAW_PAULI) {
+        // the paper's HEA (Fig. 2c): H, the RY(pi/4) wall, Pauli rotations
+#pragma unroll
+        for (int k = 0; k < 16; ++k) out[k] = make_double2(0, 0);
+        if (g == 0) {
+            const double h = 0.70710678118654752440;
+            out[0] = make_double2(h, 0); out[1] = make_double2(h, 0);
+            out[2] = make_double2(h, 0); out[3] = make_double2(-h, 0);
+        } else if (g <= sp.n) {
+            // RY(pi/4) = [[c, -s], [s, c]], c = cos(pi/8), s = sin(pi/8)
+            double s, c;
+            sincospi(0.125, &s, &c);
+            out[0] = make_double2(c, 0); out[1] = make_double2(-s, 0);
+            out[2] = make_double2(s, 0); out[3] = make_double2(c, 0);
+        } else {
+            const int r = g - 1 - sp.n, t = r / sp.n, q = r % sp.n;
+            U64x4 x = philox(sp.seed, (uint64_t)t, (uint64_t)q, pi.pair, (uint64_t)wr);
+            const double th = (double)(x.x[0] >> 11) * 0x1.0p-53;   // theta in turns of 2 pi
+            const uint32_t axis = pick(x.x[1], 3u);
+            double s, c;
+            sincospi(th, &s, &c);                // sin, cos of theta/2
+            // exp(-i theta P/2) = c I - i s P
+            if (axis == 0) {        // X
+                out[0] = make_double2(c, 0); out[1] = make_double2(0, -s);
+                out[2] = make_double2(0, -s); out[3] = make_double2(c, 0);
+            } else if (axis == 1) { // Y
+                out[0] = make_double2(c, 0); out[1] = make_double2(-s, 0);
+                out[2] = make_double2(s, 0); out[3] = make_double2(c, 0);
+            } else {                // Z
+                out[0] = make_double2(c, -s); out[3] = make_double2(c, s);
+            }
+        }
     } else {   // RAW_ROT2: HEA rotation RY(theta) RZ(phi), raw index g = t*n + q
         int t = g / sp.n, q = g % sp.n;
         U64x4 x = philox(sp.seed, (uint64_t)t, (uint64_t)q, pi.pair, (uint64_t)wr);

@@ -46,6 +46,21 @@ std::vector<GateSlot> layout_hea(int n, int L) {
     return g;
 }
 
+std::vector<GateSlot> layout_hea_pauli(int n, int L, bool cz) {
+    std::vector<GateSlot> g;
+    for (int q = 0; q < n; ++q) g.push_back({1, q, 1 + q});   // RY(pi/4) wall
+    for (int t = 0; t < L; ++t) {
+        for (int q = 0; q < n; ++q) g.push_back({1, q, 1 + n + t * n + q});
+        for (int par = 0; par < 2; ++par)
+            for (int b = par; b <= n - 2; b += 2) {
+                if (!cz) g.push_back({3, b + 1, 0});          // H on the target
+                g.push_back({2, b, -1});
+                if (!cz) g.push_back({3, b + 1, 0});
+            }
+    }
+    return g;
+}
+
 std::vector<GateSlot> layout_local(int n, const std::vector<int> &bonds) {
     (void)n;
     std::vector<GateSlot> g;
@@ -58,6 +73,7 @@ namespace {
 struct SeqEl {
     int kind;                       // 0 gate2 (data), 1 gate1 (data), 2 constant diagonal
     int q;
+    bool invol = false;             // a lone constant involution (GateSlot kind 3)
     std::vector<MergeRef> chain;    // application order
     double dre[4], dim[4];          // kind 2 entries
 };
@@ -119,8 +135,11 @@ void merge_sequence(std::vector<SeqEl> &seq) {
                     if (re != 1.0 || im != 0.0) ident = false;
                 }
                 if (ident) unlink(j);   // CZ . CZ = identity: both go
+            } else if (seq[i].invol && m.invol && seq[i].chain[0].gate == m.chain[0].gate) {
+                unlink(j);   // H . H = identity: both go
             } else {
                 // application order: seq[i]'s chain first, then m's
+                m.invol = false;
                 std::vector<MergeRef> c = std::move(seq[i].chain);
                 c.insert(c.end(), m.chain.begin(), m.chain.end());
                 m.chain = std::move(c);
@@ -168,13 +187,14 @@ HostPlan make_plan(int n, const std::vector<GateSlot> &U, const std::vector<Gate
     std::vector<SeqEl> seq;
     auto push = [&](const GateSlot &g, int which, int dagger) {
         SeqEl e;
-        e.kind = g.kind;
+        e.kind = g.kind == 3 ? 1 : g.kind;
+        e.invol = g.kind == 3;
         e.q = g.q;
         for (int k = 0; k < 4; ++k) { e.dre[k] = 1; e.dim[k] = 0; }
         if (g.kind == 2) {
             e.dre[3] = -1.0;   // CZ = diag(1, 1, 1, -1), its own conjugate
         } else {
-            e.chain.push_back({which, g.raw, dagger, g.kind == 1 ? 2 : dim});
+            e.chain.push_back({which, g.raw, dagger, e.kind == 1 ? 2 : dim});
         }
         seq.push_back(e);
     };

@@ -11,7 +11,9 @@ namespace fpk {
 // One gate of a circuit as laid out by an ensemble (values come from the sampler).
 struct GateSlot {
     int kind;   // 0: 2-qubit on bond q (raw gate), 1: 1-qubit on q (raw gate),
-                // 2: constant diagonal 2-qubit (CZ) on bond q
+                // 2: constant diagonal 2-qubit (CZ) on bond q, 3: 1-qubit on q
+                // (raw gate) that is the same constant involution in U and V
+                // (the Hadamard of a CNOT): two of them meeting cancel
     int q;
     int raw;    // raw gate index within the circuit, -1 for constants
 };
@@ -39,6 +41,11 @@ struct HostPlan {
 std::vector<GateSlot> layout_brickwork(int n, int l);
 std::vector<GateSlot> layout_hea(int n, int L);
 std::vector<GateSlot> layout_local(int n, const std::vector<int> &bonds);
+// The paper's HEA (Fig. 2c): RY(pi/4) wall, then per layer Pauli rotations and
+// CNOT walls on the even, then the odd bonds (CZ walls when `cz`).  A CNOT is
+// laid out as H(target) CZ H(target) (H of kind 3), so that its control wire
+// stays uncut.
+std::vector<GateSlot> layout_hea_pauli(int n, int L, bool cz);
 
 // Plan the contraction of Tr(U^dagger V).  `cut`: the left sweep owns bonds
 // 0..cut-1 and the 1-qubit gates of qubits 0..cut-1, the right sweep the rest.
