@@ -481,7 +481,8 @@ fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t
 }
 
 // Build and upload one brickwork plan variant.
-fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int TH, std::unique_ptr<BrickCache> &out) {
+fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int TH, int persist,
+                           std::unique_ptr<BrickCache> &out) {
     auto bc = std::make_unique<BrickCache>();
     // K > N: shared-memory sweep, K == N: one tile
     bc->hp = make_brick_plan(E->d.n, l, K, fp32 ? 5 : 4, R, E->d.kind == FP_HEA ? 1 : 0);
@@ -497,6 +498,7 @@ fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int T
     bc->dp.rgates = bc->d_rgates.as<RegGate>();
     bc->dp.win_bits = R;
     bc->dp.threads = TH;
+    bc->dp.persist = persist;
     out = std::move(bc);
     return FP_OK;
 }
@@ -510,15 +512,18 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
     const fp_ensemble_desc &d = E->d;
     const int N = 2 * (l - 1);
     const int key = l * 2 + (fp32 ? 1 : 0);
-    struct Cand { int K, R, TH; };
-    // K = 99: whole boundary in one CTA's shared memory (brick_smem_kernel)
-    std::vector<Cand> cands = fp32 ? std::vector<Cand>{{14, 4, 512}, {14, 5, 256}, {13, 4, 512}, {13, 4, 256}, {13, 5, 256}}
-                                   : std::vector<Cand>{{13, 3, 512}, {13, 4, 256}};
-    if (((size_t)1 << N) * (fp32 ? sizeof(float2) : sizeof(double2)) <= (size_t)200 * 1024) cands.push_back({99, 0, 0});
+    struct Cand { int K, R, TH, P; };
+    // K = 99: whole boundary in one CTA's shared memory (brick_smem_kernel);
+    // P = 1: persistent double-buffered tile passes (brick_pass_db_kernel)
+    std::vector<Cand> cands = fp32 ? std::vector<Cand>{{14, 4, 512, 0}, {14, 5, 256, 0}, {13, 4, 512, 0},
+                                                       {13, 4, 256, 0}, {13, 5, 256, 0}, {13, 4, 512, 1},
+                                                       {13, 5, 256, 1}}
+                                   : std::vector<Cand>{{13, 3, 512, 0}, {13, 4, 256, 0}};
+    if (((size_t)1 << N) * (fp32 ? sizeof(float2) : sizeof(double2)) <= (size_t)200 * 1024) cands.push_back({99, 0, 0, 0});
     const int kmin = 12;   // boundaries up to 2^12: shared-memory sweep, nothing to tune
     char ckey[256];
     snprintf(ckey, sizeof ckey, "%s n=%d l=%d %s", E->gpu_name.c_str(), d.n, l, fp32 ? "fp32" : "fp64");
-    int bestK = cands[0].K, bestR = cands[0].R, bestT = cands[0].TH;
+    int bestK = cands[0].K, bestR = cands[0].R, bestT = cands[0].TH, bestP = 0;
     bool have = false;
     const char *cache = getenv("FP_AUTOTUNE_CACHE");
     if (N <= kmin) {
@@ -529,10 +534,10 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
         if (f) {
             char line[512];
             while (fgets(line, sizeof line, f)) {
-                int K, R, T;
+                int K, R, T, Pp = 0;
                 char k2[256];
-                if (sscanf(line, "%255[^|]|%d %d %d", k2, &K, &R, &T) == 4 && strcmp(k2, ckey) == 0) {
-                    bestK = K; bestR = R; bestT = T; have = true;
+                if (sscanf(line, "%255[^|]|%d %d %d %d", k2, &K, &R, &T, &Pp) >= 4 && strcmp(k2, ckey) == 0) {
+                    bestK = K; bestR = R; bestT = T; bestP = Pp; have = true;
                 }
             }
             fclose(f);
@@ -561,7 +566,8 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
         float best_ms = 1e30f;
         for (const Cand &c : cands) {
             std::unique_ptr<BrickCache> bc;
-            fp_status s = make_brick_cache(E, l, fp32, c.K, c.R, c.TH, bc);
+            if (c.K != 99 && c.K > N) continue;   // tiles larger than the boundary
+            fp_status s = make_brick_cache(E, l, fp32, c.K, c.R, c.TH, c.P, bc);
             if (s != FP_OK) continue;
             float ms_sum = 0;
             for (int rep = 0; rep < 2; ++rep) {
@@ -580,15 +586,15 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
                 CK(cudaEventElapsedTime(&ms, E->ev0, E->ev1));
                 if (rep == 1) ms_sum += ms;     // first repetition warms caches and code
             }
-            if (ms_sum < best_ms) { best_ms = ms_sum; bestK = c.K; bestR = c.R; bestT = c.TH; }
+            if (ms_sum < best_ms) { best_ms = ms_sum; bestK = c.K; bestR = c.R; bestT = c.TH; bestP = c.P; }
         }
         if (cache) {
             FILE *f = fopen(cache, "a");
-            if (f) { fprintf(f, "%s|%d %d %d\n", ckey, bestK, bestR, bestT); fclose(f); }
+            if (f) { fprintf(f, "%s|%d %d %d %d\n", ckey, bestK, bestR, bestT, bestP); fclose(f); }
         }
     }
     std::unique_ptr<BrickCache> bc;
-    fp_status s = make_brick_cache(E, l, fp32, bestK, bestR, bestT, bc);
+    fp_status s = make_brick_cache(E, l, fp32, bestK, bestR, bestT, bestP, bc);
     if (s != FP_OK) return s;
     E->brick_plans.emplace(key, std::move(bc));
     return FP_OK;

@@ -38,6 +38,7 @@ struct BrickPass {
     int32_t gate_off, n_gates;
     uint32_t smask;     // physical bits held by the tile
     int32_t rp_off, n_rp;   // register passes (RegPass) of this tile pass
+    int32_t rg_off;         // first RegGate of this tile pass
 };
 
 // One register pass inside a tile pass: every thread holds 2^r amplitudes
@@ -75,6 +76,7 @@ struct BrickDevPlan {
     const RegGate *rgates;
     int win_bits;
     int threads;
+    int persist;        // 1: persistent double-buffered tile passes
 };
 
 struct BrickHostPlan {

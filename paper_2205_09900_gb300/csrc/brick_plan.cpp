@@ -23,6 +23,7 @@ static void schedule_registers(BrickHostPlan &P, BrickPass &ps, const int *ring,
     for (int k = 0; k < K; ++k) rpos[ring[k]] = k;
     std::vector<char> done(G, 0);
     ps.rp_off = (int)P.rpasses.size();
+    ps.rg_off = (int)P.rgates.size();
     int left = G;
     while (left > 0) {
         int best_c = -1;

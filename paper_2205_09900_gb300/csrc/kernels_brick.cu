@@ -12,6 +12,8 @@
 // K6   brick_dot:   FP64 meet of the two boundaries with the cancellation ratio.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "brick.h"
 #include "kernels.h"
 
@@ -437,65 +439,34 @@ __device__ __forceinline__ void win_dispatch(int type, C (&v)[1 << R], const C *
     }
 }
 
+// Asynchronous global -> shared copies (cp.async): every element of a tile
+// is requested before any is waited for, so a tile load costs about one
+// memory latency instead of one per few elements.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem_src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 constexpr int kMaxRegPasses = 160;
 
-__device__ __forceinline__ int srp_gate_base(const RegPass *rps, const BrickPass &ps) { return rps[ps.rp_off].gate_off; }
 
-// One light-cone pass of one side over all pairs: blockIdx.x = tile, blockIdx.y = pair.
-// The tile (2^K amplitudes, a contiguous cyclic arc of segment bits) is loaded
-// into shared memory, the pass's gate maps and schedule are staged next to it,
-// and the gates are applied window by window with 2^R amplitudes per thread
-// in registers; one barrier per window.
+// The register passes of one tile pass over a tile in shared memory: every
+// thread holds 2^R amplitudes of a window in registers, applies the window's
+// gates, writes them back; one barrier per window.
 template <typename C, int K, int R, int TH>
-__global__ void __launch_bounds__(TH) brick_pass_kernel(BrickDev d, int side, BrickPass ps,
-                                                        const BrickGate *__restrict__ gates,
-                                                        const RegPass *__restrict__ rps,
-                                                        const RegGate *__restrict__ rgs,
-                                                        const C *__restrict__ maps, C *__restrict__ states) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *tile = (C *)smem_raw;
-    C *smaps = tile + (1u << K);
+__device__ __forceinline__ void tile_register_passes(C *__restrict__ tile, const C *__restrict__ smaps,
+                                                     const RegPass *__restrict__ srp, const RegGate *__restrict__ srg,
+                                                     int n_rp, int g0) {
     constexpr int MW = MapSlot<C>::width;
-    __shared__ uint32_t lut_lo[128], lut_hi[1 << (K - 7)];
-    __shared__ int pos[32];
-    __shared__ RegPass srp[kMaxRegPasses];
-    __shared__ RegGate srg[256];
-    const int N = d.N, m = d.m;
-    const uint32_t S = 1u << N;
-    if (threadIdx.x == 0) {
-        int k = 0;
-        for (int b = 0; b < N; ++b) if (ps.smask & (1u << b)) pos[k++] = b;
-    }
-    for (int i = threadIdx.x; i < ps.n_rp; i += TH) srp[i] = rps[ps.rp_off + i];
-    for (int i = threadIdx.x; i < ps.n_gates; i += TH) srg[i] = rgs[srp_gate_base(rps, ps) + i];
-    __syncthreads();
-    uint32_t base = 0;
-    {
-        uint32_t t = blockIdx.x;
-        for (int b = 0; b < N; ++b)
-            if (!(ps.smask & (1u << b))) { base |= (t & 1u) << b; t >>= 1; }
-    }
-    for (int i = threadIdx.x; i < 128; i += TH) {
-        uint32_t o = 0;
-        for (int k = 0; k < 7; ++k) o |= ((i >> k) & 1u) << pos[k];
-        lut_lo[i] = o;
-    }
-    for (int i = threadIdx.x; i < (1 << (K - 7)); i += TH) {
-        uint32_t o = 0;
-        for (int k = 0; k < K - 7; ++k) o |= ((i >> k) & 1u) << pos[7 + k];
-        lut_hi[i] = o;
-    }
-    const C *mp = maps + (size_t)blockIdx.y * maps_per_pair(d) * 16;
-    for (int i = threadIdx.x; i < ps.n_gates * 16; i += TH) {
-        const BrickGate gg = gates[ps.gate_off + i / 16];
-        stage_entry<C>(smaps + (i / 16) * MW, i % 16, mp[(size_t)map_index(d, side, gg.layer, gg.j) * 16 + (i % 16)]);
-    }
-    __syncthreads();
-    C *st = states + ((size_t)blockIdx.y * 2 + side) * S + base;
-    for (uint32_t i = threadIdx.x; i < (1u << K); i += TH) tile[swz(i)] = st[lut_lo[i & 127] | lut_hi[i >> 7]];
-    __syncthreads();
-    const int g0 = srp[0].gate_off;
-    for (int p = 0; p < ps.n_rp; ++p) {
+    for (int p = 0; p < n_rp; ++p) {
         const RegPass rp = srp[p];
         uint32_t sw[R];
 #pragma unroll
@@ -527,7 +498,153 @@ __global__ void __launch_bounds__(TH) brick_pass_kernel(BrickDev d, int side, Br
         }
         __syncthreads();
     }
+}
+
+// Physical bits of a tile pass (ascending) and the tile's gather tables:
+// element i of the tile is amplitude base | lut_lo[i & 127] | lut_hi[i >> 7].
+template <int K, int TH>
+__device__ __forceinline__ void tile_tables(const BrickPass &ps, int N, int *pos, uint32_t *lut_lo, uint32_t *lut_hi) {
+    if (threadIdx.x == 0) {
+        int k = 0;
+        for (int b = 0; b < N; ++b) if (ps.smask & (1u << b)) pos[k++] = b;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 128; i += TH) {
+        uint32_t o = 0;
+        for (int k = 0; k < 7; ++k) o |= ((i >> k) & 1u) << pos[k];
+        lut_lo[i] = o;
+    }
+    for (int i = threadIdx.x; i < (1 << (K - 7)); i += TH) {
+        uint32_t o = 0;
+        for (int k = 0; k < K - 7; ++k) o |= ((i >> k) & 1u) << pos[7 + k];
+        lut_hi[i] = o;
+    }
+    __syncthreads();
+}
+
+// base amplitude index of tile t: t's bits spread over the bits outside the tile
+__device__ __forceinline__ uint32_t tile_base(uint32_t t, uint32_t smask, int N) {
+    uint32_t base = 0;
+    for (int b = 0; b < N; ++b)
+        if (!(smask & (1u << b))) { base |= (t & 1u) << b; t >>= 1; }
+    return base;
+}
+
+// One light-cone pass of one side over all pairs: blockIdx.x = tile, blockIdx.y = pair.
+// The tile (2^K amplitudes, a contiguous cyclic arc of segment bits) is loaded
+// into shared memory, the pass's gate maps and schedule are staged next to it,
+// and the gates are applied window by window with 2^R amplitudes per thread
+// in registers; one barrier per window.
+template <typename C, int K, int R, int TH>
+__global__ void __launch_bounds__(TH) brick_pass_kernel(BrickDev d, int side, BrickPass ps,
+                                                        const BrickGate *__restrict__ gates,
+                                                        const RegPass *__restrict__ rps,
+                                                        const RegGate *__restrict__ rgs,
+                                                        const C *__restrict__ maps, C *__restrict__ states) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tile = (C *)smem_raw;
+    C *smaps = tile + (1u << K);
+    constexpr int MW = MapSlot<C>::width;
+    __shared__ uint32_t lut_lo[128], lut_hi[1 << (K - 7)];
+    __shared__ int pos[32];
+    __shared__ RegPass srp[kMaxRegPasses];
+    __shared__ RegGate srg[256];
+    const int N = d.N;
+    const uint32_t S = 1u << N;
+    tile_tables<K, TH>(ps, N, pos, lut_lo, lut_hi);
+    const uint32_t base = tile_base(blockIdx.x, ps.smask, N);
+    // the tile: all 2^K element copies in flight at once ...
+    static_assert((1 << K) % TH == 0, "tile size must be a multiple of the block size");
+    C *st = states + ((size_t)blockIdx.y * 2 + side) * S + base;
+#pragma unroll
+    for (int j = 0; j < (1 << K) / TH; ++j) {
+        const uint32_t i = threadIdx.x + (uint32_t)j * TH;
+        cp_async<sizeof(C)>(&tile[swz(i)], &st[lut_lo[i & 127] | lut_hi[i >> 7]]);
+    }
+    // ... while the register schedule and the pass's gate maps are staged
+    for (int i = threadIdx.x; i < ps.n_rp; i += TH) srp[i] = rps[ps.rp_off + i];
+    for (int i = threadIdx.x; i < ps.n_gates; i += TH) srg[i] = rgs[ps.rg_off + i];
+    const C *mp = maps + (size_t)blockIdx.y * maps_per_pair(d) * 16;
+    for (int i = threadIdx.x; i < ps.n_gates * 16; i += TH) {
+        const BrickGate gg = gates[ps.gate_off + i / 16];
+        stage_entry<C>(smaps + (i / 16) * MW, i % 16, mp[(size_t)map_index(d, side, gg.layer, gg.j) * 16 + (i % 16)]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    tile_register_passes<C, K, R, TH>(tile, smaps, srp, srg, ps.n_rp, ps.rg_off);
     for (uint32_t i = threadIdx.x; i < (1u << K); i += TH) st[lut_lo[i & 127] | lut_hi[i >> 7]] = tile[swz(i)];
+}
+
+// Persistent, double-buffered form of brick_pass_kernel: each CTA walks the
+// (pair, tile) items of the pass with a stride of gridDim.x; while it applies
+// the gates of one item, the cp.async copies of the next item's tile and raw
+// gate maps fill the other buffer, so tile loads overlap compute.  Shared
+// memory: two 2^K tiles, two raw map sets, one staged map set.
+template <typename C, int K, int R, int TH>
+__global__ void __launch_bounds__(TH) brick_pass_db_kernel(BrickDev d, int side, BrickPass ps, int npairs,
+                                                           const BrickGate *__restrict__ gates,
+                                                           const RegPass *__restrict__ rps,
+                                                           const RegGate *__restrict__ rgs,
+                                                           const C *__restrict__ maps, C *__restrict__ states) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int MW = MapSlot<C>::width;
+    const int G = ps.n_gates;
+    C *tiles = (C *)smem_raw;                      // [2][2^K]
+    C *raw = tiles + 2 * (1u << K);                // [2][G*16]
+    C *smaps = raw + 2 * G * 16;                   // [G*MW]
+    __shared__ uint32_t lut_lo[128], lut_hi[1 << (K - 7)];
+    __shared__ int pos[32];
+    __shared__ RegPass srp[kMaxRegPasses];
+    __shared__ RegGate srg[256];
+    __shared__ int mslot[256];                     // map index of each gate of the pass
+    const int N = d.N;
+    const uint32_t S = 1u << N;
+    tile_tables<K, TH>(ps, N, pos, lut_lo, lut_hi);
+    for (int i = threadIdx.x; i < ps.n_rp; i += TH) srp[i] = rps[ps.rp_off + i];
+    for (int i = threadIdx.x; i < G; i += TH) {
+        srg[i] = rgs[ps.rg_off + i];
+        const BrickGate gg = gates[ps.gate_off + i];
+        mslot[i] = map_index(d, side, gg.layer, gg.j);
+    }
+    __syncthreads();
+    const uint32_t ntiles = 1u << (N - K);
+    const uint32_t items = (uint32_t)npairs * ntiles;
+    static_assert((1 << K) % TH == 0, "tile size must be a multiple of the block size");
+    auto issue = [&](uint32_t it, int buf) {
+        const uint32_t pair = it / ntiles, t = it - pair * ntiles;
+        const C *st = states + ((size_t)pair * 2 + side) * S + tile_base(t, ps.smask, N);
+        C *dst = tiles + (size_t)buf * (1u << K);
+#pragma unroll
+        for (int j = 0; j < (1 << K) / TH; ++j) {
+            const uint32_t i = threadIdx.x + (uint32_t)j * TH;
+            cp_async<sizeof(C)>(&dst[swz(i)], &st[lut_lo[i & 127] | lut_hi[i >> 7]]);
+        }
+        const C *mp = maps + (size_t)pair * maps_per_pair(d) * 16;
+        C *rdst = raw + (size_t)buf * G * 16;
+        for (int i = threadIdx.x; i < G * 16; i += TH)
+            cp_async<sizeof(C)>(&rdst[i], &mp[(size_t)mslot[i / 16] * 16 + (i % 16)]);
+    };
+    uint32_t it = blockIdx.x;
+    if (it < items) issue(it, 0);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    for (int k = 0; it < items; it += gridDim.x, ++k) {
+        const int buf = k & 1;
+        const uint32_t nxt = it + gridDim.x;
+        if (nxt < items) issue(nxt, buf ^ 1);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // this item's copies are in
+        __syncthreads();
+        const C *rsrc = raw + (size_t)buf * G * 16;
+        for (int i = threadIdx.x; i < G * 16; i += TH) stage_entry<C>(smaps + (i / 16) * MW, i % 16, rsrc[i]);
+        __syncthreads();
+        C *tile = tiles + (size_t)buf * (1u << K);
+        tile_register_passes<C, K, R, TH>(tile, smaps, srp, srg, ps.n_rp, ps.rg_off);
+        const uint32_t pair = it / ntiles, t = it - pair * ntiles;
+        C *st = states + ((size_t)pair * 2 + side) * S + tile_base(t, ps.smask, N);
+        for (uint32_t i = threadIdx.x; i < (1u << K); i += TH) st[lut_lo[i & 127] | lut_hi[i >> 7]] = tile[swz(i)];
+        __syncthreads();   // the tile and raw maps of this buffer are free for item k + 2
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 template <typename C>
@@ -570,6 +687,31 @@ cudaError_t run_passes(const BrickDev &d, const BrickPass *hpasses, const BrickD
             dim3 grid(1u << (d.N - K), npairs);
             brick_pass_kernel<C, K, R, TH><<<grid, TH, smem, st>>>(d, side, hpasses[d.pass_off[side] + p], dp.gates,
                                                                     dp.rpasses, dp.rgates, maps, states);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+template <typename C, int K, int R, int TH>
+cudaError_t run_passes_db(const BrickDev &d, const BrickPass *hpasses, const BrickDevPlan &dp, int npairs,
+                          const C *maps, C *states, cudaStream_t st) {
+    int maxg = 0;
+    for (int i = 0; i < d.n_passes[0] + d.n_passes[1]; ++i) maxg = hpasses[i].n_gates > maxg ? hpasses[i].n_gates : maxg;
+    const size_t smem = ((size_t)2 * ((size_t)1 << K) + (size_t)maxg * (2 * 16 + MapSlot<C>::width)) * sizeof(C);
+    auto kern = brick_pass_db_kernel<C, K, R, TH>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TH, smem)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const uint64_t items = (uint64_t)npairs << (d.N - K);
+    const unsigned grid = (unsigned)std::min<uint64_t>(items, (uint64_t)sms * per_sm);
+    for (int side = 0; side < 2; ++side)
+        for (int p = 0; p < d.n_passes[side]; ++p) {
+            kern<<<grid, TH, smem, st>>>(d, side, hpasses[d.pass_off[side] + p], npairs, dp.gates, dp.rpasses,
+                                          dp.rgates, maps, states);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     return cudaSuccess;
@@ -621,7 +763,7 @@ cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const Bric
         if (fp32) brick_init_kernel<float2><<<ib, 256, 0, st>>>(d, npairs, (float2 *)states);
         else brick_init_kernel<double2><<<ib, 256, 0, st>>>(d, npairs, (double2 *)states);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const int key = d.tile_bits * 100 + dp.win_bits * 10 + (dp.threads == 256 ? 1 : 0);
+        const int key = dp.persist * 10000 + d.tile_bits * 100 + dp.win_bits * 10 + (dp.threads == 256 ? 1 : 0);
         if (fp32) {
             const float2 *mp = (const float2 *)maps;
             float2 *sp = (float2 *)states;
@@ -631,6 +773,8 @@ cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const Bric
                 case 1340: e = run_passes<float2, 13, 4, 512>(d, hpasses, dp, npairs, mp, sp, st); break;
                 case 1341: e = run_passes<float2, 13, 4, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
                 case 1351: e = run_passes<float2, 13, 5, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 11340: e = run_passes_db<float2, 13, 4, 512>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 11351: e = run_passes_db<float2, 13, 5, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
                 default: return cudaErrorInvalidValue;
             }
         } else {
