@@ -62,10 +62,14 @@ def parse():
     ap.add_argument("--workload", default="brickwork", choices=sorted(WORKLOADS),
                     help="brickwork (the headline workload), hea (n=50, L=1..8), hea_paper (n=50, L=1..8) "
                          "or local (n=20, T=20..100)")
+    ap.add_argument("--depth", type=int, default=0,
+                    help="run one depth group only (l or L; profiling runs of a single tile-pass shape)")
     a = ap.parse_args()
     WORK.update(WORKLOADS[a.workload])
     if a.pairs == 100_000 and a.workload != "brickwork":
         a.pairs = WORK["pairs"]
+    if a.depth:
+        WORK["depth_min"] = WORK["depth_max"] = a.depth
     return a
 
 
@@ -84,6 +88,8 @@ def workload_config(args, world):
                          "CNOT walls on even then odd bonds",
             "local": "local random circuits n=20, T uniform in {20,40,...,100} Haar U(4) gates on uniformly "
                      "random neighbour bonds per circuit"}[WORK["name"]]
+    if args.depth:
+        desc += f" (single depth {args.depth} only)"
     return {"workload": f"{desc}, {args.pairs} pairs per step per GPU",
             "n": WORK["n"], "depth": list(WORK["T"]) if "T" in WORK else [WORK["depth_min"], WORK["depth_max"]],
             "pairs_per_step": args.pairs,

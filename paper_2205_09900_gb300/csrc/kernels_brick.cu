@@ -356,23 +356,26 @@ struct WinApply<float2, k, R> {
         float2 t[32];
 #pragma unroll
         for (int e = 0; e < 32; ++e) t[e] = T[e];
+        // the four outputs of a quad accumulate side by side (inputs outer,
+        // outputs inner), so consecutive packed FMAs are independent
 #pragma unroll
         for (int i = 0; i < (1 << R); ++i) {
             if (i & (3 << k)) continue;
-            float2 x[4], xs[4];
+            float2 x[4], xs[4], acc[4];
             x[0] = v[i]; x[1] = v[i | (1 << k)]; x[2] = v[i | (2 << k)]; x[3] = v[i | (3 << k)];
 #pragma unroll
             for (int f = 0; f < 4; ++f) xs[f] = make_float2(x[f].y, x[f].x);
 #pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                float2 acc = make_float2(0.f, 0.f);
+            for (int o = 0; o < 4; ++o) acc[o] = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int f = 0; f < 4; ++f) {
-                    acc = ffma2(t[2 * (4 * o + f)], x[f], acc);
-                    acc = ffma2(t[2 * (4 * o + f) + 1], xs[f], acc);
-                }
-                v[i | (o << k)] = acc;
+            for (int f = 0; f < 4; ++f) {
+#pragma unroll
+                for (int o = 0; o < 4; ++o) acc[o] = ffma2(t[2 * (4 * o + f)], x[f], acc[o]);
+#pragma unroll
+                for (int o = 0; o < 4; ++o) acc[o] = ffma2(t[2 * (4 * o + f) + 1], xs[f], acc[o]);
             }
+#pragma unroll
+            for (int o = 0; o < 4; ++o) v[i | (o << k)] = acc[o];
         }
     }
 };
