@@ -504,11 +504,16 @@ def main():
     peak = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     if prec == fp.PREC_FP64:
         peak = peak / 64.0       # FP64 FMA rate is a small fraction of FP32 on this part
-    traffic = None
     roof = {"bound": "alu", "kernel": fp.K_NAMES.get(cls, str(cls)), "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": traffic,
+            "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
             "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz",
             "kernel_ms_share": ks.ms[cls] / ms if ms else None}
+    if WORK["name"] == "brickwork" and prec == fp.PREC_FP32:
+        # DRAM bytes (read + write) of the dominant kernel from one ncu capture of the current
+        # tile-pass code: brick_pass_kernel<float2, 14, 5, 256>, depth 10, one pass over 256 pairs
+        roof["traffic"] = 537.914112e6 + 477.020928e6
+        roof["traffic_launch"] = ("brick_pass_kernel<float2,14,5,256>, l=10, one tile pass of 256 pairs; "
+                                  "algorithmic bytes 2 x 256 x 2^18 x 8 = 1.0737e9")
 
     metric = {"brickwork": METRIC, "hea": "Tr(U^dagger V) contractions/s at n=50 (HEA, L=1..8)",
               "hea_paper": "Tr(U^dagger V) contractions/s at n=50 (paper HEA with CNOT walls, L=1..8)",

@@ -544,7 +544,7 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
         }
     }
     if (!have && !idx.empty()) {
-        const uint64_t nt = std::min<uint64_t>(idx.size(), 96);
+        const uint64_t nt = std::min<uint64_t>(idx.size(), 192);   // several waves of tiles per variant
         const int n_raw = d.kind == FP_HEA ? l * d.n : (int)layout_brickwork(d.n, l).size();
         const int n_maps = (d.kind == FP_HEA ? 2 * d.n : d.n - 1) * (l - 1);
         const size_t celem = fp32 ? sizeof(float2) : sizeof(double2);
