@@ -129,11 +129,6 @@ struct fp_ensemble {
     // CUDA graphs of the brickwork sub-batch pipeline
     cudaStream_t gst = nullptr;
     cudaEvent_t gev[2] = {};
-    // brickwork sampler stream: sub-batch i+1 is sampled into the second pair
-    // and raw-gate buffers while sub-batch i is contracted
-    cudaStream_t sst = nullptr;
-    cudaEvent_t sev_up = nullptr, sev_done[2] = {}, sev_t[2][2] = {};
-    DBuf d_pairs2, d_raw2;
     std::map<GraphKey, cudaGraphExec_t> graphs;
     uint64_t graph_replays = 0;
     // FP_FLAG_SKIP_INFEASIBLE: slots (relative to the current call's first pair)
@@ -632,9 +627,7 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
     bool both = false;
     if (bd.tile_bits == 0) brick_smem_bytes(bd, fp32, &both);
     const size_t per_state = bd.tile_bits ? 2 * S * celem : (both ? 0 : S * celem);
-    // raw gates and pair records are double-buffered (sampling of the next sub-batch
-    // overlaps the contraction of the current one)
-    const size_t per_pair = 2 * per_raw + per_map + per_state;
+    const size_t per_pair = per_raw + per_map + per_state;
     uint64_t cap = std::max<uint64_t>(1, std::min<uint64_t>(65535, E->ws_budget / per_pair));
     // flop count of the sweep (complex multiply-adds): 4 per amplitude per gate
     const double cmac_pair = 4.0 * (double)S * (double)maps_per_pair(bd);
@@ -643,71 +636,31 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
     sp.n = d.n;
     sp.raw_kind = E->raw_kind;
     sp.self_pair = (d.flags & FP_FLAG_SELF_PAIR) ? 1 : 0;
-    std::vector<std::pair<uint64_t, uint64_t>> subs;   // (offset into idx, pairs)
-    for (uint64_t done = 0; done < count; done += std::min<uint64_t>(cap, count - done))
-        subs.push_back({done, std::min<uint64_t>(cap, count - done)});
-    const uint64_t nmax = subs.front().second;
-    DBuf *pairs_b[2] = {&E->d_pairs, &E->d_pairs2}, *raw_b[2] = {&E->d_raw, &E->d_raw2};
-    for (int b = 0; b < 2 && b < (int)subs.size(); ++b) {
-        CK(pairs_b[b]->reserve(nmax * sizeof(PairInfo)));
-        CK(raw_b[b]->reserve(nmax * per_raw));
-    }
-    CK(E->d_maps.reserve(nmax * per_map));
-    CK(E->d_states.reserve(std::max<size_t>(16, nmax * per_state)));
-    // Sub-batch j: its pair records go up on the ensemble stream (after sub-batch j-2,
-    // the last user of buffer j%2, has been contracted there), then the sampler stream
-    // draws its gates while the ensemble stream contracts sub-batch j-1.
-    auto enqueue_sample = [&](size_t j) -> fp_status {
-        const uint64_t off = subs[j].first, nb = subs[j].second;
+    for (uint64_t done = 0; done < count;) {
+        const uint64_t nb = std::min<uint64_t>(cap, count - done);
         std::vector<PairInfo> pinfo(nb);
         for (uint64_t i = 0; i < nb; ++i) {
             std::memset(&pinfo[i], 0, sizeof(PairInfo));
-            pinfo[i].pair = first + idx[off + i];
+            pinfo[i].pair = first + idx[done + i];
             pinfo[i].n_raw = n_raw;
             pinfo[i].raw_off = (int64_t)i * 2 * n_raw;
-            pinfo[i].out = (int64_t)idx[off + i];
+            pinfo[i].out = (int64_t)idx[done + i];
         }
-        CK(cudaMemcpyAsync(pairs_b[j % 2]->p, pinfo.data(), nb * sizeof(PairInfo), cudaMemcpyHostToDevice, E->st));
-        CK(cudaEventRecord(E->sev_up, E->st));
-        CK(cudaStreamWaitEvent(E->sst, E->sev_up, 0));
-        if (E->timing) CK(cudaEventRecord(E->sev_t[j % 2][0], E->sst));
-        CK(launch_sample(sp, pairs_b[j % 2]->as<PairInfo>(), (int)nb, n_raw, raw_b[j % 2]->as<double2>(), E->sst, 64));
-        if (E->timing) CK(cudaEventRecord(E->sev_t[j % 2][1], E->sst));
-        CK(cudaEventRecord(E->sev_done[j % 2], E->sst));
-        return FP_OK;
-    };
-    auto sample_time = [&](size_t j) -> fp_status {   // FP_FLAG_TIMING: sampler time of sub-batch j
-        if (!E->timing) return FP_OK;
-        CK(cudaEventSynchronize(E->sev_t[j % 2][1]));
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, E->sev_t[j % 2][0], E->sev_t[j % 2][1]));
-        E->kst.ms[FP_K_SAMPLE] += ms;
-        E->kst.launches[FP_K_SAMPLE] += 1;
-        E->kst.work[FP_K_SAMPLE] += (double)subs[j].second;
-        return FP_OK;
-    };
-    // device time of sub-batch j: from the end of sub-batch j-1 (for j = 0, before its
-    // sampling) to the end of its contraction, so overlapped sampling is counted once
-    CK(cudaEventRecord(E->ev0, E->st));
-    fp_status fs = enqueue_sample(0);
-    if (fs != FP_OK) return fs;
-    for (size_t j = 0; j < subs.size(); ++j) {
-        const uint64_t nb = subs[j].second;
-        if (j > 0) CK(cudaEventRecord(E->ev0, E->st));
-        if (j + 1 < subs.size() && (fs = enqueue_sample(j + 1)) != FP_OK) return fs;
-        const PairInfo *pairs_d = pairs_b[j % 2]->as<PairInfo>();
-        const double2 *raw_d = raw_b[j % 2]->as<double2>();
+        CK(upload(E->d_pairs, pinfo, E->st));
+        CK(E->d_raw.reserve(nb * per_raw));
+        CK(E->d_maps.reserve(nb * per_map));
+        CK(E->d_states.reserve(std::max<size_t>(16, nb * per_state)));
         const double G = (double)std::max(bd.n_layers[0], bd.n_layers[1]) * bd.m;
         const double err_scale = FP_ERR_SAFETY * (fp32 ? 0x1.0p-24 : 0x1.0p-53) * std::sqrt(G);
-        CK(cudaStreamWaitEvent(E->st, E->sev_done[j % 2], 0));
-        // CUDA graph replay: the launch sequence of a sub-batch's contraction (maps,
-        // init, passes, meet) is captured once per (depth, precision, size, buffers) on
-        // the ensemble's internal stream and replayed; the first sub-batch of a shape
-        // runs directly (it also sets the kernels' shared-memory attributes outside
-        // any capture).
+        // CUDA graph replay: the launch sequence of a sub-batch (sampler, maps,
+        // init, passes, meet) is captured once per (depth, precision, size,
+        // buffers) on the ensemble's internal stream and replayed with fresh
+        // pair records; the first sub-batch of a shape runs directly (it also
+        // sets the kernels' shared-memory attributes outside any capture).
         const bool use_graph = !E->timing && !(d.flags & FP_FLAG_NO_GRAPHS);
-        GraphKey gk{key, nb, pairs_d, raw_d, E->d_maps.p, E->d_states.p, tr, kappa, err};
+        GraphKey gk{key, nb, E->d_pairs.p, E->d_raw.p, E->d_maps.p, E->d_states.p, tr, kappa, err};
         auto git = use_graph ? E->graphs.find(gk) : E->graphs.end();
+        CK(cudaEventRecord(E->ev0, E->st));
         if (use_graph && git != E->graphs.end() && git->second) {
             CK(cudaEventRecord(E->gev[0], E->st));
             CK(cudaStreamWaitEvent(E->gst, E->gev[0], 0));
@@ -717,10 +670,16 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
             E->graph_replays++;
         } else {
             {
+                KTimer t(E, FP_K_SAMPLE);
+                CK(launch_sample(sp, E->d_pairs.as<PairInfo>(), (int)nb, n_raw, E->d_raw.as<double2>(), E->st));
+                CK(t.stop((double)nb));
+            }
+            {
                 KTimer t(E, FP_K_BRICK);
                 int nl = 0;
-                CK(launch_brick(bd, bp.passes.data(), it->second->dp, pairs_d, (int)nb, raw_d, E->d_maps.p,
-                                E->d_states.p, fp32, err_scale, tr, kappa, err, E->st, &nl));
+                CK(launch_brick(bd, bp.passes.data(), it->second->dp, E->d_pairs.as<PairInfo>(), (int)nb,
+                                E->d_raw.as<double2>(), E->d_maps.p, E->d_states.p, fp32, err_scale, tr, kappa, err,
+                                E->st, &nl));
                 CK(t.stop(cmac_pair * (double)nb));
                 if (E->timing) E->kst.launches[FP_K_BRICK] += (uint64_t)(nl - 1);
             }
@@ -732,9 +691,12 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
                 cudaGraph_t graph = nullptr;
                 cudaGraphExec_t exec = nullptr;
                 CK(cudaStreamBeginCapture(E->gst, cudaStreamCaptureModeThreadLocal));
+                cudaError_t ce = launch_sample(sp, E->d_pairs.as<PairInfo>(), (int)nb, n_raw, E->d_raw.as<double2>(), E->gst);
                 int nl = 0;
-                cudaError_t ce = launch_brick(bd, bp.passes.data(), it->second->dp, pairs_d, (int)nb, raw_d,
-                                              E->d_maps.p, E->d_states.p, fp32, err_scale, tr, kappa, err, E->gst, &nl);
+                if (ce == cudaSuccess)
+                    ce = launch_brick(bd, bp.passes.data(), it->second->dp, E->d_pairs.as<PairInfo>(), (int)nb,
+                                      E->d_raw.as<double2>(), E->d_maps.p, E->d_states.p, fp32, err_scale, tr, kappa,
+                                      err, E->gst, &nl);
                 cudaError_t ee = cudaStreamEndCapture(E->gst, &graph);
                 if (ce == cudaSuccess && ee == cudaSuccess && graph) {
                     ce = cudaGraphInstantiate(&exec, graph, 0);
@@ -751,7 +713,7 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
         CK(cudaEventElapsedTime(&ms, E->ev0, E->ev1));
         if (gpu_ms) *gpu_ms += ms;
         E->kst.pairs += nb;
-        if ((fs = sample_time(j)) != FP_OK) return fs;
+        done += nb;
     }
     return FP_OK;
 }
@@ -918,13 +880,6 @@ fp_status fp_ensemble_create(const fp_ensemble_desc *desc, void *cuda_stream, fp
     CK(cudaStreamCreateWithFlags(&E->gst, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&E->gev[0], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&E->gev[1], cudaEventDisableTiming));
-    CK(cudaStreamCreateWithFlags(&E->sst, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&E->sev_up, cudaEventDisableTiming));
-    for (int k = 0; k < 2; ++k) {
-        CK(cudaEventCreateWithFlags(&E->sev_done[k], cudaEventDisableTiming));
-        CK(cudaEventCreate(&E->sev_t[k][0]));
-        CK(cudaEventCreate(&E->sev_t[k][1]));
-    }
     for (int k = 0; k < 2 * FP_K_CLASSES; ++k) CK(cudaEventCreate(&E->kev[k]));
     *out = E.release();
     return FP_OK;
@@ -942,13 +897,6 @@ void fp_ensemble_destroy(fp_ensemble *ens) {
     for (auto &kv : ens->graphs) if (kv.second) cudaGraphExecDestroy(kv.second);
     for (int k = 0; k < 2; ++k) if (ens->gev[k]) cudaEventDestroy(ens->gev[k]);
     if (ens->gst) cudaStreamDestroy(ens->gst);
-    if (ens->sst) cudaStreamSynchronize(ens->sst);
-    if (ens->sev_up) cudaEventDestroy(ens->sev_up);
-    for (int k = 0; k < 2; ++k) {
-        if (ens->sev_done[k]) cudaEventDestroy(ens->sev_done[k]);
-        for (int h = 0; h < 2; ++h) if (ens->sev_t[k][h]) cudaEventDestroy(ens->sev_t[k][h]);
-    }
-    if (ens->sst) cudaStreamDestroy(ens->sst);
     delete ens;
 }
 

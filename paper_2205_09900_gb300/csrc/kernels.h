@@ -15,11 +15,9 @@ struct SampleParams {
     int32_t self_pair;
 };
 
-// Sampler: raw gates of U and V for every pair of the batch (FP64).  `threads`
-// (64 or 128) per block; 64 lets a sampler block share an SM with a tile pass.
+// Sampler: raw gates of U and V for every pair of the batch (FP64).
 cudaError_t launch_sample(const SampleParams &sp, const PairInfo *pairs, int npairs, int max_raw,
-                          double2 *raw, cudaStream_t st,
-                          int threads = 128);
+                          double2 *raw, cudaStream_t st);
 // Merged gates: ordered products of raw gates (FP64).
 cudaError_t launch_merge(const PairInfo *pairs, int npairs, int max_merged, const DevPlan *plans,
                          const MergeItem *items, const MergeRef *refs, const double2 *raw,

@@ -227,11 +227,10 @@ __global__ void table_kernel(const PairInfo *__restrict__ pairs, const DevPlan *
 }  // namespace
 
 cudaError_t launch_sample(const SampleParams &sp, const PairInfo *pairs, int npairs, int max_raw,
-                          double2 *raw, cudaStream_t st, int threads) {
+                          double2 *raw, cudaStream_t st) {
     if (npairs <= 0) return cudaSuccess;
-    if (threads != 64 && threads != 128) return cudaErrorInvalidValue;
-    dim3 grid((2 * max_raw + threads - 1) / threads, npairs);
-    sample_kernel<<<grid, threads, 0, st>>>(sp, pairs, raw);
+    dim3 grid((2 * max_raw + 127) / 128, npairs);
+    sample_kernel<<<grid, 128, 0, st>>>(sp, pairs, raw);
     return cudaGetLastError();
 }
 
