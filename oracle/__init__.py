@@ -86,6 +86,8 @@ def lib():
             L.orc_weingarten_f2_brickwork.restype = ctypes.c_double
             L.orc_weingarten_fk_brickwork.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
             L.orc_weingarten_fk_brickwork.restype = ctypes.c_double
+            L.orc_weingarten_fkq_brickwork.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.orc_weingarten_fkq_brickwork.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -190,9 +192,9 @@ def weingarten_f2_brickwork(n, l):
     return float(lib().orc_weingarten_f2_brickwork(n, l))
 
 
-def weingarten_fk_brickwork(n, l, k):
-    """Exact ensemble F^(k) (k = 2, 3) of brickwork circuits."""
-    return float(lib().orc_weingarten_fk_brickwork(n, l, k))
+def weingarten_fk_brickwork(n, l, k, q=2):
+    """Exact ensemble F^(k) (k = 2, 3) of brickwork circuits of qudits of dimension q."""
+    return float(lib().orc_weingarten_fkq_brickwork(n, l, k, q))
 
 
 def bootstrap(tr, group, n_groups, kmax, B, seed):

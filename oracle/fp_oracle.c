@@ -576,18 +576,19 @@ void orc_bootstrap(const double *tr, const int32_t *group, int64_t count, int n_
 }
 
 /* ------------------------------------------------------------------------ */
-/* Exact ensemble F^(k), k = 2 or 3, of brickwork circuits: the same         */
-/* statistical-mechanics model as orc_weingarten_f2_brickwork with the       */
+/* Exact ensemble F^(k), k = 2 or 3, of brickwork circuits of qudits of      */
+/* local dimension q (Sec. "Frame potential": the paper's qudit remark): the */
+/* same statistical-mechanics model as orc_weingarten_f2_brickwork with the  */
 /* pairings running over the permutation group S_k.  Averaging a Haar U(d)   */
-/* gate over k copies of U and k of U^* gives                                */
+/* gate, d = q^2, over k copies of U and k of U^* gives                      */
 /*   sum_{sigma, tau in S_k} Wg(sigma^-1 tau, d) |sigma>><<tau|              */
-/* with the Weingarten function of U(d), d = 4 (Collins 2003):               */
+/* with the Weingarten function of U(d) (Collins 2003):                       */
 /*   k = 2: Wg(e) = 1/(d^2-1), Wg(2-cycle) = -1/(d(d^2-1));                  */
 /*   k = 3: Wg(e) = (d^2-2)/(d(d^2-1)(d^2-4)), Wg(2-cycle) =                 */
 /*          -1/((d^2-1)(d^2-4)), Wg(3-cycle) = 2/(d(d^2-1)(d^2-4)).          */
 /* Along a qubit wire, the output pairing sigma_a of a gate meets the input  */
-/* pairing tau_b of the next gate on the wire: q^{#cycles(sigma_a^-1 tau_b)} */
-/* with q = 2; a qubit touched by no gate gives q^{2k}.  Summed with the     */
+/* pairing tau_b of the next gate on the wire: q^{#cycles(sigma_a^-1 tau_b)};*/
+/* a qudit touched by no gate gives q^{2k}.  Summed with the                 */
 /* same explicit transfer matrix over bonds as the k = 2 routine.            */
 /* ------------------------------------------------------------------------ */
 static int perms_of(int k, int P[6][3])
@@ -621,10 +622,10 @@ static int cycles_of(const int *a, const int *b, int k)   /* #cycles of a^-1 b *
     return c;
 }
 
-double orc_weingarten_fk_brickwork(int n, int l, int k)
+double orc_weingarten_fkq_brickwork(int n, int l, int k, int q)
 {
-    if (n < 2 || l < 1 || k < 2 || k > 3) return NAN;
-    const double d = 4.0;
+    if (n < 2 || l < 1 || k < 2 || k > 3 || q < 2) return NAN;
+    const double d = (double)q * q;
     int Pm[6][3];
     const int np = perms_of(k, Pm), sg = np * np;   /* (sigma, tau) states per gate */
     double wg_by_cycles[4] = {0, 0, 0, 0};
@@ -641,9 +642,9 @@ double orc_weingarten_fk_brickwork(int n, int l, int k)
         for (int t = 0; t < np; ++t) {
             int c = cycles_of(Pm[s], Pm[t], k);
             wg[s * np + t] = wg_by_cycles[c];
-            link[s][t] = ldexp(1.0, c);
+            link[s][t] = pow((double)q, c);
         }
-    const double idle = ldexp(1.0, 2 * k);
+    const double idle = pow((double)q, 2 * k);
     int P = (l == 1) ? 1 : 2 * (l - 1), nb = n - 1;
     int *g_of_bond = calloc(nb, sizeof(int));
     int **times = calloc(nb, sizeof(int *));
@@ -721,6 +722,8 @@ double orc_weingarten_fk_brickwork(int n, int l, int k)
     free(times); free(g_of_bond); free(v); free(w);
     return result;
 }
+
+double orc_weingarten_fk_brickwork(int n, int l, int k) { return orc_weingarten_fkq_brickwork(n, l, k, 2); }
 
 /* ------------------------------------------------------------------------ */
 /* Exact ensemble F^(2) of brickwork circuits (the statistical-mechanics    */

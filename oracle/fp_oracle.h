@@ -97,6 +97,8 @@ double orc_weingarten_f2_brickwork(int n, int l);
 /* Exact ensemble F^(k), k = 2 or 3, of brickwork circuits (the same model
  * over S_k pairings); NaN for other k. */
 double orc_weingarten_fk_brickwork(int n, int l, int k);
+/* The same for qudits of local dimension q >= 2 (Haar U(q^2) gates). */
+double orc_weingarten_fkq_brickwork(int n, int l, int k, int q);
 /* Bootstrap distribution of F^(k) per group (Supplementary "Bootstrapping for
  * uncertainty quantification"): every group's N_g traces are resampled N_g
  * times with replacement, B times.  Draw i of resample b in group g takes

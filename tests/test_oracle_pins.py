@@ -296,6 +296,30 @@ def test_weingarten_k3_closed_forms():
         assert abs(a - b) < 1e-12 * b
 
 
+@pytest.mark.parametrize("q", [3, 4])
+def test_weingarten_qudits_closed_forms_and_bound(q):
+    # qudits of local dimension q (Haar U(q^2) gates): n = 2 is one Haar gate,
+    # F^(k) = k! for k <= q^2; l = 1 is a product of floor(n/2) gates and an idle
+    # qudit with Tr(I_q)^{2k} = q^{2k}; the paper's Eq. theory_eq bound
+    # F^(2) <= 2 (1 + (2q/(q^2+1))^{2(l-1)})^{n_g - 1}, an equality at l = 1 for even n
+    for l in range(1, 5):
+        for k in (2, 3):
+            assert abs(O.weingarten_fk_brickwork(2, l, k, q) - math.factorial(k)) < 1e-11
+    for n in range(2, 9):
+        for k in (2, 3):
+            exact = math.factorial(k) ** (n // 2) * float(q) ** (2 * k * (n % 2))
+            assert abs(O.weingarten_fk_brickwork(n, 1, k, q) - exact) < 1e-9 * exact
+    for n in (4, 6, 8):
+        ng = n // 2
+        for l in range(1, 5):
+            bound = 2 * (1 + (2 * q / (q * q + 1)) ** (2 * (l - 1))) ** (ng - 1)
+            f = O.weingarten_fk_brickwork(n, l, 2, q)
+            if l == 1:
+                assert abs(f - bound) < 1e-9 * bound
+            else:
+                assert 2.0 < f < bound
+
+
 @pytest.mark.parametrize("n,l", [(4, 2), (5, 3)])
 def test_weingarten_k3_matches_monte_carlo(n, l):
     d = O.desc(O.PARALLEL, n, l, seed=300 + 10 * n + l)
