@@ -302,9 +302,11 @@ def exact_fk_report(fp, mc=None):
                 row["monte_carlo"] = [F, se]
                 row["z"] = (F - f) / se if se > 0 else None
             out[f"F{k}"][str(l)] = row
+    out["F2_qutrits"] = {str(l): fp.exact_brickwork_fk(WORK["n"], l, 2, q=3) for l in range(2, 11)}
     out["note"] = ("variance-free reference: Haar average of every gate as a sum over S_k pairings with U(4) "
                    "Weingarten weights, summed by an FP64 transfer-matrix sweep over the bonds; Monte Carlo "
-                   "z-scores use the naive standard error, unreliable for the heavy tails at l <= 4")
+                   "z-scores use the naive standard error, unreliable for the heavy tails at l <= 4; "
+                   "F2_qutrits: the same for qudits of local dimension 3 (Haar U(9) gates)")
     return out
 
 

@@ -272,6 +272,12 @@ fp_status fp_design_layers(int32_t n_depths, const double *depths, const double 
  * does not fit in free device memory. */
 fp_status fp_exact_brickwork_fk(int32_t n, int32_t l, int32_t k, void *cuda_stream, double *F);
 
+/* The same for brickwork circuits of qudits of local dimension q (2 <= q <= 64):
+ * Haar U(q^2) gates, Weingarten function of U(q^2), links q^{#cycles} (the paper
+ * treats general q in Sec. "Frame potential"; its Eq. theory_eq bound has q).
+ * fp_exact_brickwork_fk is q = 2. */
+fp_status fp_exact_brickwork_fkq(int32_t n, int32_t l, int32_t k, int32_t q, void *cuda_stream, double *F);
+
 /* Monte Carlo frame potential.  Contracts pairs first, first+1, ... in batches
  * until every group's relative standard error of F^(2) (or of F^(1) when
  * k_max = 1) is <= target_rel_stderr, or max_pairs pairs are done.

@@ -30,7 +30,7 @@ STATUS = {0: "FP_OK", -1: "FP_ERR_ARG", -2: "FP_ERR_CUDA", -3: "FP_ERR_OOM", -4:
 EXPORTED = ["fp_ensemble_create", "fp_ensemble_destroy", "fp_groups", "fp_pair_groups", "fp_export_gates",
             "fp_trace_batch", "fp_reduce_moments", "fp_frame_potential", "fp_kernel_stats_get",
             "fp_trace_brick_static", "fp_cv_frame_potential", "fp_gemm_bf16", "fp_bootstrap", "fp_epsilon_max",
-            "fp_design_layers", "fp_exact_brickwork_fk", "fp_last_error"]
+            "fp_design_layers", "fp_exact_brickwork_fk", "fp_exact_brickwork_fkq", "fp_last_error"]
 
 
 class FpError(RuntimeError):
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
     L.fp_epsilon_max.argtypes = [f64, i32, i32, i32, P(f64)]
     L.fp_design_layers.argtypes = [i32, vp, vp, i32, i32, i32, f64, f64, P(f64), P(f64), P(f64)]
     L.fp_exact_brickwork_fk.argtypes = [i32, i32, i32, vp, P(f64)]
+    L.fp_exact_brickwork_fkq.argtypes = [i32, i32, i32, i32, vp, P(f64)]
     L.fp_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name not in ("fp_ensemble_destroy", "fp_last_error"):
@@ -152,12 +153,16 @@ def gemm_bf16(A, Bt, bias=None, mode=0, Z=None, C=None, C_bf16=None, Ct_bf16=Non
                                _ptr(C), _ptr(C_bf16), _ptr(Ct_bf16), st))
 
 
-def exact_brickwork_fk(n, l, k, stream=None):
-    """Exact ensemble F^(k) (k = 2, 3) of depth-l brickwork circuits on n qubits,
-    by the Weingarten transfer-matrix sweep on the GPU (fp_exact_brickwork_fk)."""
+def exact_brickwork_fk(n, l, k, stream=None, q=2):
+    """Exact ensemble F^(k) (k = 2, 3) of depth-l brickwork circuits on n qubits (or
+    qudits of local dimension q), by the Weingarten transfer-matrix sweep on the GPU
+    (fp_exact_brickwork_fk / fp_exact_brickwork_fkq)."""
     out = ctypes.c_double()
     st = None if stream is None else ctypes.c_void_p(stream)
-    _check(load().fp_exact_brickwork_fk(n, l, k, st, ctypes.byref(out)))
+    if q == 2:
+        _check(load().fp_exact_brickwork_fk(n, l, k, st, ctypes.byref(out)))
+    else:
+        _check(load().fp_exact_brickwork_fkq(n, l, k, q, st, ctypes.byref(out)))
     return out.value
 
 

@@ -1,4 +1,5 @@
-// weingarten.cu -- exact ensemble F^(k) (k = 2, 3) of brickwork circuits.
+// weingarten.cu -- exact ensemble F^(k) (k = 2, 3) of brickwork circuits of qubits
+// or of qudits of local dimension q (Haar U(q^2) gates).
 //
 // Averaging every Haar U(4) gate of the cyclic U^dagger V circuit over the
 // Haar measure turns the k-th moment |Tr(U^dagger V)|^{2k} into a classical
@@ -6,7 +7,7 @@
 // Sec. "Frame potential"): each gate carries an output and an input pairing
 // sigma, tau in S_k with weight Wg(sigma^-1 tau) (the Weingarten function of
 // U(4)), and consecutive gates on a qubit wire, output pairing sigma_a then
-// input pairing tau_b, meet with weight 2^{#cycles(sigma_a^-1 tau_b)}.
+// input pairing tau_b, meet with weight q^{#cycles(sigma_a^-1 tau_b)}.
 //
 // After the middle and cyclic merges a depth-l brickwork pair is a cyclic
 // brickwork of P = 2(l-1) time positions; bond b holds the gates at the
@@ -15,7 +16,7 @@
 // Storing a gate's output pairing in slot t and its input pairing in slot
 // t-1 (mod P), the variables of one bond occupy every slot exactly once, and
 // the transfer across qubit b is
-//   (1) the 2^{#cycles} link matrix applied to every slot (each link of the
+//   (1) the q^{#cycles} link matrix applied to every slot (each link of the
 //       qubit pairs one slot of bond b-1 with the same slot of bond b), then
 //   (2) the Wg factors of bond b's gates, a diagonal over slot pairs (t, t-1).
 // The chain ends close with the links among one bond's gates, slots (t, t+1).
@@ -35,7 +36,7 @@ constexpr int kMaxSlots = 22;   // k = 2: l <= 12; k = 3 is limited to 12 slots 
 
 struct WgTab {
     int P;                  // slots
-    double link[36];        // link[x * s + y] = 2^{#cycles(x^-1 y)}
+    double link[36];        // link[x * s + y] = q^{#cycles(x^-1 y)}
     double wg[36];          // wg[sigma * s + tau] = Wg(sigma^-1 tau)
 };
 
@@ -215,10 +216,12 @@ cudaError_t run_sweep(const WgTab &T, int n, uint64_t N, double *v, double *maxe
 }  // namespace
 }  // namespace fpk
 
-extern "C" fp_status fp_exact_brickwork_fk(int32_t n, int32_t l, int32_t k, void *cuda_stream, double *F) {
+extern "C" fp_status fp_exact_brickwork_fkq(int32_t n, int32_t l, int32_t k, int32_t q, void *cuda_stream,
+                                             double *F) {
     using namespace fpk;
     if (!F) return api_fail(FP_ERR_ARG, "F is NULL");
     if (n < 2 || n > 1 << 20) return api_fail(FP_ERR_ARG, "n outside [2, 2^20]");
+    if (q < 2 || q > 64) return api_fail(FP_ERR_ARG, "local dimension q outside [2, 64]");
     if (k != 2 && k != 3) return api_fail(FP_ERR_ARG, "k must be 2 or 3");
     if (l < 2 || (k == 2 && l > 12) || (k == 3 && l > 7))
         return api_fail(FP_ERR_ARG, "depth l outside [2, 12] (k = 2) or [2, 7] (k = 3)");
@@ -226,11 +229,11 @@ extern "C" fp_status fp_exact_brickwork_fk(int32_t n, int32_t l, int32_t k, void
     T.P = 2 * (l - 1);
     int p[6][3];
     const int s = perms(k, p);
-    const double d = 4.0;
+    const double d = (double)q * q;   // Haar U(q^2) gates on neighbouring qudits
     for (int a = 0; a < s; ++a)
         for (int b = 0; b < s; ++b) {
             const int c = cycles(p[a], p[b], k);
-            T.link[a * s + b] = std::ldexp(1.0, c);
+            T.link[a * s + b] = std::pow((double)q, c);
             double w;
             if (k == 2) w = c == 2 ? 1.0 / (d * d - 1) : -1.0 / (d * (d * d - 1));
             else w = c == 3 ? (d * d - 2) / (d * (d * d - 1) * (d * d - 4))
@@ -258,4 +261,8 @@ extern "C" fp_status fp_exact_brickwork_fk(int32_t n, int32_t l, int32_t k, void
     cudaFree(buf);
     if (e != cudaSuccess) return api_fail(FP_ERR_CUDA, cudaGetErrorString(e));
     return FP_OK;
+}
+
+extern "C" fp_status fp_exact_brickwork_fk(int32_t n, int32_t l, int32_t k, void *cuda_stream, double *F) {
+    return fp_exact_brickwork_fkq(n, l, k, 2, cuda_stream, F);
 }

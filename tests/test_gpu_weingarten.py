@@ -43,6 +43,14 @@ def test_exact_f3_matches_oracle(fp, n, l):
     assert abs(got - ref) <= TOL * abs(ref), (got, ref)
 
 
+@pytest.mark.parametrize("q,n,l,k", [(3, 2, 3, 2), (3, 4, 2, 2), (3, 6, 3, 2), (3, 8, 4, 2), (4, 7, 3, 2),
+                                     (3, 50, 4, 2), (3, 4, 2, 3), (3, 5, 3, 3), (4, 12, 3, 3)])
+def test_exact_fk_qudits_match_oracle(fp, q, n, l, k):
+    got = fp.exact_brickwork_fk(n, l, k, q=q)
+    ref = O.weingarten_fk_brickwork(n, l, k, q)
+    assert abs(got - ref) <= TOL * abs(ref), (got, ref)
+
+
 def test_exact_fk_full_size_properties(fp):
     # n = 50 at every depth the benchmark draws: above the Haar value k!, below the
     # paper's F^(2) bound 2 (1 + (4/5)^{2(l-1)})^{n_g - 1} (Eq. theory_eq, q = 2), and
@@ -73,3 +81,5 @@ def test_exact_fk_argument_checks(fp):
     for n, l, k in [(50, 1, 2), (50, 13, 2), (50, 8, 3), (50, 4, 4), (1, 4, 2)]:
         with pytest.raises(fp.FpError):
             fp.exact_brickwork_fk(n, l, k)
+    with pytest.raises(fp.FpError):
+        fp.exact_brickwork_fk(8, 3, 2, q=1)
