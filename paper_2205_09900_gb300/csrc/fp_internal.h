@@ -92,6 +92,7 @@ struct DevRecipe {
     int32_t merged;        // merged gate id, or -1 for constants
     int32_t nent;          // 2^(nc+nk+nn)
     int8_t src[16][4];     // merged-gate slots summed into entry e (-1: unused)
+    int8_t sgn[16][4];     // +1 / -1 weight of each summed slot (a fused CZ sign)
     double cre[16];        // constant entries (merged == -1)
     double cim[16];
 };

@@ -213,7 +213,7 @@ __global__ void table_kernel(const PairInfo *__restrict__ pairs, const DevPlan *
             if (M) {
                 for (int s = 0; s < 4; ++s) {
                     int k = r.src[e][s];
-                    if (k >= 0) { re += M[k].x; im += M[k].y; }
+                    if (k >= 0) { re += r.sgn[e][s] * M[k].x; im += r.sgn[e][s] * M[k].y; }
                 }
             } else {
                 re = r.cre[e];

@@ -156,10 +156,11 @@ void merge_sequence(std::vector<SeqEl> &seq) {
 }
 
 struct Factor {
-    int kind;               // 0 gate2, 1 gate1, 2 const diag
+    int kind;               // 0 gate2, 1 gate1, 2 const diag, 3 gate1 times a +-1 diagonal
     int q;
-    int merged;             // merged gate id (kinds 0, 1)
-    int slot_var[4];        // gate2: out_q, out_q1, in_q, in_q1; gate1: out, in; diag: y_q, y_q1
+    int merged;             // merged gate id (kinds 0, 1, 3)
+    int slot_var[4];        // gate2: out_q, out_q1, in_q, in_q1; gate1: out, in; diag: y_q, y_q1;
+                            // kind 3: gate1's out, in, then the diagonal's y_q, y_q1
     int nslots;
     double dre[4], dim[4];
     int side;               // 0 left, 1 right
@@ -168,8 +169,21 @@ struct Factor {
 
 int slot_entry(const Factor &f, const int *val) {
     if (f.kind == 0) return (val[0] * 2 + val[1]) * 4 + (val[2] * 2 + val[3]);
-    if (f.kind == 1) return val[0] * 2 + val[1];
+    if (f.kind == 1 || f.kind == 3) return val[0] * 2 + val[1];
     return val[0] * 2 + val[1];   // diagonal index
+}
+
+bool shares_var(const Factor &a, const Factor &b) {
+    for (int i = 0; i < a.nslots; ++i)
+        for (int j = 0; j < b.nslots; ++j)
+            if (a.slot_var[i] == b.slot_var[j]) return true;
+    return false;
+}
+
+bool sign_diagonal(const Factor &f) {   // a constant diagonal with entries +-1 (CZ products)
+    for (int e = 0; e < 4; ++e)
+        if (f.dim[e] != 0.0 || (f.dre[e] != 1.0 && f.dre[e] != -1.0)) return false;
+    return true;
 }
 
 }  // namespace
@@ -293,6 +307,38 @@ HostPlan make_plan(int n, const std::vector<GateSlot> &U, const std::vector<Gate
         for (auto &k : key) order[side].push_back(k.second);
     }
 
+    // Fusion: a constant +-1 diagonal (CZ) next to a 1-qubit factor on a shared
+    // segment in the processing order becomes one factor over their <= 3 segments.
+    // The CZ otherwise opens the neighbour's segment while the shared segment is
+    // still waiting for the 1-qubit op that closes it, one boundary bit more.
+    for (int side = 0; side < 2; ++side) {
+        std::vector<int> fused;
+        const std::vector<int> &ord = order[side];
+        for (size_t p = 0; p < ord.size(); ++p) {
+            if (p + 1 < ord.size()) {
+                const Factor A = fs[ord[p]], B = fs[ord[p + 1]];
+                const bool ab = A.kind == 2 && B.kind == 1, ba = A.kind == 1 && B.kind == 2;
+                if ((ab || ba) && shares_var(A, B)) {
+                    const Factor &X = ab ? B : A, &D = ab ? A : B;
+                    if (sign_diagonal(D)) {
+                        Factor F = X;
+                        F.kind = 3;
+                        F.slot_var[2] = D.slot_var[0];
+                        F.slot_var[3] = D.slot_var[1];
+                        F.nslots = 4;
+                        for (int e = 0; e < 4; ++e) { F.dre[e] = D.dre[e]; F.dim[e] = 0.0; }
+                        fs.push_back(F);
+                        fused.push_back((int)fs.size() - 1);
+                        ++p;
+                        continue;
+                    }
+                }
+            }
+            fused.push_back(ord[p]);
+        }
+        order[side] = fused;
+    }
+
     // 4. sweep programs
     std::vector<int> final_layout[2];
     int bits_max = 0;
@@ -364,7 +410,8 @@ HostPlan make_plan(int n, const std::vector<GateSlot> &U, const std::vector<Gate
             r.merged = f.merged;
             int nbits = op.nc + op.nk + op.nn;
             r.nent = 1 << nbits;
-            for (int e = 0; e < 16; ++e) for (int z = 0; z < 4; ++z) r.src[e][z] = -1;
+            for (int e = 0; e < 16; ++e)
+                for (int z = 0; z < 4; ++z) { r.src[e][z] = -1; r.sgn[e][z] = 1; }
             std::vector<int> ivars;   // var of each table-index bit
             for (int v : cons_s) ivars.push_back(v);
             for (int v : keep) ivars.push_back(v);
@@ -383,8 +430,12 @@ HostPlan make_plan(int n, const std::vector<GateSlot> &U, const std::vector<Gate
                     }
                     int ent = slot_entry(f, val);
                     if (f.kind == 2) { cre += f.dre[ent]; cim += f.dim[ent]; }
-                    else if (f.kind == 0) r.src[e][ns++] = (int8_t)ent;
-                    else r.src[e][ns++] = (int8_t)ent;   // 2x2 slots 0..3
+                    else if (f.kind == 3) {   // 2x2 slot times the diagonal's sign
+                        r.sgn[e][ns] = (int8_t)f.dre[val[2] * 2 + val[3]];
+                        r.src[e][ns++] = (int8_t)ent;
+                    } else {
+                        r.src[e][ns++] = (int8_t)ent;   // 4x4 slots 0..15, 2x2 slots 0..3
+                    }
                 }
                 r.cre[e] = cre;
                 r.cim[e] = cim;
