@@ -498,8 +498,8 @@ def main():
 
     n_skipped = int(skipped.item())
     value = world * (P * args.steps - n_skipped) / (ms / 1e3)
-    # roofline of the dominant kernel class
-    cls = max(range(8), key=lambda i: ks.ms[i])
+    # roofline of the dominant contraction class (the sweep kernels carry the flop count)
+    cls = max((fp.K_SWEEP, fp.K_BRICK), key=lambda i: ks.ms[i])
     flops = 8.0 * ks.work[cls]                 # complex multiply-add = 8 real flops
     achieved = flops / (ks.ms[cls] / 1e3) / 1e12 if ks.ms[cls] > 0 else 0.0
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0

@@ -517,10 +517,10 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
     // P = 1: persistent double-buffered tile passes (brick_pass_db_kernel)
     std::vector<Cand> cands = fp32 ? std::vector<Cand>{{14, 4, 512, 0}, {14, 5, 256, 0}, {13, 4, 512, 0},
                                                        {13, 4, 256, 0}, {13, 5, 256, 0}, {13, 4, 512, 1},
-                                                       {13, 5, 256, 1}}
+                                                       {13, 5, 256, 1}, {12, 4, 256, 0}, {12, 5, 128, 0}}
                                    : std::vector<Cand>{{13, 3, 512, 0}, {13, 4, 256, 0}};
     if (((size_t)1 << N) * (fp32 ? sizeof(float2) : sizeof(double2)) <= (size_t)200 * 1024) cands.push_back({99, 0, 0, 0});
-    const int kmin = 12;   // boundaries up to 2^12: shared-memory sweep, nothing to tune
+    const int kmin = 10;   // boundaries up to 2^10: shared-memory sweep, nothing to tune
     char ckey[256];
     snprintf(ckey, sizeof ckey, "%s n=%d l=%d %s", E->gpu_name.c_str(), d.n, l, fp32 ? "fp32" : "fp64");
     int bestK = cands[0].K, bestR = cands[0].R, bestT = cands[0].TH, bestP = 0;

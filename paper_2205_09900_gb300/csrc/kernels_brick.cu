@@ -224,12 +224,30 @@ __device__ __forceinline__ double wsum(double v) {
     return v;
 }
 
+// Asynchronous global -> shared copies (cp.async): every element of a tile
+// is requested before any is waited for, so a tile load costs about one
+// memory latency instead of one per few elements.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem_src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Whole boundary in shared memory.  `gt` threads per pair: 32 (warp mode,
-// several pairs per CTA) or blockDim.x (one pair per CTA).
+// several pairs per CTA) or blockDim.x (one pair per CTA).  With `stage_maps`
+// the pair's gate maps are copied next to the boundary (cp.async) before the
+// sweep, so that every gate reads its map from shared memory.
 template <typename C>
 __global__ void __launch_bounds__(512) brick_smem_kernel(BrickDev d, const PairInfo *__restrict__ pairs, int npairs,
                                                          const C *__restrict__ maps, C *__restrict__ lscratch,
-                                                         int gt, int both, double err_scale,
+                                                         int gt, int both, int stage_maps, double err_scale,
                                                          double *__restrict__ tr, double *__restrict__ kappa,
                                                          double *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -246,9 +264,16 @@ __global__ void __launch_bounds__(512) brick_smem_kernel(BrickDev d, const PairI
         if (warp_mode) __syncwarp();
         else __syncthreads();
     };
-    C *A = sm + (size_t)grp * (both ? 2 : 1) * S;
+    const size_t mpp = (size_t)maps_per_pair(d) * 16;
+    C *A = sm + (size_t)grp * ((both ? 2 : 1) * (size_t)S + (stage_maps ? mpp : 0));
     C *Lp = both ? A + S : lscratch + (size_t)pidx * S;
-    const C *mp = maps + (size_t)pidx * maps_per_pair(d) * 16;
+    const C *mp = maps + (size_t)pidx * mpp;
+    if (stage_maps) {   // visible to the group after the first sync() below
+        C *ms = A + (both ? 2 : 1) * (size_t)S;
+        for (size_t i = tid; i < mpp; i += gt) cp_async<sizeof(C)>(&ms[i], &mp[i]);
+        cp_async_wait_all();
+        mp = ms;
+    }
     for (int side = 0; side < 2; ++side) {
         for (uint32_t w = tid; w < S; w += gt) {
             C v;
@@ -440,22 +465,6 @@ __device__ __forceinline__ void win_dispatch(int type, C (&v)[1 << R], const C *
         case 3: if constexpr (R > 4) win_apply<C, 3, R>(v, T); break;
         default: break;
     }
-}
-
-// Asynchronous global -> shared copies (cp.async): every element of a tile
-// is requested before any is waited for, so a tile load costs about one
-// memory latency instead of one per few elements.
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem_src), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 constexpr int kMaxRegPasses = 160;
@@ -747,16 +756,19 @@ cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const Bric
         const uint32_t quads = (1u << d.N) >> 2;
         int gt = quads <= 32 ? 32 : (quads >= 512 ? 512 : (int)((quads + 31) / 32 * 32));
         int gpc = gt == 32 ? 8 : 1;
-        size_t smem_cta = smem * gpc;
+        // one pair per CTA: its maps go to shared memory too, when they fit
+        const size_t map_bytes = (size_t)nm * 16 * (fp32 ? sizeof(float2) : sizeof(double2));
+        const int stage = gt > 32 && smem + map_bytes <= (size_t)200 * 1024 ? 1 : 0;
+        size_t smem_cta = (smem + (stage ? map_bytes : 0)) * gpc;
         int grid = (npairs + gpc - 1) / gpc;
         if (fp32) {
             if ((e = cudaFuncSetAttribute(brick_smem_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cta)) != cudaSuccess) return e;
             brick_smem_kernel<float2><<<grid, gt * gpc, smem_cta, st>>>(d, pairs, npairs, (const float2 *)maps,
-                                                                         (float2 *)states, gt, both, err_scale, tr, kappa, err);
+                                                                         (float2 *)states, gt, both, stage, err_scale, tr, kappa, err);
         } else {
             if ((e = cudaFuncSetAttribute(brick_smem_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cta)) != cudaSuccess) return e;
             brick_smem_kernel<double2><<<grid, gt * gpc, smem_cta, st>>>(d, pairs, npairs, (const double2 *)maps,
-                                                                          (double2 *)states, gt, both, err_scale, tr, kappa, err);
+                                                                          (double2 *)states, gt, both, stage, err_scale, tr, kappa, err);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         nl += 1;
@@ -766,11 +778,14 @@ cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const Bric
         if (fp32) brick_init_kernel<float2><<<ib, 256, 0, st>>>(d, npairs, (float2 *)states);
         else brick_init_kernel<double2><<<ib, 256, 0, st>>>(d, npairs, (double2 *)states);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const int key = dp.persist * 10000 + d.tile_bits * 100 + dp.win_bits * 10 + (dp.threads == 256 ? 1 : 0);
+        const int key = dp.persist * 10000 + d.tile_bits * 100 + dp.win_bits * 10 +
+                        (dp.threads == 256 ? 1 : (dp.threads == 128 ? 2 : 0));
         if (fp32) {
             const float2 *mp = (const float2 *)maps;
             float2 *sp = (float2 *)states;
             switch (key) {
+                case 1241: e = run_passes<float2, 12, 4, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
+                case 1252: e = run_passes<float2, 12, 5, 128>(d, hpasses, dp, npairs, mp, sp, st); break;
                 case 1440: e = run_passes<float2, 14, 4, 512>(d, hpasses, dp, npairs, mp, sp, st); break;
                 case 1451: e = run_passes<float2, 14, 5, 256>(d, hpasses, dp, npairs, mp, sp, st); break;
                 case 1340: e = run_passes<float2, 13, 4, 512>(d, hpasses, dp, npairs, mp, sp, st); break;
