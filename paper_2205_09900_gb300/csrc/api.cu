@@ -100,6 +100,11 @@ struct BrickCache {
     BrickDevPlan dp;
 };
 
+struct SpiralCache {        // one depth of the paper's HEA on the spiral sweep
+    SpiralPlan sp;
+    DBuf d_maps, d_items, d_refs, d_plan;
+};
+
 struct fp_ensemble {
     fp_ensemble_desc d;
     cudaStream_t st = nullptr;
@@ -124,6 +129,9 @@ struct fp_ensemble {
     bool timing = false;
     // brickwork fast path
     std::map<int, std::unique_ptr<BrickCache>> brick_plans;   // key 2*l + fp32
+    // spiral sweep (the paper's HEA), per depth; null: the depth is not spiral-shaped
+    std::map<int, std::unique_ptr<SpiralCache>> spiral_plans;
+    DBuf d_spiral_scratch;
     DBuf d_maps, d_states;
     std::string gpu_name;
     // CUDA graphs of the brickwork sub-batch pipeline
@@ -718,6 +726,104 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
     return FP_OK;
 }
 
+// The spiral program of depth L (built and uploaded once); null when the
+// circuit is not spiral-shaped (the generic sweep takes it then).
+SpiralCache *spiral_plan(fp_ensemble *E, int L) {
+    auto it = E->spiral_plans.find(L);
+    if (it != E->spiral_plans.end()) return it->second.get();
+    std::unique_ptr<SpiralCache> sc;
+    int n_raw = 0;
+    const std::vector<GateSlot> lay = circuit_layout(E->d, 0, 0, L, &n_raw);
+    SpiralPlan sp = make_spiral_plan(E->d.n, lay, lay, E->raw_kind);
+    if (sp.ok) {
+        sc = std::make_unique<SpiralCache>();
+        sc->sp = std::move(sp);
+        DevPlan pl;
+        std::memset(&pl, 0, sizeof pl);
+        pl.n_merged = (int)sc->sp.merges.size();
+        pl.n_raw = n_raw;
+        pl.raw_kind = E->raw_kind;
+        if (upload(sc->d_maps, sc->sp.maps, E->st) != cudaSuccess || upload(sc->d_items, sc->sp.merges, E->st) != cudaSuccess ||
+            upload(sc->d_refs, sc->sp.refs, E->st) != cudaSuccess ||
+            upload(sc->d_plan, std::vector<DevPlan>{pl}, E->st) != cudaSuccess)
+            sc.reset();
+    }
+    SpiralCache *out = sc.get();
+    E->spiral_plans.emplace(L, std::move(sc));
+    return out;
+}
+
+// Spiral sweep for pairs of one depth L (FP_HEA_PAULI with CNOT walls):
+// sampler, merged 1-qubit operators, maps, one CTA per pair; sub-batches
+// under the workspace budget.
+fp_status run_spiral(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx, int L, SpiralCache *sc, int prec,
+                     double *tr, double *kappa, double *err, float *gpu_ms) {
+    const fp_ensemble_desc &d = E->d;
+    const SpiralPlan &sp = sc->sp;
+    const bool fp32 = prec != FP_PREC_FP64;
+    const size_t celem = fp32 ? sizeof(float2) : sizeof(double2);
+    const int n_raw = 1 + d.n + L * d.n;
+    const int n_merged = (int)sp.merges.size(), nmaps = (int)sp.maps.size();
+    const size_t scr = spiral_scratch_elems(sp.bits, fp32);
+    const size_t per_pair = (size_t)2 * n_raw * 16 * sizeof(double2) + (size_t)n_merged * 16 * sizeof(double2) +
+                            (size_t)nmaps * 16 * celem + scr * celem;
+    const uint64_t cap = std::max<uint64_t>(1, std::min<uint64_t>(1 << 20, E->ws_budget / per_pair));
+    const double err_scale = FP_ERR_SAFETY * (fp32 ? 0x1.0p-24 : 0x1.0p-53) * std::sqrt((double)nmaps);
+    const double cmac_pair = 4.0 * (double)nmaps * (double)((size_t)1 << sp.bits);
+    SampleParams smp;
+    smp.seed = d.seed;
+    smp.n = d.n;
+    smp.raw_kind = E->raw_kind;
+    smp.self_pair = (d.flags & FP_FLAG_SELF_PAIR) ? 1 : 0;
+    for (uint64_t done = 0; done < idx.size();) {
+        const uint64_t nb = std::min<uint64_t>(cap, idx.size() - done);
+        std::vector<PairInfo> pinfo(nb);
+        for (uint64_t i = 0; i < nb; ++i) {
+            std::memset(&pinfo[i], 0, sizeof(PairInfo));
+            pinfo[i].pair = first + idx[done + i];
+            pinfo[i].plan = 0;
+            pinfo[i].n_raw = n_raw;
+            pinfo[i].raw_off = (int64_t)i * 2 * n_raw;
+            pinfo[i].merged_off = (int64_t)i * n_merged;
+            pinfo[i].out = (int64_t)idx[done + i];
+        }
+        CK(upload(E->d_pairs, pinfo, E->st));
+        CK(E->d_raw.reserve(nb * 2 * n_raw * 16 * sizeof(double2)));
+        CK(E->d_merged.reserve(std::max<size_t>(16, nb * n_merged * 16 * sizeof(double2))));
+        CK(E->d_maps.reserve(nb * nmaps * 16 * celem));
+        CK(E->d_spiral_scratch.reserve(std::max<size_t>(16, nb * scr * celem)));
+        CK(cudaEventRecord(E->ev0, E->st));
+        {
+            KTimer t(E, FP_K_SAMPLE);
+            CK(launch_sample(smp, E->d_pairs.as<PairInfo>(), (int)nb, n_raw, E->d_raw.as<double2>(), E->st));
+            CK(t.stop((double)nb));
+        }
+        {
+            KTimer t(E, FP_K_MERGE);
+            CK(launch_merge(E->d_pairs.as<PairInfo>(), (int)nb, n_merged, sc->d_plan.as<DevPlan>(),
+                            sc->d_items.as<MergeItem>(), sc->d_refs.as<MergeRef>(), E->d_raw.as<double2>(),
+                            E->d_merged.as<double2>(), E->st));
+            CK(t.stop((double)nb));
+        }
+        {
+            KTimer t(E, FP_K_SWEEP);
+            CK(launch_spiral(E->d_pairs.as<PairInfo>(), (int)nb, sc->d_maps.as<SpiralMap>(), nmaps, sp.bits,
+                             sp.first_bit, E->d_merged.as<double2>(), E->d_maps.p, E->d_spiral_scratch.p, fp32,
+                             err_scale, tr, kappa, err, E->st));
+            CK(t.stop(cmac_pair * (double)nb));
+            if (E->timing) E->kst.launches[FP_K_SWEEP] += 1;   // maps + sweep
+        }
+        CK(cudaEventRecord(E->ev1, E->st));
+        CK(cudaEventSynchronize(E->ev1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, E->ev0, E->ev1));
+        if (gpu_ms) *gpu_ms += ms;
+        E->kst.pairs += nb;
+        done += nb;
+    }
+    return FP_OK;
+}
+
 // Route pairs first + idx[i] to the brickwork or generic path.
 __global__ void mark_skipped_kernel(const uint64_t *slots, uint64_t n, double *tr, double *kappa, double *err) {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -732,10 +838,15 @@ fp_status route(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx
                 int prec, double *tr, double *kappa, double *err, float *gpu_ms) {
     const fp_ensemble_desc &d = E->d;
     const bool brick = (d.kind == FP_PARALLEL || d.kind == FP_HEA) && !(d.flags & FP_FLAG_GENERIC_ONLY);
+    const bool spiral = d.kind == FP_HEA_PAULI && !(d.flags & (FP_FLAG_GENERIC_ONLY | FP_FLAG_HEA_CZ));
     const bool skip = (d.flags & FP_FLAG_SKIP_INFEASIBLE) != 0;
-    std::map<int, std::vector<uint64_t>> by_depth;
+    std::map<int, std::vector<uint64_t>> by_depth, spiral_depth;
     std::vector<uint64_t> generic;
     for (uint64_t i : idx) {
+        if (spiral && depth[i] >= 2 && spiral_plan(E, depth[i])) {
+            spiral_depth[depth[i]].push_back(i);
+            continue;
+        }
         if (brick && depth[i] >= 2) {
             if (skip && 2 * (depth[i] - 1) > FP_MAX_STATE_BITS) {   // boundary of 2(l-1) segment bits
                 E->skipped.push_back(i);
@@ -749,6 +860,11 @@ fp_status route(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx
     // deepest first: the largest working sets get the memory while it is free
     for (auto it = by_depth.rbegin(); it != by_depth.rend(); ++it) {
         fp_status s = run_brick(E, first, it->second, it->first, prec, tr, kappa, err, gpu_ms);
+        if (s != FP_OK) return s;
+    }
+    for (auto it = spiral_depth.rbegin(); it != spiral_depth.rend(); ++it) {
+        fp_status s = run_spiral(E, first, it->second, it->first, E->spiral_plans[it->first].get(), prec, tr, kappa,
+                                 err, gpu_ms);
         if (s != FP_OK) return s;
     }
     return run_generic(E, first, generic, depth, prec, tr, kappa, err, gpu_ms);

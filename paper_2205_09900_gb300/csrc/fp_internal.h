@@ -97,6 +97,24 @@ struct DevRecipe {
     double cim[16];
 };
 
+// One 4x4 map of the spiral sweep (planner.cpp: make_spiral_plan).
+enum SpiralType : uint8_t {
+    SP_DIAG_BA = 0,   // delta(o, i) G[i_b][i_a]
+    SP_START = 1,     // delta(o_a, o_b) H[o_b][i_b]                    (a = aux: copy, old aux summed)
+    SP_MID = 2,       // F[o_a][i_a] G[o_b][o_a] H[o_b][i_b]
+    SP_MID_AUX = 3,   // delta(o_b, i_b) F[o_a][i_a] G[o_b][o_a]
+    SP_RL = 4,        // delta(o_a, i_a) G[o_b][i_a] H[o_b][i_b]
+    SP_MID_RR = 5,    // F[o_a][i_a] G[o_b][o_a] delta(i_b, 0)
+    SP_RR = 6,        // delta(o_a, i_a) G[o_b][i_a] delta(i_b, 0)
+    SP_LL = 7,        // delta(o_a, 0) G[o_b][i_a] H[o_b][i_b]
+    SP_LL_AUX = 8     // delta(o_a, 0) delta(o_b, i_b) G[i_b][i_a]
+};
+struct SpiralMap {
+    uint8_t a, b;     // state bits of the map's low and high index bit
+    uint8_t type;     // SpiralType
+    uint8_t pad;
+    int32_t f, g;     // merged 1-qubit items the recipe uses (-1: none)
+};
 // One pair of a batch.
 struct PairInfo {
     uint64_t pair;        // global pair index (Philox counter word)

@@ -57,6 +57,13 @@ cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const Bric
                          bool fp32, double err_scale, double *tr, double *kappa, double *err, cudaStream_t st,
                          int *launches);
 size_t brick_smem_bytes(const BrickDev &d, bool fp32, bool *both);
+// Spiral sweep (the paper's HEA): maps from merged 1-qubit operators, then one
+// CTA per pair applies them to a 2^bits state (shared memory when it fits,
+// else `scratch`, spiral_scratch_elems(bits) elements per pair).
+cudaError_t launch_spiral(const PairInfo *pairs, int npairs, const SpiralMap *sm, int nmaps, int bits, int first_bit,
+                          const double2 *merged, void *maps, void *scratch, bool fp32, double err_scale, double *tr,
+                          double *kappa, double *err, cudaStream_t st);
+size_t spiral_scratch_elems(int bits, bool fp32);
 // Set the thread-local message returned by fp_last_error().
 void set_last_error(const char *msg);
 // Internal access for the control-variate driver (cv.cu).

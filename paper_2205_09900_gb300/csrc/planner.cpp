@@ -24,6 +24,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 
@@ -186,7 +188,195 @@ bool sign_diagonal(const Factor &f) {   // a constant diagonal with entries +-1 
     return true;
 }
 
+// cyclic sequence of U^dagger V (V's gates first to last, then U's last to
+// first, conjugate-transposed), merged
+std::vector<SeqEl> merged_cycle(const std::vector<GateSlot> &U, const std::vector<GateSlot> &V, int raw_kind) {
+    const int dim = raw_kind == RAW_ROT2 ? 2 : 4;
+    std::vector<SeqEl> seq;
+    auto push = [&](const GateSlot &g, int which, int dagger) {
+        SeqEl e;
+        e.kind = g.kind == 3 ? 1 : g.kind;
+        e.invol = g.kind == 3;
+        e.q = g.q;
+        for (int k = 0; k < 4; ++k) { e.dre[k] = 1; e.dim[k] = 0; }
+        if (g.kind == 2) {
+            e.dre[3] = -1.0;   // CZ = diag(1, 1, 1, -1), its own conjugate
+        } else {
+            e.chain.push_back({which, g.raw, dagger, e.kind == 1 ? 2 : dim});
+        }
+        seq.push_back(e);
+    };
+    for (const auto &g : V) push(g, 1, 0);
+    for (auto it = U.rbegin(); it != U.rend(); ++it) push(*it, 0, 1);
+    merge_sequence(seq);
+    return seq;
+}
+
 }  // namespace
+
+// Spiral program.  Every wire of the merged cycle is cut by its 1-qubit
+// operators into segments; a CZ on bond (q, q+1) couples one segment of q and
+// one of q+1 with (-1)^{y y'} = H[y][y'] (H = [[1, 1], [1, -1]]).  When every
+// segment of a wire holds exactly one CZ, qubit q is a ring of segments tapped
+// on the left (L) or the right (R) bond, consecutive segments joined by the
+// 1-qubit operators X[out][in].  The state holds one variable per CZ of a bond
+// (the neighbouring qubit's segment, before the CZ coupling H) plus an
+// auxiliary bit; qubit q turns it into the variables of its R segments:
+// START couples the ring's first L segment S_0 (H), sums the old auxiliary
+// bit and copies S_0 into it; then the ring is walked S_0, S_1, ... back to
+// S_0 (reached through the auxiliary copy), one 4x4 map per step:
+//   L -> R   the R segment takes the L segment's bit (fused with the next step);
+//   R -> L   the L bit is coupled (H) and multiplied by X (the R bit stays);
+//   L -> L   the old L is summed out and its bit zeroed (freed);
+//   R -> R   the new R takes a freed bit.
+// The walk starts at an L segment from which every R -> R step finds a freed
+// bit (L -> L and R -> R steps are equally many on a ring with as many L as R
+// segments).  The first qubit (R taps only) starts from delta(aux, S_0's bit)
+// and multiplies X[S_{i+1}][S_i] on its ring; the last (L taps only) couples
+// and multiplies without freeing; the trace is the sum of the final state.
+// Map entries, with o/i the output/input values of bits a (low) and b (high),
+// are listed at SpiralType.
+SpiralPlan make_spiral_plan(int n, const std::vector<GateSlot> &U, const std::vector<GateSlot> &V, int raw_kind) {
+    SpiralPlan P;
+    std::vector<SeqEl> seq = merged_cycle(U, V, raw_kind);
+    std::vector<int> item(seq.size(), -1), tap(seq.size(), -1), ntap(n, 0);
+    for (size_t i = 0; i < seq.size(); ++i) {
+        const SeqEl &e = seq[i];
+        if (e.kind == 0) { P.why = "two-qubit gates"; return P; }
+        if (e.kind == 2) {
+            for (int k = 0; k < 4; ++k)
+                if (e.dim[k] != 0.0 || e.dre[k] != (k == 3 ? -1.0 : 1.0)) { P.why = "diagonal other than CZ"; return P; }
+            tap[i] = ntap[e.q]++;
+            continue;
+        }
+        item[i] = (int)P.merges.size();
+        MergeItem mi;
+        mi.first = (int)P.refs.size();
+        mi.count = (int)e.chain.size();
+        P.refs.insert(P.refs.end(), e.chain.begin(), e.chain.end());
+        P.merges.push_back(mi);
+    }
+    const int M = n >= 2 ? ntap[0] : 0;
+    if (n < 3 || M < 1) { P.why = "no CZ left"; return P; }
+    for (int b = 0; b < n - 1; ++b)
+        if (ntap[b] != M) { P.why = "bonds with different CZ counts"; return P; }
+    if (M + 1 > FP_MAX_STATE_BITS) { P.why = "boundary too large"; return P; }
+    P.bits = M + 1;
+    const int aux = M;
+    std::vector<int> pos(M);   // state bit of each CZ of the current bond
+    auto map = [&](int a, int b, int type, int f, int g) {
+        P.maps.push_back({(uint8_t)a, (uint8_t)b, (uint8_t)type, 0, f, g});
+    };
+    for (int q = 0; q < n; ++q) {
+        // the wire of q in cyclic order: 1-qubit items and taps (side 0 left, 1 right)
+        struct Ev { int op, side, id; };
+        std::vector<Ev> ev;
+        for (size_t i = 0; i < seq.size(); ++i) {
+            const SeqEl &e = seq[i];
+            if (e.kind == 1 && e.q == q) ev.push_back({item[i], -1, -1});
+            else if (e.kind == 2 && e.q == q - 1) ev.push_back({-1, 0, tap[i]});
+            else if (e.kind == 2 && e.q == q) ev.push_back({-1, 1, tap[i]});
+        }
+        int first_op = -1;
+        for (size_t i = 0; i < ev.size(); ++i) if (ev[i].op >= 0) { first_op = (int)i; break; }
+        if (first_op < 0) { P.why = "a wire without 1-qubit operators"; return P; }
+        struct Seg { int side, id, op_out; };   // op_out: the operator leaving the segment
+        std::vector<Seg> segs;
+        const int E = (int)ev.size();
+        for (int k = 0; k < E; ++k) {
+            if (ev[(first_op + k) % E].op < 0) continue;
+            int side = -1, id = -1, cnt = 0, j = 1;
+            for (; j < E; ++j) {
+                const Ev &y = ev[(first_op + k + j) % E];
+                if (y.op >= 0) break;
+                side = y.side; id = y.id; ++cnt;
+            }
+            if (cnt != 1) { P.why = "a segment without exactly one CZ"; return P; }
+            segs.push_back({side, id, ev[(first_op + k + j) % E].op});
+        }
+        const int S = (int)segs.size();
+        const bool first = q == 0, last = q == n - 1;
+        if ((first || last) ? S != M : S != 2 * M) { P.why = "segment count"; return P; }
+        if (first) {
+            for (int i = 0; i < M; ++i) {
+                if (segs[i].side != 1) { P.why = "left taps on the first qubit"; return P; }
+                pos[segs[i].id] = i;
+            }
+            P.first_bit = pos[segs[0].id];
+            for (int i = 0; i < M; ++i)
+                map(pos[segs[i].id], i + 1 < M ? pos[segs[i + 1].id] : aux, SP_DIAG_BA, -1, segs[i].op_out);
+            continue;
+        }
+        if (last) {
+            for (int i = 0; i < M; ++i)
+                if (segs[i].side != 0) { P.why = "right taps on the last qubit"; return P; }
+            map(aux, pos[segs[0].id], SP_START, -1, -1);
+            for (int i = 0; i + 1 < M; ++i) map(pos[segs[i].id], pos[segs[i + 1].id], SP_RL, -1, segs[i].op_out);
+            map(pos[segs[M - 1].id], aux, SP_DIAG_BA, -1, segs[M - 1].op_out);
+            continue;
+        }
+        // start: an L segment from which freed bits always precede their use
+        int s0 = -1;
+        for (int c = 0; c < S && s0 < 0; ++c) {
+            if (segs[c].side != 0) continue;
+            int bal = 0;
+            bool ok = true;
+            for (int k = 0; k < S && ok; ++k) {
+                const int a = segs[(c + k) % S].side, b = segs[(c + k + 1) % S].side;
+                if (a == 0 && b == 0) ++bal;
+                if (a == 1 && b == 1 && --bal < 0) ok = false;
+            }
+            if (ok) s0 = c;
+        }
+        if (s0 < 0) { P.why = "no valid start on the ring"; return P; }
+        std::vector<int> npos(M, -1), freed;
+        map(aux, pos[segs[s0].id], SP_START, -1, -1);
+        int cb = pos[segs[s0].id], cside = 0, pendF = -1;   // carry bit, its side, deferred L -> R operator
+        for (int k = 0; k < S; ++k) {
+            const Seg &cur = segs[(s0 + k) % S];
+            const bool close = k == S - 1;                  // the step back to S_0 (through aux)
+            const Seg &nxt = segs[(s0 + k + 1) % S];
+            const int op = cur.op_out;
+            const int nb = close ? aux : pos[nxt.id];
+            if (cside == 0 && nxt.side == 1) {              // L -> R: deferred
+                if (close) { P.why = "ring closes on R"; return P; }
+                pendF = op;
+                cside = 1;
+                npos[nxt.id] = cb;
+                continue;
+            }
+            if (cside == 0 && nxt.side == 0) {              // L -> L: free the carry's bit
+                map(cb, nb, close ? SP_LL_AUX : SP_LL, -1, op);
+                freed.push_back(cb);
+                cb = nb;
+                continue;
+            }
+            if (nxt.side == 0) {                            // R -> L
+                if (pendF >= 0) map(cb, nb, close ? SP_MID_AUX : SP_MID, pendF, op);
+                else if (close) map(cb, nb, SP_DIAG_BA, -1, op);
+                else map(cb, nb, SP_RL, -1, op);
+                pendF = -1;
+                cside = 0;
+                cb = nb;
+                continue;
+            }
+            // R -> R: the new R segment takes a freed bit
+            if (freed.empty()) { P.why = "no freed bit"; return P; }
+            const int fb = freed.back();
+            freed.pop_back();
+            if (pendF >= 0) map(cb, fb, SP_MID_RR, pendF, op);
+            else map(cb, fb, SP_RR, -1, op);
+            pendF = -1;
+            npos[nxt.id] = fb;
+            cb = fb;
+        }
+        for (int u = 0; u < M; ++u)
+            if (npos[u] < 0) { P.why = "an R segment without a bit"; return P; }
+        pos = npos;
+    }
+    P.ok = true;
+    return P;
+}
 
 HostPlan make_plan(int n, const std::vector<GateSlot> &U, const std::vector<GateSlot> &V,
                    int raw_kind, int n_raw, int cut, int max_bits) {

@@ -47,6 +47,22 @@ std::vector<GateSlot> layout_local(int n, const std::vector<int> &bonds);
 // stays uncut.
 std::vector<GateSlot> layout_hea_pauli(int n, int L, bool cz);
 
+// Spiral program (the paper's HEA with CNOT walls, and any circuit of 1-qubit
+// gates and CZs whose wires alternate between taps on the left and the right
+// bond).  The state holds one variable per CZ of a bond (M bits) plus an
+// auxiliary bit M; a qubit's wire, a ring of segments each tapped by one CZ, is
+// absorbed by M+1 in-place 4x4 maps (planner.cpp explains the recipes).
+struct SpiralPlan {
+    bool ok = false;
+    int bits = 0;               // M + 1
+    int first_bit = 0;          // start state delta(aux, bit first_bit)
+    std::vector<MergeRef> refs;
+    std::vector<MergeItem> merges;
+    std::vector<SpiralMap> maps;
+    std::string why;            // why not, when !ok
+};
+SpiralPlan make_spiral_plan(int n, const std::vector<GateSlot> &U, const std::vector<GateSlot> &V, int raw_kind);
+
 // Plan the contraction of Tr(U^dagger V).  `cut`: the left sweep owns bonds
 // 0..cut-1 and the 1-qubit gates of qubits 0..cut-1, the right sweep the rest.
 HostPlan make_plan(int n, const std::vector<GateSlot> &U, const std::vector<GateSlot> &V,

@@ -121,3 +121,18 @@ def test_paper_hea_flag_checks(fp):
         fp.Ensemble(fp.HEA, 8, 2, flags=fp.FLAG_HEA_CZ)
     with pytest.raises(fp.FpError):
         fp.Ensemble(fp.HEA_PAULI, 8, 2, flags=fp.FLAG_DIAGONAL_GATES)
+
+
+@pytest.mark.parametrize("n,L_min,L_max", [(3, 2, 3), (4, 2, 4), (9, 2, 5), (50, 2, 8), (51, 3, 6)])
+def test_paper_hea_spiral_matches_generic_sweep(fp, n, L_min, L_max):
+    # the spiral sweep (default for CNOT walls) against the generic sweep on the same
+    # pairs: FP64 to 1e-10 of max(|Tr|, 1), FP32 to 1e-4 absolute
+    a = fp.Ensemble(fp.HEA_PAULI, n, L_min, L_max, seed=31 + n)
+    b = fp.Ensemble(fp.HEA_PAULI, n, L_min, L_max, seed=31 + n, flags=fp.FLAG_GENERIC_ONLY)
+    N = 40
+    ta, _, ga = a.trace_batch(0, N, fp.PREC_FP64)
+    tb, _, gb = b.trace_batch(0, N, fp.PREC_FP64)
+    assert np.array_equal(ga, gb)
+    assert rel_err(ta, tb).max() <= TOL64, (ta, tb)
+    t32, _, _ = a.trace_batch(0, N, fp.PREC_FP32_RAW)
+    assert np.abs(t32 - tb).max() <= TOL32
