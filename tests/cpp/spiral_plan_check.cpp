@@ -1,0 +1,118 @@
+// spiral_plan_check.cpp -- host check of the spiral program of the paper's
+// hardware-efficient ansatz (planner.cpp: make_spiral_plan), independent of
+// the GPU: random 2x2 unitaries for the raw gates (the CNOTs' Hadamards exact),
+// the spiral maps applied to a 2^bits state in FP64, against Tr(U^dagger V)
+// of the dense 2^n matrices built gate by gate.  Prints one line per (n, L)
+// with the absolute difference; exit status 1 if it exceeds 1e-12 max(|Tr|, 1).
+#include "planner.h"
+#include <complex>
+#include <cstdio>
+#include <cstdlib>
+#include <random>
+#include <algorithm>
+#include <cmath>
+using namespace fpk;
+typedef std::complex<double> cd;
+struct M2 { cd m[4]; };
+static M2 mul(const M2 &A, const M2 &B) { M2 C; for (int r = 0; r < 2; ++r) for (int c = 0; c < 2; ++c) C.m[2*r+c] = A.m[2*r]*B.m[c] + A.m[2*r+1]*B.m[2+c]; return C; }
+int main(int argc, char **argv) {
+    int n = atoi(argv[1]), L = atoi(argv[2]);
+    std::mt19937_64 rng(n * 100 + L);  // random unitaries for every raw 1-qubit gate (raw 0 is the Hadamard)
+    std::normal_distribution<double> N01;
+    auto U = layout_hea_pauli(n, L, false), V = U;
+    int n_raw = 1 + n + L * n;
+    SpiralPlan P = make_spiral_plan(n, U, V, RAW_PAULI);
+    if (!P.ok) { printf("n=%d L=%d not spiral: %s\n", n, L, P.why.c_str()); return 2; }
+    std::vector<M2> raw[2];
+    for (int w = 0; w < 2; ++w) {
+        raw[w].resize(n_raw);
+        double h = 1 / std::sqrt(2.0);
+        raw[w][0].m[0] = h; raw[w][0].m[1] = h; raw[w][0].m[2] = h; raw[w][0].m[3] = -h;
+        for (int g = 1; g < n_raw; ++g) {   // random unitary via QR-free: exp of random hermitian is overkill; use random SU(2) params
+            double a = N01(rng), b = N01(rng), c = N01(rng), d = N01(rng);
+            double nn = std::sqrt(a*a+b*b+c*c+d*d); a/=nn; b/=nn; c/=nn; d/=nn;
+            cd ph = std::polar(1.0, N01(rng));
+            raw[w][g].m[0] = cd(a, b) * ph; raw[w][g].m[1] = cd(-c, d) * ph; raw[w][g].m[2] = cd(c, d) * ph; raw[w][g].m[3] = cd(a, -b) * ph;
+        }
+    }
+    std::vector<M2> merged(P.merges.size());
+    for (size_t i = 0; i < P.merges.size(); ++i) {
+        M2 Mx; Mx.m[0] = 1; Mx.m[1] = 0; Mx.m[2] = 0; Mx.m[3] = 1;
+        for (int c = 0; c < P.merges[i].count; ++c) {
+            const MergeRef &r = P.refs[P.merges[i].first + c];
+            M2 G = raw[r.which][r.gate];
+            if (r.dagger) { M2 D; D.m[0] = std::conj(G.m[0]); D.m[1] = std::conj(G.m[2]); D.m[2] = std::conj(G.m[1]); D.m[3] = std::conj(G.m[3]); G = D; }
+            Mx = mul(G, Mx);
+        }
+        merged[i] = Mx;
+    }
+    const int B = P.bits, aux = B - 1;
+    std::vector<cd> st((size_t)1 << B, 0.0);
+    for (size_t x = 0; x < st.size(); ++x) st[x] = (((x >> aux) & 1) == ((x >> P.first_bit) & 1)) ? 1.0 : 0.0;
+    const double Hm[2][2] = {{1, 1}, {1, -1}};
+    for (const SpiralMap &mp : P.maps) {
+        cd T[4][4];
+        const M2 *F = mp.f >= 0 ? &merged[mp.f] : nullptr, *G = mp.g >= 0 ? &merged[mp.g] : nullptr;
+        for (int o = 0; o < 4; ++o) for (int f = 0; f < 4; ++f) {
+            int oa = o & 1, ob = o >> 1, ia = f & 1, ib = f >> 1;
+            cd v = 0;
+            auto Fm = [&](int r, int c) { return F->m[2 * r + c]; };
+            auto Gm = [&](int r, int c) { return G->m[2 * r + c]; };
+            switch (mp.type) {
+                case SP_DIAG_BA: v = (o == f) ? Gm(ib, ia) : 0.0; break;
+                case SP_START: v = (oa == ob) ? Hm[ob][ib] : 0.0; break;
+                case SP_MID: v = Fm(oa, ia) * Gm(ob, oa) * Hm[ob][ib]; break;
+                case SP_MID_AUX: v = (ob == ib) ? Fm(oa, ia) * Gm(ob, oa) : 0.0; break;
+                case SP_RL: v = (oa == ia) ? Gm(ob, ia) * Hm[ob][ib] : 0.0; break;
+                case SP_MID_RR: v = (ib == 0) ? Fm(oa, ia) * Gm(ob, oa) : 0.0; break;
+                case SP_RR: v = (oa == ia && ib == 0) ? Gm(ob, ia) : 0.0; break;
+                case SP_LL: v = (oa == 0) ? Gm(ob, ia) * Hm[ob][ib] : 0.0; break;
+                case SP_LL_AUX: v = (oa == 0 && ob == ib) ? Gm(ib, ia) : 0.0; break;
+            }
+            T[o][f] = v;
+        }
+        std::vector<cd> nx(st.size());
+        for (size_t x = 0; x < st.size(); ++x) {
+            int oa = (x >> mp.a) & 1, ob = (x >> mp.b) & 1, o = oa + 2 * ob;
+            size_t base = x & ~(((size_t)1 << mp.a) | ((size_t)1 << mp.b));
+            cd acc = 0;
+            for (int f = 0; f < 4; ++f) acc += T[o][f] * st[base | ((size_t)(f & 1) << mp.a) | ((size_t)(f >> 1) << mp.b)];
+            nx[x] = acc;
+        }
+        st.swap(nx);
+    }
+    cd tr_sp = 0; for (auto v : st) tr_sp += v;
+    // dense reference
+    size_t D = (size_t)1 << n;
+    auto build = [&](int w) {
+        std::vector<cd> Mt(D * D, 0.0);
+        for (size_t i = 0; i < D; ++i) Mt[i * D + i] = 1;
+        for (const GateSlot &g : (w ? V : U)) {
+            std::vector<cd> Nt(D * D, 0.0);
+            if (g.kind == 2) {
+                for (size_t i = 0; i < D; ++i) {
+                    int a = (i >> (n - 1 - g.q)) & 1, b = (i >> (n - 2 - g.q)) & 1;
+                    double sgn = (a & b) ? -1 : 1;
+                    for (size_t j = 0; j < D; ++j) Nt[i * D + j] = sgn * Mt[i * D + j];
+                }
+            } else {
+                const M2 &G = raw[w][g.kind == 3 ? 0 : g.raw];
+                int sh = n - 1 - g.q;
+                for (size_t i = 0; i < D; ++i) {
+                    int bi = (i >> sh) & 1;
+                    for (int bo = 0; bo < 2; ++bo) {
+                        size_t i2 = (i & ~((size_t)1 << sh)) | ((size_t)bo << sh);
+                        for (size_t j = 0; j < D; ++j) Nt[i2 * D + j] += G.m[2 * bo + bi] * Mt[i * D + j];
+                    }
+                }
+            }
+            Mt.swap(Nt);
+        }
+        return Mt;
+    };
+    auto Ud = build(0), Vd = build(1);
+    cd tr = 0; for (size_t k = 0; k < D * D; ++k) tr += std::conj(Ud[k]) * Vd[k];
+    printf("n=%d L=%d bits=%d maps=%zu: spiral %.12f%+.12fi dense %.12f%+.12fi  |diff| %.2e\n", n, L, B, P.maps.size(),
+           tr_sp.real(), tr_sp.imag(), tr.real(), tr.imag(), std::abs(tr_sp - tr));
+    return std::abs(tr_sp - tr) <= 1e-12 * std::max(1.0, std::abs(tr)) ? 0 : 1;
+}
