@@ -103,6 +103,9 @@ struct BrickCache {
 struct SpiralCache {        // one depth of the paper's HEA on the spiral sweep
     SpiralPlan sp;
     DBuf d_maps, d_items, d_refs, d_plan;
+    SpiralConfig cfg[2];       // FP64, FP32
+    DBuf d_wins[2], d_ij[2];   // register windows of cfg[p]
+    int nwins[2] = {0, 0}, h[2] = {-1, -1};
 };
 
 struct fp_ensemble {
@@ -747,6 +750,16 @@ SpiralCache *spiral_plan(fp_ensemble *E, int L) {
             upload(sc->d_refs, sc->sp.refs, E->st) != cudaSuccess ||
             upload(sc->d_plan, std::vector<DevPlan>{pl}, E->st) != cudaSuccess)
             sc.reset();
+        for (int p = 0; sc && p < 2; ++p) {
+            sc->cfg[p] = spiral_config(sc->sp.bits, p == 1);
+            if (sc->cfg[p].R == 0) continue;
+            std::vector<SpiralWin> wins;
+            std::vector<uint8_t> ij;
+            spiral_windows(sc->sp, sc->cfg[p].R, sc->cfg[p].split, wins, ij, &sc->h[p]);
+            sc->nwins[p] = (int)wins.size();
+            if (upload(sc->d_wins[p], wins, E->st) != cudaSuccess || upload(sc->d_ij[p], ij, E->st) != cudaSuccess)
+                sc.reset();
+        }
     }
     SpiralCache *out = sc.get();
     E->spiral_plans.emplace(L, std::move(sc));
@@ -764,9 +777,11 @@ fp_status run_spiral(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
     const size_t celem = fp32 ? sizeof(float2) : sizeof(double2);
     const int n_raw = 1 + d.n + L * d.n;
     const int n_merged = (int)sp.merges.size(), nmaps = (int)sp.maps.size();
-    const size_t scr = spiral_scratch_elems(sp.bits, fp32);
+    const int pi32 = fp32 ? 1 : 0;
+    const SpiralConfig &cfg = sc->cfg[pi32];
+    const size_t scr = cfg.scratch_elems, mw = spiral_map_elems(fp32);
     const size_t per_pair = (size_t)2 * n_raw * 16 * sizeof(double2) + (size_t)n_merged * 16 * sizeof(double2) +
-                            (size_t)nmaps * 16 * celem + scr * celem;
+                            (size_t)nmaps * mw * celem + scr * celem;
     const uint64_t cap = std::max<uint64_t>(1, std::min<uint64_t>(1 << 20, E->ws_budget / per_pair));
     const double err_scale = FP_ERR_SAFETY * (fp32 ? 0x1.0p-24 : 0x1.0p-53) * std::sqrt((double)nmaps);
     const double cmac_pair = 4.0 * (double)nmaps * (double)((size_t)1 << sp.bits);
@@ -790,7 +805,7 @@ fp_status run_spiral(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
         CK(upload(E->d_pairs, pinfo, E->st));
         CK(E->d_raw.reserve(nb * 2 * n_raw * 16 * sizeof(double2)));
         CK(E->d_merged.reserve(std::max<size_t>(16, nb * n_merged * 16 * sizeof(double2))));
-        CK(E->d_maps.reserve(nb * nmaps * 16 * celem));
+        CK(E->d_maps.reserve(nb * nmaps * mw * celem));
         CK(E->d_spiral_scratch.reserve(std::max<size_t>(16, nb * scr * celem)));
         CK(cudaEventRecord(E->ev0, E->st));
         {
@@ -807,8 +822,11 @@ fp_status run_spiral(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
         }
         {
             KTimer t(E, FP_K_SWEEP);
+            const bool use_win = cfg.R > 0;
             CK(launch_spiral(E->d_pairs.as<PairInfo>(), (int)nb, sc->d_maps.as<SpiralMap>(), nmaps, sp.bits,
-                             sp.first_bit, E->d_merged.as<double2>(), E->d_maps.p, E->d_spiral_scratch.p, fp32,
+                             sp.first_bit, cfg, use_win ? sc->d_wins[pi32].as<SpiralWin>() : nullptr,
+                             use_win ? sc->nwins[pi32] : 0, use_win ? sc->d_ij[pi32].as<uint8_t>() : nullptr,
+                             sc->h[pi32], E->d_merged.as<double2>(), E->d_maps.p, E->d_spiral_scratch.p, fp32,
                              err_scale, tr, kappa, err, E->st));
             CK(t.stop(cmac_pair * (double)nb));
             if (E->timing) E->kst.launches[FP_K_SWEEP] += 1;   // maps + sweep

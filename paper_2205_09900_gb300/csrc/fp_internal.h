@@ -115,6 +115,31 @@ struct SpiralMap {
     uint8_t pad;
     int32_t f, g;     // merged 1-qubit items the recipe uses (-1: none)
 };
+// A register window of the spiral sweep: maps [first, first + n_maps) act only
+// on the window's nb state bits (ascending); map k acts on window bits
+// (ij[k] & 15, ij[k] >> 4) as its (low, high) index bits.
+// The state is split over `split` = 0 or 1 cluster bits: with split = 1 state
+// bit h lives in the CTA rank of a 2-CTA cluster and the other bits form the
+// local index (bits above h move down by one).  Local amplitudes are stored
+// at swizzled addresses s(y) = y ^ fold4(y >> 4) (fold4: XOR of the 4-bit
+// chunks), so that 16 lanes walking the lane bits hit 16 distinct 8-byte slots.
+// Threads build a group base from their group index t: the low 4 bits of t go
+// to the local positions lane[], the rest to the free local positions (zeros
+// inserted at ins[0..n_ins), ascending).
+constexpr int kSpiralMaxWin = 5;
+constexpr int kSpiralWinMaxMaps = 16;   // maps per window (staged in shared memory)
+struct SpiralWin {
+    uint8_t bits[kSpiralMaxWin];   // state bits of the window, ascending
+    uint8_t nb;                    // window bits (the register block is 2^nb)
+    uint8_t n_maps;
+    int8_t hk;                     // index in bits[] of the cluster bit h; -1: none
+    uint8_t n_ins;
+    uint8_t ins[kSpiralMaxWin + 4];
+    uint8_t lane[4];
+    uint16_t off[kSpiralMaxWin];   // s(local unit vector) of each window bit (0 for h)
+    int32_t first;
+};
+
 // One pair of a batch.
 struct PairInfo {
     uint64_t pair;        // global pair index (Philox counter word)

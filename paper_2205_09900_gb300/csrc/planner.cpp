@@ -24,8 +24,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <cstdio>
-#include <cstdlib>
 #include <cstring>
 #include <map>
 
@@ -376,6 +374,82 @@ SpiralPlan make_spiral_plan(int n, const std::vector<GateSlot> &U, const std::ve
     }
     P.ok = true;
     return P;
+}
+
+static uint32_t spiral_swizzle(uint32_t y) {   // s(y) of the spiral window kernel
+    const uint32_t q = y >> 4;
+    return y ^ ((q ^ (q >> 4) ^ (q >> 8) ^ (q >> 12)) & 15u);
+}
+
+void spiral_windows(const SpiralPlan &P, int R, int split, std::vector<SpiralWin> &wins, std::vector<uint8_t> &ij,
+                    int *h_out) {
+    wins.clear();
+    ij.assign(P.maps.size(), 0);
+    R = std::min(std::max(R, 2), std::min(kSpiralMaxWin, P.bits));
+    std::vector<uint32_t> sets;
+    size_t k = 0;
+    while (k < P.maps.size()) {
+        uint32_t set = 0;
+        size_t e = k;
+        for (; e < P.maps.size(); ++e) {
+            const uint32_t s2 = set | (1u << P.maps[e].a) | (1u << P.maps[e].b);
+            if (__builtin_popcount(s2) > R || e - k >= (size_t)kSpiralWinMaxMaps) break;
+            set = s2;
+        }
+        // pad the window to R bits with the lowest other state bits (every window moves 2^R amplitudes)
+        for (int b = 0; b < P.bits && __builtin_popcount(set) < R; ++b) set |= 1u << b;
+        SpiralWin w;
+        std::memset(&w, 0, sizeof w);
+        int loc[32], nb = 0;
+        for (int b = 0; b < P.bits; ++b)
+            if (set & (1u << b)) { loc[b] = nb; w.bits[nb++] = (uint8_t)b; }
+        w.nb = (uint8_t)nb;
+        w.n_maps = (uint8_t)(e - k);
+        w.first = (int32_t)k;
+        for (size_t m = k; m < e; ++m) ij[m] = (uint8_t)(loc[P.maps[m].a] | (loc[P.maps[m].b] << 4));
+        wins.push_back(w);
+        sets.push_back(set);
+        k = e;
+    }
+    // cluster bit: the state bit in the fewest windows
+    int h = -1;
+    if (split) {
+        int best = 1 << 30;
+        for (int b = 0; b < P.bits; ++b) {
+            int c = 0;
+            for (uint32_t s : sets) c += (s >> b) & 1;
+            if (c < best) { best = c; h = b; }
+        }
+    }
+    if (h_out) *h_out = h;
+    const int LB = P.bits - (split ? 1 : 0);   // local index bits
+    auto local = [&](int b) { return h >= 0 && b > h ? b - 1 : b; };
+    for (size_t i = 0; i < wins.size(); ++i) {
+        SpiralWin &w = wins[i];
+        w.hk = -1;
+        uint32_t used = 0;   // local positions taken by the window
+        for (int q = 0; q < w.nb; ++q) {
+            if (w.bits[q] == h) { w.hk = (int8_t)q; w.off[q] = 0; continue; }
+            const int p = local(w.bits[q]);
+            used |= 1u << p;
+            w.off[q] = (uint16_t)spiral_swizzle(1u << p);
+        }
+        // lane q: the lowest free local position of residue q mod 4 (16 lanes then
+        // touch 16 distinct slots of s); else the lowest free position left
+        uint32_t lanes = 0;
+        for (int q = 0; q < 4; ++q) {
+            int pick = -1;
+            for (int p = 0; p < LB && pick < 0; ++p)
+                if (!((used | lanes) >> p & 1) && p % 4 == q) pick = p;
+            for (int p = 0; p < LB && pick < 0; ++p)
+                if (!((used | lanes) >> p & 1)) pick = p;
+            w.lane[q] = (uint8_t)std::max(pick, 0);
+            if (pick >= 0) lanes |= 1u << pick;
+        }
+        w.n_ins = 0;
+        for (int p = 0; p < LB; ++p)
+            if ((used | lanes) >> p & 1) w.ins[w.n_ins++] = (uint8_t)p;
+    }
 }
 
 HostPlan make_plan(int n, const std::vector<GateSlot> &U, const std::vector<GateSlot> &V,

@@ -62,6 +62,12 @@ struct SpiralPlan {
     std::string why;            // why not, when !ok
 };
 SpiralPlan make_spiral_plan(int n, const std::vector<GateSlot> &U, const std::vector<GateSlot> &V, int raw_kind);
+// Consecutive maps grouped into windows of R state bits (R <= kSpiralMaxWin,
+// padded with the lowest other bits); ij[k]: map k's window-local (low, high)
+// bits.  split = 1 also picks the cluster bit h (the state bit fewest windows
+// touch; returned in *h) and the local addressing of every window.
+void spiral_windows(const SpiralPlan &P, int R, int split, std::vector<SpiralWin> &wins, std::vector<uint8_t> &ij,
+                    int *h);
 
 // Plan the contraction of Tr(U^dagger V).  `cut`: the left sweep owns bonds
 // 0..cut-1 and the 1-qubit gates of qubits 0..cut-1, the right sweep the rest.

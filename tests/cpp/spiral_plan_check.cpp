@@ -2,14 +2,18 @@
 // hardware-efficient ansatz (planner.cpp: make_spiral_plan), independent of
 // the GPU: random 2x2 unitaries for the raw gates (the CNOTs' Hadamards exact),
 // the spiral maps applied to a 2^bits state in FP64, against Tr(U^dagger V)
-// of the dense 2^n matrices built gate by gate.  Prints one line per (n, L)
-// with the absolute difference; exit status 1 if it exceeds 1e-12 max(|Tr|, 1).
+// of the dense 2^n matrices built gate by gate (skipped with a third argument
+// "nodense"), and the register-window program (addressing of the window
+// kernel emulated on the host) against the map-by-map sweep.  Prints the
+// differences; exit status 1 if one exceeds 1e-12 max(|Tr|, 1).
 #include "planner.h"
 #include <complex>
 #include <cstdio>
 #include <cstdlib>
 #include <random>
+#include <string>
 #include <algorithm>
+#include <array>
 #include <cmath>
 using namespace fpk;
 typedef std::complex<double> cd;
@@ -50,6 +54,7 @@ int main(int argc, char **argv) {
     std::vector<cd> st((size_t)1 << B, 0.0);
     for (size_t x = 0; x < st.size(); ++x) st[x] = (((x >> aux) & 1) == ((x >> P.first_bit) & 1)) ? 1.0 : 0.0;
     const double Hm[2][2] = {{1, 1}, {1, -1}};
+    std::vector<std::array<cd, 16>> Tall;
     for (const SpiralMap &mp : P.maps) {
         cd T[4][4];
         const M2 *F = mp.f >= 0 ? &merged[mp.f] : nullptr, *G = mp.g >= 0 ? &merged[mp.g] : nullptr;
@@ -71,6 +76,9 @@ int main(int argc, char **argv) {
             }
             T[o][f] = v;
         }
+        std::array<cd, 16> Tf;
+        for (int e = 0; e < 16; ++e) Tf[e] = T[e / 4][e % 4];
+        Tall.push_back(Tf);
         std::vector<cd> nx(st.size());
         for (size_t x = 0; x < st.size(); ++x) {
             int oa = (x >> mp.a) & 1, ob = (x >> mp.b) & 1, o = oa + 2 * ob;
@@ -82,6 +90,93 @@ int main(int argc, char **argv) {
         st.swap(nx);
     }
     cd tr_sp = 0; for (auto v : st) tr_sp += v;
+    // register windows (spiral_windows): consecutive runs covering every map once,
+    // in order, each of exactly min(R, bits) ascending bits holding its maps' bits;
+    // then the window kernel's addressing emulated in FP64 (swizzled slots, lane
+    // and insert positions, the 2-CTA split): every slot visited once per window,
+    // every index in bounds, and the same trace as the map-by-map sweep
+    auto swz = [](uint32_t y) { uint32_t q = y >> 4; return y ^ ((q ^ (q >> 4) ^ (q >> 8) ^ (q >> 12)) & 15u); };
+    auto ins0 = [](uint32_t x, int p) { return (x & ((1u << p) - 1u)) | ((x >> p) << (p + 1)); };
+    for (int R = 4; R <= 5; ++R)
+        for (int split = 0; split <= 1; ++split) {
+            if (B - R - split < 4) continue;   // the kernel's precondition
+            std::vector<SpiralWin> wins;
+            std::vector<uint8_t> ij;
+            int h = -1;
+            spiral_windows(P, R, split, wins, ij, &h);
+            size_t next = 0;
+            for (const SpiralWin &w : wins) {
+                bool ok = w.first == (int)next && w.n_maps > 0 && w.nb == std::min(R, B);
+                for (int k = 1; k < w.nb; ++k) ok = ok && w.bits[k - 1] < w.bits[k];
+                for (int k = 0; k < w.nb; ++k) ok = ok && w.bits[k] < B;
+                for (int m = w.first; ok && m < w.first + w.n_maps; ++m) {
+                    const int i = ij[m] & 15, j = ij[m] >> 4;
+                    ok = i < w.nb && j < w.nb && w.bits[i] == P.maps[m].a && w.bits[j] == P.maps[m].b;
+                }
+                if (!ok) { printf("n=%d L=%d: bad %d-bit window at map %d\n", n, L, R, w.first); return 1; }
+                next += w.n_maps;
+            }
+            if (next != P.maps.size()) { printf("n=%d L=%d: %d-bit windows cover %zu of %zu maps\n", n, L, R, next, P.maps.size()); return 1; }
+            const int LBt = B - split, CLt = 1 << split;
+            const uint32_t SL = 1u << LBt, G = 1u << (B - R - split);
+            std::vector<std::vector<cd>> buf(CLt, std::vector<cd>(SL));
+            for (int r = 0; r < CLt; ++r)
+                for (uint32_t y = 0; y < SL; ++y) {
+                    const uint32_t x = split ? (ins0(y, h) | ((uint32_t)r << h)) : y;
+                    buf[r][swz(y)] = (((x >> aux) ^ (x >> P.first_bit)) & 1u) ? 0.0 : 1.0;
+                }
+            for (const SpiralWin &w : wins) {
+                const bool cross = split && w.hk >= 0;
+                std::vector<std::vector<char>> seen(CLt, std::vector<char>(SL, 0));
+                for (int r = 0; r < CLt; ++r)
+                    for (uint32_t t = 0; t < G; ++t) {
+                        const uint32_t tt = (cross ? r * G : 0u) + t;
+                        uint32_t b = tt >> 4;
+                        for (int j = 0; j < w.n_ins; ++j) b = ins0(b, w.ins[j]);
+                        for (int k = 0; k < 4; ++k) b |= ((tt >> k) & 1u) << w.lane[k];
+                        const uint32_t pb = swz(b);
+                        const int nv = 1 << R;
+                        std::vector<cd> v(nv);
+                        std::vector<uint32_t> addr(nv);
+                        std::vector<int> cta(nv);
+                        for (int i = 0; i < nv; ++i) {
+                            uint32_t a = pb;
+                            for (int k = 0; k < R; ++k) if ((i >> k) & 1) a ^= w.off[k];
+                            const int c = cross ? ((i >> w.hk) & 1) : r;
+                            if (a >= SL || seen[c][a]) { printf("n=%d L=%d R=%d split=%d: slot %u of CTA %d out of range or revisited\n", n, L, R, split, a, c); return 1; }
+                            seen[c][a] = 1;
+                            addr[i] = a; cta[i] = c; v[i] = buf[c][a];
+                        }
+                        for (int m = w.first; m < w.first + w.n_maps; ++m) {
+                            const int I = ij[m] & 15, J = ij[m] >> 4;
+                            for (int x = 0; x < nv; ++x) {
+                                if (x & ((1 << I) | (1 << J))) continue;
+                                const int id[4] = {x, x | (1 << I), x | (1 << J), x | (1 << I) | (1 << J)};
+                                cd y[4];
+                                for (int o = 0; o < 4; ++o) {
+                                    y[o] = 0;
+                                    for (int f = 0; f < 4; ++f) y[o] += Tall[m][4 * o + f] * v[id[f]];
+                                }
+                                for (int o = 0; o < 4; ++o) v[id[o]] = y[o];
+                            }
+                        }
+                        for (int i = 0; i < nv; ++i) buf[cta[i]][addr[i]] = v[i];
+                    }
+                for (int r = 0; r < CLt; ++r)
+                    for (uint32_t a = 0; a < SL; ++a)
+                        if (!seen[r][a]) { printf("n=%d L=%d R=%d split=%d: slot %u of CTA %d not visited\n", n, L, R, split, a, r); return 1; }
+            }
+            cd tw = 0;
+            for (auto &bb : buf) for (auto v : bb) tw += v;
+            printf("n=%d L=%d: %zu maps in %zu windows of %d bits, split %d (h=%d): |window - direct| %.2e\n", n, L,
+                   P.maps.size(), wins.size(), R, split, h, std::abs(tw - tr_sp));
+            if (std::abs(tw - tr_sp) > 1e-12 * std::max(1.0, std::abs(tr_sp))) return 1;
+        }
+    if (argc > 3 && std::string(argv[3]) == "nodense") {   // sizes beyond the dense check: windows only
+        printf("n=%d L=%d bits=%d maps=%zu: spiral %.12f%+.12fi (no dense check)\n", n, L, B, P.maps.size(),
+               tr_sp.real(), tr_sp.imag());
+        return 0;
+    }
     // dense reference
     size_t D = (size_t)1 << n;
     auto build = [&](int w) {

@@ -136,3 +136,25 @@ def test_paper_hea_spiral_matches_generic_sweep(fp, n, L_min, L_max):
     assert rel_err(ta, tb).max() <= TOL64, (ta, tb)
     t32, _, _ = a.trace_batch(0, N, fp.PREC_FP32_RAW)
     assert np.abs(t32 - tb).max() <= TOL32
+
+
+@pytest.mark.parametrize("n,L", [(12, 5), (50, 6), (50, 7), (50, 8), (51, 8)])
+def test_spiral_window_kernels_match_map_by_map(fp, n, L, monkeypatch):
+    # register windows of 4 and 5 bits (one CTA, or a 2-CTA cluster at 2^15
+    # amplitudes) against one map per pass on the same pairs; FP_SPIRAL_WIN is
+    # read when an ensemble plans a depth.  FP64 to 1e-10 of max(|Tr|, 1), FP32
+    # to 1e-4 absolute
+    N = 24
+    out = {}
+    for win in ("0", "4", "5"):
+        monkeypatch.setenv("FP_SPIRAL_WIN", win)
+        e = fp.Ensemble(fp.HEA_PAULI, n, L, seed=77 + L)
+        t64, k64, _ = e.trace_batch(0, N, fp.PREC_FP64)
+        t32, _, _ = e.trace_batch(0, N, fp.PREC_FP32_RAW)
+        e.close()
+        out[win] = (t64, t32, k64)
+    t64, t32, k64 = out["0"]
+    for win in ("4", "5"):
+        assert rel_err(out[win][0], t64).max() <= TOL64, win
+        assert np.abs(out[win][1] - t64).max() <= TOL32, win
+        assert np.all(np.isfinite(out[win][2]))
