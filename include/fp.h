@@ -59,7 +59,9 @@
  * Environment.  FP_AUTOTUNE_CACHE names a file in which the brickwork
  * autotuner keeps its choices; FP_SWEEP_CLUSTER (1, 4, 8 or 16) fixes the
  * number of CTAs that share one pair on the generic sweep (default: by
- * boundary size).
+ * boundary size); FP_SPIRAL_WIN (0, 4 or 5) fixes the register-window width
+ * of the spiral sweep of FP_HEA_PAULI (0: one map per pass; default: by
+ * state size), read when an ensemble first contracts a depth.
  *
  * Errors.  Calls return an fp_status; nothing is thrown across the ABI.
  * fp_last_error() gives a thread-local message for the last failing call on
