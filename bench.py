@@ -482,7 +482,7 @@ def main():
         # host->device per step: PairInfo (40 B) + order (4 B) + group (4 B) per pair;
         # device->host: kappa (8 B/pair, FP32 policy) + per-batch moments
         batches = 0
-        b, done = 4096, 0
+        b, done = 1 << 20, 0   # no target: fp_frame_potential takes batches of up to 2^20 pairs
         while done < P:
             done += min(b, P - done)
             batches += 1
@@ -499,7 +499,7 @@ def main():
     n_skipped = int(skipped.item())
     value = world * (P * args.steps - n_skipped) / (ms / 1e3)
     # roofline of the dominant contraction class (the sweep kernels carry the flop count)
-    cls = max((fp.K_SWEEP, fp.K_BRICK), key=lambda i: ks.ms[i])
+    cls = max((fp.K_SWEEP, fp.K_BRICK, fp.K_SPIRAL), key=lambda i: ks.ms[i])
     flops = 8.0 * ks.work[cls]                 # complex multiply-add = 8 real flops
     achieved = flops / (ks.ms[cls] / 1e3) / 1e12 if ks.ms[cls] > 0 else 0.0
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0

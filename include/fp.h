@@ -123,6 +123,7 @@ enum {
     FP_K_BRICK = 4,       /* brickwork boundary sweep + meet */
     FP_K_MOMENTS = 5,     /* Monte Carlo moments */
     FP_K_BOOTSTRAP = 6,   /* bootstrap resampling */
+    FP_K_SPIRAL = 7,      /* spiral sweep of FP_HEA_PAULI (maps + sweep) */
     FP_K_CLASSES = 8
 };
 
@@ -282,7 +283,9 @@ fp_status fp_exact_brickwork_fkq(int32_t n, int32_t l, int32_t k, int32_t q, voi
 
 /* Monte Carlo frame potential.  Contracts pairs first, first+1, ... in batches
  * until every group's relative standard error of F^(2) (or of F^(1) when
- * k_max = 1) is <= target_rel_stderr, or max_pairs pairs are done.
+ * k_max = 1) is <= target_rel_stderr, or max_pairs pairs are done.  With a
+ * target the batches start at 4096 pairs and double (up to 2^20); with
+ * target_rel_stderr <= 0 all max_pairs pairs run, in batches of 2^20.
  *   F, stderr  [n_groups * k_max] doubles (host), F[g*k_max + k-1] = F^(k) of group g,
  *              stderr = s/sqrt(N) with s the N-1 sample deviation;
  *   stats      may be NULL. */

@@ -20,9 +20,9 @@ PARALLEL, LOCAL, HEA, HEA_PAULI = 0, 1, 2, 3
 PREC_FP64, PREC_FP32, PREC_FP32_RAW = 0, 1, 2
 FLAG_SELF_PAIR, FLAG_DIAGONAL_GATES, FLAG_GENERIC_ONLY, FLAG_TIMING, FLAG_NO_GRAPHS = 1, 2, 4, 8, 16
 FLAG_SKIP_INFEASIBLE, FLAG_HEA_CZ = 32, 64
-K_SAMPLE, K_MERGE, K_TABLES, K_SWEEP, K_BRICK, K_MOMENTS, K_BOOTSTRAP, K_CLASSES = 0, 1, 2, 3, 4, 5, 6, 8
+K_SAMPLE, K_MERGE, K_TABLES, K_SWEEP, K_BRICK, K_MOMENTS, K_BOOTSTRAP, K_SPIRAL, K_CLASSES = 0, 1, 2, 3, 4, 5, 6, 7, 8
 K_NAMES = {0: "sample", 1: "merge", 2: "tables", 3: "sweep_generic", 4: "sweep_brick", 5: "moments",
-           6: "bootstrap"}
+           6: "bootstrap", 7: "sweep_spiral"}
 MAX_STATE_BITS = 24
 STATUS = {0: "FP_OK", -1: "FP_ERR_ARG", -2: "FP_ERR_CUDA", -3: "FP_ERR_OOM", -4: "FP_ERR_TIMEOUT",
           -5: "FP_ERR_INFEASIBLE"}

@@ -103,9 +103,11 @@ struct BrickCache {
 struct SpiralCache {        // one depth of the paper's HEA on the spiral sweep
     SpiralPlan sp;
     DBuf d_maps, d_items, d_refs, d_plan;
-    SpiralConfig cfg[2];       // FP64, FP32
-    DBuf d_wins[2], d_ij[2];   // register windows of cfg[p]
-    int nwins[2] = {0, 0}, h[2] = {-1, -1};
+    // variants: FP64, FP32, FP64 spread over a 4-CTA cluster (small batches:
+    // the FP64 recontraction of a few flagged pairs)
+    SpiralConfig cfg[3];
+    DBuf d_wins[3], d_ij[3];   // register windows of cfg[p]
+    int nwins[3] = {0, 0, 0}, h[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
 };
 
 struct fp_ensemble {
@@ -750,12 +752,12 @@ SpiralCache *spiral_plan(fp_ensemble *E, int L) {
             upload(sc->d_refs, sc->sp.refs, E->st) != cudaSuccess ||
             upload(sc->d_plan, std::vector<DevPlan>{pl}, E->st) != cudaSuccess)
             sc.reset();
-        for (int p = 0; sc && p < 2; ++p) {
-            sc->cfg[p] = spiral_config(sc->sp.bits, p == 1);
+        for (int p = 0; sc && p < 3; ++p) {
+            sc->cfg[p] = spiral_config(sc->sp.bits, p == 1, p == 2 ? 2 : 0);
             if (sc->cfg[p].R == 0) continue;
             std::vector<SpiralWin> wins;
             std::vector<uint8_t> ij;
-            spiral_windows(sc->sp, sc->cfg[p].R, sc->cfg[p].split, wins, ij, &sc->h[p]);
+            spiral_windows(sc->sp, sc->cfg[p].R, sc->cfg[p].split, wins, ij, sc->h[p]);
             sc->nwins[p] = (int)wins.size();
             if (upload(sc->d_wins[p], wins, E->st) != cudaSuccess || upload(sc->d_ij[p], ij, E->st) != cudaSuccess)
                 sc.reset();
@@ -777,8 +779,8 @@ fp_status run_spiral(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
     const size_t celem = fp32 ? sizeof(float2) : sizeof(double2);
     const int n_raw = 1 + d.n + L * d.n;
     const int n_merged = (int)sp.merges.size(), nmaps = (int)sp.maps.size();
-    const int pi32 = fp32 ? 1 : 0;
-    const SpiralConfig &cfg = sc->cfg[pi32];
+    const int pv = fp32 ? 1 : 0;
+    const SpiralConfig &cfg = sc->cfg[pv];
     const size_t scr = cfg.scratch_elems, mw = spiral_map_elems(fp32);
     const size_t per_pair = (size_t)2 * n_raw * 16 * sizeof(double2) + (size_t)n_merged * 16 * sizeof(double2) +
                             (size_t)nmaps * mw * celem + scr * celem;
@@ -821,15 +823,21 @@ fp_status run_spiral(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
             CK(t.stop((double)nb));
         }
         {
-            KTimer t(E, FP_K_SWEEP);
-            const bool use_win = cfg.R > 0;
+            KTimer t(E, FP_K_SPIRAL);
+            // too few FP64 pairs to fill the SMs: the 4-CTA form (same windows, smaller parts)
+            int p = pv;
+            if (!fp32 && sc->cfg[2].R > 0 && sc->cfg[2].split > cfg.split &&
+                (int64_t)nb * (1 << cfg.split) < (int64_t)E->sms)
+                p = 2;
+            const SpiralConfig &cf = sc->cfg[p];
+            const bool use_win = cf.R > 0;
             CK(launch_spiral(E->d_pairs.as<PairInfo>(), (int)nb, sc->d_maps.as<SpiralMap>(), nmaps, sp.bits,
-                             sp.first_bit, cfg, use_win ? sc->d_wins[pi32].as<SpiralWin>() : nullptr,
-                             use_win ? sc->nwins[pi32] : 0, use_win ? sc->d_ij[pi32].as<uint8_t>() : nullptr,
-                             sc->h[pi32], E->d_merged.as<double2>(), E->d_maps.p, E->d_spiral_scratch.p, fp32,
-                             err_scale, tr, kappa, err, E->st));
+                             sp.first_bit, cf, use_win ? sc->d_wins[p].as<SpiralWin>() : nullptr,
+                             use_win ? sc->nwins[p] : 0, use_win ? sc->d_ij[p].as<uint8_t>() : nullptr, sc->h[p],
+                             E->d_merged.as<double2>(), E->d_maps.p, E->d_spiral_scratch.p, fp32, err_scale, tr,
+                             kappa, err, E->st));
             CK(t.stop(cmac_pair * (double)nb));
-            if (E->timing) E->kst.launches[FP_K_SWEEP] += 1;   // maps + sweep
+            if (E->timing) E->kst.launches[FP_K_SPIRAL] += 1;   // maps + sweep
         }
         CK(cudaEventRecord(E->ev1, E->st));
         CK(cudaEventSynchronize(E->ev1));
@@ -1178,7 +1186,9 @@ fp_status fp_frame_potential(fp_ensemble *ens, uint64_t first, uint64_t max_pair
     std::memset(&st, 0, sizeof st);
     st.n_groups = ng;
     const int kt = k_max >= 2 ? 2 : 1;
-    uint64_t batch = 4096, done = 0;
+    // with a target: batches from 4096 pairs, doubling, so the stop can come early;
+    // without one: batches as large as the workspace allows
+    uint64_t batch = target_rel_stderr > 0 ? 4096 : (1u << 20), done = 0;
     bool reached = false;
     while (done < max_pairs && !reached) {
         uint64_t nb = std::min<uint64_t>(batch, max_pairs - done);

@@ -118,25 +118,27 @@ struct SpiralMap {
 // A register window of the spiral sweep: maps [first, first + n_maps) act only
 // on the window's nb state bits (ascending); map k acts on window bits
 // (ij[k] & 15, ij[k] >> 4) as its (low, high) index bits.
-// The state is split over `split` = 0 or 1 cluster bits: with split = 1 state
-// bit h lives in the CTA rank of a 2-CTA cluster and the other bits form the
-// local index (bits above h move down by one).  Local amplitudes are stored
-// at swizzled addresses s(y) = y ^ fold4(y >> 4) (fold4: XOR of the 4-bit
-// chunks), so that 16 lanes walking the lane bits hit 16 distinct 8-byte slots.
-// Threads build a group base from their group index t: the low 4 bits of t go
-// to the local positions lane[], the rest to the free local positions (zeros
-// inserted at ins[0..n_ins), ascending).
+// The state is split over s = 0, 1 or 2 cluster bits h0 < h1: amplitude x
+// lives in CTA rank (x_h0 + 2 x_h1) of a 2^s-CTA cluster at local index
+// y = x without those bits, stored at the swizzled slot
+// sw(y) = y ^ fold4(y >> 4) (fold4: XOR of the 4-bit chunks).  A CTA handles
+// the window's groups t' = rank * G + t; the group base takes bit j of t' at
+// state bit pos[j] (the four lane bits first, the cluster bits last, so that a
+// window without cluster bits stays in its CTA).  Amplitude i of a group sits
+// at slot sw(base) ^ (XOR of off[k] over the set bits k of i) in CTA
+// rank(base) ^ (XOR of ctab[k]).
 constexpr int kSpiralMaxWin = 5;
 constexpr int kSpiralWinMaxMaps = 16;   // maps per window (staged in shared memory)
+constexpr int kSpiralMaxPos = 24;
 struct SpiralWin {
     uint8_t bits[kSpiralMaxWin];   // state bits of the window, ascending
     uint8_t nb;                    // window bits (the register block is 2^nb)
     uint8_t n_maps;
-    int8_t hk;                     // index in bits[] of the cluster bit h; -1: none
-    uint8_t n_ins;
-    uint8_t ins[kSpiralMaxWin + 4];
-    uint8_t lane[4];
-    uint16_t off[kSpiralMaxWin];   // s(local unit vector) of each window bit (0 for h)
+    uint8_t cross;                 // 1: the window holds a cluster bit
+    uint8_t n_pos;                 // bits - nb
+    uint8_t ctab[kSpiralMaxWin];   // rank contribution of each window bit (cluster bits)
+    uint8_t pos[kSpiralMaxPos];
+    uint16_t off[kSpiralMaxWin];   // sw(local unit vector) of each window bit (0: cluster bit)
     int32_t first;
 };
 

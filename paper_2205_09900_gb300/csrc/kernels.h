@@ -61,18 +61,19 @@ size_t brick_smem_bytes(const BrickDev &d, bool fp32, bool *both);
 // (spiral_map_elems(fp32) elements of C per map), then the sweep.  The
 // configuration of a state of 2^bits amplitudes: R = 0 applies one map per
 // pass (shared memory when it fits, else `scratch`, scratch_elems per pair);
-// R = 4 or 5 runs windows of R bits (spiral_windows with `split`; cluster bit
-// h) over shared memory of one CTA (split = 0) or a 2-CTA cluster (split = 1).
+// R = 4 or 5 runs windows of R bits (spiral_windows with `split`; cluster bits
+// h[0], h[1]) over shared memory of one CTA (split = 0) or a 2^split-CTA
+// cluster (split = 1, 2).
 constexpr size_t kSpiralSmemMax = 128 * 1024;
 struct SpiralConfig {
     int R = 0;
     int split = 0;
     size_t scratch_elems = 0;
 };
-SpiralConfig spiral_config(int bits, bool fp32);
+SpiralConfig spiral_config(int bits, bool fp32, int min_split = 0);   // split >= min_split (<= 2)
 size_t spiral_map_elems(bool fp32);
 cudaError_t launch_spiral(const PairInfo *pairs, int npairs, const SpiralMap *sm, int nmaps, int bits, int first_bit,
-                          const SpiralConfig &cfg, const SpiralWin *wins, int nwins, const uint8_t *ij, int h,
+                          const SpiralConfig &cfg, const SpiralWin *wins, int nwins, const uint8_t *ij, const int *h,
                           const double2 *merged, void *maps, void *scratch, bool fp32, double err_scale, double *tr,
                           double *kappa, double *err, cudaStream_t st);
 // Set the thread-local message returned by fp_last_error().

@@ -11,9 +11,9 @@
 //                        state bits run on 2^R amplitudes per thread in
 //                        registers, one barrier per window.  The state sits
 //                        in shared memory (swizzled), in one CTA or split
-//                        over a 2-CTA cluster (distributed shared memory);
+//                        over a 2- or 4-CTA cluster (distributed shared memory);
 //   spiral_sweep_kernel  one map per pass (small states, or states too large
-//                        for two CTAs: a per-pair global slice).
+//                        for four CTAs: a per-pair global slice).
 // Both sweeps start from delta(aux, first bit) and end with the FP64 sum of
 // the state = Tr, its cancellation ratio and rounding-error estimate.
 #include <cooperative_groups.h>
@@ -55,45 +55,43 @@ template <typename C> struct MapW { static constexpr int w = 16; };
 template <> struct MapW<float2> { static constexpr int w = 32; };
 
 template <typename C> __device__ __forceinline__ void put_entry(C *dst, int e, double2 t) { dst[e] = mk<C>(t.x, t.y); }
-template <> __device__ __forceinline__ void put_entry<float2>(float2 *dst, int e, double2 t) {
-    dst[2 * e] = make_float2((float)t.x, (float)t.x);
-    dst[2 * e + 1] = make_float2((float)-t.y, (float)t.y);
+template <> __device__ __forceinline__ void put_entry<float2>(float2 *dst, int e, double2 t) {   // one 16-byte store
+    *reinterpret_cast<float4 *>(dst + 2 * e) = make_float4((float)t.x, (float)t.x, (float)-t.y, (float)t.y);
 }
 
-// entries of one map, T[4 o + f], o = o_a + 2 o_b, f = i_a + 2 i_b (SpiralType)
+// Entry T[4 o + f] of every map, o = o_a + 2 o_b, f = i_a + 2 i_b (SpiralType):
+// one thread per entry, so the 16 threads of a map store its record contiguously.
 template <typename C>
-__global__ void spiral_maps_kernel(const PairInfo *__restrict__ pairs, const SpiralMap *__restrict__ sm, int nmaps,
-                                   const double2 *__restrict__ merged, C *__restrict__ maps) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void spiral_maps_kernel(const PairInfo *__restrict__ pairs, int npairs, const SpiralMap *__restrict__ sm,
+                                   int nmaps, const double2 *__restrict__ merged, C *__restrict__ maps) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = gid >> 4, e = gid & 15;
     if (m >= nmaps) return;
-    const PairInfo pi = pairs[blockIdx.y];
     const SpiralMap s = sm[m];
-    const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
-    double2 F[4] = {one, zero, zero, one}, G[4] = {one, zero, zero, one};
-    if (s.f >= 0)
-        for (int e = 0; e < 4; ++e) F[e] = merged[(pi.merged_off + s.f) * 16 + e];
-    if (s.g >= 0)
-        for (int e = 0; e < 4; ++e) G[e] = merged[(pi.merged_off + s.g) * 16 + e];
-    C *out = maps + ((size_t)blockIdx.y * nmaps + m) * MapW<C>::w;
-    for (int o = 0; o < 4; ++o)
-        for (int f = 0; f < 4; ++f) {
-            const int oa = o & 1, ob = o >> 1, ia = f & 1, ib = f >> 1;
-            const double h = (ob & ib) ? -1.0 : 1.0;   // H[o_b][i_b] = (-1)^{o_b i_b}
-            double2 v = zero;
-            switch (s.type) {
-                case SP_DIAG_BA: if (o == f) v = G[2 * ib + ia]; break;
-                case SP_START: if (oa == ob) v = make_double2(h, 0); break;
-                case SP_MID: v = zm(F[2 * oa + ia], G[2 * ob + oa]); v.x *= h; v.y *= h; break;
-                case SP_MID_AUX: if (ob == ib) v = zm(F[2 * oa + ia], G[2 * ob + oa]); break;
-                case SP_RL: if (oa == ia) { v = G[2 * ob + ia]; v.x *= h; v.y *= h; } break;
-                case SP_MID_RR: if (ib == 0) v = zm(F[2 * oa + ia], G[2 * ob + oa]); break;
-                case SP_RR: if (oa == ia && ib == 0) v = G[2 * ob + ia]; break;
-                case SP_LL: if (oa == 0) { v = G[2 * ob + ia]; v.x *= h; v.y *= h; } break;
-                case SP_LL_AUX: if (oa == 0 && ob == ib) v = G[2 * ib + ia]; break;
-                default: break;
-            }
-            put_entry<C>(out, 4 * o + f, v);
+    const int o = e >> 2, f = e & 3;
+    const int oa = o & 1, ob = o >> 1, ia = f & 1, ib = f >> 1;
+    const double h = (ob & ib) ? -1.0 : 1.0;   // H[o_b][i_b] = (-1)^{o_b i_b}
+    for (int p = blockIdx.y; p < npairs; p += gridDim.y) {   // grid.y is capped at 65535
+        const int64_t mo = pairs[p].merged_off;
+        // entry (r, c) of merged item k (the identity when k < 0)
+        auto mat = [&](int k, int r, int c) {
+            return k >= 0 ? merged[(mo + k) * 16 + 2 * r + c] : make_double2(r == c ? 1.0 : 0.0, 0.0);
+        };
+        double2 v = make_double2(0, 0);
+        switch (s.type) {
+            case SP_DIAG_BA: if (o == f) v = mat(s.g, ib, ia); break;
+            case SP_START: if (oa == ob) v = make_double2(h, 0); break;
+            case SP_MID: v = zm(mat(s.f, oa, ia), mat(s.g, ob, oa)); v.x *= h; v.y *= h; break;
+            case SP_MID_AUX: if (ob == ib) v = zm(mat(s.f, oa, ia), mat(s.g, ob, oa)); break;
+            case SP_RL: if (oa == ia) { v = mat(s.g, ob, ia); v.x *= h; v.y *= h; } break;
+            case SP_MID_RR: if (ib == 0) v = zm(mat(s.f, oa, ia), mat(s.g, ob, oa)); break;
+            case SP_RR: if (oa == ia && ib == 0) v = mat(s.g, ob, ia); break;
+            case SP_LL: if (oa == 0) { v = mat(s.g, ob, ia); v.x *= h; v.y *= h; } break;
+            case SP_LL_AUX: if (oa == 0 && ob == ib) v = mat(s.g, ib, ia); break;
+            default: break;
         }
+        put_entry<C>(maps + ((size_t)p * nmaps + m) * MapW<C>::w, e, v);
+    }
 }
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {   // a * b + c, lane-wise
@@ -299,19 +297,31 @@ __device__ __forceinline__ void dsm_st(uint32_t a, double2 v) {
 
 template <int CL>
 __device__ __forceinline__ void win_sync(bool cluster_wide) {
-    if constexpr (CL == 2) {
+    if constexpr (CL > 1) {
         if (cluster_wide) { cg::this_cluster().sync(); return; }
     }
     __syncthreads();
 }
 
-// Register windows over a state held in the shared memory of CL = 1 or 2 CTAs
-// (one pair per CTA or per cluster).  With CL = 2 state bit h is the CTA
-// rank; a window holding h ("cross" window) reads and writes both CTAs'
-// halves through distributed shared memory and is fenced by cluster
-// barriers; the other windows stay in their own CTA.
-// Threads per CTA: the cluster form runs one CTA per SM (its half of the state
-// fills the shared memory), so it takes as many warps as its registers allow.
+__device__ __forceinline__ uint32_t del_bit(uint32_t x, int p) {   // remove bit p
+    return (x & ((1u << p) - 1u)) | ((x >> (p + 1)) << p);
+}
+
+template <int CL>
+__device__ __forceinline__ uint32_t pick_cta(const uint32_t (&ac)[CL], uint32_t r) {
+    if constexpr (CL == 1) return ac[0];
+    else if constexpr (CL == 2) return r ? ac[1] : ac[0];
+    else return (r & 2) ? ((r & 1) ? ac[3] : ac[2]) : ((r & 1) ? ac[1] : ac[0]);
+}
+
+// Register windows over a state held in the shared memory of CL = 1, 2 or 4
+// CTAs (one pair per CTA or per cluster).  With CL > 1 the cluster bits h0
+// (and h1) of an amplitude give its CTA rank; a window holding one of them
+// ("cross" window) reads and writes other CTAs' parts through distributed
+// shared memory and is fenced by cluster barriers; the other windows stay in
+// their own CTA.  Addressing: SpiralWin.
+// Threads per CTA: the FP32 two-CTA form runs one CTA per SM (its half of the
+// state fills the shared memory), so it takes as many warps as its registers allow.
 template <typename C, int CL> struct WinThreads { static constexpr int n = 256; };
 template <> struct WinThreads<float2, 2> { static constexpr int n = 512; };
 
@@ -319,29 +329,33 @@ template <typename C, int R, int CL>
 __global__ void __launch_bounds__(WinThreads<C, CL>::n) spiral_win_kernel(const PairInfo *__restrict__ pairs,
                                                          const SpiralWin *__restrict__ wins, int nwins,
                                                          const uint8_t *__restrict__ ij, int nmaps, int bits,
-                                                         int first_bit, int h, const C *__restrict__ maps,
+                                                         int first_bit, int h0, int h1, const C *__restrict__ maps,
                                                          double err_scale, double *__restrict__ tr,
                                                          double *__restrict__ kappa, double *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[4][16];
-    __shared__ double part[4];   // CL = 2: rank 1's sums, written into rank 0
-    constexpr int c = CL == 2 ? 1 : 0;
+    __shared__ double part[3][4];   // CL > 1: ranks 1.. write their sums into rank 0
+    constexpr int c = CL == 4 ? 2 : (CL == 2 ? 1 : 0);
     constexpr int MB = kSpiralWinMaxMaps * MapW<C>::w;   // elements of one staged window of maps
     C *st = (C *)smem_raw;
     const uint32_t SL = 1u << (bits - c);
     C *mbuf = st + SL;   // two windows of maps: this one and the next (cp.async)
-    uint32_t rank = 0, a0 = 0, a1 = 0;   // a0, a1: the two halves in the cluster window
-    double *part0 = part;
-    if constexpr (CL == 2) {
+    uint32_t rank = 0, ac[CL];   // ac[r]: rank r's part in the cluster window
+    double *part0 = &part[0][0];
+    if constexpr (CL > 1) {
         cg::cluster_group cl = cg::this_cluster();
         rank = cl.block_rank();
-        a0 = cluster_addr(st, 0);
-        a1 = cluster_addr(st, 1);
-        part0 = cl.map_shared_rank(part, 0);
+#pragma unroll
+        for (int r = 0; r < CL; ++r) ac[r] = cluster_addr(st, r);
+        part0 = cl.map_shared_rank(&part[0][0], 0);
+    } else {
+        ac[0] = 0;
     }
     const int aux = bits - 1;
     for (uint32_t y = threadIdx.x; y < SL; y += blockDim.x) {
-        const uint32_t x = CL == 2 ? (ins0s(y, h) | (rank << h)) : y;
+        uint32_t x = y;
+        if constexpr (c >= 1) x = ins0s(x, h0) | ((rank & 1u) << h0);
+        if constexpr (c == 2) x = ins0s(x, h1) | (((rank >> 1) & 1u) << h1);
         st[swz(y)] = mk<C>((((x >> aux) ^ (x >> first_bit)) & 1u) ? 0.0 : 1.0, 0.0);
     }
     const C *mp = maps + (size_t)(blockIdx.x / CL) * nmaps * MapW<C>::w;
@@ -354,27 +368,25 @@ __global__ void __launch_bounds__(WinThreads<C, CL>::n) spiral_win_kernel(const 
     };
     if (nwins > 0) stage(0);
     cp_async_wait_all();
-    win_sync<CL>(true);   // with CL = 2 also: both halves exist before any remote access
+    win_sync<CL>(true);   // with CL > 1 also: every part exists before any remote access
     const uint32_t G = 1u << (bits - R - c);   // groups this CTA handles per window
     for (int w = 0; w < nwins; ++w) {
         const SpiralWin &W = wins[w];   // uniform reads (read-only path)
-        const int hk = W.hk, n_ins = W.n_ins, first = W.first, n_maps = W.n_maps;
+        const int n_pos = W.n_pos, first = W.first, n_maps = W.n_maps;
+        const bool cross = CL > 1 && W.cross;
         if (w + 1 < nwins) stage(w + 1);   // lands while this window computes
         const C *mw = mbuf + (w & 1) * MB;
-        const bool cross = CL == 2 && hk >= 0;
-        uint32_t off[R], lane[4];
+        uint32_t off[R], ctab[R];
 #pragma unroll
-        for (int k = 0; k < R; ++k) off[k] = W.off[k];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) lane[k] = W.lane[k];
-        const uint32_t tb = cross ? rank * G : 0u;
+        for (int k = 0; k < R; ++k) { off[k] = W.off[k]; ctab[k] = W.ctab[k]; }
         for (uint32_t t = threadIdx.x; t < G; t += blockDim.x) {
-            const uint32_t tt = tb + t;
-            uint32_t b = tt >> 4;
-            for (int j = 0; j < n_ins; ++j) b = ins0s(b, W.ins[j]);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) b |= ((tt >> k) & 1u) << lane[k];
-            uint32_t pb = swz(b);
+            const uint32_t tt = rank * G + t;
+            uint32_t b = 0;
+            for (int j = 0; j < n_pos; ++j) b |= ((tt >> j) & 1u) << W.pos[j];
+            uint32_t cb = 0, lb = b;
+            if constexpr (c == 2) { cb = ((b >> h0) & 1u) | (((b >> h1) & 1u) << 1); lb = del_bit(del_bit(b, h1), h0); }
+            if constexpr (c == 1) { cb = (b >> h0) & 1u; lb = del_bit(b, h0); }
+            uint32_t pb = swz(lb);
             C v[1 << R];
             if (!cross) {
 #pragma unroll
@@ -387,10 +399,10 @@ __global__ void __launch_bounds__(WinThreads<C, CL>::n) spiral_win_kernel(const 
             } else {
 #pragma unroll
                 for (int i = 0; i < (1 << R); ++i) {
-                    uint32_t a = pb;
+                    uint32_t a = pb, r = cb;
 #pragma unroll
-                    for (int k = 0; k < R; ++k) if ((i >> k) & 1) a ^= off[k];
-                    v[i] = dsm_ld((((i >> hk) & 1) ? a1 : a0) + a * (uint32_t)sizeof(C), C());
+                    for (int k = 0; k < R; ++k) if ((i >> k) & 1) { a ^= off[k]; r ^= ctab[k]; }
+                    v[i] = dsm_ld(pick_cta<CL>(ac, r) + a * (uint32_t)sizeof(C), C());
                 }
             }
             for (int m = 0; m < n_maps; ++m) {
@@ -400,7 +412,7 @@ __global__ void __launch_bounds__(WinThreads<C, CL>::n) spiral_win_kernel(const 
                 win_map_ij<C, R>(q & 15, q >> 4, v, T);
             }
             // the store addresses are rebuilt from pb (not kept live across the maps)
-            asm volatile("" : "+r"(pb));
+            asm volatile("" : "+r"(pb), "+r"(cb));
             if (!cross) {
 #pragma unroll
                 for (int i = 0; i < (1 << R); ++i) {
@@ -412,26 +424,27 @@ __global__ void __launch_bounds__(WinThreads<C, CL>::n) spiral_win_kernel(const 
             } else {
 #pragma unroll
                 for (int i = 0; i < (1 << R); ++i) {
-                    uint32_t a = pb;
+                    uint32_t a = pb, r = cb;
 #pragma unroll
-                    for (int k = 0; k < R; ++k) if ((i >> k) & 1) a ^= off[k];
-                    dsm_st((((i >> hk) & 1) ? a1 : a0) + a * (uint32_t)sizeof(C), v[i]);
+                    for (int k = 0; k < R; ++k) if ((i >> k) & 1) { a ^= off[k]; r ^= ctab[k]; }
+                    dsm_st(pick_cta<CL>(ac, r) + a * (uint32_t)sizeof(C), v[i]);
                 }
             }
         }
-        const bool next_cross = CL == 2 && w + 1 < nwins && wins[w + 1].hk >= 0;
+        const bool next_cross = CL > 1 && w + 1 < nwins && wins[w + 1].cross;
         cp_async_wait_all();   // the next window's maps are in place before the barrier
         win_sync<CL>(cross || next_cross);
     }
     double s[4];
     block_sums<C>(st, SL, red, s);
-    if constexpr (CL == 2) {
-        if (rank == 1 && threadIdx.x == 0)
-            for (int k = 0; k < 4; ++k) part0[k] = s[k];
-        cg::this_cluster().sync();   // rank 1's sums are in rank 0; rank 1 may exit after this
+    if constexpr (CL > 1) {
+        if (rank > 0 && threadIdx.x == 0)
+            for (int k = 0; k < 4; ++k) part0[(rank - 1) * 4 + k] = s[k];
+        cg::this_cluster().sync();   // every rank's sums are in rank 0; ranks > 0 may exit after this
         if (rank == 0 && threadIdx.x == 0) {
-            for (int k = 0; k < 4; ++k) s[k] += part[k];
-            write_result(pairs[blockIdx.x / 2], s, err_scale, tr, kappa, err);
+            for (int r = 1; r < CL; ++r)
+                for (int k = 0; k < 4; ++k) s[k] += part[r - 1][k];
+            write_result(pairs[blockIdx.x / CL], s, err_scale, tr, kappa, err);
         }
     } else {
         if (threadIdx.x == 0) write_result(pairs[blockIdx.x], s, err_scale, tr, kappa, err);
@@ -440,9 +453,9 @@ __global__ void __launch_bounds__(WinThreads<C, CL>::n) spiral_win_kernel(const 
 
 template <typename C, int R, int CL>
 cudaError_t win_t(const PairInfo *pairs, int npairs, const SpiralWin *wins, int nwins, const uint8_t *ij, int nmaps,
-                  int bits, int first_bit, int h, const void *maps, double err_scale, double *tr, double *kappa,
+                  int bits, int first_bit, const int *h, const void *maps, double err_scale, double *tr, double *kappa,
                   double *err, cudaStream_t st) {
-    constexpr int c = CL == 2 ? 1 : 0;
+    constexpr int c = CL == 4 ? 2 : (CL == 2 ? 1 : 0);
     const size_t bytes = (((size_t)1 << (bits - c)) + 2 * kSpiralWinMaxMaps * MapW<C>::w) * sizeof(C);
     const uint32_t G = 1u << (bits - R - c);
     const int threads = (int)std::min<uint32_t>(WinThreads<C, CL>::n, std::max<uint32_t>(32u, G));
@@ -461,8 +474,8 @@ cudaError_t win_t(const PairInfo *pairs, int npairs, const SpiralWin *wins, int 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, pairs, wins, nwins, ij, nmaps, bits, first_bit, h, (const C *)maps, err_scale,
-                              tr, kappa, err);
+    return cudaLaunchKernelEx(&cfg, k, pairs, wins, nwins, ij, nmaps, bits, first_bit, h[0], h[1], (const C *)maps,
+                              err_scale, tr, kappa, err);
 }
 
 template <typename C>
@@ -488,49 +501,54 @@ cudaError_t sweep_t(const PairInfo *pairs, int npairs, const SpiralMap *sm, int 
 
 size_t spiral_map_elems(bool fp32) { return fp32 ? MapW<float2>::w : MapW<double2>::w; }
 
-SpiralConfig spiral_config(int bits, bool fp32) {
+SpiralConfig spiral_config(int bits, bool fp32, int min_split) {
     SpiralConfig c;
     const size_t bytes = ((size_t)1 << bits) * (fp32 ? sizeof(float2) : sizeof(double2));
-    c.split = bytes <= kSpiralSmemMax ? 0 : (bytes <= 2 * kSpiralSmemMax ? 1 : -1);
+    c.split = bytes <= kSpiralSmemMax ? 0 : bytes <= 2 * kSpiralSmemMax ? 1 : bytes <= 4 * kSpiralSmemMax ? 2 : -1;
+    if (c.split >= 0) c.split = std::max(c.split, std::min(min_split, 2));
     // measured on GB300 (n = 50, depths 5..8): 5-bit windows from 2^13 FP32
     // amplitudes up, else 4
     c.R = fp32 && bits >= 13 ? 5 : 4;
     if (const char *ev = std::getenv("FP_SPIRAL_WIN")) c.R = std::atoi(ev);   // tuning override: 0, 4 or 5
     if (c.R != 0 && c.R != 4 && !(c.R == 5 && fp32)) c.R = 4;
     // windows need 16 lane groups per CTA and a state in (distributed) shared memory
-    if (c.split < 0 || bits - c.R - c.split < 4) c.R = 0;
+    if (c.split < 0 || bits - c.R - c.split < 4 || bits - c.R > kSpiralMaxPos) c.R = 0;
     if (c.R == 0) c.split = 0;
     c.scratch_elems = (c.R == 0 && bytes > kSpiralSmemMax) ? ((size_t)1 << bits) : 0;
     return c;
 }
 
 cudaError_t launch_spiral(const PairInfo *pairs, int npairs, const SpiralMap *sm, int nmaps, int bits, int first_bit,
-                          const SpiralConfig &cfg, const SpiralWin *wins, int nwins, const uint8_t *ij, int h,
+                          const SpiralConfig &cfg, const SpiralWin *wins, int nwins, const uint8_t *ij, const int *h,
                           const double2 *merged, void *maps, void *scratch, bool fp32, double err_scale, double *tr,
                           double *kappa, double *err, cudaStream_t st) {
     if (npairs <= 0) return cudaSuccess;
-    dim3 gm((nmaps + 127) / 128, npairs);
-    if (fp32) spiral_maps_kernel<float2><<<gm, 128, 0, st>>>(pairs, sm, nmaps, merged, (float2 *)maps);
-    else spiral_maps_kernel<double2><<<gm, 128, 0, st>>>(pairs, sm, nmaps, merged, (double2 *)maps);
+    dim3 gm((16 * nmaps + 255) / 256, std::min(npairs, 65535));
+    if (fp32) spiral_maps_kernel<float2><<<gm, 256, 0, st>>>(pairs, npairs, sm, nmaps, merged, (float2 *)maps);
+    else spiral_maps_kernel<double2><<<gm, 256, 0, st>>>(pairs, npairs, sm, nmaps, merged, (double2 *)maps);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (wins && cfg.R > 0) {
-        const int sel = (fp32 ? 4 : 0) + (cfg.R == 5 ? 2 : 0) + cfg.split;
-        switch (sel) {
-            case 0: return win_t<double2, 4, 1>(pairs, npairs, wins, nwins, ij, nmaps, bits, first_bit, h, maps,
-                                                err_scale, tr, kappa, err, st);
-            case 1: return win_t<double2, 4, 2>(pairs, npairs, wins, nwins, ij, nmaps, bits, first_bit, h, maps,
-                                                err_scale, tr, kappa, err, st);
-            case 4: return win_t<float2, 4, 1>(pairs, npairs, wins, nwins, ij, nmaps, bits, first_bit, h, maps,
-                                               err_scale, tr, kappa, err, st);
-            case 5: return win_t<float2, 4, 2>(pairs, npairs, wins, nwins, ij, nmaps, bits, first_bit, h, maps,
-                                               err_scale, tr, kappa, err, st);
-            case 6: return win_t<float2, 5, 1>(pairs, npairs, wins, nwins, ij, nmaps, bits, first_bit, h, maps,
-                                               err_scale, tr, kappa, err, st);
-            case 7: return win_t<float2, 5, 2>(pairs, npairs, wins, nwins, ij, nmaps, bits, first_bit, h, maps,
-                                               err_scale, tr, kappa, err, st);
-            default: return cudaErrorInvalidValue;
+#define FP_SPIRAL_WIN_CASE(C, R, CL)                                                                               \
+    return win_t<C, R, CL>(pairs, npairs, wins, nwins, ij, nmaps, bits, first_bit, h, maps, err_scale, tr, kappa, \
+                           err, st)
+        const int CL = 1 << cfg.split;
+        if (!fp32) {
+            if (cfg.R != 4) return cudaErrorInvalidValue;
+            if (CL == 1) FP_SPIRAL_WIN_CASE(double2, 4, 1);
+            if (CL == 2) FP_SPIRAL_WIN_CASE(double2, 4, 2);
+            if (CL == 4) FP_SPIRAL_WIN_CASE(double2, 4, 4);
+        } else if (cfg.R == 4) {
+            if (CL == 1) FP_SPIRAL_WIN_CASE(float2, 4, 1);
+            if (CL == 2) FP_SPIRAL_WIN_CASE(float2, 4, 2);
+            if (CL == 4) FP_SPIRAL_WIN_CASE(float2, 4, 4);
+        } else if (cfg.R == 5) {
+            if (CL == 1) FP_SPIRAL_WIN_CASE(float2, 5, 1);
+            if (CL == 2) FP_SPIRAL_WIN_CASE(float2, 5, 2);
+            if (CL == 4) FP_SPIRAL_WIN_CASE(float2, 5, 4);
         }
+#undef FP_SPIRAL_WIN_CASE
+        return cudaErrorInvalidValue;
     }
     return fp32 ? sweep_t<float2>(pairs, npairs, sm, nmaps, bits, first_bit, maps, scratch, err_scale, tr, kappa, err, st)
                 : sweep_t<double2>(pairs, npairs, sm, nmaps, bits, first_bit, maps, scratch, err_scale, tr, kappa, err, st);

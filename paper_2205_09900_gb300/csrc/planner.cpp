@@ -382,13 +382,14 @@ static uint32_t spiral_swizzle(uint32_t y) {   // s(y) of the spiral window kern
 }
 
 void spiral_windows(const SpiralPlan &P, int R, int split, std::vector<SpiralWin> &wins, std::vector<uint8_t> &ij,
-                    int *h_out) {
+                    int h_out[2]) {
     wins.clear();
     ij.assign(P.maps.size(), 0);
     R = std::min(std::max(R, 2), std::min(kSpiralMaxWin, P.bits));
+    // runs of consecutive maps on at most R bits
     std::vector<uint32_t> sets;
-    size_t k = 0;
-    while (k < P.maps.size()) {
+    std::vector<std::pair<size_t, size_t>> runs;
+    for (size_t k = 0; k < P.maps.size();) {
         uint32_t set = 0;
         size_t e = k;
         for (; e < P.maps.size(); ++e) {
@@ -396,59 +397,72 @@ void spiral_windows(const SpiralPlan &P, int R, int split, std::vector<SpiralWin
             if (__builtin_popcount(s2) > R || e - k >= (size_t)kSpiralWinMaxMaps) break;
             set = s2;
         }
-        // pad the window to R bits with the lowest other state bits (every window moves 2^R amplitudes)
-        for (int b = 0; b < P.bits && __builtin_popcount(set) < R; ++b) set |= 1u << b;
+        sets.push_back(set);
+        runs.push_back({k, e});
+        k = e;
+    }
+    // cluster bits: the state bits the fewest runs touch
+    int hb[2] = {-1, -1};
+    {
+        std::vector<std::pair<int, int>> use;   // (runs touching the bit, bit)
+        for (int b = 0; b < P.bits; ++b) {
+            int c = 0;
+            for (uint32_t s : sets) c += (s >> b) & 1;
+            use.push_back({c, b});
+        }
+        std::sort(use.begin(), use.end());
+        for (int q = 0; q < split && q < 2; ++q) hb[q] = use[q].second;
+        if (split == 2 && hb[0] > hb[1]) std::swap(hb[0], hb[1]);
+    }
+    uint32_t hmask = 0;
+    for (int q = 0; q < 2; ++q) if (hb[q] >= 0) hmask |= 1u << hb[q];
+    for (size_t i = 0; i < runs.size(); ++i) {
+        // pad to R bits with the lowest other non-cluster bits (every window moves 2^R amplitudes)
+        uint32_t &set = sets[i];
+        for (int pass = 0; pass < 2; ++pass)
+            for (int b = 0; b < P.bits && __builtin_popcount(set) < R; ++b)
+                if (pass == 1 || !(hmask >> b & 1)) set |= 1u << b;
         SpiralWin w;
         std::memset(&w, 0, sizeof w);
         int loc[32], nb = 0;
         for (int b = 0; b < P.bits; ++b)
             if (set & (1u << b)) { loc[b] = nb; w.bits[nb++] = (uint8_t)b; }
         w.nb = (uint8_t)nb;
-        w.n_maps = (uint8_t)(e - k);
-        w.first = (int32_t)k;
-        for (size_t m = k; m < e; ++m) ij[m] = (uint8_t)(loc[P.maps[m].a] | (loc[P.maps[m].b] << 4));
+        w.n_maps = (uint8_t)(runs[i].second - runs[i].first);
+        w.first = (int32_t)runs[i].first;
+        for (size_t m = runs[i].first; m < runs[i].second; ++m)
+            ij[m] = (uint8_t)(loc[P.maps[m].a] | (loc[P.maps[m].b] << 4));
         wins.push_back(w);
-        sets.push_back(set);
-        k = e;
     }
-    // cluster bit: the state bit in the fewest windows
-    int h = -1;
-    if (split) {
-        int best = 1 << 30;
-        for (int b = 0; b < P.bits; ++b) {
-            int c = 0;
-            for (uint32_t s : sets) c += (s >> b) & 1;
-            if (c < best) { best = c; h = b; }
-        }
-    }
-    if (h_out) *h_out = h;
-    const int LB = P.bits - (split ? 1 : 0);   // local index bits
-    auto local = [&](int b) { return h >= 0 && b > h ? b - 1 : b; };
+    if (h_out) { h_out[0] = hb[0]; h_out[1] = hb[1]; }
+    auto local = [&](int b) { return b - __builtin_popcount(hmask & ((1u << b) - 1u)); };
     for (size_t i = 0; i < wins.size(); ++i) {
         SpiralWin &w = wins[i];
-        w.hk = -1;
-        uint32_t used = 0;   // local positions taken by the window
+        const uint32_t set = sets[i];
+        w.cross = (set & hmask) ? 1 : 0;
         for (int q = 0; q < w.nb; ++q) {
-            if (w.bits[q] == h) { w.hk = (int8_t)q; w.off[q] = 0; continue; }
-            const int p = local(w.bits[q]);
-            used |= 1u << p;
-            w.off[q] = (uint16_t)spiral_swizzle(1u << p);
+            const int b = w.bits[q];
+            w.ctab[q] = (uint8_t)((b == hb[0] ? 1 : 0) | (b == hb[1] ? 2 : 0));
+            w.off[q] = (hmask >> b & 1) ? 0 : (uint16_t)spiral_swizzle(1u << local(b));
         }
-        // lane q: the lowest free local position of residue q mod 4 (16 lanes then
-        // touch 16 distinct slots of s); else the lowest free position left
+        // lane q: the free non-cluster bit of lowest local position with residue q mod 4
+        // (16 lanes then touch 16 distinct slots of sw), else the lowest one left
+        const uint32_t freem = ((1u << P.bits) - 1u) & ~set;
         uint32_t lanes = 0;
+        int n = 0;
         for (int q = 0; q < 4; ++q) {
             int pick = -1;
-            for (int p = 0; p < LB && pick < 0; ++p)
-                if (!((used | lanes) >> p & 1) && p % 4 == q) pick = p;
-            for (int p = 0; p < LB && pick < 0; ++p)
-                if (!((used | lanes) >> p & 1)) pick = p;
-            w.lane[q] = (uint8_t)std::max(pick, 0);
-            if (pick >= 0) lanes |= 1u << pick;
+            for (int b = 0; b < P.bits && pick < 0; ++b)
+                if ((freem & ~hmask & ~lanes) >> b & 1 && local(b) % 4 == q) pick = b;
+            for (int b = 0; b < P.bits && pick < 0; ++b)
+                if ((freem & ~hmask & ~lanes) >> b & 1) pick = b;
+            if (pick >= 0) { lanes |= 1u << pick; w.pos[n++] = (uint8_t)pick; }
         }
-        w.n_ins = 0;
-        for (int p = 0; p < LB; ++p)
-            if ((used | lanes) >> p & 1) w.ins[w.n_ins++] = (uint8_t)p;
+        for (int b = 0; b < P.bits; ++b)
+            if ((freem & ~hmask & ~lanes) >> b & 1) w.pos[n++] = (uint8_t)b;
+        for (int b = 0; b < P.bits; ++b)
+            if ((freem & hmask) >> b & 1) w.pos[n++] = (uint8_t)b;
+        w.n_pos = (uint8_t)n;
     }
 }
 

@@ -64,10 +64,11 @@ struct SpiralPlan {
 SpiralPlan make_spiral_plan(int n, const std::vector<GateSlot> &U, const std::vector<GateSlot> &V, int raw_kind);
 // Consecutive maps grouped into windows of R state bits (R <= kSpiralMaxWin,
 // padded with the lowest other bits); ij[k]: map k's window-local (low, high)
-// bits.  split = 1 also picks the cluster bit h (the state bit fewest windows
-// touch; returned in *h) and the local addressing of every window.
+// bits.  `split` (0, 1, 2) cluster bits are the state bits fewest windows touch
+// (returned ascending in h[0], h[1]; -1 when unused); every window gets its
+// addressing (SpiralWin).  Needs bits - R - split >= 4.
 void spiral_windows(const SpiralPlan &P, int R, int split, std::vector<SpiralWin> &wins, std::vector<uint8_t> &ij,
-                    int *h);
+                    int h[2]);
 
 // Plan the contraction of Tr(U^dagger V).  `cut`: the left sweep owns bonds
 // 0..cut-1 and the 1-qubit gates of qubits 0..cut-1, the right sweep the rest.

@@ -92,21 +92,23 @@ int main(int argc, char **argv) {
     cd tr_sp = 0; for (auto v : st) tr_sp += v;
     // register windows (spiral_windows): consecutive runs covering every map once,
     // in order, each of exactly min(R, bits) ascending bits holding its maps' bits;
-    // then the window kernel's addressing emulated in FP64 (swizzled slots, lane
-    // and insert positions, the 2-CTA split): every slot visited once per window,
-    // every index in bounds, and the same trace as the map-by-map sweep
+    // then the window kernel's addressing emulated in FP64 (group bases from the
+    // deposit positions, swizzled slots, 1/2/4-CTA parts): every slot of every
+    // part visited once per window, every index in bounds, a window without
+    // cluster bits inside its own CTA, and the same trace as map by map
     auto swz = [](uint32_t y) { uint32_t q = y >> 4; return y ^ ((q ^ (q >> 4) ^ (q >> 8) ^ (q >> 12)) & 15u); };
     auto ins0 = [](uint32_t x, int p) { return (x & ((1u << p) - 1u)) | ((x >> p) << (p + 1)); };
+    auto del = [](uint32_t x, int p) { return (x & ((1u << p) - 1u)) | ((x >> (p + 1)) << p); };
     for (int R = 4; R <= 5; ++R)
-        for (int split = 0; split <= 1; ++split) {
+        for (int split = 0; split <= 2; ++split) {
             if (B - R - split < 4) continue;   // the kernel's precondition
             std::vector<SpiralWin> wins;
             std::vector<uint8_t> ij;
-            int h = -1;
-            spiral_windows(P, R, split, wins, ij, &h);
+            int h[2] = {-1, -1};
+            spiral_windows(P, R, split, wins, ij, h);
             size_t next = 0;
             for (const SpiralWin &w : wins) {
-                bool ok = w.first == (int)next && w.n_maps > 0 && w.nb == std::min(R, B);
+                bool ok = w.first == (int)next && w.n_maps > 0 && w.nb == std::min(R, B) && w.n_pos == B - w.nb;
                 for (int k = 1; k < w.nb; ++k) ok = ok && w.bits[k - 1] < w.bits[k];
                 for (int k = 0; k < w.nb; ++k) ok = ok && w.bits[k] < B;
                 for (int m = w.first; ok && m < w.first + w.n_maps; ++m) {
@@ -117,35 +119,43 @@ int main(int argc, char **argv) {
                 next += w.n_maps;
             }
             if (next != P.maps.size()) { printf("n=%d L=%d: %d-bit windows cover %zu of %zu maps\n", n, L, R, next, P.maps.size()); return 1; }
-            const int LBt = B - split, CLt = 1 << split;
-            const uint32_t SL = 1u << LBt, G = 1u << (B - R - split);
+            const int CLt = 1 << split;
+            const uint32_t SL = 1u << (B - split), G = 1u << (B - R - split);
             std::vector<std::vector<cd>> buf(CLt, std::vector<cd>(SL));
             for (int r = 0; r < CLt; ++r)
                 for (uint32_t y = 0; y < SL; ++y) {
-                    const uint32_t x = split ? (ins0(y, h) | ((uint32_t)r << h)) : y;
+                    uint32_t x = y;
+                    if (split >= 1) x = ins0(x, h[0]) | ((uint32_t)(r & 1) << h[0]);
+                    if (split == 2) x = ins0(x, h[1]) | ((uint32_t)((r >> 1) & 1) << h[1]);
                     buf[r][swz(y)] = (((x >> aux) ^ (x >> P.first_bit)) & 1u) ? 0.0 : 1.0;
                 }
+            int ncross = 0;
             for (const SpiralWin &w : wins) {
-                const bool cross = split && w.hk >= 0;
+                ncross += w.cross;
                 std::vector<std::vector<char>> seen(CLt, std::vector<char>(SL, 0));
                 for (int r = 0; r < CLt; ++r)
                     for (uint32_t t = 0; t < G; ++t) {
-                        const uint32_t tt = (cross ? r * G : 0u) + t;
-                        uint32_t b = tt >> 4;
-                        for (int j = 0; j < w.n_ins; ++j) b = ins0(b, w.ins[j]);
-                        for (int k = 0; k < 4; ++k) b |= ((tt >> k) & 1u) << w.lane[k];
-                        const uint32_t pb = swz(b);
+                        const uint32_t tt = r * G + t;
+                        uint32_t b = 0;
+                        for (int j = 0; j < w.n_pos; ++j) b |= ((tt >> j) & 1u) << w.pos[j];
+                        uint32_t cb = 0, lb = b;
+                        if (split == 2) { cb = ((b >> h[0]) & 1u) | (((b >> h[1]) & 1u) << 1); lb = del(del(b, h[1]), h[0]); }
+                        if (split == 1) { cb = (b >> h[0]) & 1u; lb = del(b, h[0]); }
+                        const uint32_t pb = swz(lb);
                         const int nv = 1 << R;
                         std::vector<cd> v(nv);
                         std::vector<uint32_t> addr(nv);
                         std::vector<int> cta(nv);
                         for (int i = 0; i < nv; ++i) {
-                            uint32_t a = pb;
-                            for (int k = 0; k < R; ++k) if ((i >> k) & 1) a ^= w.off[k];
-                            const int c = cross ? ((i >> w.hk) & 1) : r;
-                            if (a >= SL || seen[c][a]) { printf("n=%d L=%d R=%d split=%d: slot %u of CTA %d out of range or revisited\n", n, L, R, split, a, c); return 1; }
+                            uint32_t a = pb, c = cb;
+                            for (int k = 0; k < R; ++k) if ((i >> k) & 1) { a ^= w.off[k]; c ^= w.ctab[k]; }
+                            if (a >= SL || (int)c >= CLt || seen[c][a] || (!w.cross && (int)c != r)) {
+                                printf("n=%d L=%d R=%d split=%d: slot %u of CTA %u (group of CTA %d) out of range, "
+                                       "revisited or remote in a local window\n", n, L, R, split, a, c, r);
+                                return 1;
+                            }
                             seen[c][a] = 1;
-                            addr[i] = a; cta[i] = c; v[i] = buf[c][a];
+                            addr[i] = a; cta[i] = (int)c; v[i] = buf[c][a];
                         }
                         for (int m = w.first; m < w.first + w.n_maps; ++m) {
                             const int I = ij[m] & 15, J = ij[m] >> 4;
@@ -168,8 +178,8 @@ int main(int argc, char **argv) {
             }
             cd tw = 0;
             for (auto &bb : buf) for (auto v : bb) tw += v;
-            printf("n=%d L=%d: %zu maps in %zu windows of %d bits, split %d (h=%d): |window - direct| %.2e\n", n, L,
-                   P.maps.size(), wins.size(), R, split, h, std::abs(tw - tr_sp));
+            printf("n=%d L=%d: %zu maps in %zu windows of %d bits, split %d (h=%d,%d; %d cross): |window - direct| %.2e\n",
+                   n, L, P.maps.size(), wins.size(), R, split, h[0], h[1], ncross, std::abs(tw - tr_sp));
             if (std::abs(tw - tr_sp) > 1e-12 * std::max(1.0, std::abs(tr_sp))) return 1;
         }
     if (argc > 3 && std::string(argv[3]) == "nodense") {   // sizes beyond the dense check: windows only

@@ -2,7 +2,7 @@
 tests/cpp/spiral_plan_check.cpp, compiled against the library's planner,
 applies the spiral maps in FP64 and compares with dense Tr(U^dagger V), and
 emulates the register-window kernel's addressing (swizzled slots, lane bits,
-the 2-CTA split) against the map-by-map sweep.  CPU."""
+the 2- and 4-CTA splits) against the map-by-map sweep.  CPU."""
 import os
 import shutil
 import subprocess
@@ -38,4 +38,4 @@ def test_spiral_windows_full_size(checker, n, L):
     # the benchmark's sizes: 2^11..2^15 amplitudes, every window layout the GPU runs
     r = subprocess.run([checker, str(n), str(L), "nodense"], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert "split 1" in r.stdout
+    assert "split 1" in r.stdout and "split 2" in r.stdout
