@@ -61,7 +61,9 @@
  * number of CTAs that share one pair on the generic sweep (default: by
  * boundary size); FP_SPIRAL_WIN (0, 4 or 5) fixes the register-window width
  * of the spiral sweep of FP_HEA_PAULI (0: one map per pass; default: by
- * state size), read when an ensemble first contracts a depth.
+ * state size) and FP_SPIRAL_SPLIT (0, 1 or 2) the least number of cluster
+ * bits its state is split over (default 0: as the state size needs); both are
+ * read when an ensemble first contracts a depth.
  *
  * Errors.  Calls return an fp_status; nothing is thrown across the ABI.
  * fp_last_error() gives a thread-local message for the last failing call on

@@ -505,6 +505,7 @@ SpiralConfig spiral_config(int bits, bool fp32, int min_split) {
     SpiralConfig c;
     const size_t bytes = ((size_t)1 << bits) * (fp32 ? sizeof(float2) : sizeof(double2));
     c.split = bytes <= kSpiralSmemMax ? 0 : bytes <= 2 * kSpiralSmemMax ? 1 : bytes <= 4 * kSpiralSmemMax ? 2 : -1;
+    if (const char *ev = std::getenv("FP_SPIRAL_SPLIT")) min_split = std::max(min_split, std::atoi(ev));   // tuning
     if (c.split >= 0) c.split = std::max(c.split, std::min(min_split, 2));
     // measured on GB300 (n = 50, depths 5..8): 5-bit windows from 2^13 FP32
     // amplitudes up, else 4
