@@ -512,9 +512,9 @@ def main():
             "kernel_ms_share": ks.ms[cls] / ms if ms else None}
     if WORK["name"] == "brickwork" and prec == fp.PREC_FP32:
         # DRAM bytes (read + write) of the dominant kernel from one ncu capture of the current
-        # tile-pass code: brick_pass_kernel<float2, 14, 5, 256>, depth 10, one pass over 256 pairs
-        roof["traffic"] = 537.914112e6 + 477.020928e6
-        roof["traffic_launch"] = ("brick_pass_kernel<float2,14,5,256>, l=10, one tile pass of 256 pairs; "
+        # tile-pass code: brick_pass_kernel<float2, 13, 5, 256>, depth 10, one pass over 256 pairs
+        roof["traffic"] = 538.040832e6 + 476.1664e6
+        roof["traffic_launch"] = ("brick_pass_kernel<float2,13,5,256>, l=10, one tile pass of 256 pairs; "
                                   "algorithmic bytes 2 x 256 x 2^18 x 8 = 1.0737e9")
 
     metric = {"brickwork": METRIC, "hea": "Tr(U^dagger V) contractions/s at n=50 (HEA, L=1..8)",

@@ -487,7 +487,7 @@ __device__ __forceinline__ void tile_register_passes(C *__restrict__ tile, const
             uint32_t b0 = t;
 #pragma unroll
             for (int k = 0; k < R; ++k) b0 = ins0(b0, rp.srt[k]);
-            const uint32_t sb = swz(b0);
+            uint32_t sb = swz(b0);
             C v[1 << R];
 #pragma unroll
             for (int i = 0; i < (1 << R); ++i) {
@@ -500,6 +500,8 @@ __device__ __forceinline__ void tile_register_passes(C *__restrict__ tile, const
                 const RegGate rg = srg[rp.gate_off - g0 + g];
                 win_dispatch<C, R>(rg.type, v, smaps + rg.slot * MW);
             }
+            // the store addresses are rebuilt from sb (not kept live across the gates)
+            asm volatile("" : "+r"(sb));
 #pragma unroll
             for (int i = 0; i < (1 << R); ++i) {
                 uint32_t a = sb;
@@ -548,7 +550,8 @@ __device__ __forceinline__ uint32_t tile_base(uint32_t t, uint32_t smask, int N)
 // and the gates are applied window by window with 2^R amplitudes per thread
 // in registers; one barrier per window.
 template <typename C, int K, int R, int TH>
-__global__ void __launch_bounds__(TH) brick_pass_kernel(BrickDev d, int side, BrickPass ps,
+__global__ void __launch_bounds__(TH, (sizeof(C) == 8 && K <= 13 && TH <= 256) ? 2 : 1)   // FP32 tiles <= 2^13: 2 CTAs/SM
+    brick_pass_kernel(BrickDev d, int side, BrickPass ps,
                                                         const BrickGate *__restrict__ gates,
                                                         const RegPass *__restrict__ rps,
                                                         const RegGate *__restrict__ rgs,
