@@ -784,7 +784,8 @@ fp_status run_spiral(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
     const size_t scr = cfg.scratch_elems, mw = spiral_map_elems(fp32);
     const size_t per_pair = (size_t)2 * n_raw * 16 * sizeof(double2) + (size_t)n_merged * 16 * sizeof(double2) +
                             (size_t)nmaps * mw * celem + scr * celem;
-    const uint64_t cap = std::max<uint64_t>(1, std::min<uint64_t>(1 << 20, E->ws_budget / per_pair));
+    // sub-batches of at most 65535 pairs (the sampler and merge grids index pairs by grid.y)
+    const uint64_t cap = std::max<uint64_t>(1, std::min<uint64_t>(65535, E->ws_budget / per_pair));
     const double err_scale = FP_ERR_SAFETY * (fp32 ? 0x1.0p-24 : 0x1.0p-53) * std::sqrt((double)nmaps);
     const double cmac_pair = 4.0 * (double)nmaps * (double)((size_t)1 << sp.bits);
     SampleParams smp;

@@ -158,3 +158,15 @@ def test_spiral_window_kernels_match_map_by_map(fp, n, L, monkeypatch):
         assert rel_err(out[win][0], t64).max() <= TOL64, win
         assert np.abs(out[win][1] - t64).max() <= TOL32, win
         assert np.all(np.isfinite(out[win][2]))
+
+
+def test_spiral_batch_beyond_grid_limit(fp):
+    # more pairs of one depth than one launch's grid.y holds: the sub-batches of the
+    # spiral path give every pair the same trace as a small batch at the same index
+    e = fp.Ensemble(fp.HEA_PAULI, 4, 3, seed=12)
+    big, _, _ = e.trace_batch(0, 70000, fp.PREC_FP32_RAW)
+    for first in (0, 65530, 69990):
+        small, _, _ = e.trace_batch(first, 10, fp.PREC_FP32_RAW)
+        assert np.array_equal(big[first:first + 10], small)
+    assert np.all(np.abs(big) <= 16 + 1e-3)
+    e.close()
