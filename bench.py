@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workspace-gb", type=float, default=0.0,
+                    help="device workspace cap of the ensemble (0: the library default)")
     ap.add_argument("--no-target", action="store_true",
                     help="skip the GPU-seconds-to-1%% measurement, the bootstrap report and the large-T report")
     ap.add_argument("--no-cv", action="store_true", help="skip the control-variate report")
@@ -70,6 +72,8 @@ def parse():
         a.pairs = WORK["pairs"]
     if a.depth:
         WORK["depth_min"] = WORK["depth_max"] = a.depth
+    if a.workspace_gb:
+        WORK["workspace_gb"] = a.workspace_gb
     return a
 
 
@@ -77,8 +81,9 @@ def make_ensemble(fp, flags=0, stream=None):
     T = WORK.get("T", (0, 0, 1))
     if WORK["name"] == "local":
         flags |= fp.FLAG_SKIP_INFEASIBLE   # rare pairs beyond the 2^24 boundary are counted, not contracted
+    ws = int(WORK.get("workspace_gb", 0) * (1 << 30))
     return fp.Ensemble(WORK["kind"], WORK["n"], WORK["depth_min"], WORK["depth_max"], T[0], T[1], T[2],
-                       seed=WORK["seed"], flags=flags, stream=stream)
+                       seed=WORK["seed"], flags=flags, workspace_bytes=ws, stream=stream)
 
 
 def workload_config(args, world):

@@ -145,7 +145,7 @@ typedef struct {
                                  ratio exceeds this; <= 0: no cap */
     double fp32_tol;          /* FP_PREC_FP32: recontract in FP64 when the estimated
                                  absolute error of Tr exceeds this; <= 0: 1e-4 */
-    uint64_t workspace_bytes; /* device workspace cap; 0: library default */
+    uint64_t workspace_bytes; /* device workspace cap; 0: library default, min(32 GB, free/2) */
 } fp_ensemble_desc;
 
 /* Error estimate of one trace (the `err` output of fp_trace_batch): with

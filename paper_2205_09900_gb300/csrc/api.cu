@@ -1015,7 +1015,9 @@ fp_status fp_ensemble_create(const fp_ensemble_desc *desc, void *cuda_stream, fp
     E->n_groups = d.kind == FP_LOCAL ? (d.T_max - d.T_min) / d.T_step + 1 : d.depth_max - d.depth_min + 1;
     size_t freeb = 0, totb = 0;
     CK(cudaMemGetInfo(&freeb, &totb));
-    size_t cap = d.workspace_bytes ? (size_t)d.workspace_bytes : ((size_t)8 << 30);
+    // default: 32 GB (room for as many 2^24-amplitude generic-sweep slots as 16-CTA
+    // clusters can be resident), at most half the free memory
+    size_t cap = d.workspace_bytes ? (size_t)d.workspace_bytes : ((size_t)32 << 30);
     E->ws_budget = std::min(cap, freeb / 2);
     CK(cudaEventCreate(&E->ev0));
     CK(cudaEventCreate(&E->ev1));
