@@ -289,7 +289,7 @@ struct KTimer {
     KTimer(fp_ensemble *e, int c) : E(e), cls(c) {
         if (E->timing) cudaEventRecord(E->kev[2 * cls], E->st);
     }
-    cudaError_t stop(double work) {
+    cudaError_t stop(double work, int launches = 1) {
         if (!E->timing) return cudaSuccess;
         cudaError_t e = cudaEventRecord(E->kev[2 * cls + 1], E->st);
         if (e != cudaSuccess) return e;
@@ -297,7 +297,7 @@ struct KTimer {
         float ms = 0;
         if ((e = cudaEventElapsedTime(&ms, E->kev[2 * cls], E->kev[2 * cls + 1])) != cudaSuccess) return e;
         E->kst.ms[cls] += ms;
-        E->kst.launches[cls] += 1;
+        E->kst.launches[cls] += (uint64_t)launches;
         E->kst.work[cls] += work;
         return cudaSuccess;
     }
@@ -459,7 +459,7 @@ fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t
         {
             KTimer t(E, FP_K_SAMPLE);
             CK(launch_sample(sp, E->d_pairs.as<PairInfo>(), (int)nb, max_raw, E->d_raw.as<double2>(), E->st));
-            CK(t.stop((double)nb));
+            CK(t.stop((double)nb, sample_launch_count(E->raw_kind)));
         }
         {
             KTimer t(E, FP_K_MERGE);
@@ -685,7 +685,7 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
             {
                 KTimer t(E, FP_K_SAMPLE);
                 CK(launch_sample(sp, E->d_pairs.as<PairInfo>(), (int)nb, n_raw, E->d_raw.as<double2>(), E->st));
-                CK(t.stop((double)nb));
+                CK(t.stop((double)nb, sample_launch_count(E->raw_kind)));
             }
             {
                 KTimer t(E, FP_K_BRICK);
@@ -814,7 +814,7 @@ fp_status run_spiral(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
         {
             KTimer t(E, FP_K_SAMPLE);
             CK(launch_sample(smp, E->d_pairs.as<PairInfo>(), (int)nb, n_raw, E->d_raw.as<double2>(), E->st));
-            CK(t.stop((double)nb));
+            CK(t.stop((double)nb, sample_launch_count(E->raw_kind)));
         }
         {
             KTimer t(E, FP_K_MERGE);

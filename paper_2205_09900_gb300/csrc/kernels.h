@@ -16,6 +16,8 @@ struct SampleParams {
 };
 
 // Sampler: raw gates of U and V for every pair of the batch (FP64).
+// kernels one launch_sample issues (Haar gates: Gaussian draws, then the QR)
+int sample_launch_count(int raw_kind);
 cudaError_t launch_sample(const SampleParams &sp, const PairInfo *pairs, int npairs, int max_raw,
                           double2 *raw, cudaStream_t st);
 // Merged gates: ordered products of raw gates (FP64).

@@ -14,24 +14,27 @@ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -
 // Haar U(4): QR of a 4x4 complex Gaussian by Householder reflections, then
 // the columns of Q rotated so that R's diagonal is positive real (the Haar
 // sampler of the Methods section, "Sampling U(d^2)", realised as in Mezzadri
-// 2007).  Gaussian entries by Box-Muller from Philox words (keying in fp.h).
-__device__ void haar_u4(uint64_t seed, uint64_t pair, int w, int g, double2 *out) {
+// 2007).  Gaussian entries by Box-Muller from Philox words (keying in fp.h):
+// block j of the gate gives entries 2j and 2j+1 (row-major).
+__device__ __forceinline__ void gauss_pair(uint64_t seed, uint64_t pair, int w, int g, int j, double2 *out) {
+    U64x4 x = philox(seed, (uint64_t)j, (uint64_t)g, pair, (uint64_t)w);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint64_t xa = x.x[2 * h], xb = x.x[2 * h + 1];
+        double u1 = (double)((xa >> 11) + 1) * 0x1.0p-53;
+        double u2 = (double)(xb >> 11) * 0x1.0p-53;
+        double rad = sqrt(-2.0 * log(u1)) * 0.70710678118654752440;
+        double s, c;
+        sincospi(2.0 * u2, &s, &c);
+        out[2 * j + h] = make_double2(rad * c, rad * s);
+    }
+}
+
+// In place: the 16 Gaussian entries at g (row-major) become the Haar unitary.
+__device__ void haar_qr(double2 *g) {
     double2 A[4][4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        U64x4 x = philox(seed, (uint64_t)j, (uint64_t)g, pair, (uint64_t)w);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            uint64_t xa = x.x[2 * h], xb = x.x[2 * h + 1];
-            double u1 = (double)((xa >> 11) + 1) * 0x1.0p-53;
-            double u2 = (double)(xb >> 11) * 0x1.0p-53;
-            double rad = sqrt(-2.0 * log(u1)) * 0.70710678118654752440;
-            double s, c;
-            sincospi(2.0 * u2, &s, &c);
-            int k = 2 * j + h;
-            A[k / 4][k % 4] = make_double2(rad * c, rad * s);
-        }
-    }
+    for (int k = 0; k < 16; ++k) A[k / 4][k % 4] = g[k];
     double2 Q[4][4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -80,8 +83,28 @@ __device__ void haar_u4(uint64_t seed, uint64_t pair, int w, int g, double2 *out
         double a = hypot(A[c][c].x, A[c][c].y);
         double2 ph = a > 0 ? make_double2(A[c][c].x / a, A[c][c].y / a) : make_double2(1.0, 0.0);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) out[4 * r + c] = cmul(Q[r][c], ph);
+        for (int r = 0; r < 4; ++r) g[4 * r + c] = cmul(Q[r][c], ph);
     }
+}
+
+// Haar gates in two passes, so that the transcendental-heavy Gaussian draws
+// run at full occupancy: one thread per Philox block (8 per gate) writes the
+// gate's Gaussian entries into its raw record, then one thread per gate
+// factorises them in place.
+__global__ void gauss_kernel(SampleParams sp, const PairInfo *__restrict__ pairs, double2 *__restrict__ raw) {
+    const PairInfo pi = pairs[blockIdx.y];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int idx = t >> 3, j = t & 7;
+    if (idx >= 2 * pi.n_raw) return;
+    const int w = idx / pi.n_raw, g = idx % pi.n_raw;
+    gauss_pair(sp.seed, pi.pair, sp.self_pair ? 0 : w, g, j, raw + (pi.raw_off + idx) * 16);
+}
+
+__global__ void haar_qr_kernel(const PairInfo *__restrict__ pairs, double2 *__restrict__ raw) {
+    const PairInfo pi = pairs[blockIdx.y];
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 2 * pi.n_raw) return;
+    haar_qr(raw + (pi.raw_off + idx) * 16);
 }
 
 __global__ void sample_kernel(SampleParams sp, const PairInfo *__restrict__ pairs, double2 *__restrict__ raw) {
@@ -91,9 +114,7 @@ __global__ void sample_kernel(SampleParams sp, const PairInfo *__restrict__ pair
     int w = idx / pi.n_raw, g = idx % pi.n_raw;
     int wr = sp.self_pair ? 0 : w;
     double2 *out = raw + (pi.raw_off + idx) * 16;
-    if (sp.raw_kind == RAW_HAAR4) {
-        haar_u4(sp.seed, pi.pair, wr, g, out);
-    } else if (sp.raw_kind == RAW_DIAG4) {
+    if (sp.raw_kind == RAW_DIAG4) {
         U64x4 x = philox(sp.seed, 0, (uint64_t)g, pi.pair, (uint64_t)wr);
 #pragma unroll
         for (int k = 0; k < 16; ++k) out[k] = make_double2(0, 0);
@@ -226,9 +247,16 @@ __global__ void table_kernel(const PairInfo *__restrict__ pairs, const DevPlan *
 
 }  // namespace
 
+int sample_launch_count(int raw_kind) { return raw_kind == RAW_HAAR4 ? 2 : 1; }
+
 cudaError_t launch_sample(const SampleParams &sp, const PairInfo *pairs, int npairs, int max_raw,
                           double2 *raw, cudaStream_t st) {
     if (npairs <= 0) return cudaSuccess;
+    if (sp.raw_kind == RAW_HAAR4) {
+        gauss_kernel<<<dim3((16 * max_raw + 255) / 256, npairs), 256, 0, st>>>(sp, pairs, raw);
+        haar_qr_kernel<<<dim3((2 * max_raw + 127) / 128, npairs), 128, 0, st>>>(pairs, raw);
+        return cudaGetLastError();
+    }
     dim3 grid((2 * max_raw + 127) / 128, npairs);
     sample_kernel<<<grid, 128, 0, st>>>(sp, pairs, raw);
     return cudaGetLastError();
