@@ -521,6 +521,11 @@ def main():
         roof["traffic"] = 538.040832e6 + 476.1664e6
         roof["traffic_launch"] = ("brick_pass_kernel<float2,13,5,256>, l=10, one tile pass of 256 pairs; "
                                   "algorithmic bytes 2 x 256 x 2^18 x 8 = 1.0737e9")
+    if WORK["name"] == "hea_paper" and prec == fp.PREC_FP32:
+        # the dominant spiral kernel from one ncu capture: its DRAM traffic is the maps it reads
+        roof["traffic"] = 412.827392e6 + 4.156928e6
+        roof["traffic_launch"] = ("spiral_win_kernel<float2,5,2>, L=8, one launch of 2000 pairs; "
+                                  "algorithmic bytes 2000 x 797 maps x 256 B = 4.081e8")
 
     metric = {"brickwork": METRIC, "hea": "Tr(U^dagger V) contractions/s at n=50 (HEA, L=1..8)",
               "hea_paper": "Tr(U^dagger V) contractions/s at n=50 (paper HEA with CNOT walls, L=1..8)",
