@@ -337,27 +337,29 @@ fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config *cfg, fp_cv
 
 /* Allocation-free brickwork traces (the paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they need
- * traces -- code running while a stream is captured into a CUDA graph, where
- * an allocation is not stream-ordered; plugins inside a framework whose pool
- * already holds the device memory; loops that must not block in an
- * allocator).  It contracts pairs first..first+count-1 of the brickwork
- * ensemble (n qubits, every pair of depth l, Philox key `seed`) on the
- * brickwork shared-memory path, with all intermediate data in one scratch
- * array of FP_STATIC_SCRATCH_BYTES compiled into the library (held by every
- * GPU that loads it until the process exits).  It calls no cudaMalloc or
- * cudaFree and no allocating library routine.
+ * traces -- plugins inside a framework whose memory pool already holds the
+ * device memory, where a cudaMalloc can fail or fragment that pool; loops that
+ * must not block in an allocator).  It contracts pairs first..first+count-1 of
+ * the brickwork ensemble (n qubits, every pair of depth l, Philox key `seed`)
+ * on the brickwork shared-memory path, with all intermediate data in one
+ * scratch array of FP_STATIC_SCRATCH_BYTES compiled into the library (held by
+ * every GPU that loads it until the process exits).  It calls no cudaMalloc
+ * or cudaFree and no allocating library routine.
  *   l         2..7 (boundaries of at most 12 bits);
  *   prec      FP_PREC_FP64 or FP_PREC_FP32_RAW (no FP64 recontraction);
  *   tr        [2*count] doubles, kappa [count] doubles or NULL: device (or
- *             managed) memory owned by the caller;
- *   cuda_stream  the launches are ordered on it; the call does not wait for
+ *             managed) memory of the current device, owned by the caller;
+ *   cuda_stream  a stream of the current device (NULL: the default stream);
+ *             the launches are ordered on it and the call does not wait for
  *             them (results are in tr/kappa once the stream reaches that point).
  * A count whose scratch would exceed FP_STATIC_SCRATCH_BYTES returns
- * FP_ERR_ARG with the largest count that fits (fp_last_error).  The first
- * call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make it before any stream
- * capture.  All calls share the one array: calls that overlap on the GPU
- * (unordered streams) race; nothing in it needs to start at zero. */
+ * FP_ERR_ARG with the largest count that fits (fp_last_error); so do outputs
+ * or a stream of another device.  The first call on a device looks up the
+ * scratch array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array: calls that overlap on the GPU (unordered streams) race;
+ * nothing in it needs to start at zero (every kernel writes what it later
+ * reads). */
 #define FP_STATIC_SCRATCH_BYTES (32u << 20)
 fp_status fp_trace_brick_static(int32_t n, int32_t l, uint64_t seed, uint64_t first, uint64_t count,
                                 int32_t prec, double *tr, double *kappa, void *cuda_stream);
@@ -383,6 +385,26 @@ fp_status fp_trace_brick_static(int32_t n, int32_t l, uint64_t seed, uint64_t fi
 fp_status fp_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *A, int32_t lda, const void *Bt, int32_t ldb,
                        const float *bias, int32_t mode, float *Z, float *C, void *C_bf16, void *Ct_bf16,
                        void *cuda_stream);
+
+/* Measured arithmetic peaks of the current device (the paper has no
+ * counterpart: these are the denominators of the roofline fractions that the
+ * benchmark reports for the contraction kernels).  One microbenchmark keeps one
+ * pipe busy with independent work:
+ *   FP_PEAK_FFMA     scalar FP32 fused multiply-adds (fma.rn.f32),
+ *   FP_PEAK_FFMA2    packed FP32 pairs (fma.rn.f32x2, the contraction's arithmetic),
+ *   FP_PEAK_DFMA     FP64 fused multiply-adds,
+ *   FP_PEAK_TC_TF32  tcgen05.mma kind::tf32, 128x256 outputs, K = 8 per MMA,
+ *   FP_PEAK_TC_BF16  tcgen05.mma kind::f16 with BF16 operands, K = 16 per MMA;
+ * the tensor kernels keep both operands in shared memory and the accumulator
+ * in tensor memory (no global traffic).  iters scales the work (0: default,
+ * about 1-3 ms).  One untimed launch precedes the timed one.  Output (host):
+ *   out[0] TFLOP/s (2 flops per multiply-add), out[1] kernel milliseconds,
+ *   out[2] SM clock in MHz during the run (clock64 over the global timer, CTA 0),
+ *   out[3] flops per clock per SM, out[4] SMs.
+ * Ordered on cuda_stream; waits for the result.  FP_ERR_TIMEOUT if the
+ * tensor-core completion wait (bounded at 2 s) ran out. */
+enum { FP_PEAK_FFMA = 0, FP_PEAK_FFMA2 = 1, FP_PEAK_DFMA = 2, FP_PEAK_TC_TF32 = 3, FP_PEAK_TC_BF16 = 4 };
+fp_status fp_measure_peak(int32_t which, int32_t iters, void *cuda_stream, double *out);
 
 /* Thread-local message of the last failing call ("" if none). */
 const char *fp_last_error(void);

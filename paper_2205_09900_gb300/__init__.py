@@ -30,7 +30,8 @@ STATUS = {0: "FP_OK", -1: "FP_ERR_ARG", -2: "FP_ERR_CUDA", -3: "FP_ERR_OOM", -4:
 EXPORTED = ["fp_ensemble_create", "fp_ensemble_destroy", "fp_groups", "fp_pair_groups", "fp_export_gates",
             "fp_trace_batch", "fp_reduce_moments", "fp_frame_potential", "fp_kernel_stats_get",
             "fp_trace_brick_static", "fp_cv_frame_potential", "fp_gemm_bf16", "fp_bootstrap", "fp_epsilon_max",
-            "fp_design_layers", "fp_exact_brickwork_fk", "fp_exact_brickwork_fkq", "fp_last_error"]
+            "fp_design_layers", "fp_exact_brickwork_fk", "fp_exact_brickwork_fkq", "fp_measure_peak",
+            "fp_last_error"]
 
 
 class FpError(RuntimeError):
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH):
     L.fp_design_layers.argtypes = [i32, vp, vp, i32, i32, i32, f64, f64, P(f64), P(f64), P(f64)]
     L.fp_exact_brickwork_fk.argtypes = [i32, i32, i32, vp, P(f64)]
     L.fp_exact_brickwork_fkq.argtypes = [i32, i32, i32, i32, vp, P(f64)]
+    L.fp_measure_peak.argtypes = [i32, i32, vp, vp]
     L.fp_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name not in ("fp_ensemble_destroy", "fp_last_error"):
@@ -164,6 +166,20 @@ def exact_brickwork_fk(n, l, k, stream=None, q=2):
     else:
         _check(load().fp_exact_brickwork_fkq(n, l, k, q, st, ctypes.byref(out)))
     return out.value
+
+
+PEAK_FFMA, PEAK_FFMA2, PEAK_DFMA, PEAK_TC_TF32, PEAK_TC_BF16 = 0, 1, 2, 3, 4
+
+
+def measure_peak(which, iters=0, stream=None):
+    """Measured peak of one arithmetic pipe (fp_measure_peak): dict with tflops, ms,
+    sm_mhz (clock during the run), flops_per_clk_sm and sms."""
+    import numpy as np
+    out = np.zeros(5)
+    st = None if stream is None else ctypes.c_void_p(stream)
+    _check(load().fp_measure_peak(which, iters, st, _ptr(out)))
+    return {"tflops": float(out[0]), "ms": float(out[1]), "sm_mhz": float(out[2]),
+            "flops_per_clk_sm": float(out[3]), "sms": int(out[4])}
 
 
 def epsilon_max_log10(F, k, n, q=2):

@@ -96,8 +96,9 @@ struct GraphKey {
 
 struct BrickCache {
     BrickHostPlan hp;
-    DBuf d_gates, d_rpasses, d_rgates;
+    DBuf d_gates, d_rpasses, d_rgates, d_tcwins;
     BrickDevPlan dp;
+    size_t extra_per_pair = 0;   // tensor-core window matrices (bytes per pair, after the boundaries)
 };
 
 struct SpiralCache {        // one depth of the paper's HEA on the spiral sweep
@@ -138,6 +139,7 @@ struct fp_ensemble {
     std::map<int, std::unique_ptr<SpiralCache>> spiral_plans;
     DBuf d_spiral_scratch;
     DBuf d_maps, d_states;
+    DBuf d_flag;               // device error flag of kernels with bounded waits (zero when clear)
     std::string gpu_name;
     // CUDA graphs of the brickwork sub-batch pipeline
     cudaStream_t gst = nullptr;
@@ -494,6 +496,17 @@ fp_status run_generic(fp_ensemble *E, uint64_t first, const std::vector<uint64_t
 }
 
 // Build and upload one brickwork plan variant.
+// The device error flag of kernels with bounded waits: a raised flag is
+// reported as FP_ERR_TIMEOUT and cleared, so that the ensemble stays usable.
+fp_status check_flag(fp_ensemble *E) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, E->d_flag.p, sizeof h, cudaMemcpyDeviceToHost, E->st));
+    CK(cudaStreamSynchronize(E->st));
+    if (!h) return FP_OK;
+    CK(cudaMemsetAsync(E->d_flag.p, 0, sizeof h, E->st));
+    return fail(FP_ERR_TIMEOUT, "a bounded device wait ran out in the tensor-core tile pass (results discarded)");
+}
+
 fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int TH, int persist,
                            std::unique_ptr<BrickCache> &out) {
     auto bc = std::make_unique<BrickCache>();
@@ -502,6 +515,19 @@ fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int T
     for (const auto &ps : bc->hp.passes) {
         if (ps.n_gates > 255) return fail(FP_ERR_ARG, "tile pass with %d gates exceeds 255", ps.n_gates);
         if (ps.n_rp > 160) return fail(FP_ERR_ARG, "tile pass with %d register passes exceeds 160", ps.n_rp);
+    }
+    if (persist == 2) {   // tensor-core windows: FP32, 12-bit tiles, 5-bit windows only
+        if (!fp32 || !tc_plan_ok(bc->hp.dev, bc->hp.passes.data(), bc->hp.rpasses.data()))
+            return fail(FP_ERR_ARG, "the tensor-core tile pass needs FP32, %d-bit tiles, %d-bit windows and l >= 8",
+                        kTcTile, kMaxWin);
+        CK(upload(bc->d_tcwins, make_tc_windows(bc->hp), E->st));
+        bc->dp.tcwins = bc->d_tcwins.as<TcWin>();
+        bc->extra_per_pair = tc_wmat_bytes_per_pair(bc->hp.dev, bc->hp.passes.data());
+        if (!E->d_flag.p) {
+            CK(E->d_flag.reserve(16));
+            CK(cudaMemsetAsync(E->d_flag.p, 0, 16, E->st));
+        }
+        bc->dp.err_flag = E->d_flag.as<int>();
     }
     CK(upload(bc->d_gates, bc->hp.gates, E->st));
     CK(upload(bc->d_rpasses, bc->hp.rpasses, E->st));
@@ -533,6 +559,8 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
                                                        {13, 5, 256, 1}, {12, 4, 256, 0}, {12, 5, 128, 0}}
                                    : std::vector<Cand>{{13, 3, 512, 0}, {13, 4, 256, 0}};
     if (((size_t)1 << N) * (fp32 ? sizeof(float2) : sizeof(double2)) <= (size_t)200 * 1024) cands.push_back({99, 0, 0, 0});
+    // P = 2: tensor-core windows (TF32 x 3 tcgen05 MMAs), boundaries of more than two 12-bit tiles
+    if (fp32 && N >= kTcTile + 2) cands.push_back({kTcTile, kMaxWin, 256, 2});
     const int kmin = 10;   // boundaries up to 2^10: shared-memory sweep, nothing to tune
     char ckey[256];
     snprintf(ckey, sizeof ckey, "%s n=%d l=%d %s", E->gpu_name.c_str(), d.n, l, fp32 ? "fp32" : "fp64");
@@ -582,6 +610,7 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
             if (c.K != 99 && c.K > N) continue;   // tiles larger than the boundary
             fp_status s = make_brick_cache(E, l, fp32, c.K, c.R, c.TH, c.P, bc);
             if (s != FP_OK) continue;
+            if (bc->extra_per_pair) CK(E->d_states.reserve(nt * (2 * ((size_t)1 << N) * celem + bc->extra_per_pair)));
             float ms_sum = 0;
             for (int rep = 0; rep < 2; ++rep) {
                 CK(cudaEventRecord(E->ev0, E->st));
@@ -598,6 +627,10 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
                 float ms = 0;
                 CK(cudaEventElapsedTime(&ms, E->ev0, E->ev1));
                 if (rep == 1) ms_sum += ms;     // first repetition warms caches and code
+                if (bc->dp.err_flag) {
+                    fp_status fs = check_flag(E);
+                    if (fs != FP_OK) return fs;
+                }
             }
             if (ms_sum < best_ms) { best_ms = ms_sum; bestK = c.K; bestR = c.R; bestT = c.TH; bestP = c.P; }
         }
@@ -639,7 +672,7 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
     const size_t per_map = (size_t)maps_per_pair(bd) * 16 * celem;
     bool both = false;
     if (bd.tile_bits == 0) brick_smem_bytes(bd, fp32, &both);
-    const size_t per_state = bd.tile_bits ? 2 * S * celem : (both ? 0 : S * celem);
+    const size_t per_state = bd.tile_bits ? 2 * S * celem + it->second->extra_per_pair : (both ? 0 : S * celem);
     const size_t per_pair = per_raw + per_map + per_state;
     uint64_t cap = std::max<uint64_t>(1, std::min<uint64_t>(65535, E->ws_budget / per_pair));
     // flop count of the sweep (complex multiply-adds): 4 per amplitude per gate
@@ -725,6 +758,10 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, E->ev0, E->ev1));
         if (gpu_ms) *gpu_ms += ms;
+        if (it->second->dp.err_flag) {
+            fp_status fs = check_flag(E);
+            if (fs != FP_OK) return fs;
+        }
         E->kst.pairs += nb;
         done += nb;
     }

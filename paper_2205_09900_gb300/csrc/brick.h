@@ -69,14 +69,36 @@ struct BrickDev {       // uniform over a sub-batch (one depth)
     int32_t tile_bits;        // K of the tiled path (0: whole state in one CTA)
 };
 
+// Tensor-core form of a register window (tile passes of kTcTile bits,
+// windows of kMaxWin bits): the window's gates fused into one dense 32 x 32
+// complex matrix W, applied to the tile viewed as a [128 rows x 32] complex
+// matrix (rows: the other tile bits) by tcgen05 MMAs.  cb[b] is the byte
+// offset contributed by tile-local bit b to an element's address in the MMA
+// operand layout of this window (K-major, 128-byte swizzle; the layout is
+// linear over GF(2), so an address is the XOR of its bits' contributions).
+constexpr int kTcTile = 12;
+constexpr int kTcRows = kTcTile - kMaxWin;
+struct TcWin {
+    uint8_t win[kMaxWin];     // tile-local bit of window position k (ring order)
+    uint8_t row[kTcRows];     // tile-local bits of the row index, ascending
+    uint32_t cb[kTcTile];
+};
+// A-operand byte address of element (row r, window index j): complex j
+// occupies K columns 2j (re), 2j+1 (im); K splits into two 128-byte regions of
+// 128 rows; 16-byte chunk c of row r sits at chunk c ^ (r % 8).
+FP_HD uint32_t tc_addr(uint32_t r, uint32_t j) {
+    return (j >> 4) * 16384u + r * 128u + ((((j >> 1) & 7u) ^ (r & 7u)) << 4) + (j & 1u) * 8u;
+}
 // Device copies of a plan's schedule (gates and register passes).
 struct BrickDevPlan {
     const BrickGate *gates;
     const RegPass *rpasses;
     const RegGate *rgates;
+    const TcWin *tcwins;    // persist == 2: one per register pass
+    int *err_flag;          // persist == 2: raised by a kernel whose bounded wait ran out
     int win_bits;
     int threads;
-    int persist;        // 1: persistent double-buffered tile passes
+    int persist;        // 1: persistent double-buffered tile passes; 2: tensor-core windows
 };
 
 struct BrickHostPlan {
@@ -112,5 +134,8 @@ FP_HD int maps_per_pair(const BrickDev &d) { return (d.n_layers[0] + d.n_layers[
 // rotations without a ladder.
 
 BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win_bits, int kind = 0);
+// Tensor-core window tables (one per register pass) of a plan with kTcTile-bit
+// tiles and kMaxWin-bit windows.
+std::vector<TcWin> make_tc_windows(const BrickHostPlan &P);
 
 }  // namespace fpk

@@ -168,4 +168,26 @@ BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win
     return P;
 }
 
+std::vector<TcWin> make_tc_windows(const BrickHostPlan &P) {
+    std::vector<TcWin> out(P.rpasses.size());
+    for (size_t w = 0; w < P.rpasses.size(); ++w) {
+        const RegPass &rp = P.rpasses[w];
+        TcWin &t = out[w];
+        std::memset(&t, 0, sizeof t);
+        int in_win[32] = {0};
+        for (int k = 0; k < kMaxWin; ++k) {
+            t.win[k] = rp.win[k];
+            in_win[rp.win[k]] = 1;
+            t.cb[rp.win[k]] = tc_addr(0, 1u << k);
+        }
+        for (int b = 0, r = 0; b < kTcTile; ++b)
+            if (!in_win[b]) {
+                t.row[r] = (uint8_t)b;
+                t.cb[b] = tc_addr(1u << r, 0);
+                ++r;
+            }
+    }
+    return out;
+}
+
 }  // namespace fpk

@@ -59,6 +59,14 @@ cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const Bric
                          bool fp32, double err_scale, double *tr, double *kappa, double *err, cudaStream_t st,
                          int *launches);
 size_t brick_smem_bytes(const BrickDev &d, bool fp32, bool *both);
+// Tensor-core tile passes (kernels_brick_tc.cu): whether a plan qualifies
+// (kTcTile-bit tiles, kMaxWin-bit windows, boundary of more than one tile
+// pair), the window-matrix workspace per pair (placed after the boundaries in
+// `states`), and the launches of both sides.
+bool tc_plan_ok(const BrickDev &d, const BrickPass *hpasses, const RegPass *rps);
+size_t tc_wmat_bytes_per_pair(const BrickDev &d, const BrickPass *hpasses);
+cudaError_t run_passes_tc(const BrickDev &d, const BrickPass *hpasses, const BrickDevPlan &dp, int npairs,
+                          const float2 *maps, float2 *states, float *wm, int *err, cudaStream_t st);
 // Spiral sweep (the paper's HEA): maps from merged 1-qubit operators
 // (spiral_map_elems(fp32) elements of C per map), then the sweep.  The
 // configuration of a state of 2^bits amplitudes: R = 0 applies one map per

@@ -1,0 +1,421 @@
+// kernels_brick_tc.cu -- brickwork tile passes on the tensor cores (tcgen05).
+//
+// The FFMA tile pass applies the gates of each register window (5 ring bits
+// of a 12-bit tile) one 4x4 map at a time.  Here the window's gates are first
+// multiplied into one dense 32 x 32 complex matrix W per (pair, window)
+// (tc_wmat_kernel, FP64 products of the FP32 maps), and the tile, viewed as a
+// [128 rows x 32] complex matrix whose rows are the 7 other tile bits, is
+// multiplied by W^T on the tensor cores: complex numbers as real pairs (K
+// columns 2j, 2j+1 hold re, im of window index j; W as the real 64 x 64 block
+// matrix [[Re, -Im], [Im, Re]]), TF32 operands split into hi + lo parts
+// (hi = rna(x), lo = rna(x - hi)) and three MMAs per K step (hi.lo, lo.hi,
+// hi.hi), accumulated in FP32 in tensor memory (tcgen05.mma kind::tf32,
+// M = 128, N = 64, K = 8).
+//
+// One CTA takes two tiles of one pair (X and Y) through every window of the
+// pass, alternating: while the tensor cores multiply one tile, the 256
+// threads read the other tile's result out of tensor memory (tcgen05.ld),
+// split it, and store it into shared memory in the next window's operand
+// layout (K-major, 128-byte swizzle; every element's address is the XOR of
+// its bits' contributions, the TcWin tables).  Window matrices stream in by
+// bulk copies (cp.async.bulk) into two buffers, one window ahead.  The first
+// window's operands are loaded from the boundary in global memory, the last
+// window's result is written back to it.
+//
+// Every mbarrier wait is bounded by the global timer (1 s); on a timeout the
+// CTA raises the error flag, stops issuing work, drains the MMAs and bulk
+// copies it has issued (bounded again), frees its tensor memory and returns;
+// later launches that find the flag raised return at once.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "brick.h"
+#include "kernels.h"
+
+namespace fpk {
+namespace {
+
+constexpr uint64_t kTcWaitNs = 1000000000ull;
+constexpr int kTcThreads = 256;
+constexpr int kMaxTcWins = 48;
+constexpr uint32_t kAOp = 32768;                 // bytes of one A operand (hi or lo) of one tile
+constexpr uint32_t kWMat = 32768;                // bytes of one window matrix (hi + lo)
+constexpr uint32_t kWFloats = kWMat / 4;
+constexpr size_t kTcSmem = 4 * (size_t)kAOp + 2 * (size_t)kWMat + 1024;
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+    const uint64_t t0 = gtimer();
+    for (;;) {
+        uint32_t d;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(d)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (d) return true;
+        if (gtimer() - t0 > kTcWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// ---------------------------------------------------------------------------
+// Window matrices: W = G_last ... G_first of the window's gates (4x4 maps on
+// window bits (k, k+1)), column j built by thread j in FP64, stored as the B
+// operand of the MMA: rows n = 2o (re, -im) and 2o + 1 (im, re) of output o,
+// K columns 2j, 2j + 1, K-major with the 128-byte swizzle in two regions of
+// 64 rows x 128 bytes; hi part then lo part.
+template <int k>
+__device__ __forceinline__ void wapply(double2 (&v)[32], const double2 *__restrict__ T) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        if (i & (3 << k)) continue;
+        const double2 x0 = v[i], x1 = v[i | (1 << k)], x2 = v[i | (2 << k)], x3 = v[i | (3 << k)];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const double2 t0 = T[4 * o], t1 = T[4 * o + 1], t2 = T[4 * o + 2], t3 = T[4 * o + 3];
+            double2 a;
+            a.x = t0.x * x0.x - t0.y * x0.y + t1.x * x1.x - t1.y * x1.y + t2.x * x2.x - t2.y * x2.y + t3.x * x3.x -
+                  t3.y * x3.y;
+            a.y = t0.x * x0.y + t0.y * x0.x + t1.x * x1.y + t1.y * x1.x + t2.x * x2.y + t2.y * x2.x + t3.x * x3.y +
+                  t3.y * x3.x;
+            v[i | (o << k)] = a;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t wb_addr(uint32_t n, uint32_t kc) {   // B operand: row n, K column kc
+    return (kc >> 5) * 8192u + n * 128u + ((((kc >> 2) & 7u) ^ (n & 7u)) << 4) + (kc & 3u) * 4u;
+}
+
+__global__ void __launch_bounds__(32) tc_wmat_kernel(BrickDev d, int side, BrickPass ps,
+                                                     const BrickGate *__restrict__ gates,
+                                                     const RegPass *__restrict__ rps, const RegGate *__restrict__ rgs,
+                                                     const float2 *__restrict__ maps, float *__restrict__ wm) {
+    __shared__ double2 T[kMaxTcWins][16];
+    const RegPass rp = rps[ps.rp_off + blockIdx.x];
+    const int ng = rp.n_gates < kMaxTcWins ? rp.n_gates : kMaxTcWins;
+    const float2 *mp = maps + (size_t)blockIdx.y * maps_per_pair(d) * 16;
+    for (int i = threadIdx.x; i < ng * 16; i += 32) {
+        const RegGate rg = rgs[rp.gate_off + i / 16];
+        const BrickGate gg = gates[ps.gate_off + rg.slot];
+        const float2 v = mp[(size_t)map_index(d, side, gg.layer, gg.j) * 16 + (i % 16)];
+        T[i / 16][i % 16] = make_double2(v.x, v.y);
+    }
+    __syncwarp();
+    const int j = threadIdx.x;
+    double2 v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    for (int g = 0; g < ng; ++g) {
+        switch (rgs[rp.gate_off + g].type) {
+            case 0: wapply<0>(v, T[g]); break;
+            case 1: wapply<1>(v, T[g]); break;
+            case 2: wapply<2>(v, T[g]); break;
+            default: wapply<3>(v, T[g]); break;
+        }
+    }
+    unsigned char *out = (unsigned char *)(wm + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kWFloats);
+#pragma unroll
+    for (int o = 0; o < 32; ++o) {
+        const float re = (float)v[o].x, im = (float)v[o].y;
+        const float rh = tf32_rna(re), ih = tf32_rna(im);
+        const float rl = tf32_rna((float)(v[o].x - (double)rh)), il = tf32_rna((float)(v[o].y - (double)ih));
+        const uint32_t a0 = wb_addr(2 * o, 2 * j), a1 = wb_addr(2 * o + 1, 2 * j);
+        *(float2 *)(out + a0) = make_float2(rh, -ih);
+        *(float2 *)(out + a1) = make_float2(ih, rh);
+        *(float2 *)(out + 16384 + a0) = make_float2(rl, -il);
+        *(float2 *)(out + 16384 + a1) = make_float2(il, rl);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The tile pass.
+__device__ __forceinline__ uint32_t tile_base_of(uint32_t t, uint32_t smask, int N) {
+    uint32_t base = 0;
+    for (int b = 0; b < N; ++b)
+        if (!(smask & (1u << b))) { base |= (t & 1u) << b; t >>= 1; }
+    return base;
+}
+
+__device__ __forceinline__ void st_hilo(unsigned char *A, uint32_t a, float x, float y) {
+    const float xh = tf32_rna(x), yh = tf32_rna(y);
+    const float xl = tf32_rna(x - xh), yl = tf32_rna(y - yh);
+    *(float2 *)(A + a) = make_float2(xh, yh);
+    *(float2 *)(A + kAOp + a) = make_float2(xl, yl);
+}
+
+// 3 x 8 MMAs (hi.lo, lo.hi, hi.hi) of one tile: D[128 x 64] (+)= A[128 x 64] . B[64 x 64]^T
+__device__ __forceinline__ void issue_tile_mmas(uint32_t dtm, uint32_t sA, uint32_t sW) {
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+    const uint32_t pa[3] = {sA, sA + kAOp, sA}, pb[3] = {sW + 16384, sW, sW};
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const uint64_t ad = desc_sw128(pa[p] + (s >> 2) * 16384 + (s & 3) * 32);
+            const uint64_t bd = desc_sw128(pb[p] + (s >> 2) * 8192 + (s & 3) * 32);
+            const uint32_t acc = (p > 0 || s > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n\t}" ::"r"(dtm),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+}
+
+__device__ __forceinline__ void commit_to(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Read this thread's 16 complex results of one tile out of tensor memory and
+// scatter them: into the A operands of the next window (next != nullptr:
+// address = XOR of next[b] over the element's tile bits) or to the boundary
+// in global memory (gdst, contributions gcb: physical index bits).
+__device__ __forceinline__ void drain_tile(uint32_t tm, const TcWin &cw, const uint32_t *__restrict__ cbn,
+                                           unsigned char *A, float2 *gdst) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t v[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(tm + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2))));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const uint32_t r = 32u * (warp & 3) + lane;
+    uint32_t base = 0;
+#pragma unroll
+    for (int t = 0; t < kTcRows; ++t)
+        if ((r >> t) & 1u) base ^= cbn[cw.row[t]];
+    if (warp >> 2) base ^= cbn[cw.win[4]];
+    const uint32_t c0 = cbn[cw.win[0]], c1 = cbn[cw.win[1]], c2 = cbn[cw.win[2]], c3 = cbn[cw.win[3]];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const uint32_t a = base ^ ((u & 1) ? c0 : 0u) ^ ((u & 2) ? c1 : 0u) ^ ((u & 4) ? c2 : 0u) ^ ((u & 8) ? c3 : 0u);
+        const float x = __uint_as_float(v[2 * u]), y = __uint_as_float(v[2 * u + 1]);
+        if (A) st_hilo(A, a, x, y);
+        else gdst[a] = make_float2(x, y);
+    }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    brick_tc_pass_kernel(BrickDev d, int side, BrickPass ps, const TcWin *__restrict__ wins,
+                         const float *__restrict__ wm, float2 *__restrict__ states, int *err) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t wbar[2], mbar[2], fbar;
+    __shared__ uint32_t taddr_sh;
+    __shared__ int abort_sh;
+    __shared__ int pos[32];
+    __shared__ uint32_t lut_lo[128], lut_hi[1 << (kTcTile - 7)], alo[128], ahi[1 << (kTcTile - 7)], gcb[kTcTile];
+    __shared__ TcWin sw[kMaxTcWins];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x;
+    const int nw = ps.n_rp;
+    const int N = d.N;
+    const uint32_t S = 1u << N;
+    if (tid == 0) abort_sh = *(volatile const int *)err;   // an earlier launch timed out
+    if (tid == 0) {
+        int k = 0;
+        for (int b = 0; b < N; ++b)
+            if (ps.smask & (1u << b)) pos[k++] = b;
+    }
+    for (int i = tid; i < nw; i += kTcThreads) sw[i] = wins[ps.rp_off + i];
+    __syncthreads();
+    if (abort_sh) return;
+    for (int i = tid; i < 128; i += kTcThreads) {
+        uint32_t o = 0, a = 0;
+        for (int k = 0; k < 7; ++k)
+            if ((i >> k) & 1) { o |= 1u << pos[k]; a ^= sw[0].cb[k]; }
+        lut_lo[i] = o;
+        alo[i] = a;
+    }
+    if (tid < (1 << (kTcTile - 7))) {
+        uint32_t o = 0, a = 0;
+        for (int k = 0; k < kTcTile - 7; ++k)
+            if ((tid >> k) & 1) { o |= 1u << pos[7 + k]; a ^= sw[0].cb[7 + k]; }
+        lut_hi[tid] = o;
+        ahi[tid] = a;
+    }
+    if (tid < kTcTile) gcb[tid] = 1u << pos[tid];
+    if (tid < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&taddr_sh)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 32) {
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&wbar[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[b])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t taddr = taddr_sh;
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t sW = sbase + 4 * kAOp;
+    const float *wp = wm + (size_t)blockIdx.y * nw * kWFloats;
+    // window matrices 0 and 1 (thread 0 also issues every MMA; counts kept for the drain)
+    int tma_issued[2] = {0, 0}, tma_waited[2] = {0, 0};
+    if (tid == 0)
+        for (int b = 0; b < 2 && b < nw; ++b) {
+            bulk_load(sW + b * kWMat, wp + (size_t)b * kWFloats, kWMat, &wbar[b]);
+            ++tma_issued[b];
+        }
+    // both tiles: boundary -> A operands of window 0
+    float2 *st = states + ((size_t)blockIdx.y * 2 + side) * S;
+    const uint32_t gb[2] = {tile_base_of(2 * blockIdx.x, ps.smask, N), tile_base_of(2 * blockIdx.x + 1, ps.smask, N)};
+#pragma unroll
+    for (int tt = 0; tt < 2; ++tt) {
+        unsigned char *A = smem + tt * 2 * kAOp;
+        const float2 *src = st + gb[tt];
+#pragma unroll 4
+        for (int m = 0; m < (1 << kTcTile) / kTcThreads; ++m) {
+            const uint32_t i = tid + (uint32_t)m * kTcThreads;
+            const float2 x = src[lut_lo[i & 127] | lut_hi[i >> 7]];
+            st_hilo(A, alo[i & 127] ^ ahi[i >> 7], x.x, x.y);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    bool issued_any = false;
+    for (int w = 0; w < nw; ++w) {
+        // MMAs of tile X, window w
+        if (tid == 0) {
+            if (!mbar_wait(smem_u32(&wbar[w & 1]), (uint32_t)(w >> 1) & 1u)) {
+                abort_sh = 1;
+            } else {
+                ++tma_waited[w & 1];
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                issue_tile_mmas(taddr, sbase, sW + (w & 1) * kWMat);
+                commit_to(&mbar[0]);
+                issued_any = true;
+            }
+        }
+        // tile Y: result of window w-1 -> operands of window w
+        if (w > 0) {
+            if (!mbar_wait(smem_u32(&mbar[1]), (uint32_t)(w - 1) & 1u)) abort_sh = 1;
+            else {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                drain_tile(taddr + 64, sw[w - 1], sw[w].cb, smem + 2 * kAOp, nullptr);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (abort_sh) break;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // window buffer (w-1) & 1 is free (X and Y of window w-1 are done): next matrix in
+            if (w > 0 && w + 1 < nw) {
+                bulk_load(sW + ((w + 1) & 1) * kWMat, wp + (size_t)(w + 1) * kWFloats, kWMat, &wbar[(w + 1) & 1]);
+                ++tma_issued[(w + 1) & 1];
+            }
+            issue_tile_mmas(taddr + 64, sbase + 2 * kAOp, sW + (w & 1) * kWMat);
+            commit_to(&mbar[1]);
+        }
+        // tile X: result of window w -> operands of window w+1, or the boundary
+        if (!mbar_wait(smem_u32(&mbar[0]), (uint32_t)w & 1u)) abort_sh = 1;
+        else {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (w + 1 < nw) drain_tile(taddr, sw[w], sw[w + 1].cb, smem, nullptr);
+            else drain_tile(taddr, sw[w], gcb, nullptr, st + gb[0]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (abort_sh) break;
+    }
+    if (!abort_sh) {
+        // tile Y: last window's result -> the boundary
+        if (!mbar_wait(smem_u32(&mbar[1]), (uint32_t)(nw - 1) & 1u)) abort_sh = 1;
+        else {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            drain_tile(taddr + 64, sw[nw - 1], gcb, nullptr, st + gb[1]);
+        }
+    }
+    __syncthreads();
+    if (abort_sh) {
+        // drain what thread 0 issued: every MMA (one more commit tracks them all)
+        // and bulk copies not yet waited for, then report
+        if (tid == 0) {
+            if (issued_any) {
+                commit_to(&fbar);
+                mbar_wait(smem_u32(&fbar), 0u);
+            }
+            for (int b = 0; b < 2; ++b)
+                if (tma_issued[b] > tma_waited[b]) mbar_wait(smem_u32(&wbar[b]), (uint32_t)(tma_issued[b] - 1) & 1u);
+            atomicExch(err, 1);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(taddr));
+}
+
+}  // namespace
+
+size_t tc_wmat_bytes_per_pair(const BrickDev &d, const BrickPass *hpasses) {
+    int mx = 0;
+    for (int i = 0; i < d.n_passes[0] + d.n_passes[1]; ++i) mx = hpasses[i].n_rp > mx ? hpasses[i].n_rp : mx;
+    return (size_t)mx * kWMat;
+}
+
+bool tc_plan_ok(const BrickDev &d, const BrickPass *hpasses, const RegPass *rps) {
+    if (d.tile_bits != kTcTile || d.N < kTcTile + 1) return false;
+    for (int i = 0; i < d.n_passes[0] + d.n_passes[1]; ++i) {
+        const BrickPass &p = hpasses[i];
+        if (p.n_rp < 1 || p.n_rp > kMaxTcWins) return false;
+        for (int w = 0; w < p.n_rp; ++w)
+            if (rps[p.rp_off + w].r != kMaxWin || rps[p.rp_off + w].n_gates > kMaxTcWins) return false;
+    }
+    return true;
+}
+
+cudaError_t run_passes_tc(const BrickDev &d, const BrickPass *hpasses, const BrickDevPlan &dp, int npairs,
+                          const float2 *maps, float2 *states, float *wm, int *err, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(brick_tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e != cudaSuccess) return e;
+    for (int side = 0; side < 2; ++side)
+        for (int p = 0; p < d.n_passes[side]; ++p) {
+            const BrickPass &ps = hpasses[d.pass_off[side] + p];
+            tc_wmat_kernel<<<dim3(ps.n_rp, npairs), 32, 0, st>>>(d, side, ps, dp.gates, dp.rpasses, dp.rgates, maps, wm);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            brick_tc_pass_kernel<<<dim3(1u << (d.N - kTcTile - 1), npairs), kTcThreads, kTcSmem, st>>>(
+                d, side, ps, dp.tcwins, wm, states, err);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+}  // namespace fpk

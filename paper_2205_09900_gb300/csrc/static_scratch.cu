@@ -1,14 +1,13 @@
 // static_scratch.cu -- brickwork traces without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they want
-// traces: code that runs while a stream is being captured into a CUDA graph
-// (an allocation there is not stream-ordered and breaks the capture), plugins
-// hosted by a framework whose memory pool already owns the device memory,
-// and latency-bound loops that must never block inside the allocator.  For
-// them fp_trace_brick_static runs the brickwork path (sampler, maps,
-// shared-memory sweep and meet) with every intermediate buffer carved out of
-// one fixed array compiled into this library.  The array is FP_STATIC_SCRATCH_BYTES
-// large and every GPU that loads the library holds it until the process exits.
+// traces: plugins hosted by a framework whose memory pool already owns the
+// device memory (a cudaMalloc there can fail or fragment the pool), and
+// latency-bound loops that must never block inside the allocator.  For them
+// fp_trace_brick_static runs the brickwork path (sampler, maps, shared-memory
+// sweep and meet) with every intermediate buffer carved out of one fixed array
+// compiled into this library.  The array is FP_STATIC_SCRATCH_BYTES large and
+// every GPU that loads the library holds it until the process exits.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -63,7 +62,12 @@ extern "C" fp_status fp_trace_brick_static(int32_t n, int32_t l, uint64_t seed, 
         return sfail(FP_ERR_ARG, "precision must be FP_PREC_FP64 or FP_PREC_FP32_RAW");
     if (!tr) return sfail(FP_ERR_ARG, "tr is NULL");
     if (count == 0) return FP_OK;
-    // outputs must be device-accessible: nothing is staged through host memory
+    // the current device: the scratch address and every launch belong to it
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return sfail(FP_ERR_CUDA, "cudaGetDevice failed");
+    // outputs must be reachable from this device: nothing is staged through
+    // host memory, and memory of another GPU would be an illegal address here
     for (const void *p : {(const void *)tr, (const void *)kappa}) {
         if (!p) continue;
         cudaPointerAttributes a;
@@ -71,20 +75,28 @@ extern "C" fp_status fp_trace_brick_static(int32_t n, int32_t l, uint64_t seed, 
             cudaGetLastError();
             return sfail(FP_ERR_ARG, "tr and kappa must be device (or managed) memory");
         }
+        if (a.type == cudaMemoryTypeDevice && a.device != dev) {
+            snprintf(msg, sizeof msg, "tr and kappa must be memory of the current device %d (got device %d)", dev,
+                     a.device);
+            return sfail(FP_ERR_ARG, msg);
+        }
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (st) {
+        int sdev = -1;
+        if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+            cudaGetLastError();
+            return sfail(FP_ERR_ARG, "cuda_stream is not a valid stream");
+        }
+        if (sdev != dev) {
+            snprintf(msg, sizeof msg, "cuda_stream belongs to device %d, not the current device %d", sdev, dev);
+            return sfail(FP_ERR_ARG, msg);
+        }
     }
     const bool fp32 = prec == FP_PREC_FP32_RAW;
-    fpk::BrickDev d;
-    std::memset(&d, 0, sizeof d);
-    d.n = n;
-    d.l = l;
-    d.m = l - 1;
-    d.N = 2 * d.m;
-    d.cut = n / 2;
-    d.n_layers[0] = d.cut;
-    d.n_layers[1] = n - 1 - d.cut;
-    d.delta_par[0] = 0;
-    d.delta_par[1] = n % 2;
-    d.tile_bits = 0;
+    // the brickwork sweep's uniform parameters, as fp_trace_batch builds them
+    // (whole boundary in one CTA: no tile schedule; host work only)
+    const fpk::BrickDev d = fpk::make_brick_plan(n, l, 0, 0, 0, 0).dev;
     int n_raw = 0;
     for (int t = 1; t <= l; ++t) n_raw += (n - (t - 1) % 2) / 2;
     bool both = false;
@@ -109,9 +121,6 @@ extern "C" fp_status fp_trace_brick_static(int32_t n, int32_t l, uint64_t seed, 
     }
     // set-up, once per device, with that device current: the device address of
     // the scratch array (its host-side name is only a stand-in)
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return sfail(FP_ERR_CUDA, "cudaGetDevice failed");
     unsigned char *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -130,7 +139,6 @@ extern "C" fp_status fp_trace_brick_static(int32_t n, int32_t l, uint64_t seed, 
     double2 *raw = (double2 *)(base + align256(count * per_info));
     void *maps = base + align256(count * per_info) + align256(count * per_raw);
     void *lbuf = base + align256(count * per_info) + align256(count * per_raw) + align256(count * per_map);
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     fill_pairs_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(first, (uint32_t)count, n_raw, pairs);
     if ((e = cudaGetLastError()) != cudaSuccess) return sfail(FP_ERR_CUDA, cudaGetErrorString(e));
     fpk::SampleParams sp;

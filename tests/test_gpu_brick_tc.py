@@ -1,0 +1,88 @@
+"""The tensor-core tile pass of the brickwork sweep (kernels_brick_tc.cu):
+window matrices on tcgen05 (TF32 x 3, FP32 accumulation in tensor memory),
+forced through the autotuner's cache file, against the FP64 path and the
+oracle at the deep depths l = 8, 9, 10 where it runs."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+TC = "12 5 256 2"
+
+
+@pytest.fixture(scope="module")
+def fp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_09900_gb300 import build
+    build.build()
+    import paper_2205_09900_gb300 as fpm
+    fpm.load()
+    return fpm
+
+
+def _force(tmp_path, monkeypatch, n, depths, variant=TC):
+    import torch
+    cache = tmp_path / "tune.txt"
+    name = torch.cuda.get_device_name(0)
+    cache.write_text("".join(f"{name} n={n} l={l} fp32|{variant}\n" for l in depths))
+    monkeypatch.setenv("FP_AUTOTUNE_CACHE", str(cache))
+
+
+@pytest.mark.parametrize("n", [30, 31])
+def test_tc_pass_matches_fp64(fp, n, tmp_path, monkeypatch):
+    # ragged batches (not a multiple of anything), even and odd chains; the
+    # per-pair error estimate bounds the actual difference
+    _force(tmp_path, monkeypatch, n, (8, 9, 10))
+    for l in (8, 9, 10):
+        ens = fp.Ensemble(fp.PARALLEL, n, l, l, seed=60 + l)
+        t32, _, _, e32 = ens.trace_batch(0, 77, fp.PREC_FP32_RAW, with_err=True)
+        t64, _, _ = ens.trace_batch(0, 77, fp.PREC_FP64)
+        d = np.abs(t32 - t64)
+        assert d.max() <= 1e-4, (l, d.max())
+        assert np.all(d <= e32), (l, (d / e32).max())
+        ens.close()
+
+
+def test_tc_pass_matches_oracle_n50(fp, tmp_path, monkeypatch):
+    # one pair of each deep depth of the benchmark ensemble against the oracle
+    import concurrent.futures as cf
+    _force(tmp_path, monkeypatch, 50, (8, 9, 10))
+    picks = {8: 3, 9: 5, 10: 7}
+    refs = {}
+    with cf.ThreadPoolExecutor(max_workers=3) as ex:
+        futs = {l: ex.submit(lambda l=l: O.trace_batch(O.desc(O.PARALLEL, 50, l, seed=80 + l), picks[l], 1, "ve")[0])
+                for l in picks}
+        for l, f in futs.items():
+            refs[l] = f.result()
+    for l, p in picks.items():
+        ens = fp.Ensemble(fp.PARALLEL, 50, l, l, seed=80 + l)
+        t32, _, _ = ens.trace_batch(p, 1, fp.PREC_FP32)
+        assert abs(t32[0] - refs[l]) <= 1e-4, (l, t32[0], refs[l])
+        ens.close()
+
+
+def test_tc_pass_full_size_self_pair(fp, tmp_path, monkeypatch):
+    # V = U: Tr(U^dagger U) = 2^50 exactly, through the tensor-core passes at l = 10
+    _force(tmp_path, monkeypatch, 50, (10,))
+    ens = fp.Ensemble(fp.PARALLEL, 50, 10, 10, seed=3, flags=fp.FLAG_SELF_PAIR)
+    t, _, _ = ens.trace_batch(0, 8, fp.PREC_FP32_RAW)
+    assert np.all(np.abs(t / 2.0 ** 50 - 1) < 1e-4), t
+    ens.close()
+
+
+def test_tc_pass_frame_potential_within_1e3(fp, tmp_path, monkeypatch):
+    # F^(k), k = 1..4, of the FP32 policy (tensor-core passes) within 1e-3 of FP64
+    _force(tmp_path, monkeypatch, 50, (8, 9, 10))
+    for l in (8, 9, 10):
+        ens = fp.Ensemble(fp.PARALLEL, 50, l, l, seed=90 + l)
+        N = 1500
+        t64, _, _ = ens.trace_batch(0, N, fp.PREC_FP64)
+        t32, _, _ = ens.trace_batch(0, N, fp.PREC_FP32)
+        for k in (1, 2, 3, 4):
+            f64 = np.mean(np.abs(t64) ** (2 * k))
+            f32 = np.mean(np.abs(t32) ** (2 * k))
+            assert abs(f32 - f64) <= 1e-3 * f64, (l, k)
+        ens.close()

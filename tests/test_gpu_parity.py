@@ -480,3 +480,65 @@ def test_bootstrap_matches_oracle(fp):
     assert np.allclose(out.cpu().numpy().reshape(4, K, B), ref, rtol=1e-12, atol=0, equal_nan=True)
     # deterministic
     assert np.array_equal(ens.bootstrap(t, grp, N, K, B, seed=23), got, equal_nan=True)
+
+
+# ---------------------------------------------------------------------------
+# Local circuits at T = 100 (the deepest T of the local workload): the pairs
+# whose boundaries reach 2^18-2^24 amplitudes and run on 4- and 16-CTA
+# clusters, against the oracle's variable elimination (minutes of CPU per
+# pair, computed once for all cluster sizes, one pair per thread).
+_T100 = {}
+
+
+def _t100_reference():
+    if not _T100:
+        import concurrent.futures as cf
+        od = O.desc(O.LOCAL, 20, 1, 1, T_min=100, T_max=100, T_step=20, seed=37)
+        picks = list(range(6))
+        with cf.ThreadPoolExecutor(max_workers=len(picks)) as ex:
+            ref = list(ex.map(lambda p: O.trace_batch(od, p, 1, "ve")[0], picks))
+        _T100["picks"], _T100["ref"] = picks, np.array(ref)
+    return _T100["picks"], _T100["ref"]
+
+
+@pytest.mark.parametrize("cluster", ["default", "4", "8", "16"])
+def test_local_T100_matches_oracle(fp, cluster, monkeypatch):
+    if cluster != "default":
+        monkeypatch.setenv("FP_SWEEP_CLUSTER", cluster)
+    picks, ref = _t100_reference()
+    ens = fp.Ensemble(fp.LOCAL, 20, 1, 1, 100, 100, 20, seed=37)
+    N = len(picks)
+    tr, kap, grp = ens.trace_batch(0, N, fp.PREC_FP64)
+    assert rel_err(tr, ref).max() <= TOL64, rel_err(tr, ref)
+    tr32, _, _ = ens.trace_batch(0, N, fp.PREC_FP32_RAW)
+    assert np.abs(tr32 - ref).max() <= TOL32
+    tr32p, _, _ = ens.trace_batch(0, N, fp.PREC_FP32)        # with the FP64 recontraction policy
+    assert np.abs(tr32p - ref).max() <= TOL32
+    ens.close()
+
+
+def test_fp32_frame_potential_within_1e3_of_fp64_bench_ensemble(fp):
+    # The benchmark's ensemble (n = 50, l uniform in 2..10, seed 4): F^(k), k = 1..4,
+    # of the FP32 policy path within 1e-3 relative of the FP64 path on the same
+    # 20,000 pairs, per depth group.
+    import torch
+    P = 20000
+    ens = fp.Ensemble(fp.PARALLEL, 50, 2, 10, seed=4)
+    out = {}
+    for prec in (fp.PREC_FP64, fp.PREC_FP32):
+        tr_d = torch.empty(2 * P, dtype=torch.float64, device="cuda")
+        gr_d = torch.empty(P, dtype=torch.int32, device="cuda")
+        ens.trace_batch(1_000_000, P, prec, tr_d, None, gr_d)
+        t = tr_d.cpu().numpy()
+        out[prec] = (t[0::2] + 1j * t[1::2], gr_d.cpu().numpy())
+    t64, g64 = out[fp.PREC_FP64]
+    t32, g32 = out[fp.PREC_FP32]
+    assert np.array_equal(g64, g32)
+    for g in range(9):
+        sel = g64 == g
+        assert sel.sum() > 1500
+        for k in (1, 2, 3, 4):
+            f64 = np.mean(np.abs(t64[sel]) ** (2 * k))
+            f32 = np.mean(np.abs(t32[sel]) ** (2 * k))
+            assert abs(f32 - f64) <= 1e-3 * f64, (g + 2, k, f32, f64)
+    ens.close()

@@ -271,6 +271,66 @@ def test_weingarten_one_layer_and_paper_bound():
     assert abs(2 * C * math.log(q) - pv["theory_slope_k2"]) < 0.05
 
 
+def _haar_projector_k2(d=4):
+    """E[G x G x conj(G) x conj(G)] for Haar G in U(d): the orthogonal projector
+    onto the span of the permutation vectors |sigma> (sigma in S_2) of
+    (C^d)^{x4}, built from their Gram matrix (Schur-Weyl duality), not from
+    tabulated Weingarten weights.  Returned as a tensor over the two qubits'
+    4-copy legs (dim 16 each): Q[out_a, out_b, in_a, in_b]."""
+    vecs = []
+    for sig in ((0, 1), (1, 0)):
+        v = np.zeros((d,) * 4)
+        for i1 in range(d):
+            for i2 in range(d):
+                i = (i1, i2)
+                v[i1, i2, i[sig[0]], i[sig[1]]] = 1.0
+        vecs.append(v.reshape(-1))
+    V = np.stack(vecs, axis=1)                         # [d^4, 2]
+    P = V @ np.linalg.inv(V.T @ V) @ V.T                # orthogonal projector
+    # copy c's gate index (a b), a the more significant qubit -> per-qubit legs
+    P = P.reshape((2, 2) * 8)                           # out c1..c4 (a, b), in c1..c4 (a, b)
+    out_a, out_b = [0, 2, 4, 6], [1, 3, 5, 7]
+    P = P.transpose(out_a + out_b + [8 + x for x in out_a] + [8 + x for x in out_b])
+    return P.reshape(16, 16, 16, 16)
+
+
+def _brickwork_f2_moment_operator(n, l):
+    """F^(2) = Tr(M^dagger M) with M the second-moment operator of the depth-l
+    brickwork ensemble (M = M_l ... M_1, M_t the tensor product of the Haar
+    projectors of layer t, identity on idle qubits; U and V independent):
+    the trace of the cyclic product P_1 P_2 ... P_l ... P_2 of projectors,
+    contracted over the qubits' 4-copy legs with numpy.einsum."""
+    Q = _haar_projector_k2()
+    layers = list(range(1, l + 1)) + list(range(l - 1, 1, -1))
+    letters = iter("abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ")
+    start = [next(letters) for _ in range(n)]
+    cur = list(start)
+    terms = []
+    for t in layers:
+        for b in range((t - 1) % 2, n - 1, 2):   # layer t acts on bonds b = t-1 mod 2, b+2, ...
+            oa, ob = next(letters), next(letters)
+            terms.append(oa + ob + cur[b] + cur[b + 1])
+            cur[b], cur[b + 1] = oa, ob
+    # close the trace: the last leg of each qubit is its first
+    ren = {c: s0 for c, s0 in zip(cur, start)}
+    terms = ["".join(ren.get(c, c) for c in tm) for tm in terms]
+    return float(np.einsum(",".join(terms) + "->", *([Q] * len(terms)), optimize="greedy"))
+
+
+@pytest.mark.parametrize("n,l,value", [(4, 2, 2.64), (4, 3, 2.2048), (5, 2, 3.0112), (6, 2, None), (5, 3, None)])
+def test_weingarten_exact_values(n, l, value):
+    # The oracle's transfer matrix against (i) the exact values 2.64, 2.2048 and
+    # 3.0112 derived from the Weingarten model behind Eq. theory_eq (Sec. "Frame
+    # potential"), and (ii) the second-moment operator of the ensemble built from
+    # orthogonal projectors onto permutation vectors -- no Weingarten weight and no
+    # link factor of the oracle enters (ii).
+    f = O.weingarten_f2_brickwork(n, l)
+    direct = _brickwork_f2_moment_operator(n, l)
+    assert abs(f - direct) < 1e-12 * direct, (f, direct)
+    if value is not None:
+        assert abs(f - value) < 1e-12, (f, value)
+
+
 @pytest.mark.parametrize("n,l", [(4, 2), (4, 3), (5, 2), (6, 2)])
 def test_weingarten_matches_monte_carlo(n, l):
     d = O.desc(O.PARALLEL, n, l, seed=100 + 10 * n + l)
