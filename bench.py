@@ -43,7 +43,6 @@ WORKLOADS = {
     "local": dict(n=20, depth_min=1, depth_max=1, T=(20, 100, 20), pairs=20_000, seed=2, k_max=4, kind=1,
                   name="local"),
 }
-SM_COUNT, FP32_LANES = 152, 128
 
 
 def parse():
@@ -64,6 +63,10 @@ def parse():
     ap.add_argument("--workload", default="brickwork", choices=sorted(WORKLOADS),
                     help="brickwork (the headline workload), hea (n=50, L=1..8), hea_paper (n=50, L=1..8) "
                          "or local (n=20, T=20..100)")
+    ap.add_argument("--cpu-depth-max", type=int, default=10,
+                    help="deepest depth the CPU oracle baseline samples (10: the whole workload)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the secondary workloads (n=8 FP64, HEA, paper HEA, local circuits)")
     ap.add_argument("--depth", type=int, default=0,
                     help="run one depth group only (l or L; profiling runs of a single tile-pass shape)")
     a = ap.parse_args()
@@ -105,38 +108,55 @@ def workload_config(args, world):
 # ---------------------------------------------------------------------------
 # CPU oracle (reported baseline; the only use of oracle/ in this file)
 # ---------------------------------------------------------------------------
-def oracle_sample(first_pair, cores, max_depth=8):
-    """Pairs of the workload in index order, skipping those deeper than max_depth
-    (the oracle needs ~30 s for l = 9 and minutes for l = 10 at n = 50)."""
+def _pairs_of_depth(d, l, count, first_pair):
+    """The first `count` pairs of depth l of the workload at or after first_pair."""
+    import oracle as O
+    out, p = [], first_pair
+    while len(out) < count:
+        if O.pair_depth(d, p) == l:
+            out.append(p)
+        p += 1
+    return out
+
+
+def oracle_depth_rate(l, cores, first_pair):
+    """Oracle throughput on pairs of depth l of the workload: cores pairs (4 x cores for
+    l <= 6, where a pair takes milliseconds), one pair per thread on `cores` threads,
+    FP64 variable elimination.  Returns (pairs/s, wall seconds, pairs)."""
+    import concurrent.futures as cf
     import oracle as O
     d = O.desc(O.PARALLEL, WORK["n"], WORK["depth_min"], WORK["depth_max"], seed=WORK["seed"])
-    pairs, p = [], first_pair
-    while len(pairs) < 2 * cores:
-        if O.pair_depth(d, p) <= max_depth:
-            pairs.append(p)
-        p += 1
-    return d, pairs
-
-
-def oracle_time(first_pair, cores):
-    import numpy as np
-    import oracle as O
-    d, pairs = oracle_sample(first_pair, cores)
-    # one pair per thread: contiguous runs are not guaranteed, so time each pair range
+    pairs = _pairs_of_depth(d, l, cores * (4 if l <= 6 else 1), first_pair)
     t0 = time.perf_counter()
-    import concurrent.futures as cf
     with cf.ThreadPoolExecutor(max_workers=cores) as ex:
         list(ex.map(lambda p: O.trace_batch(d, p, 1, "ve", threads=1), pairs))
     dt = time.perf_counter() - t0
-    depths = [O.pair_depth(d, p) for p in pairs]
-    return len(pairs) / dt, dt, len(pairs), depths
+    return len(pairs) / dt, dt, len(pairs)
 
 
-def cpu_baseline_obj(rate, cores, npairs, depths):
+def mix_rate(rates):
+    """Rate on the workload's uniform depth mix from per-depth rates: the mean time per
+    pair is the mean over depths of 1/rate."""
+    return 1.0 / (sum(1.0 / r for r in rates.values()) / len(rates))
+
+
+def oracle_baseline(cores, first_pair, depth_max=10):
+    """The oracle on the machine's host cores, per depth, combined into the uniform-mix rate."""
+    per, rates = {}, {}
+    for l in range(WORK["depth_min"], min(WORK["depth_max"], depth_max) + 1):
+        r, dt, npairs = oracle_depth_rate(l, cores, first_pair)
+        rates[l] = r
+        per[str(l)] = {"pairs": npairs, "wall_s": dt, "pairs_per_s": r, "core_s_per_pair": dt * cores / npairs}
+    return mix_rate(rates), per
+
+
+def cpu_baseline_obj(rate, cores, per, depth_max=10):
+    deep = "" if depth_max >= WORK["depth_max"] else f"; depths above {depth_max} left out"
     return {"value": rate, "unit": "contractions/s", "cores": cores, "kind": "oracle",
-            "sample": f"{npairs} pairs of the workload in index order with l<=8 (depths "
-                      f"{min(depths)}..{max(depths)}), one pair per thread, FP64 variable elimination; "
-                      "pairs with l=9,10 left out (the oracle needs ~30 s and minutes per such pair)"}
+            "sample": f"per depth l={WORK['depth_min']}..{min(WORK['depth_max'], depth_max)}: the workload's first "
+                      f"pairs of that depth (one per core for l>=7, 4 per core below), one pair per thread, FP64 "
+                      f"variable elimination; value = rate on the uniform depth mix = 1/mean_l(1/rate_l){deep}",
+            "per_depth": per}
 
 
 def run_reference(args):
@@ -144,24 +164,41 @@ def run_reference(args):
     if rank != 0:
         return
     cores = os.cpu_count() or 1
+    dmax = min(args.cpu_depth_max, WORK["depth_max"])
     first = 10_000_000
-    for _ in range(args.warmup):
-        oracle_time(first, cores)
-        first += 4 * cores
-    rates, times, last = [], [], None
-    for _ in range(args.steps):
-        r, dt, npairs, depths = oracle_time(first, cores)
-        first += 4 * cores
-        rates.append(r)
+    cheap = list(range(WORK["depth_min"], min(8, dmax) + 1))   # timed steps cycle over these depths
+    deep = list(range(9, dmax + 1))                             # measured once, before the timed steps
+    for w in range(args.warmup):
+        oracle_depth_rate(WORK["depth_min"], cores, first + 1_000_000 * (w + 1))
+    rates, per = {}, {}
+    for l in deep:
+        r, dt, npairs = oracle_depth_rate(l, cores, first)
+        rates[l] = r
+        per[str(l)] = {"pairs": npairs, "wall_s": dt, "pairs_per_s": r, "measured": "once, before the timed steps"}
+    times, step_rates = [], {}
+    for s in range(args.steps):
+        l = cheap[s % len(cheap)]
+        r, dt, npairs = oracle_depth_rate(l, cores, first + 2_000_000 * (s // len(cheap)))
         times.append(dt)
-        last = (npairs, depths)
-    value = args.steps / sum(t / (last[0]) for t in times) if times else 0.0
+        step_rates.setdefault(l, []).append(r)
+    for l in cheap:
+        if l in step_rates:
+            rates[l] = statistics.mean(step_rates[l])
+            per[str(l)] = {"pairs_per_s": rates[l], "timed_steps": len(step_rates[l])}
+        else:   # fewer timed steps than depths: measured once outside the timed steps
+            r, dt, npairs = oracle_depth_rate(l, cores, first)
+            rates[l] = r
+            per[str(l)] = {"pairs": npairs, "wall_s": dt, "pairs_per_s": r, "measured": "once, untimed"}
+    value = mix_rate(rates)
+    cb = cpu_baseline_obj(value, cores, per, dmax)
+    cb["sample"] += (f"; each timed step is one depth of {cheap[0]}..{cheap[-1]} in turn, depths "
+                     f"{deep[0] if deep else '-'}..{deep[-1] if deep else '-'} (minutes per pair) are measured once "
+                     "before the timed steps") if deep else ""
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "contractions/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded circuit pairs)",
-            "config": workload_config(args, args.gpus),
-            "cpu_baseline": cpu_baseline_obj(value, cores, last[0], last[1]),
+            "ms_per_step": 1e3 * statistics.mean(times) if times else 0.0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded circuit pairs)",
+            "config": workload_config(args, args.gpus), "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "contractions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -194,35 +231,65 @@ def per_pair_cost(fp, l, prec, count, first):
     return sum(ks.ms[i] for i in range(8)) / 1e3 / count
 
 
-def gpu_seconds_to_target(fp, mom, P, K, ng, rel=0.01):
-    """N_g pairs per depth group for rel. stderr of F^(2) <= rel, from the moments of
-    the last timed step; GPU-s = sum_g N_g x measured per-pair device time of depth g,
-    for the FP32 (mixed) and FP64 paths; plus an actual adaptive run on the mixed path."""
-    m = mom.cpu().numpy().reshape(ng, 2 * K + 1)
+def gpu_seconds_to_target(fp, rel=0.01):
+    """GPU-seconds to F^(2) at `rel` relative standard error, per depth of the n = 50
+    brickwork ensemble, measured by running fp_frame_potential to the target:
+      l >= 5: the mixed (FP32 policy) path and the plain FP64 path each run until the
+              target is met (FP64 for l <= 8; at l = 9, 10 the FP64 device time per pair,
+              measured, times the pairs the mixed run needed -- the estimator's variance
+              does not depend on the arithmetic);
+      l <= 4: |Tr|^4 is so heavy-tailed that 1 % needs far more pairs: the mixed path runs a
+              fixed budget of pairs, and the naive standard error, the bootstrap 5-95 %
+              range and the exact F^(2) (Weingarten transfer matrix) are reported beside it."""
+    import numpy as np
+    import torch
     out = {"target_rel_stderr": rel, "groups": {}}
     tot32 = tot64 = 0.0
-    for g in range(ng):
-        l = WORK["depth_min"] + g
-        N, S2, Q2 = m[g, 0], m[g, 2], m[g, K + 2]
+    for l in range(5, 11):
+        row = {}
+        for prec, tag in ((fp.PREC_FP32, "fp32"), (fp.PREC_FP64, "fp64")):
+            if prec == fp.PREC_FP64 and l >= 9:
+                c64 = per_pair_cost(fp, l, prec, 64 if l == 9 else 32, 60_000_000)
+                row["fp64"] = {"pairs": row["fp32"]["pairs"], "gpu_s": c64 * row["fp32"]["pairs"],
+                               "reached": row["fp32"]["reached"], "s_per_pair": c64,
+                               "how": "measured FP64 device seconds per pair x pairs of the mixed run"}
+                continue
+            ens = fp.Ensemble(fp.PARALLEL, WORK["n"], l, l, seed=7000 + l)
+            ens.frame_potential(10_000_000, 4096, 2, 0.0, prec)     # plans, autotuning, graphs
+            F, se, st = ens.frame_potential(0, 8_000_000, 2, rel, prec)
+            ens.close()
+            row[tag] = {"pairs": int(st.pairs), "gpu_s": st.gpu_seconds, "reached": bool(st.reached_target),
+                        "F2": float(F[0, 1]), "stderr": float(se[0, 1]), "fp64_recontracted": int(st.fp64_recontracted)}
+        row["exact_F2"] = fp.exact_brickwork_fk(WORK["n"], l, 2)
+        out["groups"][str(l)] = row
+        tot32 += row["fp32"]["gpu_s"]
+        tot64 += row["fp64"]["gpu_s"]
+    out["gpu_s_mixed_fp32_l5_10"] = tot32
+    out["gpu_s_plain_fp64_l5_10"] = tot64
+    out["speedup_l5_10"] = tot64 / tot32 if tot32 > 0 else None
+    budget = 2_000_000
+    shallow = {}
+    for l in range(2, 5):
+        ens = fp.Ensemble(fp.PARALLEL, WORK["n"], l, l, seed=7000 + l, flags=fp.FLAG_TIMING)
+        tr = torch.empty(2 * budget, dtype=torch.float64, device="cuda")
+        grp = torch.empty(budget, dtype=torch.int32, device="cuda")
+        ens.trace_batch(0, budget, fp.PREC_FP32, tr, None, grp)
+        ks = ens.kernel_stats(reset=True)
+        mom = torch.empty(2 * 2 + 1, dtype=torch.float64, device="cuda")
+        ens.reduce_moments(tr, grp, budget, 2, mom)
+        Fb = ens.bootstrap(tr, grp, budget, 2, 300, seed=11)
+        ens.close()
+        m = mom.cpu().numpy()
+        N, S2, Q2 = m[0], m[2], m[4]
         F2 = S2 / N
-        var = (Q2 - S2 * S2 / N) / (N - 1)
-        need = var / (rel * F2) ** 2
-        c32 = per_pair_cost(fp, l, fp.PREC_FP32, 2000 if l >= 9 else 4000, 50_000_000)
-        c64 = per_pair_cost(fp, l, fp.PREC_FP64, 32 if l >= 10 else (64 if l == 9 else 256), 60_000_000)
-        out["groups"][str(l)] = {"F2": F2, "pairs_needed": need, "s_per_pair_fp32": c32, "s_per_pair_fp64": c64}
-        tot32 += need * c32
-        tot64 += need * c64
-    out["gpu_s_mixed_fp32"] = tot32
-    out["gpu_s_plain_fp64"] = tot64
-    out["speedup"] = tot64 / tot32 if tot32 > 0 else None
-    out["method"] = ("pairs_needed from the variance of |Tr|^4 per depth group (last timed step); per-pair "
-                     "device seconds measured per depth with CUDA events; GPU-s = sum over groups")
-    ens = fp.Ensemble(fp.PARALLEL, WORK["n"], WORK["depth_min"], WORK["depth_max"], seed=WORK["seed"])
-    F, se, st = ens.frame_potential(70_000_000, 3_000_000, 2, rel, fp.PREC_FP32)
-    ens.close()
-    out["mixed_run"] = {"pairs": int(st.pairs), "gpu_seconds": st.gpu_seconds, "reached": bool(st.reached_target),
-                        "fp64_recontracted": int(st.fp64_recontracted),
-                        "F2_by_depth": {str(WORK["depth_min"] + g): [float(F[g, 1]), float(se[g, 1])] for g in range(ng)}}
+        se2 = math.sqrt(max(Q2 / N - F2 * F2, 0.0) / (N - 1))
+        shallow[str(l)] = {"pairs": budget, "gpu_s": sum(ks.ms[i] for i in range(8)) / 1e3, "F2": F2,
+                           "stderr": se2, "rel_stderr": se2 / F2,
+                           "bootstrap_F2_p5_p50_p95": [float(np.percentile(Fb[0, 1], q)) for q in (5, 50, 95)],
+                           "exact_F2": fp.exact_brickwork_fk(WORK["n"], l, 2)}
+    out["shallow_fixed_budget"] = shallow
+    out["method"] = ("single-depth ensembles (seed 7000+l); fp_frame_potential to rel. stderr <= 1% (batches from "
+                     "4096 pairs doubling to 2^20), stats.gpu_seconds = device time of the contraction batches")
     return out
 
 
@@ -397,6 +464,143 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+# ---------------------------------------------------------------------------
+# measured peaks and rooflines
+# ---------------------------------------------------------------------------
+def measure_peaks(fp):
+    """The arithmetic peaks of this GPU, measured by fp_measure_peak (microbenchmarks
+    timed with CUDA events, SM clock read in-kernel)."""
+    names = {fp.PEAK_FFMA: "fp32_ffma", fp.PEAK_FFMA2: "fp32_ffma2", fp.PEAK_DFMA: "fp64_dfma",
+             fp.PEAK_TC_TF32: "tf32_tcgen05", fp.PEAK_TC_BF16: "bf16_tcgen05"}
+    return {nm: fp.measure_peak(w) for w, nm in names.items()}
+
+
+def roofline(fp, ks, ms_total, prec, peaks, clocks):
+    """Roofline of the dominant contraction class: algorithmic flops (8 real flops per
+    complex multiply-add of the method, ks.work) over that class's device time, against
+    the measured FP32 (packed FFMA) or FP64 peak at the run's median SM clock."""
+    cls = max((fp.K_SWEEP, fp.K_BRICK, fp.K_SPIRAL), key=lambda i: ks.ms[i])
+    flops = 8.0 * ks.work[cls]
+    achieved = flops / (ks.ms[cls] / 1e3) / 1e12 if ks.ms[cls] > 0 else 0.0
+    key = "fp64_dfma" if prec == fp.PREC_FP64 else "fp32_ffma2"
+    pk = peaks[key]
+    mhz = (clocks or {}).get("sm_mhz") or pk["sm_mhz"]
+    peak = pk["flops_per_clk_sm"] * pk["sms"] * mhz * 1e6 / 1e12
+    return {"bound": "alu", "kernel": fp.K_NAMES.get(cls, str(cls)), "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
+            "peak_source": (f"measured: {key} microbenchmark {pk['flops_per_clk_sm']:.1f} flop/clk/SM x {pk['sms']} "
+                            f"SMs x {mhz:.0f} MHz (median SM clock of the timed region); "
+                            f"{pk['tflops']:.1f} TFLOP/s at {pk['sm_mhz']:.0f} MHz in the microbenchmark"),
+            "kernel_ms_share": ks.ms[cls] / ms_total if ms_total else None}
+
+
+# ---------------------------------------------------------------------------
+def measure(fp, args, work, P, steps, warmup, prec, stream, rank, world, dist):
+    """W untimed + K timed steps of one workload (sample -> contraction -> moments),
+    CUDA events on the library's stream, max over ranks; clocks sampled during the
+    timed region."""
+    import torch
+    from paper_2205_09900_gb300.shard import max_over_ranks, pair_range
+    saved = dict(WORK)
+    WORK.clear()
+    WORK.update(work)
+    try:
+        K = WORK["k_max"]
+        ens = make_ensemble(fp, fp.FLAG_TIMING, stream.cuda_stream)
+        ng = len(ens.groups())
+        tr = torch.empty(2 * P, dtype=torch.float64, device="cuda")
+        kap = torch.empty(P, dtype=torch.float64, device="cuda")
+        err = torch.empty(P, dtype=torch.float64, device="cuda")
+        grp = torch.empty(P, dtype=torch.int32, device="cuda")
+        mom = torch.empty(ng * (2 * K + 1), dtype=torch.float64, device="cuda")
+        skipped = torch.zeros((), dtype=torch.int64, device="cuda")
+
+        def first_of(s):
+            return pair_range(s, rank, world, P)[0]
+
+        def step(s):
+            ens.trace_batch(first_of(s), P, prec, tr, kap, grp, err)
+            ens.reduce_moments(tr, grp, P, K, mom)
+            if WORK["name"] == "local":
+                skipped.add_((grp < 0).sum())
+
+        for s in range(warmup):
+            step(s)
+        torch.cuda.synchronize()
+        skipped.zero_()
+        ens.kernel_stats(reset=True)
+        clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(warmup, warmup + steps):
+            step(s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, device="cuda")
+        if dist:
+            dist.barrier()
+        ks = ens.kernel_stats(reset=True)
+        n_skipped = int(skipped.item())
+        out = {"ms": ms, "ks": ks, "clocks": clocks, "mom": mom.cpu().numpy(), "groups": ens.groups(),
+               "value": world * (P * steps - n_skipped) / (ms / 1e3), "skipped": n_skipped,
+               "launches": int(sum(ks.launches[i] for i in range(8))), "tr": tr, "first_last": first_of(warmup + steps - 1)}
+        ens.close()
+        return out
+    finally:
+        WORK.clear()
+        WORK.update(saved)
+
+
+def secondary_workloads(fp, peaks, stream):
+    """The other configurations of the metric, measured the same way (device time of
+    whole steps, clocks, roofline against the measured peaks), compactly:
+      n8_fp64      brickwork n = 8, l = 4, 10^4 pairs, FP64, F^(1..3), with the error
+                   against the oracle's dense 256 x 256 traces on 256 of the pairs;
+      hea          HEA n = 50, L = 1..8, 10^6 pairs per step;
+      hea_paper    the paper's HEA (CNOT walls) n = 50, L = 1..8, 10^5 pairs per step;
+      local        local circuits n = 20, T = 20..100, 2 x 10^4 pairs per step."""
+    import numpy as np
+    cfgs = {
+        "n8_fp64": (dict(n=8, depth_min=4, depth_max=4, pairs=10_000, seed=1, k_max=3, kind=0, name="brickwork"),
+                    10_000, 5, fp.PREC_FP64),
+        "hea": (WORKLOADS["hea"], 1_000_000, 2, fp.PREC_FP32),
+        "hea_paper": (WORKLOADS["hea_paper"], 100_000, 3, fp.PREC_FP32),
+        "local": (WORKLOADS["local"], 20_000, 3, fp.PREC_FP32),
+    }
+    out = {}
+    for name, (work, P, steps, prec) in cfgs.items():
+        r = measure(fp, None, dict(work), P, steps, 2, prec, stream, 0, 1, None)
+        K = work["k_max"]
+        m = r["mom"].reshape(len(r["groups"]), 2 * K + 1)
+        F = {}
+        for g, dv in enumerate(r["groups"]):
+            N = m[g, 0]
+            if N < 2:
+                continue
+            f = [float(m[g, k] / N) for k in range(1, K + 1)]
+            se = [math.sqrt(max(m[g, K + k] / N - f[k - 1] ** 2, 0.0) / (N - 1)) for k in range(1, K + 1)]
+            F[str(int(dv))] = {"F": f, "stderr": se}
+        row = {"value": r["value"], "unit": "contractions/s", "ms_per_step": r["ms"] / steps, "steps": steps,
+               "pairs_per_step": P, "dtype": "f64" if prec == fp.PREC_FP64 else "f32", "clocks": r["clocks"],
+               "roofline": roofline(fp, r["ks"], r["ms"], prec, peaks, r["clocks"]), "gpu_launches": r["launches"],
+               "F_by_group_last_step": F}
+        if name == "local":
+            row["infeasible_pairs_in_timed_steps"] = r["skipped"]
+        if name == "n8_fp64":
+            import oracle as O
+            t = r["tr"].cpu().numpy()
+            got = t[0:512:2] + 1j * t[1:512:2]
+            ref = O.trace_batch(O.desc(O.PARALLEL, 8, 4, seed=1), r["first_last"], 256, "dense", threads=8)
+            row["max_rel_err_vs_oracle_dense_256_pairs"] = float(np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1)))
+        out[name] = row
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -420,54 +624,17 @@ def main():
     if dist:
         dist.barrier()
     import paper_2205_09900_gb300 as fp
+    from paper_2205_09900_gb300.shard import pair_range
 
     prec = fp.PREC_FP32 if args.prec == "fp32" else fp.PREC_FP64
     stream = torch.cuda.current_stream()
     P, K = args.pairs, WORK["k_max"]
-    ens = make_ensemble(fp, fp.FLAG_TIMING, stream.cuda_stream)
-    ng = len(ens.groups())
-    tr = torch.empty(2 * P, dtype=torch.float64, device="cuda")
-    kap = torch.empty(P, dtype=torch.float64, device="cuda")
-    err = torch.empty(P, dtype=torch.float64, device="cuda")
-    grp = torch.empty(P, dtype=torch.int32, device="cuda")
-    mom = torch.empty(ng * (2 * K + 1), dtype=torch.float64, device="cuda")
-
-    from paper_2205_09900_gb300.shard import max_over_ranks, pair_range
+    peaks = measure_peaks(fp)
+    r = measure(fp, args, dict(WORK), P, args.steps, args.warmup, prec, stream, rank, world, dist)
+    ms, ks, clocks, launches = r["ms"], r["ks"], r["clocks"], r["launches"]
 
     def first_of(step):
         return pair_range(step, rank, world, P)[0]
-
-    skipped = torch.zeros((), dtype=torch.int64, device="cuda")
-
-    def step(s):
-        ens.trace_batch(first_of(s), P, prec, tr, kap, grp, err)
-        ens.reduce_moments(tr, grp, P, K, mom)
-        if WORK["name"] == "local":
-            skipped.add_((grp < 0).sum())
-
-    for s in range(args.warmup):
-        step(s)
-    torch.cuda.synchronize()
-    skipped.zero_()
-    ens.kernel_stats(reset=True)
-
-    clk = Clocks(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clk.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for s in range(args.warmup, args.warmup + args.steps):
-        step(s)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1), dist, device="cuda")
-    if dist:
-        dist.barrier()
-    ks = ens.kernel_stats(reset=True)
-    launches = int(sum(ks.launches[i] for i in range(8)))
 
     # e2e: the public Monte Carlo call, results to host memory, host wall clock
     e2e = None
@@ -483,6 +650,7 @@ def main():
             contracted += rst.pairs
         dt = time.perf_counter() - t0
         replays = int(ens_u.kernel_stats().graph_replays)
+        ng = len(ens_u.groups())
         ens_u.close()
         # host->device per step: PairInfo (40 B) + order (4 B) + group (4 B) per pair;
         # device->host: kappa (8 B/pair, FP32 policy) + per-batch moments
@@ -501,31 +669,8 @@ def main():
             e2e["note"] = ("includes the host planning of every pair (own topology per pair); the per-pair "
                            "contraction programs it uploads are not counted in h2d_bytes_per_step")
 
-    n_skipped = int(skipped.item())
-    value = world * (P * args.steps - n_skipped) / (ms / 1e3)
-    # roofline of the dominant contraction class (the sweep kernels carry the flop count)
-    cls = max((fp.K_SWEEP, fp.K_BRICK, fp.K_SPIRAL), key=lambda i: ks.ms[i])
-    flops = 8.0 * ks.work[cls]                 # complex multiply-add = 8 real flops
-    achieved = flops / (ks.ms[cls] / 1e3) / 1e12 if ks.ms[cls] > 0 else 0.0
-    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
-    if prec == fp.PREC_FP64:
-        peak = peak / 64.0       # FP64 FMA rate is a small fraction of FP32 on this part
-    roof = {"bound": "alu", "kernel": fp.K_NAMES.get(cls, str(cls)), "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
-            "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz",
-            "kernel_ms_share": ks.ms[cls] / ms if ms else None}
-    if WORK["name"] == "brickwork" and prec == fp.PREC_FP32:
-        # DRAM bytes (read + write) of the dominant kernel from one ncu capture of the current
-        # tile-pass code: brick_pass_kernel<float2, 13, 5, 256>, depth 10, one pass over 256 pairs
-        roof["traffic"] = 538.040832e6 + 476.1664e6
-        roof["traffic_launch"] = ("brick_pass_kernel<float2,13,5,256>, l=10, one tile pass of 256 pairs; "
-                                  "algorithmic bytes 2 x 256 x 2^18 x 8 = 1.0737e9")
-    if WORK["name"] == "hea_paper" and prec == fp.PREC_FP32:
-        # the dominant spiral kernel from one ncu capture: its DRAM traffic is the maps it reads
-        roof["traffic"] = 412.827392e6 + 4.156928e6
-        roof["traffic_launch"] = ("spiral_win_kernel<float2,5,2>, L=8, one launch of 2000 pairs; "
-                                  "algorithmic bytes 2000 x 797 maps x 256 B = 4.081e8")
+    value = r["value"]
+    roof = roofline(fp, ks, ms, prec, peaks, clocks)
 
     metric = {"brickwork": METRIC, "hea": "Tr(U^dagger V) contractions/s at n=50 (HEA, L=1..8)",
               "hea_paper": "Tr(U^dagger V) contractions/s at n=50 (paper HEA with CNOT walls, L=1..8)",
@@ -535,28 +680,30 @@ def main():
             "vs_baseline": None, "dtype": "f32" if prec != fp.PREC_FP64 else "f64",
             "data": "synthetic (seeded circuit pairs)", "config": workload_config(args, world),
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "peaks_measured": peaks,
             "kernel_ms": {fp.K_NAMES.get(i, str(i)): ks.ms[i] for i in range(8) if ks.launches[i]}}
     if WORK["name"] == "local":
-        line["infeasible_pairs_in_timed_steps"] = n_skipped
+        line["infeasible_pairs_in_timed_steps"] = r["skipped"]
     if WORK["name"] == "hea_paper":
-        line["F_by_depth_last_step"] = moments_report(mom.cpu().numpy(), ens.groups(), K)
-    if rank == 0 and world == 1 and not args.no_target and WORK["name"] == "brickwork":
-        line["gpu_s_to_1pct_F2"] = gpu_seconds_to_target(fp, mom, P, K, ng)
-    if rank == 0 and world == 1 and not args.no_cv and WORK["name"] == "brickwork":
+        line["F_by_depth_last_step"] = moments_report(r["mom"], r["groups"], K)
+    solo = rank == 0 and world == 1
+    if solo and not args.no_secondary and WORK["name"] == "brickwork" and args.depth == 0:
+        line["secondary"] = secondary_workloads(fp, peaks, stream)
+    if solo and not args.no_target and WORK["name"] == "brickwork":
+        line["gpu_s_to_1pct_F2"] = gpu_seconds_to_target(fp)
+    if solo and not args.no_cv and WORK["name"] == "brickwork":
         line["control_variate"] = control_variate_report(fp)
-    if rank == 0 and world == 1 and not args.no_target and WORK["name"] == "brickwork":
+    if solo and not args.no_target and WORK["name"] == "brickwork":
         line["bootstrap"] = bootstrap_report(fp)
-        mc = line.get("gpu_s_to_1pct_F2", {}).get("mixed_run", {}).get("F2_by_depth")
-        line["exact_weingarten"] = exact_fk_report(fp, mc)
-    if rank == 0 and world == 1 and not args.no_target and WORK["name"] == "local":
+        line["exact_weingarten"] = exact_fk_report(fp)
+    if solo and not args.no_target and WORK["name"] == "local":
         line["local_large_T"] = local_large_T_report(fp)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and WORK["name"] == "brickwork":
+    if solo and not args.no_cpu_baseline and WORK["name"] == "brickwork":
         cores = os.cpu_count() or 1
-        r, dt, npairs, depths = oracle_time(10_000_000, cores)
-        line["cpu_baseline"] = cpu_baseline_obj(r, cores, npairs, depths)
+        rate, per = oracle_baseline(cores, 10_000_000, args.cpu_depth_max)
+        line["cpu_baseline"] = cpu_baseline_obj(rate, cores, per, args.cpu_depth_max)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ens.close()
     if dist:
         dist.destroy_process_group()
 

@@ -320,6 +320,10 @@ typedef struct {
     uint64_t n_train;         /* exactly contracted training pairs (>= batch) */
     uint64_t n_correct;       /* exactly contracted correction pairs (>= 2) */
     uint64_t m_surrogate;     /* surrogate-only pairs (>= 2) */
+    double *g_correct;        /* optional [n_correct] output (host or device, NULL: none):
+                                 g on the correction pairs, in units of |Tr|^4 */
+    double *f_correct;        /* optional [n_correct] output: f = |Tr|^4 on the correction pairs */
+    double *g_surrogate;      /* optional [m_surrogate] output: g on the surrogate pairs */
 } fp_cv_config;
 
 typedef struct {

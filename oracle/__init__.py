@@ -74,12 +74,16 @@ def lib():
             L.orc_trace_dense.argtypes = [ctypes.c_int, ctypes.c_int, P(Op), ctypes.c_int, P(Op),
                                           P(ctypes.c_double)]
             L.orc_trace_ve.argtypes = L.orc_trace_dense.argtypes
+            L.orc_trace_ve_greedy.argtypes = L.orc_trace_dense.argtypes
             L.orc_trace_pair.argtypes = [P(Desc), ctypes.c_uint64, ctypes.c_int, P(ctypes.c_double)]
             L.orc_trace_batch.argtypes = [P(Desc), ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                           ctypes.c_int, P(ctypes.c_double)]
             L.orc_moments.argtypes = [P(ctypes.c_double), ctypes.c_int64, ctypes.c_int,
                                       P(ctypes.c_double), P(ctypes.c_double)]
             L.orc_weingarten_f2_brickwork.argtypes = [ctypes.c_int, ctypes.c_int]
+            L.orc_cv_estimate.argtypes = [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int64,
+                                          P(ctypes.c_double), ctypes.c_int64, P(ctypes.c_double)]
+            L.orc_cv_estimate.restype = None
             L.orc_bootstrap.argtypes = [P(ctypes.c_double), P(ctypes.c_int32), ctypes.c_int64, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_uint64, P(ctypes.c_double)]
             L.orc_bootstrap.restype = None
@@ -153,9 +157,10 @@ def _to_ops(gates):
 
 
 def trace_ops(n, U, V, method="ve"):
-    """Tr(U^dagger V) for explicit gate lists (dense for method='dense')."""
+    """Tr(U^dagger V) for explicit gate lists (method 'dense', 've' in qubit order or
+    've_greedy' in min-degree order)."""
     tr = np.zeros(2)
-    fn = lib().orc_trace_dense if method == "dense" else lib().orc_trace_ve
+    fn = {"dense": lib().orc_trace_dense, "ve": lib().orc_trace_ve, "ve_greedy": lib().orc_trace_ve_greedy}[method]
     rc = fn(n, len(U), _to_ops(U), len(V), _to_ops(V), _dp(tr))
     if rc:
         raise RuntimeError(f"oracle trace failed: {rc}")
@@ -163,7 +168,7 @@ def trace_ops(n, U, V, method="ve"):
 
 
 def trace_pair(d, pair, method="auto"):
-    m = {"auto": -1, "dense": 0, "ve": 1}[method]
+    m = {"auto": -1, "dense": 0, "ve": 1, "ve_greedy": 2}[method]
     tr = np.zeros(2)
     rc = lib().orc_trace_pair(ctypes.byref(d), pair, m, _dp(tr))
     if rc:
@@ -172,7 +177,7 @@ def trace_pair(d, pair, method="auto"):
 
 
 def trace_batch(d, first, count, method="auto", threads=1):
-    m = {"auto": -1, "dense": 0, "ve": 1}[method]
+    m = {"auto": -1, "dense": 0, "ve": 1, "ve_greedy": 2}[method]
     tr = np.zeros(2 * count)
     rc = lib().orc_trace_batch(ctypes.byref(d), first, count, m, threads, _dp(tr))
     if rc:
@@ -186,6 +191,17 @@ def moments(tr, kmax):
     se = np.zeros(kmax)
     lib().orc_moments(_dp(t), len(tr), kmax, _dp(F), _dp(se))
     return F, se
+
+
+def cv_estimate(g_corr, f_corr, g_sur):
+    """Control-variate estimate of F^(2) (orc_cv_estimate): dict with F, stderr, F_plain,
+    stderr_plain, var_f, var_f_minus_g, var_g."""
+    gc = np.ascontiguousarray(g_corr, dtype=np.float64)
+    fc = np.ascontiguousarray(f_corr, dtype=np.float64)
+    gs = np.ascontiguousarray(g_sur, dtype=np.float64)
+    out = np.zeros(7)
+    lib().orc_cv_estimate(_dp(gc), _dp(fc), len(gc), _dp(gs), len(gs), _dp(out))
+    return dict(zip(("F", "stderr", "F_plain", "stderr_plain", "var_f", "var_f_minus_g", "var_g"), map(float, out)))
 
 
 def weingarten_f2_brickwork(n, l):

@@ -321,7 +321,24 @@ static void dagger_op(const orc_op *in, orc_op *out)
         for (int i = 0; i < 4; ++i) h[i] = conj(g[i]);
 }
 
+static int trace_ve_order(int n, int nU, const orc_op *U, int nV, const orc_op *V, int greedy, double tr[2]);
+
 int orc_trace_ve(int n, int nU, const orc_op *U, int nV, const orc_op *V, double tr[2])
+{
+    return trace_ve_order(n, nU, U, nV, V, 0, tr);
+}
+
+/* The same variable elimination with a min-degree order: every step sums out
+ * the variable whose factors together span the fewest distinct variables
+ * (ties: the lowest index).  The result is the same trace; only the order of
+ * the sums, and so the sizes of the intermediate factors, differ -- local
+ * circuits with many gates stay within reach of a CPU this way. */
+int orc_trace_ve_greedy(int n, int nU, const orc_op *U, int nV, const orc_op *V, double tr[2])
+{
+    return trace_ve_order(n, nU, U, nV, V, 1, tr);
+}
+
+static int trace_ve_order(int n, int nU, const orc_op *U, int nV, const orc_op *V, int greedy, double tr[2])
 {
     int T = nU + nV, rc = 0;
     orc_op *seq = malloc(sizeof(orc_op) * (T > 0 ? T : 1));
@@ -376,8 +393,36 @@ int orc_trace_ve(int n, int nU, const orc_op *U, int nV, const orc_op *V, double
     int *uvars = malloc(sizeof(int) * (nvars + 8));
     int *sel = malloc(sizeof(int) * (nf + 1));
     int **posf = malloc(sizeof(int *) * (nf + 1));
-    for (int q = n - 1; q >= 0 && rc == 0; --q) {
-        for (int v = base[q]; v < base[q + 1] && rc == 0; ++v) {
+    /* elimination order: qubits n-1 down to 0, each qubit's segments in order;
+     * or min-degree (greedy) */
+    int *order = malloc(sizeof(int) * (nvars > 0 ? nvars : 1));
+    char *gone = calloc(nvars > 0 ? nvars : 1, 1);
+    for (int q = n - 1, k = 0; q >= 0; --q)
+        for (int v = base[q]; v < base[q + 1]; ++v) order[k++] = v;
+    for (int step = 0; step < nvars && rc == 0; ++step) {
+        int v = order[step];
+        if (greedy) {
+            int best = -1, best_w = 1 << 30;
+            for (int c = 0; c < nvars; ++c) {
+                if (gone[c]) continue;
+                int nu = 0;
+                for (int f = 0; f < nf; ++f) {
+                    if (!fs[f].t) continue;
+                    int has = 0;
+                    for (int k = 0; k < fs[f].nv; ++k) has |= fs[f].vars[k] == c;
+                    if (!has) continue;
+                    for (int k = 0; k < fs[f].nv; ++k) {
+                        int u;
+                        for (u = 0; u < nu; ++u) if (uvars[u] == fs[f].vars[k]) break;
+                        if (u == nu) uvars[nu++] = fs[f].vars[k];
+                    }
+                }
+                if (nu < best_w) { best_w = nu; best = c; }
+            }
+            v = best;
+        }
+        gone[v] = 1;
+        {
             int ns = 0;
             for (int f = 0; f < nf; ++f) {
                 if (!fs[f].t) continue;
@@ -434,6 +479,7 @@ int orc_trace_ve(int n, int nU, const orc_op *U, int nV, const orc_op *V, double
             nfac->t = res;
         }
     }
+    free(order); free(gone);
     for (int f = 0; f < nf; ++f) {
         if (fs[f].t) {
             if (rc == 0) scalar *= fs[f].t[0];   /* every variable is summed: scalars remain */
@@ -460,6 +506,7 @@ int orc_trace_pair(const orc_desc *d, uint64_t pair, int method, double tr[2])
     int nU = orc_circuit(d, pair, 0, U, cap), nV = orc_circuit(d, pair, 1, V, cap), rc;
     if (nU < 0 || nV < 0) rc = -2;
     else if (method == 0 || (method < 0 && d->n <= 10)) rc = orc_trace_dense(d->n, nU, U, nV, V, tr);
+    else if (method == 2) rc = orc_trace_ve_greedy(d->n, nU, U, nV, V, tr);
     else rc = orc_trace_ve(d->n, nU, U, nV, V, tr);
     free(U); free(V);
     return rc;
@@ -530,6 +577,48 @@ void orc_moments(const double *tr, int64_t N, int kmax, double *F, double *se)
         F[k - 1] = mean;
         se[k - 1] = N > 1 ? sqrt((v + vc) / (double)(N - 1) / (double)N) : 0.0;
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Control-variate estimate of F^(2) = E f, f = |Tr|^4 (the paper's estimand, */
+/* Sec. "Frame potential"; the control variate itself is not in the paper):  */
+/* with a predictor g evaluated on M surrogate pairs and on the N correction  */
+/* pairs (where f is also known),                                            */
+/*     F = mean_M g + mean_N (f - g),                                        */
+/*     stderr^2 = Var_M(g) / M + Var_N(f - g) / N,                           */
+/* sample variances with N - 1 (M - 1); the plain estimate mean_N f and its   */
+/* standard error beside it.  Two passes (mean, then centred squares), both   */
+/* Neumaier-compensated.                                                     */
+/* out: F, stderr, F_plain, stderr_plain, Var f, Var (f - g), Var g.         */
+/* ------------------------------------------------------------------------ */
+static void mean_var(const double *a, const double *b, int64_t n, double *mean, double *var)
+{
+    /* the values are a[i] - b[i] (b may be NULL) */
+    double s = 0, c = 0;
+    for (int64_t i = 0; i < n; ++i) neumaier_add(&s, &c, a[i] - (b ? b[i] : 0.0));
+    *mean = (s + c) / (double)n;
+    double v = 0, vc = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double d = a[i] - (b ? b[i] : 0.0) - *mean;
+        neumaier_add(&v, &vc, d * d);
+    }
+    *var = n > 1 ? (v + vc) / (double)(n - 1) : 0.0;
+}
+
+void orc_cv_estimate(const double *g_corr, const double *f_corr, int64_t N, const double *g_sur, int64_t M,
+                     double *out)
+{
+    double mfg, vfg, mf, vf, mg, vg;
+    mean_var(f_corr, g_corr, N, &mfg, &vfg);
+    mean_var(f_corr, NULL, N, &mf, &vf);
+    mean_var(g_sur, NULL, M, &mg, &vg);
+    out[0] = mg + mfg;
+    out[1] = sqrt(vg / (double)M + vfg / (double)N);
+    out[2] = mf;
+    out[3] = sqrt(vf / (double)N);
+    out[4] = vf;
+    out[5] = vfg;
+    out[6] = vg;
 }
 
 /* ------------------------------------------------------------------------ */

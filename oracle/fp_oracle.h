@@ -89,10 +89,17 @@ int    orc_pair_depth(const orc_desc *d, uint64_t pair);
 int    orc_circuit(const orc_desc *d, uint64_t pair, int which, orc_op *ops, int max_ops);
 int    orc_trace_dense(int n, int nU, const orc_op *U, int nV, const orc_op *V, double tr[2]);
 int    orc_trace_ve(int n, int nU, const orc_op *U, int nV, const orc_op *V, double tr[2]);
+/* the same elimination in min-degree order (same trace, smaller intermediates) */
+int    orc_trace_ve_greedy(int n, int nU, const orc_op *U, int nV, const orc_op *V, double tr[2]);
 int    orc_trace_pair(const orc_desc *d, uint64_t pair, int method, double tr[2]);
 int    orc_trace_batch(const orc_desc *d, uint64_t first, uint64_t count, int method,
                        int nthreads, double *tr);
 void   orc_moments(const double *tr, int64_t N, int kmax, double *F, double *se);
+/* Control-variate estimate of F^(2) from g on N correction and M surrogate pairs
+ * and f = |Tr|^4 on the correction pairs: out[7] = F, stderr, F_plain,
+ * stderr_plain, Var f, Var (f - g), Var g (see fp_oracle.c). */
+void   orc_cv_estimate(const double *g_corr, const double *f_corr, int64_t N, const double *g_sur, int64_t M,
+                       double *out);
 double orc_weingarten_f2_brickwork(int n, int l);
 /* Exact ensemble F^(k), k = 2 or 3, of brickwork circuits (the same model
  * over S_k pairings); NaN for other k. */

@@ -61,7 +61,8 @@ class KernelStats(ctypes.Structure):
 class CvConfig(ctypes.Structure):
     _fields_ = [("hidden", ctypes.c_int32), ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("lr", ctypes.c_double), ("first", ctypes.c_uint64),
-                ("n_train", ctypes.c_uint64), ("n_correct", ctypes.c_uint64), ("m_surrogate", ctypes.c_uint64)]
+                ("n_train", ctypes.c_uint64), ("n_correct", ctypes.c_uint64), ("m_surrogate", ctypes.c_uint64),
+                ("g_correct", ctypes.c_void_p), ("f_correct", ctypes.c_void_p), ("g_surrogate", ctypes.c_void_p)]
 
 
 class CvResult(ctypes.Structure):
@@ -302,9 +303,14 @@ class Ensemble:
         _check(load().fp_kernel_stats_get(self._h, ctypes.byref(st), int(bool(reset))))
         return st
 
-    def cv_frame_potential(self, first, n_train, n_correct, m_surrogate, hidden=256, epochs=20, batch=512, lr=1e-3):
-        """Control-variate F^(2) of a single-depth HEA ensemble (see fp_cv_frame_potential)."""
-        cfg = CvConfig(hidden, epochs, batch, 0, lr, first, n_train, n_correct, m_surrogate)
+    def cv_frame_potential(self, first, n_train, n_correct, m_surrogate, hidden=256, epochs=20, batch=512, lr=1e-3,
+                           g_correct=None, f_correct=None, g_surrogate=None):
+        """Control-variate F^(2) of a single-depth HEA ensemble (see fp_cv_frame_potential);
+        g_correct, f_correct [n_correct] and g_surrogate [m_surrogate] float64 arrays (host or
+        device, optional) receive the per-pair values behind the estimate."""
+        p = lambda x: None if x is None else _ptr(x).value
+        cfg = CvConfig(hidden, epochs, batch, 0, lr, first, n_train, n_correct, m_surrogate, p(g_correct),
+                       p(f_correct), p(g_surrogate))
         res = CvResult()
         _check(load().fp_cv_frame_potential(self._h, ctypes.byref(cfg), ctypes.byref(res)))
         return res

@@ -218,6 +218,12 @@ __global__ void adam_kernel(long long n, float *w, const float *g, float *m, flo
     }
 }
 
+// g in units of |Tr|^4 (FP64) for export
+__global__ void gexport_kernel(int count, const float *g, double gscale, double *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = (double)g[i] * gscale;
+}
+
 // sums over a batch of (g, g^2) or (f - g, (f - g)^2, f, f^2) in FP64
 __global__ void cv_sums_kernel(int count, const float *g, double gscale, const double *f, double *sums) {
     __shared__ double sh[4][256];
@@ -581,12 +587,22 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
     CKC(cudaEventRecord(e0, st));
     CKC(fc.alloc(NC * sizeof(double)));
     abs4_kernel<<<(unsigned)((NC + 255) / 256), 256, 0, st>>>(dtr, (int)NC, 1.0, nullptr, fc.d());
+    if (cfg->f_correct) CKC(cudaMemcpyAsync(cfg->f_correct, fc.d(), NC * sizeof(double), cudaMemcpyDefault, st));
+    Buf gx;   // per-pair g for the optional exports
+    if (cfg->g_correct || cfg->g_surrogate) CKC(gx.alloc(chunk * sizeof(double)));
+    auto export_g = [&](double *dst, int cnt) -> cudaError_t {
+        if (!dst) return cudaSuccess;
+        gexport_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, gc.f(), res->target_scale, gx.d());
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? cudaMemcpyAsync(dst, gx.d(), cnt * sizeof(double), cudaMemcpyDefault, st) : e;
+    };
     CKC(cudaMemsetAsync(sums.p, 0, 4 * sizeof(double), st));
     for (uint64_t c0 = 0; c0 < NC; c0 += chunk) {
         const int cnt = (int)std::min<uint64_t>(chunk, NC - c0);
         CKC(surrogate(f_corr + c0, cnt));
         cv_sums_kernel<<<256, 256, 0, st>>>(cnt, gc.f(), res->target_scale, fc.d() + c0, sums.d());
         CKC(cudaGetLastError());
+        CKC(export_g(cfg->g_correct ? cfg->g_correct + c0 : nullptr, cnt));
     }
     double sc[4];
     CKC(cudaMemcpyAsync(sc, sums.p, sizeof sc, cudaMemcpyDeviceToHost, st));
@@ -601,6 +617,7 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
         CKC(surrogate(f_sur + c0, cnt));
         cv_sums_kernel<<<256, 256, 0, st>>>(cnt, gc.f(), res->target_scale, nullptr, sums.d());
         CKC(cudaGetLastError());
+        CKC(export_g(cfg->g_surrogate ? cfg->g_surrogate + c0 : nullptr, cnt));
     }
     CKC(cudaMemcpyAsync(sc, sums.p, sizeof sc, cudaMemcpyDeviceToHost, st));
     CKC(cudaStreamSynchronize(st));

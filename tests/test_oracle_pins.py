@@ -101,7 +101,9 @@ def test_dense_matches_variable_elimination(kind, n, dmin, dmax, extra):
     for p in range(6):
         a = O.trace_pair(d, p, "dense")
         b = O.trace_pair(d, p, "ve")
+        c = O.trace_pair(d, p, "ve_greedy")       # the same sums in min-degree order
         assert abs(a - b) <= 1e-12 * max(1.0, abs(a))
+        assert abs(a - c) <= 1e-12 * max(1.0, abs(a))
 
 
 # --------------------------------------------------------------------------
@@ -574,3 +576,29 @@ def test_design_layers_on_the_theory_bound():
     slope1 = (res[40] - res[20]) / 20
     slope2 = (res[80] - res[40]) / 40
     assert abs(slope1 / slope2 - 1) < 0.05       # linear in n
+
+
+# --------------------------------------------------------------------------
+# Control-variate estimator of F^(2) (the estimand of Sec. "Frame potential";
+# F = mean_M g + mean_N (f - g), stderr^2 = Var g / M + Var (f - g) / N).
+# --------------------------------------------------------------------------
+def test_cv_estimator_hand_example():
+    # f - g = (1, 0, 2): mean 1, variance 1; surrogate g = (1, 3): mean 2, variance 2;
+    # F = 3, stderr = sqrt(2/2 + 1/3); plain: mean f = 3, Var f = 3, stderr 1
+    r = O.cv_estimate([1, 2, 3], [2, 2, 5], [1, 3])
+    assert r["F"] == 3.0 and abs(r["stderr"] - math.sqrt(1 + 1 / 3)) < 1e-15
+    assert r["F_plain"] == 3.0 and r["var_f"] == 3.0 and r["stderr_plain"] == 1.0
+    assert r["var_f_minus_g"] == 1.0 and r["var_g"] == 2.0
+
+
+def test_cv_estimator_special_cases():
+    rng = np.random.default_rng(3)
+    f = rng.exponential(size=1000) ** 2
+    gs = rng.normal(size=500)
+    # a perfect predictor on the correction pairs: the estimate is the surrogate mean
+    r = O.cv_estimate(f, f, gs)
+    assert abs(r["F"] - gs.mean()) < 1e-12 and abs(r["stderr"] - gs.std(ddof=1) / math.sqrt(500)) < 1e-12
+    # g = 0: the plain estimator
+    r = O.cv_estimate(np.zeros(1000), f, np.zeros(500))
+    assert abs(r["F"] - f.mean()) < 1e-12 and abs(r["stderr"] - r["stderr_plain"]) < 1e-15
+    assert abs(r["stderr_plain"] - f.std(ddof=1) / math.sqrt(1000)) < 1e-12
