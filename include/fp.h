@@ -85,7 +85,8 @@ typedef enum {
     FP_ERR_CUDA = -2,         /* CUDA runtime error (message in fp_last_error) */
     FP_ERR_OOM = -3,          /* device or host allocation failed */
     FP_ERR_TIMEOUT = -4,      /* a bounded device wait ran out */
-    FP_ERR_INFEASIBLE = -5    /* a pair's boundary exceeds FP_MAX_STATE_BITS */
+    FP_ERR_INFEASIBLE = -5,   /* a pair's boundary exceeds FP_MAX_STATE_BITS */
+    FP_ERR_CANCELLED = -6     /* fp_cancel stopped a Monte Carlo run between batches */
 } fp_status;
 
 typedef enum { FP_PARALLEL = 0, FP_LOCAL = 1, FP_HEA = 2, FP_HEA_PAULI = 3 } fp_kind;
@@ -294,6 +295,55 @@ fp_status fp_exact_brickwork_fkq(int32_t n, int32_t l, int32_t k, int32_t q, voi
 fp_status fp_frame_potential(fp_ensemble *ens, uint64_t first, uint64_t max_pairs, int32_t k_max,
                              double target_rel_stderr, int32_t prec, double *F, double *stderr_,
                              fp_run_stats *stats);
+
+/* Checkpoint of a Monte Carlo run (fp_frame_potential_resume).  The paper's
+ * adaptive sample sizes (Supplementary Methods, "Determination of sample
+ * sizes") add samples to stored ones until the error bars are small enough;
+ * this state is what such a run needs to continue later or elsewhere.
+ * Before the first call: next_pair = the run's first pair, next_batch = 0,
+ * sums zero.  Every completed batch updates it, so after an error or a
+ * cancellation it holds the last completed batch. */
+typedef struct {
+    uint64_t next_pair;       /* first pair of the next batch */
+    uint64_t next_batch;      /* size of the next batch (0: the run has not started) */
+    uint64_t pairs_done;      /* pairs taken so far (contracted + infeasible) */
+    int32_t k_max, n_groups;  /* set by the first call; a resume must use the same k_max */
+    double *sums;             /* caller-owned host array of 2 * n_groups * (2*k_max+1) doubles:
+                                 the FP64 moment sums per group (layout of fp_reduce_moments),
+                                 then their Neumaier compensations */
+    fp_run_stats stats;       /* accumulated over all calls of the run */
+} fp_checkpoint;
+
+/* The Monte Carlo driver of fp_frame_potential, resumable: continues the run
+ * in *ck with batches of the same schedule (so a run split over several calls
+ * gives bit-identical F and stderr to one uninterrupted call) until the target
+ * is met, pairs_done reaches max_pairs, or max_batches batches (0: no limit)
+ * have run in this call.  F and stderr_ as in fp_frame_potential, from all
+ * batches so far.  FP_ERR_CANCELLED (checkpoint intact) when fp_cancel was
+ * called; the cancellation is consumed by that return. */
+fp_status fp_frame_potential_resume(fp_ensemble *ens, fp_checkpoint *ck, uint64_t max_pairs, uint64_t max_batches,
+                                    int32_t k_max, double target_rel_stderr, int32_t prec, double *F,
+                                    double *stderr_);
+
+/* Ask a running (or the next) Monte Carlo run of this ensemble to stop before
+ * its next batch (fp_frame_potential / fp_frame_potential_resume return
+ * FP_ERR_CANCELLED).  Safe to call from another host thread. */
+fp_status fp_cancel(fp_ensemble *ens);
+
+/* Fault injection for tests of the error paths (host side; no device fault):
+ * the next `count` device allocations of ensemble workspaces fail as if the
+ * device were out of memory, so the call returns FP_ERR_OOM and leaves the
+ * ensemble usable.  0 clears it. */
+fp_status fp_inject_alloc_failures(int32_t count);
+
+/* Time limit of every bounded device wait (mbarrier waits of the tcgen05
+ * kernels), in nanoseconds of the device's global timer; 0 restores the
+ * default of 1 s.  A wait that runs out makes the kernel stop issuing work,
+ * drain what it issued (within a fixed 1 s), release its tensor memory and
+ * raise a device flag that the call reports as FP_ERR_TIMEOUT.  Applies to
+ * launches made after the call (captured CUDA graphs keep the limit they
+ * were captured with). */
+fp_status fp_set_wait_limit_ns(uint64_t ns);
 
 /* Copy the ensemble's kernel counters into *out; reset them if `reset`. */
 fp_status fp_kernel_stats_get(fp_ensemble *ens, fp_kernel_stats *out, int32_t reset);

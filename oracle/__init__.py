@@ -81,6 +81,12 @@ def lib():
             L.orc_moments.argtypes = [P(ctypes.c_double), ctypes.c_int64, ctypes.c_int,
                                       P(ctypes.c_double), P(ctypes.c_double)]
             L.orc_weingarten_f2_brickwork.argtypes = [ctypes.c_int, ctypes.c_int]
+            L.orc_haar_uq.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                      P(ctypes.c_double)]
+            L.orc_haar_uq.restype = None
+            for fn in (L.orc_trace_qudit_dense, L.orc_trace_qudit_ve):
+                fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                               P(ctypes.c_double)]
             L.orc_cv_estimate.argtypes = [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int64,
                                           P(ctypes.c_double), ctypes.c_int64, P(ctypes.c_double)]
             L.orc_cv_estimate.restype = None
@@ -191,6 +197,24 @@ def moments(tr, kmax):
     se = np.zeros(kmax)
     lib().orc_moments(_dp(t), len(tr), kmax, _dp(F), _dp(se))
     return F, se
+
+
+def haar_uq(q, seed, pair, which, gate):
+    """Haar U(q^2) gate g of circuit `which` of a qudit pair (orc_haar_uq), q^2 x q^2 complex."""
+    d = q * q
+    out = np.zeros(2 * d * d)
+    lib().orc_haar_uq(q, seed, pair, which, gate, _dp(out))
+    return (out[0::2] + 1j * out[1::2]).reshape(d, d)
+
+
+def trace_qudit(q, n, l, seed, pair, method="ve", self_pair=False):
+    """Tr(U^dagger V) of pair `pair` of the depth-l qudit brickwork ensemble (method 'dense' or 've')."""
+    tr = np.zeros(2)
+    fn = lib().orc_trace_qudit_dense if method == "dense" else lib().orc_trace_qudit_ve
+    rc = fn(q, n, l, seed, pair, int(self_pair), _dp(tr))
+    if rc:
+        raise RuntimeError(f"oracle qudit trace failed: {rc}")
+    return complex(tr[0], tr[1])
 
 
 def cv_estimate(g_corr, f_corr, g_sur):

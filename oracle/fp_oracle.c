@@ -929,3 +929,258 @@ double orc_weingarten_f2_brickwork(int n, int l)
     free(times); free(g_of_bond); free(v); free(w);
     return result;
 }
+
+/* ======================================================================== */
+/* Qudit brickwork (the paper states its method for local dimension q: Sec.  */
+/* "Frame potential" and the qudit paragraph of Sec. "Algorithm             */
+/* description"; the Haar gates are U(q^2)).  Open chain of n qudits, layer  */
+/* t acting on bonds b = (t-1) mod 2, b+2, ...; qudit 0 is the most         */
+/* significant digit; a gate on (b, b+1) has matrix index a_b q + a_{b+1}.   */
+/* Gate g of circuit w of a pair: the d x d complex Gaussian (d = q^2),      */
+/* entry k = d r + c from Philox block c0 = k/2, c1 = g, stream = w, words   */
+/* (x0, x1) for even k and (x2, x3) for odd k (the qubit rule for d = 4),    */
+/* then classical Gram-Schmidt QR with positive-real R diagonal.             */
+/* ======================================================================== */
+void orc_haar_uq(int q, uint64_t seed, uint64_t pair, int which, int gate, double *out)
+{
+    const int d = q * q;
+    cplx *Z = malloc(sizeof(cplx) * d * d), *Q = malloc(sizeof(cplx) * d * d), *v = malloc(sizeof(cplx) * d);
+    for (int k = 0; k < d * d; ++k) {
+        uint64_t w[4];
+        draw(seed, (uint64_t)(k / 2), (uint64_t)gate, pair, (uint64_t)which, w);
+        uint64_t xa = (k % 2 == 0) ? w[0] : w[2];
+        uint64_t xb = (k % 2 == 0) ? w[1] : w[3];
+        double u1 = (double)((xa >> 11) + 1) * 0x1.0p-53;
+        double u2 = (double)(xb >> 11) * 0x1.0p-53;
+        double rad = sqrt(-2.0 * log(u1));
+        Z[k] = (rad * cos(2.0 * ORC_PI * u2) + I * rad * sin(2.0 * ORC_PI * u2)) / sqrt(2.0);
+    }
+    for (int c = 0; c < d; ++c) {
+        for (int r = 0; r < d; ++r) v[r] = Z[d * r + c];
+        for (int j = 0; j < c; ++j) {
+            cplx dot = 0;
+            for (int r = 0; r < d; ++r) dot += conj(Q[d * r + j]) * Z[d * r + c];
+            for (int r = 0; r < d; ++r) v[r] -= dot * Q[d * r + j];
+        }
+        double nrm = 0;
+        for (int r = 0; r < d; ++r) nrm += creal(v[r] * conj(v[r]));
+        nrm = sqrt(nrm);
+        for (int r = 0; r < d; ++r) Q[d * r + c] = v[r] / nrm;
+    }
+    for (int k = 0; k < d * d; ++k) { out[2 * k] = creal(Q[k]); out[2 * k + 1] = cimag(Q[k]); }
+    free(Z); free(Q); free(v);
+}
+
+/* the gates of one circuit: bonds[g] and matrices gates[g * 2 d^2 ...] */
+static int qudit_circuit(int q, int n, int l, uint64_t seed, uint64_t pair, int which, int *bonds, double *gates)
+{
+    const int d = q * q;
+    int g = 0;
+    for (int t = 1; t <= l; ++t)
+        for (int b = (t - 1) % 2; b <= n - 2; b += 2) {
+            bonds[g] = b;
+            orc_haar_uq(q, seed, pair, which, g, gates + (size_t)g * 2 * d * d);
+            ++g;
+        }
+    return g;
+}
+
+static int qudit_gate_count(int n, int l)
+{
+    int g = 0;
+    for (int t = 1; t <= l; ++t)
+        for (int b = (t - 1) % 2; b <= n - 2; b += 2) ++g;
+    return g;
+}
+
+/* Tr(U^dagger V) = sum_ij conj(U_ij) V_ij with U, V built densely (q^n x q^n). */
+int orc_trace_qudit_dense(int q, int n, int l, uint64_t seed, uint64_t pair, int self_pair, double tr[2])
+{
+    size_t D = 1;
+    for (int i = 0; i < n; ++i) D *= (size_t)q;
+    if (D > 4096) return -1;
+    const int d = q * q, G = qudit_gate_count(n, l);
+    int *bonds = malloc(sizeof(int) * (G > 0 ? G : 1));
+    double *gates = malloc(sizeof(double) * 2 * d * d * (G > 0 ? G : 1));
+    cplx *M[2];
+    for (int w = 0; w < 2; ++w) {
+        M[w] = calloc(D * D, sizeof(cplx));
+        for (size_t i = 0; i < D; ++i) M[w][i * D + i] = 1;
+        qudit_circuit(q, n, l, seed, pair, self_pair ? 0 : w, bonds, gates);
+        for (int g = 0; g < G; ++g) {
+            const cplx *U = (const cplx *)(gates + (size_t)g * 2 * d * d);
+            size_t s1 = 1;                                 /* place value of qudit b+1 */
+            for (int i = bonds[g] + 2; i < n; ++i) s1 *= (size_t)q;
+            size_t s0 = s1 * (size_t)q;                    /* qudit b */
+            cplx *a = malloc(sizeof(cplx) * d);
+            for (size_t col = 0; col < D; ++col)
+                for (size_t r = 0; r < D; ++r) {
+                    if ((r / s0) % q != 0 || (r / s1) % q != 0) continue;   /* r: both digits zero */
+                    for (int e = 0; e < d; ++e) a[e] = M[w][(r + (e / q) * s0 + (e % q) * s1) * D + col];
+                    for (int o = 0; o < d; ++o) {
+                        cplx acc = 0;
+                        for (int e = 0; e < d; ++e) acc += U[o * d + e] * a[e];
+                        M[w][(r + (o / q) * s0 + (o % q) * s1) * D + col] = acc;
+                    }
+                }
+            free(a);
+        }
+    }
+    cplx s = 0;
+    for (size_t i = 0; i < D * D; ++i) s += conj(M[0][i]) * M[1][i];
+    tr[0] = creal(s); tr[1] = cimag(s);
+    free(M[0]); free(M[1]); free(bonds); free(gates);
+    return 0;
+}
+
+/* Variable elimination over q-ary wire segments (the qubit elimination with   */
+/* digits in place of bits): every gate of U^dagger V cuts the wires of its    */
+/* two qudits; a segment is a q-ary variable; a gate is a factor over its two  */
+/* output and two input segments; the sums run in min-degree order.            */
+typedef struct { int nv; int *vars; cplx *t; } qfactor;
+
+static size_t ipow(int q, int e) { size_t r = 1; while (e-- > 0) r *= (size_t)q; return r; }
+
+int orc_trace_qudit_ve(int q, int n, int l, uint64_t seed, uint64_t pair, int self_pair, double tr[2])
+{
+    const int d = q * q, G = qudit_gate_count(n, l), T = 2 * G;
+    int *bonds[2];
+    double *gates[2];
+    for (int w = 0; w < 2; ++w) {
+        bonds[w] = malloc(sizeof(int) * (G > 0 ? G : 1));
+        gates[w] = malloc(sizeof(double) * 2 * d * d * (G > 0 ? G : 1));
+        qudit_circuit(q, n, l, seed, pair, self_pair ? 0 : w, bonds[w], gates[w]);
+    }
+    /* time order of U^dagger V: V's gates, then U's gates last to first, daggered */
+    int *sb = malloc(sizeof(int) * (T > 0 ? T : 1));
+    cplx *sg = malloc(sizeof(cplx) * d * d * (T > 0 ? T : 1));
+    for (int g = 0; g < G; ++g) {
+        sb[g] = bonds[1][g];
+        memcpy(&sg[(size_t)g * d * d], gates[1] + (size_t)g * 2 * d * d, sizeof(cplx) * d * d);
+        const cplx *u = (const cplx *)(gates[0] + (size_t)(G - 1 - g) * 2 * d * d);
+        sb[G + g] = bonds[0][G - 1 - g];
+        for (int r = 0; r < d; ++r)
+            for (int c = 0; c < d; ++c) sg[(size_t)(G + g) * d * d + r * d + c] = conj(u[c * d + r]);
+    }
+    int *s = calloc(n, sizeof(int)), *base = calloc(n + 1, sizeof(int)), *pos = malloc(sizeof(int) * 2 * (T > 0 ? T : 1));
+    for (int t = 0; t < T; ++t) { pos[2 * t] = s[sb[t]]++; pos[2 * t + 1] = s[sb[t] + 1]++; }
+    for (int i = 0; i < n; ++i) base[i + 1] = base[i] + (s[i] > 0 ? s[i] : 1);
+    const int nvars = base[n];
+    int nf = T, capf = T + 8;
+    qfactor *fs = calloc(capf, sizeof(qfactor));
+    for (int t = 0; t < T; ++t) {
+        int vo[2], vi[2];
+        for (int i = 0; i < 2; ++i) {
+            int qq = sb[t] + i, sq = s[qq];
+            vo[i] = base[qq] + pos[2 * t + i];
+            vi[i] = base[qq] + (pos[2 * t + i] - 1 + sq) % sq;
+        }
+        /* factor over (out_b, out_b1, in_b, in_b1): entry = G[(o_b q + o_b1), (i_b q + i_b1)];  */
+        /* a segment that is both input and output of the gate (a qudit with one gate) is one  */
+        /* variable: the factor then keeps the diagonal                                        */
+        int all[4] = {vo[0], vo[1], vi[0], vi[1]}, uv[4], nu = 0, map[4];
+        for (int k = 0; k < 4; ++k) {
+            int j;
+            for (j = 0; j < nu; ++j) if (uv[j] == all[k]) break;
+            if (j == nu) uv[nu++] = all[k];
+            map[k] = j;
+        }
+        fs[t].nv = nu;
+        fs[t].vars = malloc(sizeof(int) * nu);
+        memcpy(fs[t].vars, uv, sizeof(int) * nu);
+        size_t sz = ipow(q, nu);
+        fs[t].t = malloc(sizeof(cplx) * sz);
+        for (size_t x = 0; x < sz; ++x) {
+            int val[4], dv[4];
+            size_t y = x;
+            for (int j = 0; j < nu; ++j) { dv[j] = (int)(y % q); y /= q; }
+            for (int k = 0; k < 4; ++k) val[k] = dv[map[k]];
+            fs[t].t[x] = sg[(size_t)t * d * d + (val[0] * q + val[1]) * d + (val[2] * q + val[3])];
+        }
+    }
+    cplx scalar = 1;
+    char *gone = calloc(nvars > 0 ? nvars : 1, 1);
+    int *uvars = malloc(sizeof(int) * (nvars + 8)), *sel = malloc(sizeof(int) * (capf + 1));
+    for (int step = 0; step < nvars; ++step) {
+        int best = -1, best_w = 1 << 30;
+        for (int c = 0; c < nvars; ++c) {
+            if (gone[c]) continue;
+            int nu = 0;
+            for (int f = 0; f < nf; ++f) {
+                if (!fs[f].t) continue;
+                int has = 0;
+                for (int k = 0; k < fs[f].nv; ++k) has |= fs[f].vars[k] == c;
+                if (!has) continue;
+                for (int k = 0; k < fs[f].nv; ++k) {
+                    int u;
+                    for (u = 0; u < nu; ++u) if (uvars[u] == fs[f].vars[k]) break;
+                    if (u == nu) uvars[nu++] = fs[f].vars[k];
+                }
+            }
+            if (nu < best_w) { best_w = nu; best = c; }
+        }
+        const int v = best;
+        gone[v] = 1;
+        int ns = 0;
+        for (int f = 0; f < nf; ++f) {
+            if (!fs[f].t) continue;
+            for (int k = 0; k < fs[f].nv; ++k) if (fs[f].vars[k] == v) { sel[ns++] = f; break; }
+        }
+        if (ns == 0) { scalar *= q; continue; }        /* a free wire loop: Tr(I_q) */
+        int nu = 0;
+        uvars[nu++] = v;
+        for (int i = 0; i < ns; ++i)
+            for (int k = 0; k < fs[sel[i]].nv; ++k) {
+                int u;
+                for (u = 0; u < nu; ++u) if (uvars[u] == fs[sel[i]].vars[k]) break;
+                if (u == nu) uvars[nu++] = fs[sel[i]].vars[k];
+            }
+        const int nr = nu - 1;
+        const size_t rsz = ipow(q, nr);
+        cplx *res = malloc(sizeof(cplx) * rsz);
+        int *dig = malloc(sizeof(int) * nu);
+        for (size_t r = 0; r < rsz; ++r) {
+            size_t y = r;
+            for (int j = 1; j < nu; ++j) { dig[j] = (int)(y % q); y /= q; }
+            cplx acc = 0;
+            for (int x = 0; x < q; ++x) {
+                dig[0] = x;
+                cplx p = 1;
+                for (int i = 0; i < ns; ++i) {
+                    const qfactor *f = &fs[sel[i]];
+                    size_t idx = 0, pw = 1;
+                    for (int k = 0; k < f->nv; ++k) {
+                        int u;
+                        for (u = 0; u < nu; ++u) if (uvars[u] == f->vars[k]) break;
+                        idx += (size_t)dig[u] * pw;
+                        pw *= (size_t)q;
+                    }
+                    p *= f->t[idx];
+                }
+                acc += p;
+            }
+            res[r] = acc;
+        }
+        free(dig);
+        for (int i = 0; i < ns; ++i) {
+            free(fs[sel[i]].t); fs[sel[i]].t = NULL;
+            free(fs[sel[i]].vars); fs[sel[i]].vars = NULL;
+        }
+        if (nf >= capf) {
+            capf *= 2;
+            fs = realloc(fs, sizeof(qfactor) * capf);
+            sel = realloc(sel, sizeof(int) * (capf + 1));
+        }
+        qfactor *nfac = &fs[nf++];
+        nfac->nv = nr;
+        nfac->vars = malloc(sizeof(int) * (nr > 0 ? nr : 1));
+        memcpy(nfac->vars, uvars + 1, sizeof(int) * nr);
+        nfac->t = res;
+    }
+    for (int f = 0; f < nf; ++f)
+        if (fs[f].t) { scalar *= fs[f].t[0]; free(fs[f].t); free(fs[f].vars); }
+    tr[0] = creal(scalar); tr[1] = cimag(scalar);
+    free(fs); free(gone); free(uvars); free(sel); free(s); free(base); free(pos); free(sb); free(sg);
+    for (int w = 0; w < 2; ++w) { free(bonds[w]); free(gates[w]); }
+    return 0;
+}

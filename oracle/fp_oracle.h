@@ -117,6 +117,14 @@ double orc_weingarten_fkq_brickwork(int n, int l, int k, int q);
 void   orc_bootstrap(const double *tr, const int32_t *group, int64_t count, int n_groups, int kmax,
                      int B, uint64_t seed, double *F_boot);
 
+/* Qudit brickwork (local dimension q, Haar U(q^2) gates; see fp_oracle.c):
+ * the Haar sampler (out: 2 q^4 doubles), Tr(U^dagger V) of pair `pair` of
+ * depth l densely (q^n <= 4096) or by variable elimination over q-ary wire
+ * segments in min-degree order. */
+void   orc_haar_uq(int q, uint64_t seed, uint64_t pair, int which, int gate, double *out);
+int    orc_trace_qudit_dense(int q, int n, int l, uint64_t seed, uint64_t pair, int self_pair, double tr[2]);
+int    orc_trace_qudit_ve(int q, int n, int l, uint64_t seed, uint64_t pair, int self_pair, double tr[2]);
+
 #ifdef __cplusplus
 }
 #endif

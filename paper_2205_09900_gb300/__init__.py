@@ -25,12 +25,13 @@ K_NAMES = {0: "sample", 1: "merge", 2: "tables", 3: "sweep_generic", 4: "sweep_b
            6: "bootstrap", 7: "sweep_spiral"}
 MAX_STATE_BITS = 24
 STATUS = {0: "FP_OK", -1: "FP_ERR_ARG", -2: "FP_ERR_CUDA", -3: "FP_ERR_OOM", -4: "FP_ERR_TIMEOUT",
-          -5: "FP_ERR_INFEASIBLE"}
+          -5: "FP_ERR_INFEASIBLE", -6: "FP_ERR_CANCELLED"}
 
 EXPORTED = ["fp_ensemble_create", "fp_ensemble_destroy", "fp_groups", "fp_pair_groups", "fp_export_gates",
             "fp_trace_batch", "fp_reduce_moments", "fp_frame_potential", "fp_kernel_stats_get",
             "fp_trace_brick_static", "fp_cv_frame_potential", "fp_gemm_bf16", "fp_bootstrap", "fp_epsilon_max",
             "fp_design_layers", "fp_exact_brickwork_fk", "fp_exact_brickwork_fkq", "fp_measure_peak",
+            "fp_frame_potential_resume", "fp_cancel", "fp_inject_alloc_failures", "fp_set_wait_limit_ns",
             "fp_last_error"]
 
 
@@ -51,6 +52,12 @@ class RunStats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_uint64), ("fp64_recontracted", ctypes.c_uint64),
                 ("gpu_seconds", ctypes.c_double), ("max_kappa", ctypes.c_double),
                 ("n_groups", ctypes.c_int32), ("reached_target", ctypes.c_int32), ("infeasible", ctypes.c_uint64)]
+
+
+class Checkpoint(ctypes.Structure):
+    _fields_ = [("next_pair", ctypes.c_uint64), ("next_batch", ctypes.c_uint64), ("pairs_done", ctypes.c_uint64),
+                ("k_max", ctypes.c_int32), ("n_groups", ctypes.c_int32), ("sums", ctypes.c_void_p),
+                ("stats", RunStats)]
 
 
 class KernelStats(ctypes.Structure):
@@ -110,6 +117,10 @@ def load(path: str = LIB_PATH):
     L.fp_exact_brickwork_fk.argtypes = [i32, i32, i32, vp, P(f64)]
     L.fp_exact_brickwork_fkq.argtypes = [i32, i32, i32, i32, vp, P(f64)]
     L.fp_measure_peak.argtypes = [i32, i32, vp, vp]
+    L.fp_frame_potential_resume.argtypes = [vp, P(Checkpoint), u64, u64, i32, f64, i32, vp, vp]
+    L.fp_cancel.argtypes = [vp]
+    L.fp_inject_alloc_failures.argtypes = [i32]
+    L.fp_set_wait_limit_ns.argtypes = [u64]
     L.fp_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name not in ("fp_ensemble_destroy", "fp_last_error"):
@@ -181,6 +192,16 @@ def measure_peak(which, iters=0, stream=None):
     _check(load().fp_measure_peak(which, iters, st, _ptr(out)))
     return {"tflops": float(out[0]), "ms": float(out[1]), "sm_mhz": float(out[2]),
             "flops_per_clk_sm": float(out[3]), "sms": int(out[4])}
+
+
+def inject_alloc_failures(count):
+    """The next `count` device allocations of ensemble workspaces fail (fp_inject_alloc_failures)."""
+    _check(load().fp_inject_alloc_failures(count))
+
+
+def set_wait_limit_ns(ns):
+    """Time limit of every bounded device wait (fp_set_wait_limit_ns; 0: default 1 s)."""
+    _check(load().fp_set_wait_limit_ns(ns))
 
 
 def epsilon_max_log10(F, k, n, q=2):
@@ -314,6 +335,29 @@ class Ensemble:
         res = CvResult()
         _check(load().fp_cv_frame_potential(self._h, ctypes.byref(cfg), ctypes.byref(res)))
         return res
+
+    def checkpoint(self, first, k_max):
+        """A fresh run state for frame_potential_resume (keeps its sums array alive)."""
+        import numpy as np
+        ck = Checkpoint()
+        ck.next_pair = first
+        ck._sums = np.zeros(2 * len(self.groups()) * (2 * k_max + 1))
+        ck.sums = ck._sums.ctypes.data
+        return ck
+
+    def frame_potential_resume(self, ck, max_pairs, k_max, target_rel_stderr=0.0, prec=PREC_FP64, max_batches=0):
+        """Continue the run in `ck` (fp_frame_potential_resume); returns (F, stderr, stats)."""
+        import numpy as np
+        ng = len(self.groups())
+        F = np.zeros(ng * k_max)
+        se = np.zeros(ng * k_max)
+        _check(load().fp_frame_potential_resume(self._h, ctypes.byref(ck), max_pairs, max_batches, k_max,
+                                                target_rel_stderr, prec, _ptr(F), _ptr(se)))
+        return F.reshape(ng, k_max), se.reshape(ng, k_max), ck.stats
+
+    def cancel(self):
+        """Stop a running (or the next) Monte Carlo run before its next batch (fp_cancel)."""
+        _check(load().fp_cancel(self._h))
 
     def frame_potential(self, first, max_pairs, k_max, target_rel_stderr=0.0, prec=PREC_FP64):
         import numpy as np

@@ -51,6 +51,12 @@ fp_status fail(fp_status s, const char *fmt, ...) {
                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
     } while (0)
 
+// Host-side fault injection (fp_inject_alloc_failures): the next N device
+// allocations of ensemble buffers fail as if the device were out of memory.
+std::atomic<int> g_alloc_failures{0};
+// Time limit of every bounded device wait (fp_set_wait_limit_ns).
+std::atomic<uint64_t> g_wait_ns{1000000000ull};
+
 // Device buffer that grows on demand.
 struct DBuf {
     void *p = nullptr;
@@ -61,6 +67,8 @@ struct DBuf {
         if (p) cudaFree(p);
         p = nullptr;
         bytes = 0;
+        for (int f = g_alloc_failures.load(); f > 0;)
+            if (g_alloc_failures.compare_exchange_weak(f, f - 1)) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaMalloc(&p, b);
         if (e == cudaSuccess) bytes = b;
         return e;
@@ -82,6 +90,7 @@ bool is_device_ptr(const void *p) {
 
 namespace fpk {
 void set_last_error(const char *msg) { g_err = msg; }
+uint64_t wait_limit_ns() { return g_wait_ns.load(); }
 }  // namespace fpk
 
 struct GraphKey {
@@ -140,6 +149,7 @@ struct fp_ensemble {
     DBuf d_spiral_scratch;
     DBuf d_maps, d_states;
     DBuf d_flag;               // device error flag of kernels with bounded waits (zero when clear)
+    std::atomic<int> cancel{0};   // fp_cancel: checked by the Monte Carlo driver between batches
     std::string gpu_name;
     // CUDA graphs of the brickwork sub-batch pipeline
     cudaStream_t gst = nullptr;
@@ -511,7 +521,10 @@ fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int T
                            std::unique_ptr<BrickCache> &out) {
     auto bc = std::make_unique<BrickCache>();
     // K > N: shared-memory sweep, K == N: one tile
-    bc->hp = make_brick_plan(E->d.n, l, K, fp32 ? 5 : 4, R, E->d.kind == FP_HEA ? 1 : 0);
+    // arcs hold the 5 (FP32) or 4 (FP64) lowest bits, so that tile loads read contiguous runs;
+    // the tensor-core pass (12-bit tiles) holds 3: at l = 10 a 12-bit arc through the 5
+    // lowest bits would need 49 passes instead of 18
+    bc->hp = make_brick_plan(E->d.n, l, K, persist == 2 ? 3 : (fp32 ? 5 : 4), R, E->d.kind == FP_HEA ? 1 : 0);
     for (const auto &ps : bc->hp.passes) {
         if (ps.n_gates > 255) return fail(FP_ERR_ARG, "tile pass with %d gates exceeds 255", ps.n_gates);
         if (ps.n_rp > 160) return fail(FP_ERR_ARG, "tile pass with %d register passes exceeds 160", ps.n_rp);
@@ -1214,48 +1227,32 @@ fp_status fp_bootstrap(fp_ensemble *ens, const double *tr, const int32_t *group,
     return FP_OK;
 }
 
-fp_status fp_frame_potential(fp_ensemble *ens, uint64_t first, uint64_t max_pairs, int32_t k_max,
-                             double target_rel_stderr, int32_t prec, double *F, double *stderr_,
-                             fp_run_stats *stats) {
-    if (!ens || !F || !stderr_) return fail(FP_ERR_ARG, "null argument");
+fp_status fp_frame_potential_resume(fp_ensemble *ens, fp_checkpoint *ck, uint64_t max_pairs, uint64_t max_batches,
+                                    int32_t k_max, double target_rel_stderr, int32_t prec, double *F,
+                                    double *stderr_) {
+    if (!ens || !ck || !ck->sums || !F || !stderr_) return fail(FP_ERR_ARG, "null argument");
     if (k_max < 1 || k_max > FP_MAX_KMAX) return fail(FP_ERR_ARG, "k_max = %d outside [1, %d]", k_max, FP_MAX_KMAX);
     if (prec < FP_PREC_FP64 || prec > FP_PREC_FP32_RAW) return fail(FP_ERR_ARG, "unknown precision %d", prec);
     const int ng = ens->n_groups, nv = 2 * k_max + 1;
-    std::vector<double> acc((size_t)ng * nv, 0.0), comp((size_t)ng * nv, 0.0), part((size_t)ng * nv);
-    fp_run_stats st;
-    std::memset(&st, 0, sizeof st);
+    if (ck->next_batch == 0) {   // first call of a run
+        ck->k_max = k_max;
+        ck->n_groups = ng;
+        ck->pairs_done = 0;
+        std::memset(&ck->stats, 0, sizeof ck->stats);
+        // with a target: batches from 4096 pairs, doubling, so the stop can come early;
+        // without one: batches as large as the workspace allows
+        ck->next_batch = target_rel_stderr > 0 ? 4096 : (1u << 20);
+    } else if (ck->k_max != k_max || ck->n_groups != ng) {
+        return fail(FP_ERR_ARG, "checkpoint of k_max = %d, %d groups resumed with k_max = %d, %d groups", ck->k_max,
+                    ck->n_groups, k_max, ng);
+    }
+    double *acc = ck->sums, *comp = ck->sums + (size_t)ng * nv;
+    std::vector<double> part((size_t)ng * nv);
+    fp_run_stats &st = ck->stats;
     st.n_groups = ng;
     const int kt = k_max >= 2 ? 2 : 1;
-    // with a target: batches from 4096 pairs, doubling, so the stop can come early;
-    // without one: batches as large as the workspace allows
-    uint64_t batch = target_rel_stderr > 0 ? 4096 : (1u << 20), done = 0;
-    bool reached = false;
-    while (done < max_pairs && !reached) {
-        uint64_t nb = std::min<uint64_t>(batch, max_pairs - done);
-        float ms = 0;
-        fp_status s = trace_device(ens, first + done, nb, prec, &ms, &st.fp64_recontracted, &st.max_kappa);
-        if (s != FP_OK) return s;
-        st.infeasible += ens->skipped.size();
-        st.gpu_seconds += ms * 1e-3;
-        int nb_blocks = moments_blocks(nb);
-        CK(ens->d_partials.reserve((size_t)nb_blocks * ng * nv * sizeof(double)));
-        CK(ens->d_moments.reserve((size_t)ng * nv * sizeof(double)));
-        {
-            KTimer t(ens, FP_K_MOMENTS);
-            CK(launch_moments(ens->d_tr.as<double>(), ens->d_group.as<int32_t>(), nb, k_max, ng,
-                              ens->d_partials.as<double>(), nb_blocks, ens->d_moments.as<double>(), ens->st));
-            CK(t.stop((double)nb));
-        }
-        CK(cudaMemcpyAsync(part.data(), ens->d_moments.p, part.size() * sizeof(double), cudaMemcpyDeviceToHost, ens->st));
-        CK(cudaStreamSynchronize(ens->st));
-        for (size_t i = 0; i < part.size(); ++i) {   // Neumaier accumulation across batches
-            double y = acc[i] + part[i];
-            comp[i] += std::fabs(acc[i]) >= std::fabs(part[i]) ? (acc[i] - y) + part[i] : (part[i] - y) + acc[i];
-            acc[i] = y;
-        }
-        done += nb;
-        st.pairs = done - st.infeasible;
-        reached = target_rel_stderr > 0;
+    auto estimate = [&]() {   // F, stderr from the sums; whether every group met the target
+        bool ok = target_rel_stderr > 0;
         for (int g = 0; g < ng; ++g) {
             double N = acc[g * nv] + comp[g * nv];
             for (int k = 1; k <= k_max; ++k) {
@@ -1267,12 +1264,85 @@ fp_status fp_frame_potential(fp_ensemble *ens, uint64_t first, uint64_t max_pair
                 stderr_[g * k_max + k - 1] = N > 1 ? std::sqrt(var / N) : NAN;
             }
             double f = F[g * k_max + kt - 1], e = stderr_[g * k_max + kt - 1];
-            if (!(N > 1 && f > 0 && e / f <= target_rel_stderr)) reached = false;
+            if (!(N > 1 && f > 0 && e / f <= target_rel_stderr)) ok = false;
         }
-        if (batch < (1u << 20)) batch *= 2;
+        return ok;
+    };
+    bool reached = ck->pairs_done > 0 && estimate();
+    for (uint64_t nbatches = 0; ck->pairs_done < max_pairs && !reached && (max_batches == 0 || nbatches < max_batches);
+         ++nbatches) {
+        if (ens->cancel.exchange(0)) {
+            estimate();
+            return fail(FP_ERR_CANCELLED, "cancelled before the batch at pair %llu (the checkpoint can be resumed)",
+                        (unsigned long long)ck->next_pair);
+        }
+        uint64_t nb = std::min<uint64_t>(ck->next_batch, max_pairs - ck->pairs_done);
+        float ms = 0;
+        uint64_t recon = 0;
+        double mk = 0;
+        fp_status s = trace_device(ens, ck->next_pair, nb, prec, &ms, &recon, &mk);
+        if (s != FP_OK) return s;
+        int nb_blocks = moments_blocks(nb);
+        CK(ens->d_partials.reserve((size_t)nb_blocks * ng * nv * sizeof(double)));
+        CK(ens->d_moments.reserve((size_t)ng * nv * sizeof(double)));
+        {
+            KTimer t(ens, FP_K_MOMENTS);
+            CK(launch_moments(ens->d_tr.as<double>(), ens->d_group.as<int32_t>(), nb, k_max, ng,
+                              ens->d_partials.as<double>(), nb_blocks, ens->d_moments.as<double>(), ens->st));
+            CK(t.stop((double)nb));
+        }
+        CK(cudaMemcpyAsync(part.data(), ens->d_moments.p, part.size() * sizeof(double), cudaMemcpyDeviceToHost, ens->st));
+        CK(cudaStreamSynchronize(ens->st));
+        // the batch is complete: fold it into the checkpoint
+        for (size_t i = 0; i < part.size(); ++i) {   // Neumaier accumulation across batches
+            double y = acc[i] + part[i];
+            comp[i] += std::fabs(acc[i]) >= std::fabs(part[i]) ? (acc[i] - y) + part[i] : (part[i] - y) + acc[i];
+            acc[i] = y;
+        }
+        st.fp64_recontracted += recon;
+        st.max_kappa = std::max(st.max_kappa, mk);
+        st.infeasible += ens->skipped.size();
+        st.gpu_seconds += ms * 1e-3;
+        ck->pairs_done += nb;
+        ck->next_pair += nb;
+        st.pairs = ck->pairs_done - st.infeasible;
+        if (ck->next_batch < (1u << 20)) ck->next_batch *= 2;
+        reached = estimate();
     }
+    if (ck->pairs_done == 0) estimate();
     st.reached_target = reached ? 1 : 0;
-    if (stats) *stats = st;
+    return FP_OK;
+}
+
+fp_status fp_frame_potential(fp_ensemble *ens, uint64_t first, uint64_t max_pairs, int32_t k_max,
+                             double target_rel_stderr, int32_t prec, double *F, double *stderr_,
+                             fp_run_stats *stats) {
+    if (!ens || !F || !stderr_) return fail(FP_ERR_ARG, "null argument");
+    if (k_max < 1 || k_max > FP_MAX_KMAX) return fail(FP_ERR_ARG, "k_max = %d outside [1, %d]", k_max, FP_MAX_KMAX);
+    std::vector<double> sums((size_t)2 * ens->n_groups * (2 * k_max + 1), 0.0);
+    fp_checkpoint ck;
+    std::memset(&ck, 0, sizeof ck);
+    ck.next_pair = first;
+    ck.sums = sums.data();
+    fp_status s = fp_frame_potential_resume(ens, &ck, max_pairs, 0, k_max, target_rel_stderr, prec, F, stderr_);
+    if (s == FP_OK && stats) *stats = ck.stats;
+    return s;
+}
+
+fp_status fp_cancel(fp_ensemble *ens) {
+    if (!ens) return fail(FP_ERR_ARG, "null argument");
+    ens->cancel.store(1);
+    return FP_OK;
+}
+
+fp_status fp_inject_alloc_failures(int32_t count) {
+    if (count < 0) return fail(FP_ERR_ARG, "count < 0");
+    g_alloc_failures.store(count);
+    return FP_OK;
+}
+
+fp_status fp_set_wait_limit_ns(uint64_t ns) {
+    g_wait_ns.store(ns ? ns : 1000000000ull);
     return FP_OK;
 }
 

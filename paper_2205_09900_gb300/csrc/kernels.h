@@ -86,6 +86,9 @@ cudaError_t launch_spiral(const PairInfo *pairs, int npairs, const SpiralMap *sm
                           const SpiralConfig &cfg, const SpiralWin *wins, int nwins, const uint8_t *ij, const int *h,
                           const double2 *merged, void *maps, void *scratch, bool fp32, double err_scale, double *tr,
                           double *kappa, double *err, cudaStream_t st);
+// Time limit of one bounded device wait (nanoseconds of the global timer):
+// fp_set_wait_limit_ns, default 1 s.
+uint64_t wait_limit_ns();
 // Set the thread-local message returned by fp_last_error().
 void set_last_error(const char *msg);
 // Internal access for the control-variate driver (cv.cu).
@@ -118,6 +121,7 @@ struct TcGemm {
     __nv_bfloat16 *Cbt;
     int ldct;
     int *err;
+    uint64_t wait_ns;   // bounded-wait limit (set at launch from wait_limit_ns())
 };
 const char *tc_gemm_check(const TcGemm &g);   // nullptr if the arguments are valid
 cudaError_t launch_tc_gemm(const TcGemm &g, cudaStream_t st);

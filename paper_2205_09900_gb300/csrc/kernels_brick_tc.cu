@@ -3,7 +3,7 @@
 // The FFMA tile pass applies the gates of each register window (5 ring bits
 // of a 12-bit tile) one 4x4 map at a time.  Here the window's gates are first
 // multiplied into one dense 32 x 32 complex matrix W per (pair, window)
-// (tc_wmat_kernel, FP64 products of the FP32 maps), and the tile, viewed as a
+// (tc_wmat_kernel, FP32 products of the FP32 maps), and the tile, viewed as a
 // [128 rows x 32] complex matrix whose rows are the 7 other tile bits, is
 // multiplied by W^T on the tensor cores: complex numbers as real pairs (K
 // columns 2j, 2j+1 hold re, im of window index j; W as the real 64 x 64 block
@@ -36,7 +36,7 @@
 namespace fpk {
 namespace {
 
-constexpr uint64_t kTcWaitNs = 1000000000ull;
+constexpr uint64_t kTcDrainNs = 1000000000ull;   // waits for work already issued (after a timeout)
 constexpr int kTcThreads = 256;
 constexpr int kMaxTcWins = 48;
 constexpr uint32_t kAOp = 32768;                 // bytes of one A operand (hi or lo) of one tile
@@ -51,7 +51,7 @@ __device__ __forceinline__ uint64_t gtimer() {
 }
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, uint64_t limit_ns) {
     const uint64_t t0 = gtimer();
     for (;;) {
         uint32_t d;
@@ -62,7 +62,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
             : "r"(mbar), "r"(phase)
             : "memory");
         if (d) return true;
-        if (gtimer() - t0 > kTcWaitNs) return false;
+        if (gtimer() - t0 > limit_ns) return false;
     }
 }
 
@@ -79,20 +79,20 @@ __device__ __forceinline__ float tf32_rna(float x) {
 
 // ---------------------------------------------------------------------------
 // Window matrices: W = G_last ... G_first of the window's gates (4x4 maps on
-// window bits (k, k+1)), column j built by thread j in FP64, stored as the B
+// window bits (k, k+1)), column j built by thread j in FP32, stored as the B
 // operand of the MMA: rows n = 2o (re, -im) and 2o + 1 (im, re) of output o,
 // K columns 2j, 2j + 1, K-major with the 128-byte swizzle in two regions of
 // 64 rows x 128 bytes; hi part then lo part.
 template <int k>
-__device__ __forceinline__ void wapply(double2 (&v)[32], const double2 *__restrict__ T) {
+__device__ __forceinline__ void wapply(float2 (&v)[32], const float2 *__restrict__ T) {
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
         if (i & (3 << k)) continue;
-        const double2 x0 = v[i], x1 = v[i | (1 << k)], x2 = v[i | (2 << k)], x3 = v[i | (3 << k)];
+        const float2 x0 = v[i], x1 = v[i | (1 << k)], x2 = v[i | (2 << k)], x3 = v[i | (3 << k)];
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
-            const double2 t0 = T[4 * o], t1 = T[4 * o + 1], t2 = T[4 * o + 2], t3 = T[4 * o + 3];
-            double2 a;
+            const float2 t0 = T[4 * o], t1 = T[4 * o + 1], t2 = T[4 * o + 2], t3 = T[4 * o + 3];
+            float2 a;
             a.x = t0.x * x0.x - t0.y * x0.y + t1.x * x1.x - t1.y * x1.y + t2.x * x2.x - t2.y * x2.y + t3.x * x3.x -
                   t3.y * x3.y;
             a.y = t0.x * x0.y + t0.y * x0.x + t1.x * x1.y + t1.y * x1.x + t2.x * x2.y + t2.y * x2.x + t3.x * x3.y +
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(32) tc_wmat_kernel(BrickDev d, int side, Brick
                                                      const BrickGate *__restrict__ gates,
                                                      const RegPass *__restrict__ rps, const RegGate *__restrict__ rgs,
                                                      const float2 *__restrict__ maps, float *__restrict__ wm) {
-    __shared__ double2 T[kMaxTcWins][16];
+    __shared__ float2 T[kMaxTcWins][16];
     const RegPass rp = rps[ps.rp_off + blockIdx.x];
     const int ng = rp.n_gates < kMaxTcWins ? rp.n_gates : kMaxTcWins;
     const float2 *mp = maps + (size_t)blockIdx.y * maps_per_pair(d) * 16;
@@ -118,13 +118,13 @@ __global__ void __launch_bounds__(32) tc_wmat_kernel(BrickDev d, int side, Brick
         const RegGate rg = rgs[rp.gate_off + i / 16];
         const BrickGate gg = gates[ps.gate_off + rg.slot];
         const float2 v = mp[(size_t)map_index(d, side, gg.layer, gg.j) * 16 + (i % 16)];
-        T[i / 16][i % 16] = make_double2(v.x, v.y);
+        T[i / 16][i % 16] = v;
     }
     __syncwarp();
     const int j = threadIdx.x;
-    double2 v[32];
+    float2 v[32];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    for (int i = 0; i < 32; ++i) v[i] = make_float2(i == j ? 1.f : 0.f, 0.f);
     for (int g = 0; g < ng; ++g) {
         switch (rgs[rp.gate_off + g].type) {
             case 0: wapply<0>(v, T[g]); break;
@@ -136,9 +136,9 @@ __global__ void __launch_bounds__(32) tc_wmat_kernel(BrickDev d, int side, Brick
     unsigned char *out = (unsigned char *)(wm + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kWFloats);
 #pragma unroll
     for (int o = 0; o < 32; ++o) {
-        const float re = (float)v[o].x, im = (float)v[o].y;
+        const float re = v[o].x, im = v[o].y;
         const float rh = tf32_rna(re), ih = tf32_rna(im);
-        const float rl = tf32_rna((float)(v[o].x - (double)rh)), il = tf32_rna((float)(v[o].y - (double)ih));
+        const float rl = tf32_rna(re - rh), il = tf32_rna(im - ih);
         const uint32_t a0 = wb_addr(2 * o, 2 * j), a1 = wb_addr(2 * o + 1, 2 * j);
         *(float2 *)(out + a0) = make_float2(rh, -ih);
         *(float2 *)(out + a1) = make_float2(ih, rh);
@@ -228,7 +228,7 @@ __device__ __forceinline__ void drain_tile(uint32_t tm, const TcWin &cw, const u
 
 __global__ void __launch_bounds__(kTcThreads, 1)
     brick_tc_pass_kernel(BrickDev d, int side, BrickPass ps, const TcWin *__restrict__ wins,
-                         const float *__restrict__ wm, float2 *__restrict__ states, int *err) {
+                         const float *__restrict__ wm, float2 *__restrict__ states, int *err, uint64_t wait_ns) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t wbar[2], mbar[2], fbar;
     __shared__ uint32_t taddr_sh;
@@ -291,19 +291,40 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             bulk_load(sW + b * kWMat, wp + (size_t)b * kWFloats, kWMat, &wbar[b]);
             ++tma_issued[b];
         }
-    // both tiles: boundary -> A operands of window 0
+    // both tiles: boundary -> A operands of window 0.  Every element copy of
+    // both tiles is in flight at once (cp.async into tile Y's operand space,
+    // X raw in its hi part, Y raw in its lo part), then each thread converts
+    // the elements it copied: X straight into its operands; Y through
+    // registers, as its operands overlap the staging space.
     float2 *st = states + ((size_t)blockIdx.y * 2 + side) * S;
     const uint32_t gb[2] = {tile_base_of(2 * blockIdx.x, ps.smask, N), tile_base_of(2 * blockIdx.x + 1, ps.smask, N)};
+    constexpr int kPer = (1 << kTcTile) / kTcThreads;
+    float2 *stage = (float2 *)(smem + 2 * kAOp);
 #pragma unroll
-    for (int tt = 0; tt < 2; ++tt) {
-        unsigned char *A = smem + tt * 2 * kAOp;
-        const float2 *src = st + gb[tt];
-#pragma unroll 4
-        for (int m = 0; m < (1 << kTcTile) / kTcThreads; ++m) {
+    for (int tt = 0; tt < 2; ++tt)
+#pragma unroll
+        for (int m = 0; m < kPer; ++m) {
             const uint32_t i = tid + (uint32_t)m * kTcThreads;
-            const float2 x = src[lut_lo[i & 127] | lut_hi[i >> 7]];
-            st_hilo(A, alo[i & 127] ^ ahi[i >> 7], x.x, x.y);
+            const uint32_t d = smem_u32(stage + tt * (1 << kTcTile) + i);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d),
+                         "l"(st + gb[tt] + (lut_lo[i & 127] | lut_hi[i >> 7]))
+                         : "memory");
         }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+#pragma unroll
+    for (int m = 0; m < kPer; ++m) {
+        const uint32_t i = tid + (uint32_t)m * kTcThreads;
+        const float2 x = stage[i];
+        st_hilo(smem, alo[i & 127] ^ ahi[i >> 7], x.x, x.y);
+    }
+    float2 yv[kPer];
+#pragma unroll
+    for (int m = 0; m < kPer; ++m) yv[m] = stage[(1 << kTcTile) + tid + m * kTcThreads];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < kPer; ++m) {
+        const uint32_t i = tid + (uint32_t)m * kTcThreads;
+        st_hilo(smem + 2 * kAOp, alo[i & 127] ^ ahi[i >> 7], yv[m].x, yv[m].y);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -311,7 +332,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int w = 0; w < nw; ++w) {
         // MMAs of tile X, window w
         if (tid == 0) {
-            if (!mbar_wait(smem_u32(&wbar[w & 1]), (uint32_t)(w >> 1) & 1u)) {
+            if (!mbar_wait(smem_u32(&wbar[w & 1]), (uint32_t)(w >> 1) & 1u, wait_ns)) {
                 abort_sh = 1;
             } else {
                 ++tma_waited[w & 1];
@@ -323,7 +344,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         // tile Y: result of window w-1 -> operands of window w
         if (w > 0) {
-            if (!mbar_wait(smem_u32(&mbar[1]), (uint32_t)(w - 1) & 1u)) abort_sh = 1;
+            if (!mbar_wait(smem_u32(&mbar[1]), (uint32_t)(w - 1) & 1u, wait_ns)) abort_sh = 1;
             else {
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 drain_tile(taddr + 64, sw[w - 1], sw[w].cb, smem + 2 * kAOp, nullptr);
@@ -344,7 +365,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             commit_to(&mbar[1]);
         }
         // tile X: result of window w -> operands of window w+1, or the boundary
-        if (!mbar_wait(smem_u32(&mbar[0]), (uint32_t)w & 1u)) abort_sh = 1;
+        if (!mbar_wait(smem_u32(&mbar[0]), (uint32_t)w & 1u, wait_ns)) abort_sh = 1;
         else {
             asm volatile("tcgen05.fence::after_thread_sync;");
             if (w + 1 < nw) drain_tile(taddr, sw[w], sw[w + 1].cb, smem, nullptr);
@@ -357,7 +378,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (!abort_sh) {
         // tile Y: last window's result -> the boundary
-        if (!mbar_wait(smem_u32(&mbar[1]), (uint32_t)(nw - 1) & 1u)) abort_sh = 1;
+        if (!mbar_wait(smem_u32(&mbar[1]), (uint32_t)(nw - 1) & 1u, wait_ns)) abort_sh = 1;
         else {
             asm volatile("tcgen05.fence::after_thread_sync;");
             drain_tile(taddr + 64, sw[nw - 1], gcb, nullptr, st + gb[1]);
@@ -370,10 +391,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (tid == 0) {
             if (issued_any) {
                 commit_to(&fbar);
-                mbar_wait(smem_u32(&fbar), 0u);
+                mbar_wait(smem_u32(&fbar), 0u, kTcDrainNs);
             }
             for (int b = 0; b < 2; ++b)
-                if (tma_issued[b] > tma_waited[b]) mbar_wait(smem_u32(&wbar[b]), (uint32_t)(tma_issued[b] - 1) & 1u);
+                if (tma_issued[b] > tma_waited[b])
+                    mbar_wait(smem_u32(&wbar[b]), (uint32_t)(tma_issued[b] - 1) & 1u, kTcDrainNs);
             atomicExch(err, 1);
         }
     }
@@ -412,7 +434,7 @@ cudaError_t run_passes_tc(const BrickDev &d, const BrickPass *hpasses, const Bri
             tc_wmat_kernel<<<dim3(ps.n_rp, npairs), 32, 0, st>>>(d, side, ps, dp.gates, dp.rpasses, dp.rgates, maps, wm);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             brick_tc_pass_kernel<<<dim3(1u << (d.N - kTcTile - 1), npairs), kTcThreads, kTcSmem, st>>>(
-                d, side, ps, dp.tcwins, wm, states, err);
+                d, side, ps, dp.tcwins, wm, states, err, wait_limit_ns());
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     return cudaSuccess;

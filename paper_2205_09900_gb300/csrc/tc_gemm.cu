@@ -38,7 +38,7 @@ namespace fpk {
 namespace {
 
 constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 128, TC_MAXN = 256, TC_STAGES = 4;
-constexpr long long TC_WAIT_LIMIT = 1LL << 22;
+constexpr uint64_t TC_DRAIN_NS = 1000000000ull;   // waits for work already issued (after a timeout)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -59,8 +59,16 @@ __device__ __forceinline__ uint32_t make_idesc(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-    for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Poll an mbarrier phase until it completes or `limit_ns` of global time pass.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, uint64_t limit_ns) {
+    const uint64_t t0 = gtimer();
+    for (;;) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -70,8 +78,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
             : "r"(mbar), "r"(phase)
             : "memory");
         if (done) return true;
+        if (gtimer() - t0 > limit_ns) return false;
     }
-    return false;
 }
 
 __device__ __forceinline__ float gelu_f(float v) { return 0.5f * v * (1.0f + erff(v * 0.70710678f)); }
@@ -134,11 +142,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcGemm g, const 
     const uint32_t taddr = taddr_sh;
     const int nk = (g.K + TC_BK - 1) / TC_BK;
     const uint32_t sbase = smem_u32(smem);
+    int issued = 0;   // producer: stages whose TMA loads were issued
     if (tid == 0) {
         // producer: TMA loads of stage kt once the MMAs of stage kt - S have drained the buffer
         for (int kt = 0; kt < nk; ++kt) {
             const int s = kt % TC_STAGES, u = kt / TC_STAGES;
-            if (u > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)(u - 1) & 1u)) {
+            if (abort_sh || (u > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)(u - 1) & 1u, g.wait_ns))) {
                 abort_sh = 1;
                 break;
             }
@@ -148,17 +157,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcGemm g, const 
             const uint32_t sa = sbase + s * stage_bytes, sb = sa + a_bytes;
             tma_load(sa, &tmA, kt * TC_BK, m0, fb);
             tma_load(sb, &tmB, kt * TC_BK, n0, fb);
+            ++issued;
         }
+        // after a timeout: wait (bounded) for the loads still in flight, the last
+        // issued phase of each stage buffer
+        if (abort_sh)
+            for (int kt = (issued > TC_STAGES ? issued - TC_STAGES : 0); kt < issued; ++kt)
+                mbar_wait(smem_u32(&full[kt % TC_STAGES]), (uint32_t)(kt / TC_STAGES) & 1u, TC_DRAIN_NS);
     } else if (tid == 32) {
         // MMA issuer: four K = 16 steps per stage, then release the buffer
         const uint32_t idesc = make_idesc(TC_BM, NT);
-        bool ok = true;
+        bool ok = true, any = false;
         for (int kt = 0; kt < nk; ++kt) {
             const int s = kt % TC_STAGES, u = kt / TC_STAGES;
-            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)u & 1u)) {
+            if (abort_sh || !mbar_wait(smem_u32(&full[s]), (uint32_t)u & 1u, g.wait_ns)) {
                 ok = false;
                 break;
             }
+            any = true;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t sa = sbase + s * stage_bytes, sb = sa + a_bytes;
 #pragma unroll
@@ -176,16 +192,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(TcGemm g, const 
                              smem_u32(&empty[s]))
                          : "memory");
         }
-        if (ok)
+        if (!ok) abort_sh = 1;
+        // the last commit covers every MMA issued before it (also after a timeout,
+        // so that none is in flight when the tensor memory is released)
+        if (any)
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&done))
                          : "memory");
         else
-            abort_sh = 1;
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&done)) : "memory");
     }
     __syncwarp();
-    // everyone: wait for the accumulator (the last commit covers every MMA issued before it)
-    if (!mbar_wait(smem_u32(&done), 0u)) abort_sh = 1;
+    // everyone: wait for the accumulator (or, after a timeout, for the MMAs in flight)
+    if (!mbar_wait(smem_u32(&done), 0u, abort_sh ? TC_DRAIN_NS : g.wait_ns)) {
+        abort_sh = 1;
+        mbar_wait(smem_u32(&done), 0u, TC_DRAIN_NS);   // every arrival on `done` is certain: drain
+    }
     __syncthreads();
     if (abort_sh) {
         if (tid == 0 && g.err) atomicExch(g.err, 1);
@@ -321,7 +343,9 @@ cudaError_t launch_tc_gemm(const TcGemm &g, cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     dim3 grid((g.M + TC_BM - 1) / TC_BM, (g.N + TC_MAXN - 1) / TC_MAXN);
-    tc_gemm_kernel<<<grid, TC_THREADS, smem, st>>>(g, ma, mb, boxn);
+    TcGemm gk = g;
+    gk.wait_ns = wait_limit_ns();
+    tc_gemm_kernel<<<grid, TC_THREADS, smem, st>>>(gk, ma, mb, boxn);
     return cudaGetLastError();
 }
 

@@ -60,7 +60,7 @@ static void apply4(std::vector<cd> &s, int N, int pa, int pb, const cd *T) {
 
 int main(int argc, char **argv) {
     const int n = atoi(argv[1]), l = atoi(argv[2]);
-    BrickHostPlan P = make_brick_plan(n, l, kTcTile, 5, kMaxWin, 0);
+    BrickHostPlan P = make_brick_plan(n, l, kTcTile, 3, kMaxWin, 0);   // the plan the tensor-core pass runs
     const BrickDev &d = P.dev;
     const int N = d.N;
     const uint32_t S = 1u << N;

@@ -602,3 +602,60 @@ def test_cv_estimator_special_cases():
     r = O.cv_estimate(np.zeros(1000), f, np.zeros(500))
     assert abs(r["F"] - f.mean()) < 1e-12 and abs(r["stderr"] - r["stderr_plain"]) < 1e-15
     assert abs(r["stderr_plain"] - f.std(ddof=1) / math.sqrt(1000)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Qudit brickwork (local dimension q = 3, Haar U(9) gates).
+# --------------------------------------------------------------------------
+def test_qudit_haar_sampler_moments():
+    # Haar U(d), d = 9: E|U_ij|^2 = 1/d, E|U_ij|^4 = 2/(d(d+1)); unitary to rounding
+    us = [O.haar_uq(3, 5, p, w, g) for p in range(40) for w in (0, 1) for g in range(25)]
+    d = 9
+    for U in us[:20]:
+        assert np.abs(U.conj().T @ U - np.eye(d)).max() < 1e-13
+    a = np.array([np.abs(U) ** 2 for U in us])
+    assert abs(a.mean() - 1 / d) < 1e-12                  # rows of a unitary: exact
+    m4 = (a ** 2).mean()
+    se = (a ** 2).std() / math.sqrt(a.size / d)           # entries of a row are correlated
+    assert abs(m4 - 2 / (d * (d + 1))) < 5 * se
+
+
+@pytest.mark.parametrize("n,l", [(2, 1), (3, 2), (4, 3), (5, 2), (6, 3), (5, 4)])
+def test_qudit_dense_matches_elimination(n, l):
+    for p in range(4):
+        a = O.trace_qudit(3, n, l, 19, p, "dense")
+        b = O.trace_qudit(3, n, l, 19, p, "ve")
+        assert abs(a - b) <= 1e-12 * max(1.0, abs(a))
+
+
+def test_qudit_self_pair_is_dimension():
+    # V = U: Tr(U^dagger U) = q^n exactly, at the benchmark's size
+    for l in (2, 3, 4):
+        t = O.trace_qudit(3, 50, l, 3, 1, "ve", self_pair=True)
+        assert abs(t / 3.0 ** 50 - 1) < 1e-12
+
+
+@pytest.mark.parametrize("n", [4, 7, 50])
+def test_qudit_one_layer_product_form(n):
+    # l = 1: U and V are products of the gates on bonds 0, 2, 4, ...; Tr(U^dagger V)
+    # is the product of Tr(G_U^dagger G_V) over them, times q for an idle last qudit
+    for p in range(3):
+        expect = 1.0 + 0j
+        for g, b in enumerate(range(0, n - 1, 2)):
+            gu, gv = O.haar_uq(3, 23, p, 0, g), O.haar_uq(3, 23, p, 1, g)
+            expect *= np.trace(gu.conj().T @ gv)
+        if n % 2:
+            expect *= 3
+        t = O.trace_qudit(3, n, 1, 23, p, "ve")
+        assert abs(t - expect) <= 1e-11 * max(1.0, abs(expect))
+
+
+def test_qudit_monte_carlo_matches_exact_weingarten():
+    # the qudit traces against the oracle's exact qutrit F^(2) (Weingarten transfer
+    # matrix, pinned separately): n = 4, l = 2, 20,000 dense pairs, 5 sigma
+    tr = np.array([O.trace_qudit(3, 4, 2, 31, p, "dense") for p in range(20000)])
+    x = np.abs(tr) ** 4
+    F, se = x.mean(), x.std(ddof=1) / math.sqrt(len(x))
+    assert abs(np.mean(np.abs(tr) ** 2) - 1.0) < 5 * np.std(np.abs(tr) ** 2) / math.sqrt(len(x))
+    exact = O.weingarten_fk_brickwork(4, 2, 2, q=3)
+    assert abs(F - exact) < 5 * se, (F, se, exact)
