@@ -147,6 +147,12 @@ typedef struct {
     double fp32_tol;          /* FP_PREC_FP32: recontract in FP64 when the estimated
                                  absolute error of Tr exceeds this; <= 0: 1e-4 */
     uint64_t workspace_bytes; /* device workspace cap; 0: library default, min(32 GB, free/2) */
+    int32_t q;                /* local dimension: 0 or 2 = qubits; 3 or 4 = qudits (FP_PARALLEL
+                                 only: Haar U(q^2) gates, gate g of circuit w drawn as the
+                                 q^2 x q^2 Gaussian whose entry k takes Philox block c0 = k/2,
+                                 c1 = g, stream = w, words as for qubits; depth l >= 2;
+                                 boundary q^{2(l-1)} amplitudes, at most 2^FP_MAX_STATE_BITS) */
+    int32_t reserved;
 } fp_ensemble_desc;
 
 /* Error estimate of one trace (the `err` output of fp_trace_batch): with
@@ -198,7 +204,9 @@ fp_status fp_groups(const fp_ensemble *ens, int32_t *n_groups, int32_t *values);
 fp_status fp_pair_groups(const fp_ensemble *ens, uint64_t first, uint64_t count, int32_t *group);
 
 /* Sampled gates of circuit `which` (0 = U, 1 = V) of one pair, as they enter
- * the contraction: per gate a record {int32 kind, int32 qubit, 32 doubles =
+ * the contraction (the circuits of the ensembles of Fig. 2, Sec. "Results";
+ * the paper draws U and V independently from the ensemble, Sec. "Frame
+ * potential"); an input feed for independent checks of the traces: per gate a record {int32 kind, int32 qubit, 32 doubles =
  * 16 complex entries (re,im)}, kind 0 = 4x4 on (q,q+1), 1 = 2x2 on q in the
  * first 4 entries, 2 = diagonal 2-qubit (4 entries).  FP_HEA_PAULI with CNOT
  * walls lists each CNOT as H on the target, CZ, H on the target (the form
@@ -208,7 +216,10 @@ fp_status fp_pair_groups(const fp_ensemble *ens, uint64_t first, uint64_t count,
 fp_status fp_export_gates(fp_ensemble *ens, uint64_t pair, int32_t which, void *host_buf,
                           size_t *bytes);
 
-/* Contract pairs first..first+count-1.
+/* Contract pairs first..first+count-1: every pair's Tr(U^dagger V), the closed
+ * trace network of U^dagger V contracted exactly along the qubit chain (Sec.
+ * "Algorithm description", Fig. 3a; the paper's samples |Tr(U^dagger V)|^{2k}
+ * of the frame potential, Sec. "Frame potential").
  *   tr     [2*count] doubles: Tr(U^dagger V) as (re, im) per pair;
  *   kappa  [count] doubles or NULL: cancellation ratio sum_j |L_j R_j| / |sum_j L_j R_j|
  *          of the final boundary dot product (1 when no cancellation);
@@ -221,7 +232,9 @@ fp_status fp_export_gates(fp_ensemble *ens, uint64_t pair, int32_t which, void *
 fp_status fp_trace_batch(fp_ensemble *ens, uint64_t first, uint64_t count, int32_t prec,
                          double *tr, double *kappa, double *err, int32_t *group);
 
-/* FP64 moments of |Tr|^{2k} per group (the reduction of the estimator):
+/* FP64 moments of |Tr|^{2k} per group: the sums behind the Monte Carlo
+ * estimate F^(k) ~= (1/N) sum |Tr|^{2k} and its standard error (Sec.
+ * "Algorithm description"; the paper's error bars are standard errors):
  * moments[g*(2*k_max+1) + 0] = N_g, [.. + k] = sum |Tr|^{2k}, [.. + k_max + k] =
  * sum |Tr|^{4k}, for k = 1..k_max.  tr/group as produced by fp_trace_batch,
  * on the device; moments on host or device.  Deterministic (fixed tree). */
@@ -350,11 +363,12 @@ fp_status fp_kernel_stats_get(fp_ensemble *ens, fp_kernel_stats *out, int32_t re
 
 /* Learned control variate for F^(2) (the paper has none; the estimate is the
  * paper's F^(2), Sec. "Frame potential").  For a single-depth HEA ensemble
- * (depth_min == depth_max == L) an MLP g -- input the 4nL angles of both
- * circuits as 2u-1 (u the uniform draw of each angle), three hidden layers of
- * `hidden` units with GELU, one output -- is trained (Adam, mean squared
- * error on |Tr|^4 divided by its training mean) on n_train exactly contracted
- * pairs, then
+ * (depth_min == depth_max == L) an MLP -- input 12 features per (layer,
+ * qubit): cos and sin of both circuits' theta and phi and of their
+ * differences; three hidden layers of `hidden` units with GELU; one output --
+ * is trained (Adam, mean squared error) on the normalised log |Tr|^2 of
+ * n_train exactly contracted pairs; g = beta exp(2 x prediction) predicts
+ * |Tr|^4, beta = Cov(f, g) / Var(g) on the training pairs.  Then
  *     F^(2) = mean over m_surrogate pairs of g + mean over n_correct pairs of (|Tr|^4 - g),
  * the three pair ranges consecutive from `first` and disjoint, so the
  * estimate is unbiased for any g; stderr_ = sqrt(Var g / M + Var(f - g) / N).
@@ -380,7 +394,7 @@ typedef struct {
     double F2, stderr_;               /* control-variate estimate and its standard error */
     double F2_plain, stderr_plain;    /* plain estimate on the correction pairs */
     double var_f, var_f_minus_g, var_g;   /* per-pair variances */
-    double target_scale;              /* training mean of |Tr|^4 (g's unit) */
+    double target_scale;              /* the fitted coefficient beta of g */
     double train_loss;                /* last epoch's mean squared error (scaled units) */
     double gpu_seconds_exact;         /* device time of the exact contractions */
     double gpu_seconds_train;         /* device time of feature generation and training */

@@ -45,7 +45,8 @@ class Desc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("depth_min", ctypes.c_int32),
                 ("depth_max", ctypes.c_int32), ("T_min", ctypes.c_int32), ("T_max", ctypes.c_int32),
                 ("T_step", ctypes.c_int32), ("flags", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("kappa_max", ctypes.c_double), ("fp32_tol", ctypes.c_double), ("workspace_bytes", ctypes.c_uint64)]
+                ("kappa_max", ctypes.c_double), ("fp32_tol", ctypes.c_double), ("workspace_bytes", ctypes.c_uint64),
+                ("q", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class RunStats(ctypes.Structure):
@@ -226,10 +227,10 @@ class Ensemble:
     """One ensemble of circuit pairs (``fp_ensemble``)."""
 
     def __init__(self, kind, n, depth_min=1, depth_max=None, T_min=0, T_max=0, T_step=1, seed=1,
-                 flags=0, kappa_max=0.0, fp32_tol=0.0, workspace_bytes=0, stream=None):
+                 flags=0, kappa_max=0.0, fp32_tol=0.0, workspace_bytes=0, stream=None, q=2):
         L = load()
         self.desc = Desc(kind, n, depth_min, depth_min if depth_max is None else depth_max, T_min, T_max,
-                         T_step, flags, seed, kappa_max, fp32_tol, workspace_bytes)
+                         T_step, flags, seed, kappa_max, fp32_tol, workspace_bytes, q, 0)
         h = ctypes.c_void_p()
         st = None if stream is None else ctypes.c_void_p(stream)
         _check(L.fp_ensemble_create(ctypes.byref(self.desc), st, ctypes.byref(h)))

@@ -911,9 +911,68 @@ __global__ void mark_skipped_kernel(const uint64_t *slots, uint64_t n, double *t
     err[s] = NAN;
 }
 
+// Qudit brickwork pairs of one depth l: sampler, maps, sweep and meet
+// (kernels_qudit.cu), in sub-batches under the workspace budget.
+fp_status run_qudit(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx, int l, int prec, double *tr,
+                    double *kappa, double *err, float *gpu_ms) {
+    const fp_ensemble_desc &d = E->d;
+    const uint64_t count = idx.size();
+    if (count == 0) return FP_OK;
+    const bool fp32 = prec != FP_PREC_FP64;
+    const BrickDev bd = make_brick_plan(d.n, l, 0, 0, 0, 0).dev;
+    double S = 1;
+    for (int i = 0; i < bd.N; ++i) S *= d.q;
+    if (S > (double)(1u << FP_MAX_STATE_BITS))
+        return fail(FP_ERR_INFEASIBLE, "qudit depth %d: boundary of %d^%d amplitudes exceeds 2^%d", l, d.q, bd.N,
+                    FP_MAX_STATE_BITS);
+    const int n_raw = (int)layout_brickwork(d.n, l).size();
+    const size_t per_pair = qudit_workspace_per_pair(d.q, bd, n_raw, fp32);
+    const uint64_t cap = std::max<uint64_t>(1, std::min<uint64_t>(65535, E->ws_budget / per_pair));
+    const double G = (double)std::max(bd.n_layers[0], bd.n_layers[1]) * bd.m;
+    const double err_scale = FP_ERR_SAFETY * (fp32 ? 0x1.0p-24 : 0x1.0p-53) * std::sqrt(G);
+    const double cmac_pair = (double)maps_per_pair(bd) * S * d.q * d.q;   // each map: S/q^2 groups of q^4
+    for (uint64_t done = 0; done < count;) {
+        const uint64_t nb = std::min<uint64_t>(cap, count - done);
+        std::vector<PairInfo> pinfo(nb);
+        for (uint64_t i = 0; i < nb; ++i) {
+            std::memset(&pinfo[i], 0, sizeof(PairInfo));
+            pinfo[i].pair = first + idx[done + i];
+            pinfo[i].n_raw = n_raw;
+            pinfo[i].out = (int64_t)idx[done + i];
+        }
+        CK(upload(E->d_pairs, pinfo, E->st));
+        CK(E->d_states.reserve(nb * per_pair));
+        CK(cudaEventRecord(E->ev0, E->st));
+        {
+            KTimer t(E, FP_K_BRICK);
+            CK(launch_qudit(d.q, bd, d.seed, E->d_pairs.as<PairInfo>(), (int)nb, n_raw,
+                            (d.flags & FP_FLAG_SELF_PAIR) ? 1 : 0, fp32, E->d_states.p, err_scale, tr, kappa, err,
+                            E->st));
+            CK(t.stop(cmac_pair * (double)nb, 3));
+        }
+        CK(cudaEventRecord(E->ev1, E->st));
+        CK(cudaEventSynchronize(E->ev1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, E->ev0, E->ev1));
+        if (gpu_ms) *gpu_ms += ms;
+        E->kst.pairs += nb;
+        done += nb;
+    }
+    return FP_OK;
+}
+
 fp_status route(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx, const std::vector<int> &depth,
                 int prec, double *tr, double *kappa, double *err, float *gpu_ms) {
     const fp_ensemble_desc &d = E->d;
+    if (d.q > 2) {   // qudit brickwork: its own sweep, per depth
+        std::map<int, std::vector<uint64_t>> qd;
+        for (uint64_t i : idx) qd[depth[i]].push_back(i);
+        for (auto it = qd.rbegin(); it != qd.rend(); ++it) {
+            fp_status s = run_qudit(E, first, it->second, it->first, prec, tr, kappa, err, gpu_ms);
+            if (s != FP_OK) return s;
+        }
+        return FP_OK;
+    }
     const bool brick = (d.kind == FP_PARALLEL || d.kind == FP_HEA) && !(d.flags & FP_FLAG_GENERIC_ONLY);
     const bool spiral = d.kind == FP_HEA_PAULI && !(d.flags & (FP_FLAG_GENERIC_ONLY | FP_FLAG_HEA_CZ));
     const bool skip = (d.flags & FP_FLAG_SKIP_INFEASIBLE) != 0;
@@ -1049,6 +1108,12 @@ fp_status fp_ensemble_create(const fp_ensemble_desc *desc, void *cuda_stream, fp
         return fail(FP_ERR_ARG, "FP_FLAG_DIAGONAL_GATES applies to Haar-gate ensembles only");
     if ((d.flags & FP_FLAG_HEA_CZ) && d.kind != FP_HEA_PAULI)
         return fail(FP_ERR_ARG, "FP_FLAG_HEA_CZ applies to FP_HEA_PAULI only");
+    if (d.q != 0 && d.q != 2 && !(d.kind == FP_PARALLEL && (d.q == 3 || d.q == 4)))
+        return fail(FP_ERR_ARG, "local dimension q = %d: qudits (q = 3, 4) are supported for FP_PARALLEL only", d.q);
+    if (d.q > 2 && (d.flags & (FP_FLAG_DIAGONAL_GATES | FP_FLAG_GENERIC_ONLY)))
+        return fail(FP_ERR_ARG, "FP_FLAG_DIAGONAL_GATES and FP_FLAG_GENERIC_ONLY apply to qubits only");
+    if (d.q > 2 && d.depth_min < 2)
+        return fail(FP_ERR_ARG, "qudit brickwork needs depth >= 2 (at depth 1 the trace is the product of the gates' traces)");
     std::unique_ptr<fp_ensemble> E(new fp_ensemble());
     E->d = d;
     E->st = (cudaStream_t)cuda_stream;
@@ -1113,6 +1178,7 @@ fp_status fp_pair_groups(const fp_ensemble *ens, uint64_t first, uint64_t count,
 fp_status fp_export_gates(fp_ensemble *ens, uint64_t pair, int32_t which, void *host_buf, size_t *bytes) {
     if (!ens || !bytes || (which != 0 && which != 1)) return fail(FP_ERR_ARG, "bad argument");
     const fp_ensemble_desc &d = ens->d;
+    if (d.q > 2) return fail(FP_ERR_ARG, "gates of qudit ensembles are not exported (records hold 4x4 matrices)");
     int depth = depth_of_pair(d, pair);
     int n_raw = 0;
     std::vector<GateSlot> lay = circuit_layout(d, pair, which, depth, &n_raw);

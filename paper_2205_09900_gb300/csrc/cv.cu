@@ -1,8 +1,10 @@
 // cv.cu -- learned control variate for F^(2) of single-depth HEA ensembles.
 //
-// A small MLP g maps a pair's circuit angles to a prediction of |Tr|^4.  It is
-// trained on exactly contracted pairs, evaluated on many cheap surrogate
-// pairs, and corrected on fresh exactly contracted pairs:
+// A small MLP maps periodic features of a pair's circuit angles to a
+// prediction of log |Tr|^2; g = beta exp(2 prediction) predicts |Tr|^4, with
+// beta = Cov(f, g) / Var(g) fitted on the training pairs.  The MLP is trained
+// on exactly contracted pairs, g is evaluated on many cheap surrogate pairs and
+// corrected on fresh exactly contracted pairs:
 //     F^(2) ~= mean_M g(x) + mean_N (f(x) - g(x)),   f = |Tr(U^dagger V)|^4,
 // with the three pair ranges disjoint, so the estimate stays unbiased for any
 // g; its variance is Var(g)/M + Var(f - g)/N.  The plain estimator mean_N f on
@@ -36,20 +38,66 @@ using bf16 = __nv_bfloat16;
 using fpk::U64x4;
 using fpk::philox;
 
-// features: u in [0,1) of every angle of both circuits, mapped to 2u - 1, in
-// column ((w * L + t) * n + q) * 2 + a  (a = 0: theta, 1: phi) of the row-major
-// [count x ldx] BF16 matrix X (columns >= 4nL untouched)
+// features of one pair, 12 per (layer t, qubit q), column 12 (t n + q) + f:
+// cos and sin of U's theta and phi, of V's theta and phi, and of the
+// differences theta_U - theta_V, phi_U - phi_V (the trace depends on the angles
+// periodically; at one layer |Tr|^2 is a product over qubits of
+// (1 + cos dtheta)(1 + cos dphi)), into the row-major [count x ldx] BF16 matrix
+// X (columns >= 12 n L untouched)
 __global__ void features_kernel(uint64_t seed, uint64_t first, int count, int n, int L, bf16 *X, int ldx) {
-    const long long total = (long long)count * (2 * L * n);
+    const long long total = (long long)count * L * n;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int p = (int)(i / (2 * L * n));
-        const int r = (int)(i % (2 * L * n));
-        const int w = r / (L * n), t = (r / n) % L, q = r % n;
-        U64x4 x = philox(seed, (uint64_t)t, (uint64_t)q, first + p, (uint64_t)w);
-        const int c = ((w * L + t) * n + q) * 2;
-        X[(size_t)p * ldx + c] = __float2bfloat16(2.0f * (float)((double)(x.x[0] >> 11) * 0x1.0p-53) - 1.0f);
-        X[(size_t)p * ldx + c + 1] = __float2bfloat16(2.0f * (float)((double)(x.x[1] >> 11) * 0x1.0p-53) - 1.0f);
+        const int p = (int)(i / (L * n));
+        const int r = (int)(i % (L * n));
+        const int t = r / n, q = r % n;
+        float ang[2][2];
+        for (int w = 0; w < 2; ++w) {
+            U64x4 x = philox(seed, (uint64_t)t, (uint64_t)q, first + p, (uint64_t)w);
+            ang[w][0] = (float)((double)(x.x[0] >> 11) * 0x1.0p-53);   // theta / (2 pi)
+            ang[w][1] = (float)((double)(x.x[1] >> 11) * 0x1.0p-53);   // phi / (2 pi)
+        }
+        float f[12];
+        for (int w = 0; w < 2; ++w)
+            for (int a = 0; a < 2; ++a) sincospif(2.0f * ang[w][a], &f[4 * w + 2 * a + 1], &f[4 * w + 2 * a]);
+        for (int a = 0; a < 2; ++a) sincospif(2.0f * (ang[0][a] - ang[1][a]), &f[8 + 2 * a + 1], &f[8 + 2 * a]);
+        bf16 *row = X + (size_t)p * ldx + 12 * r;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) row[k] = __float2bfloat16(f[k]);
     }
+}
+
+// training target: (log(|Tr|^2 + 1e-6) - mu) / sigma
+__global__ void logt_kernel(const double *tr, int count, double mu, double inv_sigma, float *y) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double a2 = tr[2 * i] * tr[2 * i] + tr[2 * i + 1] * tr[2 * i + 1];
+    y[i] = (float)((log(a2 + 1e-6) - mu) * inv_sigma);
+}
+
+// model output -> prediction of |Tr|^4: exp(2 (sigma out + mu))
+__global__ void gtrans_kernel(int count, float *g, float mu, float sigma) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) g[i] = expf(fminf(2.0f * (sigma * g[i] + mu), 80.0f));
+}
+
+// sums over the training pairs for the control-variate coefficient:
+// (g, g^2, f g, f), f = |Tr|^4 from the traces
+__global__ void beta_sums_kernel(int count, const float *g, const double *tr, double *sums) {
+    __shared__ double sh[4][256];
+    double s[4] = {0, 0, 0, 0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const double a2 = tr[2 * i] * tr[2 * i] + tr[2 * i + 1] * tr[2 * i + 1], f = a2 * a2, gv = g[i];
+        s[0] += gv; s[1] += gv * gv; s[2] += f * gv; s[3] += f;
+    }
+    for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) atomicAdd(&sums[k], sh[k][0]);
 }
 
 __global__ void abs4_kernel(const double *tr, int count, double scale, float *y, double *f) {
@@ -327,7 +375,7 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
     const fp_ensemble_desc d = fpk::ens_desc(ens);
     if (d.kind != FP_HEA || d.depth_min != d.depth_max)
         return fpk::api_fail(FP_ERR_ARG, "the control variate needs a single-depth HEA ensemble");
-    const int n = d.n, L = d.depth_min, D = 4 * n * L;
+    const int n = d.n, L = d.depth_min, D = 12 * n * L;
     const int H = cfg->hidden > 0 ? cfg->hidden : 256;
     const int epochs = cfg->epochs > 0 ? cfg->epochs : 20;
     const int B = cfg->batch > 0 ? cfg->batch : 512;
@@ -397,6 +445,7 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
 
     const uint64_t f_train = cfg->first, f_corr = f_train + NT, f_sur = f_corr + NC;
     Mlp m = make_mlp(D, H);
+    double t_mu = 0, t_sigma = 1;   // the log-scale target's normalisation
     // ---- 1. exact contractions of the training pairs -> targets
     Buf X, y;
     CKC(X.alloc(NT * m.Dp * sizeof(bf16)));
@@ -411,15 +460,24 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
         std::vector<double> h(2 * NT);
         CKC(cudaMemcpyAsync(h.data(), dtr, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
         CKC(cudaStreamSynchronize(st));
-        double mean = 0;
+        double mean = 0, lm = 0, lv = 0;
         for (uint64_t i = 0; i < NT; ++i) {
             double a2 = h[2 * i] * h[2 * i] + h[2 * i + 1] * h[2 * i + 1];
             mean += a2 * a2;
+            lm += std::log(a2 + 1e-6);
         }
         mean /= (double)NT;
+        lm /= (double)NT;
+        for (uint64_t i = 0; i < NT; ++i) {
+            double a2 = h[2 * i] * h[2 * i] + h[2 * i + 1] * h[2 * i + 1], dl = std::log(a2 + 1e-6) - lm;
+            lv += dl * dl;
+        }
         res->target_scale = mean > 0 ? mean : 1.0;
+        t_mu = lm;
+        t_sigma = NT > 1 ? std::sqrt(lv / (double)(NT - 1)) : 1.0;
+        if (!(t_sigma > 0)) t_sigma = 1.0;
     }
-    abs4_kernel<<<(unsigned)((NT + 255) / 256), 256, 0, st>>>(dtr, (int)NT, 1.0 / res->target_scale, y.f(), nullptr);
+    logt_kernel<<<(unsigned)((NT + 255) / 256), 256, 0, st>>>(dtr, (int)NT, t_mu, 1.0 / t_sigma, y.f());
     CKC(cudaGetLastError());
     CKC(cudaMemsetAsync(X.p, 0, NT * m.Dp * sizeof(bf16), st));
     features_kernel<<<1024, 256, 0, st>>>(d.seed, f_train, (int)NT, n, L, X.h(), m.Dp);
@@ -560,7 +618,6 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
     }
     CKS(check_err());
     res->train_loss = last_loss;
-    res->gpu_seconds_train = elapsed();
     // ---- 3. correction pairs: exact f and the surrogate g on the same pairs
     Buf Xc, gc, fc, sums, big[3];
     const size_t chunk = 1 << 16;
@@ -579,8 +636,29 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
         if (e != cudaSuccess) return e;
         out_kernel<<<(unsigned)(((size_t)cnt * 32 + 255) / 256), 256, 0, st>>>(
             cnt, H, cap[2], W.f() + m.woff[3], W.f() + m.boff[3], nullptr, gc.f(), nullptr, nullptr, nullptr);
+        gtrans_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, gc.f(), (float)t_mu, (float)t_sigma);
         return cudaGetLastError();
     };
+    // the control-variate coefficient beta = Cov(f, g) / Var(g) on the training pairs
+    // (their traces are still in dtr); the correction and surrogate pairs are disjoint
+    // from them, so beta g is a fixed function there and the estimate stays unbiased
+    double beta = 1.0;
+    {
+        CKC(cudaMemsetAsync(sums.p, 0, 4 * sizeof(double), st));
+        for (uint64_t c0 = 0; c0 < NT; c0 += chunk) {
+            const int cnt = (int)std::min<uint64_t>(chunk, NT - c0);
+            CKC(surrogate(f_train + c0, cnt));
+            beta_sums_kernel<<<256, 256, 0, st>>>(cnt, gc.f(), dtr + 2 * c0, sums.d());
+            CKC(cudaGetLastError());
+        }
+        double bs[4];
+        CKC(cudaMemcpyAsync(bs, sums.p, sizeof bs, cudaMemcpyDeviceToHost, st));
+        CKC(cudaStreamSynchronize(st));
+        const double Nt = (double)NT, vg = bs[1] - bs[0] * bs[0] / Nt, cfg_ = bs[2] - bs[0] * bs[3] / Nt;
+        if (vg > 0 && std::isfinite(cfg_ / vg)) beta = cfg_ / vg;
+    }
+    res->target_scale = beta;
+    res->gpu_seconds_train = elapsed();   // features, training and the coefficient fit
     CKS(fpk::cv_trace(ens, f_corr, NC, &dtr, &ms_trace));
     res->gpu_seconds_exact += ms_trace * 1e-3;
     CKC(join_user());
@@ -592,7 +670,7 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
     if (cfg->g_correct || cfg->g_surrogate) CKC(gx.alloc(chunk * sizeof(double)));
     auto export_g = [&](double *dst, int cnt) -> cudaError_t {
         if (!dst) return cudaSuccess;
-        gexport_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, gc.f(), res->target_scale, gx.d());
+        gexport_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, gc.f(), beta, gx.d());
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? cudaMemcpyAsync(dst, gx.d(), cnt * sizeof(double), cudaMemcpyDefault, st) : e;
     };
@@ -600,7 +678,7 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
     for (uint64_t c0 = 0; c0 < NC; c0 += chunk) {
         const int cnt = (int)std::min<uint64_t>(chunk, NC - c0);
         CKC(surrogate(f_corr + c0, cnt));
-        cv_sums_kernel<<<256, 256, 0, st>>>(cnt, gc.f(), res->target_scale, fc.d() + c0, sums.d());
+        cv_sums_kernel<<<256, 256, 0, st>>>(cnt, gc.f(), beta, fc.d() + c0, sums.d());
         CKC(cudaGetLastError());
         CKC(export_g(cfg->g_correct ? cfg->g_correct + c0 : nullptr, cnt));
     }
@@ -615,7 +693,7 @@ extern "C" fp_status fp_cv_frame_potential(fp_ensemble *ens, const fp_cv_config 
     for (uint64_t c0 = 0; c0 < MS; c0 += chunk) {
         const int cnt = (int)std::min<uint64_t>(chunk, MS - c0);
         CKC(surrogate(f_sur + c0, cnt));
-        cv_sums_kernel<<<256, 256, 0, st>>>(cnt, gc.f(), res->target_scale, nullptr, sums.d());
+        cv_sums_kernel<<<256, 256, 0, st>>>(cnt, gc.f(), beta, nullptr, sums.d());
         CKC(cudaGetLastError());
         CKC(export_g(cfg->g_surrogate ? cfg->g_surrogate + c0 : nullptr, cnt));
     }

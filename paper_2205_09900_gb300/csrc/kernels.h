@@ -86,6 +86,14 @@ cudaError_t launch_spiral(const PairInfo *pairs, int npairs, const SpiralMap *sm
                           const SpiralConfig &cfg, const SpiralWin *wins, int nwins, const uint8_t *ij, const int *h,
                           const double2 *merged, void *maps, void *scratch, bool fp32, double err_scale, double *tr,
                           double *kappa, double *err, cudaStream_t st);
+// Qudit brickwork (kernels_qudit.cu): sampler, maps and sweep of pairs
+// pairs[0..npairs) of one depth (BrickDev of the qubit plan with N = 2(l-1)
+// q-ary digits); `ws` holds qudit_workspace_per_pair bytes per pair; results
+// at slot pairs[i].out of tr/kappa/err.
+size_t qudit_workspace_per_pair(int q, const BrickDev &d, int n_raw, bool fp32);
+cudaError_t launch_qudit(int q, const BrickDev &d, uint64_t seed, const PairInfo *pairs, int npairs, int n_raw,
+                         int self_pair, bool fp32, void *ws, double err_scale, double *tr, double *kappa, double *err,
+                         cudaStream_t st);
 // Time limit of one bounded device wait (nanoseconds of the global timer):
 // fp_set_wait_limit_ns, default 1 s.
 uint64_t wait_limit_ns();

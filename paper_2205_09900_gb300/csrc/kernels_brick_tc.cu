@@ -13,7 +13,7 @@
 // M = 128, N = 64, K = 8).
 //
 // One CTA takes two tiles of one pair (X and Y) through every window of the
-// pass, alternating: while the tensor cores multiply one tile, the 256
+// pass, alternating: while the tensor cores multiply one tile, the 512
 // threads read the other tile's result out of tensor memory (tcgen05.ld),
 // split it, and store it into shared memory in the next window's operand
 // layout (K-major, 128-byte swizzle; every element's address is the XOR of
@@ -37,7 +37,7 @@ namespace fpk {
 namespace {
 
 constexpr uint64_t kTcDrainNs = 1000000000ull;   // waits for work already issued (after a timeout)
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
 constexpr int kMaxTcWins = 48;
 constexpr uint32_t kAOp = 32768;                 // bytes of one A operand (hi or lo) of one tile
 constexpr uint32_t kWMat = 32768;                // bytes of one window matrix (hi + lo)
@@ -193,33 +193,35 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
                  : "memory");
 }
 
-// Read this thread's 16 complex results of one tile out of tensor memory and
+// Read this thread's 8 complex results of one tile out of tensor memory and
 // scatter them: into the A operands of the next window (next != nullptr:
 // address = XOR of next[b] over the element's tile bits) or to the boundary
-// in global memory (gdst, contributions gcb: physical index bits).
+// in global memory (gdst, contributions gcb: physical index bits).  Warp w
+// reads TMEM lanes 32 (w mod 4) .. + 31 (tile rows) and columns 16 (w / 4) ..
+// + 15 (window outputs 8 (w / 4) .. + 7, as re, im pairs).
 __device__ __forceinline__ void drain_tile(uint32_t tm, const TcWin &cw, const uint32_t *__restrict__ cbn,
                                            unsigned char *A, float2 *gdst) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t v[32];
+    uint32_t v[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(tm + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2))));
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(tm + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * (warp >> 2))));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     const uint32_t r = 32u * (warp & 3) + lane;
     uint32_t base = 0;
 #pragma unroll
     for (int t = 0; t < kTcRows; ++t)
         if ((r >> t) & 1u) base ^= cbn[cw.row[t]];
-    if (warp >> 2) base ^= cbn[cw.win[4]];
-    const uint32_t c0 = cbn[cw.win[0]], c1 = cbn[cw.win[1]], c2 = cbn[cw.win[2]], c3 = cbn[cw.win[3]];
+    const int og = warp >> 2;   // window output bits 3, 4
+    if (og & 1) base ^= cbn[cw.win[3]];
+    if (og & 2) base ^= cbn[cw.win[4]];
+    const uint32_t c0 = cbn[cw.win[0]], c1 = cbn[cw.win[1]], c2 = cbn[cw.win[2]];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-        const uint32_t a = base ^ ((u & 1) ? c0 : 0u) ^ ((u & 2) ? c1 : 0u) ^ ((u & 4) ? c2 : 0u) ^ ((u & 8) ? c3 : 0u);
+    for (int u = 0; u < 8; ++u) {
+        const uint32_t a = base ^ ((u & 1) ? c0 : 0u) ^ ((u & 2) ? c1 : 0u) ^ ((u & 4) ? c2 : 0u);
         const float x = __uint_as_float(v[2 * u]), y = __uint_as_float(v[2 * u + 1]);
         if (A) st_hilo(A, a, x, y);
         else gdst[a] = make_float2(x, y);

@@ -11,7 +11,7 @@
 //              operand layout, the MMA read through the hardware's view of
 //              the K-major 128-byte-swizzled operands (row r, K column k at
 //              region k/32, row offset 128 r, 16-byte chunk (k/4 mod 8) ^ (r mod 8)),
-//              D = A B^T, then every thread's 16 results scattered through the
+//              D = A B^T, then every thread's 8 results (16 warps) scattered through the
 //              XOR address tables into the next window's operand or the boundary.
 // Every operand address is checked to be in bounds and every window layout
 // to be a bijection.  Exit status 1 if the two sweeps differ by more than
@@ -175,18 +175,20 @@ int main(int argc, char **argv) {
                     const bool last = w + 1 == ps.n_rp;
                     const uint32_t *cbn = last ? gcb : W[ps.rp_off + w + 1].cb;
                     std::vector<double> A2(8192, 0.0);
-                    for (int warp = 0; warp < 8; ++warp)
+                    for (int warp = 0; warp < 16; ++warp)
                         for (int lane = 0; lane < 32; ++lane) {
                             const uint32_t r = 32u * (warp & 3) + lane;
                             uint32_t bs = 0;
                             for (int q = 0; q < kTcRows; ++q)
                                 if ((r >> q) & 1u) bs ^= cbn[cw.row[q]];
-                            if (warp >> 2) bs ^= cbn[cw.win[4]];
-                            for (int u = 0; u < 16; ++u) {
+                            const int og = warp >> 2;
+                            if (og & 1) bs ^= cbn[cw.win[3]];
+                            if (og & 2) bs ^= cbn[cw.win[4]];
+                            for (int u = 0; u < 8; ++u) {
                                 uint32_t a = bs;
-                                for (int q = 0; q < 4; ++q)
+                                for (int q = 0; q < 3; ++q)
                                     if ((u >> q) & 1) a ^= cbn[cw.win[q]];
-                                const uint32_t col = 32u * (warp >> 2) + 2u * u;
+                                const uint32_t col = 16u * (warp >> 2) + 2u * u;
                                 const double x = D[r * 64 + col], y = D[r * 64 + col + 1];
                                 if (last) {
                                     CHECK((a & ~(S - 1)) == 0 && (a & base) == 0, "boundary index out of the tile");
