@@ -313,7 +313,7 @@ def control_variate_report(fp, n_train=100_000, n_correct=10_000, m_surrogate=10
         cv_s = r.gpu_seconds_exact + r.gpu_seconds_train + r.gpu_seconds_surrogate
         plain_pairs = r.var_f / r.stderr_ ** 2
         # MLP work of the surrogate phase (correction + surrogate evaluations), algorithmic FLOPs
-        D, H = 4 * 50 * L, 256
+        D, H = 12 * 50 * L, 256
         mlp_flop = 2.0 * (D * H + 2 * H * H + H) * (n_correct + m_surrogate)
         out[str(L)] = {"F2_cv": r.F2, "stderr_cv": r.stderr_, "F2_plain_on_corrections": r.F2_plain,
                        "stderr_plain_on_corrections": r.stderr_plain,
@@ -324,8 +324,9 @@ def control_variate_report(fp, n_train=100_000, n_correct=10_000, m_surrogate=10
                        "gpu_s_plain_same_stderr": plain_pairs * c_pair,
                        "train_loss": r.train_loss}
     return {"config": f"HEA n=50, L=4..6, {n_train} training pairs, {m_surrogate} surrogate evaluations, "
-                      f"{n_correct} exact corrections; MLP 4nL-256-256-256-1 GELU, Adam; hidden layers "
-                      f"as BF16 tcgen05 GEMMs with FP32 accumulation",
+                      f"{n_correct} exact corrections; MLP 12nL-256-256-256-1 GELU on periodic angle features, Adam, "
+                      f"log|Tr|^2 target, g = beta exp(2 prediction) with beta fitted on the training pairs; "
+                      f"hidden layers as BF16 tcgen05 GEMMs with FP32 accumulation",
             "by_depth": out}
 
 

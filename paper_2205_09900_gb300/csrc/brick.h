@@ -82,6 +82,12 @@ struct TcWin {
     uint8_t win[kMaxWin];     // tile-local bit of window position k (ring order)
     uint8_t row[kTcRows];     // tile-local bits of the row index, ascending
     uint32_t cb[kTcTile];
+    // store order of the scatter from this window's result into the next
+    // window's operand: lane L (bits 0-3) visits its outputs u ^ rot(L),
+    // rot bit i = parity(L & (rotm >> 4i)), chosen on the host so that the 16
+    // lanes of a half-warp hit 16 distinct 8-byte bank pairs (or as few
+    // repeats as the layouts allow)
+    uint16_t rotm;
 };
 // A-operand byte address of element (row r, window index j): complex j
 // occupies K columns 2j (re), 2j+1 (im); K splits into two 128-byte regions of

@@ -168,6 +168,42 @@ BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win
     return P;
 }
 
+// Bank-pair index (8-byte banks of a 128-byte line) of an operand byte address.
+static int bank8(uint32_t a) { return (int)((a >> 3) & 15u); }
+
+// The store order of the scatter from window `cw` into the layout `nx` (see
+// TcWin::rotm): the 16 lanes of a half-warp hold rows whose bits 0-3 are the
+// lane bits; the rotation that makes their bank pairs distinct at every step,
+// else the one with the fewest repeats.
+static uint16_t tc_rotation(const TcWin &cw, const TcWin &nx) {
+    uint32_t rowc[4], winc[3];
+    for (int t = 0; t < 4; ++t) rowc[t] = nx.cb[cw.row[t]];
+    for (int q = 0; q < 3; ++q) winc[q] = nx.cb[cw.win[q]];
+    int best = 1 << 30;
+    uint16_t best_m = 0;
+    for (uint32_t m = 0; m < (1u << 12); ++m) {
+        int cost = 0;
+        for (int step = 0; step < 8 && cost < best; ++step) {
+            int hits[16] = {0}, worst = 0;
+            for (int lane = 0; lane < 16; ++lane) {
+                uint32_t a = 0;
+                for (int t = 0; t < 4; ++t)
+                    if ((lane >> t) & 1) a ^= rowc[t];
+                int rot = 0;
+                for (int i = 0; i < 3; ++i) rot |= (__builtin_popcount(lane & ((m >> (4 * i)) & 15u)) & 1) << i;
+                const int u = step ^ rot;
+                for (int q = 0; q < 3; ++q)
+                    if ((u >> q) & 1) a ^= winc[q];
+                worst = std::max(worst, ++hits[bank8(a)]);
+            }
+            cost += worst;
+        }
+        if (cost < best) { best = cost; best_m = (uint16_t)m; }
+        if (best == 8) break;   // one wavefront per step: conflict-free
+    }
+    return best_m;
+}
+
 std::vector<TcWin> make_tc_windows(const BrickHostPlan &P) {
     std::vector<TcWin> out(P.rpasses.size());
     for (size_t w = 0; w < P.rpasses.size(); ++w) {
@@ -187,6 +223,8 @@ std::vector<TcWin> make_tc_windows(const BrickHostPlan &P) {
                 ++r;
             }
     }
+    for (const BrickPass &ps : P.passes)
+        for (int w = 0; w + 1 < ps.n_rp; ++w) out[ps.rp_off + w].rotm = tc_rotation(out[ps.rp_off + w], out[ps.rp_off + w + 1]);
     return out;
 }
 

@@ -219,8 +219,29 @@ __device__ __forceinline__ void drain_tile(uint32_t tm, const TcWin &cw, const u
     if (og & 1) base ^= cbn[cw.win[3]];
     if (og & 2) base ^= cbn[cw.win[4]];
     const uint32_t c0 = cbn[cw.win[0]], c1 = cbn[cw.win[1]], c2 = cbn[cw.win[2]];
+    // lanes of a half-warp whose rows map to the same bank pairs would collide
+    // if they stored the same output at once: each lane visits its 8 outputs in
+    // the order u ^ rot (a butterfly of register swaps), rot a linear function
+    // of the lane bits chosen on the host for this pair of layouts (TcWin::rotm)
+    const uint32_t rm = A ? cw.rotm : 0u, l4 = (uint32_t)lane & 15u;
+    const int rot = (__popc(l4 & (rm & 15u)) & 1) | ((__popc(l4 & ((rm >> 4) & 15u)) & 1) << 1) |
+                    ((__popc(l4 & ((rm >> 8) & 15u)) & 1) << 2);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int b = 0; b < 3; ++b) {
+        if ((rot >> b) & 1) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (!((u >> b) & 1)) {
+                    const int w2 = u | (1 << b);
+                    uint32_t t0 = v[2 * u], t1 = v[2 * u + 1];
+                    v[2 * u] = v[2 * w2]; v[2 * u + 1] = v[2 * w2 + 1];
+                    v[2 * w2] = t0; v[2 * w2 + 1] = t1;
+                }
+        }
+    }
+    base ^= ((rot & 1) ? c0 : 0u) ^ ((rot & 2) ? c1 : 0u) ^ ((rot & 4) ? c2 : 0u);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {   // register u holds output u ^ rot
         const uint32_t a = base ^ ((u & 1) ? c0 : 0u) ^ ((u & 2) ? c1 : 0u) ^ ((u & 4) ? c2 : 0u);
         const float x = __uint_as_float(v[2 * u]), y = __uint_as_float(v[2 * u + 1]);
         if (A) st_hilo(A, a, x, y);

@@ -184,10 +184,18 @@ int main(int argc, char **argv) {
                             const int og = warp >> 2;
                             if (og & 1) bs ^= cbn[cw.win[3]];
                             if (og & 2) bs ^= cbn[cw.win[4]];
-                            for (int u = 0; u < 8; ++u) {
+                            // the kernel visits output u ^ rot at step u (rot by lane, TcWin::rotm)
+                            const uint32_t rm = last ? 0u : cw.rotm, l4 = (uint32_t)lane & 15u;
+                            int rot = 0;
+                            for (int i = 0; i < 3; ++i)
+                                rot |= (__builtin_popcount(l4 & ((rm >> (4 * i)) & 15u)) & 1) << i;
+                            for (int step = 0; step < 8; ++step) {
+                                const int u = step ^ rot;
                                 uint32_t a = bs;
                                 for (int q = 0; q < 3; ++q)
-                                    if ((u >> q) & 1) a ^= cbn[cw.win[q]];
+                                    if ((rot >> q) & 1) a ^= cbn[cw.win[q]];
+                                for (int q = 0; q < 3; ++q)
+                                    if ((step >> q) & 1) a ^= cbn[cw.win[q]];
                                 const uint32_t col = 16u * (warp >> 2) + 2u * u;
                                 const double x = D[r * 64 + col], y = D[r * 64 + col + 1];
                                 if (last) {

@@ -42,12 +42,12 @@ def test_qudit_traces_match_oracle(fp, n, l, method):
 
 def test_qudit_mixed_depths_and_global_state(fp):
     # depths 2..6 in one call (l = 6: 3^10 amplitudes per side, kept in global memory)
-    ens = fp.Ensemble(fp.PARALLEL, 8, 2, 6, seed=43, q=3)
+    ens = fp.Ensemble(fp.PARALLEL, 6, 2, 6, seed=43, q=3)
     t, _, g = ens.trace_batch(0, 40, fp.PREC_FP64)
-    d = O.desc(O.PARALLEL, 8, 2, 6, seed=43)
+    d = O.desc(O.PARALLEL, 6, 2, 6, seed=43)
     ls = [O.pair_depth(d, p) for p in range(40)]
     assert sorted(set(ls)) == [2, 3, 4, 5, 6] and np.array_equal(g, np.array(ls) - 2)
-    ref = np.array([O.trace_qudit(3, 8, l, 43, p, "ve") for p, l in enumerate(ls)])
+    ref = np.array([O.trace_qudit(3, 6, l, 43, p, "dense") for p, l in enumerate(ls)])
     assert rel(t, ref).max() <= 1e-10
 
 
