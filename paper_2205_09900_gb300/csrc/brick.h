@@ -39,6 +39,11 @@ struct BrickPass {
     uint32_t smask;     // physical bits held by the tile
     int32_t rp_off, n_rp;   // register passes (RegPass) of this tile pass
     int32_t rg_off;         // first RegGate of this tile pass
+    // shared-memory layout of the tile: element i sits at i ^ s(i >> 4), s
+    // linear over GF(2) into the low 4 bits, s of tile bit 4 + j = swz[j];
+    // chosen per pass so that the 16 lanes of a half-warp reading one
+    // register window hit 16 distinct 8-byte bank pairs
+    uint8_t swz[12];
 };
 
 // One register pass inside a tile pass: every thread holds 2^r amplitudes

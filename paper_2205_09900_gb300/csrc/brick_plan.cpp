@@ -72,6 +72,58 @@ static void schedule_registers(BrickHostPlan &P, BrickPass &ps, const int *ring,
     ps.n_rp = (int)P.rpasses.size() - ps.rp_off;
 }
 
+// Rank over GF(2) of up to 4 vectors of 4 bits.
+static int rank4(uint32_t *v, int nv) {
+    int r = 0;
+    for (int bit = 3; bit >= 0 && r < nv; --bit) {
+        int p = -1;
+        for (int i = r; i < nv; ++i)
+            if ((v[i] >> bit) & 1u) { p = i; break; }
+        if (p < 0) continue;
+        std::swap(v[r], v[p]);
+        for (int i = 0; i < nv; ++i)
+            if (i != r && ((v[i] >> bit) & 1u)) v[i] ^= v[r];
+        ++r;
+    }
+    return r;
+}
+
+// The tile layout of one pass (BrickPass::swz): the lanes of a half-warp are
+// consecutive groups t, whose bits 0-3 land on the 4 lowest tile bits outside
+// the window; their 8-byte bank pairs (element index mod 16 after the
+// swizzle) are distinct when those 4 bits' bank contributions are linearly
+// independent.  Start from the fixed pattern (bit b -> b mod 4) and search
+// (deterministic pseudo-random changes) until every window qualifies.
+static void choose_swizzle(const BrickHostPlan &P, BrickPass &ps, int K) {
+    for (int j = 0; j < 12; ++j) ps.swz[j] = (uint8_t)(1u << ((4 + j) % 4));
+    if (K <= 4) return;
+    auto bad = [&](const uint8_t *sw) {
+        int cnt = 0;
+        for (int w = 0; w < ps.n_rp; ++w) {
+            const RegPass &rp = P.rpasses[ps.rp_off + w];
+            uint32_t v[4];
+            int nv = 0;
+            for (int b = 0; b < K && nv < 4; ++b) {
+                bool in = false;
+                for (int k = 0; k < rp.r; ++k) in = in || rp.win[k] == b;
+                if (!in) v[nv++] = b < 4 ? (1u << b) : sw[b - 4];
+            }
+            cnt += 4 - rank4(v, nv);
+        }
+        return cnt;
+    };
+    int best = bad(ps.swz);
+    uint32_t x = 0x9E3779B9u ^ (uint32_t)ps.gate_off;
+    for (int it = 0; it < 4000 && best > 0; ++it) {
+        uint8_t trial[12];
+        std::memcpy(trial, ps.swz, 12);
+        x ^= x << 13; x ^= x >> 17; x ^= x << 5;
+        trial[(x >> 4) % (uint32_t)(K - 4)] = (uint8_t)(x & 15u);
+        const int v = bad(trial);
+        if (v <= best) { best = v; std::memcpy(ps.swz, trial, 12); }
+    }
+}
+
 BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win_bits, int kind) {
     BrickHostPlan P;
     BrickDev &d = P.dev;
@@ -161,6 +213,7 @@ BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win
             for (int k = 0; k < K; ++k) ring[k] = loc[(start + k) % N];
             if (whole) for (int k = 0; k < K; ++k) ring[k] = loc[k];
             schedule_registers(P, ps, ring, K, std::min(win_bits, K), whole);
+            choose_swizzle(P, ps, K);
             P.passes.push_back(ps);
         }
         d.n_passes[side] = (int)P.passes.size() - d.pass_off[side];

@@ -334,15 +334,11 @@ __global__ void brick_init_kernel(BrickDev d, int npairs, C *__restrict__ states
     }
 }
 
-// Shared-memory tile layout: the low 4 index bits are XORed with the XOR of
-// the higher nibbles, so that threads whose indices differ only above bit 3
-// still spread over all banks.  The map is linear over GF(2):
-// swz(a ^ b) = swz(a) ^ swz(b), so an address built from disjoint bit groups
-// is the XOR of their swizzled parts.
-__device__ __forceinline__ uint32_t swz(uint32_t i) {
-    uint32_t h = i >> 4;
-    return i ^ ((h ^ (h >> 4) ^ (h >> 8) ^ (h >> 12)) & 15u);
-}
+// Shared-memory tile layout: the low 4 index bits are XORed with a linear
+// (over GF(2)) function of the higher bits, chosen per pass on the host
+// (BrickPass::swz) so that the lanes reading one register window spread over
+// all banks.  Linearity makes swz(a ^ b) = swz(a) ^ swz(b), so an address
+// built from disjoint bit groups is the XOR of their swizzled parts.
 
 // Packed FP32 pair FMA (two lanes per instruction): d = a * b + c lane-wise.
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
@@ -473,21 +469,33 @@ constexpr int kMaxRegPasses = 160;
 // The register passes of one tile pass over a tile in shared memory: every
 // thread holds 2^R amplitudes of a window in registers, applies the window's
 // gates, writes them back; one barrier per window.
+// The pass's tile layout (BrickPass::swz): element i at i ^ shi[i >> 4].
+template <int K, int TH>
+__device__ __forceinline__ void swizzle_table(const BrickPass &ps, uint8_t *shi) {
+    for (int h = threadIdx.x; h < (1 << (K - 4)); h += TH) {
+        uint32_t v = 0;
+        for (int j = 0; j < K - 4; ++j)
+            if ((h >> j) & 1) v ^= ps.swz[j];
+        shi[h] = (uint8_t)v;
+    }
+}
+__device__ __forceinline__ uint32_t swzt(const uint8_t *shi, uint32_t i) { return i ^ shi[i >> 4]; }
+
 template <typename C, int K, int R, int TH>
 __device__ __forceinline__ void tile_register_passes(C *__restrict__ tile, const C *__restrict__ smaps,
                                                      const RegPass *__restrict__ srp, const RegGate *__restrict__ srg,
-                                                     int n_rp, int g0) {
+                                                     int n_rp, int g0, const uint8_t *__restrict__ shi) {
     constexpr int MW = MapSlot<C>::width;
     for (int p = 0; p < n_rp; ++p) {
         const RegPass rp = srp[p];
         uint32_t sw[R];
 #pragma unroll
-        for (int k = 0; k < R; ++k) sw[k] = swz(1u << rp.win[k]);
+        for (int k = 0; k < R; ++k) sw[k] = swzt(shi, 1u << rp.win[k]);
         for (uint32_t t = threadIdx.x; t < (1u << (K - R)); t += TH) {
             uint32_t b0 = t;
 #pragma unroll
             for (int k = 0; k < R; ++k) b0 = ins0(b0, rp.srt[k]);
-            uint32_t sb = swz(b0);
+            uint32_t sb = swzt(shi, b0);
             C v[1 << R];
 #pragma unroll
             for (int i = 0; i < (1 << R); ++i) {
@@ -564,9 +572,11 @@ __global__ void __launch_bounds__(TH, (sizeof(C) == 8 && K <= 13 && TH <= 256) ?
     __shared__ int pos[32];
     __shared__ RegPass srp[kMaxRegPasses];
     __shared__ RegGate srg[256];
+    __shared__ uint8_t shi[1 << (K - 4)];
     const int N = d.N;
     const uint32_t S = 1u << N;
-    tile_tables<K, TH>(ps, N, pos, lut_lo, lut_hi);
+    swizzle_table<K, TH>(ps, shi);
+    tile_tables<K, TH>(ps, N, pos, lut_lo, lut_hi);   // (its barriers publish shi too)
     const uint32_t base = tile_base(blockIdx.x, ps.smask, N);
     // the tile: all 2^K element copies in flight at once ...
     static_assert((1 << K) % TH == 0, "tile size must be a multiple of the block size");
@@ -574,7 +584,7 @@ __global__ void __launch_bounds__(TH, (sizeof(C) == 8 && K <= 13 && TH <= 256) ?
 #pragma unroll
     for (int j = 0; j < (1 << K) / TH; ++j) {
         const uint32_t i = threadIdx.x + (uint32_t)j * TH;
-        cp_async<sizeof(C)>(&tile[swz(i)], &st[lut_lo[i & 127] | lut_hi[i >> 7]]);
+        cp_async<sizeof(C)>(&tile[swzt(shi, i)], &st[lut_lo[i & 127] | lut_hi[i >> 7]]);
     }
     // ... while the register schedule and the pass's gate maps are staged
     for (int i = threadIdx.x; i < ps.n_rp; i += TH) srp[i] = rps[ps.rp_off + i];
@@ -586,8 +596,8 @@ __global__ void __launch_bounds__(TH, (sizeof(C) == 8 && K <= 13 && TH <= 256) ?
     }
     cp_async_wait_all();
     __syncthreads();
-    tile_register_passes<C, K, R, TH>(tile, smaps, srp, srg, ps.n_rp, ps.rg_off);
-    for (uint32_t i = threadIdx.x; i < (1u << K); i += TH) st[lut_lo[i & 127] | lut_hi[i >> 7]] = tile[swz(i)];
+    tile_register_passes<C, K, R, TH>(tile, smaps, srp, srg, ps.n_rp, ps.rg_off, shi);
+    for (uint32_t i = threadIdx.x; i < (1u << K); i += TH) st[lut_lo[i & 127] | lut_hi[i >> 7]] = tile[swzt(shi, i)];
 }
 
 // Persistent, double-buffered form of brick_pass_kernel: each CTA walks the
@@ -612,8 +622,10 @@ __global__ void __launch_bounds__(TH) brick_pass_db_kernel(BrickDev d, int side,
     __shared__ RegPass srp[kMaxRegPasses];
     __shared__ RegGate srg[256];
     __shared__ int mslot[256];                     // map index of each gate of the pass
+    __shared__ uint8_t shi[1 << (K - 4)];
     const int N = d.N;
     const uint32_t S = 1u << N;
+    swizzle_table<K, TH>(ps, shi);
     tile_tables<K, TH>(ps, N, pos, lut_lo, lut_hi);
     for (int i = threadIdx.x; i < ps.n_rp; i += TH) srp[i] = rps[ps.rp_off + i];
     for (int i = threadIdx.x; i < G; i += TH) {
@@ -632,7 +644,7 @@ __global__ void __launch_bounds__(TH) brick_pass_db_kernel(BrickDev d, int side,
 #pragma unroll
         for (int j = 0; j < (1 << K) / TH; ++j) {
             const uint32_t i = threadIdx.x + (uint32_t)j * TH;
-            cp_async<sizeof(C)>(&dst[swz(i)], &st[lut_lo[i & 127] | lut_hi[i >> 7]]);
+            cp_async<sizeof(C)>(&dst[swzt(shi, i)], &st[lut_lo[i & 127] | lut_hi[i >> 7]]);
         }
         const C *mp = maps + (size_t)pair * maps_per_pair(d) * 16;
         C *rdst = raw + (size_t)buf * G * 16;
@@ -653,10 +665,10 @@ __global__ void __launch_bounds__(TH) brick_pass_db_kernel(BrickDev d, int side,
         for (int i = threadIdx.x; i < G * 16; i += TH) stage_entry<C>(smaps + (i / 16) * MW, i % 16, rsrc[i]);
         __syncthreads();
         C *tile = tiles + (size_t)buf * (1u << K);
-        tile_register_passes<C, K, R, TH>(tile, smaps, srp, srg, ps.n_rp, ps.rg_off);
+        tile_register_passes<C, K, R, TH>(tile, smaps, srp, srg, ps.n_rp, ps.rg_off, shi);
         const uint32_t pair = it / ntiles, t = it - pair * ntiles;
         C *st = states + ((size_t)pair * 2 + side) * S + tile_base(t, ps.smask, N);
-        for (uint32_t i = threadIdx.x; i < (1u << K); i += TH) st[lut_lo[i & 127] | lut_hi[i >> 7]] = tile[swz(i)];
+        for (uint32_t i = threadIdx.x; i < (1u << K); i += TH) st[lut_lo[i & 127] | lut_hi[i >> 7]] = tile[swzt(shi, i)];
         __syncthreads();   // the tile and raw maps of this buffer are free for item k + 2
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
