@@ -249,18 +249,34 @@ __device__ __forceinline__ void drain_tile(uint32_t tm, const TcWin &cw, const u
     }
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp roles: warps 0..15 drain (TMEM -> next operand, 8 outputs per thread),
+// warp 16 controls (lane 0 issues the bulk copies of the window matrices and
+// every MMA).  They meet only on mbarriers, per tile t (X = 0, Y = 1):
+//   afull[t]  completion k: the operand of tile t for window k is in shared
+//             memory (one arrival per drain warp);
+//   dfull[t]  completion k: the MMAs of tile t, window k, are done (commit);
+//   wfull[b]  the window matrix in buffer b has arrived (bulk copy).
+// Each drain warp works through X(w), Y(w), X(w+1), ... as soon as each MMA
+// is done; the control lane issues X(w), Y(w) as soon as both operands and
+// the matrix are there, and reloads a matrix buffer once Y(w) -- and with it
+// every earlier MMA -- is done.
+__global__ void __launch_bounds__(kTcThreads + 32, 1)
     brick_tc_pass_kernel(BrickDev d, int side, BrickPass ps, const TcWin *__restrict__ wins,
                          const float *__restrict__ wm, float2 *__restrict__ states, int *err, uint64_t wait_ns) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t wbar[2], mbar[2], fbar;
+    __shared__ __align__(8) uint64_t wfull[2], dfull[2], afull[2], fbar;
     __shared__ uint32_t taddr_sh;
     __shared__ int abort_sh;
     __shared__ int pos[32];
     __shared__ uint32_t lut_lo[128], lut_hi[1 << (kTcTile - 7)], alo[128], ahi[1 << (kTcTile - 7)], gcb[kTcTile];
     __shared__ TcWin sw[kMaxTcWins];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool ctrl = warp == kTcThreads / 32;
     const int nw = ps.n_rp;
     const int N = d.N;
     const uint32_t S = 1u << N;
@@ -270,10 +286,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int b = 0; b < N; ++b)
             if (ps.smask & (1u << b)) pos[k++] = b;
     }
-    for (int i = tid; i < nw; i += kTcThreads) sw[i] = wins[ps.rp_off + i];
+    for (int i = tid; i < nw; i += kTcThreads + 32) sw[i] = wins[ps.rp_off + i];
     __syncthreads();
     if (abort_sh) return;
-    for (int i = tid; i < 128; i += kTcThreads) {
+    for (int i = tid; i < 128; i += kTcThreads + 32) {
         uint32_t o = 0, a = 0;
         for (int k = 0; k < 7; ++k)
             if ((i >> k) & 1) { o |= 1u << pos[k]; a ^= sw[0].cb[k]; }
@@ -294,8 +310,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (tid == 32) {
         for (int b = 0; b < 2; ++b) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&wbar[b])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&wfull[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&dfull[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull[b])), "r"(kTcThreads / 32));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fbar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -307,119 +324,99 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t sbase = smem_u32(smem);
     const uint32_t sW = sbase + 4 * kAOp;
     const float *wp = wm + (size_t)blockIdx.y * nw * kWFloats;
-    // window matrices 0 and 1 (thread 0 also issues every MMA; counts kept for the drain)
-    int tma_issued[2] = {0, 0}, tma_waited[2] = {0, 0};
-    if (tid == 0)
-        for (int b = 0; b < 2 && b < nw; ++b) {
-            bulk_load(sW + b * kWMat, wp + (size_t)b * kWFloats, kWMat, &wbar[b]);
-            ++tma_issued[b];
-        }
-    // both tiles: boundary -> A operands of window 0.  Every element copy of
-    // both tiles is in flight at once (cp.async into tile Y's operand space,
-    // X raw in its hi part, Y raw in its lo part), then each thread converts
-    // the elements it copied: X straight into its operands; Y through
-    // registers, as its operands overlap the staging space.
+    auto ab = [&]() { return *(volatile int *)&abort_sh != 0; };   // set by any thread whose wait ran out
     float2 *st = states + ((size_t)blockIdx.y * 2 + side) * S;
     const uint32_t gb[2] = {tile_base_of(2 * blockIdx.x, ps.smask, N), tile_base_of(2 * blockIdx.x + 1, ps.smask, N)};
-    constexpr int kPer = (1 << kTcTile) / kTcThreads;
-    float2 *stage = (float2 *)(smem + 2 * kAOp);
+    if (ctrl) {
+        if (lane == 0) {
+            int tma_issued[2] = {0, 0}, tma_waited[2] = {0, 0};
+            bool any = false;
+            for (int b = 0; b < 2 && b < nw; ++b) {
+                bulk_load(sW + b * kWMat, wp + (size_t)b * kWFloats, kWMat, &wfull[b]);
+                ++tma_issued[b];
+            }
+            for (int w = 0; w < nw && !ab(); ++w) {
+                for (int t = 0; t < 2 && !ab(); ++t) {
+                    if (!mbar_wait(smem_u32(&afull[t]), (uint32_t)w & 1u, wait_ns)) { abort_sh = 1; break; }
+                    if (t == 0) {
+                        if (!mbar_wait(smem_u32(&wfull[w & 1]), (uint32_t)(w >> 1) & 1u, wait_ns)) { abort_sh = 1; break; }
+                        ++tma_waited[w & 1];
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    issue_tile_mmas(taddr + 64u * t, sbase + 2 * kAOp * t, sW + (w & 1) * kWMat);
+                    commit_to(&dfull[t]);
+                    any = true;
+                }
+                // the matrix buffer of window w is free once Y(w) is done (commits complete in order)
+                if (!ab() && w + 2 < nw) {
+                    if (!mbar_wait(smem_u32(&dfull[1]), (uint32_t)w & 1u, wait_ns)) { abort_sh = 1; break; }
+                    bulk_load(sW + (w & 1) * kWMat, wp + (size_t)(w + 2) * kWFloats, kWMat, &wfull[w & 1]);
+                    ++tma_issued[w & 1];
+                }
+            }
+            if (ab()) {
+                // drain what this lane issued (every MMA through one more commit; bulk
+                // copies by their last armed phase), then report
+                if (any) {
+                    commit_to(&fbar);
+                    mbar_wait(smem_u32(&fbar), 0u, kTcDrainNs);
+                }
+                for (int b = 0; b < 2; ++b)
+                    if (tma_issued[b] > tma_waited[b])
+                        mbar_wait(smem_u32(&wfull[b]), (uint32_t)(tma_issued[b] - 1) & 1u, kTcDrainNs);
+                atomicExch(err, 1);
+            }
+        }
+    } else {
+        // both tiles: boundary -> A operands of window 0 (every element copy in
+        // flight at once through tile Y's operand space; Y via registers)
+        constexpr int kPer = (1 << kTcTile) / kTcThreads;
+        float2 *stage = (float2 *)(smem + 2 * kAOp);
 #pragma unroll
-    for (int tt = 0; tt < 2; ++tt)
+        for (int tt = 0; tt < 2; ++tt)
+#pragma unroll
+            for (int m = 0; m < kPer; ++m) {
+                const uint32_t i = tid + (uint32_t)m * kTcThreads;
+                const uint32_t dd = smem_u32(stage + tt * (1 << kTcTile) + i);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dd),
+                             "l"(st + gb[tt] + (lut_lo[i & 127] | lut_hi[i >> 7]))
+                             : "memory");
+            }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 #pragma unroll
         for (int m = 0; m < kPer; ++m) {
             const uint32_t i = tid + (uint32_t)m * kTcThreads;
-            const uint32_t d = smem_u32(stage + tt * (1 << kTcTile) + i);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d),
-                         "l"(st + gb[tt] + (lut_lo[i & 127] | lut_hi[i >> 7]))
-                         : "memory");
+            const float2 x = stage[i];
+            st_hilo(smem, alo[i & 127] ^ ahi[i >> 7], x.x, x.y);
         }
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        float2 yv[kPer];
 #pragma unroll
-    for (int m = 0; m < kPer; ++m) {
-        const uint32_t i = tid + (uint32_t)m * kTcThreads;
-        const float2 x = stage[i];
-        st_hilo(smem, alo[i & 127] ^ ahi[i >> 7], x.x, x.y);
-    }
-    float2 yv[kPer];
+        for (int m = 0; m < kPer; ++m) yv[m] = stage[(1 << kTcTile) + tid + m * kTcThreads];
+        asm volatile("bar.sync 1, %0;" ::"n"(kTcThreads));   // drain warps only: staging reads done
 #pragma unroll
-    for (int m = 0; m < kPer; ++m) yv[m] = stage[(1 << kTcTile) + tid + m * kTcThreads];
-    __syncthreads();
-#pragma unroll
-    for (int m = 0; m < kPer; ++m) {
-        const uint32_t i = tid + (uint32_t)m * kTcThreads;
-        st_hilo(smem + 2 * kAOp, alo[i & 127] ^ ahi[i >> 7], yv[m].x, yv[m].y);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    bool issued_any = false;
-    for (int w = 0; w < nw; ++w) {
-        // MMAs of tile X, window w
-        if (tid == 0) {
-            if (!mbar_wait(smem_u32(&wbar[w & 1]), (uint32_t)(w >> 1) & 1u, wait_ns)) {
-                abort_sh = 1;
-            } else {
-                ++tma_waited[w & 1];
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                issue_tile_mmas(taddr, sbase, sW + (w & 1) * kWMat);
-                commit_to(&mbar[0]);
-                issued_any = true;
-            }
-        }
-        // tile Y: result of window w-1 -> operands of window w
-        if (w > 0) {
-            if (!mbar_wait(smem_u32(&mbar[1]), (uint32_t)(w - 1) & 1u, wait_ns)) abort_sh = 1;
-            else {
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                drain_tile(taddr + 64, sw[w - 1], sw[w].cb, smem + 2 * kAOp, nullptr);
-            }
+        for (int m = 0; m < kPer; ++m) {
+            const uint32_t i = tid + (uint32_t)m * kTcThreads;
+            st_hilo(smem + 2 * kAOp, alo[i & 127] ^ ahi[i >> 7], yv[m].x, yv[m].y);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        if (abort_sh) break;
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            // window buffer (w-1) & 1 is free (X and Y of window w-1 are done): next matrix in
-            if (w > 0 && w + 1 < nw) {
-                bulk_load(sW + ((w + 1) & 1) * kWMat, wp + (size_t)(w + 1) * kWFloats, kWMat, &wbar[(w + 1) & 1]);
-                ++tma_issued[(w + 1) & 1];
+        asm volatile("bar.sync 1, %0;" ::"n"(kTcThreads));   // both operands complete
+        if (lane == 0) { mbar_arrive(&afull[0]); mbar_arrive(&afull[1]); }
+        for (int w = 0; w < nw; ++w) {
+            for (int t = 0; t < 2; ++t) {
+                if (ab()) break;
+                if (!mbar_wait(smem_u32(&dfull[t]), (uint32_t)w & 1u, wait_ns)) { abort_sh = 1; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                if (w + 1 < nw) {
+                    drain_tile(taddr + 64u * t, sw[w], sw[w + 1].cb, smem + 2 * kAOp * t, nullptr);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&afull[t]);
+                } else {
+                    drain_tile(taddr + 64u * t, sw[w], gcb, nullptr, st + gb[t]);
+                }
             }
-            issue_tile_mmas(taddr + 64, sbase + 2 * kAOp, sW + (w & 1) * kWMat);
-            commit_to(&mbar[1]);
-        }
-        // tile X: result of window w -> operands of window w+1, or the boundary
-        if (!mbar_wait(smem_u32(&mbar[0]), (uint32_t)w & 1u, wait_ns)) abort_sh = 1;
-        else {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            if (w + 1 < nw) drain_tile(taddr, sw[w], sw[w + 1].cb, smem, nullptr);
-            else drain_tile(taddr, sw[w], gcb, nullptr, st + gb[0]);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        if (abort_sh) break;
-    }
-    if (!abort_sh) {
-        // tile Y: last window's result -> the boundary
-        if (!mbar_wait(smem_u32(&mbar[1]), (uint32_t)(nw - 1) & 1u, wait_ns)) abort_sh = 1;
-        else {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            drain_tile(taddr + 64, sw[nw - 1], gcb, nullptr, st + gb[1]);
-        }
-    }
-    __syncthreads();
-    if (abort_sh) {
-        // drain what thread 0 issued: every MMA (one more commit tracks them all)
-        // and bulk copies not yet waited for, then report
-        if (tid == 0) {
-            if (issued_any) {
-                commit_to(&fbar);
-                mbar_wait(smem_u32(&fbar), 0u, kTcDrainNs);
-            }
-            for (int b = 0; b < 2; ++b)
-                if (tma_issued[b] > tma_waited[b])
-                    mbar_wait(smem_u32(&wbar[b]), (uint32_t)(tma_issued[b] - 1) & 1u, kTcDrainNs);
-            atomicExch(err, 1);
+            if (ab()) break;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -456,7 +453,7 @@ cudaError_t run_passes_tc(const BrickDev &d, const BrickPass *hpasses, const Bri
             const BrickPass &ps = hpasses[d.pass_off[side] + p];
             tc_wmat_kernel<<<dim3(ps.n_rp, npairs), 32, 0, st>>>(d, side, ps, dp.gates, dp.rpasses, dp.rgates, maps, wm);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            brick_tc_pass_kernel<<<dim3(1u << (d.N - kTcTile - 1), npairs), kTcThreads, kTcSmem, st>>>(
+            brick_tc_pass_kernel<<<dim3(1u << (d.N - kTcTile - 1), npairs), kTcThreads + 32, kTcSmem, st>>>(
                 d, side, ps, dp.tcwins, wm, states, err, wait_limit_ns());
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
