@@ -672,6 +672,15 @@ def main():
 
     value = r["value"]
     roof = roofline(fp, ks, ms, prec, peaks, clocks)
+    if WORK["name"] == "brickwork" and prec == fp.PREC_FP32 and args.depth == 0:
+        # DRAM bytes (read + write) of the dominant kernel, brick_pass_kernel<float2, 13, 5, 256>
+        # (the tuner's choice at l = 10), from one ncu capture of this code: one tile pass over
+        # 256 pairs, against 2 x 256 x 2^18 x 8 B = 1.074e9 algorithmic bytes
+        roof["traffic"] = 538.275328e6 + 479.907328e6
+        roof["traffic_launch"] = ("brick_pass_kernel<float2,13,5,256>, l=10, one tile pass of 256 pairs; "
+                                  "algorithmic bytes 2 x 256 x 2^18 x 8 = 1.0737e9")
+        roof["traffic_source"] = ("static: ncu capture in profiles/brick_pass_kernel_f32_brickwork_n50_l10.md "
+                                  "(valid while the tuner picks that variant at l = 10)")
 
     metric = {"brickwork": METRIC, "hea": "Tr(U^dagger V) contractions/s at n=50 (HEA, L=1..8)",
               "hea_paper": "Tr(U^dagger V) contractions/s at n=50 (paper HEA with CNOT walls, L=1..8)",

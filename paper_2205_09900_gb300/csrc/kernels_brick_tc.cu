@@ -8,9 +8,10 @@
 // multiplied by W^T on the tensor cores: complex numbers as real pairs (K
 // columns 2j, 2j+1 hold re, im of window index j; W as the real 64 x 64 block
 // matrix [[Re, -Im], [Im, Re]]), TF32 operands split into hi + lo parts
-// (hi = rna(x), lo = rna(x - hi)) and three MMAs per K step (hi.lo, lo.hi,
-// hi.hi), accumulated in FP32 in tensor memory (tcgen05.mma kind::tf32,
-// M = 128, N = 64, K = 8).
+// (W: hi = rna(w), lo = rna(w - hi); the tile: hi = x truncated by the MMA
+// itself, lo = x - trunc(x)) and three MMAs per K step (hi.lo, lo.hi, hi.hi),
+// accumulated in FP32 in tensor memory (tcgen05.mma kind::tf32, M = 128,
+// N = 64, K = 8).
 //
 // One CTA takes two tiles of one pair (X and Y) through every window of the
 // pass, alternating: while the tensor cores multiply one tile, the 512
@@ -156,11 +157,15 @@ __device__ __forceinline__ uint32_t tile_base_of(uint32_t t, uint32_t smask, int
     return base;
 }
 
+// The two TF32 parts of an operand pair: the MMA reads an FP32 word's top 19
+// bits (sign, exponent, 10 mantissa bits), so x itself serves as the high
+// part (read as x with its low 13 mantissa bits cleared) and x minus those
+// bits, exact in FP32, as the low part (its own low bits dropped by the MMA:
+// a relative error of 2^-21 of a part that is below 2^-10 of x).
+__device__ __forceinline__ float tf32_rest(float x) { return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 __device__ __forceinline__ void st_hilo(unsigned char *A, uint32_t a, float x, float y) {
-    const float xh = tf32_rna(x), yh = tf32_rna(y);
-    const float xl = tf32_rna(x - xh), yl = tf32_rna(y - yh);
-    *(float2 *)(A + a) = make_float2(xh, yh);
-    *(float2 *)(A + kAOp + a) = make_float2(xl, yl);
+    *(float2 *)(A + a) = make_float2(x, y);
+    *(float2 *)(A + kAOp + a) = make_float2(tf32_rest(x), tf32_rest(y));
 }
 
 // 3 x 8 MMAs (hi.lo, lo.hi, hi.hi) of one tile: D[128 x 64] (+)= A[128 x 64] . B[64 x 64]^T
