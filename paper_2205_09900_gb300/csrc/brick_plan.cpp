@@ -8,6 +8,7 @@
 // most not-yet-applied gates whose bits lie in the arc and whose
 // predecessors (gates of the previous layer sharing a bit) are applied.
 #include <algorithm>
+#include <array>
 #include <cstring>
 
 #include "brick.h"
@@ -257,27 +258,117 @@ static uint16_t tc_rotation(const TcWin &cw, const TcWin &nx) {
     return best_m;
 }
 
+// Rank over GF(2) of 4-bit vectors.
+static int rank_bits4(uint32_t *v, int nv) {
+    int r = 0;
+    for (int bit = 3; bit >= 0 && r < nv; --bit) {
+        int p = -1;
+        for (int i = r; i < nv; ++i)
+            if ((v[i] >> bit) & 1u) { p = i; break; }
+        if (p < 0) continue;
+        std::swap(v[r], v[p]);
+        for (int i = 0; i < nv; ++i)
+            if (i != r && ((v[i] >> bit) & 1u)) v[i] ^= v[r];
+        ++r;
+    }
+    return r;
+}
+
+// A window's operand layout for a given row order (tile bits of row positions 0..6).
+static void tc_layout(TcWin &t, const RegPass &rp, const uint8_t *rows) {
+    std::memset(&t, 0, sizeof t);
+    for (int k = 0; k < kMaxWin; ++k) {
+        t.win[k] = rp.win[k];
+        t.cb[rp.win[k]] = tc_addr(0, 1u << k);
+    }
+    for (int r = 0; r < kTcRows; ++r) {
+        t.row[r] = rows[r];
+        t.cb[rows[r]] = tc_addr(1u << r, 0);
+    }
+}
+
 std::vector<TcWin> make_tc_windows(const BrickHostPlan &P) {
     std::vector<TcWin> out(P.rpasses.size());
-    for (size_t w = 0; w < P.rpasses.size(); ++w) {
-        const RegPass &rp = P.rpasses[w];
-        TcWin &t = out[w];
-        std::memset(&t, 0, sizeof t);
-        int in_win[32] = {0};
-        for (int k = 0; k < kMaxWin; ++k) {
-            t.win[k] = rp.win[k];
-            in_win[rp.win[k]] = 1;
-            t.cb[rp.win[k]] = tc_addr(0, 1u << k);
+    for (const BrickPass &ps : P.passes) {
+        // Row orders of the pass's windows.  The 16 lanes of a half-warp drain the
+        // rows that differ in row positions 0-3 and store into the next window's
+        // layout; they hit distinct 8-byte bank pairs when those 4 tile bits have
+        // linearly independent bank contributions there (next-window positions 0-3:
+        // bank bits 0-3; next-layout row positions 0, 1, 2: bank bits 1, 2, 3 through
+        // the swizzle; the rest: none).  A dynamic program over the ordered choice
+        // of the first 4 row positions of every window minimises the rank deficit
+        // summed over the transitions; the rest of the rows stay ascending.
+        const int nw = ps.n_rp;
+        std::vector<std::vector<uint8_t>> rowbits(nw);
+        for (int w = 0; w < nw; ++w) {
+            const RegPass &rp = P.rpasses[ps.rp_off + w];
+            int in_win[32] = {0};
+            for (int k = 0; k < kMaxWin; ++k) in_win[rp.win[k]] = 1;
+            for (int b = 0; b < kTcTile; ++b)
+                if (!in_win[b]) rowbits[w].push_back((uint8_t)b);
         }
-        for (int b = 0, r = 0; b < kTcTile; ++b)
-            if (!in_win[b]) {
-                t.row[r] = (uint8_t)b;
-                t.cb[b] = tc_addr(1u << r, 0);
-                ++r;
+        // candidate prefixes: ordered 4-tuples of distinct row bits (indices into rowbits)
+        std::vector<std::array<uint8_t, 4>> pre;
+        for (int a = 0; a < kTcRows; ++a)
+            for (int b = 0; b < kTcRows; ++b)
+                for (int c = 0; c < kTcRows; ++c)
+                    for (int d = 0; d < kTcRows; ++d)
+                        if (a != b && a != c && a != d && b != c && b != d && c != d)
+                            pre.push_back({(uint8_t)a, (uint8_t)b, (uint8_t)c, (uint8_t)d});
+        const int np = (int)pre.size();
+        auto rows_of = [&](int w, int pi, uint8_t *rows) {
+            bool used[kTcRows] = {false};
+            for (int i = 0; i < 4; ++i) {
+                rows[i] = rowbits[w][pre[pi][i]];
+                used[pre[pi][i]] = true;
             }
+            for (int j = 0, r = 4; j < kTcRows; ++j)
+                if (!used[j]) rows[r++] = rowbits[w][j];
+        };
+        // bank contribution (4 bits) of tile bit b in window w's layout with prefix pi
+        auto bank = [&](int w, int pi, int b) -> uint32_t {
+            const RegPass &rp = P.rpasses[ps.rp_off + w];
+            for (int k = 0; k < kMaxWin; ++k)
+                if (rp.win[k] == b) return k < 4 ? 1u << k : 0u;
+            for (int r = 0; r < 3; ++r)
+                if (rowbits[w][pre[pi][r]] == b) return 1u << (r + 1);
+            return 0u;
+        };
+        std::vector<std::vector<int>> cost(nw, std::vector<int>(np, 0)), from(nw, std::vector<int>(np, -1));
+        std::vector<uint32_t> bk((size_t)np * kTcTile);
+        for (int w = 1; w < nw; ++w) {
+            for (int q = 0; q < np; ++q)
+                for (int b = 0; b < kTcTile; ++b) bk[(size_t)q * kTcTile + b] = bank(w, q, b);
+            // the transition depends on the previous prefix only through its 4 lane bits
+            for (int q = 0; q < np; ++q) {
+                int best = 1 << 30, arg = 0;
+                const uint32_t *bq = &bk[(size_t)q * kTcTile];
+                for (int p = 0; p < np && best > 0; ++p) {
+                    if (cost[w - 1][p] >= best) continue;
+                    uint32_t v[4];
+                    for (int i = 0; i < 4; ++i) v[i] = bq[rowbits[w - 1][pre[p][i]]];
+                    const int c = cost[w - 1][p] + 4 - rank_bits4(v, 4);
+                    if (c < best) { best = c; arg = p; }
+                }
+                cost[w][q] = best;
+                from[w][q] = arg;
+            }
+        }
+        int q = 0;
+        for (int i = 1; i < np; ++i)
+            if (cost[nw - 1][i] < cost[nw - 1][q]) q = i;
+        std::vector<int> choice(nw);
+        for (int w = nw - 1; w >= 0; --w) {
+            choice[w] = q;
+            if (w > 0) q = from[w][q];
+        }
+        for (int w = 0; w < nw; ++w) {
+            uint8_t rows[kTcRows];
+            rows_of(w, choice[w], rows);
+            tc_layout(out[ps.rp_off + w], P.rpasses[ps.rp_off + w], rows);
+        }
+        for (int w = 0; w + 1 < nw; ++w) out[ps.rp_off + w].rotm = tc_rotation(out[ps.rp_off + w], out[ps.rp_off + w + 1]);
     }
-    for (const BrickPass &ps : P.passes)
-        for (int w = 0; w + 1 < ps.n_rp; ++w) out[ps.rp_off + w].rotm = tc_rotation(out[ps.rp_off + w], out[ps.rp_off + w + 1]);
     return out;
 }
 
