@@ -171,13 +171,16 @@ __device__ __forceinline__ void st_hilo(unsigned char *A, uint32_t a, float x, f
 // 3 x 8 MMAs (hi.lo, lo.hi, hi.hi) of one tile: D[128 x 64] (+)= A[128 x 64] . B[64 x 64]^T
 __device__ __forceinline__ void issue_tile_mmas(uint32_t dtm, uint32_t sA, uint32_t sW) {
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
-    const uint32_t pa[3] = {sA, sA + kAOp, sA}, pb[3] = {sW + 16384, sW, sW};
+    // base descriptors once; a K step adds its byte offset / 16 to the address field
+    // (shared-memory addresses stay below 256 KB, so the 14-bit field never carries)
+    const uint64_t dA[3] = {desc_sw128(sA), desc_sw128(sA + kAOp), desc_sw128(sA)};
+    const uint64_t dB[3] = {desc_sw128(sW + 16384), desc_sw128(sW), desc_sw128(sW)};
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
-            const uint64_t ad = desc_sw128(pa[p] + (s >> 2) * 16384 + (s & 3) * 32);
-            const uint64_t bd = desc_sw128(pb[p] + (s >> 2) * 8192 + (s & 3) * 32);
+            const uint64_t ad = dA[p] + (uint64_t)((((s >> 2) * 16384) + (s & 3) * 32) >> 4);
+            const uint64_t bd = dB[p] + (uint64_t)((((s >> 2) * 8192) + (s & 3) * 32) >> 4);
             const uint32_t acc = (p > 0 || s > 0) ? 1u : 0u;
             asm volatile(
                 "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %4, 0;\n\t"
@@ -430,6 +433,201 @@ __global__ void __launch_bounds__(kTcThreads + 32, 1)
     if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(taddr));
 }
 
+// ---------------------------------------------------------------------------
+// One tile per CTA, two CTAs per SM (96 KB of operands and one window-matrix
+// buffer each, 64 tensor-memory columns): 8 drain warps (16 outputs per
+// thread) and a control warp.  Per window the control lane waits for the
+// operand and the matrix, issues the 24 MMAs and, once they are done, loads the
+// next window's matrix into the one buffer -- while the drain warps empty the
+// accumulator -- so the matrix load overlaps the drain, and the other CTA on
+// the SM keeps the tensor cores busy while this one loads, drains and stores.
+constexpr int kTc1Drain = 256;
+constexpr size_t kTc1Smem = 2 * (size_t)kAOp + (size_t)kWMat + 1024;
+
+__device__ __forceinline__ void drain_tile16(uint32_t tm, const TcWin &cw, const uint32_t *__restrict__ cbn,
+                                             unsigned char *A, float2 *gdst) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t v[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(tm + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2))));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const uint32_t r = 32u * (warp & 3) + lane;
+    uint32_t base = 0;
+#pragma unroll
+    for (int t = 0; t < kTcRows; ++t)
+        if ((r >> t) & 1u) base ^= cbn[cw.row[t]];
+    if (warp >> 2) base ^= cbn[cw.win[4]];   // window output bit 4
+    const uint32_t c0 = cbn[cw.win[0]], c1 = cbn[cw.win[1]], c2 = cbn[cw.win[2]], c3 = cbn[cw.win[3]];
+    // the store order of TcWin::rotm over output bits 0-2 (as in drain_tile)
+    const uint32_t rm = A ? cw.rotm : 0u, l4 = (uint32_t)lane & 15u;
+    const int rot = (__popc(l4 & (rm & 15u)) & 1) | ((__popc(l4 & ((rm >> 4) & 15u)) & 1) << 1) |
+                    ((__popc(l4 & ((rm >> 8) & 15u)) & 1) << 2);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        if ((rot >> b) & 1) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                if (!((u >> b) & 1)) {
+                    const int w2 = u | (1 << b);
+                    uint32_t t0 = v[2 * u], t1 = v[2 * u + 1];
+                    v[2 * u] = v[2 * w2]; v[2 * u + 1] = v[2 * w2 + 1];
+                    v[2 * w2] = t0; v[2 * w2 + 1] = t1;
+                }
+        }
+    }
+    base ^= ((rot & 1) ? c0 : 0u) ^ ((rot & 2) ? c1 : 0u) ^ ((rot & 4) ? c2 : 0u);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {   // register u holds output u ^ rot (bits 0-2)
+        const uint32_t a = base ^ ((u & 1) ? c0 : 0u) ^ ((u & 2) ? c1 : 0u) ^ ((u & 4) ? c2 : 0u) ^ ((u & 8) ? c3 : 0u);
+        const float x = __uint_as_float(v[2 * u]), y = __uint_as_float(v[2 * u + 1]);
+        if (A) st_hilo(A, a, x, y);
+        else gdst[a] = make_float2(x, y);
+    }
+}
+
+__global__ void __launch_bounds__(kTc1Drain + 32, 2)
+    brick_tc1_pass_kernel(BrickDev d, int side, BrickPass ps, const TcWin *__restrict__ wins,
+                          const float *__restrict__ wm, float2 *__restrict__ states, int *err, uint64_t wait_ns) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t wfull, dfull, afull, fbar;
+    __shared__ uint32_t taddr_sh;
+    __shared__ int abort_sh;
+    __shared__ int pos[32];
+    __shared__ uint32_t lut_lo[128], lut_hi[1 << (kTcTile - 7)], alo[128], ahi[1 << (kTcTile - 7)], gcb[kTcTile];
+    __shared__ TcWin sw[kMaxTcWins];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool ctrl = warp == kTc1Drain / 32;
+    const int nw = ps.n_rp;
+    const int N = d.N;
+    const uint32_t S = 1u << N;
+    if (tid == 0) {
+        abort_sh = *(volatile const int *)err;   // an earlier launch timed out
+        int k = 0;
+        for (int b = 0; b < N; ++b)
+            if (ps.smask & (1u << b)) pos[k++] = b;
+    }
+    for (int i = tid; i < nw; i += kTc1Drain + 32) sw[i] = wins[ps.rp_off + i];
+    __syncthreads();
+    if (abort_sh) return;
+    for (int i = tid; i < 128; i += kTc1Drain + 32) {
+        uint32_t o = 0, a = 0;
+        for (int k = 0; k < 7; ++k)
+            if ((i >> k) & 1) { o |= 1u << pos[k]; a ^= sw[0].cb[k]; }
+        lut_lo[i] = o;
+        alo[i] = a;
+    }
+    if (tid < (1 << (kTcTile - 7))) {
+        uint32_t o = 0, a = 0;
+        for (int k = 0; k < kTcTile - 7; ++k)
+            if ((tid >> k) & 1) { o |= 1u << pos[7 + k]; a ^= sw[0].cb[7 + k]; }
+        lut_hi[tid] = o;
+        ahi[tid] = a;
+    }
+    if (tid < kTcTile) gcb[tid] = 1u << pos[tid];
+    if (tid < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&taddr_sh)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 32) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&wfull)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&dfull)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull)), "r"(kTc1Drain / 32));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t taddr = taddr_sh;
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t sW = sbase + 2 * kAOp;
+    const float *wp = wm + (size_t)blockIdx.y * nw * kWFloats;
+    auto ab = [&]() { return *(volatile int *)&abort_sh != 0; };
+    float2 *st = states + ((size_t)blockIdx.y * 2 + side) * S;
+    const uint32_t gb = tile_base_of(blockIdx.x, ps.smask, N);
+    if (ctrl) {
+        if (lane == 0) {
+            int tma_issued = 0, tma_waited = 0;
+            bool any = false;
+            bulk_load(sW, wp, kWMat, &wfull);
+            ++tma_issued;
+            for (int w = 0; w < nw && !ab(); ++w) {
+                if (!mbar_wait(smem_u32(&afull), (uint32_t)w & 1u, wait_ns)) { abort_sh = 1; break; }
+                if (!mbar_wait(smem_u32(&wfull), (uint32_t)w & 1u, wait_ns)) { abort_sh = 1; break; }
+                ++tma_waited;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                issue_tile_mmas(taddr, sbase, sW);
+                commit_to(&dfull);
+                any = true;
+                if (w + 1 < nw) {   // the buffer is free once these MMAs are done
+                    if (!mbar_wait(smem_u32(&dfull), (uint32_t)w & 1u, wait_ns)) { abort_sh = 1; break; }
+                    bulk_load(sW, wp + (size_t)(w + 1) * kWFloats, kWMat, &wfull);
+                    ++tma_issued;
+                }
+            }
+            if (ab()) {
+                if (any) {
+                    commit_to(&fbar);
+                    mbar_wait(smem_u32(&fbar), 0u, kTcDrainNs);
+                }
+                if (tma_issued > tma_waited) mbar_wait(smem_u32(&wfull), (uint32_t)(tma_issued - 1) & 1u, kTcDrainNs);
+                atomicExch(err, 1);
+            }
+        }
+    } else {
+        // the tile: boundary -> A operand of window 0 (all copies in flight at once,
+        // staged in the operand's low half, converted through registers)
+        constexpr int kPer = (1 << kTcTile) / kTc1Drain;
+        float2 *stage = (float2 *)(smem + kAOp);
+#pragma unroll
+        for (int m = 0; m < kPer; ++m) {
+            const uint32_t i = tid + (uint32_t)m * kTc1Drain;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(stage + i)),
+                         "l"(st + gb + (lut_lo[i & 127] | lut_hi[i >> 7]))
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        float2 xv[kPer];
+#pragma unroll
+        for (int m = 0; m < kPer; ++m) xv[m] = stage[tid + m * kTc1Drain];
+        asm volatile("bar.sync 1, %0;" ::"n"(kTc1Drain));   // staging reads done
+#pragma unroll
+        for (int m = 0; m < kPer; ++m) {
+            const uint32_t i = tid + (uint32_t)m * kTc1Drain;
+            st_hilo(smem, alo[i & 127] ^ ahi[i >> 7], xv[m].x, xv[m].y);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&afull);
+        for (int w = 0; w < nw; ++w) {
+            if (ab()) break;
+            if (!mbar_wait(smem_u32(&dfull), (uint32_t)w & 1u, wait_ns)) { abort_sh = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (w + 1 < nw) {
+                drain_tile16(taddr, sw[w], sw[w + 1].cb, smem, nullptr);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&afull);
+            } else {
+                drain_tile16(taddr, sw[w], gcb, nullptr, st + gb);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(taddr));
+}
+
 }  // namespace
 
 size_t tc_wmat_bytes_per_pair(const BrickDev &d, const BrickPass *hpasses) {
@@ -451,15 +649,23 @@ bool tc_plan_ok(const BrickDev &d, const BrickPass *hpasses, const RegPass *rps)
 
 cudaError_t run_passes_tc(const BrickDev &d, const BrickPass *hpasses, const BrickDevPlan &dp, int npairs,
                           const float2 *maps, float2 *states, float *wm, int *err, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(brick_tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    const bool one = dp.persist == 3;   // one tile per CTA, two CTAs per SM
+    cudaError_t e = one ? cudaFuncSetAttribute(brick_tc1_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kTc1Smem)
+                        : cudaFuncSetAttribute(brick_tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kTcSmem);
     if (e != cudaSuccess) return e;
     for (int side = 0; side < 2; ++side)
         for (int p = 0; p < d.n_passes[side]; ++p) {
             const BrickPass &ps = hpasses[d.pass_off[side] + p];
             tc_wmat_kernel<<<dim3(ps.n_rp, npairs), 32, 0, st>>>(d, side, ps, dp.gates, dp.rpasses, dp.rgates, maps, wm);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            brick_tc_pass_kernel<<<dim3(1u << (d.N - kTcTile - 1), npairs), kTcThreads + 32, kTcSmem, st>>>(
-                d, side, ps, dp.tcwins, wm, states, err, wait_limit_ns());
+            if (one)
+                brick_tc1_pass_kernel<<<dim3(1u << (d.N - kTcTile), npairs), kTc1Drain + 32, kTc1Smem, st>>>(
+                    d, side, ps, dp.tcwins, wm, states, err, wait_limit_ns());
+            else
+                brick_tc_pass_kernel<<<dim3(1u << (d.N - kTcTile - 1), npairs), kTcThreads + 32, kTcSmem, st>>>(
+                    d, side, ps, dp.tcwins, wm, states, err, wait_limit_ns());
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     return cudaSuccess;

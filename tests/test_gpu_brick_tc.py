@@ -8,7 +8,9 @@ import pytest
 import oracle as O
 
 pytestmark = pytest.mark.gpu
-TC = "12 5 256 2"
+TC = "12 5 256 2"     # two tiles per CTA
+TC1 = "12 5 256 3"    # one tile per CTA, two CTAs per SM
+_ORACLE = {}
 
 
 @pytest.fixture(scope="module")
@@ -31,11 +33,11 @@ def _force(tmp_path, monkeypatch, n, depths, variant=TC):
     monkeypatch.setenv("FP_AUTOTUNE_CACHE", str(cache))
 
 
-@pytest.mark.parametrize("n", [30, 31])
-def test_tc_pass_matches_fp64(fp, n, tmp_path, monkeypatch):
+@pytest.mark.parametrize("n,variant", [(30, TC), (31, TC), (30, TC1), (31, TC1)])
+def test_tc_pass_matches_fp64(fp, n, variant, tmp_path, monkeypatch):
     # ragged batches (not a multiple of anything), even and odd chains; the
     # per-pair error estimate bounds the actual difference
-    _force(tmp_path, monkeypatch, n, (8, 9, 10))
+    _force(tmp_path, monkeypatch, n, (8, 9, 10), variant)
     for l in (8, 9, 10):
         ens = fp.Ensemble(fp.PARALLEL, n, l, l, seed=60 + l)
         t32, _, _, e32 = ens.trace_batch(0, 77, fp.PREC_FP32_RAW, with_err=True)
@@ -46,17 +48,19 @@ def test_tc_pass_matches_fp64(fp, n, tmp_path, monkeypatch):
         ens.close()
 
 
-def test_tc_pass_matches_oracle_n50(fp, tmp_path, monkeypatch):
+@pytest.mark.parametrize("variant", [TC, TC1])
+def test_tc_pass_matches_oracle_n50(fp, variant, tmp_path, monkeypatch):
     # one pair of each deep depth of the benchmark ensemble against the oracle
     import concurrent.futures as cf
-    _force(tmp_path, monkeypatch, 50, (8, 9, 10))
+    _force(tmp_path, monkeypatch, 50, (8, 9, 10), variant)
     picks = {8: 3, 9: 5, 10: 7}
-    refs = {}
-    with cf.ThreadPoolExecutor(max_workers=3) as ex:
-        futs = {l: ex.submit(lambda l=l: O.trace_batch(O.desc(O.PARALLEL, 50, l, seed=80 + l), picks[l], 1, "ve")[0])
-                for l in picks}
-        for l, f in futs.items():
-            refs[l] = f.result()
+    if not _ORACLE:   # computed once for both variants (about a minute of CPU at l = 10)
+        with cf.ThreadPoolExecutor(max_workers=3) as ex:
+            futs = {l: ex.submit(lambda l=l: O.trace_batch(O.desc(O.PARALLEL, 50, l, seed=80 + l), picks[l], 1,
+                                                           "ve")[0]) for l in picks}
+            for l, f in futs.items():
+                _ORACLE[l] = f.result()
+    refs = _ORACLE
     for l, p in picks.items():
         ens = fp.Ensemble(fp.PARALLEL, 50, l, l, seed=80 + l)
         t32, _, _ = ens.trace_batch(p, 1, fp.PREC_FP32)
@@ -64,9 +68,10 @@ def test_tc_pass_matches_oracle_n50(fp, tmp_path, monkeypatch):
         ens.close()
 
 
-def test_tc_pass_full_size_self_pair(fp, tmp_path, monkeypatch):
+@pytest.mark.parametrize("variant", [TC, TC1])
+def test_tc_pass_full_size_self_pair(fp, variant, tmp_path, monkeypatch):
     # V = U: Tr(U^dagger U) = 2^50 exactly, through the tensor-core passes at l = 10
-    _force(tmp_path, monkeypatch, 50, (10,))
+    _force(tmp_path, monkeypatch, 50, (10,), variant)
     ens = fp.Ensemble(fp.PARALLEL, 50, 10, 10, seed=3, flags=fp.FLAG_SELF_PAIR)
     t, _, _ = ens.trace_batch(0, 8, fp.PREC_FP32_RAW)
     assert np.all(np.abs(t / 2.0 ** 50 - 1) < 1e-4), t
