@@ -476,6 +476,15 @@ def measure_peaks(fp):
     return {nm: fp.measure_peak(w) for w, nm in names.items()}
 
 
+# DRAM read and write bytes of one tile-pass launch over 256 pairs at l = 10, per sweep
+# variant ("tile bits, window bits, threads, pass kind" as fp_brick_variant gives it),
+# from ncu captures of the committed code (the summaries under profiles/)
+TRAFFIC_L10 = {
+    "13 5 256 0": ("brick_pass_kernel<float2,13,5,256>", 538.275328e6, 479.907328e6,
+                   "profiles/brick_pass_kernel_f32_brickwork_n50_l10.md"),
+}
+
+
 def roofline(fp, ks, ms_total, prec, peaks, clocks):
     """Roofline of the dominant contraction class: algorithmic flops (8 real flops per
     complex multiply-add of the method, ks.work) over that class's device time, against
@@ -547,7 +556,15 @@ def measure(fp, args, work, P, steps, warmup, prec, stream, rank, world, dist):
             dist.barrier()
         ks = ens.kernel_stats(reset=True)
         n_skipped = int(skipped.item())
+        variants = {}
+        if WORK["kind"] in (0, 2):   # brickwork and HEA: the tuner's choice of sweep per depth
+            for dv in ens.groups():
+                try:
+                    variants[int(dv)] = " ".join(str(x) for x in ens.brick_variant(int(dv), prec))
+                except fp.FpError:
+                    pass             # depth 1 or a depth this step did not contract
         out = {"ms": ms, "ks": ks, "clocks": clocks, "mom": mom.cpu().numpy(), "groups": ens.groups(),
+               "variants": variants,
                "value": world * (P * steps - n_skipped) / (ms / 1e3), "skipped": n_skipped,
                "launches": int(sum(ks.launches[i] for i in range(8))), "tr": tr, "first_last": first_of(warmup + steps - 1)}
         ens.close()
@@ -672,15 +689,15 @@ def main():
 
     value = r["value"]
     roof = roofline(fp, ks, ms, prec, peaks, clocks)
-    if WORK["name"] == "brickwork" and prec == fp.PREC_FP32 and args.depth == 0:
-        # DRAM bytes (read + write) of the dominant kernel, brick_pass_kernel<float2, 13, 5, 256>
-        # (the tuner's choice at l = 10), from one ncu capture of this code: one tile pass over
-        # 256 pairs, against 2 x 256 x 2^18 x 8 B = 1.074e9 algorithmic bytes
-        roof["traffic"] = 538.275328e6 + 479.907328e6
-        roof["traffic_launch"] = ("brick_pass_kernel<float2,13,5,256>, l=10, one tile pass of 256 pairs; "
+    chosen = r["variants"].get(10)
+    if WORK["name"] == "brickwork" and prec == fp.PREC_FP32 and args.depth == 0 and chosen in TRAFFIC_L10:
+        # DRAM bytes (read + write) of one tile-pass launch of the sweep variant the tuner chose
+        # at l = 10 (the depth that dominates the step), from one ncu capture of this code
+        kname, rd, wr, prof = TRAFFIC_L10[chosen]
+        roof["traffic"] = rd + wr
+        roof["traffic_launch"] = (f"{kname}, l=10, one tile pass of 256 pairs; "
                                   "algorithmic bytes 2 x 256 x 2^18 x 8 = 1.0737e9")
-        roof["traffic_source"] = ("static: ncu capture in profiles/brick_pass_kernel_f32_brickwork_n50_l10.md "
-                                  "(valid while the tuner picks that variant at l = 10)")
+        roof["traffic_source"] = f"static: ncu capture in {prof} (the tuner chose '{chosen}' at l = 10 in this run)"
 
     metric = {"brickwork": METRIC, "hea": "Tr(U^dagger V) contractions/s at n=50 (HEA, L=1..8)",
               "hea_paper": "Tr(U^dagger V) contractions/s at n=50 (paper HEA with CNOT walls, L=1..8)",
@@ -690,7 +707,7 @@ def main():
             "vs_baseline": None, "dtype": "f32" if prec != fp.PREC_FP64 else "f64",
             "data": "synthetic (seeded circuit pairs)", "config": workload_config(args, world),
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-            "peaks_measured": peaks,
+            "peaks_measured": peaks, "sweep_variants": {str(k): v for k, v in r["variants"].items()},
             "kernel_ms": {fp.K_NAMES.get(i, str(i)): ks.ms[i] for i in range(8) if ks.launches[i]}}
     if WORK["name"] == "local":
         line["infeasible_pairs_in_timed_steps"] = r["skipped"]

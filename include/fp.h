@@ -358,6 +358,17 @@ fp_status fp_inject_alloc_failures(int32_t count);
  * were captured with). */
 fp_status fp_set_wait_limit_ns(uint64_t ns);
 
+/* The brickwork sweep variant chosen for one depth (FP_PARALLEL and FP_HEA
+ * ensembles, depth l >= 2): out[0] = tile bits of a tile pass (99: the whole
+ * boundary in one CTA's shared memory), out[1] = register-window bits,
+ * out[2] = threads per CTA, out[3] = pass kind (0: FP32/FP64 FMA tile passes,
+ * 1: persistent double-buffered FMA passes, 2: tensor-core passes with two
+ * tiles per CTA, 3: tensor-core passes with one tile per CTA).  The autotuner
+ * chooses it the first time the ensemble contracts that depth at that
+ * precision (FP_PREC_FP32 and FP_PREC_FP32_RAW share one choice); before that
+ * the call returns FP_ERR_ARG.  `out` is a host array of 4 int32. */
+fp_status fp_brick_variant(const fp_ensemble *ens, int32_t depth, int32_t precision, int32_t *out);
+
 /* Copy the ensemble's kernel counters into *out; reset them if `reset`. */
 fp_status fp_kernel_stats_get(fp_ensemble *ens, fp_kernel_stats *out, int32_t reset);
 

@@ -28,7 +28,7 @@ STATUS = {0: "FP_OK", -1: "FP_ERR_ARG", -2: "FP_ERR_CUDA", -3: "FP_ERR_OOM", -4:
           -5: "FP_ERR_INFEASIBLE", -6: "FP_ERR_CANCELLED"}
 
 EXPORTED = ["fp_ensemble_create", "fp_ensemble_destroy", "fp_groups", "fp_pair_groups", "fp_export_gates",
-            "fp_trace_batch", "fp_reduce_moments", "fp_frame_potential", "fp_kernel_stats_get",
+            "fp_trace_batch", "fp_reduce_moments", "fp_frame_potential", "fp_kernel_stats_get", "fp_brick_variant",
             "fp_trace_brick_static", "fp_cv_frame_potential", "fp_gemm_bf16", "fp_bootstrap", "fp_epsilon_max",
             "fp_design_layers", "fp_exact_brickwork_fk", "fp_exact_brickwork_fkq", "fp_measure_peak",
             "fp_frame_potential_resume", "fp_cancel", "fp_inject_alloc_failures", "fp_set_wait_limit_ns",
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
     L.fp_frame_potential.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double,
                                      ctypes.c_int32, vp, vp, P(RunStats)]
     L.fp_kernel_stats_get.argtypes = [vp, P(KernelStats), ctypes.c_int32]
+    L.fp_brick_variant.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32)]
     L.fp_trace_brick_static.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
                                         ctypes.c_uint64, ctypes.c_int32, vp, vp, vp]
     L.fp_cv_frame_potential.argtypes = [vp, P(CvConfig), P(CvResult)]
@@ -319,6 +320,13 @@ class Ensemble:
     def reduce_moments(self, tr_dev, group_dev, count, k_max, out):
         _check(load().fp_reduce_moments(self._h, _ptr(tr_dev), _ptr(group_dev), count, k_max, _ptr(out)))
         return out
+
+    def brick_variant(self, depth, prec=PREC_FP32):
+        """(tile bits, window bits, threads, pass kind) of the brickwork sweep the
+        autotuner chose for `depth` at `prec` (see fp_brick_variant)."""
+        out = (ctypes.c_int32 * 4)()
+        _check(load().fp_brick_variant(self._h, int(depth), int(prec), out))
+        return tuple(int(x) for x in out)
 
     def kernel_stats(self, reset=False):
         st = KernelStats()

@@ -108,6 +108,7 @@ struct BrickCache {
     DBuf d_gates, d_rpasses, d_rgates, d_tcwins;
     BrickDevPlan dp;
     size_t extra_per_pair = 0;   // tensor-core window matrices (bytes per pair, after the boundaries)
+    int variant[4] = {0, 0, 0, 0};   // tile bits, window bits, threads, pass kind (fp_brick_variant)
 };
 
 struct SpiralCache {        // one depth of the paper's HEA on the spiral sweep
@@ -520,6 +521,7 @@ fp_status check_flag(fp_ensemble *E) {
 fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int TH, int persist,
                            std::unique_ptr<BrickCache> &out) {
     auto bc = std::make_unique<BrickCache>();
+    bc->variant[0] = K; bc->variant[1] = R; bc->variant[2] = TH; bc->variant[3] = persist;
     // K > N: shared-memory sweep, K == N: one tile
     // arcs hold the 5 (FP32) or 4 (FP64) lowest bits, so that tile loads read contiguous runs;
     // the tensor-core pass (12-bit tiles) holds 3: at l = 10 a 12-bit arc through the 5
@@ -579,7 +581,9 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
     }
     const int kmin = 10;   // boundaries up to 2^10: shared-memory sweep, nothing to tune
     char ckey[256];
-    snprintf(ckey, sizeof ckey, "%s n=%d l=%d %s", E->gpu_name.c_str(), d.n, l, fp32 ? "fp32" : "fp64");
+    // the HEA's ring has its own plans: its entries carry the kind after the precision
+    snprintf(ckey, sizeof ckey, "%s n=%d l=%d %s%s", E->gpu_name.c_str(), d.n, l, fp32 ? "fp32" : "fp64",
+             d.kind == FP_HEA ? " hea" : "");
     int bestK = cands[0].K, bestR = cands[0].R, bestT = cands[0].TH, bestP = 0;
     bool have = false;
     const char *cache = getenv("FP_AUTOTUNE_CACHE");
@@ -599,6 +603,11 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
             }
             fclose(f);
         }
+    }
+    std::unique_ptr<BrickCache> cached;
+    if (have && N > kmin && make_brick_cache(E, l, fp32, bestK, bestR, bestT, bestP, cached) != FP_OK) {
+        have = false;   // a cache entry this depth cannot run (another build's file): tune instead
+        cached.reset();
     }
     if (!have && !idx.empty()) {
         const uint64_t nt = std::min<uint64_t>(idx.size(), 192);   // several waves of tiles per variant
@@ -655,9 +664,11 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
             if (f) { fprintf(f, "%s|%d %d %d %d\n", ckey, bestK, bestR, bestT, bestP); fclose(f); }
         }
     }
-    std::unique_ptr<BrickCache> bc;
-    fp_status s = make_brick_cache(E, l, fp32, bestK, bestR, bestT, bestP, bc);
-    if (s != FP_OK) return s;
+    std::unique_ptr<BrickCache> bc = std::move(cached);
+    if (!bc) {
+        fp_status s = make_brick_cache(E, l, fp32, bestK, bestR, bestT, bestP, bc);
+        if (s != FP_OK) return s;
+    }
     E->brick_plans.emplace(key, std::move(bc));
     return FP_OK;
 }
@@ -1412,6 +1423,17 @@ fp_status fp_inject_alloc_failures(int32_t count) {
 
 fp_status fp_set_wait_limit_ns(uint64_t ns) {
     g_wait_ns.store(ns ? ns : 1000000000ull);
+    return FP_OK;
+}
+
+fp_status fp_brick_variant(const fp_ensemble *ens, int32_t depth, int32_t precision, int32_t *out) {
+    if (!ens || !out) return fail(FP_ERR_ARG, "null argument");
+    if (precision != FP_PREC_FP64 && precision != FP_PREC_FP32 && precision != FP_PREC_FP32_RAW)
+        return fail(FP_ERR_ARG, "unknown precision %d", precision);
+    auto it = ens->brick_plans.find(depth * 2 + (precision != FP_PREC_FP64 ? 1 : 0));
+    if (it == ens->brick_plans.end())
+        return fail(FP_ERR_ARG, "no brickwork sweep of depth %d at this precision has run on this ensemble", depth);
+    for (int i = 0; i < 4; ++i) out[i] = it->second->variant[i];
     return FP_OK;
 }
 

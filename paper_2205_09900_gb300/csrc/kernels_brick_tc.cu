@@ -9,7 +9,7 @@
 // columns 2j, 2j+1 hold re, im of window index j; W as the real 64 x 64 block
 // matrix [[Re, -Im], [Im, Re]]), TF32 operands split into hi + lo parts
 // (W: hi = rna(w), lo = rna(w - hi); the tile: hi = x truncated by the MMA
-// itself, lo = x - trunc(x)) and three MMAs per K step (hi.lo, lo.hi, hi.hi),
+// itself, lo = rna(x - trunc(x))) and three MMAs per K step (hi.lo, lo.hi, hi.hi),
 // accumulated in FP32 in tensor memory (tcgen05.mma kind::tf32, M = 128,
 // N = 64, K = 8).
 //
@@ -159,10 +159,16 @@ __device__ __forceinline__ uint32_t tile_base_of(uint32_t t, uint32_t smask, int
 
 // The two TF32 parts of an operand pair: the MMA reads an FP32 word's top 19
 // bits (sign, exponent, 10 mantissa bits), so x itself serves as the high
-// part (read as x with its low 13 mantissa bits cleared) and x minus those
-// bits, exact in FP32, as the low part (its own low bits dropped by the MMA:
-// a relative error of 2^-21 of a part that is below 2^-10 of x).
-__device__ __forceinline__ float tf32_rest(float x) { return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// part (read as x with its low 13 mantissa bits cleared, i.e. truncated) and
+// the rest x - trunc(x), exact in FP32 and of the same sign as x, rounded to
+// the nearest TF32 value (half away from zero) as the low part.  Left to the
+// MMA's truncation, the rest would lose up to 2^-10 of itself, always towards
+// zero: a bias of up to 2^-20 of x per window that adds up over the windows of
+// a sweep; rounded, the error is at most 2^-21 of x and of either sign.
+__device__ __forceinline__ float tf32_rest(float x) {
+    const float r = x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+    return __uint_as_float((__float_as_uint(r) + 0x1000u) & 0xFFFFE000u);
+}
 __device__ __forceinline__ void st_hilo(unsigned char *A, uint32_t a, float x, float y) {
     *(float2 *)(A + a) = make_float2(x, y);
     *(float2 *)(A + kAOp + a) = make_float2(tf32_rest(x), tf32_rest(y));

@@ -91,3 +91,48 @@ def test_tc_pass_frame_potential_within_1e3(fp, tmp_path, monkeypatch):
             f32 = np.mean(np.abs(t32) ** (2 * k))
             assert abs(f32 - f64) <= 1e-3 * f64, (l, k)
         ens.close()
+
+
+@pytest.mark.parametrize("variant", [TC, TC1, "13 5 256 0"])
+def test_brick_variant_reports_the_forced_choice(fp, variant, tmp_path, monkeypatch):
+    # fp_brick_variant: FP_ERR_ARG before the depth has run, then the variant the
+    # tuner's cache file fixed, shared by FP32 and FP32 without recontraction
+    _force(tmp_path, monkeypatch, 50, (10,), variant)
+    ens = fp.Ensemble(fp.PARALLEL, 50, 10, 10, seed=5)
+    with pytest.raises(fp.FpError):
+        ens.brick_variant(10, fp.PREC_FP32)
+    ens.trace_batch(0, 4, fp.PREC_FP32_RAW)
+    want = tuple(int(x) for x in variant.split())
+    assert ens.brick_variant(10, fp.PREC_FP32) == want
+    assert ens.brick_variant(10, fp.PREC_FP32_RAW) == want
+    with pytest.raises(fp.FpError):
+        ens.brick_variant(10, fp.PREC_FP64)
+    with pytest.raises(fp.FpError):
+        ens.brick_variant(9, fp.PREC_FP32)
+    ens.close()
+
+
+def test_tune_cache_entries_are_per_kind(fp, tmp_path, monkeypatch):
+    # 12-bit tiles through the 5 lowest bits, 128 threads: a brickwork choice at l = 7, 8;
+    # the HEA's l = 7 plan of that shape has passes of 300 gates (over the limit of 255).
+    # A brickwork entry does not apply to the HEA, and an HEA entry it cannot run is
+    # retuned instead of failing the call.
+    import torch
+    name = torch.cuda.get_device_name(0)
+    cache = tmp_path / "tune.txt"
+    cache.write_text(f"{name} n=50 l=7 fp32|12 5 128 0\n{name} n=50 l=8 fp32|12 5 128 0\n"
+                     f"{name} n=50 l=7 fp32 hea|12 5 128 0\n")
+    monkeypatch.setenv("FP_AUTOTUNE_CACHE", str(cache))
+    ens = fp.Ensemble(fp.HEA, 50, 7, 8, seed=4)
+    t, _, _ = ens.trace_batch(0, 16, fp.PREC_FP32)
+    assert np.all(np.isfinite(t))
+    lines = cache.read_text().splitlines()
+    assert sum(" n=50 l=7 fp32 hea|" in x for x in lines) == 2, lines   # the unusable entry, then the tuned one
+    assert any(" n=50 l=8 fp32 hea|" in x for x in lines), lines
+    assert ens.brick_variant(7, fp.PREC_FP32) != (12, 5, 128, 0)
+    ens.close()
+    brick = fp.Ensemble(fp.PARALLEL, 50, 7, 8, seed=4)
+    brick.trace_batch(0, 8, fp.PREC_FP32)
+    assert brick.brick_variant(7, fp.PREC_FP32) == (12, 5, 128, 0)
+    assert brick.brick_variant(8, fp.PREC_FP32) == (12, 5, 128, 0)
+    brick.close()
