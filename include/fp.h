@@ -362,8 +362,9 @@ fp_status fp_set_wait_limit_ns(uint64_t ns);
  * ensembles, depth l >= 2): out[0] = tile bits of a tile pass (99: the whole
  * boundary in one CTA's shared memory), out[1] = register-window bits,
  * out[2] = threads per CTA, out[3] = pass kind (0: FP32/FP64 FMA tile passes,
- * 1: persistent double-buffered FMA passes, 2: tensor-core passes with two
- * tiles per CTA, 3: tensor-core passes with one tile per CTA).  The autotuner
+ * 1: persistent double-buffered FMA passes, 3: tensor-core passes with the
+ * tile's operand in shared memory, 4: tensor-core passes with the tile's
+ * operand in tensor memory, persistent over the tiles).  The autotuner
  * chooses it the first time the ensemble contracts that depth at that
  * precision (FP_PREC_FP32 and FP_PREC_FP32_RAW share one choice); before that
  * the call returns FP_ERR_ARG.  `out` is a host array of 4 int32. */

@@ -526,12 +526,12 @@ fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int T
     // arcs hold the 5 (FP32) or 4 (FP64) lowest bits, so that tile loads read contiguous runs;
     // the tensor-core pass (12-bit tiles) holds 3: at l = 10 a 12-bit arc through the 5
     // lowest bits would need 49 passes instead of 18
-    bc->hp = make_brick_plan(E->d.n, l, K, persist >= 2 ? 3 : (fp32 ? 5 : 4), R, E->d.kind == FP_HEA ? 1 : 0);
+    bc->hp = make_brick_plan(E->d.n, l, K, persist >= 3 ? 3 : (fp32 ? 5 : 4), R, E->d.kind == FP_HEA ? 1 : 0);
     for (const auto &ps : bc->hp.passes) {
         if (ps.n_gates > 255) return fail(FP_ERR_ARG, "tile pass with %d gates exceeds 255", ps.n_gates);
         if (ps.n_rp > 160) return fail(FP_ERR_ARG, "tile pass with %d register passes exceeds 160", ps.n_rp);
     }
-    if (persist == 2 || persist == 3) {   // tensor-core windows: FP32, 12-bit tiles, 5-bit windows only
+    if (persist == 3 || persist == 4) {   // tensor-core windows: FP32, 12-bit tiles, 5-bit windows only
         if (!fp32 || !tc_plan_ok(bc->hp.dev, bc->hp.passes.data(), bc->hp.rpasses.data()))
             return fail(FP_ERR_ARG, "the tensor-core tile pass needs FP32, %d-bit tiles, %d-bit windows and l >= 8",
                         kTcTile, kMaxWin);
@@ -574,10 +574,10 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
                                                        {13, 5, 256, 1}, {12, 4, 256, 0}, {12, 5, 128, 0}}
                                    : std::vector<Cand>{{13, 3, 512, 0}, {13, 4, 256, 0}};
     if (((size_t)1 << N) * (fp32 ? sizeof(float2) : sizeof(double2)) <= (size_t)200 * 1024) cands.push_back({99, 0, 0, 0});
-    // P = 2: tensor-core windows (TF32 x 3 tcgen05 MMAs), boundaries of more than two 12-bit tiles
+    // P = 3, 4: tensor-core windows (TF32 x 3 tcgen05 MMAs), boundaries of more than two 12-bit tiles
     if (fp32 && N >= kTcTile + 2) {
-        cands.push_back({kTcTile, kMaxWin, 256, 2});   // two tiles per CTA
-        cands.push_back({kTcTile, kMaxWin, 256, 3});   // one tile per CTA, two CTAs per SM
+        cands.push_back({kTcTile, kMaxWin, 256, 3});   // the tile's operand in shared memory
+        cands.push_back({kTcTile, kMaxWin, 256, 4});   // in tensor memory, persistent over the tiles
     }
     const int kmin = 10;   // boundaries up to 2^10: shared-memory sweep, nothing to tune
     char ckey[256];

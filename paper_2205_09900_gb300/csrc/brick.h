@@ -93,6 +93,15 @@ struct TcWin {
     // lanes of a half-warp hit 16 distinct 8-byte bank pairs (or as few
     // repeats as the layouts allow)
     uint16_t rotm;
+    // tensor-memory operand form (brick_tcm_pass_kernel): the byte offset of
+    // tile-local bit b in the 32 KB shared-memory exchange buffer through which
+    // this window's input arrives (window 0: the tile loaded from the boundary,
+    // lanes storing consecutive tile indices; window k: window k-1's results).
+    // The addresses are linear over GF(2); bits 3-6 (the 8-byte bank pair) give
+    // the storing lanes' 4 bits and this window's row positions 0-3 (the
+    // loading lanes) 16 distinct bank pairs each, the 8 tile bits outside the
+    // storing lanes' 4 fill bits 7-14 in ascending order.
+    uint32_t xcb[kTcTile];
 };
 // A-operand byte address of element (row r, window index j): complex j
 // occupies K columns 2j (re), 2j+1 (im); K splits into two 128-byte regions of
@@ -105,11 +114,11 @@ struct BrickDevPlan {
     const BrickGate *gates;
     const RegPass *rpasses;
     const RegGate *rgates;
-    const TcWin *tcwins;    // persist == 2: one per register pass
-    int *err_flag;          // persist == 2: raised by a kernel whose bounded wait ran out
+    const TcWin *tcwins;    // persist >= 2: one per register pass
+    int *err_flag;          // persist >= 2: raised by a kernel whose bounded wait ran out
     int win_bits;
     int threads;
-    int persist;        // 1: persistent double-buffered tile passes; 2: tensor-core windows
+    int persist;        // 1: persistent double-buffered tile passes; 3, 4: tensor-core windows (fp_brick_variant)
 };
 
 struct BrickHostPlan {

@@ -287,6 +287,35 @@ static void tc_layout(TcWin &t, const RegPass &rp, const uint8_t *rows) {
     }
 }
 
+// The exchange map into a window: u = the 4 tile bits the storing lanes
+// differ in (bank bits 0-3 in that order), v = the loading lanes' 4 bits (the
+// window's row positions 0-3).  v's bits outside u take the bank bits u's
+// members among them leave free, so both sets reach all 16 bank pairs; the
+// tile bits outside u give the high address bits, which makes the map a
+// bijection onto the 4096 8-byte slots.
+static void tc_exchange(uint32_t *xcb, const uint8_t *u, const uint8_t *v) {
+    uint32_t g[kTcTile] = {0};
+    bool in_u[kTcTile] = {false};
+    for (int i = 0; i < 4; ++i) {
+        g[u[i]] = 1u << i;
+        in_u[u[i]] = true;
+    }
+    uint32_t covered = 0;
+    for (int i = 0; i < 4; ++i)
+        if (in_u[v[i]]) covered |= g[v[i]];
+    int next = 0;
+    for (int i = 0; i < 4; ++i)
+        if (!in_u[v[i]]) {
+            while ((covered >> next) & 1u) ++next;
+            g[v[i]] = 1u << next;
+            covered |= 1u << next;
+        }
+    for (int b = 0, h = 0; b < kTcTile; ++b) {
+        xcb[b] = g[b] << 3;
+        if (!in_u[b]) xcb[b] |= 1u << (7 + h++);
+    }
+}
+
 std::vector<TcWin> make_tc_windows(const BrickHostPlan &P) {
     std::vector<TcWin> out(P.rpasses.size());
     for (const BrickPass &ps : P.passes) {
@@ -368,6 +397,9 @@ std::vector<TcWin> make_tc_windows(const BrickHostPlan &P) {
             tc_layout(out[ps.rp_off + w], P.rpasses[ps.rp_off + w], rows);
         }
         for (int w = 0; w + 1 < nw; ++w) out[ps.rp_off + w].rotm = tc_rotation(out[ps.rp_off + w], out[ps.rp_off + w + 1]);
+        const uint8_t first[4] = {0, 1, 2, 3};   // the tile load: lanes store consecutive tile indices
+        for (int w = 0; w < nw; ++w)
+            tc_exchange(out[ps.rp_off + w].xcb, w ? out[ps.rp_off + w - 1].row : first, out[ps.rp_off + w].row);
     }
     return out;
 }

@@ -798,7 +798,7 @@ cudaError_t launch_brick(const BrickDev &d, const BrickPass *hpasses, const Bric
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const int key = dp.persist * 10000 + d.tile_bits * 100 + dp.win_bits * 10 +
                         (dp.threads == 256 ? 1 : (dp.threads == 128 ? 2 : 0));
-        if (fp32 && (dp.persist == 2 || dp.persist == 3)) {
+        if (fp32 && (dp.persist == 3 || dp.persist == 4)) {
             float2 *sp = (float2 *)states;
             float *wm = (float *)(sp + (size_t)npairs * 2 * ((size_t)1 << d.N));
             e = run_passes_tc(d, hpasses, dp, npairs, (const float2 *)maps, sp, wm, dp.err_flag, st);

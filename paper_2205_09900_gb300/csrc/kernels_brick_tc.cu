@@ -13,15 +13,18 @@
 // accumulated in FP32 in tensor memory (tcgen05.mma kind::tf32, M = 128,
 // N = 64, K = 8).
 //
-// One CTA takes two tiles of one pair (X and Y) through every window of the
-// pass, alternating: while the tensor cores multiply one tile, the 512
-// threads read the other tile's result out of tensor memory (tcgen05.ld),
-// split it, and store it into shared memory in the next window's operand
-// layout (K-major, 128-byte swizzle; every element's address is the XOR of
-// its bits' contributions, the TcWin tables).  Window matrices stream in by
-// bulk copies (cp.async.bulk) into two buffers, one window ahead.  The first
-// window's operands are loaded from the boundary in global memory, the last
-// window's result is written back to it.
+// Two kernels.  brick_tc1_pass_kernel takes one tile per CTA, two CTAs per
+// SM: the tile's operands sit in shared memory (K-major, 128-byte swizzle;
+// every element's address is the XOR of its bits' contributions, the TcWin
+// tables), and after each window 8 drain warps read the result out of tensor
+// memory (tcgen05.ld), split it and store it into the next window's operand
+// layout.  brick_tcm_pass_kernel keeps the tile's operand in tensor memory
+// (the A operand read from TMEM), exchanges each window's result through a
+// shared-memory buffer into the next window's row order, and is persistent
+// over the tiles.  In both a control warp's lane issues every MMA and the
+// bulk copies (cp.async.bulk) of the window matrices, and meets the drain
+// warps on mbarriers only.  The first window's operand is loaded from the
+// boundary in global memory, the last window's result is written back to it.
 //
 // Every mbarrier wait is bounded by the global timer (1 s); on a timeout the
 // CTA raises the error flag, stops issuing work, drains the MMAs and bulk
@@ -29,6 +32,7 @@
 // later launches that find the flag raised return at once.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "brick.h"
@@ -38,12 +42,10 @@ namespace fpk {
 namespace {
 
 constexpr uint64_t kTcDrainNs = 1000000000ull;   // waits for work already issued (after a timeout)
-constexpr int kTcThreads = 512;
 constexpr int kMaxTcWins = 48;
 constexpr uint32_t kAOp = 32768;                 // bytes of one A operand (hi or lo) of one tile
 constexpr uint32_t kWMat = 32768;                // bytes of one window matrix (hi + lo)
 constexpr uint32_t kWFloats = kWMat / 4;
-constexpr size_t kTcSmem = 4 * (size_t)kAOp + 2 * (size_t)kWMat + 1024;
 
 __device__ __forceinline__ uint64_t gtimer() {
     uint64_t t;
@@ -174,7 +176,12 @@ __device__ __forceinline__ void st_hilo(unsigned char *A, uint32_t a, float x, f
     *(float2 *)(A + kAOp + a) = make_float2(tf32_rest(x), tf32_rest(y));
 }
 
-// 3 x 8 MMAs (hi.lo, lo.hi, hi.hi) of one tile: D[128 x 64] (+)= A[128 x 64] . B[64 x 64]^T
+// 3 x 8 MMAs of one tile: D[128 x 64] (+)= A[128 x 64] . B[64 x 64]^T, the
+// products of the low parts first (hi.lo, then lo.hi, over all K steps), then
+// hi.hi.  The tensor core's FP32 accumulation truncates: with the small terms
+// summed before the large ones they keep their bits (adding them K step by K
+// step to the large partial sums instead tripled the measured error and its
+// bias towards zero).
 __device__ __forceinline__ void issue_tile_mmas(uint32_t dtm, uint32_t sA, uint32_t sW) {
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
     // base descriptors once; a K step adds its byte offset / 16 to the address field
@@ -207,236 +214,8 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
                  : "memory");
 }
 
-// Read this thread's 8 complex results of one tile out of tensor memory and
-// scatter them: into the A operands of the next window (next != nullptr:
-// address = XOR of next[b] over the element's tile bits) or to the boundary
-// in global memory (gdst, contributions gcb: physical index bits).  Warp w
-// reads TMEM lanes 32 (w mod 4) .. + 31 (tile rows) and columns 16 (w / 4) ..
-// + 15 (window outputs 8 (w / 4) .. + 7, as re, im pairs).
-__device__ __forceinline__ void drain_tile(uint32_t tm, const TcWin &cw, const uint32_t *__restrict__ cbn,
-                                           unsigned char *A, float2 *gdst) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t v[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(tm + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * (warp >> 2))));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const uint32_t r = 32u * (warp & 3) + lane;
-    uint32_t base = 0;
-#pragma unroll
-    for (int t = 0; t < kTcRows; ++t)
-        if ((r >> t) & 1u) base ^= cbn[cw.row[t]];
-    const int og = warp >> 2;   // window output bits 3, 4
-    if (og & 1) base ^= cbn[cw.win[3]];
-    if (og & 2) base ^= cbn[cw.win[4]];
-    const uint32_t c0 = cbn[cw.win[0]], c1 = cbn[cw.win[1]], c2 = cbn[cw.win[2]];
-    // lanes of a half-warp whose rows map to the same bank pairs would collide
-    // if they stored the same output at once: each lane visits its 8 outputs in
-    // the order u ^ rot (a butterfly of register swaps), rot a linear function
-    // of the lane bits chosen on the host for this pair of layouts (TcWin::rotm)
-    const uint32_t rm = A ? cw.rotm : 0u, l4 = (uint32_t)lane & 15u;
-    const int rot = (__popc(l4 & (rm & 15u)) & 1) | ((__popc(l4 & ((rm >> 4) & 15u)) & 1) << 1) |
-                    ((__popc(l4 & ((rm >> 8) & 15u)) & 1) << 2);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        if ((rot >> b) & 1) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (!((u >> b) & 1)) {
-                    const int w2 = u | (1 << b);
-                    uint32_t t0 = v[2 * u], t1 = v[2 * u + 1];
-                    v[2 * u] = v[2 * w2]; v[2 * u + 1] = v[2 * w2 + 1];
-                    v[2 * w2] = t0; v[2 * w2 + 1] = t1;
-                }
-        }
-    }
-    base ^= ((rot & 1) ? c0 : 0u) ^ ((rot & 2) ? c1 : 0u) ^ ((rot & 4) ? c2 : 0u);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {   // register u holds output u ^ rot
-        const uint32_t a = base ^ ((u & 1) ? c0 : 0u) ^ ((u & 2) ? c1 : 0u) ^ ((u & 4) ? c2 : 0u);
-        const float x = __uint_as_float(v[2 * u]), y = __uint_as_float(v[2 * u + 1]);
-        if (A) st_hilo(A, a, x, y);
-        else gdst[a] = make_float2(x, y);
-    }
-}
-
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Warp roles: warps 0..15 drain (TMEM -> next operand, 8 outputs per thread),
-// warp 16 controls (lane 0 issues the bulk copies of the window matrices and
-// every MMA).  They meet only on mbarriers, per tile t (X = 0, Y = 1):
-//   afull[t]  completion k: the operand of tile t for window k is in shared
-//             memory (one arrival per drain warp);
-//   dfull[t]  completion k: the MMAs of tile t, window k, are done (commit);
-//   wfull[b]  the window matrix in buffer b has arrived (bulk copy).
-// Each drain warp works through X(w), Y(w), X(w+1), ... as soon as each MMA
-// is done; the control lane issues X(w), Y(w) as soon as both operands and
-// the matrix are there, and reloads a matrix buffer once Y(w) -- and with it
-// every earlier MMA -- is done.
-__global__ void __launch_bounds__(kTcThreads + 32, 1)
-    brick_tc_pass_kernel(BrickDev d, int side, BrickPass ps, const TcWin *__restrict__ wins,
-                         const float *__restrict__ wm, float2 *__restrict__ states, int *err, uint64_t wait_ns) {
-    extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t wfull[2], dfull[2], afull[2], fbar;
-    __shared__ uint32_t taddr_sh;
-    __shared__ int abort_sh;
-    __shared__ int pos[32];
-    __shared__ uint32_t lut_lo[128], lut_hi[1 << (kTcTile - 7)], alo[128], ahi[1 << (kTcTile - 7)], gcb[kTcTile];
-    __shared__ TcWin sw[kMaxTcWins];
-    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool ctrl = warp == kTcThreads / 32;
-    const int nw = ps.n_rp;
-    const int N = d.N;
-    const uint32_t S = 1u << N;
-    if (tid == 0) abort_sh = *(volatile const int *)err;   // an earlier launch timed out
-    if (tid == 0) {
-        int k = 0;
-        for (int b = 0; b < N; ++b)
-            if (ps.smask & (1u << b)) pos[k++] = b;
-    }
-    for (int i = tid; i < nw; i += kTcThreads + 32) sw[i] = wins[ps.rp_off + i];
-    __syncthreads();
-    if (abort_sh) return;
-    for (int i = tid; i < 128; i += kTcThreads + 32) {
-        uint32_t o = 0, a = 0;
-        for (int k = 0; k < 7; ++k)
-            if ((i >> k) & 1) { o |= 1u << pos[k]; a ^= sw[0].cb[k]; }
-        lut_lo[i] = o;
-        alo[i] = a;
-    }
-    if (tid < (1 << (kTcTile - 7))) {
-        uint32_t o = 0, a = 0;
-        for (int k = 0; k < kTcTile - 7; ++k)
-            if ((tid >> k) & 1) { o |= 1u << pos[7 + k]; a ^= sw[0].cb[7 + k]; }
-        lut_hi[tid] = o;
-        ahi[tid] = a;
-    }
-    if (tid < kTcTile) gcb[tid] = 1u << pos[tid];
-    if (tid < 32) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&taddr_sh)));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (tid == 32) {
-        for (int b = 0; b < 2; ++b) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&wfull[b])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&dfull[b])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull[b])), "r"(kTcThreads / 32));
-        }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fbar)));
-        asm volatile("fence.mbarrier_init.release.cluster;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t taddr = taddr_sh;
-    const uint32_t sbase = smem_u32(smem);
-    const uint32_t sW = sbase + 4 * kAOp;
-    const float *wp = wm + (size_t)blockIdx.y * nw * kWFloats;
-    auto ab = [&]() { return *(volatile int *)&abort_sh != 0; };   // set by any thread whose wait ran out
-    float2 *st = states + ((size_t)blockIdx.y * 2 + side) * S;
-    const uint32_t gb[2] = {tile_base_of(2 * blockIdx.x, ps.smask, N), tile_base_of(2 * blockIdx.x + 1, ps.smask, N)};
-    if (ctrl) {
-        if (lane == 0) {
-            int tma_issued[2] = {0, 0}, tma_waited[2] = {0, 0};
-            bool any = false;
-            for (int b = 0; b < 2 && b < nw; ++b) {
-                bulk_load(sW + b * kWMat, wp + (size_t)b * kWFloats, kWMat, &wfull[b]);
-                ++tma_issued[b];
-            }
-            for (int w = 0; w < nw && !ab(); ++w) {
-                for (int t = 0; t < 2 && !ab(); ++t) {
-                    if (!mbar_wait(smem_u32(&afull[t]), (uint32_t)w & 1u, wait_ns)) { abort_sh = 1; break; }
-                    if (t == 0) {
-                        if (!mbar_wait(smem_u32(&wfull[w & 1]), (uint32_t)(w >> 1) & 1u, wait_ns)) { abort_sh = 1; break; }
-                        ++tma_waited[w & 1];
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    issue_tile_mmas(taddr + 64u * t, sbase + 2 * kAOp * t, sW + (w & 1) * kWMat);
-                    commit_to(&dfull[t]);
-                    any = true;
-                }
-                // the matrix buffer of window w is free once Y(w) is done (commits complete in order)
-                if (!ab() && w + 2 < nw) {
-                    if (!mbar_wait(smem_u32(&dfull[1]), (uint32_t)w & 1u, wait_ns)) { abort_sh = 1; break; }
-                    bulk_load(sW + (w & 1) * kWMat, wp + (size_t)(w + 2) * kWFloats, kWMat, &wfull[w & 1]);
-                    ++tma_issued[w & 1];
-                }
-            }
-            if (ab()) {
-                // drain what this lane issued (every MMA through one more commit; bulk
-                // copies by their last armed phase), then report
-                if (any) {
-                    commit_to(&fbar);
-                    mbar_wait(smem_u32(&fbar), 0u, kTcDrainNs);
-                }
-                for (int b = 0; b < 2; ++b)
-                    if (tma_issued[b] > tma_waited[b])
-                        mbar_wait(smem_u32(&wfull[b]), (uint32_t)(tma_issued[b] - 1) & 1u, kTcDrainNs);
-                atomicExch(err, 1);
-            }
-        }
-    } else {
-        // both tiles: boundary -> A operands of window 0 (every element copy in
-        // flight at once through tile Y's operand space; Y via registers)
-        constexpr int kPer = (1 << kTcTile) / kTcThreads;
-        float2 *stage = (float2 *)(smem + 2 * kAOp);
-#pragma unroll
-        for (int tt = 0; tt < 2; ++tt)
-#pragma unroll
-            for (int m = 0; m < kPer; ++m) {
-                const uint32_t i = tid + (uint32_t)m * kTcThreads;
-                const uint32_t dd = smem_u32(stage + tt * (1 << kTcTile) + i);
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dd),
-                             "l"(st + gb[tt] + (lut_lo[i & 127] | lut_hi[i >> 7]))
-                             : "memory");
-            }
-        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-#pragma unroll
-        for (int m = 0; m < kPer; ++m) {
-            const uint32_t i = tid + (uint32_t)m * kTcThreads;
-            const float2 x = stage[i];
-            st_hilo(smem, alo[i & 127] ^ ahi[i >> 7], x.x, x.y);
-        }
-        float2 yv[kPer];
-#pragma unroll
-        for (int m = 0; m < kPer; ++m) yv[m] = stage[(1 << kTcTile) + tid + m * kTcThreads];
-        asm volatile("bar.sync 1, %0;" ::"n"(kTcThreads));   // drain warps only: staging reads done
-#pragma unroll
-        for (int m = 0; m < kPer; ++m) {
-            const uint32_t i = tid + (uint32_t)m * kTcThreads;
-            st_hilo(smem + 2 * kAOp, alo[i & 127] ^ ahi[i >> 7], yv[m].x, yv[m].y);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("bar.sync 1, %0;" ::"n"(kTcThreads));   // both operands complete
-        if (lane == 0) { mbar_arrive(&afull[0]); mbar_arrive(&afull[1]); }
-        for (int w = 0; w < nw; ++w) {
-            for (int t = 0; t < 2; ++t) {
-                if (ab()) break;
-                if (!mbar_wait(smem_u32(&dfull[t]), (uint32_t)w & 1u, wait_ns)) { abort_sh = 1; break; }
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                if (w + 1 < nw) {
-                    drain_tile(taddr + 64u * t, sw[w], sw[w + 1].cb, smem + 2 * kAOp * t, nullptr);
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    asm volatile("tcgen05.fence::before_thread_sync;");
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&afull[t]);
-                } else {
-                    drain_tile(taddr + 64u * t, sw[w], gcb, nullptr, st + gb[t]);
-                }
-            }
-            if (ab()) break;
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(taddr));
 }
 
 // ---------------------------------------------------------------------------
@@ -452,7 +231,7 @@ constexpr size_t kTc1Smem = 2 * (size_t)kAOp + (size_t)kWMat + 1024;
 
 __device__ __forceinline__ void drain_tile16(uint32_t tm, const TcWin &cw, const uint32_t *__restrict__ cbn,
                                              unsigned char *A, float2 *gdst) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = (threadIdx.x >> 5) & 7, lane = threadIdx.x & 31;   // warp within its group of 8
     uint32_t v[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
@@ -634,6 +413,313 @@ __global__ void __launch_bounds__(kTc1Drain + 32, 2)
     if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(taddr));
 }
 
+// ---------------------------------------------------------------------------
+// The tile's operand in tensor memory (the A operand of tcgen05.mma read from
+// TMEM): per window the MMAs read only the window matrix from shared memory.
+// Persistent: two CTAs per SM, each taking tiles t = blockIdx.x, + gridDim.x,
+// ...; 8 drain warps and a control warp as above.  TMEM columns: D 0-63, A
+// high parts 64-127, A low parts 128-191.  A window's result goes from D
+// through registers into a 32 KB shared-memory exchange buffer (TcWin::xcb of
+// the next window: both the storing and the loading half-warps hit 16
+// distinct bank pairs), every drain warp arrives on an mbarrier, and each
+// thread then loads its row of the next window's operand, splits it into TF32
+// parts and stores them into TMEM (tcgen05.st).  Exchanges alternate between
+// two buffers; the next tile's elements are copied into the free one while
+// the current tile's last window is multiplied and written back.  Shared
+// memory traffic per window and tile: 32 KB stored and 32 KB loaded by the
+// exchange, 48 KB of window matrix read by the 24 MMAs, 32 KB of window
+// matrix copied in (the shared-memory operand form: 64 KB stored, 96 + 48 KB
+// read by the MMAs, 32 KB copied in).
+constexpr int kTcmDrain = 256;
+constexpr uint32_t kXch = 32768;
+constexpr size_t kTcmSmem = 2 * (size_t)kXch + (size_t)kWMat + 1024;
+
+// As issue_tile_mmas with the tile's operand in tensor memory (columns 64-127
+// high parts, 128-191 low parts; K step s reads 8 columns from 8 s)
+__device__ __forceinline__ void issue_tile_mmas_tm(uint32_t tm, uint32_t sW) {
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+    const uint64_t dB[3] = {desc_sw128(sW + 16384), desc_sw128(sW), desc_sw128(sW)};
+    const uint32_t aC[3] = {64u, 128u, 64u};
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const uint64_t bd = dB[p] + (uint64_t)((((s >> 2) * 8192) + (s & 3) * 32) >> 4);
+            const uint32_t acc = (p > 0 || s > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, q;\n\t}" ::"r"(tm),
+                "r"(tm + aC[p] + 8u * s), "l"(bd), "r"(idesc), "r"(acc));
+        }
+}
+
+// Exchange address of this thread's element u of a [128 x 32] view (row r =
+// 32 (warp mod 4) + lane, window index 16 (warp / 4) + u) through the map cb,
+// with the row and window bits of window cw: base ^ the contributions of u.
+struct XchAddr {
+    uint32_t base, c0, c1, c2, c3;
+    __device__ __forceinline__ XchAddr(const uint32_t *cb, const TcWin &cw, uint32_t r, uint32_t half) {
+        base = 0;
+#pragma unroll
+        for (int t = 0; t < kTcRows; ++t)
+            if ((r >> t) & 1u) base ^= cb[cw.row[t]];
+        if (half) base ^= cb[cw.win[4]];
+        c0 = cb[cw.win[0]]; c1 = cb[cw.win[1]]; c2 = cb[cw.win[2]]; c3 = cb[cw.win[3]];
+    }
+    __device__ __forceinline__ uint32_t at(int u) const {
+        return base ^ ((u & 1) ? c0 : 0u) ^ ((u & 2) ? c1 : 0u) ^ ((u & 4) ? c2 : 0u) ^ ((u & 8) ? c3 : 0u);
+    }
+};
+
+// This thread's operand row of window cw: exchange buffer -> TF32 high and low
+// parts -> tensor memory (lanes 32 (warp mod 4) .., columns 64 / 128 + 32 (warp / 4) ..).
+// All 16 loads are in flight at once; the parts go out in two halves of 16 columns.
+__device__ __forceinline__ void tm_load_operand(uint32_t tm, const TcWin &cw, uint32_t xs) {
+    const int warp = (threadIdx.x >> 5) & 7, lane = threadIdx.x & 31;   // warp within its group of 8
+    const uint32_t r = 32u * (warp & 3) + lane, half = (uint32_t)(warp >> 2);
+    const XchAddr xa(cw.xcb, cw, r, half);
+    const uint32_t ta = tm + ((32u * (warp & 3)) << 16) + 32u * half;
+    uint32_t h[32];
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+        asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(h[2 * u]), "=r"(h[2 * u + 1]) : "r"(xs + xa.at(u)) : "memory");
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const uint32_t *hq = h + 16 * q;
+        uint32_t lo[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) lo[i] = __float_as_uint(tf32_rest(__uint_as_float(hq[i])));
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16};" ::"r"(ta + 64u + 16u * q),
+            "r"(hq[0]), "r"(hq[1]), "r"(hq[2]), "r"(hq[3]), "r"(hq[4]), "r"(hq[5]), "r"(hq[6]), "r"(hq[7]),
+            "r"(hq[8]), "r"(hq[9]), "r"(hq[10]), "r"(hq[11]), "r"(hq[12]), "r"(hq[13]), "r"(hq[14]), "r"(hq[15])
+            : "memory");
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16};" ::"r"(ta + 128u + 16u * q),
+            "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]), "r"(lo[7]),
+            "r"(lo[8]), "r"(lo[9]), "r"(lo[10]), "r"(lo[11]), "r"(lo[12]), "r"(lo[13]), "r"(lo[14]), "r"(lo[15])
+            : "memory");
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// This thread's 16 results of window cw (D row r, window outputs 16 (warp / 4) ..)
+// into the exchange buffer through map cb (the next window's xcb)
+__device__ __forceinline__ void tm_store_result(uint32_t tm, const TcWin &cw, const uint32_t *cb, uint32_t xs) {
+    const int warp = (threadIdx.x >> 5) & 7, lane = threadIdx.x & 31;   // warp within its group of 8
+    const uint32_t r = 32u * (warp & 3) + lane, half = (uint32_t)(warp >> 2);
+    const uint32_t ta = tm + ((32u * (warp & 3)) << 16) + 32u * half;
+    const XchAddr xa(cb, cw, r, half);
+    // two halves of 16 columns: the second half's read is in flight while the first is stored
+    uint32_t v[16], y[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(y[0]), "=r"(y[1]), "=r"(y[2]), "=r"(y[3]), "=r"(y[4]), "=r"(y[5]), "=r"(y[6]), "=r"(y[7]),
+          "=r"(y[8]), "=r"(y[9]), "=r"(y[10]), "=r"(y[11]), "=r"(y[12]), "=r"(y[13]), "=r"(y[14]), "=r"(y[15])
+        : "r"(ta + 16u));
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(xs + xa.at(u)), "r"(v[2 * u]), "r"(v[2 * u + 1])
+                     : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(xs + xa.at(8 + u)), "r"(y[2 * u]), "r"(y[2 * u + 1])
+                     : "memory");
+}
+
+// Tiles t = blockIdx.x, + gridDim.x, ... < ntiles (tile t: pair t >> (N - 12),
+// tile index t mod 2^(N - 12)).  Counters run over the CTA's tiles: g =
+// windows (phases of afull, wfull, dfull), x = exchanges (phases of xbar;
+// exchange x uses buffer x mod 2: a tile's input, then its windows' results).
+__global__ void __launch_bounds__(kTcmDrain + 32, 2)
+    brick_tcm_pass_kernel(BrickDev d, int side, BrickPass ps, const TcWin *__restrict__ wins,
+                          const float *__restrict__ wm, float2 *__restrict__ states, int *err, uint64_t wait_ns,
+                          uint32_t ntiles) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t wfull, dfull, afull, xbar, fbar;
+    __shared__ uint32_t taddr_sh;
+    __shared__ int abort_sh;
+    __shared__ int pos[32];
+    // tile index -> boundary offset (lut), -> input address (a); tile bit -> boundary offset (gcb)
+    __shared__ uint32_t lut_lo[128], lut_hi[1 << (kTcTile - 7)], alo[128], ahi[1 << (kTcTile - 7)], gcb[kTcTile];
+    __shared__ TcWin sw[kMaxTcWins];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool ctrl = warp == kTcmDrain / 32;
+    const int nw = ps.n_rp;
+    const int N = d.N;
+    const uint32_t S = 1u << N;
+    const int tb = N - kTcTile;   // tile-index bits
+    if (blockIdx.x >= ntiles) return;
+    if (tid == 0) {
+        abort_sh = *(volatile const int *)err;   // an earlier launch timed out
+        int k = 0;
+        for (int b = 0; b < N; ++b)
+            if (ps.smask & (1u << b)) pos[k++] = b;
+    }
+    for (int i = tid; i < nw; i += kTcmDrain + 32) sw[i] = wins[ps.rp_off + i];
+    __syncthreads();
+    if (abort_sh) return;
+    for (int i = tid; i < 128; i += kTcmDrain + 32) {
+        uint32_t o = 0, a = 0;
+        for (int k = 0; k < 7; ++k)
+            if ((i >> k) & 1) { o |= 1u << pos[k]; a ^= sw[0].xcb[k]; }
+        lut_lo[i] = o;
+        alo[i] = a;
+    }
+    if (tid < (1 << (kTcTile - 7))) {
+        uint32_t o = 0, a = 0;
+        for (int k = 0; k < kTcTile - 7; ++k)
+            if ((tid >> k) & 1) { o |= 1u << pos[7 + k]; a ^= sw[0].xcb[7 + k]; }
+        lut_hi[tid] = o;
+        ahi[tid] = a;
+    }
+    if (tid < kTcTile) gcb[tid] = 1u << pos[tid];
+    if (tid < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&taddr_sh)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 32) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&wfull)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&dfull)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull)), "r"(kTcmDrain / 32));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&xbar)), "r"(kTcmDrain / 32));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t taddr = taddr_sh;
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t sW = sbase + 2 * kXch;
+    auto ab = [&]() { return *(volatile int *)&abort_sh != 0; };
+    auto wmat = [&](uint32_t t) { return wm + (size_t)(t >> tb) * nw * kWFloats; };
+    auto tile_ptr = [&](uint32_t t) {
+        return states + ((size_t)(t >> tb) * 2 + side) * S + tile_base_of(t & ((1u << tb) - 1u), ps.smask, N);
+    };
+    if (ctrl) {
+        if (lane == 0) {
+            int tma_issued = 0, tma_waited = 0;
+            bool any = false, stop = false;
+            uint32_t g = 0;
+            bulk_load(sW, wmat(blockIdx.x), kWMat, &wfull);
+            ++tma_issued;
+            for (uint32_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+                for (int w = 0; w < nw; ++w, ++g) {
+                    if (ab()) { stop = true; break; }
+                    if (!mbar_wait(smem_u32(&afull), g & 1u, wait_ns)) { abort_sh = 1; stop = true; break; }
+                    if (!mbar_wait(smem_u32(&wfull), g & 1u, wait_ns)) { abort_sh = 1; stop = true; break; }
+                    ++tma_waited;
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    issue_tile_mmas_tm(taddr, sW);
+                    commit_to(&dfull);
+                    any = true;
+                    // the matrix buffer is free once these MMAs are done: the next window's
+                    // matrix, or window 0's of the CTA's next tile
+                    const float *nxt = w + 1 < nw ? wmat(t) + (size_t)(w + 1) * kWFloats
+                                                  : (t + gridDim.x < ntiles ? wmat(t + gridDim.x) : nullptr);
+                    if (nxt) {
+                        if (!mbar_wait(smem_u32(&dfull), g & 1u, wait_ns)) { abort_sh = 1; stop = true; break; }
+                        bulk_load(sW, nxt, kWMat, &wfull);
+                        ++tma_issued;
+                    }
+                }
+            }
+            if (ab()) {
+                if (any) {
+                    commit_to(&fbar);
+                    mbar_wait(smem_u32(&fbar), 0u, kTcDrainNs);
+                }
+                if (tma_issued > tma_waited) mbar_wait(smem_u32(&wfull), (uint32_t)(tma_issued - 1) & 1u, kTcDrainNs);
+                atomicExch(err, 1);
+            }
+        }
+    } else {
+        // every exit decision of a drain warp is warp-uniform: the tcgen05 loads
+        // and stores below are warp-collective
+        const unsigned full = 0xFFFFFFFFu;
+        constexpr int kPer = (1 << kTcTile) / kTcmDrain;
+        // copies m0 .. m1 - 1 of this thread's share of tile t's boundary elements
+        // -> exchange buffer xb (window 0's map)
+        auto load_tile = [&](uint32_t t, uint32_t xb, int m0, int m1) {
+            const float2 *src = tile_ptr(t);
+#pragma unroll
+            for (int m = 0; m < kPer; ++m) {
+                if (m < m0 || m >= m1) continue;
+                const uint32_t i = tid + (uint32_t)m * kTcmDrain;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(xb + (alo[i & 127] ^ ahi[i >> 7])),
+                             "l"(src + (lut_lo[i & 127] | lut_hi[i >> 7]))
+                             : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        // one exchange: this warp's stores are done; wait for every drain warp's
+        auto exchange = [&](uint32_t &x) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&xbar);
+            const bool ok = __all_sync(full, mbar_wait(smem_u32(&xbar), x & 1u, wait_ns));
+            ++x;
+            if (!ok) abort_sh = 1;
+            return ok;
+        };
+        auto operand_ready = [&]() {
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&afull);
+        };
+        uint32_t g = 0, x = 0;
+        bool stop = false;
+        load_tile(blockIdx.x, sbase, 0, kPer);   // exchange 0: buffer 0
+        for (uint32_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+            const uint32_t tn = t + gridDim.x;   // the CTA's next tile
+            uint32_t xs = sbase + (x & 1u) * kXch;
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (!exchange(x)) break;
+            tm_load_operand(taddr, sw[0], xs);
+            operand_ready();
+            // exchange x (now the next tile's input) goes to the buffer whose last
+            // loads (exchange x - 2) every drain warp finished before exchange x - 1
+            if (nw == 1 && tn < ntiles) load_tile(tn, sbase + (x & 1u) * kXch, 0, kPer);
+            for (int w = 0; w < nw; ++w, ++g) {
+                if (__any_sync(full, ab())) { stop = true; break; }
+                if (!__all_sync(full, mbar_wait(smem_u32(&dfull), g & 1u, wait_ns))) {
+                    abort_sh = 1;
+                    stop = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                if (w + 1 < nw) {
+                    xs = sbase + (x & 1u) * kXch;
+                    tm_store_result(taddr, sw[w], sw[w + 1].xcb, xs);
+                    if (!exchange(x)) { stop = true; break; }
+                    tm_load_operand(taddr, sw[w + 1], xs);
+                    operand_ready();
+                    if (w + 2 == nw && tn < ntiles) load_tile(tn, sbase + (x & 1u) * kXch, 0, kPer);
+                } else {
+                    drain_tile16(taddr, sw[w], gcb, nullptr, tile_ptr(t));
+                }
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy outlives the CTA
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(taddr));
+}
+
 }  // namespace
 
 size_t tc_wmat_bytes_per_pair(const BrickDev &d, const BrickPass *hpasses) {
@@ -655,23 +741,29 @@ bool tc_plan_ok(const BrickDev &d, const BrickPass *hpasses, const RegPass *rps)
 
 cudaError_t run_passes_tc(const BrickDev &d, const BrickPass *hpasses, const BrickDevPlan &dp, int npairs,
                           const float2 *maps, float2 *states, float *wm, int *err, cudaStream_t st) {
-    const bool one = dp.persist == 3;   // one tile per CTA, two CTAs per SM
-    cudaError_t e = one ? cudaFuncSetAttribute(brick_tc1_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)kTc1Smem)
-                        : cudaFuncSetAttribute(brick_tc_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)kTcSmem);
+    // 3: the tile's operand in shared memory, one tile per CTA; 4: in tensor memory, persistent
+    const bool tm = dp.persist == 4;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = tm ? cudaFuncSetAttribute(brick_tcm_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcmSmem)
+           : cudaFuncSetAttribute(brick_tc1_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc1Smem);
     if (e != cudaSuccess) return e;
     for (int side = 0; side < 2; ++side)
         for (int p = 0; p < d.n_passes[side]; ++p) {
             const BrickPass &ps = hpasses[d.pass_off[side] + p];
             tc_wmat_kernel<<<dim3(ps.n_rp, npairs), 32, 0, st>>>(d, side, ps, dp.gates, dp.rpasses, dp.rgates, maps, wm);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            if (one)
+            if (tm) {   // two CTAs per SM
+                const uint32_t ntiles = (uint32_t)npairs << (d.N - kTcTile);
+                const uint32_t grid = std::min<uint32_t>(ntiles, 2u * (uint32_t)sms);
+                brick_tcm_pass_kernel<<<grid, kTcmDrain + 32, kTcmSmem, st>>>(d, side, ps, dp.tcwins, wm, states, err,
+                                                                              wait_limit_ns(), ntiles);
+            } else {
                 brick_tc1_pass_kernel<<<dim3(1u << (d.N - kTcTile), npairs), kTc1Drain + 32, kTc1Smem, st>>>(
                     d, side, ps, dp.tcwins, wm, states, err, wait_limit_ns());
-            else
-                brick_tc_pass_kernel<<<dim3(1u << (d.N - kTcTile - 1), npairs), kTcThreads + 32, kTcSmem, st>>>(
-                    d, side, ps, dp.tcwins, wm, states, err, wait_limit_ns());
+            }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     return cudaSuccess;

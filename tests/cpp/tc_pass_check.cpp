@@ -11,7 +11,7 @@
 //              operand layout, the MMA read through the hardware's view of
 //              the K-major 128-byte-swizzled operands (row r, K column k at
 //              region k/32, row offset 128 r, 16-byte chunk (k/4 mod 8) ^ (r mod 8)),
-//              D = A B^T, then every thread's 8 results (16 warps) scattered through the
+//              D = A B^T, then every thread's 16 results (8 warps) scattered through the
 //              XOR address tables into the next window's operand or the boundary.
 // Every operand address is checked to be in bounds and every window layout
 // to be a bijection.  Exit status 1 if the two sweeps differ by more than
@@ -22,6 +22,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <random>
+#include <string>
 #include <vector>
 
 #include "brick.h"
@@ -58,8 +59,20 @@ static void apply4(std::vector<cd> &s, int N, int pa, int pb, const cd *T) {
     }
 }
 
+// 8-byte bank pair (address bits 3-6) of each of 16 lanes' addresses: all distinct?
+static bool distinct_banks(const uint32_t *a) {
+    unsigned seen = 0;
+    for (int i = 0; i < 16; ++i) seen |= 1u << ((a[i] >> 3) & 15u);
+    return seen == 0xFFFFu;
+}
+
 int main(int argc, char **argv) {
     const int n = atoi(argv[1]), l = atoi(argv[2]);
+    // "tcm": the tensor-memory operand form (brick_tcm_pass_kernel): every window's input
+    // through the shared-memory exchange buffer (TcWin::xcb) into a [128 x 32] complex
+    // operand held by 8 warps x 32 lanes x 16 window indices, results stored back by
+    // the same threads into the next window's exchange buffer
+    const bool tcm = argc > 3 && std::string(argv[3]) == "tcm";
     BrickHostPlan P = make_brick_plan(n, l, kTcTile, 3, kMaxWin, 0);   // the plan the tensor-core pass runs
     const BrickDev &d = P.dev;
     const int N = d.N;
@@ -145,9 +158,94 @@ int main(int argc, char **argv) {
                 }
                 CHECK(std::count(seen.begin(), seen.end(), 1) == 4096, "B layout is not a bijection");
             }
-            // emulation of every CTA (two tiles each)
             uint32_t gcb[kTcTile];
             for (int b = 0; b < kTcTile; ++b) gcb[b] = 1u << pos[b];
+            if (tcm) {
+                const uint32_t ntiles = 1u << (N - kTcTile);
+                auto xaddr = [](const uint32_t *cb, const uint8_t *rows, uint32_t r, const uint8_t *win, uint32_t j) {
+                    uint32_t a = 0;
+                    for (int q = 0; q < kTcRows; ++q)
+                        if ((r >> q) & 1u) a ^= cb[rows[q]];
+                    for (int q = 0; q < kMaxWin; ++q)
+                        if ((j >> q) & 1u) a ^= cb[win[q]];
+                    return a;
+                };
+                for (uint32_t t = 0; t < ntiles; ++t) {
+                    uint32_t base = 0, tt = t;
+                    for (int b = 0; b < N; ++b)
+                        if (!(ps.smask & (1u << b))) { base |= (tt & 1u) << b; tt >>= 1; }
+                    std::vector<cd> X(4096), X2(4096);
+                    const TcWin &w0 = W[ps.rp_off];
+                    for (uint32_t i0 = 0; i0 < 4096; i0 += 16) {   // the tile load, 16 lanes at a time
+                        uint32_t ad[16];
+                        for (uint32_t q = 0; q < 16; ++q) {
+                            const uint32_t i = i0 + q;
+                            uint32_t phys = base, a = 0;
+                            for (int b = 0; b < kTcTile; ++b)
+                                if ((i >> b) & 1u) { phys |= 1u << pos[b]; a ^= w0.xcb[b]; }
+                            CHECK(a < 32768 && a % 8 == 0, "exchange address %u", a);
+                            X[(a / 8) & 4095] = emu[phys];
+                            ad[q] = a;
+                        }
+                        CHECK(distinct_banks(ad), "tile load: repeated bank pair");
+                    }
+                    for (int w = 0; w < ps.n_rp; ++w) {
+                        const TcWin &cw = W[ps.rp_off + w];
+                        // operand rows: warp (0..7) and lane give the row, u the window index
+                        std::vector<double> Ar(128 * 64);
+                        for (int warp = 0; warp < 8; ++warp)
+                            for (int u = 0; u < 16; ++u)
+                                for (int h = 0; h < 2; ++h) {
+                                    uint32_t ad[16];
+                                    for (int q = 0; q < 16; ++q) {
+                                        const uint32_t r = 32u * (warp & 3) + 16u * h + q, j = 16u * (warp >> 2) + u;
+                                        ad[q] = xaddr(cw.xcb, cw.row, r, cw.win, j);
+                                        const cd x = X[(ad[q] / 8) & 4095];
+                                        Ar[r * 64 + 2 * j] = x.real();
+                                        Ar[r * 64 + 2 * j + 1] = x.imag();
+                                    }
+                                    CHECK(distinct_banks(ad), "window %d load: repeated bank pair", w);
+                                }
+                        std::vector<double> D(128 * 64);
+                        for (uint32_t r = 0; r < 128; ++r)
+                            for (uint32_t nn = 0; nn < 64; ++nn) {
+                                double acc = 0;
+                                for (uint32_t kk = 0; kk < 64; ++kk) acc += Ar[r * 64 + kk] * B[w][hw_b(nn, kk) / 4];
+                                D[r * 64 + nn] = acc;
+                            }
+                        const bool last = w + 1 == ps.n_rp;
+                        std::vector<char> hit(4096, 0);
+                        for (int warp = 0; warp < 8; ++warp)
+                            for (int u = 0; u < 16; ++u)
+                                for (int h = 0; h < 2; ++h) {
+                                    uint32_t ad[16];
+                                    for (int q = 0; q < 16; ++q) {
+                                        const uint32_t r = 32u * (warp & 3) + 16u * h + q, o = 16u * (warp >> 2) + u;
+                                        const cd y(D[r * 64 + 2 * o], D[r * 64 + 2 * o + 1]);
+                                        if (last) {   // straight to the boundary
+                                            const uint32_t g = xaddr(gcb, cw.row, r, cw.win, o);
+                                            CHECK((g & base) == 0 && g < S, "boundary index out of the tile");
+                                            emu[base | g] = y;
+                                            ad[q] = 8u * q;
+                                        } else {
+                                            const TcWin &nx = W[ps.rp_off + w + 1];
+                                            ad[q] = xaddr(nx.xcb, cw.row, r, cw.win, o);
+                                            CHECK(ad[q] < 32768 && ad[q] % 8 == 0, "exchange address %u", ad[q]);
+                                            X2[(ad[q] / 8) & 4095] = y;
+                                            hit[(ad[q] / 8) & 4095]++;
+                                        }
+                                    }
+                                    CHECK(distinct_banks(ad), "window %d store: repeated bank pair", w);
+                                }
+                        if (!last) {
+                            CHECK(std::count(hit.begin(), hit.end(), 1) == 4096, "exchange %d is not a bijection", w);
+                            X.swap(X2);
+                        }
+                    }
+                }
+                continue;
+            }
+            // emulation of every tile (one per CTA)
             const uint32_t ntiles = 1u << (N - kTcTile);
             for (uint32_t t = 0; t < ntiles; ++t) {
                 uint32_t base = 0, tt = t;
@@ -175,28 +273,27 @@ int main(int argc, char **argv) {
                     const bool last = w + 1 == ps.n_rp;
                     const uint32_t *cbn = last ? gcb : W[ps.rp_off + w + 1].cb;
                     std::vector<double> A2(8192, 0.0);
-                    for (int warp = 0; warp < 16; ++warp)
+                    for (int warp = 0; warp < 8; ++warp)
                         for (int lane = 0; lane < 32; ++lane) {
                             const uint32_t r = 32u * (warp & 3) + lane;
                             uint32_t bs = 0;
                             for (int q = 0; q < kTcRows; ++q)
                                 if ((r >> q) & 1u) bs ^= cbn[cw.row[q]];
-                            const int og = warp >> 2;
-                            if (og & 1) bs ^= cbn[cw.win[3]];
-                            if (og & 2) bs ^= cbn[cw.win[4]];
+                            const int half = warp >> 2;
+                            if (half) bs ^= cbn[cw.win[4]];
                             // the kernel visits output u ^ rot at step u (rot by lane, TcWin::rotm)
                             const uint32_t rm = last ? 0u : cw.rotm, l4 = (uint32_t)lane & 15u;
                             int rot = 0;
                             for (int i = 0; i < 3; ++i)
                                 rot |= (__builtin_popcount(l4 & ((rm >> (4 * i)) & 15u)) & 1) << i;
-                            for (int step = 0; step < 8; ++step) {
+                            for (int step = 0; step < 16; ++step) {
                                 const int u = step ^ rot;
                                 uint32_t a = bs;
                                 for (int q = 0; q < 3; ++q)
                                     if ((rot >> q) & 1) a ^= cbn[cw.win[q]];
-                                for (int q = 0; q < 3; ++q)
+                                for (int q = 0; q < 4; ++q)
                                     if ((step >> q) & 1) a ^= cbn[cw.win[q]];
-                                const uint32_t col = 16u * (warp >> 2) + 2u * u;
+                                const uint32_t col = 32u * half + 2u * u;
                                 const double x = D[r * 64 + col], y = D[r * 64 + col + 1];
                                 if (last) {
                                     CHECK((a & ~(S - 1)) == 0 && (a & base) == 0, "boundary index out of the tile");

@@ -8,8 +8,8 @@ import pytest
 import oracle as O
 
 pytestmark = pytest.mark.gpu
-TC = "12 5 256 2"     # two tiles per CTA
-TC1 = "12 5 256 3"    # one tile per CTA, two CTAs per SM
+TC1 = "12 5 256 3"    # the tile's operand in shared memory, one tile per CTA, two CTAs per SM
+TCM = "12 5 256 4"    # the tile's operand in tensor memory, persistent over the tiles
 _ORACLE = {}
 
 
@@ -25,7 +25,7 @@ def fp():
     return fpm
 
 
-def _force(tmp_path, monkeypatch, n, depths, variant=TC):
+def _force(tmp_path, monkeypatch, n, depths, variant=TCM):
     import torch
     cache = tmp_path / "tune.txt"
     name = torch.cuda.get_device_name(0)
@@ -33,7 +33,7 @@ def _force(tmp_path, monkeypatch, n, depths, variant=TC):
     monkeypatch.setenv("FP_AUTOTUNE_CACHE", str(cache))
 
 
-@pytest.mark.parametrize("n,variant", [(30, TC), (31, TC), (30, TC1), (31, TC1)])
+@pytest.mark.parametrize("n,variant", [(30, TC1), (31, TC1), (30, TCM), (31, TCM)])
 def test_tc_pass_matches_fp64(fp, n, variant, tmp_path, monkeypatch):
     # ragged batches (not a multiple of anything), even and odd chains; the
     # per-pair error estimate bounds the actual difference
@@ -48,7 +48,7 @@ def test_tc_pass_matches_fp64(fp, n, variant, tmp_path, monkeypatch):
         ens.close()
 
 
-@pytest.mark.parametrize("variant", [TC, TC1])
+@pytest.mark.parametrize("variant", [TC1, TCM])
 def test_tc_pass_matches_oracle_n50(fp, variant, tmp_path, monkeypatch):
     # one pair of each deep depth of the benchmark ensemble against the oracle
     import concurrent.futures as cf
@@ -68,7 +68,7 @@ def test_tc_pass_matches_oracle_n50(fp, variant, tmp_path, monkeypatch):
         ens.close()
 
 
-@pytest.mark.parametrize("variant", [TC, TC1])
+@pytest.mark.parametrize("variant", [TC1, TCM])
 def test_tc_pass_full_size_self_pair(fp, variant, tmp_path, monkeypatch):
     # V = U: Tr(U^dagger U) = 2^50 exactly, through the tensor-core passes at l = 10
     _force(tmp_path, monkeypatch, 50, (10,), variant)
@@ -93,7 +93,7 @@ def test_tc_pass_frame_potential_within_1e3(fp, tmp_path, monkeypatch):
         ens.close()
 
 
-@pytest.mark.parametrize("variant", [TC, TC1, "13 5 256 0"])
+@pytest.mark.parametrize("variant", [TC1, TCM, "13 5 256 0"])
 def test_brick_variant_reports_the_forced_choice(fp, variant, tmp_path, monkeypatch):
     # fp_brick_variant: FP_ERR_ARG before the depth has run, then the variant the
     # tuner's cache file fixed, shared by FP32 and FP32 without recontraction

@@ -5,7 +5,10 @@ window matrices in the MMA's B layout, the MMA read through the hardware's
 view of the swizzled K-major operands, the XOR-table scatter into the next
 window's operand or the boundary) and compares it with the gate-by-gate
 sweep of the same windows.  Every operand address is bounds-checked and every
-window layout checked to be a bijection.  CPU."""
+window layout checked to be a bijection.  The "tcm" mode emulates the
+tensor-memory operand form instead: every window's input through the
+shared-memory exchange buffer, with every exchange checked to be a bijection
+and every half-warp's 16 stores and loads to hit 16 distinct bank pairs.  CPU."""
 import os
 import shutil
 import subprocess
@@ -28,7 +31,8 @@ def checker(tmp_path_factory):
     return out
 
 
+@pytest.mark.parametrize("mode", ["smem", "tcm"])
 @pytest.mark.parametrize("n,l", [(20, 8), (50, 8), (50, 9), (51, 9), (50, 10)])
-def test_tc_pass_emulation_matches_gate_sweep(checker, n, l):
-    r = subprocess.run([checker, str(n), str(l)], capture_output=True, text=True, timeout=600)
+def test_tc_pass_emulation_matches_gate_sweep(checker, n, l, mode):
+    r = subprocess.run([checker, str(n), str(l), mode], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
