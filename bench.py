@@ -482,6 +482,8 @@ def measure_peaks(fp):
 TRAFFIC_L10 = {
     "13 5 256 0": ("brick_pass_kernel<float2,13,5,256>", 538.275328e6, 479.907328e6,
                    "profiles/brick_pass_kernel_f32_brickwork_n50_l10.md"),
+    "12 5 256 4": ("brick_tcm_pass_kernel", 589.198848e6, 481.595136e6,
+                   "profiles/brick_tcm_pass_kernel_brickwork_n50_l10.md"),
 }
 
 
@@ -501,7 +503,26 @@ def roofline(fp, ks, ms_total, prec, peaks, clocks):
             "peak_source": (f"measured: {key} microbenchmark {pk['flops_per_clk_sm']:.1f} flop/clk/SM x {pk['sms']} "
                             f"SMs x {mhz:.0f} MHz (median SM clock of the timed region); "
                             f"{pk['tflops']:.1f} TFLOP/s at {pk['sm_mhz']:.0f} MHz in the microbenchmark"),
-            "kernel_ms_share": ks.ms[cls] / ms_total if ms_total else None}
+            "kernel_ms_share": ks.ms[cls] / ms_total if ms_total else None,
+            "tensor_view": tensor_view(ks, cls, peaks)}
+
+
+def tensor_view(ks, cls, peaks):
+    """The brickwork tensor-core passes against the tensor pipe: TF32 flops issued to the
+    tensor cores (three products per operand pair, 2 per multiply-add, counted by the
+    library) over the device time of the whole brickwork class (which also holds the
+    gate maps, the tile loads of the first pass and the meet, so the rate is a lower
+    bound), against the measured tcgen05 kind::tf32 rate of the microbenchmark."""
+    mma = float(getattr(ks, "mma_flops", 0.0))
+    if mma <= 0 or ks.ms[cls] <= 0 or "tf32_tcgen05" not in peaks:
+        return None
+    achieved = mma / (ks.ms[cls] / 1e3) / 1e12
+    pk = peaks["tf32_tcgen05"]
+    return {"bound": "tensor", "achieved": achieved, "peak": pk["tflops"], "unit": "TFLOP/s",
+            "frac": achieved / pk["tflops"],
+            "peak_source": (f"measured: tcgen05 kind::tf32 microbenchmark, {pk['tflops']:.0f} TFLOP/s at "
+                            f"{pk['sm_mhz']:.0f} MHz"),
+            "note": "time = whole brickwork class (lower bound on the tensor-core passes' own rate)"}
 
 
 # ---------------------------------------------------------------------------

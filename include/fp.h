@@ -186,6 +186,9 @@ typedef struct {
                                          classes, pairs for the others */
     uint64_t pairs;                   /* pairs contracted */
     uint64_t graph_replays;           /* sub-batches run by CUDA-graph replay (counted always) */
+    double mma_flops;                 /* flops issued to the tensor cores by the brickwork
+                                         tensor-core tile passes (2 per multiply-add; three
+                                         TF32 products per operand pair) */
 } fp_kernel_stats;
 
 /* Create an ensemble.  `cuda_stream` is a cudaStream_t (NULL: default stream).

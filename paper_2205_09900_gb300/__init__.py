@@ -63,7 +63,7 @@ class Checkpoint(ctypes.Structure):
 
 class KernelStats(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8), ("work", ctypes.c_double * 8),
-                ("pairs", ctypes.c_uint64), ("graph_replays", ctypes.c_uint64)]
+                ("pairs", ctypes.c_uint64), ("graph_replays", ctypes.c_uint64), ("mma_flops", ctypes.c_double)]
 
 
 class CvConfig(ctypes.Structure):

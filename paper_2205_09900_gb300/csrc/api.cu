@@ -109,6 +109,7 @@ struct BrickCache {
     BrickDevPlan dp;
     size_t extra_per_pair = 0;   // tensor-core window matrices (bytes per pair, after the boundaries)
     int variant[4] = {0, 0, 0, 0};   // tile bits, window bits, threads, pass kind (fp_brick_variant)
+    double mma_flops_pair = 0;       // tensor-core flops issued per pair (tensor-core passes)
 };
 
 struct SpiralCache {        // one depth of the paper's HEA on the spiral sweep
@@ -538,6 +539,10 @@ fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int T
         CK(upload(bc->d_tcwins, make_tc_windows(bc->hp), E->st));
         bc->dp.tcwins = bc->d_tcwins.as<TcWin>();
         bc->extra_per_pair = tc_wmat_bytes_per_pair(bc->hp.dev, bc->hp.passes.data());
+        // per window and tile: 3 products x 8 K steps of a 128 x 64 x 8 MMA
+        double windows = 0;
+        for (const BrickPass &ps : bc->hp.passes) windows += ps.n_rp;
+        bc->mma_flops_pair = windows * (double)(1u << (bc->hp.dev.N - kTcTile)) * 3.0 * 2.0 * 128.0 * 64.0 * 64.0;
         if (!E->d_flag.p) {
             CK(E->d_flag.reserve(16));
             CK(cudaMemsetAsync(E->d_flag.p, 0, 16, E->st));
@@ -754,7 +759,10 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
                                 E->d_raw.as<double2>(), E->d_maps.p, E->d_states.p, fp32, err_scale, tr, kappa, err,
                                 E->st, &nl));
                 CK(t.stop(cmac_pair * (double)nb));
-                if (E->timing) E->kst.launches[FP_K_BRICK] += (uint64_t)(nl - 1);
+                if (E->timing) {
+                    E->kst.launches[FP_K_BRICK] += (uint64_t)(nl - 1);
+                    E->kst.mma_flops += it->second->mma_flops_pair * (double)nb;
+                }
             }
             if (use_graph) {
                 if (E->graphs.size() > 64) {
