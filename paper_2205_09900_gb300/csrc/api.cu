@@ -105,7 +105,7 @@ struct GraphKey {
 
 struct BrickCache {
     BrickHostPlan hp;
-    DBuf d_gates, d_rpasses, d_rgates, d_tcwins;
+    DBuf d_gates, d_rpasses, d_rgates, d_tcwins, d_tcxa;
     BrickDevPlan dp;
     size_t extra_per_pair = 0;   // tensor-core window matrices (bytes per pair, after the boundaries)
     int variant[4] = {0, 0, 0, 0};   // tile bits, window bits, threads, pass kind (fp_brick_variant)
@@ -536,8 +536,11 @@ fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int T
         if (!fp32 || !tc_plan_ok(bc->hp.dev, bc->hp.passes.data(), bc->hp.rpasses.data()))
             return fail(FP_ERR_ARG, "the tensor-core tile pass needs FP32, %d-bit tiles, %d-bit windows and l >= 8",
                         kTcTile, kMaxWin);
-        CK(upload(bc->d_tcwins, make_tc_windows(bc->hp), E->st));
+        const std::vector<TcWin> wins = make_tc_windows(bc->hp);
+        CK(upload(bc->d_tcwins, wins, E->st));
+        CK(upload(bc->d_tcxa, make_tc_xaddr(bc->hp, wins), E->st));
         bc->dp.tcwins = bc->d_tcwins.as<TcWin>();
+        bc->dp.tcxa = bc->d_tcxa.as<TcXa>();
         bc->extra_per_pair = tc_wmat_bytes_per_pair(bc->hp.dev, bc->hp.passes.data());
         // per window and tile: 3 products x 8 K steps of a 128 x 64 x 8 MMA
         double windows = 0;

@@ -103,6 +103,17 @@ struct TcWin {
     // storing lanes' 4 fill bits 7-14 in ascending order.
     uint32_t xcb[kTcTile];
 };
+// The exchange addresses of one window for the tensor-memory operand form, by
+// thread position: a drain thread (warp w of 8, lane l) holds row 32 (w mod 4)
+// + l and window indices 16 (w / 4) + u, u = 0..15; its address of element u
+// is lane[l] ^ warp[w] ^ (the c[k] of the set bits k of u).  ld: this window's
+// operand, loaded through its own map xcb; st: this window's result, stored
+// through the next window's map (zero for a pass's last window).
+struct TcXa {
+    uint32_t ld_lane[32], st_lane[32];
+    uint32_t ld_warp[8], st_warp[8];
+    uint32_t ld_c[4], st_c[4];
+};
 // A-operand byte address of element (row r, window index j): complex j
 // occupies K columns 2j (re), 2j+1 (im); K splits into two 128-byte regions of
 // 128 rows; 16-byte chunk c of row r sits at chunk c ^ (r % 8).
@@ -115,6 +126,7 @@ struct BrickDevPlan {
     const RegPass *rpasses;
     const RegGate *rgates;
     const TcWin *tcwins;    // persist >= 2: one per register pass
+    const TcXa *tcxa;       // persist == 4: one per register pass
     int *err_flag;          // persist >= 2: raised by a kernel whose bounded wait ran out
     int win_bits;
     int threads;
@@ -157,5 +169,7 @@ BrickHostPlan make_brick_plan(int n, int l, int tile_bits, int low_bits, int win
 // Tensor-core window tables (one per register pass) of a plan with kTcTile-bit
 // tiles and kMaxWin-bit windows.
 std::vector<TcWin> make_tc_windows(const BrickHostPlan &P);
+// Per-thread exchange address tables of those windows (one per register pass).
+std::vector<TcXa> make_tc_xaddr(const BrickHostPlan &P, const std::vector<TcWin> &W);
 
 }  // namespace fpk

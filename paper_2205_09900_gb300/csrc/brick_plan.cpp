@@ -404,4 +404,38 @@ std::vector<TcWin> make_tc_windows(const BrickHostPlan &P) {
     return out;
 }
 
+std::vector<TcXa> make_tc_xaddr(const BrickHostPlan &P, const std::vector<TcWin> &W) {
+    std::vector<TcXa> out(P.rpasses.size());
+    for (const BrickPass &ps : P.passes)
+        for (int w = 0; w < ps.n_rp; ++w) {
+            const TcWin &cw = W[ps.rp_off + w];
+            TcXa &x = out[ps.rp_off + w];
+            std::memset(&x, 0, sizeof x);
+            const bool last = w + 1 == ps.n_rp;
+            const uint32_t *lm = cw.xcb, *sm = last ? nullptr : W[ps.rp_off + w + 1].xcb;
+            for (int l = 0; l < 32; ++l)
+                for (int t = 0; t < 5; ++t)
+                    if ((l >> t) & 1) {
+                        x.ld_lane[l] ^= lm[cw.row[t]];
+                        if (sm) x.st_lane[l] ^= sm[cw.row[t]];
+                    }
+            for (int wp = 0; wp < 8; ++wp) {
+                for (int t = 5; t < kTcRows; ++t)
+                    if (((wp & 3) >> (t - 5)) & 1) {
+                        x.ld_warp[wp] ^= lm[cw.row[t]];
+                        if (sm) x.st_warp[wp] ^= sm[cw.row[t]];
+                    }
+                if (wp >> 2) {
+                    x.ld_warp[wp] ^= lm[cw.win[4]];
+                    if (sm) x.st_warp[wp] ^= sm[cw.win[4]];
+                }
+            }
+            for (int k = 0; k < 4; ++k) {
+                x.ld_c[k] = lm[cw.win[k]];
+                if (sm) x.st_c[k] = sm[cw.win[k]];
+            }
+        }
+    return out;
+}
+
 }  // namespace fpk

@@ -453,32 +453,27 @@ __device__ __forceinline__ void issue_tile_mmas_tm(uint32_t tm, uint32_t sW) {
         }
 }
 
-// Exchange address of this thread's element u of a [128 x 32] view (row r =
-// 32 (warp mod 4) + lane, window index 16 (warp / 4) + u) through the map cb,
-// with the row and window bits of window cw: base ^ the contributions of u.
+// A thread's exchange addresses for one window and direction, from the
+// window's table (TcXa): element u at base ^ (c[k] of the set bits k of u)
 struct XchAddr {
     uint32_t base, c0, c1, c2, c3;
-    __device__ __forceinline__ XchAddr(const uint32_t *cb, const TcWin &cw, uint32_t r, uint32_t half) {
-        base = 0;
-#pragma unroll
-        for (int t = 0; t < kTcRows; ++t)
-            if ((r >> t) & 1u) base ^= cb[cw.row[t]];
-        if (half) base ^= cb[cw.win[4]];
-        c0 = cb[cw.win[0]]; c1 = cb[cw.win[1]]; c2 = cb[cw.win[2]]; c3 = cb[cw.win[3]];
+    __device__ __forceinline__ XchAddr(const uint32_t *lane_t, const uint32_t *warp_t, const uint32_t *c) {
+        const int warp = (threadIdx.x >> 5) & 7, lane = threadIdx.x & 31;   // warp within its group of 8
+        base = __ldg(lane_t + lane) ^ __ldg(warp_t + warp);
+        const uint4 cc = __ldg(reinterpret_cast<const uint4 *>(c));
+        c0 = cc.x; c1 = cc.y; c2 = cc.z; c3 = cc.w;
     }
     __device__ __forceinline__ uint32_t at(int u) const {
         return base ^ ((u & 1) ? c0 : 0u) ^ ((u & 2) ? c1 : 0u) ^ ((u & 4) ? c2 : 0u) ^ ((u & 8) ? c3 : 0u);
     }
 };
 
-// This thread's operand row of window cw: exchange buffer -> TF32 high and low
-// parts -> tensor memory (lanes 32 (warp mod 4) .., columns 64 / 128 + 32 (warp / 4) ..).
+// This thread's operand row (lanes 32 (warp mod 4) .., columns 64 / 128 + 32 (warp / 4) ..
+// of tensor memory) from the exchange buffer, split into TF32 high and low parts.
 // All 16 loads are in flight at once; the parts go out in two halves of 16 columns.
-__device__ __forceinline__ void tm_load_operand(uint32_t tm, const TcWin &cw, uint32_t xs) {
-    const int warp = (threadIdx.x >> 5) & 7, lane = threadIdx.x & 31;   // warp within its group of 8
-    const uint32_t r = 32u * (warp & 3) + lane, half = (uint32_t)(warp >> 2);
-    const XchAddr xa(cw.xcb, cw, r, half);
-    const uint32_t ta = tm + ((32u * (warp & 3)) << 16) + 32u * half;
+__device__ __forceinline__ void tm_load_operand(uint32_t tm, const XchAddr &xa, uint32_t xs) {
+    const int warp = (threadIdx.x >> 5) & 7;   // warp within its group of 8
+    const uint32_t ta = tm + ((32u * (warp & 3)) << 16) + 32u * (uint32_t)(warp >> 2);
     uint32_t h[32];
 #pragma unroll
     for (int u = 0; u < 16; ++u)
@@ -505,13 +500,11 @@ __device__ __forceinline__ void tm_load_operand(uint32_t tm, const TcWin &cw, ui
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// This thread's 16 results of window cw (D row r, window outputs 16 (warp / 4) ..)
-// into the exchange buffer through map cb (the next window's xcb)
-__device__ __forceinline__ void tm_store_result(uint32_t tm, const TcWin &cw, const uint32_t *cb, uint32_t xs) {
-    const int warp = (threadIdx.x >> 5) & 7, lane = threadIdx.x & 31;   // warp within its group of 8
-    const uint32_t r = 32u * (warp & 3) + lane, half = (uint32_t)(warp >> 2);
-    const uint32_t ta = tm + ((32u * (warp & 3)) << 16) + 32u * half;
-    const XchAddr xa(cb, cw, r, half);
+// This thread's 16 results (D row 32 (warp mod 4) + lane, window outputs 16 (warp / 4) ..)
+// into the exchange buffer
+__device__ __forceinline__ void tm_store_result(uint32_t tm, const XchAddr &xa, uint32_t xs) {
+    const int warp = (threadIdx.x >> 5) & 7;   // warp within its group of 8
+    const uint32_t ta = tm + ((32u * (warp & 3)) << 16) + 32u * (uint32_t)(warp >> 2);
     // two halves of 16 columns: the second half's read is in flight while the first is stored
     uint32_t v[16], y[16];
     asm volatile(
@@ -538,14 +531,10 @@ __device__ __forceinline__ void tm_store_result(uint32_t tm, const TcWin &cw, co
                      : "memory");
 }
 
-// Tiles t = blockIdx.x, + gridDim.x, ... < ntiles (tile t: pair t >> (N - 12),
-// tile index t mod 2^(N - 12)).  Counters run over the CTA's tiles: g =
-// windows (phases of afull, wfull, dfull), x = exchanges (phases of xbar;
-// exchange x uses buffer x mod 2: a tile's input, then its windows' results).
 __global__ void __launch_bounds__(kTcmDrain + 32, 2)
     brick_tcm_pass_kernel(BrickDev d, int side, BrickPass ps, const TcWin *__restrict__ wins,
-                          const float *__restrict__ wm, float2 *__restrict__ states, int *err, uint64_t wait_ns,
-                          uint32_t ntiles) {
+                          const TcXa *__restrict__ xat, const float *__restrict__ wm, float2 *__restrict__ states,
+                          int *err, uint64_t wait_ns, uint32_t ntiles) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t wfull, dfull, afull, xbar, fbar;
     __shared__ uint32_t taddr_sh;
@@ -687,7 +676,10 @@ __global__ void __launch_bounds__(kTcmDrain + 32, 2)
             uint32_t xs = sbase + (x & 1u) * kXch;
             asm volatile("cp.async.wait_group 0;" ::: "memory");
             if (!exchange(x)) break;
-            tm_load_operand(taddr, sw[0], xs);
+            {
+                const TcXa &xa = xat[ps.rp_off];
+                tm_load_operand(taddr, XchAddr(xa.ld_lane, xa.ld_warp, xa.ld_c), xs);
+            }
             operand_ready();
             // exchange x (now the next tile's input) goes to the buffer whose last
             // loads (exchange x - 2) every drain warp finished before exchange x - 1
@@ -702,9 +694,10 @@ __global__ void __launch_bounds__(kTcmDrain + 32, 2)
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 if (w + 1 < nw) {
                     xs = sbase + (x & 1u) * kXch;
-                    tm_store_result(taddr, sw[w], sw[w + 1].xcb, xs);
+                    const TcXa &xa = xat[ps.rp_off + w], &xn = xat[ps.rp_off + w + 1];
+                    tm_store_result(taddr, XchAddr(xa.st_lane, xa.st_warp, xa.st_c), xs);
                     if (!exchange(x)) { stop = true; break; }
-                    tm_load_operand(taddr, sw[w + 1], xs);
+                    tm_load_operand(taddr, XchAddr(xn.ld_lane, xn.ld_warp, xn.ld_c), xs);
                     operand_ready();
                     if (w + 2 == nw && tn < ntiles) load_tile(tn, sbase + (x & 1u) * kXch, 0, kPer);
                 } else {
@@ -758,8 +751,8 @@ cudaError_t run_passes_tc(const BrickDev &d, const BrickPass *hpasses, const Bri
             if (tm) {   // two CTAs per SM
                 const uint32_t ntiles = (uint32_t)npairs << (d.N - kTcTile);
                 const uint32_t grid = std::min<uint32_t>(ntiles, 2u * (uint32_t)sms);
-                brick_tcm_pass_kernel<<<grid, kTcmDrain + 32, kTcmSmem, st>>>(d, side, ps, dp.tcwins, wm, states, err,
-                                                                              wait_limit_ns(), ntiles);
+                brick_tcm_pass_kernel<<<grid, kTcmDrain + 32, kTcmSmem, st>>>(d, side, ps, dp.tcwins, dp.tcxa, wm,
+                                                                              states, err, wait_limit_ns(), ntiles);
             } else {
                 brick_tc1_pass_kernel<<<dim3(1u << (d.N - kTcTile), npairs), kTc1Drain + 32, kTc1Smem, st>>>(
                     d, side, ps, dp.tcwins, wm, states, err, wait_limit_ns());

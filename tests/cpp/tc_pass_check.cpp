@@ -71,7 +71,8 @@ int main(int argc, char **argv) {
     // "tcm": the tensor-memory operand form (brick_tcm_pass_kernel): every window's input
     // through the shared-memory exchange buffer (TcWin::xcb) into a [128 x 32] complex
     // operand held by 8 warps x 32 lanes x 16 window indices, results stored back by
-    // the same threads into the next window's exchange buffer
+    // the same threads into the next window's exchange buffer; every address also
+    // recomputed from the per-thread tables (TcXa) the kernel reads
     const bool tcm = argc > 3 && std::string(argv[3]) == "tcm";
     BrickHostPlan P = make_brick_plan(n, l, kTcTile, 3, kMaxWin, 0);   // the plan the tensor-core pass runs
     const BrickDev &d = P.dev;
@@ -79,6 +80,7 @@ int main(int argc, char **argv) {
     const uint32_t S = 1u << N;
     CHECK(d.tile_bits == kTcTile && N >= kTcTile + 1, "plan is not tiled with %d-bit tiles", kTcTile);
     std::vector<TcWin> W = make_tc_windows(P);
+    std::vector<TcXa> XA = make_tc_xaddr(P, W);   // the tensor-memory kernel's per-thread tables
     std::mt19937_64 rng(1000 * n + l);
     std::normal_distribution<double> N01;
     // random unitary maps (Gram-Schmidt on complex Gaussian columns): norms stay 1 over the sweep
@@ -200,6 +202,11 @@ int main(int argc, char **argv) {
                                     for (int q = 0; q < 16; ++q) {
                                         const uint32_t r = 32u * (warp & 3) + 16u * h + q, j = 16u * (warp >> 2) + u;
                                         ad[q] = xaddr(cw.xcb, cw.row, r, cw.win, j);
+                                        const TcXa &xa = XA[ps.rp_off + w];
+                                        uint32_t tab = xa.ld_lane[16 * h + q] ^ xa.ld_warp[warp];
+                                        for (int k = 0; k < 4; ++k)
+                                            if ((u >> k) & 1) tab ^= xa.ld_c[k];
+                                        CHECK(tab == ad[q], "window %d: load table differs from the map", w);
                                         const cd x = X[(ad[q] / 8) & 4095];
                                         Ar[r * 64 + 2 * j] = x.real();
                                         Ar[r * 64 + 2 * j + 1] = x.imag();
@@ -230,6 +237,11 @@ int main(int argc, char **argv) {
                                         } else {
                                             const TcWin &nx = W[ps.rp_off + w + 1];
                                             ad[q] = xaddr(nx.xcb, cw.row, r, cw.win, o);
+                                            const TcXa &xa = XA[ps.rp_off + w];
+                                            uint32_t tab = xa.st_lane[16 * h + q] ^ xa.st_warp[warp];
+                                            for (int k = 0; k < 4; ++k)
+                                                if ((u >> k) & 1) tab ^= xa.st_c[k];
+                                            CHECK(tab == ad[q], "window %d: store table differs from the map", w);
                                             CHECK(ad[q] < 32768 && ad[q] % 8 == 0, "exchange address %u", ad[q]);
                                             X2[(ad[q] / 8) & 4095] = y;
                                             hit[(ad[q] / 8) & 4095]++;
