@@ -54,15 +54,19 @@ __device__ __forceinline__ uint64_t gtimer() {
 }
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Wait for the phase of parity `phase` to complete, at most limit_ns.  The
+// try_wait carries a suspend-time hint: the thread is parked until the phase
+// completes (or the hint runs out) instead of spinning, so waiting warps take
+// no issue slots from the working ones.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, uint64_t limit_ns) {
     const uint64_t t0 = gtimer();
     for (;;) {
         uint32_t d;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(d)
-            : "r"(mbar), "r"(phase)
+            : "r"(mbar), "r"(phase), "r"(1000000u)
             : "memory");
         if (d) return true;
         if (gtimer() - t0 > limit_ns) return false;
