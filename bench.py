@@ -482,7 +482,7 @@ def measure_peaks(fp):
 TRAFFIC_L10 = {
     "13 5 256 0": ("brick_pass_kernel<float2,13,5,256>", 538.275328e6, 479.907328e6,
                    "profiles/brick_pass_kernel_f32_brickwork_n50_l10.md"),
-    "12 5 256 4": ("brick_tcm_pass_kernel", 589.198848e6, 481.595136e6,
+    "12 5 256 4": ("brick_tcm_pass_kernel", 587.271680e6, 481.361664e6,
                    "profiles/brick_tcm_pass_kernel_brickwork_n50_l10.md"),
 }
 
