@@ -95,12 +95,20 @@ typedef enum { FP_PARALLEL = 0, FP_LOCAL = 1, FP_HEA = 2, FP_HEA_PAULI = 3 } fp_
  * |Tr|^{2k} powers and all Monte Carlo moments are FP64 in every mode. */
 typedef enum {
     FP_PREC_FP64 = 0,         /* boundary tensors and gate maps in FP64 */
-    FP_PREC_FP32 = 1,         /* boundary tensors and gate maps in FP32 (FFMA),
-                                 FP64 meet and reduction; a pair whose
+    FP_PREC_FP32 = 1,         /* boundary tensors and gate maps in FP32, FP64 meet
+                                 and reduction; the brickwork autotuner takes the
+                                 faster of the FFMA tile passes and the TF32 x 3
+                                 tensor-core passes per depth; a pair whose
                                  estimated error exceeds fp32_tol, or whose
                                  cancellation ratio exceeds kappa_max, is
                                  recontracted in FP64 */
-    FP_PREC_FP32_RAW = 2      /* FP32 as above without the FP64 recontraction */
+    FP_PREC_FP32_RAW = 2,     /* FP32 as above without the FP64 recontraction */
+    FP_PREC_TF32X3 = 3        /* FP_PREC_FP32 with the brickwork tile passes on the
+                                 tensor cores wherever they apply (12-bit tiles,
+                                 boundaries of 2^14 amplitudes and more: brickwork
+                                 l >= 8, HEA L >= 8): window matrices applied by
+                                 three TF32 products with FP32 accumulation; the
+                                 FP32 path elsewhere */
 } fp_prec;
 
 enum {
@@ -369,8 +377,9 @@ fp_status fp_set_wait_limit_ns(uint64_t ns);
  * tile's operand in shared memory, 4: tensor-core passes with the tile's
  * operand in tensor memory, persistent over the tiles).  The autotuner
  * chooses it the first time the ensemble contracts that depth at that
- * precision (FP_PREC_FP32 and FP_PREC_FP32_RAW share one choice); before that
- * the call returns FP_ERR_ARG.  `out` is a host array of 4 int32. */
+ * precision (FP_PREC_FP32 and FP_PREC_FP32_RAW share one choice,
+ * FP_PREC_TF32X3 has its own); before that the call returns FP_ERR_ARG.  `out`
+ * is a host array of 4 int32. */
 fp_status fp_brick_variant(const fp_ensemble *ens, int32_t depth, int32_t precision, int32_t *out);
 
 /* Copy the ensemble's kernel counters into *out; reset them if `reset`. */

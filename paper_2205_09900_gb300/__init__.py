@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfp_gb300.so")
 
 PARALLEL, LOCAL, HEA, HEA_PAULI = 0, 1, 2, 3
-PREC_FP64, PREC_FP32, PREC_FP32_RAW = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_FP32_RAW, PREC_TF32X3 = 0, 1, 2, 3
 FLAG_SELF_PAIR, FLAG_DIAGONAL_GATES, FLAG_GENERIC_ONLY, FLAG_TIMING, FLAG_NO_GRAPHS = 1, 2, 4, 8, 16
 FLAG_SKIP_INFEASIBLE, FLAG_HEA_CZ = 32, 64
 K_SAMPLE, K_MERGE, K_TABLES, K_SWEEP, K_BRICK, K_MOMENTS, K_BOOTSTRAP, K_SPIRAL, K_CLASSES = 0, 1, 2, 3, 4, 5, 6, 7, 8

@@ -145,7 +145,7 @@ struct fp_ensemble {
     uint64_t kst_requeued = 0;
     bool timing = false;
     // brickwork fast path
-    std::map<int, std::unique_ptr<BrickCache>> brick_plans;   // key 2*l + fp32
+    std::map<int, std::unique_ptr<BrickCache>> brick_plans;   // key brick_key(l, prec)
     // spiral sweep (the paper's HEA), per depth; null: the depth is not spiral-shaped
     std::map<int, std::unique_ptr<SpiralCache>> spiral_plans;
     DBuf d_spiral_scratch;
@@ -519,6 +519,12 @@ fp_status check_flag(fp_ensemble *E) {
     return fail(FP_ERR_TIMEOUT, "a bounded device wait ran out in the tensor-core tile pass (results discarded)");
 }
 
+// The brickwork plan cache's key: depth and precision class (FP64; FP32 with the
+// autotuner's free choice; FP32 restricted to the tensor-core passes).
+int brick_key(int l, int prec) {
+    return 4 * l + (prec == FP_PREC_FP64 ? 0 : prec == FP_PREC_TF32X3 ? 2 : 1);
+}
+
 fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int TH, int persist,
                            std::unique_ptr<BrickCache> &out) {
     auto bc = std::make_unique<BrickCache>();
@@ -570,10 +576,11 @@ fp_status make_brick_cache(fp_ensemble *E, int l, bool fp32, int K, int R, int T
 // each variant's init + passes + meet), keep the fastest.  Results persist in
 // the file named by FP_AUTOTUNE_CACHE (if set), keyed by GPU name, n, l and
 // precision.
-fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx, int l, bool fp32) {
+fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> &idx, int l, int prec) {
     const fp_ensemble_desc &d = E->d;
     const int N = 2 * (l - 1);
-    const int key = l * 2 + (fp32 ? 1 : 0);
+    const bool fp32 = prec != FP_PREC_FP64;
+    const int key = brick_key(l, prec);
     struct Cand { int K, R, TH, P; };
     // K = 99: whole boundary in one CTA's shared memory (brick_smem_kernel);
     // P = 1: persistent double-buffered tile passes (brick_pass_db_kernel)
@@ -584,13 +591,15 @@ fp_status tune_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t>
     if (((size_t)1 << N) * (fp32 ? sizeof(float2) : sizeof(double2)) <= (size_t)200 * 1024) cands.push_back({99, 0, 0, 0});
     // P = 3, 4: tensor-core windows (TF32 x 3 tcgen05 MMAs), boundaries of more than two 12-bit tiles
     if (fp32 && N >= kTcTile + 2) {
+        if (prec == FP_PREC_TF32X3) cands.clear();     // tensor-core passes only
         cands.push_back({kTcTile, kMaxWin, 256, 3});   // the tile's operand in shared memory
         cands.push_back({kTcTile, kMaxWin, 256, 4});   // in tensor memory, persistent over the tiles
     }
     const int kmin = 10;   // boundaries up to 2^10: shared-memory sweep, nothing to tune
     char ckey[256];
     // the HEA's ring has its own plans: its entries carry the kind after the precision
-    snprintf(ckey, sizeof ckey, "%s n=%d l=%d %s%s", E->gpu_name.c_str(), d.n, l, fp32 ? "fp32" : "fp64",
+    snprintf(ckey, sizeof ckey, "%s n=%d l=%d %s%s", E->gpu_name.c_str(), d.n, l,
+             !fp32 ? "fp64" : (prec == FP_PREC_TF32X3 && N >= kTcTile + 2) ? "tf32x3" : "fp32",
              d.kind == FP_HEA ? " hea" : "");
     int bestK = cands[0].K, bestR = cands[0].R, bestT = cands[0].TH, bestP = 0;
     bool have = false;
@@ -691,10 +700,10 @@ fp_status run_brick(fp_ensemble *E, uint64_t first, const std::vector<uint64_t> 
     const int N = 2 * (l - 1);
     if (N > FP_MAX_STATE_BITS)
         return fail(FP_ERR_INFEASIBLE, "depth %d: boundary of %d bits exceeds the limit of %d", l, N, FP_MAX_STATE_BITS);
-    const int key = l * 2 + (fp32 ? 1 : 0);
+    const int key = brick_key(l, prec);
     auto it = E->brick_plans.find(key);
     if (it == E->brick_plans.end()) {
-        fp_status s = tune_brick(E, first, idx, l, fp32);
+        fp_status s = tune_brick(E, first, idx, l, prec);
         if (s != FP_OK) return s;
         it = E->brick_plans.find(key);
     }
@@ -1067,7 +1076,8 @@ fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec,
             E->d_skip.as<uint64_t>(), E->skipped.size(), tr, kap, err);
         CK(cudaGetLastError());
     }
-    if (prec == FP_PREC_FP32 || max_kappa) {
+    const bool policy = prec == FP_PREC_FP32 || prec == FP_PREC_TF32X3;   // FP64 recontraction of flagged pairs
+    if (policy || max_kappa) {
         std::vector<double> k(count), e(count);
         CK(cudaMemcpyAsync(k.data(), kap, count * sizeof(double), cudaMemcpyDeviceToHost, E->st));
         CK(cudaMemcpyAsync(e.data(), err, count * sizeof(double), cudaMemcpyDeviceToHost, E->st));
@@ -1077,7 +1087,7 @@ fp_status trace_device(fp_ensemble *E, uint64_t first, uint64_t count, int prec,
         for (uint64_t i = 0; i < count; ++i) {
             if (max_kappa && std::isfinite(k[i])) *max_kappa = std::max(*max_kappa, k[i]);
             const bool over = !(e[i] <= tol) || (d.kappa_max > 0 && !(k[i] <= d.kappa_max));
-            if (prec == FP_PREC_FP32 && over && !skipped[i]) redo.push_back(i);
+            if (policy && over && !skipped[i]) redo.push_back(i);
         }
         if (!redo.empty()) {
             if (requeued) *requeued += redo.size();
@@ -1242,7 +1252,7 @@ fp_status fp_export_gates(fp_ensemble *ens, uint64_t pair, int32_t which, void *
 fp_status fp_trace_batch(fp_ensemble *ens, uint64_t first, uint64_t count, int32_t prec, double *tr,
                          double *kappa, double *err, int32_t *group) {
     if (!ens || (!tr && count)) return fail(FP_ERR_ARG, "null argument");
-    if (prec < FP_PREC_FP64 || prec > FP_PREC_FP32_RAW) return fail(FP_ERR_ARG, "unknown precision %d", prec);
+    if (prec < FP_PREC_FP64 || prec > FP_PREC_TF32X3) return fail(FP_ERR_ARG, "unknown precision %d", prec);
     if (count == 0) return FP_OK;
     fp_status s = trace_device(ens, first, count, prec, nullptr, nullptr, nullptr);
     if (s != FP_OK) return s;
@@ -1323,7 +1333,7 @@ fp_status fp_frame_potential_resume(fp_ensemble *ens, fp_checkpoint *ck, uint64_
                                     double *stderr_) {
     if (!ens || !ck || !ck->sums || !F || !stderr_) return fail(FP_ERR_ARG, "null argument");
     if (k_max < 1 || k_max > FP_MAX_KMAX) return fail(FP_ERR_ARG, "k_max = %d outside [1, %d]", k_max, FP_MAX_KMAX);
-    if (prec < FP_PREC_FP64 || prec > FP_PREC_FP32_RAW) return fail(FP_ERR_ARG, "unknown precision %d", prec);
+    if (prec < FP_PREC_FP64 || prec > FP_PREC_TF32X3) return fail(FP_ERR_ARG, "unknown precision %d", prec);
     const int ng = ens->n_groups, nv = 2 * k_max + 1;
     if (ck->next_batch == 0) {   // first call of a run
         ck->k_max = k_max;
@@ -1439,9 +1449,8 @@ fp_status fp_set_wait_limit_ns(uint64_t ns) {
 
 fp_status fp_brick_variant(const fp_ensemble *ens, int32_t depth, int32_t precision, int32_t *out) {
     if (!ens || !out) return fail(FP_ERR_ARG, "null argument");
-    if (precision != FP_PREC_FP64 && precision != FP_PREC_FP32 && precision != FP_PREC_FP32_RAW)
-        return fail(FP_ERR_ARG, "unknown precision %d", precision);
-    auto it = ens->brick_plans.find(depth * 2 + (precision != FP_PREC_FP64 ? 1 : 0));
+    if (precision < FP_PREC_FP64 || precision > FP_PREC_TF32X3) return fail(FP_ERR_ARG, "unknown precision %d", precision);
+    auto it = ens->brick_plans.find(brick_key(depth, precision));
     if (it == ens->brick_plans.end())
         return fail(FP_ERR_ARG, "no brickwork sweep of depth %d at this precision has run on this ensemble", depth);
     for (int i = 0; i < 4; ++i) out[i] = it->second->variant[i];

@@ -48,20 +48,27 @@ def test_tc_pass_matches_fp64(fp, n, variant, tmp_path, monkeypatch):
         ens.close()
 
 
+PICKS = {8: 3, 9: 5, 10: 7}   # one pair of each deep depth of the benchmark ensemble
+
+
+def _oracle_refs():
+    # computed once per session (about a minute of CPU at l = 10)
+    import concurrent.futures as cf
+    if not _ORACLE:
+        with cf.ThreadPoolExecutor(max_workers=3) as ex:
+            futs = {l: ex.submit(lambda l=l: O.trace_batch(O.desc(O.PARALLEL, 50, l, seed=80 + l), PICKS[l], 1,
+                                                           "ve")[0]) for l in PICKS}
+            for l, f in futs.items():
+                _ORACLE[l] = f.result()
+    return _ORACLE
+
+
 @pytest.mark.parametrize("variant", [TC1, TCM])
 def test_tc_pass_matches_oracle_n50(fp, variant, tmp_path, monkeypatch):
     # one pair of each deep depth of the benchmark ensemble against the oracle
-    import concurrent.futures as cf
     _force(tmp_path, monkeypatch, 50, (8, 9, 10), variant)
-    picks = {8: 3, 9: 5, 10: 7}
-    if not _ORACLE:   # computed once for both variants (about a minute of CPU at l = 10)
-        with cf.ThreadPoolExecutor(max_workers=3) as ex:
-            futs = {l: ex.submit(lambda l=l: O.trace_batch(O.desc(O.PARALLEL, 50, l, seed=80 + l), picks[l], 1,
-                                                           "ve")[0]) for l in picks}
-            for l, f in futs.items():
-                _ORACLE[l] = f.result()
-    refs = _ORACLE
-    for l, p in picks.items():
+    refs = _oracle_refs()
+    for l, p in PICKS.items():
         ens = fp.Ensemble(fp.PARALLEL, 50, l, l, seed=80 + l)
         t32, _, _ = ens.trace_batch(p, 1, fp.PREC_FP32)
         assert abs(t32[0] - refs[l]) <= 1e-4, (l, t32[0], refs[l])
@@ -136,3 +143,26 @@ def test_tune_cache_entries_are_per_kind(fp, tmp_path, monkeypatch):
     assert brick.brick_variant(7, fp.PREC_FP32) == (12, 5, 128, 0)
     assert brick.brick_variant(8, fp.PREC_FP32) == (12, 5, 128, 0)
     brick.close()
+
+
+def test_tf32x3_precision_takes_the_tensor_cores(fp, tmp_path, monkeypatch):
+    # FP_PREC_TF32X3: the autotuner restricted to the tensor-core passes at l >= 8,
+    # the FMA passes below; the FP32 policy's results (within 1e-4 of FP64 and of
+    # the oracle); an unknown precision is refused
+    monkeypatch.setenv("FP_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    ens = fp.Ensemble(fp.PARALLEL, 50, 7, 10, seed=13)
+    t, _, g = ens.trace_batch(0, 40, fp.PREC_TF32X3)
+    t64, _, _ = ens.trace_batch(0, 40, fp.PREC_FP64)
+    assert np.abs(t - t64).max() <= 1e-4
+    for l in sorted(set(int(x) + 7 for x in g)):
+        kind = ens.brick_variant(l, fp.PREC_TF32X3)[3]
+        assert kind in ((3, 4) if l >= 8 else (0, 1)), (l, kind)
+    with pytest.raises(fp.FpError):
+        ens.trace_batch(0, 1, 4)
+    ens.close()
+    refs = _oracle_refs()
+    for l, p in PICKS.items():
+        e = fp.Ensemble(fp.PARALLEL, 50, l, l, seed=80 + l)
+        t, _, _ = e.trace_batch(p, 1, fp.PREC_TF32X3)
+        assert abs(t[0] - refs[l]) <= 1e-4, (l, t[0], refs[l])
+        e.close()

@@ -393,16 +393,18 @@ def test_graph_replay_matches_direct_launches(fp, l, prec, tmp_path, monkeypatch
 
 
 @pytest.mark.parametrize("variant", ["14 4 512 0", "14 5 256 0", "13 4 512 0", "13 4 256 0", "13 5 256 0",
-                                     "13 4 512 1", "13 5 256 1", "12 4 256 0", "12 5 128 0"])
+                                     "13 4 512 1", "13 5 256 1", "12 4 256 0", "12 5 128 0",
+                                     "12 5 256 3", "12 5 256 4"])
 def test_every_tile_variant_matches_fp64(fp, variant, tmp_path, monkeypatch):
     # Each tiled variant the autotuner can pick (tile bits, window bits, threads,
-    # persistent double-buffered), forced through the tuner's cache file, at the
-    # two deepest benchmark depths (and at l = 7, where a 12-bit tile is the
-    # whole ring); ragged batch (not a multiple of the grid).
+    # pass kind: FMA, persistent double-buffered FMA, tensor cores with the tile's
+    # operand in shared or in tensor memory), forced through the tuner's cache
+    # file, at the two deepest benchmark depths (and at l = 7, where a 12-bit tile
+    # is the whole ring, for the FMA passes); ragged batch (not a multiple of the grid).
     import torch
     cache = tmp_path / "tune.txt"
     name = torch.cuda.get_device_name(0)
-    depths = (7, 9, 10) if variant.startswith("12 ") else (9, 10)
+    depths = (7, 9, 10) if variant.startswith("12 ") and variant.endswith(" 0") else (9, 10)
     cache.write_text("".join(f"{name} n=30 l={l} fp32|{variant}\n" for l in depths))
     monkeypatch.setenv("FP_AUTOTUNE_CACHE", str(cache))
     for l in depths:
