@@ -31,60 +31,84 @@ __device__ __forceinline__ void gauss_pair(uint64_t seed, uint64_t pair, int w, 
 }
 
 // In place: the 16 Gaussian entries at g (row-major) become the Haar unitary.
+// Householder step k maps column k to (alpha, 0, ..) with alpha = -ph |col|,
+// ph = a_kk / |a_kk|; with v = col - alpha e_k, |v|^2 = 2 nrm (nrm + |a_kk|), so
+// the reflection I - f v v^H takes f = 1 / (nrm (nrm + |a_kk|)).  Only the
+// columns right of k change (column k becomes alpha e_k, the ones left of it
+// are already reduced); R's diagonal phase for k < 3 is then alpha / |alpha| =
+// -ph, and Q's columns are rotated by those phases (the phase fix).  The
+// first reflection is applied to the identity in closed form.
 __device__ void haar_qr(double2 *g) {
     double2 A[4][4];
 #pragma unroll
     for (int k = 0; k < 16; ++k) A[k / 4][k % 4] = g[k];
     double2 Q[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) Q[r][c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+    double2 dph[4];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         double nrm2 = 0;
 #pragma unroll
         for (int r = k; r < 4; ++r) nrm2 += A[r][k].x * A[r][k].x + A[r][k].y * A[r][k].y;
-        double nrm = sqrt(nrm2);
-        double a0 = hypot(A[k][k].x, A[k][k].y);
-        double2 ph = a0 > 0 ? make_double2(A[k][k].x / a0, A[k][k].y / a0) : make_double2(1.0, 0.0);
-        double2 alpha = make_double2(-ph.x * nrm, -ph.y * nrm);
+        const double a2 = A[k][k].x * A[k][k].x + A[k][k].y * A[k][k].y;
+        const double ia = a2 > 0 ? rsqrt(a2) : 0.0, a0 = a2 * ia;   // |a_kk|
+        const double2 ph = a2 > 0 ? make_double2(A[k][k].x * ia, A[k][k].y * ia) : make_double2(1.0, 0.0);
+        const double nrm = sqrt(nrm2);
+        dph[k] = make_double2(-ph.x, -ph.y);
         double2 v[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) v[r] = r < k ? make_double2(0, 0) : A[r][k];
-        v[k].x -= alpha.x;
-        v[k].y -= alpha.y;
-        double vn2 = 0;
+        v[k].x += ph.x * nrm;
+        v[k].y += ph.y * nrm;
+        if (nrm == 0) {   // a zero column (probability 0): no reflection
+            if (k == 0)
 #pragma unroll
-        for (int r = k; r < 4; ++r) vn2 += v[r].x * v[r].x + v[r].y * v[r].y;
-        if (vn2 == 0) continue;
-        double f = 2.0 / vn2;
-        // A <- (I - f v v^H) A
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            double2 s = make_double2(0, 0);
-#pragma unroll
-            for (int r = k; r < 4; ++r) { double2 t = cmul(cconj(v[r]), A[r][c]); s.x += t.x; s.y += t.y; }
-#pragma unroll
-            for (int r = k; r < 4; ++r) { double2 t = cmul(v[r], s); A[r][c].x -= f * t.x; A[r][c].y -= f * t.y; }
+                    for (int c = 0; c < 4; ++c) Q[r][c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+            continue;
         }
-        // Q <- Q (I - f v v^H)
+        const double f = 1.0 / (nrm * (nrm + a0));
+        // A <- (I - f v v^H) A, columns k+1 .. 3
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            double2 s = make_double2(0, 0);
+        for (int c = k + 1; c < 4; ++c) {
+            double2 sv = make_double2(0, 0);
 #pragma unroll
-            for (int j = k; j < 4; ++j) { double2 t = cmul(Q[r][j], v[j]); s.x += t.x; s.y += t.y; }
+            for (int r = k; r < 4; ++r) { double2 t = cmul(cconj(v[r]), A[r][c]); sv.x += t.x; sv.y += t.y; }
+            sv.x *= f;
+            sv.y *= f;
 #pragma unroll
-            for (int j = k; j < 4; ++j) { double2 t = cmul(s, cconj(v[j])); Q[r][j].x -= f * t.x; Q[r][j].y -= f * t.y; }
+            for (int r = k; r < 4; ++r) { double2 t = cmul(v[r], sv); A[r][c].x -= t.x; A[r][c].y -= t.y; }
+        }
+        if (k == 0) {   // Q = I - f v v^H
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const double2 t = cmul(v[r], cconj(v[j]));
+                    Q[r][j] = make_double2((r == j ? 1.0 : 0.0) - f * t.x, -f * t.y);
+                }
+        } else {        // Q <- Q (I - f v v^H)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                double2 sv = make_double2(0, 0);
+#pragma unroll
+                for (int j = k; j < 4; ++j) { double2 t = cmul(Q[r][j], v[j]); sv.x += t.x; sv.y += t.y; }
+                sv.x *= f;
+                sv.y *= f;
+#pragma unroll
+                for (int j = k; j < 4; ++j) { double2 t = cmul(sv, cconj(v[j])); Q[r][j].x -= t.x; Q[r][j].y -= t.y; }
+            }
         }
     }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        double a = hypot(A[c][c].x, A[c][c].y);
-        double2 ph = a > 0 ? make_double2(A[c][c].x / a, A[c][c].y / a) : make_double2(1.0, 0.0);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) g[4 * r + c] = cmul(Q[r][c], ph);
+    {
+        const double a2 = A[3][3].x * A[3][3].x + A[3][3].y * A[3][3].y;
+        const double ia = a2 > 0 ? rsqrt(a2) : 0.0;
+        dph[3] = a2 > 0 ? make_double2(A[3][3].x * ia, A[3][3].y * ia) : make_double2(1.0, 0.0);
     }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) g[4 * r + c] = cmul(Q[r][c], dph[c]);
 }
 
 // Haar gates in two passes, so that the transcendental-heavy Gaussian draws
