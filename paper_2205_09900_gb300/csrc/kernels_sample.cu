@@ -2,9 +2,55 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "sample_tables.h"
 
 namespace fpk {
 namespace {
+
+// sinpi(t), cospi(t) for t in [0, 2) a multiple of 2^-52: t = k/256 + r exactly,
+// r in [0, 1/256); angle addition with the tabulated sinpi, cospi(k/256) and the
+// Taylor polynomials of sin and cos at x = pi r (|x| < 0.0123: the first omitted
+// terms, x^9/9! and x^10/10!, are below 2e-23).
+__device__ __forceinline__ void sincospi_tab(double t, double *sn, double *cs) {
+    const int k = (int)(t * 256.0);
+    const double r = t - (double)k * (1.0 / 256.0);
+    const double x = r * kPi, x2 = x * x;
+    const double sx = x * fma(x2, fma(x2, fma(x2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), 1.0);
+    const double cx = fma(x2, fma(x2, fma(x2, fma(x2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5), 1.0);
+    const double sk = __ldg(kSinCosPi + 2 * k), ck = __ldg(kSinCosPi + 2 * k + 1);
+    *sn = fma(sk, cx, ck * sx);
+    *cs = fma(ck, cx, -(sk * sx));
+}
+
+// log(u) for normal u in (0, 1]: u = m 2^e with m in [0.75, 1.5); with c_j the
+// nearest of the points 0.75 + j/128 and r_j the tabulated double near 1/c_j,
+// log u = e ln2 - log r_j + log1p(m r_j - 1), |m r_j - 1| <= 2^-7.4, log1p by its
+// series to y^9 (relative truncation below 1e-20); -log r_j and ln2 in two
+// parts.  At the point c = 1 (r = 1, log r = 0) y = m - 1 exactly, so log u keeps
+// its relative accuracy as u -> 1.
+__device__ __forceinline__ double log_tab(double u) {
+    const long long b = __double_as_longlong(u);
+    int e = (int)((b >> 52) & 0x7FF) - 1023;
+    double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+    if (m >= 1.5) {
+        m *= 0.5;
+        ++e;
+    }
+    const int j = __double2int_rn((m - 0.75) * 128.0);
+    const double r = __ldg(kLogTab + 3 * j), lh = __ldg(kLogTab + 3 * j + 1), ll = __ldg(kLogTab + 3 * j + 2);
+    const double y = fma(m, r, -1.0);
+    double p = fma(y, -1.0 / 9.0, 1.0 / 8.0);
+    p = fma(y, p, -1.0 / 7.0);
+    p = fma(y, p, 1.0 / 6.0);
+    p = fma(y, p, -1.0 / 5.0);
+    p = fma(y, p, 1.0 / 4.0);
+    p = fma(y, p, -1.0 / 3.0);
+    p = fma(y, p, 0.5);
+    p = fma(y, p, -1.0);
+    p = -(y * p);   // y - y^2/2 + y^3/3 - ... + y^9/9
+    const double ed = (double)e;
+    return fma(ed, kLn2Hi, lh) + (fma(ed, kLn2Lo, ll) + p);
+}
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -23,9 +69,9 @@ __device__ __forceinline__ void gauss_pair(uint64_t seed, uint64_t pair, int w, 
         uint64_t xa = x.x[2 * h], xb = x.x[2 * h + 1];
         double u1 = (double)((xa >> 11) + 1) * 0x1.0p-53;
         double u2 = (double)(xb >> 11) * 0x1.0p-53;
-        double rad = sqrt(-2.0 * log(u1)) * 0.70710678118654752440;
+        double rad = sqrt(-2.0 * log_tab(u1)) * 0.70710678118654752440;
         double s, c;
-        sincospi(2.0 * u2, &s, &c);
+        sincospi_tab(2.0 * u2, &s, &c);
         out[2 * j + h] = make_double2(rad * c, rad * s);
     }
 }
