@@ -200,13 +200,19 @@ template <typename C> struct MeetAcc;
 template <> struct MeetAcc<float2> {
     double sr = 0, si = 0;
     float sa = 0, s2 = 0;
+    float fr = 0, fi = 0;   // the current run of products, folded into sr, si by flush
     __device__ __forceinline__ void add(float2 l, float2 r) {
         const float px = fmaf(l.x, r.x, -l.y * r.y), py = fmaf(l.x, r.y, l.y * r.x);
         const float q = fmaf(px, px, py * py);
-        sr += (double)px;
-        si += (double)py;
+        fr += px;
+        fi += py;
         sa += sqrtf(q);
         s2 += q;
+    }
+    __device__ __forceinline__ void flush() {
+        sr += (double)fr;
+        si += (double)fi;
+        fr = fi = 0;
     }
 };
 template <> struct MeetAcc<double2> {
@@ -216,6 +222,7 @@ template <> struct MeetAcc<double2> {
         const double q = px * px + py * py;
         sr += px; si += py; sa += sqrt(q); s2 += q;
     }
+    __device__ __forceinline__ void flush() {}
 };
 
 __device__ __forceinline__ double wsum(double v) {
@@ -298,8 +305,16 @@ __global__ void __launch_bounds__(512) brick_smem_kernel(BrickDev d, const PairI
             sync();
         }
     }
-    MeetAcc<C> acc;
-    for (uint32_t w = tid; w < S; w += gt) acc.add(Lp[w], A[w]);
+    MeetAcc<C> acc;   // runs of 8 products summed in FP32 (FP32 states), then in FP64
+    int run = 0;
+    for (uint32_t w = tid; w < S; w += gt) {
+        acc.add(Lp[w], A[w]);
+        if (++run == 8) {
+            acc.flush();
+            run = 0;
+        }
+    }
+    acc.flush();
     double sr = acc.sr, si = acc.si, sa = (double)acc.sa, s2 = (double)acc.s2;
     sr = wsum(sr); si = wsum(si); sa = wsum(sa); s2 = wsum(s2);
     if (!warp_mode) {
@@ -682,8 +697,17 @@ __global__ void __launch_bounds__(1024) brick_dot_kernel(BrickDev d, const PairI
     __shared__ double red[4][32];
     const uint32_t S = 1u << d.N;
     const C *L = states + (size_t)blockIdx.x * 2 * S, *R = L + S;
+    // in FP32, the products of a thread's runs of 8 elements are summed first and
+    // each run's sum is added in FP64 (8 times fewer FP64 operations)
     MeetAcc<C> acc;
-    for (uint32_t w = threadIdx.x; w < S; w += blockDim.x) acc.add(L[w], R[w]);
+    for (uint32_t w0 = threadIdx.x; w0 < S; w0 += 8 * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t w = w0 + (uint32_t)k * blockDim.x;
+            if (w < S) acc.add(L[w], R[w]);
+        }
+        acc.flush();
+    }
     double sr = acc.sr, si = acc.si, sa = (double)acc.sa, s2 = (double)acc.s2;
     sr = wsum(sr); si = wsum(si); sa = wsum(sa); s2 = wsum(s2);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
