@@ -78,10 +78,11 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
            (2ull << 61);
 }
 
+// x rounded to the nearest TF32 value (10 mantissa bits), ties away from zero:
+// half of the dropped 13 bits' weight added to the magnitude, then those bits
+// cleared (finite x of moderate size, as the window matrices' entries are)
 __device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // ---------------------------------------------------------------------------
