@@ -168,10 +168,12 @@ __device__ __forceinline__ uint32_t tile_base_of(uint32_t t, uint32_t smask, int
 // bits (sign, exponent, 10 mantissa bits), so x itself serves as the high
 // part (read as x with its low 13 mantissa bits cleared, i.e. truncated) and
 // the rest x - trunc(x), exact in FP32 and of the same sign as x, rounded to
-// the nearest TF32 value (half away from zero) as the low part.  Left to the
-// MMA's truncation, the rest would lose up to 2^-10 of itself, always towards
-// zero: a bias of up to 2^-20 of x per window that adds up over the windows of
-// a sweep; rounded, the error is at most 2^-21 of x and of either sign.
+// the nearest TF32 value (half away from zero) as the low part.  The rest has
+// at most 13 significant bits, of which TF32 keeps 11: left to the MMA's
+// truncation it would lose up to 2^-21 of x, always towards zero (about
+// 0.9 x 2^-23 of x on average), a bias that adds up over the windows of a
+// sweep; rounded, the error is at most 2^-22 of x, and the ties that rounding
+// away from zero meets leave a mean of about 0.35 x 2^-23.
 __device__ __forceinline__ float tf32_rest(float x) {
     const float r = x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
     return __uint_as_float((__float_as_uint(r) + 0x1000u) & 0xFFFFE000u);
